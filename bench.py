@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""hPF-MD throughput on GB300: bead-steps/s of the 1M-bead A10B10 diblock melt.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  A "step" is one MD time step of the whole
+hot path: density scatter + field stencil at every field refresh (every 10
+steps), field gather, bonds and the Langevin velocity-Verlet update for every
+bead.  The state is resident in HBM before timing starts; L2 is flushed (a
+256 MB write) before every timed field period and the flush is outside the
+timed events.  With N > 1 (torchrun) every rank advances its own replica of
+the melt: replicas only, weak scaling, no data-path collective.
+
+--impl reference times the CPU oracle (plain C, FP64, int64 mesh) on the host
+cores, each step on a bounded sample of the same melt.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bead-steps/s, hPF-MD 1M beads, plain vs learned/batched at <=1e-3 force err"
+UNIT = "bead-steps/s"
+# Algorithmic HBM bytes of one bead-step of the unfused step (read + write of
+# the FP32 position and velocity, 48 B) plus the scatter, stencil and sort
+# traffic amortised over the refresh period (about 2 B at 1M beads, field
+# refresh every 10 steps): 50 B per bead-step.
+ALGO_BYTES_PER_BEAD_STEP = 50.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+STEP_SRC = os.path.join(ROOT, "paper_1310_2041_gb300", "csrc", "k_step.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="a10b10_1m")
+    ap.add_argument("--sort-every", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read only)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="hpf_clocks_", suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu),
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def traffic_record():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))["k_step"]
+    except (OSError, KeyError, ValueError):
+        return None
+    sha = hashlib.sha256(open(STEP_SRC, "rb").read()).hexdigest()
+    return rec if rec.get("source_sha256") == sha else None
+
+
+def cpu_oracle_rate(w, data, budget_s: float, max_chains: int | None = None):
+    """Oracle bead-steps/s on the first chains of the workload (full box and mesh)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    pp = w.params()
+    op = oracle.make_params(**pp)
+    n_chains_total = w.blocks[0][0]
+    clen = len(w.blocks[0][1])
+    # calibrate on 2 % of the chains, then size the sample to the budget
+    c0 = max(1, n_chains_total // 50)
+    n0 = c0 * clen
+    t = time.perf_counter()
+    oracle.run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
+               data["bonds"][: c0 * (clen - 1)], 0, 2)
+    per_bead_step = (time.perf_counter() - t) / (2 * n0)
+    steps = w.field_every
+    chains = int(min(n_chains_total, max(c0, budget_s / (per_bead_step * steps * clen))))
+    if max_chains:
+        chains = min(chains, max_chains)
+    n = chains * clen
+    t = time.perf_counter()
+    oracle.run(op, data["pos"][:n], data["vel"][:n], data["type"][:n],
+               data["bonds"][: chains * (clen - 1)], 0, steps)
+    dt = time.perf_counter() - t
+    return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} steps of the first {chains} of {n_chains_total} chains "
+                      f"({n} beads) in the full {w.box} box, mesh {w.mesh}^3"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1310_2041_gb300 import workloads as W
+    w = W.WORKLOADS[args.workload]()
+    data = W.generate(w)
+    oracle.build()
+    op = oracle.make_params(**w.params())
+    n_chains_total = w.blocks[0][0]
+    clen = len(w.blocks[0][1])
+    # calibrate, then size every step's sample so the run takes about 90 s
+    c0 = max(1, n_chains_total // 50)
+    n0 = c0 * clen
+    t = time.perf_counter()
+    oracle.run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
+               data["bonds"][: c0 * (clen - 1)], 0, 1)
+    per_bead_step = time.perf_counter() - t
+    per_bead_step /= n0
+    total = max(1, args.steps + args.warmup)
+    chains = int(min(n_chains_total, max(1, 90.0 / (total * per_bead_step * clen))))
+    n = chains * clen
+    pos, vel = data["pos"][:n].astype(np.float64), data["vel"][:n].astype(np.float64)
+    types, bonds = data["type"][:n], data["bonds"][: chains * (clen - 1)]
+    if args.warmup > 0:
+        pos, vel, _e = oracle.run(op, pos, vel, types, bonds, 0, args.warmup)
+    t = time.perf_counter()
+    pos, vel, _e = oracle.run(op, pos, vel, types, bonds, args.warmup, args.steps)
+    dt = time.perf_counter() - t
+    value = n * args.steps / dt
+    sample = (f"each step: one MD step (field refreshed every {w.field_every}) of the first "
+              f"{chains} of {n_chains_total} chains ({n} beads), full box and mesh")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_beads": w.n_beads, "sample_beads": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1310_2041_gb300 import hpf, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = W.WORKLOADS[args.workload]()
+    data = W.generate(w, seed=w.seed + rank)
+    pp = w.params()
+    pp["sort_every"] = args.sort_every
+    stream = torch.cuda.current_stream()
+    sysm = hpf.System(hpf.make_params(**pp), stream=stream)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
+    sysm.set_state(dev["pos"], dev["vel"], dev["type"], dev["bonds"])
+    fe = w.field_every
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # warm-up (untimed)
+    sysm.step(args.warmup)
+    torch.cuda.synchronize()
+    sysm.profile_read()
+
+    # timed region: K steps in field periods, L2 flushed before each period
+    chunks, left = [], args.steps
+    while left > 0:
+        c = min(fe - (args.warmup + args.steps - left) % fe, left)
+        chunks.append(c)
+        left -= c
+    starts = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    sysm.profile(True)
+    wall0 = time.perf_counter()
+    for c, a, b in zip(chunks, starts, ends):
+        flush.zero_()
+        a.record(stream)
+        sysm.step(c)
+        b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = sysm.profile_read()
+    sysm.profile(False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dev_ms = float(t_max.item())
+    value = w.n_beads * args.steps * world / (dev_ms * 1e-3)
+
+    # dominant kernel: the fused step kernel (one launch per field period)
+    step_ms, step_launches = prof["step"]
+    avg_launch_s = step_ms * 1e-3 / max(step_launches, 1)
+    bead_steps_per_launch = w.n_beads * args.steps / max(step_launches, 1)
+    achieved = ALGO_BYTES_PER_BEAD_STEP * bead_steps_per_launch / avg_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    tr = traffic_record()
+    traffic = None
+    if tr:
+        traffic = tr["dram_bytes_per_launch"] * bead_steps_per_launch / tr["bead_steps_per_launch"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": "k_step", "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
+                "avg_launch_us": avg_launch_s * 1e6,
+                "stage_ms": {k: round(v[0], 4) for k, v in prof.items()}}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state from pinned host memory, advances one step and reads the energies back
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(v).pin_memory() for k, v in data.items()}
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        sysm.set_state(host["pos"], host["vel"], host["type"], host["bonds"])
+        sysm.step(1)
+        sysm.energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sysm.set_state(host["pos"], host["vel"], host["type"], host["bonds"])
+            sysm.step(1)
+            sysm.energy()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": w.n_beads * args.e2e_steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 6 * 8,
+               "steps": args.e2e_steps,
+               "path": "hpf_set_state(pinned host) + hpf_step(1) + hpf_energy(host) per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w, data, budget_s=12.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "n_beads": w.n_beads, "mesh": w.mesh,
+                           "species": w.n_species, "field_every": fe,
+                           "sort_every": args.sort_every, "parallelism": f"replicas{world}",
+                           "l2": "flushed (256 MB write) before each timed field period",
+                           "wall_s": wall},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

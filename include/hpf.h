@@ -1,0 +1,190 @@
+/*
+ * hpf.h -- C ABI of the GB300 hybrid particle-field MD (hPF-MD / MD-SCF) library.
+ *
+ * One context simulates one periodic box of bead-spring polymers whose
+ * non-bonded interactions go through a density field, as in the MD-SCF
+ * section of Zhu et al., "GALAMOST: GPU-accelerated large-scale molecular
+ * simulation toolkit" (the external potential V_K, the force F_A = -dV_A/dr,
+ * Algorithm 1), with harmonic bonds (section "Bonded forces") and
+ * velocity-Verlet integration (section "Integration methods") plus a
+ * Langevin thermostat driven by Philox4x32-10 noise.
+ *
+ * Conventions that hold for every call:
+ *   - All arithmetic runs on the GPU, in kernels enqueued on the CUDA stream
+ *     given to hpf_init.  Calls return without waiting for the GPU unless a
+ *     call says it synchronises.
+ *   - Array arguments are plain pointers that may point to host memory
+ *     (pageable or pinned) or to device memory of the context's GPU; the
+ *     library copies through them with cudaMemcpyDefault.  The caller keeps
+ *     ownership; the library never retains a caller pointer after a call.
+ *   - Bead arrays are indexed by the bead tag 0 .. n_beads-1 (the caller's
+ *     order).  The library reorders beads internally; every output is
+ *     returned in tag order and no result depends on the internal order.
+ *   - Layouts are C order: positions, velocities, forces [n_beads][3] float32;
+ *     density [n_species][Mz][My][Mx] int64; field [n_species][Mz][My][Mx][4]
+ *     float32 = (dV/dx, dV/dy, dV/dz, V).
+ *   - Every call returns an hpf_status.  Nothing aborts the process.  The text
+ *     of the last failure of a context is kept until the next failure and is
+ *     returned by hpf_last_error.
+ */
+#ifndef HPF_H
+#define HPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPF_MAX_SPECIES 8
+#define HPF_FRAC_BITS 13              /* fixed-point bits of a CIC weight per axis */
+#define HPF_MAX_BEADS ((1 << 24) - 1) /* keeps the whole-mesh sum below 2^63 */
+
+typedef enum {
+    HPF_OK = 0,
+    HPF_ERR_INVALID = 1,   /* bad argument or parameter; nothing was changed */
+    HPF_ERR_CUDA = 2,      /* a CUDA runtime call failed; see hpf_last_error */
+    HPF_ERR_NOMEM = 3,     /* device allocation failed */
+    HPF_ERR_OVERFLOW = 4,  /* n_beads >= 2^24, or a bead left the +-2^18-cell range */
+    HPF_ERR_NONFINITE = 5, /* a position or velocity became NaN or infinite */
+    HPF_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+    HPF_ERR_STATE = 7      /* the call needs a state (hpf_set_state) first */
+} hpf_status;
+
+typedef struct hpf_ctx hpf_ctx;
+
+/* Physical and numerical parameters of one system. */
+typedef struct {
+    int32_t n_beads;      /* 0 .. HPF_MAX_BEADS */
+    int32_t n_species;    /* 1 .. HPF_MAX_SPECIES */
+    int32_t mesh[3];      /* density mesh Mx, My, Mz (>= 2 each) */
+    float box[3];         /* periodic box Lx, Ly, Lz; the mesh coordinate of x is
+                             fl32(x * fl32(M / L)) */
+    double kT;            /* thermal energy */
+    double rho0;          /* reference number density: phi_K = rho_K / rho0 */
+    double inv_kappa;     /* compressibility term 1/kappa of V_K (energy units) */
+    double chi[HPF_MAX_SPECIES * HPF_MAX_SPECIES]; /* chi_KK' in kT units, row K */
+    double bond_k;        /* U_bond = bond_k (r - bond_r0)^2 (no factor 1/2) */
+    double bond_r0;
+    double mass;          /* bead mass m */
+    double dt;            /* time step */
+    double gamma;         /* Langevin friction; 0 gives plain velocity-Verlet (NVE) */
+    uint64_t seed;        /* Philox key of the thermostat noise */
+    int32_t field_every;  /* refresh the density field when step % field_every == 0 */
+    int32_t sort_every;   /* re-sort beads every this many steps (0: only in hpf_set_state) */
+} hpf_params;
+
+/* Text for a status code (static storage). */
+const char* hpf_status_string(hpf_status s);
+
+/* Create a context: validate the parameters and allocate the device buffers
+ * (state, density mesh, field mesh, sort scratch).  `stream` is a
+ * cudaStream_t (NULL for the legacy default stream); all later work of the
+ * context is enqueued on it.  On failure *out is NULL.
+ * Errors: HPF_ERR_INVALID (bad parameter, out == NULL), HPF_ERR_OVERFLOW
+ * (n_beads > HPF_MAX_BEADS), HPF_ERR_NOMEM, HPF_ERR_CUDA. */
+hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out);
+
+/* Free a context and its device buffers (waits for its stream first). NULL is a no-op. */
+hpf_status hpf_destroy(hpf_ctx* ctx);
+
+/* Message of the context's last failure ("" if none).  Valid until the next call. */
+const char* hpf_last_error(const hpf_ctx* ctx);
+
+/* Load the bead state at step `step` and sort it for locality.
+ *   pos   [n][3] unwrapped positions x_n (the box is applied in mesh space)
+ *   vel   [n][3] half-step velocities v_{n-1/2} (see hpf_step)
+ *   type  [n]    species 0 .. n_species-1
+ *   bonds [n_bonds][2] bonded bead pairs.  The library stores chains
+ *         contiguously, so every bond must join consecutive tags (i, i+1) and
+ *         appear once (section "Bonded forces" stores partners per bead; this
+ *         library keeps only linear chains in tag order).
+ * Invalidates the density field: the next call that needs it recomputes it
+ * from these positions.  Synchronises the stream (validation result).
+ * Errors: HPF_ERR_INVALID (NULL array with n > 0, type out of range, bond not
+ * (i, i+1), duplicate bond, step < 0), HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
+hpf_status hpf_set_state(hpf_ctx* ctx, const float* pos, const float* vel, const int32_t* type,
+                         const int32_t* bonds, int64_t n_bonds, int64_t step);
+
+/* Copy the state out in tag order (either pointer may be NULL) and the step
+ * number.  Synchronises the stream.
+ * Errors: HPF_ERR_STATE, HPF_ERR_NONFINITE (state became non-finite), HPF_ERR_CUDA. */
+hpf_status hpf_get_state(hpf_ctx* ctx, float* pos, float* vel, int64_t* step);
+
+/* Cloud-in-cell density of the current positions (MD-SCF section; Algorithm 1,
+ * kernels 1-2): every bead adds w_x w_y w_z to the eight vertices of its cell,
+ * with per-axis fixed-point weights (2^13 - q, q), q = floor(2^13 frac(s)),
+ * s the mesh coordinate; one bead adds exactly 2^39.  Integer sums make the
+ * mesh independent of summation order.  The result stays in the context's
+ * mesh and is copied to D_out [n_species][Mz][My][Mx] int64 if D_out != NULL.
+ * Errors: HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_scatter_density(hpf_ctx* ctx, int64_t* D_out);
+
+/* Field of a density mesh (MD-SCF section, V_K equation; Algorithm 1, kernel 3):
+ *   phi_K = D_K 2^-39 / (rho0 h_x h_y h_z),
+ *   V_K   = kT sum_K' chi_KK' phi_K' + inv_kappa (sum_K phi_K - 1),
+ *   grad V_K by periodic central differences at the nodes.
+ * Uses D_in [n_species][Mz][My][Mx] if not NULL, else the context's mesh (the
+ * last hpf_scatter_density or field refresh).  The field becomes the frozen
+ * field of the current step; it is copied to field_out if not NULL.
+ * Errors: HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_field(hpf_ctx* ctx, const int64_t* D_in, float* field_out);
+
+#define HPF_FORCE_FIELD 1
+#define HPF_FORCE_BOND 2
+
+/* Conservative force on every bead at the current positions, in tag order:
+ * F_out [n][3] = (which & HPF_FORCE_FIELD ? -trilinear(grad V_T) : 0)
+ *              + (which & HPF_FORCE_BOND ? -2 k (r - r0) r_hat summed over bonds : 0).
+ * The field is the frozen field; if none is valid for the current step it is
+ * refreshed first (scatter + field).  No thermostat force.
+ * Errors: HPF_ERR_INVALID (which not in 1..3, F_out NULL with n > 0),
+ * HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
+
+/* Advance n_steps steps (asynchronous).  With v the stored half-step
+ * velocity, every step n does
+ *   F = F_field(x_n) + F_bond(x_n) - gamma m v + sqrt(2 gamma m kT / dt) xi
+ *   v <- v + dt F / m ;  x <- x + dt v
+ * which is velocity-Verlet with its two half kicks merged.  xi = three
+ * normals from Box-Muller on Philox4x32-10(counter = (tag, n lo, n hi, 0),
+ * key = (seed lo, seed hi)), uniforms u = (2 (r >> 9) + 1) 2^-24; x, y from
+ * (u0, u1) and z from (u2, u3).  The field is refreshed from the positions
+ * when n % field_every == 0 (or when no field is valid) and held fixed in
+ * between, as in the MD-SCF section.
+ * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
+
+/* Observables at the current step, reduced in FP64 (synchronises):
+ * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step),
+ * out[1] bond energy sum k (r - r0)^2, out[2] field energy
+ *   W = rho0 h^3 sum_nodes [1/2 kT sum_KK' chi phi_K phi_K' + 1/2 inv_kappa (sum phi - 1)^2]
+ *   of a fresh scatter of the current positions, out[3] = out[0]+out[1]+out[2],
+ * out[4] |total momentum| of v_n, out[5] kinetic temperature 2 KE / (3 N).
+ * Errors: HPF_ERR_INVALID (out NULL), HPF_ERR_STATE, HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
+hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
+
+/* Stage profiling.  Every kernel launch of a context is counted by stage;
+ * while profiling is enabled, CUDA events recorded on the context's stream
+ * around each stage also accumulate its device time. */
+#define HPF_STAGE_SCATTER 0 /* density scatter (+ mesh clear) */
+#define HPF_STAGE_FIELD 1   /* field stencil */
+#define HPF_STAGE_STEP 2    /* fused step kernel */
+#define HPF_STAGE_SORT 3    /* bead sort */
+#define HPF_STAGE_ENERGY 4  /* observables */
+#define HPF_STAGE_OTHER 5   /* state load / unload, force output */
+#define HPF_STAGE_COUNT 6
+
+/* Turn event timing on (1) or off (0).  Errors: HPF_ERR_INVALID. */
+hpf_status hpf_profile(hpf_ctx* ctx, int32_t enable);
+
+/* Device milliseconds and kernel launches per stage since the last read
+ * (either pointer may be NULL), then reset both.  Synchronises the stream.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_CUDA. */
+hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
+                            int64_t launches[HPF_STAGE_COUNT]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPF_H */

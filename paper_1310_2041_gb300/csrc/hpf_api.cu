@@ -1,0 +1,527 @@
+// hpf_api.cu -- the C ABI declared in include/hpf.h: context, state, schedule.
+#include <math.h>
+#include <string.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "hpf_internal.cuh"
+
+using namespace hpf;
+
+struct hpf_ctx {
+    hpf_params p;
+    cudaStream_t stream = nullptr;
+    int n = 0, S = 0;
+    MeshGeom geom{};
+    StepConsts sc{};
+    FieldCoef coef{};
+    EnergyConsts ec{};
+    float* state_mem = nullptr;     // 2 x 6 x n floats
+    StateBuf st[2]{};
+    int cur = 0;
+    uint32_t* meta = nullptr;
+    unsigned long long* D = nullptr;  // int64 density mesh
+    float4* G = nullptr;              // field mesh
+    float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
+    void* stage = nullptr;            // set_state input staging
+    int* dflag = nullptr;             // [0] kernel flags, [1..4] validation counters
+    int* hflag = nullptr;             // pinned mirror
+    double* partials = nullptr;
+    double* d_out6 = nullptr;
+    double* h_out6 = nullptr;         // pinned
+    bool has_state = false;
+    bool field_valid = false;
+    long long step = 0;
+    long long field_step = -1;
+    // profiling: kernel launches per stage, and event pairs while enabled
+    bool profiling = false;
+    long long launches[HPF_STAGE_COUNT] = {};
+    struct EvPair {
+        cudaEvent_t a, b;
+        int stage;
+    };
+    std::vector<EvPair> ev_used;
+    std::vector<cudaEvent_t> ev_free;
+    std::string err;
+};
+
+namespace {
+
+hpf_status fail(hpf_ctx* c, hpf_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                              \
+    } while (0)
+
+#define LAUNCH_CHECK(ctx)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), HPF_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_));     \
+    } while (0)
+
+cudaEvent_t take_event(hpf_ctx* c) {
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Counts the kernels of one stage and, while profiling, brackets them with
+// events on the context's stream.
+struct StageScope {
+    hpf_ctx* c;
+    int stage, kernels;
+    cudaEvent_t a = nullptr;
+    StageScope(hpf_ctx* c_, int stage_, int kernels_) : c(c_), stage(stage_), kernels(kernels_) {
+        if (c->profiling && (a = take_event(c)) != nullptr) cudaEventRecord(a, c->stream);
+    }
+    ~StageScope() {
+        c->launches[stage] += kernels;
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) return;
+        cudaEventRecord(b, c->stream);
+        c->ev_used.push_back({a, b, stage});
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy to a caller pointer; wait for the copy when the destination is host memory.
+hpf_status copy_out(hpf_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (!dst || bytes == 0) return HPF_OK;
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(dst)) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return HPF_OK;
+}
+
+hpf_status validate_params(const hpf_params* p) {
+    if (!p) return HPF_ERR_INVALID;
+    if (p->n_beads < 0) return HPF_ERR_INVALID;
+    if (p->n_beads > HPF_MAX_BEADS) return HPF_ERR_OVERFLOW;
+    if (p->n_species < 1 || p->n_species > HPF_MAX_SPECIES) return HPF_ERR_INVALID;
+    for (int a = 0; a < 3; ++a) {
+        if (p->mesh[a] < 2 || p->mesh[a] > 4096) return HPF_ERR_INVALID;
+        if (!(p->box[a] > 0.0f) || !isfinite(p->box[a])) return HPF_ERR_INVALID;
+    }
+    if ((long long)p->mesh[0] * p->mesh[1] * p->mesh[2] * p->n_species > (1LL << 31) - 1)
+        return HPF_ERR_INVALID;
+    if (!(p->rho0 > 0) || !(p->mass > 0) || !(p->dt > 0) || !(p->gamma >= 0) || !(p->kT >= 0))
+        return HPF_ERR_INVALID;
+    if (!isfinite(p->inv_kappa) || !isfinite(p->bond_k) || !isfinite(p->bond_r0))
+        return HPF_ERR_INVALID;
+    for (int k = 0; k < p->n_species; ++k)
+        for (int j = 0; j < p->n_species; ++j) {
+            const double a = p->chi[k * HPF_MAX_SPECIES + j], b = p->chi[j * HPF_MAX_SPECIES + k];
+            if (!isfinite(a) || a != b) return HPF_ERR_INVALID;  // chi must be symmetric
+        }
+    if (p->field_every < 1 || p->sort_every < 0) return HPF_ERR_INVALID;
+    return HPF_OK;
+}
+
+void derive_constants(hpf_ctx* c) {
+    const hpf_params& p = c->p;
+    MeshGeom& g = c->geom;
+    g.mx = p.mesh[0];
+    g.my = p.mesh[1];
+    g.mz = p.mesh[2];
+    g.nodes = g.mx * g.my * g.mz;
+    double h[3], vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        g.inv_h[a] = (float)((double)p.mesh[a] / (double)p.box[a]);
+        g.inv_m[a] = 1.0f / (float)p.mesh[a];
+        h[a] = (double)p.box[a] / (double)p.mesh[a];
+        vol *= h[a];
+    }
+    const double phi_c = ldexp(1.0, -3 * HPF_FRAC_BITS) / (p.rho0 * vol);
+    FieldCoef& f = c->coef;
+    memset(&f, 0, sizeof f);
+    f.S = p.n_species;
+    f.v0 = (float)(-p.inv_kappa);
+    for (int k = 0; k < p.n_species; ++k)
+        for (int j = 0; j < p.n_species; ++j) {
+            const double A = p.kT * p.chi[k * HPF_MAX_SPECIES + j] + p.inv_kappa;
+            f.gx[k][j] = (float)(A * phi_c / (2.0 * h[0]));
+            f.gy[k][j] = (float)(A * phi_c / (2.0 * h[1]));
+            f.gz[k][j] = (float)(A * phi_c / (2.0 * h[2]));
+            f.v[k][j] = (float)(A * phi_c);
+        }
+    StepConsts& s = c->sc;
+    s.dt = (float)p.dt;
+    s.dt_m = (float)(p.dt / p.mass);
+    s.fric = (float)(p.gamma * p.mass);
+    s.sigma = (float)sqrt(2.0 * p.gamma * p.mass * p.kT / p.dt);
+    s.two_k = (float)(2.0 * p.bond_k);
+    s.r0 = (float)p.bond_r0;
+    s.seed_lo = (uint32_t)p.seed;
+    s.seed_hi = (uint32_t)(p.seed >> 32);
+    EnergyConsts& e = c->ec;
+    memset(&e, 0, sizeof e);
+    e.half_dt_m = 0.5 * p.dt / p.mass;
+    e.mass = p.mass;
+    e.bond_k = p.bond_k;
+    e.r0 = p.bond_r0;
+    e.kT = p.kT;
+    e.inv_kappa = p.inv_kappa;
+    e.phi_c = phi_c;
+    e.w_scale = p.rho0 * vol;
+    for (int k = 0; k < p.n_species; ++k)
+        for (int j = 0; j < p.n_species; ++j) e.chi[k][j] = p.chi[k * HPF_MAX_SPECIES + j];
+    e.S = p.n_species;
+    e.n = p.n_beads;
+}
+
+size_t stage_bytes(int n) {
+    // pos, vel [3n] f32; type [n] i32; bonds [2n] i32 (a chain set has < n bonds)
+    return (size_t)n * (3 + 3 + 1 + 2) * 4 + 256;
+}
+
+StateBuf& cur_state(hpf_ctx* c) { return c->st[c->cur]; }
+
+hpf_status refresh_field(hpf_ctx* c) {
+    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
+    {
+        StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
+        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
+        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
+    }
+    {
+        StageScope sc(c, HPF_STAGE_FIELD, 1);
+        launch_field(reinterpret_cast<const long long*>(c->D), c->geom, c->coef, c->G, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->field_valid = true;
+    c->field_step = c->step;
+    return HPF_OK;
+}
+
+// The field in force at the current step: refreshed when none is valid or the
+// step is a refresh step that has not been done yet.
+hpf_status ensure_field(hpf_ctx* c) {
+    if (!c->field_valid || (c->step % c->p.field_every == 0 && c->field_step != c->step))
+        return refresh_field(c);
+    return HPF_OK;
+}
+
+hpf_status check_flags(hpf_ctx* c) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->hflag[0] & kFlagNonFinite)
+        return fail(c, HPF_ERR_NONFINITE, "a position or velocity became non-finite");
+    if (c->hflag[0] & kFlagRange)
+        return fail(c, HPF_ERR_OVERFLOW, "a bead left the +-2^18-cell coordinate range");
+    if (c->hflag[0] & kFlagTimeout) return fail(c, HPF_ERR_TIMEOUT, "a device wait timed out");
+    return HPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hpf_status_string(hpf_status s) {
+    switch (s) {
+        case HPF_OK: return "ok";
+        case HPF_ERR_INVALID: return "invalid argument";
+        case HPF_ERR_CUDA: return "CUDA error";
+        case HPF_ERR_NOMEM: return "out of device memory";
+        case HPF_ERR_OVERFLOW: return "fixed-point or coordinate range exceeded";
+        case HPF_ERR_NONFINITE: return "non-finite state";
+        case HPF_ERR_TIMEOUT: return "device wait timed out";
+        case HPF_ERR_STATE: return "no state loaded";
+    }
+    return "unknown status";
+}
+
+const char* hpf_last_error(const hpf_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
+    if (!out) return HPF_ERR_INVALID;
+    *out = nullptr;
+    const hpf_status v = validate_params(params);
+    if (v != HPF_OK) return v;
+    hpf_ctx* c = new hpf_ctx();
+    c->p = *params;
+    c->stream = (cudaStream_t)stream;
+    c->n = params->n_beads;
+    c->S = params->n_species;
+    derive_constants(c);
+    const size_t n = (size_t)(c->n > 0 ? c->n : 1);
+    const size_t nodes = (size_t)c->geom.nodes;
+    auto cleanup = [&](hpf_status s) {
+        hpf_destroy(c);
+        return s;
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&c->state_mem, sizeof(float) * 12 * n);
+    e = e ? e : cudaMalloc(&c->meta, sizeof(uint32_t) * n);
+    e = e ? e : cudaMalloc(&c->D, sizeof(unsigned long long) * nodes * c->S);
+    e = e ? e : cudaMalloc(&c->G, sizeof(float4) * nodes * c->S);
+    e = e ? e : cudaMalloc(&c->out_f, sizeof(float) * 6 * n);
+    e = e ? e : cudaMalloc(&c->stage, stage_bytes((int)n));
+    e = e ? e : cudaMalloc(&c->dflag, sizeof(int) * 8);
+    e = e ? e : cudaMallocHost(&c->hflag, sizeof(int) * 8);
+    e = e ? e : cudaMalloc(&c->partials,
+                           sizeof(double) * energy_partials_needed(c->n, c->geom.nodes));
+    e = e ? e : cudaMalloc(&c->d_out6, sizeof(double) * 8);
+    e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA);
+    }
+    for (int b = 0; b < 2; ++b) {
+        float* base = c->state_mem + (size_t)b * 6 * n;
+        c->st[b] = StateBuf{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
+    }
+    if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream) != cudaSuccess)
+        return cleanup(HPF_ERR_CUDA);
+    *out = c;
+    return HPF_OK;
+}
+
+hpf_status hpf_destroy(hpf_ctx* c) {
+    if (!c) return HPF_OK;
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->ev_used) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : c->ev_free) cudaEventDestroy(e);
+    cudaFree(c->state_mem);
+    cudaFree(c->meta);
+    cudaFree(c->D);
+    cudaFree(c->G);
+    cudaFree(c->out_f);
+    cudaFree(c->stage);
+    cudaFree(c->dflag);
+    cudaFreeHost(c->hflag);
+    cudaFree(c->partials);
+    cudaFree(c->d_out6);
+    cudaFreeHost(c->h_out6);
+    cudaGetLastError();
+    delete c;
+    return HPF_OK;
+}
+
+hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const int32_t* type,
+                         const int32_t* bonds, int64_t n_bonds, int64_t step) {
+    if (!c) return HPF_ERR_INVALID;
+    const int n = c->n;
+    if (step < 0) return fail(c, HPF_ERR_INVALID, "step must be >= 0");
+    if (n > 0 && (!pos || !vel || !type))
+        return fail(c, HPF_ERR_INVALID, "pos, vel and type are required");
+    if (n_bonds < 0 || n_bonds >= (int64_t)(n > 0 ? n : 1) || (n_bonds > 0 && !bonds))
+        return fail(c, HPF_ERR_INVALID, "n_bonds must be in [0, n_beads) with a bond array");
+    char* stg = (char*)c->stage;
+    float* spos = (float*)stg;
+    float* svel = spos + 3 * (size_t)n;
+    int32_t* stype = (int32_t*)(svel + 3 * (size_t)n);
+    int32_t* sbond = stype + n;
+    if (n > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(spos, pos, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(svel, vel, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(stype, type, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream));
+    }
+    if (n_bonds > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(sbond, bonds, sizeof(int32_t) * 2 * n_bonds, cudaMemcpyDefault,
+                                    c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream));
+    c->cur = 0;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, (n > 0) + (n_bonds > 0));
+        launch_stage_state(spos, svel, stype, n, c->S, c->st[0], c->meta, c->dflag + 1,
+                           c->stream);
+        launch_mark_bonds(sbond, n_bonds, n, c->meta, c->dflag + 1, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int) * 8, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->has_state = false;
+    c->field_valid = false;
+    if (c->hflag[1]) return fail(c, HPF_ERR_INVALID, "%d bead species out of range", c->hflag[1]);
+    if (c->hflag[2]) return fail(c, HPF_ERR_NONFINITE, "%d beads with non-finite state", c->hflag[2]);
+    if (c->hflag[3])
+        return fail(c, HPF_ERR_INVALID, "%d bonds do not join consecutive tags (i, i+1)",
+                    c->hflag[3]);
+    if (c->hflag[4]) return fail(c, HPF_ERR_INVALID, "%d bonds given twice", c->hflag[4]);
+    c->step = step;
+    c->field_step = -1;
+    c->has_state = true;
+    return HPF_OK;
+}
+
+hpf_status hpf_get_state(hpf_ctx* c, float* pos, float* vel, int64_t* step) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    float* pt = c->out_f;
+    float* vt = c->out_f + 3 * (size_t)c->n;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 1 : 0);
+        launch_unpermute(cur_state(c), c->meta, c->n, pt, vt, c->dflag, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    hpf_status s;
+    if ((s = copy_out(c, pos, pt, sizeof(float) * 3 * c->n)) != HPF_OK) return s;
+    if ((s = copy_out(c, vel, vt, sizeof(float) * 3 * c->n)) != HPF_OK) return s;
+    if (step) *step = c->step;
+    return check_flags(c);
+}
+
+hpf_status hpf_scatter_density(hpf_ctx* c, int64_t* D_out) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
+    {
+        StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
+        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
+        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, D_out, c->D, dbytes);
+}
+
+hpf_status hpf_field(hpf_ctx* c, const int64_t* D_in, float* field_out) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    const size_t nodes = (size_t)c->geom.nodes * c->S;
+    if (D_in)
+        CUDA_TRY(c, cudaMemcpyAsync(c->D, D_in, sizeof(long long) * nodes, cudaMemcpyDefault,
+                                    c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_FIELD, 1);
+        launch_field(reinterpret_cast<const long long*>(c->D), c->geom, c->coef, c->G, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->field_valid = true;
+    c->field_step = c->step;
+    return copy_out(c, field_out, c->G, sizeof(float4) * nodes);
+}
+
+hpf_status hpf_forces(hpf_ctx* c, float* F_out, int32_t which) {
+    if (!c) return HPF_ERR_INVALID;
+    if (which < 1 || which > 3) return fail(c, HPF_ERR_INVALID, "which must be 1, 2 or 3");
+    if (c->n > 0 && !F_out) return fail(c, HPF_ERR_INVALID, "F_out is required");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s;
+    if ((which & HPF_FORCE_FIELD) && (s = ensure_field(c)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 1 : 0);
+        launch_forces(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, which, c->out_f,
+                      c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, F_out, c->out_f, sizeof(float) * 3 * c->n);
+}
+
+hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
+    if (!c) return HPF_ERR_INVALID;
+    if (n_steps < 0) return fail(c, HPF_ERR_INVALID, "n_steps must be >= 0");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    const long long fe = c->p.field_every;
+    long long left = n_steps;
+    while (left > 0) {
+        hpf_status s = ensure_field(c);
+        if (s != HPF_OK) return s;
+        long long chunk = fe - (c->step % fe);  // steps until the next refresh
+        if (chunk > left) chunk = left;
+        if (chunk > step_halo_max()) chunk = step_halo_max();
+        {
+            StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
+            launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
+                        c->geom, c->G, c->sc, c->dflag, c->stream);
+        }
+        LAUNCH_CHECK(c);
+        c->cur ^= 1;
+        c->step += chunk;
+        left -= chunk;
+    }
+    return HPF_OK;
+}
+
+hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
+    if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s = ensure_field(c);
+    if (s != HPF_OK) return s;
+    // a fresh mesh of the current positions for the field energy
+    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
+    {
+        StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
+        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
+        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
+    }
+    {
+        StageScope sc(c, HPF_STAGE_ENERGY, c->n > 0 ? 3 : 2);
+        launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
+                      reinterpret_cast<const long long*>(c->D), c->ec, c->partials, c->d_out6,
+                      c->stream);
+    }
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                                c->stream));
+    if ((s = check_flags(c)) != HPF_OK) return s;
+    memcpy(out, c->h_out6, sizeof(double) * 6);
+    return HPF_OK;
+}
+
+hpf_status hpf_profile(hpf_ctx* c, int32_t enable) {
+    if (!c) return HPF_ERR_INVALID;
+    c->profiling = enable != 0;
+    return HPF_OK;
+}
+
+hpf_status hpf_profile_read(hpf_ctx* c, double ms[HPF_STAGE_COUNT],
+                            int64_t launches[HPF_STAGE_COUNT]) {
+    if (!c) return HPF_ERR_INVALID;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    double acc[HPF_STAGE_COUNT] = {};
+    for (auto& e : c->ev_used) {
+        float t = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, e.a, e.b));
+        acc[e.stage] += t;
+        c->ev_free.push_back(e.a);
+        c->ev_free.push_back(e.b);
+    }
+    c->ev_used.clear();
+    for (int k = 0; k < HPF_STAGE_COUNT; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = c->launches[k];
+        c->launches[k] = 0;
+    }
+    return HPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// hpf_internal.cuh -- shared declarations of the CUDA hPF-MD library.
+//
+// Device layout (all buffers owned by the context):
+//   state   : SoA float arrays x, y, z, vx, vy, vz in storage order, two copies
+//             (ping-pong) because the step kernel reads neighbours' old positions
+//   meta    : uint32 per bead = tag (24 bits) | species (3 bits) << 24
+//             | bonded-to-previous << 27 | bonded-to-next << 28
+//   D       : int64 density [S][Mz][My][Mx], fixed point with 2^39 per bead
+//   G       : float4 field  [S][Mz][My][Mx] = (dV/dx, dV/dy, dV/dz, V)
+// Storage order keeps every chain contiguous (bonds only join storage
+// neighbours); the sort permutes whole chains for locality.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hpf.h"
+
+namespace hpf {
+
+constexpr uint32_t kTagMask = 0x00FFFFFFu;
+constexpr int kTypeShift = 24;
+constexpr uint32_t kTypeMask = 0x7u;
+constexpr uint32_t kBondPrev = 1u << 27;
+constexpr uint32_t kBondNext = 1u << 28;
+constexpr int kFrac = HPF_FRAC_BITS;
+constexpr int kOne = 1 << kFrac;
+constexpr float kCoordLimit = 262144.0f;  // |mesh coordinate| < 2^18 keeps 2^13 s in int32
+
+// status bits raised by kernels into the context's device flag word
+constexpr int kFlagNonFinite = 1;
+constexpr int kFlagRange = 2;
+constexpr int kFlagTimeout = 4;
+
+struct MeshGeom {
+    int mx, my, mz;
+    int nodes;        // mx * my * mz
+    float inv_h[3];   // fl32(M / L): mesh coordinate s = fl32(x * inv_h)
+    float inv_m[3];   // 1 / M, used only to wrap cell indices
+};
+
+struct StepConsts {
+    float dt;
+    float dt_m;       // dt / m
+    float fric;       // gamma * m
+    float sigma;      // sqrt(2 gamma m kT / dt)
+    float two_k;      // 2 * bond_k
+    float r0;
+    uint32_t seed_lo, seed_hi;
+};
+
+// Coefficients of the field stencil: gradient of V_K from integer central
+// differences of D_K', and V_K from D_K'.
+struct FieldCoef {
+    float gx[HPF_MAX_SPECIES][HPF_MAX_SPECIES];  // A_KK' c / (2 h_x)
+    float gy[HPF_MAX_SPECIES][HPF_MAX_SPECIES];
+    float gz[HPF_MAX_SPECIES][HPF_MAX_SPECIES];
+    float v[HPF_MAX_SPECIES][HPF_MAX_SPECIES];   // A_KK' c
+    float v0;                                    // -inv_kappa
+    int S;
+};
+
+// Constants of the FP64 observables.
+struct EnergyConsts {
+    double half_dt_m;   // dt / (2m)
+    double mass;
+    double bond_k;
+    double r0;
+    double kT;
+    double inv_kappa;
+    double phi_c;       // phi per fixed-point unit: 2^-39 / (rho0 h^3)
+    double w_scale;     // rho0 h^3
+    double chi[HPF_MAX_SPECIES][HPF_MAX_SPECIES];
+    int S;
+    int n;
+};
+
+struct StateBuf {
+    float* x;
+    float* y;
+    float* z;
+    float* vx;
+    float* vy;
+    float* vz;
+};
+
+// ------------------------------------------------------------------ device helpers
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                              uint32_t& c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = c0, b = c2;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, a);
+        const uint32_t lo0 = 0xD2511F53u * a;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, b);
+        const uint32_t lo1 = 0xCD9E8D57u * b;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// (2 (r >> 9) + 1) 2^-24: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float open_uniform(uint32_t r) {
+    return __uint2float_rn(2u * (r >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+
+// Three standard normals of bead `tag` at step `step` (Box-Muller).
+__device__ __forceinline__ void gauss3(uint32_t seed_lo, uint32_t seed_hi, uint32_t tag,
+                                       long long step, float& gx, float& gy, float& gz) {
+    uint32_t c0 = tag, c1 = (uint32_t)step, c2 = (uint32_t)((unsigned long long)step >> 32),
+             c3 = 0u;
+    philox4x32_10(c0, c1, c2, c3, seed_lo, seed_hi);
+    const float a = sqrtf(-2.0f * logf(open_uniform(c0)));
+    const float b = sqrtf(-2.0f * logf(open_uniform(c2)));
+    float s1, k1;
+    sincospif(2.0f * open_uniform(c1), &s1, &k1);
+    gx = a * k1;
+    gy = a * s1;
+    gz = b * cospif(2.0f * open_uniform(c3));
+}
+
+// Mesh coordinate of one component.  t = floor(2^13 s) is exact in FP32, so
+// cell = floor(s) = t >> 13 and q = t & 8191 = floor(2^13 frac(s)) exactly.
+// f = s - floor(s) is the FP32 interpolation weight of the upper node.
+struct AxisCoord {
+    int lo, hi, q;
+    float f;
+};
+
+__device__ __forceinline__ int wrap_cell(int c, int m, float inv_m) {
+    int w = c - m * __float2int_rd(__int2float_rn(c) * inv_m);
+    if (w < 0) w += m;
+    else if (w >= m) w -= m;
+    return w;
+}
+
+__device__ __forceinline__ AxisCoord axis_coord(float x, float inv_h, int m, float inv_m) {
+    AxisCoord a;
+    const float s = __fmul_rn(x, inv_h);
+    const int t = __float2int_rd(__fmul_rn(s, 8192.0f));
+    a.q = t & (kOne - 1);
+    a.f = __fsub_rn(s, floorf(s));
+    a.lo = wrap_cell(t >> kFrac, m, inv_m);
+    a.hi = (a.lo + 1 == m) ? 0 : a.lo + 1;
+    return a;
+}
+
+__device__ __forceinline__ bool coord_in_range(float x, float inv_h) {
+    const float s = __fmul_rn(x, inv_h);
+    return fabsf(s) < kCoordLimit;
+}
+
+// -trilinear interpolation of the nodal gradient of one species.
+__device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, const MeshGeom& g,
+                                             const AxisCoord& ax, const AxisCoord& ay,
+                                             const AxisCoord& az, float& fx, float& fy,
+                                             float& fz) {
+    const float wx1 = ax.f, wx0 = 1.0f - ax.f;
+    const float wy1 = ay.f, wy0 = 1.0f - ay.f;
+    const float wz1 = az.f, wz0 = 1.0f - az.f;
+    const int r00 = (az.lo * g.my + ay.lo) * g.mx;
+    const int r01 = (az.lo * g.my + ay.hi) * g.mx;
+    const int r10 = (az.hi * g.my + ay.lo) * g.mx;
+    const int r11 = (az.hi * g.my + ay.hi) * g.mx;
+    const float4 c000 = __ldg(Gt + r00 + ax.lo), c001 = __ldg(Gt + r00 + ax.hi);
+    const float4 c010 = __ldg(Gt + r01 + ax.lo), c011 = __ldg(Gt + r01 + ax.hi);
+    const float4 c100 = __ldg(Gt + r10 + ax.lo), c101 = __ldg(Gt + r10 + ax.hi);
+    const float4 c110 = __ldg(Gt + r11 + ax.lo), c111 = __ldg(Gt + r11 + ax.hi);
+    const float w00 = wz0 * wy0, w01 = wz0 * wy1, w10 = wz1 * wy0, w11 = wz1 * wy1;
+    float gx = w00 * (wx0 * c000.x + wx1 * c001.x) + w01 * (wx0 * c010.x + wx1 * c011.x) +
+               w10 * (wx0 * c100.x + wx1 * c101.x) + w11 * (wx0 * c110.x + wx1 * c111.x);
+    float gy = w00 * (wx0 * c000.y + wx1 * c001.y) + w01 * (wx0 * c010.y + wx1 * c011.y) +
+               w10 * (wx0 * c100.y + wx1 * c101.y) + w11 * (wx0 * c110.y + wx1 * c111.y);
+    float gz = w00 * (wx0 * c000.z + wx1 * c001.z) + w01 * (wx0 * c010.z + wx1 * c011.z) +
+               w10 * (wx0 * c100.z + wx1 * c101.z) + w11 * (wx0 * c110.z + wx1 * c111.z);
+    fx -= gx;
+    fy -= gy;
+    fz -= gz;
+}
+
+// Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (r - r0) d / r, d = x_i - x_j.
+__device__ __forceinline__ void bond_force(float dx, float dy, float dz, float two_k, float r0,
+                                           float& fx, float& fy, float& fz) {
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float s = -two_k * (r - r0) / r;
+    fx += s * dx;
+    fy += s * dy;
+    fz += s * dz;
+}
+
+// ------------------------------------------------------------------ launchers
+
+void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
+                        StateBuf st, uint32_t* meta, int* err, cudaStream_t s);
+void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta, int* err,
+                       cudaStream_t s);
+void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g,
+                    unsigned long long* D, cudaStream_t s);
+void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
+                  cudaStream_t s);
+void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
+                   StepConsts c, int which, float* F_tag, cudaStream_t s);
+void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
+                 long long step0, MeshGeom g, const float4* G, StepConsts c, int* flag,
+                 cudaStream_t s);
+void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
+                   StepConsts c, long long step, const long long* D, const EnergyConsts& e,
+                   double* partials, double* out6, cudaStream_t s);
+void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,
+                      int* flag, cudaStream_t s);
+
+int step_halo_max();
+int energy_partials_needed(int n, int nodes);
+
+}  // namespace hpf

@@ -1,0 +1,104 @@
+// k_mesh.cu -- density scatter (CIC, int64 fixed point) and the field stencil.
+#include "hpf_internal.cuh"
+
+namespace hpf {
+
+// ------------------------------------------------------------------ A2 scatter
+//
+// One thread per bead adds its eight fixed-point CIC weights to D[T].  The
+// weights are integers, so the mesh is the same for any summation order.
+__global__ void __launch_bounds__(256) k_scatter(StateBuf st, const uint32_t* __restrict__ meta,
+                                                 int n, MeshGeom g,
+                                                 unsigned long long* __restrict__ D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = st.x[i], y = st.y[i], z = st.z[i];
+    const uint32_t m = meta[i];
+    const int T = (m >> kTypeShift) & kTypeMask;
+    const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+    const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+    const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+    const unsigned long long wx[2] = {(unsigned long long)(kOne - ax.q), (unsigned long long)ax.q};
+    const unsigned long long wy[2] = {(unsigned long long)(kOne - ay.q), (unsigned long long)ay.q};
+    const unsigned long long wz[2] = {(unsigned long long)(kOne - az.q), (unsigned long long)az.q};
+    const int nx[2] = {ax.lo, ax.hi}, ny[2] = {ay.lo, ay.hi}, nz[2] = {az.lo, az.hi};
+    unsigned long long* Dt = D + (size_t)T * g.nodes;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const unsigned long long wzy = wz[dz] * wy[dy];
+            const int row = (nz[dz] * g.my + ny[dy]) * g.mx;
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const unsigned long long w = wzy * wx[dx];
+                if (w) atomicAdd(Dt + row + nx[dx], w);
+            }
+        }
+}
+
+void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g, unsigned long long* D,
+                    cudaStream_t s) {
+    if (n <= 0) return;
+    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(st, meta, n, g, D);
+}
+
+// ------------------------------------------------------------------ A3 field
+//
+// One thread per node.  Integer central differences of every species' count
+// are exact; the potential gradient is their FP32 combination with the
+// coefficients A_KK' c / (2h), A = kT chi + inv_kappa, c = 2^-39 / (rho0 h^3).
+template <int S>
+__global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, MeshGeom g,
+                                               FieldCoef c, float4* __restrict__ G) {
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= g.nodes) return;
+    const int x = node % g.mx;
+    const int y = (node / g.mx) % g.my;
+    const int z = node / (g.mx * g.my);
+    const int xp = node + ((x + 1 == g.mx) ? 1 - g.mx : 1);
+    const int xm = node + ((x == 0) ? g.mx - 1 : -1);
+    const int sy = g.mx, sz = g.mx * g.my;
+    const int yp = node + ((y + 1 == g.my) ? (1 - g.my) * sy : sy);
+    const int ym = node + ((y == 0) ? (g.my - 1) * sy : -sy);
+    const int zp = node + ((z + 1 == g.mz) ? (1 - g.mz) * sz : sz);
+    const int zm = node + ((z == 0) ? (g.mz - 1) * sz : -sz);
+    float ddx[S], ddy[S], ddz[S], dc[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const long long* Dk = D + (size_t)k * g.nodes;
+        ddx[k] = (float)(__ldg(Dk + xp) - __ldg(Dk + xm));
+        ddy[k] = (float)(__ldg(Dk + yp) - __ldg(Dk + ym));
+        ddz[k] = (float)(__ldg(Dk + zp) - __ldg(Dk + zm));
+        dc[k] = (float)__ldg(Dk + node);
+    }
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        float gx = 0.f, gy = 0.f, gz = 0.f, v = c.v0;
+#pragma unroll
+        for (int kp = 0; kp < S; ++kp) {
+            gx += c.gx[k][kp] * ddx[kp];
+            gy += c.gy[k][kp] * ddy[kp];
+            gz += c.gz[k][kp] * ddz[kp];
+            v += c.v[k][kp] * dc[kp];
+        }
+        G[(size_t)k * g.nodes + node] = make_float4(gx, gy, gz, v);
+    }
+}
+
+void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
+                  cudaStream_t s) {
+    const int blocks = (g.nodes + 255) / 256;
+    switch (coef.S) {
+        case 1: k_field<1><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 2: k_field<2><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 3: k_field<3><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 4: k_field<4><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 5: k_field<5><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 6: k_field<6><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 7: k_field<7><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        default: k_field<8><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+    }
+}
+
+}  // namespace hpf

@@ -1,0 +1,285 @@
+// k_step.cu -- field gather, bonds, Langevin velocity-Verlet, FP64 observables.
+#include "hpf_internal.cuh"
+
+namespace hpf {
+
+constexpr int kStepBlock = 512;
+constexpr int kHaloMax = 16;  // most steps fused into one launch
+
+int step_halo_max() { return kHaloMax; }
+
+// ------------------------------------------------------------------ A4 + A5 forces
+//
+// Conservative force at the current positions, written in tag order.
+__global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __restrict__ meta,
+                                                int n, MeshGeom g, const float4* __restrict__ G,
+                                                StepConsts c, int which,
+                                                float* __restrict__ F_tag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = st.x[i], y = st.y[i], z = st.z[i];
+    const uint32_t m = meta[i];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (which & HPF_FORCE_BOND) {
+        if (m & kBondPrev)
+            bond_force(x - st.x[i - 1], y - st.y[i - 1], z - st.z[i - 1], c.two_k, c.r0, fx, fy, fz);
+        if (m & kBondNext)
+            bond_force(x - st.x[i + 1], y - st.y[i + 1], z - st.z[i + 1], c.two_k, c.r0, fx, fy, fz);
+    }
+    if (which & HPF_FORCE_FIELD) {
+        const int T = (m >> kTypeShift) & kTypeMask;
+        const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+        const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+        gather_field(G + (size_t)T * g.nodes, g, ax, ay, az, fx, fy, fz);
+    }
+    const uint32_t tag = m & kTagMask;
+    F_tag[3 * tag] = fx;
+    F_tag[3 * tag + 1] = fy;
+    F_tag[3 * tag + 2] = fz;
+}
+
+void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
+                   StepConsts c, int which, float* F_tag, cudaStream_t s) {
+    if (n <= 0) return;
+    k_forces<<<(n + 255) / 256, 256, 0, s>>>(st, meta, n, g, G, c, which, F_tag);
+}
+
+// ------------------------------------------------------------------ A6 fused steps
+//
+// One CTA advances a window of kStepBlock consecutive beads (whole chains or
+// not) by n_sub steps without leaving the chip: positions live in registers,
+// bonded neighbours are exchanged through shared memory, and the frozen field
+// is sampled from L1/L2.  A bead's update after k steps depends on beads up to
+// k places away along its chain, so the outer `halo` beads on each side are
+// recomputed redundantly (bit-identically, the noise is keyed by tag and step)
+// and only the inner kStepBlock - 2 halo beads are written back.
+__global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
+                                                     const uint32_t* __restrict__ meta, int n,
+                                                     int halo, int n_sub, long long step0,
+                                                     MeshGeom g, const float4* __restrict__ G,
+                                                     StepConsts c, int* __restrict__ flag) {
+    __shared__ float sx[2][kStepBlock], sy[2][kStepBlock], sz[2][kStepBlock];
+    const int t = threadIdx.x;
+    const int payload = kStepBlock - 2 * halo;
+    const long long i = (long long)blockIdx.x * payload - halo + t;
+    const bool live = (i >= 0 && i < n);
+    float x = 0.f, y = 0.f, z = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+    uint32_t m = 0;
+    if (live) {
+        x = in.x[i];
+        y = in.y[i];
+        z = in.z[i];
+        vx = in.vx[i];
+        vy = in.vy[i];
+        vz = in.vz[i];
+        m = meta[i];
+    }
+    const bool has_prev = (m & kBondPrev) && t > 0;
+    const bool has_next = (m & kBondNext) && t + 1 < kStepBlock;
+    const uint32_t tag = m & kTagMask;
+    const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes;
+    for (int k = 0; k < n_sub; ++k) {
+        const int b = k & 1;
+        sx[b][t] = x;
+        sy[b][t] = y;
+        sz[b][t] = z;
+        __syncthreads();
+        if (live) {
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            if (has_prev)
+                bond_force(x - sx[b][t - 1], y - sy[b][t - 1], z - sz[b][t - 1], c.two_k, c.r0,
+                           fx, fy, fz);
+            if (has_next)
+                bond_force(x - sx[b][t + 1], y - sy[b][t + 1], z - sz[b][t + 1], c.two_k, c.r0,
+                           fx, fy, fz);
+            const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+            const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+            const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+            gather_field(Gt, g, ax, ay, az, fx, fy, fz);
+            if (c.sigma > 0.f) {
+                float nx, ny, nz;
+                gauss3(c.seed_lo, c.seed_hi, tag, step0 + k, nx, ny, nz);
+                fx += c.sigma * nx;
+                fy += c.sigma * ny;
+                fz += c.sigma * nz;
+            }
+            fx -= c.fric * vx;
+            fy -= c.fric * vy;
+            fz -= c.fric * vz;
+            vx += c.dt_m * fx;
+            vy += c.dt_m * fy;
+            vz += c.dt_m * fz;
+            x += c.dt * vx;
+            y += c.dt * vy;
+            z += c.dt * vz;
+        }
+    }
+    if (live && t >= halo && t < kStepBlock - halo) {
+        out.x[i] = x;
+        out.y[i] = y;
+        out.z[i] = z;
+        out.vx[i] = vx;
+        out.vy[i] = vy;
+        out.vz[i] = vz;
+        const bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) &&
+                            isfinite(vy) && isfinite(vz);
+        if (!finite) atomicOr(flag, kFlagNonFinite);
+        else if (!(coord_in_range(x, g.inv_h[0]) && coord_in_range(y, g.inv_h[1]) &&
+                   coord_in_range(z, g.inv_h[2])))
+            atomicOr(flag, kFlagRange);
+    }
+}
+
+void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
+                 long long step0, MeshGeom g, const float4* G, StepConsts c, int* flag,
+                 cudaStream_t s) {
+    if (n <= 0 || n_sub <= 0) return;
+    const int halo = n_sub;
+    const int payload = kStepBlock - 2 * halo;
+    const int blocks = (n + payload - 1) / payload;
+    k_step<<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c, flag);
+}
+
+// ------------------------------------------------------------------ A7 FP64 observables
+
+constexpr int kRedBlock = 256;
+constexpr int kBeadVals = 5;  // kinetic, bond, px, py, pz
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+    return r;  // valid in thread 0
+}
+
+// Per bead: F_n exactly as the step kernel forms it, v_n = v + dt/(2m) F_n in
+// FP64, then kinetic energy, momentum and the bond energy of the bond to the
+// next bead (each bond once).
+__global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
+                                                            const uint32_t* __restrict__ meta,
+                                                            int n, MeshGeom g,
+                                                            const float4* __restrict__ G,
+                                                            StepConsts c, long long step,
+                                                            EnergyConsts e,
+                                                            double* __restrict__ partials) {
+    __shared__ double sh[kRedBlock / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0, ub = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+    if (i < n) {
+        const float x = st.x[i], y = st.y[i], z = st.z[i];
+        const float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
+        const uint32_t m = meta[i];
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        if (m & kBondPrev)
+            bond_force(x - st.x[i - 1], y - st.y[i - 1], z - st.z[i - 1], c.two_k, c.r0, fx, fy, fz);
+        if (m & kBondNext) {
+            const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
+            bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
+            const double dx = (double)x - xj, dy = (double)y - yj, dz = (double)z - zj;
+            const double dr = sqrt(dx * dx + dy * dy + dz * dz) - e.r0;
+            ub = e.bond_k * dr * dr;
+        }
+        const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+        const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+        gather_field(G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes, g, ax, ay, az, fx,
+                     fy, fz);
+        if (c.sigma > 0.f) {
+            float nx, ny, nz;
+            gauss3(c.seed_lo, c.seed_hi, m & kTagMask, step, nx, ny, nz);
+            fx += c.sigma * nx;
+            fy += c.sigma * ny;
+            fz += c.sigma * nz;
+        }
+        fx -= c.fric * vx;
+        fy -= c.fric * vy;
+        fz -= c.fric * vz;
+        const double ux = (double)vx + e.half_dt_m * (double)fx;
+        const double uy = (double)vy + e.half_dt_m * (double)fy;
+        const double uz = (double)vz + e.half_dt_m * (double)fz;
+        ke = 0.5 * e.mass * (ux * ux + uy * uy + uz * uz);
+        px = e.mass * ux;
+        py = e.mass * uy;
+        pz = e.mass * uz;
+    }
+    const double vals[kBeadVals] = {ke, ub, px, py, pz};
+#pragma unroll
+    for (int k = 0; k < kBeadVals; ++k) {
+        const double s = block_sum(vals[k], sh);
+        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kBeadVals + k] = s;
+    }
+}
+
+// Per node: the field-energy density of the mesh D (FP64 from exact integers).
+__global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __restrict__ D,
+                                                            int nodes, EnergyConsts e,
+                                                            double* __restrict__ partials) {
+    __shared__ double sh[kRedBlock / 32];
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    double w = 0.0;
+    if (node < nodes) {
+        double phi[HPF_MAX_SPECIES];
+        double tot = 0.0;
+        for (int k = 0; k < e.S; ++k) {
+            phi[k] = e.phi_c * (double)D[(size_t)k * nodes + node];
+            tot += phi[k];
+        }
+        for (int k = 0; k < e.S; ++k)
+            for (int kp = 0; kp < e.S; ++kp) w += 0.5 * e.kT * e.chi[k][kp] * phi[k] * phi[kp];
+        w += 0.5 * e.inv_kappa * (tot - 1.0) * (tot - 1.0);
+    }
+    const double s = block_sum(w, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Fixed-order final sums -> out6 = {KE, U_bond, W, total, |P|, T}.
+__global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __restrict__ bead_part,
+                                                            int nb, const double* __restrict__ node_part,
+                                                            int nn, EnergyConsts e,
+                                                            double* __restrict__ out6) {
+    __shared__ double sh[kRedBlock / 32];
+    double acc[kBeadVals + 1];
+    for (int k = 0; k < kBeadVals; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) v += bead_part[(size_t)b * kBeadVals + k];
+        acc[k] = block_sum(v, sh);
+    }
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nn; b += blockDim.x) v += node_part[b];
+    acc[kBeadVals] = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        const double ke = acc[0], ub = acc[1], w = acc[5] * e.w_scale;
+        out6[0] = ke;
+        out6[1] = ub;
+        out6[2] = w;
+        out6[3] = ke + ub + w;
+        out6[4] = sqrt(acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4]);
+        out6[5] = e.n > 0 ? 2.0 * ke / (3.0 * (double)e.n) : 0.0;
+    }
+}
+
+int energy_partials_needed(int n, int nodes) {
+    const int nb = (n + kRedBlock - 1) / kRedBlock;
+    const int nn = (nodes + kRedBlock - 1) / kRedBlock;
+    return nb * kBeadVals + nn + 1;
+}
+
+void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
+                   StepConsts c, long long step, const long long* D, const EnergyConsts& e,
+                   double* partials, double* out6, cudaStream_t s) {
+    const int nb = (n + kRedBlock - 1) / kRedBlock;
+    const int nn = (g.nodes + kRedBlock - 1) / kRedBlock;
+    double* bead_part = partials;
+    double* node_part = partials + (size_t)nb * kBeadVals;
+    if (nb > 0) k_energy_beads<<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part);
+    k_energy_nodes<<<nn, kRedBlock, 0, s>>>(D, g.nodes, e, node_part);
+    k_energy_final<<<1, kRedBlock, 0, s>>>(bead_part, nb, node_part, nn, e, out6);
+}
+
+}  // namespace hpf

@@ -1,0 +1,254 @@
+"""Thin Python binding of libhpf.so (the C ABI of include/hpf.h).
+
+Argument marshalling only: every step of the hPF-MD path runs in the CUDA
+library.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA); the library copies through the pointer with cudaMemcpyDefault.  The
+library must have been built (``python -m paper_1310_2041_gb300.build``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+MAX_SPECIES = 8
+FORCE_FIELD = 1
+FORCE_BOND = 2
+STAGES = ("scatter", "field", "step", "sort", "energy", "other")
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhpf.so")
+_lib = None
+_lock = threading.Lock()
+
+STATUS = {0: "HPF_OK", 1: "HPF_ERR_INVALID", 2: "HPF_ERR_CUDA", 3: "HPF_ERR_NOMEM",
+          4: "HPF_ERR_OVERFLOW", 5: "HPF_ERR_NONFINITE", 6: "HPF_ERR_TIMEOUT",
+          7: "HPF_ERR_STATE"}
+
+
+class HPFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of hpf_params."""
+    _fields_ = [
+        ("n_beads", ctypes.c_int32),
+        ("n_species", ctypes.c_int32),
+        ("mesh", ctypes.c_int32 * 3),
+        ("box", ctypes.c_float * 3),
+        ("kT", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("inv_kappa", ctypes.c_double),
+        ("chi", ctypes.c_double * (MAX_SPECIES * MAX_SPECIES)),
+        ("bond_k", ctypes.c_double),
+        ("bond_r0", ctypes.c_double),
+        ("mass", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("field_every", ctypes.c_int32),
+        ("sort_every", ctypes.c_int32),
+    ]
+
+
+def load():
+    """Load libhpf.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1310_2041_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.hpf_status_string.restype = ctypes.c_char_p
+        L.hpf_status_string.argtypes = [ctypes.c_int]
+        L.hpf_last_error.restype = ctypes.c_char_p
+        L.hpf_last_error.argtypes = [vp]
+        L.hpf_init.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+        L.hpf_destroy.argtypes = [vp]
+        L.hpf_set_state.argtypes = [vp, vp, vp, vp, vp, i64, i64]
+        L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+        L.hpf_scatter_density.argtypes = [vp, vp]
+        L.hpf_field.argtypes = [vp, vp, vp]
+        L.hpf_forces.argtypes = [vp, vp, i32]
+        L.hpf_step.argtypes = [vp, i32]
+        L.hpf_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_profile.argtypes = [vp, i32]
+        L.hpf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]
+        for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
+                     "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
+                     "hpf_profile", "hpf_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return _lib
+
+
+def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
+                bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
+                sort_every=0, **_ignored) -> Params:
+    p = Params()
+    p.n_beads, p.n_species = int(n_beads), int(n_species)
+    m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
+    b = (box,) * 3 if np.isscalar(box) else tuple(box)
+    for a in range(3):
+        p.mesh[a] = int(m[a])
+        p.box[a] = float(b[a])
+    p.kT, p.rho0, p.inv_kappa = float(kT), float(rho0), float(inv_kappa)
+    c = np.zeros((MAX_SPECIES, MAX_SPECIES))
+    if chi is not None:
+        chi = np.asarray(chi, dtype=np.float64)
+        c[:chi.shape[0], :chi.shape[1]] = chi
+    for k, v in enumerate(c.reshape(-1)):
+        p.chi[k] = float(v)
+    p.bond_k, p.bond_r0, p.mass, p.dt, p.gamma = (float(bond_k), float(bond_r0), float(mass),
+                                                  float(dt), float(gamma))
+    p.seed = int(seed)
+    p.field_every, p.sort_every = int(field_every), int(sort_every)
+    return p
+
+
+def _ptr(a, dtype, shape=None, name="array"):
+    """Raw pointer of a numpy array or torch tensor after dtype / layout checks."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        if shape is not None and a.size != int(np.prod(shape)):
+            raise ValueError(f"{name}: expected {shape}, got {a.shape}")
+        return a.ctypes.data, a
+    import torch  # tensors only
+    tdt = {np.float32: torch.float32, np.int32: torch.int32, np.int64: torch.int64,
+           np.float64: torch.float64}[np.dtype(dtype).type]
+    if a.dtype != tdt or not a.is_contiguous():
+        raise ValueError(f"{name}: needs a contiguous {tdt} tensor")
+    if shape is not None and a.numel() != int(np.prod(shape)):
+        raise ValueError(f"{name}: expected {shape}, got {tuple(a.shape)}")
+    return a.data_ptr(), a
+
+
+def current_stream_handle():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class System:
+    """One hPF-MD context (hpf_init ... hpf_destroy)."""
+
+    def __init__(self, params: Params | dict, stream=None):
+        self.lib = load()
+        self.p = params if isinstance(params, Params) else make_params(**params)
+        if stream is None:
+            stream = current_stream_handle()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        h = ctypes.c_void_p()
+        self._check(self.lib.hpf_init(ctypes.byref(self.p), ctypes.c_void_p(self.stream),
+                                      ctypes.byref(h)), None)
+        self.h = h
+        self.n = self.p.n_beads
+        self.S = self.p.n_species
+        self.mesh_shape = (self.S, self.p.mesh[2], self.p.mesh[1], self.p.mesh[0])
+
+    def _check(self, status, h=...):
+        if status != 0:
+            handle = self.h if h is ... else h
+            msg = self.lib.hpf_last_error(handle).decode() if handle else ""
+            raise HPFError(status, msg or self.lib.hpf_status_string(status).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hpf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- state
+    def set_state(self, pos, vel, types, bonds, step=0):
+        n = self.n
+        pp, _a = _ptr(pos, np.float32, (n, 3), "pos")
+        vp, _b = _ptr(vel, np.float32, (n, 3), "vel")
+        tp, _c = _ptr(types, np.int32, (n,), "type")
+        nb = 0 if bonds is None else (bonds.shape[0] if hasattr(bonds, "shape") else len(bonds))
+        if bonds is not None and isinstance(bonds, (list, tuple)):
+            bonds = np.asarray(bonds, dtype=np.int32).reshape(-1, 2)
+        bp, _d = _ptr(bonds, np.int32, (nb, 2), "bonds") if nb else (None, None)
+        self._check(self.lib.hpf_set_state(self.h, pp, vp, tp, bp, nb, int(step)))
+
+    def get_state(self, pos=None, vel=None):
+        if pos is None:
+            pos = np.empty((self.n, 3), dtype=np.float32)
+        if vel is None:
+            vel = np.empty((self.n, 3), dtype=np.float32)
+        step = ctypes.c_int64()
+        pp, _a = _ptr(pos, np.float32, (self.n, 3), "pos")
+        vp, _b = _ptr(vel, np.float32, (self.n, 3), "vel")
+        self._check(self.lib.hpf_get_state(self.h, pp, vp, ctypes.byref(step)))
+        return pos, vel, step.value
+
+    # ---- the path
+    def scatter_density(self, out=None):
+        if out is None:
+            out = np.empty(self.mesh_shape, dtype=np.int64)
+        op, _a = _ptr(out, np.int64, self.mesh_shape, "D_out")
+        self._check(self.lib.hpf_scatter_density(self.h, op))
+        return out
+
+    def field(self, D_in=None, out=None):
+        if out is None:
+            out = np.empty(self.mesh_shape + (4,), dtype=np.float32)
+        dp, _a = _ptr(D_in, np.int64, self.mesh_shape, "D_in")
+        op, _b = _ptr(out, np.float32, self.mesh_shape + (4,), "field_out")
+        self._check(self.lib.hpf_field(self.h, dp, op))
+        return out
+
+    def forces(self, which=FORCE_FIELD | FORCE_BOND, out=None):
+        if out is None:
+            out = np.empty((self.n, 3), dtype=np.float32)
+        op, _a = _ptr(out, np.float32, (self.n, 3), "F_out")
+        self._check(self.lib.hpf_forces(self.h, op, int(which)))
+        return out
+
+    def step(self, n_steps=1):
+        self._check(self.lib.hpf_step(self.h, int(n_steps)))
+
+    def energy(self):
+        out = (ctypes.c_double * 6)()
+        self._check(self.lib.hpf_energy(self.h, out))
+        return np.array(list(out))
+
+    # ---- profiling
+    def profile(self, enable=True):
+        self._check(self.lib.hpf_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{stage: (device ms, kernel launches)} since the last read (synchronises)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        ln = (ctypes.c_int64 * len(STAGES))()
+        self._check(self.lib.hpf_profile_read(self.h, ms, ln))
+        return {s: (ms[k], ln[k]) for k, s in enumerate(STAGES)}

@@ -1,0 +1,268 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bars: the density mesh bit-exact; per-bead force within
+1e-5 (|F_oracle| + F_rms); 10-step positions and velocities within 1e-4;
+FP64 observables within 1e-12 relative where both sides start from the same
+bits (bond, field energy) and 1e-7 where the FP32 force enters (kinetic).
+"""
+import numpy as np
+import pytest
+
+from paper_1310_2041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BEAD = 1 << 39
+
+
+def make(hpf, w: W.Workload, data=None, **over):
+    pp = w.params()
+    pp.update(over)
+    data = W.generate(w) if data is None else data
+    sys_ = hpf.System(hpf.make_params(**pp))
+    sys_.set_state(data["pos"], data["vel"], data["type"], data["bonds"], over.get("step", 0))
+    return sys_, data, pp
+
+
+def oparams(orc, pp):
+    return orc.make_params(**pp)
+
+
+def force_ok(F, Fo, rel=1e-5):
+    F = F.astype(np.float64)
+    rms = np.sqrt(np.mean(np.sum(Fo ** 2, axis=1))) if len(Fo) else 0.0
+    err = np.linalg.norm(F - Fo, axis=1)
+    bound = rel * (np.linalg.norm(Fo, axis=1) + rms)
+    return np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300))) if len(Fo) else 0.0
+
+
+SMALL = [
+    W.diblock(60, 4, 6, 9.3, 8, 1.0, name="ragged_600"),
+    W.diblock(37, 3, 2, 5.1, 5, 2.0, name="odd_185"),
+    W.Workload("aniso", [(40, [0, 1, 2, 1]), (90, [2])], 7.0, 7, 3,
+               [[0, 1.2, 0.3], [1.2, 0, 0.8], [0.3, 0.8, 0]], 0.05, 3, 10),
+]
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+def test_scatter_bit_exact(hpf_gpu, orc, w):
+    s, d, pp = make(hpf_gpu, w)
+    D = s.scatter_density()
+    Do = orc.scatter(oparams(orc, pp), d["pos"], d["type"])
+    np.testing.assert_array_equal(D, Do)
+    assert int(D.sum()) == w.n_beads * BEAD
+
+
+def test_scatter_edge_positions_bit_exact(hpf_gpu, orc):
+    """Beads on nodes, on cell faces, far outside the box, at -0.0 and at L."""
+    M, L = 6, 6.6
+    h = L / M
+    pts = [(0, 0, 0), (-0.0, 1e-30, -1e-30), (L, L, L), (h, 2 * h, 3 * h), (-3 * L - 0.01, 7.7 * L, -0.5),
+           (0.5 * h, 0.5 * h, 0.5 * h), (np.nextafter(np.float32(L), 0), 0.1, 4.0),
+           (-1e-7, -1e-7, 1e-7), (123.456, -654.321, 99.0)]
+    pos = np.array(pts, dtype=np.float32)
+    n = len(pos)
+    types = (np.arange(n) % 2).astype(np.int32)
+    w = W.diblock(1, 1, 1, L, M, 1.0)
+    pp = w.params()
+    pp["n_beads"] = n
+    s = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    s.set_state(pos, np.zeros_like(pos), types, np.zeros((0, 2), np.int32))
+    np.testing.assert_array_equal(s.scatter_density(), orc.scatter(oparams(orc, pp), pos, types))
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+def test_field_matches_oracle(hpf_gpu, orc, w):
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    Vo, Go = orc.field(op, Do)
+    Fm = s.field(D_in=Do)
+    scale = np.max(np.abs(Go)) + 1e-30
+    np.testing.assert_allclose(Fm[..., :3], Go, rtol=1e-5, atol=1e-6 * scale)
+    np.testing.assert_allclose(Fm[..., 3], Vo, rtol=1e-5, atol=1e-6 * (np.max(np.abs(Vo)) + 1))
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+@pytest.mark.parametrize("which", [1, 2, 3])
+def test_forces_match_oracle(hpf_gpu, orc, w, which):
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    Vo, Go = orc.field(op, Do)
+    Fo = np.zeros((w.n_beads, 3))
+    if which & 1:
+        Fo += orc.field_force(op, d["pos"], d["type"], Go)
+    if which & 2:
+        Fo += orc.bond_force(op, d["pos"], d["bonds"])
+    F = s.forces(which)
+    ok, worst = force_ok(F, Fo)
+    assert ok, worst
+
+
+def test_uniform_lattice_gives_exactly_zero_field_force(hpf_gpu):
+    M = 6
+    g = np.stack(np.meshgrid(np.arange(M), np.arange(M), np.arange(M), indexing="ij"), -1)
+    pos = np.repeat(g.reshape(-1, 3)[:, ::-1].astype(np.float32), 3, axis=0)
+    n = len(pos)
+    types = np.tile(np.array([0, 0, 1], np.int32), n // 3)
+    p = W.diblock(1, 1, 1, float(M), M, 1.3).params()
+    p["n_beads"] = n
+    s = hpf_gpu.System(hpf_gpu.make_params(**p))
+    s.set_state(pos, np.zeros_like(pos), types, np.zeros((0, 2), np.int32))
+    assert np.all(s.forces(1) == 0.0)
+
+
+def run_both(hpf, orc, w, n_steps, chunks=None, **over):
+    s, d, pp = make(hpf, w, **over)
+    for c in (chunks or [n_steps]):
+        s.step(c)
+    pos, vel, step = s.get_state()
+    po, vo, _ = orc.run(oparams(orc, pp), d["pos"], d["vel"], d["type"], d["bonds"],
+                        over.get("step", 0), n_steps)
+    assert step == over.get("step", 0) + n_steps
+    return pos, vel, po, vo
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+def test_ten_step_trajectory(hpf_gpu, orc, w):
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
+@pytest.mark.parametrize("fe,step0,chunks", [(3, 7, [10]), (20, 0, [40]), (7, 5, [1, 2, 3, 4]),
+                                             (1, 0, [10]), (10, 3, [10])])
+def test_field_schedule_and_chunking(hpf_gpu, orc, fe, step0, chunks):
+    w = W.diblock(80, 5, 5, 8.0, 8, 1.0)
+    n = sum(chunks)
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, n, chunks=chunks, field_every=fe, step=step0)
+    tol = 1e-4 if n <= 10 else 5e-4   # 40-step case: FP32 rounding grows with the steps
+    assert np.max(np.abs(pos - po)) <= tol
+    assert np.max(np.abs(vel - vo)) <= tol
+
+
+def test_nve_trajectory_without_thermostat(hpf_gpu, orc):
+    w = W.a5b5_10k()
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10, gamma=0.0)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+def test_energy_matches_oracle(hpf_gpu, orc, w):
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+    E = s.energy()
+    Vo, Go = orc.field(op, orc.scatter(op, d["pos"], d["type"]))
+    Eo = orc.energy(op, d["pos"], d["vel"], d["type"], d["bonds"], Vo, Go, 0)
+    assert E[1] == pytest.approx(Eo[1], rel=1e-12, abs=1e-12)   # bond: same bits in
+    assert E[2] == pytest.approx(Eo[2], rel=1e-12)              # field: exact integers in
+    assert E[0] == pytest.approx(Eo[0], rel=1e-7)               # kinetic: FP32 force enters
+    assert E[3] == pytest.approx(Eo[3], rel=1e-7)
+    assert E[4] == pytest.approx(Eo[4], rel=1e-4, abs=1e-6 * w.n_beads)
+    assert E[5] == pytest.approx(Eo[5], rel=1e-7)
+
+
+def test_resume_is_bit_identical(hpf_gpu):
+    w = W.diblock(100, 4, 4, 8.0, 8, 1.0, field_every=5)
+    a, d, pp = make(hpf_gpu, w)
+    a.step(20)
+    pa, va, _ = a.get_state()
+    b, _, _ = make(hpf_gpu, w, data=d)
+    b.step(10)
+    p1, v1, st = b.get_state()
+    c = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    c.set_state(p1, v1, d["type"], d["bonds"], st)
+    c.step(10)
+    pc, vc, _ = c.get_state()
+    np.testing.assert_array_equal(pa, pc)
+    np.testing.assert_array_equal(va, vc)
+
+
+def test_host_and_device_pointers_agree(hpf_gpu):
+    import torch
+    w = W.diblock(50, 5, 5, 6.0, 6, 1.0)
+    a, d, pp = make(hpf_gpu, w)
+    b = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    dev = {k: torch.from_numpy(v).cuda() for k, v in d.items()}
+    b.set_state(dev["pos"], dev["vel"], dev["type"], dev["bonds"])
+    Fa = a.forces()
+    Fb = torch.empty((w.n_beads, 3), dtype=torch.float32, device="cuda")
+    b.forces(out=Fb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Fa, Fb.cpu().numpy())
+
+
+def test_empty_system(hpf_gpu, orc):
+    w = W.diblock(1, 1, 1, 5.0, 5, 1.0)
+    pp = w.params()
+    pp["n_beads"] = 0
+    s = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    e = np.zeros((0, 3), np.float32)
+    s.set_state(e, e, np.zeros(0, np.int32), np.zeros((0, 2), np.int32))
+    s.step(5)
+    assert np.all(s.scatter_density() == 0)
+    E = s.energy()
+    op = oparams(orc, pp)
+    assert E[2] == pytest.approx(orc.field_energy(op, np.zeros((2, 5, 5, 5), np.int64)), rel=1e-12)
+    assert E[0] == 0.0 and E[1] == 0.0
+
+
+def test_invalid_state_is_rejected(hpf_gpu):
+    w = W.diblock(3, 2, 2, 5.0, 5, 1.0)
+    s, d, pp = make(hpf_gpu, w)
+    HPFError = hpf_gpu.HPFError
+    bad = d["type"].copy()
+    bad[2] = 2
+    with pytest.raises(HPFError, match="INVALID"):
+        s.set_state(d["pos"], d["vel"], bad, d["bonds"])
+    with pytest.raises(HPFError, match="INVALID"):
+        s.set_state(d["pos"], d["vel"], d["type"], np.array([[0, 2]], np.int32))
+    with pytest.raises(HPFError, match="INVALID"):
+        s.set_state(d["pos"], d["vel"], d["type"], np.array([[0, 1], [1, 0]], np.int32))
+    p = d["pos"].copy()
+    p[4, 1] = np.nan
+    with pytest.raises(HPFError, match="NONFINITE"):
+        s.set_state(p, d["vel"], d["type"], d["bonds"])
+    with pytest.raises(HPFError, match="STATE"):
+        s.step(1)
+    s.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+    s.step(1)
+
+
+# ---------------------------------------------------------------- full sizes
+
+@pytest.mark.parametrize("factory", [W.a10b10_1m], ids=["a10b10_1m"])
+def test_full_size_melt_parity(hpf_gpu, orc, factory):
+    """The 1M-bead melt in the benchmark's configuration: exact mesh, forces of
+    every bead, and a whole 10-step field period against the oracle."""
+    w = factory()
+    s, d, pp = make(hpf_gpu, w, sort_every=500)
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    np.testing.assert_array_equal(s.scatter_density(), Do)
+    Vo, Go = orc.field(op, Do)
+    Fo = orc.field_force(op, d["pos"], d["type"], Go) + orc.bond_force(op, d["pos"], d["bonds"])
+    ok, worst = force_ok(s.forces(), Fo)
+    assert ok, worst
+    s.step(10)
+    pos, vel, _ = s.get_state()
+    po, vo, _ = orc.run(op, d["pos"], d["vel"], d["type"], d["bonds"], 0, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
+def test_full_size_ternary_blend(hpf_gpu, orc):
+    """8.1M beads, 3 species: exact mesh and forces of every bead."""
+    w = W.ternary_8m()
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    np.testing.assert_array_equal(s.scatter_density(), Do)
+    for k in range(3):
+        assert int(Do[k].sum()) == int((d["type"] == k).sum()) * BEAD
+    Vo, Go = orc.field(op, Do)
+    Fo = orc.field_force(op, d["pos"], d["type"], Go) + orc.bond_force(op, d["pos"], d["bonds"])
+    ok, worst = force_ok(s.forces(), Fo)
+    assert ok, worst
