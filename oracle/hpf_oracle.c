@@ -143,10 +143,13 @@ static axis_coord mesh_coord(const orc_params* p, int axis, double x)
     float s = xf * orc_inv_h(p, axis); /* one FP32 multiply */
     double sd = (double)s;
     double fl = floor(sd);
-    double fr = sd - fl; /* exact: sd has 24 significant bits */
+    /* q = floor(2^13 frac(s)) evaluated without rounding: 2^13 s is exact, so
+     * q = floor(2^13 s) - 2^13 floor(s).  (s - floor(s) itself rounds when s is
+     * a tiny negative number, e.g. 1 - 1e-30 -> 1.) */
+    double t = floor(sd * (double)ONE_Q);
     axis_coord c;
-    c.q = (int64_t)floor(fr * (double)ONE_Q);
-    c.f = fr;
+    c.q = (int64_t)t - (int64_t)fl * ONE_Q;
+    c.f = sd - fl; /* interpolation weight */
     c.lo = wrap((int64_t)fl, p->mesh[axis]);
     c.hi = wrap((int64_t)fl + 1, p->mesh[axis]);
     return c;

@@ -68,6 +68,16 @@ def test_scatter_periodic_wrap_and_negative_coordinates(orc):
     assert D.sum() == BEAD
 
 
+def test_scatter_tiny_negative_coordinate(orc):
+    # s = -1e-30 lies in cell -1 with frac(s) = 1 - 1e-30, so q = floor(8192 (1 - 1e-30)) = 8191:
+    # the lower node keeps one quantum per axis (1 * 8192 * 8192 from the x axis alone)
+    p = unit_params(orc)
+    D = orc.scatter(p, [[-1e-30, 0.0, 0.0]], [0])
+    assert D[0, 0, 0, 7] == 1 * ONE * ONE
+    assert D[0, 0, 0, 0] == 8191 * ONE * ONE
+    assert D.sum() == BEAD
+
+
 def test_scatter_mass_conservation_random(orc):
     rng = np.random.default_rng(1)
     p = orc.make_params(3, (9, 10, 11), (8.7, 10.3, 12.9))
