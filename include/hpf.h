@@ -111,6 +111,16 @@ hpf_status hpf_set_state(hpf_ctx* ctx, const float* pos, const float* vel, const
  * Errors: HPF_ERR_STATE, HPF_ERR_NONFINITE (state became non-finite), HPF_ERR_CUDA. */
 hpf_status hpf_get_state(hpf_ctx* ctx, float* pos, float* vel, int64_t* step);
 
+/* The library's storage order: order[i] is the tag of storage slot i.
+ * Whole chains (runs of bonded beads) are kept contiguous and ordered by the
+ * cell of their first bead, numbered brick by brick (bricks of 8^3 cells, x
+ * fastest inside and across bricks), ties by the first bead's tag.  The
+ * order changes at hpf_set_state and every sort_every steps; no result
+ * depends on it (the paper sorts particle data for cache locality, section
+ * "DPD liquid and LJ liquid").  Synchronises if `order` is host memory.
+ * Errors: HPF_ERR_INVALID (order NULL with n > 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_get_order(hpf_ctx* ctx, int32_t* order);
+
 /* Cloud-in-cell density of the current positions (MD-SCF section; Algorithm 1,
  * kernels 1-2): every bead adds w_x w_y w_z to the eight vertices of its cell,
  * with per-axis fixed-point weights (2^13 - q, q), q = floor(2^13 frac(s)),

@@ -23,6 +23,11 @@ struct hpf_ctx {
     StateBuf st[2]{};
     int cur = 0;
     uint32_t* meta = nullptr;
+    uint32_t* meta2 = nullptr;        // sort target
+    SortBufs sb{};
+    void* sort_mem = nullptr;
+    int C = 0;                        // number of chains
+    long long last_sort_step = 0;
     unsigned long long* D = nullptr;  // int64 density mesh
     float4* G = nullptr;              // field mesh
     float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
@@ -235,6 +240,25 @@ hpf_status ensure_field(hpf_ctx* c) {
     return HPF_OK;
 }
 
+// Reorder whole chains by the cell of their first bead (results do not depend on it).
+hpf_status sort_beads(hpf_ctx* c) {
+    {
+        StageScope sc(c, HPF_STAGE_SORT, 0);
+        sc.kernels = launch_sort(c->sb, c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->meta2, c->n,
+                                 c->C, c->geom, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->cur ^= 1;
+    uint32_t* t = c->meta;
+    c->meta = c->meta2;
+    c->meta2 = t;
+    int* u = c->sb.chain_of_in;
+    c->sb.chain_of_in = c->sb.chain_of_out;
+    c->sb.chain_of_out = u;
+    c->last_sort_step = c->step;
+    return HPF_OK;
+}
+
 hpf_status check_flags(hpf_ctx* c) {
     CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
                                 c->stream));
@@ -287,6 +311,11 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMalloc(&c->state_mem, sizeof(float) * 12 * n);
     e = e ? e : cudaMalloc(&c->meta, sizeof(uint32_t) * n);
+    e = e ? e : cudaMalloc(&c->meta2, sizeof(uint32_t) * n);
+    const long long K = sort_key_space(c->geom);
+    const long long scan_words = scan_scratch_words(K > (long long)n ? K : (long long)n);
+    const size_t sort_words = 9 * n + 3 * (size_t)K + (size_t)scan_words + 64;
+    e = e ? e : cudaMalloc(&c->sort_mem, sizeof(uint32_t) * sort_words);
     e = e ? e : cudaMalloc(&c->D, sizeof(unsigned long long) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->G, sizeof(float4) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->out_f, sizeof(float) * 6 * n);
@@ -300,6 +329,23 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cleanup(e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA);
+    }
+    {
+        uint32_t* w = (uint32_t*)c->sort_mem;
+        SortBufs& b = c->sb;
+        b.cstart = (int*)w; w += n;
+        b.clen = (int*)w; w += n;
+        b.tag0 = w; w += n;
+        b.key = w; w += n;
+        b.order_tmp = (int*)w; w += n;
+        b.rank_of = (int*)w; w += n;
+        b.newstart = w; w += n;
+        b.chain_of_in = (int*)w; w += n;
+        b.chain_of_out = (int*)w; w += n;
+        b.count = w; w += K;
+        b.binoff = w; w += K;
+        b.cursor = w; w += K;
+        b.scratch = w;
     }
     for (int b = 0; b < 2; ++b) {
         float* base = c->state_mem + (size_t)b * 6 * n;
@@ -321,6 +367,8 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     for (auto e : c->ev_free) cudaEventDestroy(e);
     cudaFree(c->state_mem);
     cudaFree(c->meta);
+    cudaFree(c->meta2);
+    cudaFree(c->sort_mem);
     cudaFree(c->D);
     cudaFree(c->G);
     cudaFree(c->out_f);
@@ -365,9 +413,19 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
                            c->stream);
         launch_mark_bonds(sbond, n_bonds, n, c->meta, c->dflag + 1, c->stream);
     }
+    {
+        StageScope sc(c, HPF_STAGE_SORT, 0);
+        sc.kernels = launch_chain_build_heads(c->meta, n, c->sb.newstart, c->sb.scratch, c->stream);
+    }
     LAUNCH_CHECK(c);
     CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int) * 8, cudaMemcpyDeviceToHost,
                                 c->stream));
+    if (n > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 5, c->sb.newstart + (n - 1), sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 6, c->meta + (n - 1), sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->has_state = false;
     c->field_valid = false;
@@ -377,6 +435,20 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
         return fail(c, HPF_ERR_INVALID, "%d bonds do not join consecutive tags (i, i+1)",
                     c->hflag[3]);
     if (c->hflag[4]) return fail(c, HPF_ERR_INVALID, "%d bonds given twice", c->hflag[4]);
+    c->C = 0;
+    if (n > 0) {
+        const uint32_t last_meta = (uint32_t)c->hflag[6];
+        c->C = c->hflag[5] + ((last_meta & kBondPrev) ? 0 : 1);
+        {
+            StageScope sc(c, HPF_STAGE_SORT, 2);
+            launch_chain_build(c->meta, c->sb.newstart, n, c->C, c->sb.cstart, c->sb.tag0,
+                               c->sb.chain_of_in, c->sb.clen, c->stream);
+        }
+        LAUNCH_CHECK(c);
+    }
+    c->step = step;
+    hpf_status s2 = sort_beads(c);
+    if (s2 != HPF_OK) return s2;
     c->step = step;
     c->field_step = -1;
     c->has_state = true;
@@ -398,6 +470,18 @@ hpf_status hpf_get_state(hpf_ctx* c, float* pos, float* vel, int64_t* step) {
     if ((s = copy_out(c, vel, vt, sizeof(float) * 3 * c->n)) != HPF_OK) return s;
     if (step) *step = c->step;
     return check_flags(c);
+}
+
+hpf_status hpf_get_order(hpf_ctx* c, int32_t* order) {
+    if (!c) return HPF_ERR_INVALID;
+    if (c->n > 0 && !order) return fail(c, HPF_ERR_INVALID, "order is required");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 1 : 0);
+        launch_order(c->meta, c->n, (int32_t*)c->out_f, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, order, c->out_f, sizeof(int32_t) * c->n);
 }
 
 hpf_status hpf_scatter_density(hpf_ctx* c, int64_t* D_out) {
@@ -458,6 +542,9 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         long long chunk = fe - (c->step % fe);  // steps until the next refresh
         if (chunk > left) chunk = left;
         if (chunk > step_halo_max()) chunk = step_halo_max();
+        if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
+            if ((s = sort_beads(c)) != HPF_OK) return s;
+        }
         {
             StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
             launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,

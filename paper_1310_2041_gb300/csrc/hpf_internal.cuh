@@ -86,6 +86,23 @@ struct StateBuf {
     float* vz;
 };
 
+// Buffers of the chain sort (chain ids are fixed at state load, in tag order).
+struct SortBufs {
+    int* cstart;        // [C] storage index of each chain's first bead
+    int* clen;          // [C]
+    uint32_t* tag0;     // [C] tag of the first bead
+    uint32_t* key;      // [C] sort key
+    uint32_t* count;    // [K] bucket sizes
+    uint32_t* binoff;   // [K] bucket offsets
+    uint32_t* cursor;   // [K]
+    int* order_tmp;     // [C]
+    int* rank_of;       // [C] new position of chain c
+    uint32_t* newstart; // [max(C, n)] new first-bead index per position (also a scan temp)
+    int* chain_of_in;   // [n] chain of each bead, current order
+    int* chain_of_out;  // [n]
+    uint32_t* scratch;  // scan scratch
+};
+
 // ------------------------------------------------------------------ device helpers
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, multipliers 0xD2511F53 and
@@ -215,8 +232,20 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
 void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, long long step, const long long* D, const EnergyConsts& e,
                    double* partials, double* out6, cudaStream_t s);
+void launch_order(const uint32_t* meta, int n, int32_t* order, cudaStream_t s);
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,
                       int* flag, cudaStream_t s);
+
+long long sort_key_space(const MeshGeom& g);
+long long scan_scratch_words(long long L);
+int scan_exclusive(const uint32_t* in, uint32_t* out, long long L, uint32_t* scratch,
+                   cudaStream_t s);
+int launch_chain_build_heads(const uint32_t* meta, int n, uint32_t* hd, uint32_t* scratch,
+                             cudaStream_t s);
+int launch_chain_build(const uint32_t* meta, const uint32_t* hx, int n, int C, int* cstart,
+                       uint32_t* tag0, int* chain_of, int* clen, cudaStream_t s);
+int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* meta_in,
+                uint32_t* meta_out, int n, int C, MeshGeom g, cudaStream_t s);
 
 int step_halo_max();
 int energy_partials_needed(int n, int nodes);

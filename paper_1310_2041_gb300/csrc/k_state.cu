@@ -68,6 +68,16 @@ __global__ void k_unpermute(StateBuf st, const uint32_t* __restrict__ meta, int 
     }
 }
 
+__global__ void k_order(const uint32_t* __restrict__ meta, int n, int32_t* __restrict__ order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) order[i] = (int32_t)(meta[i] & kTagMask);
+}
+
+void launch_order(const uint32_t* meta, int n, int32_t* order, cudaStream_t s) {
+    if (n <= 0) return;
+    k_order<<<(n + 255) / 256, 256, 0, s>>>(meta, n, order);
+}
+
 void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
                         StateBuf st, uint32_t* meta, int* err, cudaStream_t s) {
     if (n <= 0) return;

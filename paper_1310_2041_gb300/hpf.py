@@ -76,6 +76,7 @@ def load():
         L.hpf_destroy.argtypes = [vp]
         L.hpf_set_state.argtypes = [vp, vp, vp, vp, vp, i64, i64]
         L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+        L.hpf_get_order.argtypes = [vp, vp]
         L.hpf_scatter_density.argtypes = [vp, vp]
         L.hpf_field.argtypes = [vp, vp, vp]
         L.hpf_forces.argtypes = [vp, vp, i32]
@@ -86,7 +87,7 @@ def load():
                                        ctypes.POINTER(ctypes.c_int64)]
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
-                     "hpf_profile", "hpf_profile_read"):
+                     "hpf_profile", "hpf_profile_read", "hpf_get_order"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib
@@ -210,6 +211,14 @@ class System:
         vp, _b = _ptr(vel, np.float32, (self.n, 3), "vel")
         self._check(self.lib.hpf_get_state(self.h, pp, vp, ctypes.byref(step)))
         return pos, vel, step.value
+
+    def order(self, out=None):
+        """Tags in the library's storage order (the locality sort's permutation)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        op, _a = _ptr(out, np.int32, (self.n,), "order")
+        self._check(self.lib.hpf_get_order(self.h, op))
+        return out
 
     # ---- the path
     def scatter_density(self, out=None):

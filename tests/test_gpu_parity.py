@@ -15,6 +15,15 @@ pytestmark = pytest.mark.gpu
 BEAD = 1 << 39
 
 
+def thermal(data, sigma=0.05, seed=5):
+    """Generated chains have every bond at exactly r0 (zero bond force); a seeded
+    jitter gives the bonds thermal-size stretches so force bars are meaningful."""
+    rng = np.random.default_rng(seed)
+    d = dict(data)
+    d["pos"] = (data["pos"] + rng.normal(0.0, sigma, data["pos"].shape)).astype(np.float32)
+    return d
+
+
 def make(hpf, w: W.Workload, data=None, **over):
     pp = w.params()
     pp.update(over)
@@ -86,7 +95,7 @@ def test_field_matches_oracle(hpf_gpu, orc, w):
 @pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
 @pytest.mark.parametrize("which", [1, 2, 3])
 def test_forces_match_oracle(hpf_gpu, orc, w, which):
-    s, d, pp = make(hpf_gpu, w)
+    s, d, pp = make(hpf_gpu, w, data=thermal(W.generate(w)))
     op = oparams(orc, pp)
     Do = orc.scatter(op, d["pos"], d["type"])
     Vo, Go = orc.field(op, Do)
@@ -180,6 +189,37 @@ def test_resume_is_bit_identical(hpf_gpu):
     np.testing.assert_array_equal(va, vc)
 
 
+def expected_order(orc, op, pos, n_chain_beads):
+    """Chain order by (brick-major cell key of the first bead, first tag), from the oracle."""
+    firsts = np.concatenate([[0], np.cumsum(n_chain_beads)[:-1]])
+    order = orc.chain_order(op, pos, firsts, 8)
+    return np.concatenate([np.arange(firsts[c], firsts[c] + n_chain_beads[c]) for c in order])
+
+
+@pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
+def test_sort_order_matches_definition(hpf_gpu, orc, w):
+    s, d, pp = make(hpf_gpu, w)
+    lens = np.concatenate([[len(seq)] * n for n, seq in w.blocks])
+    np.testing.assert_array_equal(s.order(), expected_order(orc, oparams(orc, pp), d["pos"], lens))
+    # the state comes back in tag order, bit for bit
+    pos, vel, _ = s.get_state()
+    np.testing.assert_array_equal(pos, d["pos"])
+    np.testing.assert_array_equal(vel, d["vel"])
+    # after moving, a reload sorts by the new positions
+    s.step(7)
+    pos, vel, st = s.get_state()
+    s.set_state(pos, vel, d["type"], d["bonds"], st)
+    np.testing.assert_array_equal(s.order(), expected_order(orc, oparams(orc, pp), pos, lens))
+
+
+def test_results_do_not_depend_on_sorting(hpf_gpu, orc):
+    """Re-sorting at every launch gives the oracle trajectory."""
+    w = W.diblock(150, 5, 5, 8.0, 8, 1.0, field_every=2)
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10, chunks=[3, 3, 4], sort_every=1)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
 def test_host_and_device_pointers_agree(hpf_gpu):
     import torch
     w = W.diblock(50, 5, 5, 6.0, 6, 1.0)
@@ -238,7 +278,7 @@ def test_full_size_melt_parity(hpf_gpu, orc, factory):
     """The 1M-bead melt in the benchmark's configuration: exact mesh, forces of
     every bead, and a whole 10-step field period against the oracle."""
     w = factory()
-    s, d, pp = make(hpf_gpu, w, sort_every=500)
+    s, d, pp = make(hpf_gpu, w, data=thermal(W.generate(w)), sort_every=500)
     op = oparams(orc, pp)
     Do = orc.scatter(op, d["pos"], d["type"])
     np.testing.assert_array_equal(s.scatter_density(), Do)
@@ -256,7 +296,7 @@ def test_full_size_melt_parity(hpf_gpu, orc, factory):
 def test_full_size_ternary_blend(hpf_gpu, orc):
     """8.1M beads, 3 species: exact mesh and forces of every bead."""
     w = W.ternary_8m()
-    s, d, pp = make(hpf_gpu, w)
+    s, d, pp = make(hpf_gpu, w, data=thermal(W.generate(w)))
     op = oparams(orc, pp)
     Do = orc.scatter(op, d["pos"], d["type"])
     np.testing.assert_array_equal(s.scatter_density(), Do)
