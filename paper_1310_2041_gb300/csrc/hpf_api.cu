@@ -192,6 +192,10 @@ void derive_constants(hpf_ctx* c) {
     s.r0 = (float)p.bond_r0;
     s.seed_lo = (uint32_t)p.seed;
     s.seed_hi = (uint32_t)(p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        s.rk0[r] = s.seed_lo + (uint32_t)r * 0x9E3779B9u;
+        s.rk1[r] = s.seed_hi + (uint32_t)r * 0xBB67AE85u;
+    }
     EnergyConsts& e = c->ec;
     memset(&e, 0, sizeof e);
     e.half_dt_m = 0.5 * p.dt / p.mass;

@@ -49,6 +49,7 @@ struct StepConsts {
     float two_k;      // 2 * bond_k
     float r0;
     uint32_t seed_lo, seed_hi;
+    uint32_t rk0[10], rk1[10];  // Philox round keys: seed + r * (Weyl increments)
 };
 
 // Coefficients of the field stencil: gradient of V_K from integer central
@@ -105,23 +106,20 @@ struct SortBufs {
 
 // ------------------------------------------------------------------ device helpers
 
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds, multipliers 0xD2511F53 and
-// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with multipliers 0xD2511F53 and 0xCD9E8D57; the round keys (the key bumped
+// by the Weyl increments 0x9E3779B9, 0xBB67AE85 per round) are precomputed.
 __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
-                                              uint32_t& c3, uint32_t k0, uint32_t k1) {
+                                              uint32_t& c3, const uint32_t* rk0,
+                                              const uint32_t* rk1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t a = c0, b = c2;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, a);
-        const uint32_t lo0 = 0xD2511F53u * a;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, b);
-        const uint32_t lo1 = 0xCD9E8D57u * b;
-        c0 = hi1 ^ c1 ^ k0;
-        c1 = lo1;
-        c2 = hi0 ^ c3 ^ k1;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        c1 = (uint32_t)p1;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c3 = (uint32_t)p0;
     }
 }
 
@@ -130,19 +128,47 @@ __device__ __forceinline__ float open_uniform(uint32_t r) {
     return __uint2float_rn(2u * (r >> 9) + 1u) * 5.9604644775390625e-8f;
 }
 
-// Three standard normals of bead `tag` at step `step` (Box-Muller).
-__device__ __forceinline__ void gauss3(uint32_t seed_lo, uint32_t seed_hi, uint32_t tag,
-                                       long long step, float& gx, float& gy, float& gz) {
+// ln x for x in [2^-24, 1), by the textbook reduction x = 2^e m, m in
+// [sqrt(1/2), sqrt(2)), and ln m = 2 atanh(t), t = (m - 1) / (m + 1), with the
+// odd series t + t^3/3 + ... + t^9/9 (|t| <= 0.1716: truncation below 1e-9
+// relative).  m - 1 is exact, so the relative accuracy holds as x -> 1, where
+// -ln x is the squared Box-Muller radius and a purely absolute error bound
+// would not do.
+__device__ __forceinline__ float log_unit(float x) {
+    const int bits = __float_as_int(x);
+    int e = (bits >> 23) - 127;
+    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+    if (m > 1.41421356f) {
+        m *= 0.5f;
+        e += 1;
+    }
+    const float t = __fdividef(m - 1.0f, m + 1.0f);
+    const float t2 = t * t;
+    float p = fmaf(t2, 2.0f / 9.0f, 2.0f / 7.0f);
+    p = fmaf(p, t2, 2.0f / 5.0f);
+    p = fmaf(p, t2, 2.0f / 3.0f);
+    p = fmaf(p, t2, 2.0f);
+    return fmaf((float)e, 0.693147180559945f, t * p);
+}
+
+// Three standard normals of bead `tag` at step `step` (Box-Muller):
+// x, y = sqrt(-2 ln u0) (cos, sin)(2 pi u1); z = sqrt(-2 ln u2) cos(2 pi u3).
+// The angle is taken as 2 pi (u - 1/2) + pi, inside (-pi, pi) for the
+// hardware sine and cosine.
+__device__ __forceinline__ void gauss3(const StepConsts& c, uint32_t tag, long long step,
+                                       float& gx, float& gy, float& gz) {
     uint32_t c0 = tag, c1 = (uint32_t)step, c2 = (uint32_t)((unsigned long long)step >> 32),
              c3 = 0u;
-    philox4x32_10(c0, c1, c2, c3, seed_lo, seed_hi);
-    const float a = sqrtf(-2.0f * logf(open_uniform(c0)));
-    const float b = sqrtf(-2.0f * logf(open_uniform(c2)));
+    philox4x32_10(c0, c1, c2, c3, c.rk0, c.rk1);
+    const float L0 = -2.0f * log_unit(open_uniform(c0));
+    const float L2 = -2.0f * log_unit(open_uniform(c2));
+    const float a = L0 * rsqrtf(L0);
+    const float b = L2 * rsqrtf(L2);
     float s1, k1;
-    sincospif(2.0f * open_uniform(c1), &s1, &k1);
-    gx = a * k1;
-    gy = a * s1;
-    gz = b * cospif(2.0f * open_uniform(c3));
+    __sincosf(6.28318530717958648f * (open_uniform(c1) - 0.5f), &s1, &k1);
+    gx = -a * k1;
+    gy = -a * s1;
+    gz = -b * __cosf(6.28318530717958648f * (open_uniform(c3) - 0.5f));
 }
 
 // Mesh coordinate of one component.  t = floor(2^13 s) is exact in FP32, so
@@ -168,6 +194,22 @@ __device__ __forceinline__ AxisCoord axis_coord(float x, float inv_h, int m, flo
     a.f = __fsub_rn(s, floorf(s));
     a.lo = wrap_cell(t >> kFrac, m, inv_m);
     a.hi = (a.lo + 1 == m) ? 0 : a.lo + 1;
+    return a;
+}
+
+// Lower / upper node and interpolation weight only (no fixed-point weight):
+// floor(s) and its wrap are exact integer-valued float operations.
+__device__ __forceinline__ AxisCoord axis_gather(float x, float inv_h, float m, float inv_m,
+                                                 int mi) {
+    AxisCoord a;
+    const float s = __fmul_rn(x, inv_h);
+    const float fl = floorf(s);
+    a.f = __fsub_rn(s, fl);
+    float w = __fmaf_rn(-m, floorf(fl * inv_m), fl);
+    w = (w < 0.0f) ? w + m : ((w >= m) ? w - m : w);
+    a.lo = (int)w;
+    a.hi = (a.lo + 1 == mi) ? 0 : a.lo + 1;
+    a.q = 0;
     return a;
 }
 
@@ -204,11 +246,14 @@ __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, cons
     fz -= gz;
 }
 
-// Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (r - r0) d / r, d = x_i - x_j.
+// Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (1 - r0 / r) d, d = x_i - x_j,
+// with 1 / r from the hardware reciprocal square root and one Newton step.
 __device__ __forceinline__ void bond_force(float dx, float dy, float dz, float two_k, float r0,
                                            float& fx, float& fy, float& fz) {
-    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float s = -two_k * (r - r0) / r;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float ir = rsqrtf(r2);
+    ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
+    const float s = -two_k * fmaf(-r0, ir, 1.0f);
     fx += s * dx;
     fy += s * dy;
     fz += s * dz;

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
     const bool has_next = (m & kBondNext) && t + 1 < kStepBlock;
     const uint32_t tag = m & kTagMask;
     const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes;
+    const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
     for (int k = 0; k < n_sub; ++k) {
         const int b = k & 1;
         sx[b][t] = x;
@@ -93,13 +94,13 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
             if (has_next)
                 bond_force(x - sx[b][t + 1], y - sy[b][t + 1], z - sz[b][t + 1], c.two_k, c.r0,
                            fx, fy, fz);
-            const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
-            const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
-            const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+            const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0], g.mx);
+            const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1], g.my);
+            const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2], g.mz);
             gather_field(Gt, g, ax, ay, az, fx, fy, fz);
             if (c.sigma > 0.f) {
                 float nx, ny, nz;
-                gauss3(c.seed_lo, c.seed_hi, tag, step0 + k, nx, ny, nz);
+                gauss3(c, tag, step0 + k, nx, ny, nz);
                 fx += c.sigma * nx;
                 fy += c.sigma * ny;
                 fz += c.sigma * nz;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                      fy, fz);
         if (c.sigma > 0.f) {
             float nx, ny, nz;
-            gauss3(c.seed_lo, c.seed_hi, m & kTagMask, step, nx, ny, nz);
+            gauss3(c, m & kTagMask, step, nx, ny, nz);
             fx += c.sigma * nx;
             fy += c.sigma * ny;
             fz += c.sigma * nz;
