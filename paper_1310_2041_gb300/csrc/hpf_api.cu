@@ -28,7 +28,10 @@ struct hpf_ctx {
     void* sort_mem = nullptr;
     int C = 0;                        // number of chains
     long long last_sort_step = 0;
-    unsigned long long* D = nullptr;  // int64 density mesh
+    unsigned long long* D = nullptr;  // two int64 density meshes, [2][S][M]
+    int dmesh = 0;                    // which one is the context's mesh
+    long long mesh_step = -1;         // step whose positions it holds (-1: none / injected)
+    bool next_zero = false;           // the other mesh is known to be all zero
     float4* G = nullptr;              // field mesh
     float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
     void* stage = nullptr;            // set_state input staging
@@ -219,21 +222,47 @@ size_t stage_bytes(int n) {
 
 StateBuf& cur_state(hpf_ctx* c) { return c->st[c->cur]; }
 
-hpf_status refresh_field(hpf_ctx* c) {
-    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
+size_t mesh_words(const hpf_ctx* c) { return (size_t)c->geom.nodes * c->S; }
+unsigned long long* mesh_buf(hpf_ctx* c, int k) { return c->D + (size_t)k * mesh_words(c); }
+
+// The context's mesh holds the density of the current positions afterwards:
+// scatter into the other buffer (cleared first unless known zero) and flip.
+hpf_status scatter_current(hpf_ctx* c) {
+    if (c->mesh_step == c->step) return HPF_OK;
+    unsigned long long* dst = mesh_buf(c, c->dmesh ^ 1);
     {
         StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
-        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
-        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
-    }
-    {
-        StageScope sc(c, HPF_STAGE_FIELD, 1);
-        launch_field(reinterpret_cast<const long long*>(c->D), c->geom, c->coef, c->G, c->stream);
+        if (!c->next_zero)
+            CUDA_TRY(c, cudaMemsetAsync(dst, 0, sizeof(unsigned long long) * mesh_words(c),
+                                        c->stream));
+        launch_scatter(cur_state(c), c->meta, c->n, c->geom, dst, c->stream);
     }
     LAUNCH_CHECK(c);
+    c->dmesh ^= 1;
+    c->mesh_step = c->step;
+    c->next_zero = false;
+    return HPF_OK;
+}
+
+// Field of the context's mesh; the kernel also clears the other mesh, the
+// target of the next scatter.
+hpf_status run_field(hpf_ctx* c) {
+    {
+        StageScope sc(c, HPF_STAGE_FIELD, 1);
+        launch_field(reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->geom, c->coef,
+                     c->G, mesh_buf(c, c->dmesh ^ 1), c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->next_zero = true;
     c->field_valid = true;
     c->field_step = c->step;
     return HPF_OK;
+}
+
+hpf_status refresh_field(hpf_ctx* c) {
+    hpf_status s = scatter_current(c);
+    if (s != HPF_OK) return s;
+    return run_field(c);
 }
 
 // The field in force at the current step: refreshed when none is valid or the
@@ -320,7 +349,7 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     const long long scan_words = scan_scratch_words(K > (long long)n ? K : (long long)n);
     const size_t sort_words = 9 * n + 3 * (size_t)K + (size_t)scan_words + 64;
     e = e ? e : cudaMalloc(&c->sort_mem, sizeof(uint32_t) * sort_words);
-    e = e ? e : cudaMalloc(&c->D, sizeof(unsigned long long) * nodes * c->S);
+    e = e ? e : cudaMalloc(&c->D, 2 * sizeof(unsigned long long) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->G, sizeof(float4) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->out_f, sizeof(float) * 6 * n);
     e = e ? e : cudaMalloc(&c->stage, stage_bytes((int)n));
@@ -355,8 +384,11 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
         float* base = c->state_mem + (size_t)b * 6 * n;
         c->st[b] = StateBuf{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
     }
-    if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream) != cudaSuccess)
+    if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->D, 0, 2 * sizeof(unsigned long long) * nodes * c->S, c->stream) !=
+            cudaSuccess)
         return cleanup(HPF_ERR_CUDA);
+    c->next_zero = true;
     *out = c;
     return HPF_OK;
 }
@@ -451,6 +483,7 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
         LAUNCH_CHECK(c);
     }
     c->step = step;
+    c->mesh_step = -1;
     hpf_status s2 = sort_beads(c);
     if (s2 != HPF_OK) return s2;
     c->step = step;
@@ -491,31 +524,25 @@ hpf_status hpf_get_order(hpf_ctx* c, int32_t* order) {
 hpf_status hpf_scatter_density(hpf_ctx* c, int64_t* D_out) {
     if (!c) return HPF_ERR_INVALID;
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
-    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
-    {
-        StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
-        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
-        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
-    }
-    LAUNCH_CHECK(c);
-    return copy_out(c, D_out, c->D, dbytes);
+    hpf_status s = scatter_current(c);
+    if (s != HPF_OK) return s;
+    return copy_out(c, D_out, mesh_buf(c, c->dmesh), sizeof(unsigned long long) * mesh_words(c));
 }
 
 hpf_status hpf_field(hpf_ctx* c, const int64_t* D_in, float* field_out) {
     if (!c) return HPF_ERR_INVALID;
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
-    const size_t nodes = (size_t)c->geom.nodes * c->S;
-    if (D_in)
-        CUDA_TRY(c, cudaMemcpyAsync(c->D, D_in, sizeof(long long) * nodes, cudaMemcpyDefault,
+    if (D_in) {
+        CUDA_TRY(c, cudaMemcpyAsync(mesh_buf(c, c->dmesh ^ 1), D_in,
+                                    sizeof(long long) * mesh_words(c), cudaMemcpyDefault,
                                     c->stream));
-    {
-        StageScope sc(c, HPF_STAGE_FIELD, 1);
-        launch_field(reinterpret_cast<const long long*>(c->D), c->geom, c->coef, c->G, c->stream);
+        c->dmesh ^= 1;
+        c->mesh_step = -1;  // an injected mesh is not the density of the positions
+        c->next_zero = false;
     }
-    LAUNCH_CHECK(c);
-    c->field_valid = true;
-    c->field_step = c->step;
-    return copy_out(c, field_out, c->G, sizeof(float4) * nodes);
+    hpf_status s = run_field(c);
+    if (s != HPF_OK) return s;
+    return copy_out(c, field_out, c->G, sizeof(float4) * mesh_words(c));
 }
 
 hpf_status hpf_forces(hpf_ctx* c, float* F_out, int32_t which) {
@@ -549,15 +576,23 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
             if ((s = sort_beads(c)) != HPF_OK) return s;
         }
+        // the launch that ends on a refresh step also scatters its final positions
+        const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
+        unsigned long long* Dnext = fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
         {
             StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
             launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
-                        c->geom, c->G, c->sc, c->dflag, c->stream);
+                        c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
         }
         LAUNCH_CHECK(c);
         c->cur ^= 1;
         c->step += chunk;
         left -= chunk;
+        if (fuse) {
+            c->dmesh ^= 1;
+            c->mesh_step = c->step;
+            c->next_zero = false;
+        }
     }
     return HPF_OK;
 }
@@ -567,18 +602,13 @@ hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
     hpf_status s = ensure_field(c);
     if (s != HPF_OK) return s;
-    // a fresh mesh of the current positions for the field energy
-    const size_t dbytes = sizeof(unsigned long long) * (size_t)c->geom.nodes * c->S;
-    {
-        StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
-        CUDA_TRY(c, cudaMemsetAsync(c->D, 0, dbytes, c->stream));
-        launch_scatter(cur_state(c), c->meta, c->n, c->geom, c->D, c->stream);
-    }
+    // the mesh of the current positions for the field energy
+    if ((s = scatter_current(c)) != HPF_OK) return s;
     {
         StageScope sc(c, HPF_STAGE_ENERGY, c->n > 0 ? 3 : 2);
         launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
-                      reinterpret_cast<const long long*>(c->D), c->ec, c->partials, c->d_out6,
-                      c->stream);
+                      reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->ec,
+                      c->partials, c->d_out6, c->stream);
     }
     LAUNCH_CHECK(c);
     CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,

@@ -218,6 +218,26 @@ __device__ __forceinline__ bool coord_in_range(float x, float inv_h) {
     return fabsf(s) < kCoordLimit;
 }
 
+// Add one bead's eight fixed-point CIC weights to its species' mesh.
+__device__ __forceinline__ void scatter_bead(unsigned long long* __restrict__ Dt, const MeshGeom& g,
+                                             const AxisCoord& ax, const AxisCoord& ay,
+                                             const AxisCoord& az) {
+    const unsigned long long wx0 = (unsigned long long)(kOne - ax.q), wx1 = (unsigned long long)ax.q;
+    const unsigned long long wy[2] = {(unsigned long long)(kOne - ay.q), (unsigned long long)ay.q};
+    const unsigned long long wz[2] = {(unsigned long long)(kOne - az.q), (unsigned long long)az.q};
+    const int ny[2] = {ay.lo, ay.hi}, nz[2] = {az.lo, az.hi};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const unsigned long long wzy = wz[dz] * wy[dy];
+            unsigned long long* row = Dt + (nz[dz] * g.my + ny[dy]) * g.mx;
+            const unsigned long long a = wzy * wx0, b = wzy * wx1;
+            if (a) atomicAdd(row + ax.lo, a);
+            if (b) atomicAdd(row + ax.hi, b);
+        }
+}
+
 // -trilinear interpolation of the nodal gradient of one species.
 __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, const MeshGeom& g,
                                              const AxisCoord& ax, const AxisCoord& ay,
@@ -268,12 +288,12 @@ void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta
 void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g,
                     unsigned long long* D, cudaStream_t s);
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
-                  cudaStream_t s);
+                  unsigned long long* D_clear, cudaStream_t s);
 void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, int which, float* F_tag, cudaStream_t s);
 void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
-                 long long step0, MeshGeom g, const float4* G, StepConsts c, int* flag,
-                 cudaStream_t s);
+                 long long step0, MeshGeom g, const float4* G, StepConsts c,
+                 unsigned long long* D_next, int* flag, cudaStream_t s);
 void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, long long step, const long long* D, const EnergyConsts& e,
                    double* partials, double* out6, cudaStream_t s);

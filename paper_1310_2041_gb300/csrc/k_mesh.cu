@@ -18,23 +18,7 @@ __global__ void __launch_bounds__(256) k_scatter(StateBuf st, const uint32_t* __
     const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
     const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
     const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
-    const unsigned long long wx[2] = {(unsigned long long)(kOne - ax.q), (unsigned long long)ax.q};
-    const unsigned long long wy[2] = {(unsigned long long)(kOne - ay.q), (unsigned long long)ay.q};
-    const unsigned long long wz[2] = {(unsigned long long)(kOne - az.q), (unsigned long long)az.q};
-    const int nx[2] = {ax.lo, ax.hi}, ny[2] = {ay.lo, ay.hi}, nz[2] = {az.lo, az.hi};
-    unsigned long long* Dt = D + (size_t)T * g.nodes;
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            const unsigned long long wzy = wz[dz] * wy[dy];
-            const int row = (nz[dz] * g.my + ny[dy]) * g.mx;
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const unsigned long long w = wzy * wx[dx];
-                if (w) atomicAdd(Dt + row + nx[dx], w);
-            }
-        }
+    scatter_bead(D + (size_t)T * g.nodes, g, ax, ay, az);
 }
 
 void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g, unsigned long long* D,
@@ -50,9 +34,12 @@ void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g, unsign
 // coefficients A_KK' c / (2h), A = kT chi + inv_kappa, c = 2^-39 / (rho0 h^3).
 template <int S>
 __global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, MeshGeom g,
-                                               FieldCoef c, float4* __restrict__ G) {
+                                               FieldCoef c, float4* __restrict__ G,
+                                               unsigned long long* __restrict__ D_clear) {
     const int node = blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= g.nodes) return;
+#pragma unroll
+    for (int k = 0; k < S; ++k) D_clear[(size_t)k * g.nodes + node] = 0ull;
     const int x = node % g.mx;
     const int y = (node / g.mx) % g.my;
     const int z = node / (g.mx * g.my);
@@ -87,17 +74,17 @@ __global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, 
 }
 
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
-                  cudaStream_t s) {
+                  unsigned long long* D_clear, cudaStream_t s) {
     const int blocks = (g.nodes + 255) / 256;
     switch (coef.S) {
-        case 1: k_field<1><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 2: k_field<2><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 3: k_field<3><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 4: k_field<4><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 5: k_field<5><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 6: k_field<6><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        case 7: k_field<7><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
-        default: k_field<8><<<blocks, 256, 0, s>>>(D, g, coef, G); break;
+        case 1: k_field<1><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 2: k_field<2><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 3: k_field<3><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 4: k_field<4><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 5: k_field<5><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 6: k_field<6><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        case 7: k_field<7><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
+        default: k_field<8><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
     }
 }
 

@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
                                                      const uint32_t* __restrict__ meta, int n,
                                                      int halo, int n_sub, long long step0,
                                                      MeshGeom g, const float4* __restrict__ G,
-                                                     StepConsts c, int* __restrict__ flag) {
+                                                     StepConsts c,
+                                                     unsigned long long* __restrict__ D_next,
+                                                     int* __restrict__ flag) {
     __shared__ float sx[2][kStepBlock], sy[2][kStepBlock], sz[2][kStepBlock];
     const int t = threadIdx.x;
     const int payload = kStepBlock - 2 * halo;
@@ -129,17 +131,26 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
         else if (!(coord_in_range(x, g.inv_h[0]) && coord_in_range(y, g.inv_h[1]) &&
                    coord_in_range(z, g.inv_h[2])))
             atomicOr(flag, kFlagRange);
+        if (D_next) {
+            // this launch ends on a refresh step: deposit the final positions
+            const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+            const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+            const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+            scatter_bead(D_next + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes, g, ax, ay,
+                         az);
+        }
     }
 }
 
 void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
-                 long long step0, MeshGeom g, const float4* G, StepConsts c, int* flag,
-                 cudaStream_t s) {
+                 long long step0, MeshGeom g, const float4* G, StepConsts c,
+                 unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (n <= 0 || n_sub <= 0) return;
     const int halo = n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c, flag);
+    k_step<<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c, D_next,
+                                         flag);
 }
 
 // ------------------------------------------------------------------ A7 FP64 observables

@@ -151,6 +151,22 @@ def test_field_schedule_and_chunking(hpf_gpu, orc, fe, step0, chunks):
     assert np.max(np.abs(vel - vo)) <= tol
 
 
+@pytest.mark.parametrize("fe,steps", [(10, 10), (5, 15), (20, 40), (3, 7)])
+def test_mesh_deposited_by_the_step_kernel_is_exact(hpf_gpu, orc, fe, steps):
+    """A launch that ends on a refresh step deposits its final positions into
+    the next mesh; that mesh must be the exact scatter of those positions."""
+    w = W.diblock(200, 6, 4, 9.0, 9, 1.0, field_every=fe)
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+    s.step(steps)
+    pos, vel, st = s.get_state()
+    D = s.scatter_density()
+    Do = orc.scatter(op, pos, d["type"])
+    np.testing.assert_array_equal(D, Do)
+    E = s.energy()
+    assert E[2] == pytest.approx(orc.field_energy(op, Do), rel=1e-12)
+
+
 def test_nve_trajectory_without_thermostat(hpf_gpu, orc):
     w = W.a5b5_10k()
     pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10, gamma=0.0)
