@@ -270,7 +270,8 @@ __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, cons
 // with 1 / r from the hardware reciprocal square root and one Newton step.
 __device__ __forceinline__ void bond_force(float dx, float dy, float dz, float two_k, float r0,
                                            float& fx, float& fy, float& fz) {
-    const float r2 = dx * dx + dy * dy + dz * dz;
+    // r^2 is clamped so that a masked bond (two_k = 0, zero vector) adds exactly zero
+    const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
     float ir = rsqrtf(r2);
     ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
     const float s = -two_k * fmaf(-r0, ir, 1.0f);

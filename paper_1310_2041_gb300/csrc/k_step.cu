@@ -54,6 +54,7 @@ void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
 // k places away along its chain, so the outer `halo` beads on each side are
 // recomputed redundantly (bit-identically, the noise is keyed by tag and step)
 // and only the inner kStepBlock - 2 halo beads are written back.
+template <bool kNoise>
 __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
                                                      const uint32_t* __restrict__ meta, int n,
                                                      int halo, int n_sub, long long step0,
@@ -77,8 +78,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
         vz = in.vz[i];
         m = meta[i];
     }
-    const bool has_prev = (m & kBondPrev) && t > 0;
-    const bool has_next = (m & kBondNext) && t + 1 < kStepBlock;
+    // out-of-range threads only fill their shared-memory slot
+    const bool has_prev = live && (m & kBondPrev) && t > 0;
+    const bool has_next = live && (m & kBondNext) && t + 1 < kStepBlock;
     const uint32_t tag = m & kTagMask;
     const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes;
     const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
@@ -88,35 +90,31 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
         sy[b][t] = y;
         sz[b][t] = z;
         __syncthreads();
-        if (live) {
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            if (has_prev)
-                bond_force(x - sx[b][t - 1], y - sy[b][t - 1], z - sz[b][t - 1], c.two_k, c.r0,
-                           fx, fy, fz);
-            if (has_next)
-                bond_force(x - sx[b][t + 1], y - sy[b][t + 1], z - sz[b][t + 1], c.two_k, c.r0,
-                           fx, fy, fz);
-            const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0], g.mx);
-            const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1], g.my);
-            const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2], g.mz);
-            gather_field(Gt, g, ax, ay, az, fx, fy, fz);
-            if (c.sigma > 0.f) {
-                float nx, ny, nz;
-                gauss3(c, tag, step0 + k, nx, ny, nz);
-                fx += c.sigma * nx;
-                fy += c.sigma * ny;
-                fz += c.sigma * nz;
-            }
-            fx -= c.fric * vx;
-            fy -= c.fric * vy;
-            fz -= c.fric * vz;
-            vx += c.dt_m * fx;
-            vy += c.dt_m * fy;
-            vz += c.dt_m * fz;
-            x += c.dt * vx;
-            y += c.dt * vy;
-            z += c.dt * vz;
+        // one basic block per sub-step: the field loads are issued first and
+        // the position-independent noise can fill their latency
+        const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0], g.mx);
+        const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1], g.my);
+        const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2], g.mz);
+        float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
+        gather_field(Gt, g, ax, ay, az, fx, fy, fz);
+        if (kNoise) {
+            float nx, ny, nz;
+            gauss3(c, tag, step0 + k, nx, ny, nz);
+            fx = fmaf(c.sigma, nx, fx);
+            fy = fmaf(c.sigma, ny, fy);
+            fz = fmaf(c.sigma, nz, fz);
         }
+        const int tp = has_prev ? t - 1 : t, tn = has_next ? t + 1 : t;
+        bond_force(x - sx[b][tp], y - sy[b][tp], z - sz[b][tp], has_prev ? c.two_k : 0.0f, c.r0,
+                   fx, fy, fz);
+        bond_force(x - sx[b][tn], y - sy[b][tn], z - sz[b][tn], has_next ? c.two_k : 0.0f, c.r0,
+                   fx, fy, fz);
+        vx = fmaf(c.dt_m, fx, vx);
+        vy = fmaf(c.dt_m, fy, vy);
+        vz = fmaf(c.dt_m, fz, vz);
+        x = fmaf(c.dt, vx, x);
+        y = fmaf(c.dt, vy, y);
+        z = fmaf(c.dt, vz, z);
     }
     if (live && t >= halo && t < kStepBlock - halo) {
         out.x[i] = x;
@@ -149,8 +147,12 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
     const int halo = n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c, D_next,
-                                         flag);
+    if (c.sigma > 0.f)
+        k_step<true><<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c,
+                                                   D_next, flag);
+    else
+        k_step<false><<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c,
+                                                    D_next, flag);
 }
 
 // ------------------------------------------------------------------ A7 FP64 observables
