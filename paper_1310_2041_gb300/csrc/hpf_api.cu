@@ -32,7 +32,8 @@ struct hpf_ctx {
     int dmesh = 0;                    // which one is the context's mesh
     long long mesh_step = -1;         // step whose positions it holds (-1: none / injected)
     bool next_zero = false;           // the other mesh is known to be all zero
-    float4* G = nullptr;              // field mesh
+    float4* G = nullptr;              // field mesh (ghosted)
+    float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
     float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
     void* stage = nullptr;            // set_state input staging
     int* dflag = nullptr;             // [0] kernel flags, [1..4] validation counters
@@ -144,7 +145,8 @@ hpf_status validate_params(const hpf_params* p) {
         if (p->mesh[a] < 2 || p->mesh[a] > 4096) return HPF_ERR_INVALID;
         if (!(p->box[a] > 0.0f) || !isfinite(p->box[a])) return HPF_ERR_INVALID;
     }
-    if ((long long)p->mesh[0] * p->mesh[1] * p->mesh[2] * p->n_species > (1LL << 31) - 1)
+    if ((long long)(p->mesh[0] + 1) * (p->mesh[1] + 1) * (p->mesh[2] + 1) * p->n_species >
+        (1LL << 31) - 1)
         return HPF_ERR_INVALID;
     if (!(p->rho0 > 0) || !(p->mass > 0) || !(p->dt > 0) || !(p->gamma >= 0) || !(p->kT >= 0))
         return HPF_ERR_INVALID;
@@ -166,6 +168,9 @@ void derive_constants(hpf_ctx* c) {
     g.my = p.mesh[1];
     g.mz = p.mesh[2];
     g.nodes = g.mx * g.my * g.mz;
+    g.gx = g.mx + 1;
+    g.gxy = (g.mx + 1) * (g.my + 1);
+    g.gnodes = g.gxy * (g.mz + 1);
     double h[3], vol = 1.0;
     for (int a = 0; a < 3; ++a) {
         g.inv_h[a] = (float)((double)p.mesh[a] / (double)p.box[a]);
@@ -350,7 +355,8 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     const size_t sort_words = 9 * n + 3 * (size_t)K + (size_t)scan_words + 64;
     e = e ? e : cudaMalloc(&c->sort_mem, sizeof(uint32_t) * sort_words);
     e = e ? e : cudaMalloc(&c->D, 2 * sizeof(unsigned long long) * nodes * c->S);
-    e = e ? e : cudaMalloc(&c->G, sizeof(float4) * nodes * c->S);
+    e = e ? e : cudaMalloc(&c->G, sizeof(float4) * (size_t)c->geom.gnodes * c->S);
+    e = e ? e : cudaMalloc(&c->field_stage, sizeof(float4) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->out_f, sizeof(float) * 6 * n);
     e = e ? e : cudaMalloc(&c->stage, stage_bytes((int)n));
     e = e ? e : cudaMalloc(&c->dflag, sizeof(int) * 8);
@@ -407,6 +413,7 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->sort_mem);
     cudaFree(c->D);
     cudaFree(c->G);
+    cudaFree(c->field_stage);
     cudaFree(c->out_f);
     cudaFree(c->stage);
     cudaFree(c->dflag);
@@ -542,7 +549,13 @@ hpf_status hpf_field(hpf_ctx* c, const int64_t* D_in, float* field_out) {
     }
     hpf_status s = run_field(c);
     if (s != HPF_OK) return s;
-    return copy_out(c, field_out, c->G, sizeof(float4) * mesh_words(c));
+    if (!field_out) return HPF_OK;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_unpad_field(c->G, c->geom, c->S, c->field_stage, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, field_out, c->field_stage, sizeof(float4) * mesh_words(c));
 }
 
 hpf_status hpf_forces(hpf_ctx* c, float* F_out, int32_t which) {

@@ -6,7 +6,8 @@
 //   meta    : uint32 per bead = tag (24 bits) | species (3 bits) << 24
 //             | bonded-to-previous << 27 | bonded-to-next << 28
 //   D       : int64 density [S][Mz][My][Mx], fixed point with 2^39 per bead
-//   G       : float4 field  [S][Mz][My][Mx] = (dV/dx, dV/dy, dV/dz, V)
+//   G       : float4 field  [S][Mz+1][My+1][Mx+1] = (dV/dx, dV/dy, dV/dz, V), with one
+//             periodic ghost layer per axis so a cell's upper corner is always lo + 1
 // Storage order keeps every chain contiguous (bonds only join storage
 // neighbours); the sort permutes whole chains for locality.
 #pragma once
@@ -37,6 +38,8 @@ constexpr int kFlagTimeout = 4;
 struct MeshGeom {
     int mx, my, mz;
     int nodes;        // mx * my * mz
+    int gx, gxy;      // field-array strides: mx + 1, (mx + 1)(my + 1)
+    int gnodes;       // (mx + 1)(my + 1)(mz + 1)
     float inv_h[3];   // fl32(M / L): mesh coordinate s = fl32(x * inv_h)
     float inv_m[3];   // 1 / M, used only to wrap cell indices
 };
@@ -197,18 +200,21 @@ __device__ __forceinline__ AxisCoord axis_coord(float x, float inv_h, int m, flo
     return a;
 }
 
-// Lower / upper node and interpolation weight only (no fixed-point weight):
-// floor(s) and its wrap are exact integer-valued float operations.
-__device__ __forceinline__ AxisCoord axis_gather(float x, float inv_h, float m, float inv_m,
-                                                 int mi) {
+// Lower node and interpolation weight only (the field array's ghost layers
+// make the upper node lo + 1).  floor(s) is an exact integer-valued float and
+// floor((fl + 1/2) / M) = floor(fl / M) holds in FP32 for |fl| < 2^22 (the
+// half-integer is never a multiple of M, and the relative error 2^-23 stays
+// below the distance 1/(2M) to the nearest integer), so no fix-up is needed;
+// the clamp only keeps out-of-range input inside the array.
+__device__ __forceinline__ AxisCoord axis_gather(float x, float inv_h, float m, float inv_m) {
     AxisCoord a;
     const float s = __fmul_rn(x, inv_h);
     const float fl = floorf(s);
     a.f = __fsub_rn(s, fl);
-    float w = __fmaf_rn(-m, floorf(fl * inv_m), fl);
-    w = (w < 0.0f) ? w + m : ((w >= m) ? w - m : w);
+    float w = __fmaf_rn(-m, floorf((fl + 0.5f) * inv_m), fl);
+    w = fminf(fmaxf(w, 0.0f), m - 1.0f);
     a.lo = (int)w;
-    a.hi = (a.lo + 1 == mi) ? 0 : a.lo + 1;
+    a.hi = a.lo + 1;
     a.q = 0;
     return a;
 }
@@ -238,7 +244,8 @@ __device__ __forceinline__ void scatter_bead(unsigned long long* __restrict__ Dt
         }
 }
 
-// -trilinear interpolation of the nodal gradient of one species.
+// -trilinear interpolation of the nodal gradient of one species (ghosted
+// field array: the eight corners are base + {0, 1} + {0, gx} + {0, gxy}).
 __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, const MeshGeom& g,
                                              const AxisCoord& ax, const AxisCoord& ay,
                                              const AxisCoord& az, float& fx, float& fy,
@@ -246,14 +253,12 @@ __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, cons
     const float wx1 = ax.f, wx0 = 1.0f - ax.f;
     const float wy1 = ay.f, wy0 = 1.0f - ay.f;
     const float wz1 = az.f, wz0 = 1.0f - az.f;
-    const int r00 = (az.lo * g.my + ay.lo) * g.mx;
-    const int r01 = (az.lo * g.my + ay.hi) * g.mx;
-    const int r10 = (az.hi * g.my + ay.lo) * g.mx;
-    const int r11 = (az.hi * g.my + ay.hi) * g.mx;
-    const float4 c000 = __ldg(Gt + r00 + ax.lo), c001 = __ldg(Gt + r00 + ax.hi);
-    const float4 c010 = __ldg(Gt + r01 + ax.lo), c011 = __ldg(Gt + r01 + ax.hi);
-    const float4 c100 = __ldg(Gt + r10 + ax.lo), c101 = __ldg(Gt + r10 + ax.hi);
-    const float4 c110 = __ldg(Gt + r11 + ax.lo), c111 = __ldg(Gt + r11 + ax.hi);
+    const int o00 = az.lo * g.gxy + ay.lo * g.gx + ax.lo;
+    const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
+    const float4 c000 = __ldg(Gt + o00), c001 = __ldg(Gt + o00 + 1);
+    const float4 c010 = __ldg(Gt + o01), c011 = __ldg(Gt + o01 + 1);
+    const float4 c100 = __ldg(Gt + o10), c101 = __ldg(Gt + o10 + 1);
+    const float4 c110 = __ldg(Gt + o11), c111 = __ldg(Gt + o11 + 1);
     const float w00 = wz0 * wy0, w01 = wz0 * wy1, w10 = wz1 * wy0, w11 = wz1 * wy1;
     float gx = w00 * (wx0 * c000.x + wx1 * c001.x) + w01 * (wx0 * c010.x + wx1 * c011.x) +
                w10 * (wx0 * c100.x + wx1 * c101.x) + w11 * (wx0 * c110.x + wx1 * c111.x);
@@ -267,13 +272,13 @@ __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, cons
 }
 
 // Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (1 - r0 / r) d, d = x_i - x_j,
-// with 1 / r from the hardware reciprocal square root and one Newton step.
+// with 1 / r from the hardware reciprocal square root (2 ulp: about 1e-6 of a
+// typical bond force).
 __device__ __forceinline__ void bond_force(float dx, float dy, float dz, float two_k, float r0,
                                            float& fx, float& fy, float& fz) {
     // r^2 is clamped so that a masked bond (two_k = 0, zero vector) adds exactly zero
     const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
-    float ir = rsqrtf(r2);
-    ir = ir * fmaf(-0.5f * r2 * ir, ir, 1.5f);
+    const float ir = rsqrtf(r2);
     const float s = -two_k * fmaf(-r0, ir, 1.0f);
     fx += s * dx;
     fy += s * dy;
@@ -290,6 +295,7 @@ void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g,
                     unsigned long long* D, cudaStream_t s);
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
                   unsigned long long* D_clear, cudaStream_t s);
+void launch_unpad_field(const float4* G, MeshGeom g, int S, float4* out, cudaStream_t s);
 void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, int which, float* F_tag, cudaStream_t s);
 void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,

@@ -36,13 +36,19 @@ template <int S>
 __global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, MeshGeom g,
                                                FieldCoef c, float4* __restrict__ G,
                                                unsigned long long* __restrict__ D_clear) {
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= g.nodes) return;
+    // one thread per node of the ghosted field array; ghost nodes repeat the
+    // periodic image
+    const int pnode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pnode >= g.gnodes) return;
+    const int px = pnode % g.gx;
+    const int py = (pnode / g.gx) % (g.my + 1);
+    const int pz = pnode / g.gxy;
+    const int x = px == g.mx ? 0 : px, y = py == g.my ? 0 : py, z = pz == g.mz ? 0 : pz;
+    const int node = (z * g.my + y) * g.mx + x;
+    if (px < g.mx && py < g.my && pz < g.mz) {
 #pragma unroll
-    for (int k = 0; k < S; ++k) D_clear[(size_t)k * g.nodes + node] = 0ull;
-    const int x = node % g.mx;
-    const int y = (node / g.mx) % g.my;
-    const int z = node / (g.mx * g.my);
+        for (int k = 0; k < S; ++k) D_clear[(size_t)k * g.nodes + node] = 0ull;
+    }
     const int xp = node + ((x + 1 == g.mx) ? 1 - g.mx : 1);
     const int xm = node + ((x == 0) ? g.mx - 1 : -1);
     const int sy = g.mx, sz = g.mx * g.my;
@@ -69,13 +75,28 @@ __global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, 
             gz += c.gz[k][kp] * ddz[kp];
             v += c.v[k][kp] * dc[kp];
         }
-        G[(size_t)k * g.nodes + node] = make_float4(gx, gy, gz, v);
+        G[(size_t)k * g.gnodes + pnode] = make_float4(gx, gy, gz, v);
     }
+}
+
+// Ghosted field array -> dense [S][Mz][My][Mx] float4.
+__global__ void k_unpad_field(const float4* __restrict__ G, MeshGeom g, int S,
+                              float4* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)S * g.nodes) return;
+    const int k = (int)(i / g.nodes), node = (int)(i % g.nodes);
+    const int x = node % g.mx, y = (node / g.mx) % g.my, z = node / (g.mx * g.my);
+    out[i] = G[(size_t)k * g.gnodes + (size_t)z * g.gxy + y * g.gx + x];
+}
+
+void launch_unpad_field(const float4* G, MeshGeom g, int S, float4* out, cudaStream_t s) {
+    const long long n = (long long)S * g.nodes;
+    k_unpad_field<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, g, S, out);
 }
 
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
                   unsigned long long* D_clear, cudaStream_t s) {
-    const int blocks = (g.nodes + 255) / 256;
+    const int blocks = (g.gnodes + 255) / 256;
     switch (coef.S) {
         case 1: k_field<1><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;
         case 2: k_field<2><<<blocks, 256, 0, s>>>(D, g, coef, G, D_clear); break;

@@ -28,10 +28,10 @@ __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __r
     }
     if (which & HPF_FORCE_FIELD) {
         const int T = (m >> kTypeShift) & kTypeMask;
-        const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
-        const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
-        const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
-        gather_field(G + (size_t)T * g.nodes, g, ax, ay, az, fx, fy, fz);
+        const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
+        const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
+        gather_field(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
     }
     const uint32_t tag = m & kTagMask;
     F_tag[3 * tag] = fx;
@@ -55,7 +55,7 @@ void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
 // recomputed redundantly (bit-identically, the noise is keyed by tag and step)
 // and only the inner kStepBlock - 2 halo beads are written back.
 template <bool kNoise>
-__global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
+__global__ void __launch_bounds__(kStepBlock, 3) k_step(StateBuf in, StateBuf out,
                                                      const uint32_t* __restrict__ meta, int n,
                                                      int halo, int n_sub, long long step0,
                                                      MeshGeom g, const float4* __restrict__ G,
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
     const bool has_prev = live && (m & kBondPrev) && t > 0;
     const bool has_next = live && (m & kBondNext) && t + 1 < kStepBlock;
     const uint32_t tag = m & kTagMask;
-    const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes;
+    const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
     const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
     for (int k = 0; k < n_sub; ++k) {
         const int b = k & 1;
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step(StateBuf in, StateBuf out,
         __syncthreads();
         // one basic block per sub-step: the field loads are issued first and
         // the position-independent noise can fill their latency
-        const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0], g.mx);
-        const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1], g.my);
-        const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2], g.mz);
+        const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0]);
+        const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1]);
+        const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2]);
         float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
         gather_field(Gt, g, ax, ay, az, fx, fy, fz);
         if (kNoise) {
@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
             const double dr = sqrt(dx * dx + dy * dy + dz * dz) - e.r0;
             ub = e.bond_k * dr * dr;
         }
-        const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
-        const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
-        const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
-        gather_field(G + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes, g, ax, ay, az, fx,
+        const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
+        const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
+        gather_field(G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes, g, ax, ay, az, fx,
                      fy, fz);
         if (c.sigma > 0.f) {
             float nx, ny, nz;
