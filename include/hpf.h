@@ -30,6 +30,7 @@
 #ifndef HPF_H
 #define HPF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -48,7 +49,8 @@ typedef enum {
     HPF_ERR_OVERFLOW = 4,  /* n_beads >= 2^24, or a bead left the +-2^18-cell range */
     HPF_ERR_NONFINITE = 5, /* a position or velocity became NaN or infinite */
     HPF_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
-    HPF_ERR_STATE = 7      /* the call needs a state (hpf_set_state) first */
+    HPF_ERR_STATE = 7,     /* the call needs a state (hpf_set_state) first */
+    HPF_ERR_SCRATCH = 8    /* the mesh does not fit hpf_field_forces_noalloc's static scratch */
 } hpf_status;
 
 typedef struct hpf_ctx hpf_ctx;
@@ -193,6 +195,47 @@ hpf_status hpf_profile(hpf_ctx* ctx, int32_t enable);
  * Errors: HPF_ERR_INVALID, HPF_ERR_CUDA. */
 hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
                             int64_t launches[HPF_STAGE_COUNT]);
+
+/* ---- Field forces without any device allocation ---------------------------
+ *
+ * The paper has no counterpart to this entry point.  It is here for callers
+ * that cannot let a library allocate GPU memory: for example a host program
+ * whose own memory pool has already reserved nearly all of the device, or a
+ * program that must not pay the device-wide synchronisation that cudaMalloc
+ * and cudaFree can cause in the middle of its work.  Such a caller owns every
+ * buffer it passes; the library's own working memory (one int64 density mesh,
+ * a spare mesh and the float4 field) is a single file-scope static __device__
+ * array of HPF_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads this
+ * library holds until the process exits.
+ *
+ * The call computes, with no context, the field force that hpf_forces gives
+ * with HPF_FORCE_FIELD right after loading these positions: CIC scatter of the
+ * beads, V and grad V of that mesh, trilinear gather -grad V_T at every bead.
+ * Only n_species, mesh, box, kT, rho0, inv_kappa and chi of `params` are used.
+ *   pos   [n][3] float32 positions, device memory of the current device
+ *   type  [n]    int32 species; a species outside [0, n_species) gets a NaN
+ *                force and adds nothing to the density
+ *   F_out [n][3] float32 output, device memory of the current device
+ *   stream       cudaStream_t the kernels are enqueued on (NULL: legacy
+ *                default stream); the call returns without waiting
+ * The first call on a device looks up the scratch's device address (with
+ * cudaGetSymbolAddress, that device current) and caches it; make that first
+ * call before any stream capture.  All calls on one device share the
+ * scratch, and it keeps the previous call's contents (each call clears the
+ * density mesh it needs itself): calls that overlap on the GPU (two streams
+ * or threads without ordering between them) race and give wrong forces, so
+ * order them, for instance on one stream.
+ * Errors: HPF_ERR_INVALID (bad parameter, n outside [0, HPF_MAX_BEADS], a
+ * NULL or host pointer with n > 0), HPF_ERR_SCRATCH (the mesh needs more than
+ * HPF_NOALLOC_SCRATCH_BYTES; see hpf_noalloc_scratch_bytes), HPF_ERR_CUDA. */
+#define HPF_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB: fits a 70^3 two-species mesh */
+
+/* Scratch bytes hpf_field_forces_noalloc needs for these parameters (0 if the
+ * species count or mesh is invalid). */
+size_t hpf_noalloc_scratch_bytes(const hpf_params* params);
+
+hpf_status hpf_field_forces_noalloc(const hpf_params* params, const float* pos,
+                                    const int32_t* type, int32_t n, float* F_out, void* stream);
 
 #ifdef __cplusplus
 }

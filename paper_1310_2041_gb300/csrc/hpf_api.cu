@@ -323,6 +323,7 @@ const char* hpf_status_string(hpf_status s) {
         case HPF_ERR_NONFINITE: return "non-finite state";
         case HPF_ERR_TIMEOUT: return "device wait timed out";
         case HPF_ERR_STATE: return "no state loaded";
+        case HPF_ERR_SCRATCH: return "mesh larger than the no-allocation scratch";
     }
     return "unknown status";
 }
