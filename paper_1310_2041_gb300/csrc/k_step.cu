@@ -50,19 +50,92 @@ void launch_forces(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
 // One CTA advances a window of kStepBlock consecutive beads (whole chains or
 // not) by n_sub steps without leaving the chip: positions live in registers,
 // bonded neighbours are exchanged through shared memory, and the frozen field
-// is sampled from L1/L2.  A bead's update after k steps depends on beads up to
-// k places away along its chain, so the outer `halo` beads on each side are
-// recomputed redundantly (bit-identically, the noise is keyed by tag and step)
-// and only the inner kStepBlock - 2 halo beads are written back.
+// is sampled through a per-bead cache.  A bead's update after k steps depends
+// on beads up to k places away along its chain, so the outer `halo` beads on
+// each side are recomputed redundantly (bit-identically, the noise is keyed by
+// tag and step) and only the inner kStepBlock - 2 halo beads are written back.
+//
+// Field cache: inside one cell the interpolated gradient is the trilinear
+// polynomial c0 + c1 fx + c2 fy + c3 fz + c4 fx fy + c5 fx fz + c6 fy fz
+// + c7 fx fy fz of the cell offset f (per component).  A bead keeps the 24
+// coefficients of its current cell in shared memory (six float4 planes, one
+// slot per thread, conflict-free) and rebuilds them from the eight corners
+// only when it enters another cell -- about once every 40 steps at kT = 1,
+// h = 1, dt = 0.01 -- so most sub-steps read six shared float4s instead of
+// gathering eight corners from L1/L2.
+constexpr int kCachePlanes = 6;
+constexpr size_t kStepSmem = sizeof(float4) * kCachePlanes * kStepBlock +
+                             sizeof(float) * 3 * 2 * kStepBlock;
+
+__device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
+                                                float flx, float fly, float flz,
+                                                float4* __restrict__ cache, int t) {
+    const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
+    float wx = __fmaf_rn(-fmx, floorf((flx + 0.5f) * g.inv_m[0]), flx);
+    float wy = __fmaf_rn(-fmy, floorf((fly + 0.5f) * g.inv_m[1]), fly);
+    float wz = __fmaf_rn(-fmz, floorf((flz + 0.5f) * g.inv_m[2]), flz);
+    wx = fminf(fmaxf(wx, 0.0f), fmx - 1.0f);
+    wy = fminf(fmaxf(wy, 0.0f), fmy - 1.0f);
+    wz = fminf(fmaxf(wz, 0.0f), fmz - 1.0f);
+    const int o00 = (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
+    const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
+    // corner (a, b, c) = offsets (x, y, z) in {0, 1}
+    const float4 g000 = __ldg(Gt + o00), g100 = __ldg(Gt + o00 + 1);
+    const float4 g010 = __ldg(Gt + o01), g110 = __ldg(Gt + o01 + 1);
+    const float4 g001 = __ldg(Gt + o10), g101 = __ldg(Gt + o10 + 1);
+    const float4 g011 = __ldg(Gt + o11), g111 = __ldg(Gt + o11 + 1);
+    // component-major: planes 2j, 2j+1 hold c0..c7 of component j
+#define HPF_COEF(comp, j)                                                                        \
+    {                                                                                            \
+        const float a0 = g000.comp, a1 = g100.comp - g000.comp, a2 = g010.comp - g000.comp;      \
+        const float a3 = g001.comp - g000.comp;                                                  \
+        const float a4 = (g110.comp - g100.comp) - a2;                                           \
+        const float a5 = (g101.comp - g100.comp) - a3;                                           \
+        const float a6 = (g011.comp - g010.comp) - a3;                                           \
+        const float a7 = ((g111.comp - g110.comp) - (g101.comp - g100.comp)) - a6;               \
+        cache[(2 * j) * kStepBlock + t] = make_float4(a0, a1, a2, a3);                           \
+        cache[(2 * j + 1) * kStepBlock + t] = make_float4(a4, a5, a6, a7);                       \
+    }
+    HPF_COEF(x, 0)
+    HPF_COEF(y, 1)
+    HPF_COEF(z, 2)
+#undef HPF_COEF
+}
+
+// -(trilinear polynomial) of the cached cell at offset (fx, fy, fz).
+__device__ __forceinline__ float cell_poly(const float4 lo, const float4 hi, float fx, float fy,
+                                           float fz) {
+    // lo = (c0, c1, c2, c3), hi = (c4, c5, c6, c7)
+    float a = fmaf(fz, hi.w, hi.x);
+    a = fmaf(fy, a, lo.y);
+    a = fmaf(fz, hi.y, a);
+    const float b = fmaf(fz, hi.z, lo.z);
+    float v = fmaf(fx, a, lo.x);
+    v = fmaf(fy, b, v);
+    return fmaf(fz, lo.w, v);
+}
+
+__device__ __forceinline__ void eval_cell_cache(const float4* __restrict__ cache, int t, float fx,
+                                                float fy, float fz, float& Fx, float& Fy,
+                                                float& Fz) {
+    Fx -= cell_poly(cache[0 * kStepBlock + t], cache[1 * kStepBlock + t], fx, fy, fz);
+    Fy -= cell_poly(cache[2 * kStepBlock + t], cache[3 * kStepBlock + t], fx, fy, fz);
+    Fz -= cell_poly(cache[4 * kStepBlock + t], cache[5 * kStepBlock + t], fx, fy, fz);
+}
+
 template <bool kNoise>
-__global__ void __launch_bounds__(kStepBlock, 3) k_step(StateBuf in, StateBuf out,
-                                                     const uint32_t* __restrict__ meta, int n,
-                                                     int halo, int n_sub, long long step0,
-                                                     MeshGeom g, const float4* __restrict__ G,
-                                                     StepConsts c,
-                                                     unsigned long long* __restrict__ D_next,
-                                                     int* __restrict__ flag) {
-    __shared__ float sx[2][kStepBlock], sy[2][kStepBlock], sz[2][kStepBlock];
+__global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
+                                                        const uint32_t* __restrict__ meta, int n,
+                                                        int halo, int n_sub, long long step0,
+                                                        MeshGeom g, const float4* __restrict__ G,
+                                                        StepConsts c,
+                                                        unsigned long long* __restrict__ D_next,
+                                                        int* __restrict__ flag) {
+    extern __shared__ float4 smem4[];
+    float4* cache = smem4;                                   // [kCachePlanes][kStepBlock]
+    float* sx = reinterpret_cast<float*>(smem4 + kCachePlanes * kStepBlock);  // [2][block]
+    float* sy = sx + 2 * kStepBlock;
+    float* sz = sy + 2 * kStepBlock;
     const int t = threadIdx.x;
     const int payload = kStepBlock - 2 * halo;
     const long long i = (long long)blockIdx.x * payload - halo + t;
@@ -83,20 +156,25 @@ __global__ void __launch_bounds__(kStepBlock, 3) k_step(StateBuf in, StateBuf ou
     const bool has_next = live && (m & kBondNext) && t + 1 < kStepBlock;
     const uint32_t tag = m & kTagMask;
     const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
-    const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
+    float cfx = __int_as_float(0x7fc00000), cfy = cfx, cfz = cfx;  // cached cell: none
     for (int k = 0; k < n_sub; ++k) {
         const int b = k & 1;
-        sx[b][t] = x;
-        sy[b][t] = y;
-        sz[b][t] = z;
+        sx[b * kStepBlock + t] = x;
+        sy[b * kStepBlock + t] = y;
+        sz[b * kStepBlock + t] = z;
         __syncthreads();
-        // one basic block per sub-step: the field loads are issued first and
-        // the position-independent noise can fill their latency
-        const AxisCoord ax = axis_gather(x, g.inv_h[0], fmx, g.inv_m[0]);
-        const AxisCoord ay = axis_gather(y, g.inv_h[1], fmy, g.inv_m[1]);
-        const AxisCoord az = axis_gather(z, g.inv_h[2], fmz, g.inv_m[2]);
+        const float s0 = __fmul_rn(x, g.inv_h[0]), s1 = __fmul_rn(y, g.inv_h[1]),
+                    s2 = __fmul_rn(z, g.inv_h[2]);
+        const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
+        if (flx != cfx || fly != cfy || flz != cfz) {
+            fill_cell_cache(Gt, g, flx, fly, flz, cache, t);
+            cfx = flx;
+            cfy = fly;
+            cfz = flz;
+        }
         float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
-        gather_field(Gt, g, ax, ay, az, fx, fy, fz);
+        eval_cell_cache(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly), __fsub_rn(s2, flz), fx,
+                        fy, fz);
         if (kNoise) {
             float nx, ny, nz;
             gauss3(c, tag, step0 + k, nx, ny, nz);
@@ -105,10 +183,10 @@ __global__ void __launch_bounds__(kStepBlock, 3) k_step(StateBuf in, StateBuf ou
             fz = fmaf(c.sigma, nz, fz);
         }
         const int tp = has_prev ? t - 1 : t, tn = has_next ? t + 1 : t;
-        bond_force(x - sx[b][tp], y - sy[b][tp], z - sz[b][tp], has_prev ? c.two_k : 0.0f, c.r0,
-                   fx, fy, fz);
-        bond_force(x - sx[b][tn], y - sy[b][tn], z - sz[b][tn], has_next ? c.two_k : 0.0f, c.r0,
-                   fx, fy, fz);
+        bond_force(x - sx[b * kStepBlock + tp], y - sy[b * kStepBlock + tp],
+                   z - sz[b * kStepBlock + tp], has_prev ? c.two_k : 0.0f, c.r0, fx, fy, fz);
+        bond_force(x - sx[b * kStepBlock + tn], y - sy[b * kStepBlock + tn],
+                   z - sz[b * kStepBlock + tn], has_next ? c.two_k : 0.0f, c.r0, fx, fy, fz);
         vx = fmaf(c.dt_m, fx, vx);
         vy = fmaf(c.dt_m, fy, vy);
         vz = fmaf(c.dt_m, fz, vz);
@@ -144,15 +222,23 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
                  long long step0, MeshGeom g, const float4* G, StepConsts c,
                  unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (n <= 0 || n_sub <= 0) return;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kStepSmem);
+        cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kStepSmem);
+        attr_set = true;
+    }
     const int halo = n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
     if (c.sigma > 0.f)
-        k_step<true><<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c,
-                                                   D_next, flag);
+        k_step<true><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub, step0, g,
+                                                           G, c, D_next, flag);
     else
-        k_step<false><<<blocks, kStepBlock, 0, s>>>(in, out, meta, n, halo, n_sub, step0, g, G, c,
-                                                    D_next, flag);
+        k_step<false><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub, step0,
+                                                            g, G, c, D_next, flag);
 }
 
 // ------------------------------------------------------------------ A7 FP64 observables
