@@ -123,6 +123,20 @@ __device__ __forceinline__ void eval_cell_cache(const float4* __restrict__ cache
     Fz -= cell_poly(cache[4 * kStepBlock + t], cache[5 * kStepBlock + t], fx, fy, fz);
 }
 
+// A warp reads shared positions of its own lanes and of the edge lanes of the
+// two adjacent warps only, so each sub-step synchronises adjacent warp pairs
+// (named barrier w + 1 joins warps w and w + 1) instead of the whole CTA.
+// Every warp waits on its left pair first, then its right pair, so the waits
+// form no cycle.  With two position buffers a warp can run at most one
+// sub-step ahead of a neighbour, which has by then finished reading the buffer
+// it is about to overwrite.
+static_assert(kStepBlock / 32 <= 16, "named barriers 1..15 cover at most 16 warps");
+__device__ __forceinline__ void neighbour_sync(int w) {
+    constexpr int kWarps = kStepBlock / 32;
+    if (w > 0) asm volatile("bar.sync %0, 64;" ::"r"(w) : "memory");
+    if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
+}
+
 template <bool kNoise>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
@@ -162,7 +176,7 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
         sx[b * kStepBlock + t] = x;
         sy[b * kStepBlock + t] = y;
         sz[b * kStepBlock + t] = z;
-        __syncthreads();
+        neighbour_sync(t >> 5);
         const float s0 = __fmul_rn(x, g.inv_h[0]), s1 = __fmul_rn(y, g.inv_h[1]),
                     s2 = __fmul_rn(z, g.inv_h[2]);
         const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
