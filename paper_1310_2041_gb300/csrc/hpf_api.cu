@@ -27,6 +27,8 @@ struct hpf_ctx {
     SortBufs sb{};
     void* sort_mem = nullptr;
     int C = 0;                        // number of chains
+    int max_chain = 0;                // longest chain (beads)
+    bool warp_mode = false;           // chains fit warp segments: barrier-free step kernel
     long long last_sort_step = 0;
     unsigned long long* D = nullptr;  // two int64 density meshes, [2][S][M]
     int dmesh = 0;                    // which one is the context's mesh
@@ -282,7 +284,9 @@ hpf_status ensure_field(hpf_ctx* c) {
 hpf_status sort_beads(hpf_ctx* c) {
     {
         StageScope sc(c, HPF_STAGE_SORT, 0);
-        sc.kernels = launch_sort(c->sb, c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->meta2, c->n,
+        SortBufs b = c->sb;
+        if (!c->warp_mode) b.seg_start = nullptr;
+        sc.kernels = launch_sort(b, c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->meta2, c->n,
                                  c->C, c->geom, c->stream);
     }
     LAUNCH_CHECK(c);
@@ -353,7 +357,7 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     e = e ? e : cudaMalloc(&c->meta2, sizeof(uint32_t) * n);
     const long long K = sort_key_space(c->geom);
     const long long scan_words = scan_scratch_words(K > (long long)n ? K : (long long)n);
-    const size_t sort_words = 9 * n + 3 * (size_t)K + (size_t)scan_words + 64;
+    const size_t sort_words = 13 * n + 2 * (n / 256 + 2) + 3 * (size_t)K + (size_t)scan_words + 64;
     e = e ? e : cudaMalloc(&c->sort_mem, sizeof(uint32_t) * sort_words);
     e = e ? e : cudaMalloc(&c->D, 2 * sizeof(unsigned long long) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->G, sizeof(float4) * (size_t)c->geom.gnodes * c->S);
@@ -382,6 +386,12 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
         b.newstart = w; w += n;
         b.chain_of_in = (int*)w; w += n;
         b.chain_of_out = (int*)w; w += n;
+        b.seg_start = (int*)w; w += n;
+        b.seg_count = (int*)w; w += n;
+        b.seg_tmp = (int*)w; w += 2 * n;
+        b.chunk_nseg = w; w += n / 256 + 2;
+        b.chunk_off = w; w += n / 256 + 2;
+        b.n_seg = (int*)w; w += 1;
         b.count = w; w += K;
         b.binoff = w; w += K;
         b.cursor = w; w += K;
@@ -485,11 +495,17 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
         c->C = c->hflag[5] + ((last_meta & kBondPrev) ? 0 : 1);
         {
             StageScope sc(c, HPF_STAGE_SORT, 2);
+            CUDA_TRY(c, cudaMemsetAsync(c->dflag + 7, 0, sizeof(int), c->stream));
             launch_chain_build(c->meta, c->sb.newstart, n, c->C, c->sb.cstart, c->sb.tag0,
-                               c->sb.chain_of_in, c->sb.clen, c->stream);
+                               c->sb.chain_of_in, c->sb.clen, c->dflag + 7, c->stream);
         }
         LAUNCH_CHECK(c);
+        CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 7, c->dflag + 7, sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->max_chain = c->hflag[7];
     }
+    c->warp_mode = n > 0 && c->max_chain <= 64;
     c->step = step;
     c->mesh_step = -1;
     hpf_status s2 = sort_beads(c);
@@ -586,7 +602,9 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         if (s != HPF_OK) return s;
         long long chunk = fe - (c->step % fe);  // steps until the next refresh
         if (chunk > left) chunk = left;
-        if (chunk > step_halo_max()) chunk = step_halo_max();
+        // the halo form recomputes `chunk` beads per side; the warp form has no halo
+        if (chunk > (c->warp_mode ? 64 : step_halo_max()))
+            chunk = c->warp_mode ? 64 : step_halo_max();
         if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
             if ((s = sort_beads(c)) != HPF_OK) return s;
         }
@@ -595,8 +613,13 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         unsigned long long* Dnext = fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
         {
             StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
-            launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
-                        c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
+            if (c->warp_mode)
+                launch_step_warp(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n,
+                                 c->sb.seg_start, c->sb.seg_count, c->sb.n_seg, c->C, (int)chunk,
+                                 c->step, c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
+            else
+                launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
+                            c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
         }
         LAUNCH_CHECK(c);
         c->cur ^= 1;

@@ -105,6 +105,13 @@ struct SortBufs {
     int* chain_of_in;   // [n] chain of each bead, current order
     int* chain_of_out;  // [n]
     uint32_t* scratch;  // scan scratch
+    // warp segments (whole chains, <= 64 beads each); seg_start == nullptr: not built
+    int* seg_start;     // [C]
+    int* seg_count;     // [C]
+    int* seg_tmp;       // [2 C]
+    uint32_t* chunk_nseg;  // [C / 256 + 1]
+    uint32_t* chunk_off;   // [C / 256 + 1]
+    int* n_seg;         // device scalar: number of segments
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -315,11 +322,15 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, long long L, uint32_t* scr
 int launch_chain_build_heads(const uint32_t* meta, int n, uint32_t* hd, uint32_t* scratch,
                              cudaStream_t s);
 int launch_chain_build(const uint32_t* meta, const uint32_t* hx, int n, int C, int* cstart,
-                       uint32_t* tag0, int* chain_of, int* clen, cudaStream_t s);
+                       uint32_t* tag0, int* chain_of, int* clen, int* max_len, cudaStream_t s);
 int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* meta_in,
                 uint32_t* meta_out, int n, int C, MeshGeom g, cudaStream_t s);
 
 int step_halo_max();
+void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
+                      const int* seg_start, const int* seg_count, const int* n_seg, int max_seg,
+                      int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,
+                      unsigned long long* D_next, int* flag, cudaStream_t s);
 int energy_partials_needed(int n, int nodes);
 
 }  // namespace hpf

@@ -121,9 +121,13 @@ __global__ void k_chain_build(const uint32_t* __restrict__ meta, const uint32_t*
     }
 }
 
-__global__ void k_chain_len(const int* __restrict__ cstart, int C, int n, int* __restrict__ clen) {
+__global__ void k_chain_len(const int* __restrict__ cstart, int C, int n, int* __restrict__ clen,
+                            int* __restrict__ max_len) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) clen[c] = (c + 1 < C ? cstart[c + 1] : n) - cstart[c];
+    if (c >= C) return;
+    const int len = (c + 1 < C ? cstart[c + 1] : n) - cstart[c];
+    clen[c] = len;
+    atomicMax(max_len, len);
 }
 
 // ------------------------------------------------------------------ sort
@@ -203,6 +207,57 @@ __global__ void k_update_cstart(const int* __restrict__ rank_of,
     if (c < C) cstart[c] = (int)newstart[rank_of[c]];
 }
 
+// ------------------------------------------------------------------ warp segments
+//
+// Consecutive whole chains (in storage order) are packed greedily into
+// segments of at most kSegBeads beads, one warp per segment.  Each thread
+// packs one chunk of kPackChunk chain positions sequentially (segments do not
+// straddle chunks), then the per-chunk segment lists are concatenated.
+constexpr int kPackChunk = 256;
+constexpr int kSegBeads = 64;
+
+__global__ void k_pack_chunks(const uint32_t* __restrict__ newstart, int C, int n,
+                              int* __restrict__ tmp_start, int* __restrict__ tmp_count,
+                              uint32_t* __restrict__ chunk_nseg) {
+    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p0 = chunk * kPackChunk;
+    if (p0 >= C) return;
+    const int p1 = min(C, p0 + kPackChunk);
+    int cur_start = 0, cur_count = 0, k = 0;
+    for (int p = p0; p < p1; ++p) {
+        const int st = (int)newstart[p];
+        const int len = (p + 1 < C ? (int)newstart[p + 1] : n) - st;
+        if (cur_count > 0 && cur_count + len > kSegBeads) {
+            tmp_start[p0 + k] = cur_start;
+            tmp_count[p0 + k] = cur_count;
+            ++k;
+            cur_count = 0;
+        }
+        if (cur_count == 0) cur_start = st;
+        cur_count += len;
+    }
+    tmp_start[p0 + k] = cur_start;
+    tmp_count[p0 + k] = cur_count;
+    chunk_nseg[chunk] = (uint32_t)(k + 1);
+}
+
+__global__ void k_gather_segments(const int* __restrict__ tmp_start,
+                                  const int* __restrict__ tmp_count,
+                                  const uint32_t* __restrict__ chunk_nseg,
+                                  const uint32_t* __restrict__ chunk_off, int C, int n_chunks,
+                                  int* __restrict__ seg_start, int* __restrict__ seg_count,
+                                  int* __restrict__ n_seg) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= C) return;
+    const int chunk = slot / kPackChunk, k = slot % kPackChunk;
+    if (k < (int)chunk_nseg[chunk]) {
+        const int w = (int)chunk_off[chunk] + k;
+        seg_start[w] = tmp_start[slot];
+        seg_count[w] = tmp_count[slot];
+    }
+    if (slot == 0) *n_seg = (int)(chunk_off[n_chunks - 1] + chunk_nseg[n_chunks - 1]);
+}
+
 // ------------------------------------------------------------------ host side
 
 long long sort_key_space(const MeshGeom& g) {
@@ -219,10 +274,10 @@ int launch_chain_build_heads(const uint32_t* meta, int n, uint32_t* hd, uint32_t
 }
 
 int launch_chain_build(const uint32_t* meta, const uint32_t* hx, int n, int C, int* cstart,
-                       uint32_t* tag0, int* chain_of, int* clen, cudaStream_t s) {
+                       uint32_t* tag0, int* chain_of, int* clen, int* max_len, cudaStream_t s) {
     if (n <= 0) return 0;
     k_chain_build<<<(n + 255) / 256, 256, 0, s>>>(meta, hx, n, cstart, tag0, chain_of);
-    k_chain_len<<<(C + 255) / 256, 256, 0, s>>>(cstart, C, n, clen);
+    k_chain_len<<<(C + 255) / 256, 256, 0, s>>>(cstart, C, n, clen, max_len);
     return 2;
 }
 
@@ -246,7 +301,17 @@ int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* me
     k_permute_beads<<<nb, 256, 0, s>>>(in, out, meta_in, meta_out, b.chain_of_in, b.chain_of_out,
                                        b.cstart, b.rank_of, b.newstart, n);
     k_update_cstart<<<cb, 256, 0, s>>>(b.rank_of, b.newstart, C, b.cstart);
-    return launched + 2;
+    launched += 2;
+    if (b.seg_start) {
+        const int n_chunks = (C + kPackChunk - 1) / kPackChunk;
+        k_pack_chunks<<<(n_chunks + 127) / 128, 128, 0, s>>>(b.newstart, C, n, b.seg_tmp,
+                                                            b.seg_tmp + C, b.chunk_nseg);
+        launched += 1 + scan_exclusive(b.chunk_nseg, b.chunk_off, n_chunks, b.scratch, s);
+        k_gather_segments<<<cb, 256, 0, s>>>(b.seg_tmp, b.seg_tmp + C, b.chunk_nseg, b.chunk_off,
+                                             C, n_chunks, b.seg_start, b.seg_count, b.n_seg);
+        ++launched;
+    }
+    return launched;
 }
 
 }  // namespace hpf

@@ -69,7 +69,8 @@ constexpr size_t kStepSmem = sizeof(float4) * kCachePlanes * kStepBlock +
 
 __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
                                                 float flx, float fly, float flz,
-                                                float4* __restrict__ cache, int t) {
+                                                float4* __restrict__ cache, int t,
+                                                int stride = kStepBlock) {
     const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
     float wx = __fmaf_rn(-fmx, floorf((flx + 0.5f) * g.inv_m[0]), flx);
     float wy = __fmaf_rn(-fmy, floorf((fly + 0.5f) * g.inv_m[1]), fly);
@@ -93,8 +94,8 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
         const float a5 = (g101.comp - g100.comp) - a3;                                           \
         const float a6 = (g011.comp - g010.comp) - a3;                                           \
         const float a7 = ((g111.comp - g110.comp) - (g101.comp - g100.comp)) - a6;               \
-        cache[(2 * j) * kStepBlock + t] = make_float4(a0, a1, a2, a3);                           \
-        cache[(2 * j + 1) * kStepBlock + t] = make_float4(a4, a5, a6, a7);                       \
+        cache[(2 * j) * stride + t] = make_float4(a0, a1, a2, a3);                               \
+        cache[(2 * j + 1) * stride + t] = make_float4(a4, a5, a6, a7);                           \
     }
     HPF_COEF(x, 0)
     HPF_COEF(y, 1)
@@ -117,10 +118,10 @@ __device__ __forceinline__ float cell_poly(const float4 lo, const float4 hi, flo
 
 __device__ __forceinline__ void eval_cell_cache(const float4* __restrict__ cache, int t, float fx,
                                                 float fy, float fz, float& Fx, float& Fy,
-                                                float& Fz) {
-    Fx -= cell_poly(cache[0 * kStepBlock + t], cache[1 * kStepBlock + t], fx, fy, fz);
-    Fy -= cell_poly(cache[2 * kStepBlock + t], cache[3 * kStepBlock + t], fx, fy, fz);
-    Fz -= cell_poly(cache[4 * kStepBlock + t], cache[5 * kStepBlock + t], fx, fy, fz);
+                                                float& Fz, int stride = kStepBlock) {
+    Fx -= cell_poly(cache[0 * stride + t], cache[1 * stride + t], fx, fy, fz);
+    Fy -= cell_poly(cache[2 * stride + t], cache[3 * stride + t], fx, fy, fz);
+    Fz -= cell_poly(cache[4 * stride + t], cache[5 * stride + t], fx, fy, fz);
 }
 
 // A warp reads shared positions of its own lanes and of the edge lanes of the
@@ -253,6 +254,168 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
     else
         k_step<false><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub, step0,
                                                             g, G, c, D_next, flag);
+}
+
+// ------------------------------------------------------------------ A6, warp form
+//
+// When every chain has at most 64 beads the sort also packs consecutive whole
+// chains into segments of at most 64 beads, and one warp advances one segment
+// for all n_sub steps on its own: lane l holds beads 2l and 2l + 1, so a
+// bead's chain neighbours are either its partner in the same lane or the
+// neighbouring lane's bead, exchanged with register shuffles.  No halo, no
+// shared positions and no barrier: warps never wait for one another.  The
+// field is sampled through the same per-bead cell cache as above (two slots
+// per thread).  A persistent grid walks the segment list, whose length is
+// read on the device so a re-sort needs no host synchronisation.
+constexpr int kWarpBlock = 256;
+constexpr size_t kWarpSmem = sizeof(float4) * kCachePlanes * 2 * kWarpBlock;
+
+struct Bead {
+    float x, y, z, vx, vy, vz;
+    uint32_t m;
+    float cfx, cfy, cfz;  // cached cell (floor of the mesh coordinate), NaN: none
+};
+
+template <bool kNoise>
+__device__ __forceinline__ void advance_bead(Bead& b, float px, float py, float pz, bool has_p,
+                                             float qx, float qy, float qz, bool has_q,
+                                             const float4* __restrict__ G, const MeshGeom& g,
+                                             const StepConsts& c, long long step,
+                                             float4* __restrict__ cache, int slot) {
+    const float s0 = __fmul_rn(b.x, g.inv_h[0]), s1 = __fmul_rn(b.y, g.inv_h[1]),
+                s2 = __fmul_rn(b.z, g.inv_h[2]);
+    const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
+    if (flx != b.cfx || fly != b.cfy || flz != b.cfz) {
+        fill_cell_cache(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx, fly, flz,
+                        cache, slot, 2 * kWarpBlock);
+        b.cfx = flx;
+        b.cfy = fly;
+        b.cfz = flz;
+    }
+    float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
+    eval_cell_cache(cache, slot, __fsub_rn(s0, flx), __fsub_rn(s1, fly), __fsub_rn(s2, flz), fx,
+                    fy, fz, 2 * kWarpBlock);
+    if (kNoise) {
+        float nx, ny, nz;
+        gauss3(c, b.m & kTagMask, step, nx, ny, nz);
+        fx = fmaf(c.sigma, nx, fx);
+        fy = fmaf(c.sigma, ny, fy);
+        fz = fmaf(c.sigma, nz, fz);
+    }
+    bond_force(b.x - px, b.y - py, b.z - pz, has_p ? c.two_k : 0.0f, c.r0, fx, fy, fz);
+    bond_force(b.x - qx, b.y - qy, b.z - qz, has_q ? c.two_k : 0.0f, c.r0, fx, fy, fz);
+    b.vx = fmaf(c.dt_m, fx, b.vx);
+    b.vy = fmaf(c.dt_m, fy, b.vy);
+    b.vz = fmaf(c.dt_m, fz, b.vz);
+}
+
+__device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf out,
+                                            const MeshGeom& g, unsigned long long* D_next,
+                                            int* flag) {
+    out.x[i] = b.x;
+    out.y[i] = b.y;
+    out.z[i] = b.z;
+    out.vx[i] = b.vx;
+    out.vy[i] = b.vy;
+    out.vz[i] = b.vz;
+    const bool finite = isfinite(b.x) && isfinite(b.y) && isfinite(b.z) && isfinite(b.vx) &&
+                        isfinite(b.vy) && isfinite(b.vz);
+    if (!finite) atomicOr(flag, kFlagNonFinite);
+    else if (!(coord_in_range(b.x, g.inv_h[0]) && coord_in_range(b.y, g.inv_h[1]) &&
+               coord_in_range(b.z, g.inv_h[2])))
+        atomicOr(flag, kFlagRange);
+    if (D_next) {
+        const AxisCoord ax = axis_coord(b.x, g.inv_h[0], g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_coord(b.y, g.inv_h[1], g.my, g.inv_m[1]);
+        const AxisCoord az = axis_coord(b.z, g.inv_h[2], g.mz, g.inv_m[2]);
+        scatter_bead(D_next + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.nodes, g, ax, ay, az);
+    }
+}
+
+template <bool kNoise>
+__global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp(
+    StateBuf in, StateBuf out, const uint32_t* __restrict__ meta, int n,
+    const int* __restrict__ seg_start, const int* __restrict__ seg_count,
+    const int* __restrict__ n_seg, int n_sub, long long step0, MeshGeom g,
+    const float4* __restrict__ G, StepConsts c, unsigned long long* __restrict__ D_next,
+    int* __restrict__ flag) {
+    extern __shared__ float4 wcache[];  // [kCachePlanes][2 * kWarpBlock]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nseg = *n_seg;
+    const int warps_total = gridDim.x * (kWarpBlock / 32);
+    const float nan = __int_as_float(0x7fc00000);
+    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < nseg; w += warps_total) {
+        const int base = seg_start[w], cnt = seg_count[w];
+        const int j0 = 2 * lane, j1 = j0 + 1;
+        const bool a0 = j0 < cnt, a1 = j1 < cnt;
+        Bead b0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, nan, nan, nan};
+        Bead b1 = b0;
+        if (a0) {
+            const long long i = (long long)base + j0;
+            b0.x = in.x[i]; b0.y = in.y[i]; b0.z = in.z[i];
+            b0.vx = in.vx[i]; b0.vy = in.vy[i]; b0.vz = in.vz[i];
+            b0.m = meta[i];
+        }
+        if (a1) {
+            const long long i = (long long)base + j1;
+            b1.x = in.x[i]; b1.y = in.y[i]; b1.z = in.z[i];
+            b1.vx = in.vx[i]; b1.vy = in.vy[i]; b1.vz = in.vz[i];
+            b1.m = meta[i];
+        }
+        // whole chains: every flagged neighbour is inside the segment
+        const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
+        const bool p1 = (b1.m & kBondPrev) != 0, n1 = (b1.m & kBondNext) != 0;
+        for (int k = 0; k < n_sub; ++k) {
+            // bead 2l - 1 (previous lane's second bead) and bead 2l + 2 (next lane's first)
+            const float ux = __shfl_up_sync(0xffffffffu, b1.x, 1);
+            const float uy = __shfl_up_sync(0xffffffffu, b1.y, 1);
+            const float uz = __shfl_up_sync(0xffffffffu, b1.z, 1);
+            const float dx = __shfl_down_sync(0xffffffffu, b0.x, 1);
+            const float dy = __shfl_down_sync(0xffffffffu, b0.y, 1);
+            const float dz = __shfl_down_sync(0xffffffffu, b0.z, 1);
+            const float x0 = b0.x, y0 = b0.y, z0 = b0.z;
+            advance_bead<kNoise>(b0, ux, uy, uz, p0, b1.x, b1.y, b1.z, n0, G, g, c, step0 + k,
+                                 wcache, tid);
+            advance_bead<kNoise>(b1, x0, y0, z0, p1, dx, dy, dz, n1, G, g, c, step0 + k, wcache,
+                                 kWarpBlock + tid);
+            b0.x = fmaf(c.dt, b0.vx, b0.x);
+            b0.y = fmaf(c.dt, b0.vy, b0.y);
+            b0.z = fmaf(c.dt, b0.vz, b0.z);
+            b1.x = fmaf(c.dt, b1.vx, b1.x);
+            b1.y = fmaf(c.dt, b1.vy, b1.y);
+            b1.z = fmaf(c.dt, b1.vz, b1.z);
+        }
+        if (a0) finish_bead(b0, (long long)base + j0, out, g, D_next, flag);
+        if (a1) finish_bead(b1, (long long)base + j1, out, g, D_next, flag);
+    }
+}
+
+void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
+                      const int* seg_start, const int* seg_count, const int* n_seg, int max_seg,
+                      int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,
+                      unsigned long long* D_next, int* flag, cudaStream_t s) {
+    if (n <= 0 || n_sub <= 0 || max_seg <= 0) return;
+    static int grid_cap = 0;
+    if (!grid_cap) {
+        cudaFuncSetAttribute(k_step_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp<true>, kWarpBlock,
+                                                      kWarpSmem);
+        grid_cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+    const int blocks = need < grid_cap ? need : grid_cap;
+    if (c.sigma > 0.f)
+        k_step_warp<true><<<blocks, kWarpBlock, kWarpSmem, s>>>(
+            in, out, meta, n, seg_start, seg_count, n_seg, n_sub, step0, g, G, c, D_next, flag);
+    else
+        k_step_warp<false><<<blocks, kWarpBlock, kWarpSmem, s>>>(
+            in, out, meta, n, seg_start, seg_count, n_seg, n_sub, step0, g, G, c, D_next, flag);
 }
 
 // ------------------------------------------------------------------ A7 FP64 observables

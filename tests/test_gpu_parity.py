@@ -167,6 +167,24 @@ def test_mesh_deposited_by_the_step_kernel_is_exact(hpf_gpu, orc, fe, steps):
     assert E[2] == pytest.approx(orc.field_energy(op, Do), rel=1e-12)
 
 
+def test_long_chains_take_the_halo_kernel(hpf_gpu, orc):
+    """Chains longer than 64 beads cannot be packed into warp segments; the
+    CTA kernel with recomputed halos advances them."""
+    w = W.diblock(30, 50, 50, 10.0, 10, 1.0, field_every=5)
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
+def test_long_field_period_in_warp_launches(hpf_gpu, orc):
+    """field_every = 50: whole 50-step periods in one warp launch each."""
+    w = W.diblock(120, 8, 12, 9.0, 9, 1.0, field_every=50)
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 100)
+    # 100 steps of FP32 rounding against the FP64 oracle
+    assert np.max(np.abs(pos - po)) <= 1e-3
+    assert np.max(np.abs(vel - vo)) <= 1e-3
+
+
 def test_nve_trajectory_without_thermostat(hpf_gpu, orc):
     w = W.a5b5_10k()
     pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10, gamma=0.0)
