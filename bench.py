@@ -330,10 +330,86 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 uneven A8B12 replicas (chi 0.2 .. 2.0): one batch vs 64 separate contexts."""
+    import torch
+    from paper_1310_2041_gb300 import hpf, workloads as W
+
+    torch.cuda.set_device(0)
+    ws = W.replica_set()
+    n_total = sum(w.n_beads for w in ws)
+    stream = torch.cuda.Stream()
+    params = []
+    for w in ws:
+        p = w.params()
+        p["sort_every"] = args.sort_every
+        params.append(hpf.make_params(**p))
+    data = [W.generate(w) for w in ws]
+    fe = ws[0].field_every
+
+    def load(target_states):
+        for s, d in zip(target_states, data):
+            s.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+
+    def timed(run, steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        run(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    with torch.cuda.stream(stream):
+        batch = hpf.Batch(params, stream=stream)
+        load(batch.replicas)
+        batch.step(args.warmup)
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        ms_batch = timed(batch.step, args.steps)
+        clk = clocks.stop()
+        batch.close()
+        plain = [hpf.System(p, stream=stream) for p in params]
+        load(plain)
+        for s in plain:
+            s.step(args.warmup)
+
+        def plain_run(steps):
+            left = steps
+            while left > 0:
+                c = min(fe, left)
+                for s in plain:
+                    s.step(c)
+                left -= c
+        ms_plain = timed(plain_run, args.steps)
+        for s in plain:
+            s.close()
+    value = n_total * args.steps / (ms_batch * 1e-3)
+    plain_value = n_total * args.steps / (ms_plain * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "replicas64_a8b12", "n_beads": n_total, "replicas": len(ws),
+                       "field_every": fe, "sort_every": args.sort_every,
+                       "l2": "state of all replicas (~200 MB) larger than L2, no flush",
+                       "form": "one batched field + persistent step launch per period, CUDA "
+                               "graph replays",
+                       "plain_value": plain_value, "plain_form": "64 contexts, hpf_step each",
+                       "speedup_vs_plain": value / plain_value},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "replicas64":
+        return run_batch(args)
     return run_ours(args)
 
 

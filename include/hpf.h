@@ -196,6 +196,51 @@ hpf_status hpf_profile(hpf_ctx* ctx, int32_t enable);
 hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
                             int64_t launches[HPF_STAGE_COUNT]);
 
+/* ---- Batched replicas ----------------------------------------------------
+ *
+ * Many independent systems (for instance a chi scan of a phase diagram, each
+ * replica with its own bead count, box, mesh and chi) advanced together.  The
+ * paper runs one system per GPU; batching is this library's addition.  A
+ * batch owns one hpf_ctx per replica, so every per-system call (set/get
+ * state, forces, energy, density, field, order) works on a replica through
+ * hpf_batch_replica.  hpf_batch_step advances all replicas with one batched
+ * field launch and one persistent step launch per field period: the step
+ * kernel's warps walk the segment lists of all replicas at once, so replicas
+ * of 20k beads, which would fill a fraction of the GPU alone, share it.
+ *
+ * Requirements checked by hpf_batch_step (HPF_ERR_STATE otherwise): every
+ * replica has a state, all replicas are at the same step, and all chains are
+ * at most 64 beads (the warp-segment form); replicas with longer chains make
+ * hpf_batch_step fall back to stepping the replicas one after another.
+ * Requirements checked by hpf_batch_init (HPF_ERR_INVALID): 1 <= n_replicas
+ * <= HPF_MAX_REPLICAS, equal n_species, field_every and sort_every. */
+#define HPF_MAX_REPLICAS 64
+
+typedef struct hpf_batch hpf_batch;
+
+/* params: [n_replicas] parameter sets; stream as in hpf_init.
+ * Errors: as hpf_init, plus HPF_ERR_INVALID for the batch requirements. */
+hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* stream,
+                          hpf_batch** out);
+
+/* The context of replica r (owned by the batch; do not destroy it).  NULL if r is out of range. */
+hpf_ctx* hpf_batch_replica(hpf_batch* batch, int32_t r);
+
+/* Advance every replica by n_steps (asynchronous).  Each replica follows
+ * exactly the same step as hpf_step on its own context would (same field
+ * schedule, same Philox counters keyed by its own seed and tags), so the
+ * results are those of R independent runs.  With graphs enabled (the
+ * default), each pair of steady-state field periods is replayed from a CUDA
+ * graph captured once per bead order.
+ * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_batch_step(hpf_batch* batch, int32_t n_steps);
+
+/* Use CUDA graphs for steady-state periods (1, default) or plain launches (0). */
+hpf_status hpf_batch_use_graphs(hpf_batch* batch, int32_t enable);
+
+/* Free the batch and its replica contexts.  NULL is a no-op. */
+hpf_status hpf_batch_destroy(hpf_batch* batch);
+
 /* ---- Field forces without any device allocation ---------------------------
  *
  * The paper has no counterpart to this entry point.  It is here for callers

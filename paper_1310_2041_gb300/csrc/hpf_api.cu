@@ -683,3 +683,335 @@ hpf_status hpf_profile_read(hpf_ctx* c, double ms[HPF_STAGE_COUNT],
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct hpf_batch {
+    int R = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<hpf_ctx*> rep;
+    bool use_graphs = true;
+    FieldCoef* d_coef = nullptr;  // [R]
+    long long* d_step = nullptr;  // step counter read by graph replays
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> graph_key;  // buffers the captured graph refers to
+    std::string err;
+};
+
+namespace {
+
+hpf_status bfail(hpf_batch* b, hpf_status s, const char* msg) {
+    if (b) b->err = msg;
+    return s;
+}
+
+// Batched refresh of the replicas whose field is due (all of them in steady state).
+hpf_status batch_refresh(hpf_batch* b) {
+    BatchFieldParams fp;
+    memset(&fp, 0, sizeof fp);
+    fp.coef = b->d_coef;
+    hpf_ctx* c0 = b->rep[0];
+    for (int r = 0; r < b->R; ++r) {
+        hpf_ctx* c = b->rep[r];
+        const bool due = !c->field_valid || (c->step % c->p.field_every == 0 && c->field_step != c->step);
+        if (!due) continue;
+        hpf_status s = scatter_current(c);
+        if (s != HPF_OK) return s;
+        BatchFieldRep& fr = fp.rep[fp.R];
+        fr.g = c->geom;
+        fr.D = reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh));
+        fr.G = c->G;
+        fr.D_clear = mesh_buf(c, c->dmesh ^ 1);
+        fr.blk_begin = fp.blocks;
+        fp.blocks += (c->geom.gnodes + 255) / 256;
+        // the coefficient record of replica r sits at d_coef[r]; re-index for this launch
+        fp.R++;
+    }
+    if (fp.R == 0) return HPF_OK;
+    if (fp.R != b->R) {
+        // only some replicas are due: run them one by one
+        for (int r = 0; r < b->R; ++r) {
+            hpf_ctx* c = b->rep[r];
+            const bool due = !c->field_valid || (c->step % c->p.field_every == 0 && c->field_step != c->step);
+            if (due) {
+                hpf_status s = run_field(c);
+                if (s != HPF_OK) return s;
+            }
+        }
+        return HPF_OK;
+    }
+    {
+        StageScope sc(c0, HPF_STAGE_FIELD, 1);
+        launch_field_batch(fp, c0->S, b->stream);
+    }
+    LAUNCH_CHECK(c0);
+    for (auto* c : b->rep) {
+        c->next_zero = true;
+        c->field_valid = true;
+        c->field_step = c->step;
+    }
+    return HPF_OK;
+}
+
+void fill_step_params(hpf_batch* b, BatchStepParams& p, int n_sub, bool fuse) {
+    memset(&p, 0, sizeof p);
+    hpf_ctx* c0 = b->rep[0];
+    p.R = b->R;
+    p.n_sub = n_sub;
+    p.cur = c0->cur;
+    p.fuse = fuse ? 1 : 0;
+    p.dnext = c0->dmesh ^ 1;
+    p.step0 = c0->step;
+    p.step_dev = nullptr;
+    p.flag = c0->dflag;
+    for (int r = 0; r < b->R; ++r) {
+        hpf_ctx* c = b->rep[r];
+        BatchStepRep& q = p.rep[r];
+        q.g = c->geom;
+        q.c = c->sc;
+        q.st[0] = c->st[0];
+        q.st[1] = c->st[1];
+        q.meta = c->meta;
+        q.seg_start = c->sb.seg_start;
+        q.seg_count = c->sb.seg_count;
+        q.n_seg = c->sb.n_seg;
+        q.G = c->G;
+        q.D[0] = mesh_buf(c, 0);
+        q.D[1] = mesh_buf(c, 1);
+    }
+}
+
+int batch_max_segments(hpf_batch* b) {
+    int m = 0;
+    for (auto* c : b->rep) m += c->C;
+    return m;
+}
+
+bool batch_noise(hpf_batch* b) {
+    for (auto* c : b->rep)
+        if (c->sc.sigma > 0.f) return true;
+    return false;
+}
+
+void batch_advance(hpf_batch* b, long long chunk, bool fuse) {
+    for (auto* c : b->rep) {
+        c->cur ^= 1;
+        c->step += chunk;
+        if (fuse) {
+            c->dmesh ^= 1;
+            c->mesh_step = c->step;
+            c->next_zero = false;
+        }
+    }
+}
+
+std::vector<const void*> batch_key(hpf_batch* b) {
+    std::vector<const void*> k;
+    for (auto* c : b->rep) {
+        k.push_back(c->meta);
+        k.push_back((const void*)(intptr_t)(c->cur * 2 + c->dmesh));
+    }
+    return k;
+}
+
+// Capture two steady-state field periods (refresh + fused step, twice), after
+// which every buffer parity is back where it started, so the graph can be
+// replayed; the step number comes from b->d_step, advanced inside the graph.
+hpf_status batch_capture(hpf_batch* b) {
+    hpf_ctx* c0 = b->rep[0];
+    const int fe = c0->p.field_every;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int half = 0; half < 2; ++half) {
+        BatchFieldParams fp;
+        memset(&fp, 0, sizeof fp);
+        fp.coef = b->d_coef;
+        for (int r = 0; r < b->R; ++r) {
+            hpf_ctx* c = b->rep[r];
+            const int dm = c->dmesh ^ half;
+            BatchFieldRep& fr = fp.rep[r];
+            fr.g = c->geom;
+            fr.D = reinterpret_cast<const long long*>(mesh_buf(c, dm));
+            fr.G = c->G;
+            fr.D_clear = mesh_buf(c, dm ^ 1);
+            fr.blk_begin = fp.blocks;
+            fp.blocks += (c->geom.gnodes + 255) / 256;
+        }
+        fp.R = b->R;
+        launch_field_batch(fp, c0->S, b->stream);
+        BatchStepParams sp;
+        fill_step_params(b, sp, fe, true);
+        sp.cur = c0->cur ^ half;
+        sp.dnext = c0->dmesh ^ half ^ 1;
+        sp.step_dev = b->d_step;
+        launch_step_warp_batch(sp, batch_max_segments(b), batch_noise(b), b->stream);
+        launch_advance_counter(b->d_step, fe, b->stream);
+    }
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c0, HPF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->gexec = nullptr;
+        return fail(c0, HPF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    b->graph_key = batch_key(b);
+    return HPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* stream,
+                          hpf_batch** out) {
+    if (!out) return HPF_ERR_INVALID;
+    *out = nullptr;
+    if (!params || n_replicas < 1 || n_replicas > HPF_MAX_REPLICAS) return HPF_ERR_INVALID;
+    for (int r = 1; r < n_replicas; ++r)
+        if (params[r].n_species != params[0].n_species ||
+            params[r].field_every != params[0].field_every ||
+            params[r].sort_every != params[0].sort_every)
+            return HPF_ERR_INVALID;
+    hpf_batch* b = new hpf_batch();
+    b->R = n_replicas;
+    b->stream = (cudaStream_t)stream;
+    for (int r = 0; r < n_replicas; ++r) {
+        hpf_ctx* c = nullptr;
+        hpf_status s = hpf_init(&params[r], stream, &c);
+        if (s != HPF_OK) {
+            hpf_batch_destroy(b);
+            return s;
+        }
+        b->rep.push_back(c);
+    }
+    std::vector<FieldCoef> coefs(n_replicas);
+    for (int r = 0; r < n_replicas; ++r) coefs[r] = b->rep[r]->coef;
+    cudaError_t e = cudaMalloc(&b->d_coef, sizeof(FieldCoef) * n_replicas);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_coef, coefs.data(), sizeof(FieldCoef) * n_replicas,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hpf_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA;
+    }
+    b->use_graphs = b->stream != nullptr;  // no capture on the legacy default stream
+    *out = b;
+    return HPF_OK;
+}
+
+hpf_ctx* hpf_batch_replica(hpf_batch* b, int32_t r) {
+    if (!b || r < 0 || r >= b->R) return nullptr;
+    return b->rep[r];
+}
+
+hpf_status hpf_batch_use_graphs(hpf_batch* b, int32_t enable) {
+    if (!b) return HPF_ERR_INVALID;
+    b->use_graphs = enable != 0 && b->stream != nullptr;
+    return HPF_OK;
+}
+
+hpf_status hpf_batch_destroy(hpf_batch* b) {
+    if (!b) return HPF_OK;
+    cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto* c : b->rep) hpf_destroy(c);
+    cudaFree(b->d_coef);
+    cudaFree(b->d_step);
+    cudaGetLastError();
+    delete b;
+    return HPF_OK;
+}
+
+hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
+    if (!b) return HPF_ERR_INVALID;
+    if (n_steps < 0) return bfail(b, HPF_ERR_INVALID, "n_steps must be >= 0");
+    hpf_ctx* c0 = b->rep[0];
+    bool lockstep = true, warp = true;
+    for (auto* c : b->rep) {
+        if (!c->has_state) return bfail(b, HPF_ERR_STATE, "a replica has no state");
+        if (c->step != c0->step) return bfail(b, HPF_ERR_STATE, "replicas are at different steps");
+        warp = warp && c->warp_mode;
+        lockstep = lockstep && c->cur == c0->cur && c->dmesh == c0->dmesh;
+    }
+    if (!warp || !lockstep) {
+        for (auto* c : b->rep) {
+            hpf_status s = hpf_step(c, n_steps);
+            if (s != HPF_OK) return s;
+        }
+        return HPF_OK;
+    }
+    const long long fe = c0->p.field_every;
+    const int se = c0->p.sort_every;
+    long long left = n_steps;
+    hpf_status s;
+    while (left > 0) {
+        // steady state: replay two captured periods at a time
+        const bool aligned = c0->step % fe == 0 && fe <= 64;
+        bool steady = aligned && b->use_graphs && left >= 2 * fe;
+        for (auto* c : b->rep)
+            steady = steady && c->mesh_step == c->step && c->field_step != c->step &&
+                     c->cur == c0->cur && c->dmesh == c0->dmesh;
+        if (steady) {
+            long long pairs = left / (2 * fe);
+            if (se > 0) {
+                const long long to_sort = c0->last_sort_step + se - c0->step;
+                const long long sort_pairs = to_sort > 0 ? to_sort / (2 * fe) : 0;
+                if (sort_pairs < pairs) pairs = sort_pairs;
+            }
+            if (pairs > 0) {
+                if (!b->gexec || b->graph_key != batch_key(b)) {
+                    if ((s = batch_capture(b)) != HPF_OK) return s;
+                }
+                launch_set_counter(b->d_step, c0->step, b->stream);
+                for (long long q = 0; q < pairs; ++q) {
+                    CUDA_TRY(c0, cudaGraphLaunch(b->gexec, b->stream));
+                    c0->launches[HPF_STAGE_FIELD] += 2;
+                    c0->launches[HPF_STAGE_STEP] += 2;
+                    c0->launches[HPF_STAGE_OTHER] += 2;
+                }
+                for (auto* c : b->rep) {
+                    c->step += 2 * fe * pairs;
+                    c->mesh_step = c->step;
+                    c->next_zero = false;
+                    c->field_valid = true;
+                    c->field_step = c->step - fe;
+                }
+                left -= 2 * fe * pairs;
+                continue;
+            }
+        }
+        if ((s = batch_refresh(b)) != HPF_OK) return s;
+        long long chunk = fe - (c0->step % fe);
+        if (chunk > left) chunk = left;
+        if (chunk > 64) chunk = 64;
+        if (se > 0 && c0->step - c0->last_sort_step >= se)
+            for (auto* c : b->rep)
+                if ((s = sort_beads(c)) != HPF_OK) return s;
+        bool fuse = (c0->step + chunk) % fe == 0;
+        for (auto* c : b->rep) fuse = fuse && c->next_zero && c->dmesh == c0->dmesh;
+        BatchStepParams p;
+        fill_step_params(b, p, (int)chunk, fuse);
+        {
+            StageScope sc(c0, HPF_STAGE_STEP, 1);
+            launch_step_warp_batch(p, batch_max_segments(b), batch_noise(b), b->stream);
+        }
+        LAUNCH_CHECK(c0);
+        batch_advance(b, chunk, fuse);
+        left -= chunk;
+    }
+    return HPF_OK;
+}
+
+}  // extern "C"

@@ -114,6 +114,47 @@ struct SortBufs {
     int* n_seg;         // device scalar: number of segments
 };
 
+// Per-replica records of a batch, passed by value in the kernel parameter
+// block (indexed by a warp-uniform replica id).
+struct BatchStepRep {
+    MeshGeom g;
+    StepConsts c;
+    StateBuf st[2];
+    const uint32_t* meta;
+    const int* seg_start;
+    const int* seg_count;
+    const int* n_seg;
+    const float4* G;
+    unsigned long long* D[2];
+};
+
+struct BatchStepParams {
+    int R;
+    int n_sub;
+    int cur;       // state buffer read this launch (the other is written)
+    int fuse;      // deposit the final positions into D[dnext]
+    int dnext;
+    long long step0;
+    const long long* step_dev;  // if set, the step number is read here (graph replays)
+    int* flag;
+    BatchStepRep rep[HPF_MAX_REPLICAS];
+};
+
+struct BatchFieldRep {
+    MeshGeom g;
+    const long long* D;
+    float4* G;
+    unsigned long long* D_clear;
+    int blk_begin;  // first block of this replica
+};
+
+struct BatchFieldParams {
+    int R;
+    int blocks;
+    const FieldCoef* coef;  // [R] in device memory
+    BatchFieldRep rep[HPF_MAX_REPLICAS];
+};
+
 // ------------------------------------------------------------------ device helpers
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
@@ -312,6 +353,8 @@ void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
                    StepConsts c, long long step, const long long* D, const EnergyConsts& e,
                    double* partials, double* out6, cudaStream_t s);
 void launch_order(const uint32_t* meta, int n, int32_t* order, cudaStream_t s);
+void launch_advance_counter(long long* step, long long by, cudaStream_t s);
+void launch_set_counter(long long* step, long long v, cudaStream_t s);
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,
                       int* flag, cudaStream_t s);
 
@@ -327,6 +370,9 @@ int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* me
                 uint32_t* meta_out, int n, int C, MeshGeom g, cudaStream_t s);
 
 int step_halo_max();
+void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
+                            cudaStream_t s);
+void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
 void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
                       const int* seg_start, const int* seg_count, const int* n_seg, int max_seg,
                       int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,

@@ -33,13 +33,10 @@ void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g, unsign
 // are exact; the potential gradient is their FP32 combination with the
 // coefficients A_KK' c / (2h), A = kT chi + inv_kappa, c = 2^-39 / (rho0 h^3).
 template <int S>
-__global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, MeshGeom g,
-                                               FieldCoef c, float4* __restrict__ G,
-                                               unsigned long long* __restrict__ D_clear) {
-    // one thread per node of the ghosted field array; ghost nodes repeat the
-    // periodic image
-    const int pnode = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pnode >= g.gnodes) return;
+__device__ __forceinline__ void field_node(const long long* __restrict__ D, const MeshGeom& g,
+                                           const FieldCoef& c, float4* __restrict__ G,
+                                           unsigned long long* __restrict__ D_clear, int pnode) {
+    // one node of the ghosted field array; ghost nodes repeat the periodic image
     const int px = pnode % g.gx;
     const int py = (pnode / g.gx) % (g.my + 1);
     const int pz = pnode / g.gxy;
@@ -76,6 +73,44 @@ __global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, 
             v += c.v[k][kp] * dc[kp];
         }
         G[(size_t)k * g.gnodes + pnode] = make_float4(gx, gy, gz, v);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_field(const long long* __restrict__ D, MeshGeom g,
+                                               FieldCoef c, float4* __restrict__ G,
+                                               unsigned long long* __restrict__ D_clear) {
+    const int pnode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pnode >= g.gnodes) return;
+    field_node<S>(D, g, c, G, D_clear, pnode);
+}
+
+// All replicas of a batch: each block belongs to one replica (block-uniform).
+template <int S>
+__global__ void __launch_bounds__(256) k_field_batch(const __grid_constant__ BatchFieldParams p) {
+    int lo = 0, hi = p.R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchFieldRep& r = p.rep[lo];
+    const int pnode = ((int)blockIdx.x - r.blk_begin) * blockDim.x + threadIdx.x;
+    if (pnode >= r.g.gnodes) return;
+    field_node<S>(r.D, r.g, p.coef[lo], r.G, r.D_clear, pnode);
+}
+
+void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s) {
+    if (p.blocks <= 0) return;
+    switch (S) {
+        case 1: k_field_batch<1><<<p.blocks, 256, 0, s>>>(p); break;
+        case 2: k_field_batch<2><<<p.blocks, 256, 0, s>>>(p); break;
+        case 3: k_field_batch<3><<<p.blocks, 256, 0, s>>>(p); break;
+        case 4: k_field_batch<4><<<p.blocks, 256, 0, s>>>(p); break;
+        case 5: k_field_batch<5><<<p.blocks, 256, 0, s>>>(p); break;
+        case 6: k_field_batch<6><<<p.blocks, 256, 0, s>>>(p); break;
+        case 7: k_field_batch<7><<<p.blocks, 256, 0, s>>>(p); break;
+        default: k_field_batch<8><<<p.blocks, 256, 0, s>>>(p); break;
     }
 }
 

@@ -78,6 +78,18 @@ void launch_order(const uint32_t* meta, int n, int32_t* order, cudaStream_t s) {
     k_order<<<(n + 255) / 256, 256, 0, s>>>(meta, n, order);
 }
 
+__global__ void k_advance_counter(long long* step, long long by) { *step += by; }
+
+void launch_advance_counter(long long* step, long long by, cudaStream_t s) {
+    k_advance_counter<<<1, 1, 0, s>>>(step, by);
+}
+
+__global__ void k_set_counter(long long* step, long long v) { *step = v; }
+
+void launch_set_counter(long long* step, long long v, cudaStream_t s) {
+    k_set_counter<<<1, 1, 0, s>>>(step, v);
+}
+
 void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
                         StateBuf st, uint32_t* meta, int* err, cudaStream_t s) {
     if (n <= 0) return;

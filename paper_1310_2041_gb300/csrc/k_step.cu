@@ -332,6 +332,60 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
     }
 }
 
+// One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
+template <bool kNoise>
+__device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
+                                                const uint32_t* __restrict__ meta, int base,
+                                                int cnt, int n_sub, long long step0,
+                                                const MeshGeom& g, const float4* __restrict__ G,
+                                                const StepConsts& c,
+                                                unsigned long long* __restrict__ D_next,
+                                                int* __restrict__ flag, float4* wcache, int tid) {
+    const int lane = tid & 31;
+    const float nan = __int_as_float(0x7fc00000);
+    const int j0 = 2 * lane, j1 = j0 + 1;
+    const bool a0 = j0 < cnt, a1 = j1 < cnt;
+    Bead b0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, nan, nan, nan};
+    Bead b1 = b0;
+    if (a0) {
+        const long long i = (long long)base + j0;
+        b0.x = in.x[i]; b0.y = in.y[i]; b0.z = in.z[i];
+        b0.vx = in.vx[i]; b0.vy = in.vy[i]; b0.vz = in.vz[i];
+        b0.m = meta[i];
+    }
+    if (a1) {
+        const long long i = (long long)base + j1;
+        b1.x = in.x[i]; b1.y = in.y[i]; b1.z = in.z[i];
+        b1.vx = in.vx[i]; b1.vy = in.vy[i]; b1.vz = in.vz[i];
+        b1.m = meta[i];
+    }
+    // whole chains: every flagged neighbour is inside the segment
+    const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
+    const bool p1 = (b1.m & kBondPrev) != 0, n1 = (b1.m & kBondNext) != 0;
+    for (int k = 0; k < n_sub; ++k) {
+        // bead 2l - 1 (previous lane's second bead) and bead 2l + 2 (next lane's first)
+        const float ux = __shfl_up_sync(0xffffffffu, b1.x, 1);
+        const float uy = __shfl_up_sync(0xffffffffu, b1.y, 1);
+        const float uz = __shfl_up_sync(0xffffffffu, b1.z, 1);
+        const float dx = __shfl_down_sync(0xffffffffu, b0.x, 1);
+        const float dy = __shfl_down_sync(0xffffffffu, b0.y, 1);
+        const float dz = __shfl_down_sync(0xffffffffu, b0.z, 1);
+        const float x0 = b0.x, y0 = b0.y, z0 = b0.z;
+        advance_bead<kNoise>(b0, ux, uy, uz, p0, b1.x, b1.y, b1.z, n0, G, g, c, step0 + k, wcache,
+                             tid);
+        advance_bead<kNoise>(b1, x0, y0, z0, p1, dx, dy, dz, n1, G, g, c, step0 + k, wcache,
+                             kWarpBlock + tid);
+        b0.x = fmaf(c.dt, b0.vx, b0.x);
+        b0.y = fmaf(c.dt, b0.vy, b0.y);
+        b0.z = fmaf(c.dt, b0.vz, b0.z);
+        b1.x = fmaf(c.dt, b1.vx, b1.x);
+        b1.y = fmaf(c.dt, b1.vy, b1.y);
+        b1.z = fmaf(c.dt, b1.vz, b1.z);
+    }
+    if (a0) finish_bead(b0, (long long)base + j0, out, g, D_next, flag);
+    if (a1) finish_bead(b1, (long long)base + j1, out, g, D_next, flag);
+}
+
 template <bool kNoise>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp(
     StateBuf in, StateBuf out, const uint32_t* __restrict__ meta, int n,
@@ -340,54 +394,81 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp(
     const float4* __restrict__ G, StepConsts c, unsigned long long* __restrict__ D_next,
     int* __restrict__ flag) {
     extern __shared__ float4 wcache[];  // [kCachePlanes][2 * kWarpBlock]
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int nseg = *n_seg;
     const int warps_total = gridDim.x * (kWarpBlock / 32);
-    const float nan = __int_as_float(0x7fc00000);
-    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < nseg; w += warps_total) {
-        const int base = seg_start[w], cnt = seg_count[w];
-        const int j0 = 2 * lane, j1 = j0 + 1;
-        const bool a0 = j0 < cnt, a1 = j1 < cnt;
-        Bead b0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, nan, nan, nan};
-        Bead b1 = b0;
-        if (a0) {
-            const long long i = (long long)base + j0;
-            b0.x = in.x[i]; b0.y = in.y[i]; b0.z = in.z[i];
-            b0.vx = in.vx[i]; b0.vy = in.vy[i]; b0.vz = in.vz[i];
-            b0.m = meta[i];
+    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < nseg; w += warps_total)
+        advance_segment<kNoise>(in, out, meta, seg_start[w], seg_count[w], n_sub, step0, g, G, c,
+                                D_next, flag, wcache, tid);
+}
+
+// All replicas of a batch in one persistent launch: the warps walk the
+// concatenated segment lists; each segment's replica (warp-uniform) selects
+// its record in the kernel parameter block.
+template <bool kNoise>
+__global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
+    const __grid_constant__ BatchStepParams p) {
+    extern __shared__ float4 wcache[];
+    __shared__ int s_off[HPF_MAX_REPLICAS + 1];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int acc = 0;
+        for (int r = 0; r < p.R; ++r) {
+            s_off[r] = acc;
+            acc += *p.rep[r].n_seg;
         }
-        if (a1) {
-            const long long i = (long long)base + j1;
-            b1.x = in.x[i]; b1.y = in.y[i]; b1.z = in.z[i];
-            b1.vx = in.vx[i]; b1.vy = in.vy[i]; b1.vz = in.vz[i];
-            b1.m = meta[i];
-        }
-        // whole chains: every flagged neighbour is inside the segment
-        const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
-        const bool p1 = (b1.m & kBondPrev) != 0, n1 = (b1.m & kBondNext) != 0;
-        for (int k = 0; k < n_sub; ++k) {
-            // bead 2l - 1 (previous lane's second bead) and bead 2l + 2 (next lane's first)
-            const float ux = __shfl_up_sync(0xffffffffu, b1.x, 1);
-            const float uy = __shfl_up_sync(0xffffffffu, b1.y, 1);
-            const float uz = __shfl_up_sync(0xffffffffu, b1.z, 1);
-            const float dx = __shfl_down_sync(0xffffffffu, b0.x, 1);
-            const float dy = __shfl_down_sync(0xffffffffu, b0.y, 1);
-            const float dz = __shfl_down_sync(0xffffffffu, b0.z, 1);
-            const float x0 = b0.x, y0 = b0.y, z0 = b0.z;
-            advance_bead<kNoise>(b0, ux, uy, uz, p0, b1.x, b1.y, b1.z, n0, G, g, c, step0 + k,
-                                 wcache, tid);
-            advance_bead<kNoise>(b1, x0, y0, z0, p1, dx, dy, dz, n1, G, g, c, step0 + k, wcache,
-                                 kWarpBlock + tid);
-            b0.x = fmaf(c.dt, b0.vx, b0.x);
-            b0.y = fmaf(c.dt, b0.vy, b0.y);
-            b0.z = fmaf(c.dt, b0.vz, b0.z);
-            b1.x = fmaf(c.dt, b1.vx, b1.x);
-            b1.y = fmaf(c.dt, b1.vy, b1.y);
-            b1.z = fmaf(c.dt, b1.vz, b1.z);
-        }
-        if (a0) finish_bead(b0, (long long)base + j0, out, g, D_next, flag);
-        if (a1) finish_bead(b1, (long long)base + j1, out, g, D_next, flag);
+        s_off[p.R] = acc;
     }
+    __syncthreads();
+    const int total = s_off[p.R];
+    const int warps_total = gridDim.x * (kWarpBlock / 32);
+    const long long step0 = p.step_dev ? *p.step_dev : p.step0;
+    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < total; w += warps_total) {
+        int lo = 0, hi = p.R - 1;  // replica r with s_off[r] <= w < s_off[r + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchStepRep& rp = p.rep[lo];
+        const int s = w - s_off[lo];
+        advance_segment<kNoise>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta, rp.seg_start[s],
+                                rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
+                                p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
+    }
+}
+
+static int warp_grid_cap() {
+    static int cap = 0;
+    if (!cap) {
+        cudaFuncSetAttribute(k_step_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_batch<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp<true>, kWarpBlock,
+                                                      kWarpSmem);
+        cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    return cap;
+}
+
+void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
+                            cudaStream_t s) {
+    if (max_seg_total <= 0 || p.n_sub <= 0) return;
+    const int cap = warp_grid_cap();
+    const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+    const int blocks = need < cap ? need : cap;
+    if (noise)
+        k_step_warp_batch<true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else
+        k_step_warp_batch<false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
 void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
@@ -395,19 +476,7 @@ void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
                       int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,
                       unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (n <= 0 || n_sub <= 0 || max_seg <= 0) return;
-    static int grid_cap = 0;
-    if (!grid_cap) {
-        cudaFuncSetAttribute(k_step_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kWarpSmem);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp<true>, kWarpBlock,
-                                                      kWarpSmem);
-        grid_cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
+    const int grid_cap = warp_grid_cap();
     const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < grid_cap ? need : grid_cap;
     if (c.sigma > 0.f)

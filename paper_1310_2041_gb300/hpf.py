@@ -82,6 +82,15 @@ def load():
         L.hpf_forces.argtypes = [vp, vp, i32]
         L.hpf_step.argtypes = [vp, i32]
         L.hpf_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_batch_init.argtypes = [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
+        L.hpf_batch_replica.argtypes = [vp, i32]
+        L.hpf_batch_replica.restype = vp
+        L.hpf_batch_step.argtypes = [vp, i32]
+        L.hpf_batch_use_graphs.argtypes = [vp, i32]
+        L.hpf_batch_destroy.argtypes = [vp]
+        for name in ("hpf_batch_init", "hpf_batch_step", "hpf_batch_use_graphs",
+                     "hpf_batch_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         L.hpf_profile.argtypes = [vp, i32]
         L.hpf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]
@@ -150,7 +159,18 @@ def current_stream_handle():
 class System:
     """One hPF-MD context (hpf_init ... hpf_destroy)."""
 
+    @classmethod
+    def _borrow(cls, lib, handle, params):
+        """A non-owning view of a context that a batch owns."""
+        s = cls.__new__(cls)
+        s.lib, s.p, s.h, s._owned = lib, params, ctypes.c_void_p(handle), False
+        s.stream = 0
+        s.n, s.S = params.n_beads, params.n_species
+        s.mesh_shape = (s.S, params.mesh[2], params.mesh[1], params.mesh[0])
+        return s
+
     def __init__(self, params: Params | dict, stream=None):
+        self._owned = True
         self.lib = load()
         self.p = params if isinstance(params, Params) else make_params(**params)
         if stream is None:
@@ -174,7 +194,8 @@ class System:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.hpf_destroy(self.h)
+            if getattr(self, "_owned", True):
+                self.lib.hpf_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -261,3 +282,55 @@ class System:
         ln = (ctypes.c_int64 * len(STAGES))()
         self._check(self.lib.hpf_profile_read(self.h, ms, ln))
         return {s: (ms[k], ln[k]) for k, s in enumerate(STAGES)}
+
+
+class Batch:
+    """Replicas advanced together (hpf_batch_*); replica(r) gives each one's context."""
+
+    def __init__(self, params_list, stream=None):
+        self.lib = load()
+        self.params = [p if isinstance(p, Params) else make_params(**p) for p in params_list]
+        arr = (Params * len(self.params))(*self.params)
+        if stream is None:
+            stream = current_stream_handle()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = ctypes.c_void_p()
+        st = self.lib.hpf_batch_init(arr, len(self.params), ctypes.c_void_p(int(stream)),
+                                     ctypes.byref(h))
+        if st != 0:
+            raise HPFError(st, self.lib.hpf_status_string(st).decode())
+        self.h = h
+        self.replicas = [System._borrow(self.lib, self.lib.hpf_batch_replica(h, r), p)
+                         for r, p in enumerate(self.params)]
+
+    def replica(self, r):
+        return self.replicas[r]
+
+    def step(self, n_steps=1):
+        st = self.lib.hpf_batch_step(self.h, int(n_steps))
+        if st != 0:
+            msg = self.lib.hpf_last_error(self.replicas[0].h).decode()
+            raise HPFError(st, msg or self.lib.hpf_status_string(st).decode())
+
+    def use_graphs(self, enable=True):
+        self.lib.hpf_batch_use_graphs(self.h, 1 if enable else 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for r in self.replicas:
+                r.h = None
+            self.lib.hpf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
