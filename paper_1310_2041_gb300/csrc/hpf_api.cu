@@ -36,6 +36,7 @@ struct hpf_ctx {
     bool next_zero = false;           // the other mesh is known to be all zero
     float4* G = nullptr;              // field mesh (ghosted)
     float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
+    FieldCoef* d_coef = nullptr;      // the stencil coefficients in device memory
     float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
     void* stage = nullptr;            // set_state input staging
     int* dflag = nullptr;             // [0] kernel flags, [1..4] validation counters
@@ -255,9 +256,20 @@ hpf_status scatter_current(hpf_ctx* c) {
 // target of the next scatter.
 hpf_status run_field(hpf_ctx* c) {
     {
+        // the batched kernel with one replica: a context and a batch member run
+        // the same compiled code, so their results agree bit for bit
         StageScope sc(c, HPF_STAGE_FIELD, 1);
-        launch_field(reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->geom, c->coef,
-                     c->G, mesh_buf(c, c->dmesh ^ 1), c->stream);
+        BatchFieldParams fp;
+        memset(&fp, 0, sizeof fp);
+        fp.R = 1;
+        fp.coef = c->d_coef;
+        fp.rep[0].g = c->geom;
+        fp.rep[0].D = reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh));
+        fp.rep[0].G = c->G;
+        fp.rep[0].D_clear = mesh_buf(c, c->dmesh ^ 1);
+        fp.rep[0].blk_begin = 0;
+        fp.blocks = (c->geom.gnodes + 255) / 256;
+        launch_field_batch(fp, c->S, c->stream);
     }
     LAUNCH_CHECK(c);
     c->next_zero = true;
@@ -362,6 +374,7 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     e = e ? e : cudaMalloc(&c->D, 2 * sizeof(unsigned long long) * nodes * c->S);
     e = e ? e : cudaMalloc(&c->G, sizeof(float4) * (size_t)c->geom.gnodes * c->S);
     e = e ? e : cudaMalloc(&c->field_stage, sizeof(float4) * nodes * c->S);
+    e = e ? e : cudaMalloc(&c->d_coef, sizeof(FieldCoef));
     e = e ? e : cudaMalloc(&c->out_f, sizeof(float) * 6 * n);
     e = e ? e : cudaMalloc(&c->stage, stage_bytes((int)n));
     e = e ? e : cudaMalloc(&c->dflag, sizeof(int) * 8);
@@ -401,7 +414,10 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
         float* base = c->state_mem + (size_t)b * 6 * n;
         c->st[b] = StateBuf{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
     }
-    if (cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(c->d_coef, &c->coef, sizeof(FieldCoef), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->dflag, 0, sizeof(int) * 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->D, 0, 2 * sizeof(unsigned long long) * nodes * c->S, c->stream) !=
             cudaSuccess)
         return cleanup(HPF_ERR_CUDA);
@@ -425,6 +441,7 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->D);
     cudaFree(c->G);
     cudaFree(c->field_stage);
+    cudaFree(c->d_coef);
     cudaFree(c->out_f);
     cudaFree(c->stage);
     cudaFree(c->dflag);
@@ -613,11 +630,32 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         unsigned long long* Dnext = fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
         {
             StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
-            if (c->warp_mode)
-                launch_step_warp(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n,
-                                 c->sb.seg_start, c->sb.seg_count, c->sb.n_seg, c->C, (int)chunk,
-                                 c->step, c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
-            else
+            if (c->warp_mode) {
+                // the batched kernel with one replica (shared with hpf_batch_step)
+                BatchStepParams p;
+                memset(&p, 0, sizeof(BatchStepParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+                p.R = 1;
+                p.n_sub = (int)chunk;
+                p.cur = c->cur;
+                p.fuse = fuse ? 1 : 0;
+                p.dnext = c->dmesh ^ 1;
+                p.step0 = c->step;
+                p.step_dev = nullptr;
+                p.flag = c->dflag;
+                BatchStepRep& q = p.rep[0];
+                q.g = c->geom;
+                q.c = c->sc;
+                q.st[0] = c->st[0];
+                q.st[1] = c->st[1];
+                q.meta = c->meta;
+                q.seg_start = c->sb.seg_start;
+                q.seg_count = c->sb.seg_count;
+                q.n_seg = c->sb.n_seg;
+                q.G = c->G;
+                q.D[0] = mesh_buf(c, 0);
+                q.D[1] = mesh_buf(c, 1);
+                launch_step_warp_batch(p, c->C, c->sc.sigma > 0.f, c->stream);
+            } else
                 launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
                             c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
         }

@@ -373,10 +373,6 @@ int step_halo_max();
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
                             cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
-void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
-                      const int* seg_start, const int* seg_count, const int* n_seg, int max_seg,
-                      int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,
-                      unsigned long long* D_next, int* flag, cudaStream_t s);
 int energy_partials_needed(int n, int nodes);
 
 }  // namespace hpf

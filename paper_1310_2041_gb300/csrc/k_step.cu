@@ -386,25 +386,10 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
     if (a1) finish_bead(b1, (long long)base + j1, out, g, D_next, flag);
 }
 
-template <bool kNoise>
-__global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp(
-    StateBuf in, StateBuf out, const uint32_t* __restrict__ meta, int n,
-    const int* __restrict__ seg_start, const int* __restrict__ seg_count,
-    const int* __restrict__ n_seg, int n_sub, long long step0, MeshGeom g,
-    const float4* __restrict__ G, StepConsts c, unsigned long long* __restrict__ D_next,
-    int* __restrict__ flag) {
-    extern __shared__ float4 wcache[];  // [kCachePlanes][2 * kWarpBlock]
-    const int tid = threadIdx.x;
-    const int nseg = *n_seg;
-    const int warps_total = gridDim.x * (kWarpBlock / 32);
-    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < nseg; w += warps_total)
-        advance_segment<kNoise>(in, out, meta, seg_start[w], seg_count[w], n_sub, step0, g, G, c,
-                                D_next, flag, wcache, tid);
-}
-
-// All replicas of a batch in one persistent launch: the warps walk the
-// concatenated segment lists; each segment's replica (warp-uniform) selects
-// its record in the kernel parameter block.
+// All replicas of a batch in one persistent launch (a single context is a
+// batch of one): the warps walk the concatenated segment lists; each
+// segment's replica (warp-uniform) selects its record in the kernel parameter
+// block.
 template <bool kNoise>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParams p) {
@@ -441,10 +426,6 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
 static int warp_grid_cap() {
     static int cap = 0;
     if (!cap) {
-        cudaFuncSetAttribute(k_step_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kWarpSmem);
         cudaFuncSetAttribute(k_step_warp_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kWarpSmem);
         cudaFuncSetAttribute(k_step_warp_batch<false>,
@@ -452,8 +433,8 @@ static int warp_grid_cap() {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp<true>, kWarpBlock,
-                                                      kWarpSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp_batch<true>,
+                                                      kWarpBlock, kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     return cap;
@@ -471,21 +452,6 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool no
         k_step_warp_batch<false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
-void launch_step_warp(StateBuf in, StateBuf out, const uint32_t* meta, int n,
-                      const int* seg_start, const int* seg_count, const int* n_seg, int max_seg,
-                      int n_sub, long long step0, MeshGeom g, const float4* G, StepConsts c,
-                      unsigned long long* D_next, int* flag, cudaStream_t s) {
-    if (n <= 0 || n_sub <= 0 || max_seg <= 0) return;
-    const int grid_cap = warp_grid_cap();
-    const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
-    const int blocks = need < grid_cap ? need : grid_cap;
-    if (c.sigma > 0.f)
-        k_step_warp<true><<<blocks, kWarpBlock, kWarpSmem, s>>>(
-            in, out, meta, n, seg_start, seg_count, n_seg, n_sub, step0, g, G, c, D_next, flag);
-    else
-        k_step_warp<false><<<blocks, kWarpBlock, kWarpSmem, s>>>(
-            in, out, meta, n, seg_start, seg_count, n_seg, n_sub, step0, g, G, c, D_next, flag);
-}
 
 // ------------------------------------------------------------------ A7 FP64 observables
 
