@@ -631,9 +631,9 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         {
             StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
             if (c->warp_mode) {
-                // the batched kernel with one replica (shared with hpf_batch_step)
-                BatchStepParams p;
-                memset(&p, 0, sizeof(BatchStepParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+                // the batch step kernel instantiated for one replica
+                SingleStepParams p;
+                memset(&p, 0, sizeof p);
                 p.R = 1;
                 p.n_sub = (int)chunk;
                 p.cur = c->cur;
@@ -654,7 +654,7 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
                 q.G = c->G;
                 q.D[0] = mesh_buf(c, 0);
                 q.D[1] = mesh_buf(c, 1);
-                launch_step_warp_batch(p, c->C, c->sc.sigma > 0.f, c->stream);
+                launch_step_warp_single(p, c->C, c->sc.sigma > 0.f, c->stream);
             } else
                 launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
                             c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);

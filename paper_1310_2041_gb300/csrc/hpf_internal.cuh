@@ -128,7 +128,8 @@ struct BatchStepRep {
     unsigned long long* D[2];
 };
 
-struct BatchStepParams {
+template <int kCap>
+struct BatchStepParamsT {
     int R;
     int n_sub;
     int cur;       // state buffer read this launch (the other is written)
@@ -137,8 +138,10 @@ struct BatchStepParams {
     long long step0;
     const long long* step_dev;  // if set, the step number is read here (graph replays)
     int* flag;
-    BatchStepRep rep[HPF_MAX_REPLICAS];
+    BatchStepRep rep[kCap];
 };
+using BatchStepParams = BatchStepParamsT<HPF_MAX_REPLICAS>;
+using SingleStepParams = BatchStepParamsT<1>;
 
 struct BatchFieldRep {
     MeshGeom g;
@@ -372,6 +375,7 @@ int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* me
 int step_halo_max();
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
                             cudaStream_t s);
+void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise, cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
 int energy_partials_needed(int n, int nodes);
 

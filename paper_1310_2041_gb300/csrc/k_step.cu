@@ -390,11 +390,11 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <bool kNoise>
+template <bool kNoise, int kCap>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
-    const __grid_constant__ BatchStepParams p) {
+    const __grid_constant__ BatchStepParamsT<kCap> p) {
     extern __shared__ float4 wcache[];
-    __shared__ int s_off[HPF_MAX_REPLICAS + 1];
+    __shared__ int s_off[kCap + 1];
     const int tid = threadIdx.x;
     if (tid == 0) {
         int acc = 0;
@@ -409,13 +409,16 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const int warps_total = gridDim.x * (kWarpBlock / 32);
     const long long step0 = p.step_dev ? *p.step_dev : p.step0;
     for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < total; w += warps_total) {
-        int lo = 0, hi = p.R - 1;  // replica r with s_off[r] <= w < s_off[r + 1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= w) lo = mid;
-            else hi = mid - 1;
+        int lo = 0;  // replica r with s_off[r] <= w < s_off[r + 1]
+        if (kCap > 1) {
+            int hi = p.R - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
         }
-        const BatchStepRep& rp = p.rep[lo];
+        const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
         advance_segment<kNoise>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta, rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
@@ -426,15 +429,19 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
 static int warp_grid_cap() {
     static int cap = 0;
     if (!cap) {
-        cudaFuncSetAttribute(k_step_warp_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp_batch<false>,
+        cudaFuncSetAttribute(k_step_warp_batch<true, HPF_MAX_REPLICAS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_batch<false, HPF_MAX_REPLICAS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_batch<true, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_batch<false, 1>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_warp_batch<true>,
-                                                      kWarpBlock, kWarpSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS>, kWarpBlock, kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     return cap;
@@ -447,9 +454,21 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool no
     const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
     if (noise)
-        k_step_warp_batch<true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<true, HPF_MAX_REPLICAS><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
     else
-        k_step_warp_batch<false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<false, HPF_MAX_REPLICAS><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+}
+
+void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise,
+                             cudaStream_t s) {
+    if (max_seg <= 0 || p.n_sub <= 0) return;
+    const int cap = warp_grid_cap();
+    const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+    const int blocks = need < cap ? need : cap;
+    if (noise)
+        k_step_warp_batch<true, 1><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else
+        k_step_warp_batch<false, 1><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
 
