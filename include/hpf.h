@@ -142,6 +142,15 @@ hpf_status hpf_scatter_density(hpf_ctx* ctx, int64_t* D_out);
  * Errors: HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_field(hpf_ctx* ctx, const int64_t* D_in, float* field_out);
 
+/* The field stencil runs on shared-memory tiles of the mesh, staged by TMA
+ * tensor copies when the mesh allows it (Mx even, n_species <= 4).  The tile
+ * shape is chosen the first time the field is computed, by timing six
+ * candidate shapes on this mesh (that first refresh synchronises once).
+ * shape[0..2] = tile (x, y, z) or zeros before the first refresh; *uses_tma =
+ * 1 if the tiles are staged by TMA, 0 if by plain loads.  Either pointer may
+ * be NULL.  Errors: HPF_ERR_INVALID. */
+hpf_status hpf_field_tile(const hpf_ctx* ctx, int32_t shape[3], int32_t* uses_tma);
+
 #define HPF_FORCE_FIELD 1
 #define HPF_FORCE_BOND 2
 

@@ -37,6 +37,10 @@ struct hpf_ctx {
     float4* G = nullptr;              // field mesh (ghosted)
     float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
     FieldCoef* d_coef = nullptr;      // the stencil coefficients in device memory
+    int field_tile = -1;              // tiled stencil shape chosen by the autotuner (-1: not yet)
+    int tmap_tile = -1;               // tile the tensor maps below were encoded for
+    bool tmap_ok = false;             // TMA usable for this mesh
+    CUtensorMap tmap[2];              // over mesh buffers 0 and 1
     float* out_f = nullptr;           // 2 x 3n floats of tag-order output staging
     void* stage = nullptr;            // set_state input staging
     int* dflag = nullptr;             // [0] kernel flags, [1..4] validation counters
@@ -233,6 +237,63 @@ StateBuf& cur_state(hpf_ctx* c) { return c->st[c->cur]; }
 size_t mesh_words(const hpf_ctx* c) { return (size_t)c->geom.nodes * c->S; }
 unsigned long long* mesh_buf(hpf_ctx* c, int k) { return c->D + (size_t)k * mesh_words(c); }
 
+// Tensor maps of both mesh buffers for a tile shape (TMA box = tile + halo).
+void ensure_tmaps(hpf_ctx* c, int tile) {
+    if (c->tmap_tile == tile) return;
+    c->tmap_ok = c->S <= 4;
+    for (int k = 0; k < 2 && c->tmap_ok; ++k)
+        c->tmap_ok = make_mesh_tensor_map(&c->tmap[k], reinterpret_cast<const long long*>(mesh_buf(c, k)),
+                                          c->geom, c->S, tile);
+    c->tmap_tile = tile;
+}
+
+// One replica's record of the tiled stencil reading mesh buffer `dm`.
+void fill_field_rep(hpf_ctx* c, int tile, int dm, TiledFieldRep& fr, int& blocks) {
+    ensure_tmaps(c, tile);
+    fr.tmap = c->tmap[dm];
+    fr.g = c->geom;
+    fr.D = reinterpret_cast<const long long*>(mesh_buf(c, dm));
+    fr.G = c->G;
+    fr.D_clear = mesh_buf(c, dm ^ 1);
+    fr.use_tma = c->tmap_ok ? 1 : 0;
+    int nb = 0;
+    tile_grid(c->geom, tile, &fr.tiles_x, &fr.tiles_y, &nb);
+    fr.blk_begin = blocks;
+    blocks += nb;
+}
+
+// Time every candidate tile on this launch shape and keep the fastest.  The
+// candidates compute the same field (the last launch leaves it in place).
+template <class Fill>
+int autotune_tile(cudaStream_t s, int S, Fill fill) {
+    if (S > 4) return -1;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int t = 0; t < field_tile_candidates(); ++t) {
+        TiledFieldParams p;
+        fill(t, p);
+        launch_field_tiled(p, S, t, s);  // warm
+        cudaEventRecord(a, s);
+        for (int rep = 0; rep < 3; ++rep) launch_field_tiled(p, S, t, s);
+        cudaEventRecord(b, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
 // The context's mesh holds the density of the current positions afterwards:
 // scatter into the other buffer (cleared first unless known zero) and flip.
 hpf_status scatter_current(hpf_ctx* c) {
@@ -255,9 +316,26 @@ hpf_status scatter_current(hpf_ctx* c) {
 // Field of the context's mesh; the kernel also clears the other mesh, the
 // target of the next scatter.
 hpf_status run_field(hpf_ctx* c) {
-    {
-        // the batched kernel with one replica: a context and a batch member run
-        // the same compiled code, so their results agree bit for bit
+    if (c->S <= 4) {
+        // the tiled (TMA-staged) stencil with one replica; a batch runs the same
+        // kernel, so contexts and batch members agree bit for bit
+        if (c->field_tile < 0)
+            c->field_tile = autotune_tile(c->stream, c->S, [&](int t, TiledFieldParams& p) {
+                memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+                p.R = 1;
+                p.coef = c->d_coef;
+                p.flag = c->dflag;
+                fill_field_rep(c, t, c->dmesh, p.rep[0], p.blocks);
+            });
+        StageScope sc(c, HPF_STAGE_FIELD, 1);
+        TiledFieldParams p;
+        memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+        p.R = 1;
+        p.coef = c->d_coef;
+        p.flag = c->dflag;
+        fill_field_rep(c, c->field_tile, c->dmesh, p.rep[0], p.blocks);
+        launch_field_tiled(p, c->S, c->field_tile, c->stream);
+    } else {
         StageScope sc(c, HPF_STAGE_FIELD, 1);
         BatchFieldParams fp;
         memset(&fp, 0, sizeof fp);
@@ -693,6 +771,16 @@ hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     return HPF_OK;
 }
 
+hpf_status hpf_field_tile(const hpf_ctx* c, int32_t shape[3], int32_t* uses_tma) {
+    if (!c) return HPF_ERR_INVALID;
+    int t[3] = {0, 0, 0};
+    if (c->field_tile >= 0) field_tile_shape(c->field_tile, t);
+    if (shape)
+        for (int a = 0; a < 3; ++a) shape[a] = t[a];
+    if (uses_tma) *uses_tma = (c->field_tile >= 0 && c->tmap_ok) ? 1 : 0;
+    return HPF_OK;
+}
+
 hpf_status hpf_profile(hpf_ctx* c, int32_t enable) {
     if (!c) return HPF_ERR_INVALID;
     c->profiling = enable != 0;
@@ -733,6 +821,7 @@ struct hpf_batch {
     long long* d_step = nullptr;  // step counter read by graph replays
     cudaGraphExec_t gexec = nullptr;
     std::vector<const void*> graph_key;  // buffers the captured graph refers to
+    int field_tile = -1;                 // stencil tile shape chosen for the whole batch
     std::string err;
 };
 
@@ -743,31 +832,33 @@ hpf_status bfail(hpf_batch* b, hpf_status s, const char* msg) {
     return s;
 }
 
+// The batched stencil over all replicas, each reading its mesh buffer dm_r.
+void fill_batch_field(hpf_batch* b, int tile, int flip, TiledFieldParams& p) {
+    memset(&p, 0, sizeof p);
+    p.R = b->R;
+    p.coef = b->d_coef;
+    p.flag = b->rep[0]->dflag;
+    for (int r = 0; r < b->R; ++r) {
+        hpf_ctx* c = b->rep[r];
+        fill_field_rep(c, tile, c->dmesh ^ flip, p.rep[r], p.blocks);
+    }
+}
+
 // Batched refresh of the replicas whose field is due (all of them in steady state).
 hpf_status batch_refresh(hpf_batch* b) {
-    BatchFieldParams fp;
-    memset(&fp, 0, sizeof fp);
-    fp.coef = b->d_coef;
     hpf_ctx* c0 = b->rep[0];
+    int due_n = 0;
     for (int r = 0; r < b->R; ++r) {
         hpf_ctx* c = b->rep[r];
         const bool due = !c->field_valid || (c->step % c->p.field_every == 0 && c->field_step != c->step);
         if (!due) continue;
         hpf_status s = scatter_current(c);
         if (s != HPF_OK) return s;
-        BatchFieldRep& fr = fp.rep[fp.R];
-        fr.g = c->geom;
-        fr.D = reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh));
-        fr.G = c->G;
-        fr.D_clear = mesh_buf(c, c->dmesh ^ 1);
-        fr.blk_begin = fp.blocks;
-        fp.blocks += (c->geom.gnodes + 255) / 256;
-        // the coefficient record of replica r sits at d_coef[r]; re-index for this launch
-        fp.R++;
+        ++due_n;
     }
-    if (fp.R == 0) return HPF_OK;
-    if (fp.R != b->R) {
-        // only some replicas are due: run them one by one
+    if (due_n == 0) return HPF_OK;
+    if (due_n != b->R || c0->S > 4) {
+        // only some replicas are due (or no tiled stencil): refresh them one by one
         for (int r = 0; r < b->R; ++r) {
             hpf_ctx* c = b->rep[r];
             const bool due = !c->field_valid || (c->step % c->p.field_every == 0 && c->field_step != c->step);
@@ -778,9 +869,15 @@ hpf_status batch_refresh(hpf_batch* b) {
         }
         return HPF_OK;
     }
+    if (b->field_tile < 0)
+        b->field_tile = autotune_tile(b->stream, c0->S, [&](int t, TiledFieldParams& p) {
+            fill_batch_field(b, t, 0, p);
+        });
     {
         StageScope sc(c0, HPF_STAGE_FIELD, 1);
-        launch_field_batch(fp, c0->S, b->stream);
+        TiledFieldParams p;
+        fill_batch_field(b, b->field_tile, 0, p);
+        launch_field_tiled(p, c0->S, b->field_tile, b->stream);
     }
     LAUNCH_CHECK(c0);
     for (auto* c : b->rep) {
@@ -865,22 +962,9 @@ hpf_status batch_capture(hpf_batch* b) {
     cudaGraph_t graph = nullptr;
     CUDA_TRY(c0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     for (int half = 0; half < 2; ++half) {
-        BatchFieldParams fp;
-        memset(&fp, 0, sizeof fp);
-        fp.coef = b->d_coef;
-        for (int r = 0; r < b->R; ++r) {
-            hpf_ctx* c = b->rep[r];
-            const int dm = c->dmesh ^ half;
-            BatchFieldRep& fr = fp.rep[r];
-            fr.g = c->geom;
-            fr.D = reinterpret_cast<const long long*>(mesh_buf(c, dm));
-            fr.G = c->G;
-            fr.D_clear = mesh_buf(c, dm ^ 1);
-            fr.blk_begin = fp.blocks;
-            fp.blocks += (c->geom.gnodes + 255) / 256;
-        }
-        fp.R = b->R;
-        launch_field_batch(fp, c0->S, b->stream);
+        TiledFieldParams fp;
+        fill_batch_field(b, b->field_tile, half, fp);
+        launch_field_tiled(fp, c0->S, b->field_tile, b->stream);
         BatchStepParams sp;
         fill_step_params(b, sp, fe, true);
         sp.cur = c0->cur ^ half;
@@ -997,7 +1081,7 @@ hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
     while (left > 0) {
         // steady state: replay two captured periods at a time
         const bool aligned = c0->step % fe == 0 && fe <= 64;
-        bool steady = aligned && b->use_graphs && left >= 2 * fe;
+        bool steady = aligned && b->use_graphs && left >= 2 * fe && b->field_tile >= 0;
         for (auto* c : b->rep)
             steady = steady && c->mesh_step == c->step && c->field_step != c->step &&
                      c->cur == c0->cur && c->dmesh == c0->dmesh;

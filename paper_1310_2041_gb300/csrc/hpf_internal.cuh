@@ -12,6 +12,7 @@
 // neighbours); the sort permutes whole chains for locality.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -156,6 +157,26 @@ struct BatchFieldParams {
     int blocks;
     const FieldCoef* coef;  // [R] in device memory
     BatchFieldRep rep[HPF_MAX_REPLICAS];
+};
+
+// Tiled field stencil: one record per replica (a context is a batch of one).
+struct TiledFieldRep {
+    CUtensorMap tmap;  // over D (valid when use_tma)
+    MeshGeom g;
+    const long long* D;
+    float4* G;
+    unsigned long long* D_clear;
+    int use_tma;
+    int tiles_x, tiles_y;
+    int blk_begin;
+};
+
+struct TiledFieldParams {
+    int R;
+    int blocks;
+    const FieldCoef* coef;  // [R] in device memory
+    int* flag;
+    TiledFieldRep rep[HPF_MAX_REPLICAS];
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -377,6 +398,12 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool no
                             cudaStream_t s);
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise, cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
+int field_tile_candidates();
+void field_tile_shape(int id, int out[3]);
+void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s);
+bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
+                          int tile);
+void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);
 int energy_partials_needed(int n, int nodes);
 
 }  // namespace hpf

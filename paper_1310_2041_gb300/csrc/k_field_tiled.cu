@@ -1,0 +1,244 @@
+// k_field_tiled.cu -- the field stencil (V_K and periodic central-difference
+// grad V_K, MD-SCF section; Algorithm 1, kernel 3) on shared-memory tiles.
+//
+// A CTA computes a TX x TY x TZ tile of the ghosted field array.  It needs the
+// density of the tile plus one node on every side (x: two, so the copy starts
+// on a 16-byte boundary): a (TX+4) x (TY+2) x (TZ+2) box per species, staged
+// in shared memory by one TMA tensor copy (cp.async.bulk.tensor, completion on
+// an mbarrier) when the mesh allows it (x extent even: rows are multiples of
+// 16 bytes), else by plain loads.  TMA has no periodic mode: box elements
+// outside the mesh arrive as zeros and are then replaced by their periodic
+// images with plain loads (only tiles on the mesh boundary have any).  The
+// tile shape is chosen per mesh by timing the candidates (hpf_api.cu).
+#include <cuda.h>
+
+#include "hpf_internal.cuh"
+
+namespace hpf {
+
+constexpr int kTileCandidates = 6;
+constexpr int kTileShapes[kTileCandidates][3] = {
+    {32, 4, 2}, {16, 8, 2}, {16, 4, 4}, {8, 8, 4}, {64, 4, 1}, {32, 8, 1}};
+constexpr unsigned kWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
+
+int field_tile_candidates() { return kTileCandidates; }
+
+void field_tile_shape(int id, int out[3]) {
+    for (int a = 0; a < 3; ++a) out[a] = kTileShapes[id][a];
+}
+
+size_t field_tile_smem(int id, int S) {
+    const int* t = kTileShapes[id];
+    return sizeof(long long) * (size_t)(t[0] + 4) * (t[1] + 2) * (t[2] + 2) * S;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Returns false if the barrier did not complete within kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int S, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) k_field_tiled(const __grid_constant__ TiledFieldParams p) {
+    constexpr int BX = TX + 4, BY = TY + 2, BZ = TZ + 2;
+    constexpr int BOX = BX * BY * BZ;
+    constexpr int NT = TX * TY * TZ;
+    extern __shared__ __align__(128) long long box[];  // [S][BZ][BY][BX]
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_ok;
+
+    int lo = 0, hi = p.R - 1;  // replica of this block
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const TiledFieldRep& r = p.rep[lo];
+    const MeshGeom& g = r.g;
+    const int t = (int)blockIdx.x - r.blk_begin;
+    const int x0 = (t % r.tiles_x) * TX;
+    const int y0 = ((t / r.tiles_x) % r.tiles_y) * TY;
+    const int z0 = (t / (r.tiles_x * r.tiles_y)) * TZ;
+    const int ux = x0 - 2, vy = y0 - 1, wz = z0 - 1;  // box origin (unwrapped node indices)
+    const bool interior = ux >= 0 && ux + BX <= g.mx && vy >= 0 && vy + BY <= g.my && wz >= 0 &&
+                          wz + BZ <= g.mz;
+    const int tid = threadIdx.x;
+
+    if (r.use_tma) {
+        const uint32_t b = smem_u32(&bar);
+        if (tid == 0) {
+            s_ok = 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(sizeof(long long) * BOX * S);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                         "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(box)),
+                "l"(reinterpret_cast<uint64_t>(&r.tmap)), "r"(ux), "r"(vy), "r"(wz), "r"(0),
+                "r"(b)
+                : "memory");
+        }
+        if (!mbar_wait(b, 0)) {
+            // give up on this tile: report, then wait (bounded) for the copy in flight
+            atomicOr(p.flag, kFlagTimeout);
+            s_ok = 0;
+            mbar_wait(b, 0);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+    }
+    if (!r.use_tma || !interior) {
+        // plain loads: every element, or only those the copy filled with zeros
+        for (int e = tid; e < S * BOX; e += NT) {
+            const int u = e % BX, v = (e / BX) % BY, w = (e / (BX * BY)) % BZ, k = e / BOX;
+            const int gx = ux + u, gy = vy + v, gz = wz + w;
+            const bool inside = gx >= 0 && gx < g.mx && gy >= 0 && gy < g.my && gz >= 0 &&
+                                gz < g.mz;
+            if (r.use_tma && inside) continue;
+            const int xx = (gx % g.mx + g.mx) % g.mx, yy = (gy % g.my + g.my) % g.my,
+                      zz = (gz % g.mz + g.mz) % g.mz;
+            box[e] = __ldg(r.D + (size_t)k * g.nodes + ((size_t)zz * g.my + yy) * g.mx + xx);
+        }
+    }
+    __syncthreads();
+
+    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
+    const int px = x0 + tx, py = y0 + ty, pz = z0 + tz;
+    if (px > g.mx || py > g.my || pz > g.mz) return;
+    if (px < g.mx && py < g.my && pz < g.mz) {
+        const size_t node = ((size_t)pz * g.my + py) * g.mx + px;
+#pragma unroll
+        for (int k = 0; k < S; ++k) r.D_clear[(size_t)k * g.nodes + node] = 0ull;
+    }
+    const int u = tx + 2, v = ty + 1, w = tz + 1;
+    const FieldCoef& c = p.coef[lo];
+    float ddx[S], ddy[S], ddz[S], dc[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const long long* bk = box + k * BOX;
+        const int o = (w * BY + v) * BX + u;
+        ddx[k] = (float)(bk[o + 1] - bk[o - 1]);
+        ddy[k] = (float)(bk[o + BX] - bk[o - BX]);
+        ddz[k] = (float)(bk[o + BX * BY] - bk[o - BX * BY]);
+        dc[k] = (float)bk[o];
+    }
+    const size_t pnode = (size_t)pz * g.gxy + (size_t)py * g.gx + px;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        float gx = 0.f, gy = 0.f, gz = 0.f, vv = c.v0;
+#pragma unroll
+        for (int kp = 0; kp < S; ++kp) {
+            gx = fmaf(c.gx[k][kp], ddx[kp], gx);
+            gy = fmaf(c.gy[k][kp], ddy[kp], gy);
+            gz = fmaf(c.gz[k][kp], ddz[kp], gz);
+            vv = fmaf(c.v[k][kp], dc[kp], vv);
+        }
+        r.G[(size_t)k * g.gnodes + pnode] = make_float4(gx, gy, gz, vv);
+    }
+}
+
+template <int S, int TX, int TY, int TZ>
+static void launch_tile(const TiledFieldParams& p, cudaStream_t s) {
+    const size_t smem = sizeof(long long) * (size_t)(TX + 4) * (TY + 2) * (TZ + 2) * S;
+    k_field_tiled<S, TX, TY, TZ><<<p.blocks, TX * TY * TZ, smem, s>>>(p);
+}
+
+template <int S>
+static void launch_for_species(const TiledFieldParams& p, int tile, cudaStream_t s) {
+    switch (tile) {
+        case 0: launch_tile<S, 32, 4, 2>(p, s); break;
+        case 1: launch_tile<S, 16, 8, 2>(p, s); break;
+        case 2: launch_tile<S, 16, 4, 4>(p, s); break;
+        case 3: launch_tile<S, 8, 8, 4>(p, s); break;
+        case 4: launch_tile<S, 64, 4, 1>(p, s); break;
+        default: launch_tile<S, 32, 8, 1>(p, s); break;
+    }
+}
+
+void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s) {
+    if (p.blocks <= 0) return;
+    switch (S) {
+        case 1: launch_for_species<1>(p, tile, s); break;
+        case 2: launch_for_species<2>(p, tile, s); break;
+        case 3: launch_for_species<3>(p, tile, s); break;
+        default: launch_for_species<4>(p, tile, s); break;
+    }
+}
+
+// ------------------------------------------------------------------ tensor maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// A tensor map over the int64 mesh D [S][Mz][My][Mx] with the box of `tile`.
+// False when TMA cannot be used (odd Mx, unaligned base, no driver entry point).
+bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
+                          int tile) {
+    if (g.mx % 2 != 0 || (reinterpret_cast<uintptr_t>(D) & 15u) != 0 || S > 4) return false;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const int* t = kTileShapes[tile];
+    const cuuint64_t dims[4] = {(cuuint64_t)g.mx, (cuuint64_t)g.my, (cuuint64_t)g.mz,
+                                (cuuint64_t)S};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.mx * 8, (cuuint64_t)g.mx * g.my * 8,
+                                   (cuuint64_t)g.mx * g.my * g.mz * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)(t[0] + 4), (cuuint32_t)(t[1] + 2),
+                               (cuuint32_t)(t[2] + 2), (cuuint32_t)S};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<long long*>(D), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks) {
+    const int* t = kTileShapes[tile];
+    const int nx = (g.mx + 1 + t[0] - 1) / t[0];
+    const int ny = (g.my + 1 + t[1] - 1) / t[1];
+    const int nz = (g.mz + 1 + t[2] - 1) / t[2];
+    *tiles_x = nx;
+    *tiles_y = ny;
+    *blocks = nx * ny * nz;
+}
+
+}  // namespace hpf

@@ -77,6 +77,7 @@ def load():
         L.hpf_set_state.argtypes = [vp, vp, vp, vp, vp, i64, i64]
         L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
         L.hpf_get_order.argtypes = [vp, vp]
+        L.hpf_field_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hpf_scatter_density.argtypes = [vp, vp]
         L.hpf_field.argtypes = [vp, vp, vp]
         L.hpf_forces.argtypes = [vp, vp, i32]
@@ -96,7 +97,7 @@ def load():
                                        ctypes.POINTER(ctypes.c_int64)]
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
-                     "hpf_profile", "hpf_profile_read", "hpf_get_order"):
+                     "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib
@@ -240,6 +241,13 @@ class System:
         op, _a = _ptr(out, np.int32, (self.n,), "order")
         self._check(self.lib.hpf_get_order(self.h, op))
         return out
+
+    def field_tile(self):
+        """(tile shape (x, y, z), staged by TMA) chosen for this mesh; zeros before the first field."""
+        shape = (ctypes.c_int32 * 3)()
+        tma = ctypes.c_int32()
+        self._check(self.lib.hpf_field_tile(self.h, shape, ctypes.byref(tma)))
+        return tuple(shape), bool(tma.value)
 
     # ---- the path
     def scatter_density(self, out=None):

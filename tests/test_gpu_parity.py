@@ -92,6 +92,24 @@ def test_field_matches_oracle(hpf_gpu, orc, w):
     np.testing.assert_allclose(Fm[..., 3], Vo, rtol=1e-5, atol=1e-6 * (np.max(np.abs(Vo)) + 1))
 
 
+@pytest.mark.parametrize("mesh,tma", [(8, True), (7, False), (70, True)])
+def test_field_tiles_autotuned_and_staged(hpf_gpu, orc, mesh, tma):
+    """The stencil's tile shape comes from the autotuner; even-x meshes are
+    staged by TMA (zero-filled halo faces patched with periodic images)."""
+    w = W.diblock(60, 5, 5, float(mesh) * 0.97, mesh, 1.0)
+    s, d, pp = make(hpf_gpu, w)
+    assert s.field_tile() == ((0, 0, 0), False)
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    Vo, Go = orc.field(op, Do)
+    Fm = s.field(D_in=Do)
+    shape, staged = s.field_tile()
+    assert shape in [(32, 4, 2), (16, 8, 2), (16, 4, 4), (8, 8, 4), (64, 4, 1), (32, 8, 1)]
+    assert staged == tma
+    scale = np.max(np.abs(Go)) + 1e-30
+    np.testing.assert_allclose(Fm[..., :3], Go, rtol=1e-5, atol=1e-6 * scale)
+
+
 @pytest.mark.parametrize("w", SMALL + [W.a5b5_10k()], ids=lambda w: w.name)
 @pytest.mark.parametrize("which", [1, 2, 3])
 def test_forces_match_oracle(hpf_gpu, orc, w, which):
