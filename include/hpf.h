@@ -151,6 +151,11 @@ hpf_status hpf_field(hpf_ctx* ctx, const int64_t* D_in, float* field_out);
  * be NULL.  Errors: HPF_ERR_INVALID. */
 hpf_status hpf_field_tile(const hpf_ctx* ctx, int32_t shape[3], int32_t* uses_tma);
 
+/* Pin the stencil to candidate `tile` (0 .. 6: (32,8,4), (32,8,8), (16,16,4),
+ * (64,4,4), (16,16,8), (32,4,8), untiled) instead of autotuning; -1 autotunes
+ * again at the next field.  Errors: HPF_ERR_INVALID. */
+hpf_status hpf_set_field_tile(hpf_ctx* ctx, int32_t tile);
+
 #define HPF_FORCE_FIELD 1
 #define HPF_FORCE_BOND 2
 

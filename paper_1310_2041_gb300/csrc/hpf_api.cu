@@ -781,6 +781,12 @@ hpf_status hpf_field_tile(const hpf_ctx* c, int32_t shape[3], int32_t* uses_tma)
     return HPF_OK;
 }
 
+hpf_status hpf_set_field_tile(hpf_ctx* c, int32_t tile) {
+    if (!c || tile < -1 || tile >= field_tile_candidates()) return HPF_ERR_INVALID;
+    c->field_tile = tile;
+    return HPF_OK;
+}
+
 hpf_status hpf_profile(hpf_ctx* c, int32_t enable) {
     if (!c) return HPF_ERR_INVALID;
     c->profiling = enable != 0;

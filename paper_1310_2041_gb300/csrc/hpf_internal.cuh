@@ -399,6 +399,7 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool no
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise, cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
 int field_tile_candidates();
+bool field_tile_is_plain(int id);
 void field_tile_shape(int id, int out[3]);
 void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s);
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,

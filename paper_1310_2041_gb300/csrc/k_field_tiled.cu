@@ -16,9 +16,12 @@
 
 namespace hpf {
 
-constexpr int kTileCandidates = 6;
+// Candidate tiles (x, y, z): a CTA has x * y threads, each computing z nodes
+// along a z column.  Shape {0, 0, 0} is the untiled one-node-per-thread stencil
+// with direct L1/L2 loads, so the autotuner can never pick a slower kernel.
+constexpr int kTileCandidates = 7;
 constexpr int kTileShapes[kTileCandidates][3] = {
-    {32, 4, 2}, {16, 8, 2}, {16, 4, 4}, {8, 8, 4}, {64, 4, 1}, {32, 8, 1}};
+    {32, 8, 4}, {32, 8, 8}, {16, 16, 4}, {64, 4, 4}, {16, 16, 8}, {32, 4, 8}, {0, 0, 0}};
 constexpr unsigned kWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
 
 int field_tile_candidates() { return kTileCandidates; }
@@ -29,8 +32,11 @@ void field_tile_shape(int id, int out[3]) {
 
 size_t field_tile_smem(int id, int S) {
     const int* t = kTileShapes[id];
+    if (t[0] == 0) return 0;
     return sizeof(long long) * (size_t)(t[0] + 4) * (t[1] + 2) * (t[2] + 2) * S;
 }
+
+bool field_tile_is_plain(int id) { return kTileShapes[id][0] == 0; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -52,11 +58,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+// Periodic image of an index that is at most one period outside [0, m) (the
+// general remainder only for meshes smaller than a box).
+__device__ __forceinline__ int wrap_near(int i, int m) {
+    if (i < 0) i += m;
+    else if (i >= m) i -= m;
+    if (i < 0 || i >= m) i = ((i % m) + m) % m;
+    return i;
+}
+
 template <int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ) k_field_tiled(const __grid_constant__ TiledFieldParams p) {
+__global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__ TiledFieldParams p) {
     constexpr int BX = TX + 4, BY = TY + 2, BZ = TZ + 2;
     constexpr int BOX = BX * BY * BZ;
-    constexpr int NT = TX * TY * TZ;
+    constexpr int NT = TX * TY;
     extern __shared__ __align__(128) long long box[];  // [S][BZ][BY][BX]
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int s_ok;
@@ -112,38 +127,97 @@ __global__ void __launch_bounds__(TX * TY * TZ) k_field_tiled(const __grid_const
         // plain loads: every element, or only those the copy filled with zeros
         for (int e = tid; e < S * BOX; e += NT) {
             const int u = e % BX, v = (e / BX) % BY, w = (e / (BX * BY)) % BZ, k = e / BOX;
-            const int gx = ux + u, gy = vy + v, gz = wz + w;
+            int gx = ux + u, gy = vy + v, gz = wz + w;
             const bool inside = gx >= 0 && gx < g.mx && gy >= 0 && gy < g.my && gz >= 0 &&
                                 gz < g.mz;
             if (r.use_tma && inside) continue;
-            const int xx = (gx % g.mx + g.mx) % g.mx, yy = (gy % g.my + g.my) % g.my,
-                      zz = (gz % g.mz + g.mz) % g.mz;
-            box[e] = __ldg(r.D + (size_t)k * g.nodes + ((size_t)zz * g.my + yy) * g.mx + xx);
+            gx = wrap_near(gx, g.mx);
+            gy = wrap_near(gy, g.my);
+            gz = wrap_near(gz, g.mz);
+            box[e] = __ldg(r.D + (size_t)k * g.nodes + ((size_t)gz * g.my + gy) * g.mx + gx);
         }
     }
     __syncthreads();
 
-    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
-    const int px = x0 + tx, py = y0 + ty, pz = z0 + tz;
-    if (px > g.mx || py > g.my || pz > g.mz) return;
+    const int tx = tid % TX, ty = tid / TX;
+    const int px = x0 + tx, py = y0 + ty;
+    if (px > g.mx || py > g.my) return;
+    const FieldCoef& c = p.coef[lo];
+    const int u = tx + 2, v = ty + 1;
+#pragma unroll 1
+    for (int tz = 0; tz < TZ; ++tz) {
+        const int pz = z0 + tz;
+        if (pz > g.mz) break;
+        if (px < g.mx && py < g.my && pz < g.mz) {
+            const size_t node = ((size_t)pz * g.my + py) * g.mx + px;
+#pragma unroll
+            for (int k = 0; k < S; ++k) r.D_clear[(size_t)k * g.nodes + node] = 0ull;
+        }
+        const int w = tz + 1;
+        float ddx[S], ddy[S], ddz[S], dc[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const long long* bk = box + k * BOX;
+            const int o = (w * BY + v) * BX + u;
+            ddx[k] = (float)(bk[o + 1] - bk[o - 1]);
+            ddy[k] = (float)(bk[o + BX] - bk[o - BX]);
+            ddz[k] = (float)(bk[o + BX * BY] - bk[o - BX * BY]);
+            dc[k] = (float)bk[o];
+        }
+        const size_t pnode = (size_t)pz * g.gxy + (size_t)py * g.gx + px;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            float gx = 0.f, gy = 0.f, gz = 0.f, vv = c.v0;
+#pragma unroll
+            for (int kp = 0; kp < S; ++kp) {
+                gx = fmaf(c.gx[k][kp], ddx[kp], gx);
+                gy = fmaf(c.gy[k][kp], ddy[kp], gy);
+                gz = fmaf(c.gz[k][kp], ddz[kp], gz);
+                vv = fmaf(c.v[k][kp], dc[kp], vv);
+            }
+            r.G[(size_t)k * g.gnodes + pnode] = make_float4(gx, gy, gz, vv);
+        }
+    }
+}
+
+// The untiled candidate: one thread per node of the ghosted array, neighbours
+// loaded directly (through L1/L2), same arithmetic as the tiled kernel.
+template <int S>
+__global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ TiledFieldParams p) {
+    int lo = 0, hi = p.R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const TiledFieldRep& r = p.rep[lo];
+    const MeshGeom& g = r.g;
+    const int pnode = ((int)blockIdx.x - r.blk_begin) * 256 + threadIdx.x;
+    if (pnode >= g.gnodes) return;
+    const int px = pnode % g.gx, py = (pnode / g.gx) % (g.my + 1), pz = pnode / g.gxy;
+    const int x = px == g.mx ? 0 : px, y = py == g.my ? 0 : py, z = pz == g.mz ? 0 : pz;
+    const int node = (z * g.my + y) * g.mx + x;
     if (px < g.mx && py < g.my && pz < g.mz) {
-        const size_t node = ((size_t)pz * g.my + py) * g.mx + px;
 #pragma unroll
         for (int k = 0; k < S; ++k) r.D_clear[(size_t)k * g.nodes + node] = 0ull;
     }
-    const int u = tx + 2, v = ty + 1, w = tz + 1;
+    const int xp = node + ((x + 1 == g.mx) ? 1 - g.mx : 1);
+    const int xm = node + ((x == 0) ? g.mx - 1 : -1);
+    const int sy = g.mx, sz = g.mx * g.my;
+    const int yp = node + ((y + 1 == g.my) ? (1 - g.my) * sy : sy);
+    const int ym = node + ((y == 0) ? (g.my - 1) * sy : -sy);
+    const int zp = node + ((z + 1 == g.mz) ? (1 - g.mz) * sz : sz);
+    const int zm = node + ((z == 0) ? (g.mz - 1) * sz : -sz);
     const FieldCoef& c = p.coef[lo];
     float ddx[S], ddy[S], ddz[S], dc[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        const long long* bk = box + k * BOX;
-        const int o = (w * BY + v) * BX + u;
-        ddx[k] = (float)(bk[o + 1] - bk[o - 1]);
-        ddy[k] = (float)(bk[o + BX] - bk[o - BX]);
-        ddz[k] = (float)(bk[o + BX * BY] - bk[o - BX * BY]);
-        dc[k] = (float)bk[o];
+        const long long* Dk = r.D + (size_t)k * g.nodes;
+        ddx[k] = (float)(__ldg(Dk + xp) - __ldg(Dk + xm));
+        ddy[k] = (float)(__ldg(Dk + yp) - __ldg(Dk + ym));
+        ddz[k] = (float)(__ldg(Dk + zp) - __ldg(Dk + zm));
+        dc[k] = (float)__ldg(Dk + node);
     }
-    const size_t pnode = (size_t)pz * g.gxy + (size_t)py * g.gx + px;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         float gx = 0.f, gy = 0.f, gz = 0.f, vv = c.v0;
@@ -161,18 +235,25 @@ __global__ void __launch_bounds__(TX * TY * TZ) k_field_tiled(const __grid_const
 template <int S, int TX, int TY, int TZ>
 static void launch_tile(const TiledFieldParams& p, cudaStream_t s) {
     const size_t smem = sizeof(long long) * (size_t)(TX + 4) * (TY + 2) * (TZ + 2) * S;
-    k_field_tiled<S, TX, TY, TZ><<<p.blocks, TX * TY * TZ, smem, s>>>(p);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_field_tiled<S, TX, TY, TZ>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_field_tiled<S, TX, TY, TZ><<<p.blocks, TX * TY, smem, s>>>(p);
 }
 
 template <int S>
 static void launch_for_species(const TiledFieldParams& p, int tile, cudaStream_t s) {
     switch (tile) {
-        case 0: launch_tile<S, 32, 4, 2>(p, s); break;
-        case 1: launch_tile<S, 16, 8, 2>(p, s); break;
-        case 2: launch_tile<S, 16, 4, 4>(p, s); break;
-        case 3: launch_tile<S, 8, 8, 4>(p, s); break;
-        case 4: launch_tile<S, 64, 4, 1>(p, s); break;
-        default: launch_tile<S, 32, 8, 1>(p, s); break;
+        case 0: launch_tile<S, 32, 8, 4>(p, s); break;
+        case 1: launch_tile<S, 32, 8, 8>(p, s); break;
+        case 2: launch_tile<S, 16, 16, 4>(p, s); break;
+        case 3: launch_tile<S, 64, 4, 4>(p, s); break;
+        case 4: launch_tile<S, 16, 16, 8>(p, s); break;
+        case 5: launch_tile<S, 32, 4, 8>(p, s); break;
+        default: k_field_plain<S><<<p.blocks, 256, 0, s>>>(p); break;
     }
 }
 
@@ -214,6 +295,7 @@ static EncodeTiledFn encode_fn() {
 // False when TMA cannot be used (odd Mx, unaligned base, no driver entry point).
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile) {
+    if (field_tile_is_plain(tile)) return false;
     if (g.mx % 2 != 0 || (reinterpret_cast<uintptr_t>(D) & 15u) != 0 || S > 4) return false;
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -233,6 +315,12 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
 
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks) {
     const int* t = kTileShapes[tile];
+    if (t[0] == 0) {  // untiled: 256 nodes of the ghosted array per block
+        *tiles_x = 0;
+        *tiles_y = 0;
+        *blocks = (g.gnodes + 255) / 256;
+        return;
+    }
     const int nx = (g.mx + 1 + t[0] - 1) / t[0];
     const int ny = (g.my + 1 + t[1] - 1) / t[1];
     const int nz = (g.mz + 1 + t[2] - 1) / t[2];

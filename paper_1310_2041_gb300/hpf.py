@@ -78,6 +78,7 @@ def load():
         L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
         L.hpf_get_order.argtypes = [vp, vp]
         L.hpf_field_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.hpf_set_field_tile.argtypes = [vp, i32]
         L.hpf_scatter_density.argtypes = [vp, vp]
         L.hpf_field.argtypes = [vp, vp, vp]
         L.hpf_forces.argtypes = [vp, vp, i32]
@@ -97,7 +98,8 @@ def load():
                                        ctypes.POINTER(ctypes.c_int64)]
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
-                     "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile"):
+                     "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile",
+                     "hpf_set_field_tile"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib
@@ -248,6 +250,10 @@ class System:
         tma = ctypes.c_int32()
         self._check(self.lib.hpf_field_tile(self.h, shape, ctypes.byref(tma)))
         return tuple(shape), bool(tma.value)
+
+    def force_field_tile(self, tile):
+        """Pin the stencil to candidate `tile` (0..6), or -1 to autotune again."""
+        self._check(self.lib.hpf_set_field_tile(self.h, int(tile)))
 
     # ---- the path
     def scatter_density(self, out=None):
