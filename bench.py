@@ -280,7 +280,7 @@ def run_ours(args):
         traffic = tr["dram_bytes_per_launch"] * bead_steps_per_launch / tr["bead_steps_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                "kernel": "k_step", "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
+                "kernel": "k_step_warp_batch", "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
                 "avg_launch_us": avg_launch_s * 1e6,
                 "stage_ms": {k: round(v[0], 4) for k, v in prof.items()}}
     launches = int(sum(v[1] for v in prof.values()))
