@@ -255,6 +255,112 @@ hpf_status hpf_batch_use_graphs(hpf_batch* batch, int32_t enable);
 /* Free the batch and its replica contexts.  NULL is a no-op. */
 hpf_status hpf_batch_destroy(hpf_batch* batch);
 
+/* ---- Learned density propagator ------------------------------------------
+ *
+ * The paper has no counterpart to this part: it refreshes the density with a
+ * CIC scatter at every field update.  Here a small 3-D convolutional network
+ * predicts how the per-species volume fractions phi_K = rho_K / rho0 (the
+ * quantities the external potential V_K of the MD-SCF section is built from)
+ * change over K steps, so that between true scatters, taken every K steps,
+ * the field can still be refreshed every step from predicted densities.
+ *
+ * Network (two species only): input x = (phi_A, phi_B at step t - K, phi_A,
+ * phi_B at step t), 4 channels on the periodic Mx x My x Mz mesh; three
+ * 3x3x3 periodic convolutions (cross-correlation) 4 -> 16 -> 16 -> 2 channels
+ * with SiLU after the first two; output dphi = predicted phi(t + K) - phi(t).
+ * A convolution computes out[co](n) = b[co] + sum_d sum_ci W[d][ci][co]
+ * in[ci](n + d) over the 27 offsets d = (dz, dy, dx) in {-1, 0, 1}^3, z-major.
+ * Weights and activations are BF16 on the tensor cores with FP32
+ * accumulation; the master parameters and Adam state are FP32.
+ *
+ * Parameter vector (hpf_prop_param_count() floats): for each layer in order,
+ * W [27][C_in][C_out] then b [C_out].  Mesh arrays are planar FP32,
+ * [channel][Mz][My][Mx].  Pointers may be host or device memory.
+ * The network's buffers belong to the handle: use one handle from one
+ * stream at a time (hpf_step_learned runs it on the context's stream). */
+typedef struct hpf_prop hpf_prop;
+
+/* mesh = (Mx, My, Mz), each 2..1024, at most 2^26 nodes; stream as in
+ * hpf_init.  The weights start at zero (the network predicts no change).
+ * Errors: HPF_ERR_INVALID, HPF_ERR_NOMEM, HPF_ERR_CUDA. */
+hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out);
+hpf_status hpf_prop_destroy(hpf_prop* prop); /* NULL is a no-op */
+int32_t hpf_prop_param_count(void);
+
+/* Load [param_count] FP32 parameters (and reset Adam); synchronises. */
+hpf_status hpf_prop_set_weights(hpf_prop* prop, const float* params);
+/* Copy the FP32 parameters out (synchronises for a host destination). */
+hpf_status hpf_prop_get_weights(hpf_prop* prop, float* params);
+
+/* dphi [2][Mz][My][Mx] = network(x [4][Mz][My][Mx]).  Synchronises for a
+ * host destination. */
+hpf_status hpf_prop_forward(hpf_prop* prop, const float* x, float* dphi);
+
+/* Loss L = mean over the 2 x M outputs of (network(x) - (phi_next - x[2:4]))^2
+ * and its gradient with respect to the parameter vector (back-propagation
+ * through the same BF16 kernels: data gradients with flipped, transposed
+ * weights, weight gradients as tensor-core voxel reductions).  phi_next is
+ * [2][Mz][My][Mx]; grads [param_count] and loss may be NULL.  Synchronises
+ * when loss is given or grads is host memory. */
+hpf_status hpf_prop_backward(hpf_prop* prop, const float* x, const float* phi_next, float* grads,
+                             double* loss);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) of the
+ * parameters with the given gradient vector.  Errors: HPF_ERR_INVALID (lr <= 0). */
+hpf_status hpf_prop_adam_step(hpf_prop* prop, const float* grads, float lr);
+
+/* hpf_prop_backward followed by hpf_prop_adam_step with its own gradients,
+ * all on the device (the loss before the update is returned when loss is not
+ * NULL, which synchronises). */
+hpf_status hpf_prop_train_step(hpf_prop* prop, const float* x, const float* phi_next, float lr,
+                               double* loss);
+
+/* phi [n_species][Mz][My][Mx] FP32 of the context's current positions: the
+ * CIC density mesh times 2^-39 / (rho0 h^3).  Errors: HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_density_phi(hpf_ctx* ctx, float* phi);
+
+/* Field-force error of a candidate density at the current positions:
+ * eps = || F(phi) - F(true) ||_2 / || F(true) ||_2 over all beads and
+ * components, where F(true) is the field force of the true CIC density and
+ * F(phi) that of the candidate phi [n_species][Mz][My][Mx] (FP32, taken to
+ * the mesh's fixed point; negative values count as zero).  Leaves the field
+ * of the true density in force.  Synchronises.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_judge_density(hpf_ctx* ctx, const float* phi, double* eps);
+
+/* Outcome of hpf_step_learned (totals of the call). */
+typedef struct {
+    int64_t steps;    /* steps advanced */
+    int32_t windows;  /* windows of K steps completed */
+    int32_t learned;  /* windows run on predicted densities and accepted */
+    int32_t rejected; /* learned windows whose judged error exceeded tol: rolled back, re-run plain */
+    int32_t plain;    /* windows run plain from the start (no history yet, or after a rejection) */
+    int32_t judged;   /* predictions judged (learned and shadow) */
+    double eps_last;  /* last judged field-force error */
+    double eps_max;   /* largest judged error */
+    double eps_sum;   /* sum of judged errors */
+} hpf_learned_stats;
+
+/* Advance n_windows windows of K steps (K in 2..64) with the learned
+ * propagator (two species; the network's mesh must equal the context's).
+ * A window starts at a true update t: the density D(t) is scattered and the
+ * field refreshed from it.  A learned window predicts dphi = network(phi(t-K),
+ * phi(t)) and runs steps t+1 .. t+K-1 on the field of D(t) + (j/K) dphi (in
+ * the mesh's fixed point); the last step scatters the true D(t+K).  There the
+ * judge computes eps (as hpf_judge_density) between the field force of the
+ * predicted D(t) + dphi and of the true D(t+K).  eps <= tol accepts the
+ * window; otherwise the state at t is restored and the window re-run with a
+ * true scatter and field refresh every step (the plain update), and the next
+ * windows run plain while their predictions are judged in the shadow, until
+ * one meets tol.  The first window of a context runs plain (it builds the
+ * phi(t-K) history).  Beads are re-sorted only at window starts.  With zero
+ * network weights a learned window equals field_every = K exactly.
+ * Synchronises once per window.  stats may be NULL.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_STATE, HPF_ERR_CUDA, HPF_ERR_NONFINITE,
+ * HPF_ERR_OVERFLOW. */
+hpf_status hpf_step_learned(hpf_ctx* ctx, hpf_prop* prop, int32_t n_windows, int32_t K, double tol,
+                            hpf_learned_stats* stats);
+
 /* ---- Field forces without any device allocation ---------------------------
  *
  * The paper has no counterpart to this entry point.  It is here for callers

@@ -62,6 +62,23 @@ struct hpf_ctx {
     std::vector<EvPair> ev_used;
     std::vector<cudaEvent_t> ev_free;
     std::string err;
+    struct LearnedBufs* learned = nullptr;  // learned-propagator buffers (allocated on first use)
+};
+
+// Buffers of the learned-propagator driver and the density judge.
+struct LearnedBufs {
+    unsigned long long* Dbase = nullptr;  // D(t) at the window start [S][M]
+    unsigned long long* Dp = nullptr;     // predicted / candidate mesh [S][M]
+    CUtensorMap tmap;                     // over Dp
+    int tmap_tile = -1;
+    bool tmap_ok = false;
+    float* x = nullptr;     // network input [max(4, S)][M]: phi(t - K), phi(t)
+    float* dphi = nullptr;  // predicted change [S][M]
+    float* snap = nullptr;  // state at the window start [6][n]
+    double* acc = nullptr;  // judge sums [2] and their partials
+    double* h_acc = nullptr;
+    long long hist_step = -1;  // step whose phi is in x[0:2] (-1: none)
+    bool plain_mode = false;   // run plain windows (shadow-judged) until a prediction meets tol
 };
 
 namespace {
@@ -247,19 +264,27 @@ void ensure_tmaps(hpf_ctx* c, int tile) {
     c->tmap_tile = tile;
 }
 
-// One replica's record of the tiled stencil reading mesh buffer `dm`.
-void fill_field_rep(hpf_ctx* c, int tile, int dm, TiledFieldRep& fr, int& blocks) {
-    ensure_tmaps(c, tile);
-    fr.tmap = c->tmap[dm];
+// One replica's record of the tiled stencil reading mesh D (tensor map tm,
+// usable when tm_ok) and clearing D_clear (may be NULL).
+void fill_field_rep_mesh(hpf_ctx* c, int tile, const unsigned long long* D, const CUtensorMap& tm,
+                         bool tm_ok, unsigned long long* D_clear, TiledFieldRep& fr, int& blocks) {
+    fr.tmap = tm;
     fr.g = c->geom;
-    fr.D = reinterpret_cast<const long long*>(mesh_buf(c, dm));
+    fr.D = reinterpret_cast<const long long*>(D);
     fr.G = c->G;
-    fr.D_clear = mesh_buf(c, dm ^ 1);
-    fr.use_tma = c->tmap_ok ? 1 : 0;
+    fr.D_clear = D_clear;
+    fr.use_tma = tm_ok ? 1 : 0;
     int nb = 0;
     tile_grid(c->geom, tile, &fr.tiles_x, &fr.tiles_y, &nb);
     fr.blk_begin = blocks;
     blocks += nb;
+}
+
+// The record reading mesh buffer `dm` and clearing the other one.
+void fill_field_rep(hpf_ctx* c, int tile, int dm, TiledFieldRep& fr, int& blocks) {
+    ensure_tmaps(c, tile);
+    fill_field_rep_mesh(c, tile, mesh_buf(c, dm), c->tmap[dm], c->tmap_ok, mesh_buf(c, dm ^ 1), fr,
+                        blocks);
 }
 
 // Time every candidate tile on this launch shape and keep the fastest.  The
@@ -356,6 +381,39 @@ hpf_status run_field(hpf_ctx* c) {
     return HPF_OK;
 }
 
+// Field of an arbitrary mesh D (tensor map tm when tm_ok) into the context's
+// field buffer, clearing D_clear when given.  The tile must have been chosen
+// (run_field ran before).  The context's mesh bookkeeping is not changed.
+hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap& tm, bool tm_ok,
+                      unsigned long long* D_clear) {
+    {
+        StageScope sc(c, HPF_STAGE_FIELD, 1);
+        if (c->S <= 4 && c->field_tile >= 0) {
+            TiledFieldParams p;
+            memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+            p.R = 1;
+            p.coef = c->d_coef;
+            p.flag = c->dflag;
+            fill_field_rep_mesh(c, c->field_tile, D, tm, tm_ok, D_clear, p.rep[0], p.blocks);
+            launch_field_tiled(p, c->S, c->field_tile, c->stream);
+        } else {
+            BatchFieldParams fp;
+            memset(&fp, 0, sizeof fp);
+            fp.R = 1;
+            fp.coef = c->d_coef;
+            fp.rep[0].g = c->geom;
+            fp.rep[0].D = reinterpret_cast<const long long*>(D);
+            fp.rep[0].G = c->G;
+            fp.rep[0].D_clear = D_clear;
+            fp.rep[0].blk_begin = 0;
+            fp.blocks = (c->geom.gnodes + 255) / 256;
+            launch_field_batch(fp, c->S, c->stream);
+        }
+    }
+    LAUNCH_CHECK(c);
+    return HPF_OK;
+}
+
 hpf_status refresh_field(hpf_ctx* c) {
     hpf_status s = scatter_current(c);
     if (s != HPF_OK) return s;
@@ -388,6 +446,52 @@ hpf_status sort_beads(hpf_ctx* c) {
     c->sb.chain_of_in = c->sb.chain_of_out;
     c->sb.chain_of_out = u;
     c->last_sort_step = c->step;
+    return HPF_OK;
+}
+
+// Launch `chunk` steps on the field in force; with fuse the last sub-step
+// also scatters its positions into the other mesh (which must be zero).
+hpf_status advance(hpf_ctx* c, int chunk, bool fuse) {
+    {
+        StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
+        if (c->warp_mode) {
+            // the batch step kernel instantiated for one replica
+            SingleStepParams p;
+            memset(&p, 0, sizeof p);
+            p.R = 1;
+            p.n_sub = chunk;
+            p.cur = c->cur;
+            p.fuse = fuse ? 1 : 0;
+            p.dnext = c->dmesh ^ 1;
+            p.step0 = c->step;
+            p.step_dev = nullptr;
+            p.flag = c->dflag;
+            BatchStepRep& q = p.rep[0];
+            q.g = c->geom;
+            q.c = c->sc;
+            q.st[0] = c->st[0];
+            q.st[1] = c->st[1];
+            q.meta = c->meta;
+            q.seg_start = c->sb.seg_start;
+            q.seg_count = c->sb.seg_count;
+            q.n_seg = c->sb.n_seg;
+            q.G = c->G;
+            q.D[0] = mesh_buf(c, 0);
+            q.D[1] = mesh_buf(c, 1);
+            launch_step_warp_single(p, c->C, c->sc.sigma > 0.f, c->stream);
+        } else
+            launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, chunk, c->step, c->geom,
+                        c->G, c->sc, fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr, c->dflag,
+                        c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->cur ^= 1;
+    c->step += chunk;
+    if (fuse) {
+        c->dmesh ^= 1;
+        c->mesh_step = c->step;
+        c->next_zero = false;
+    }
     return HPF_OK;
 }
 
@@ -527,6 +631,16 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->d_out6);
     cudaFreeHost(c->h_out6);
+    if (LearnedBufs* L = c->learned) {
+        cudaFree(L->Dbase);
+        cudaFree(L->Dp);
+        cudaFree(L->x);
+        cudaFree(L->dphi);
+        cudaFree(L->snap);
+        cudaFree(L->acc);
+        cudaFreeHost(L->h_acc);
+        delete L;
+    }
     cudaGetLastError();
     delete c;
     return HPF_OK;
@@ -705,47 +819,8 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         }
         // the launch that ends on a refresh step also scatters its final positions
         const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
-        unsigned long long* Dnext = fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
-        {
-            StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
-            if (c->warp_mode) {
-                // the batch step kernel instantiated for one replica
-                SingleStepParams p;
-                memset(&p, 0, sizeof p);
-                p.R = 1;
-                p.n_sub = (int)chunk;
-                p.cur = c->cur;
-                p.fuse = fuse ? 1 : 0;
-                p.dnext = c->dmesh ^ 1;
-                p.step0 = c->step;
-                p.step_dev = nullptr;
-                p.flag = c->dflag;
-                BatchStepRep& q = p.rep[0];
-                q.g = c->geom;
-                q.c = c->sc;
-                q.st[0] = c->st[0];
-                q.st[1] = c->st[1];
-                q.meta = c->meta;
-                q.seg_start = c->sb.seg_start;
-                q.seg_count = c->sb.seg_count;
-                q.n_seg = c->sb.n_seg;
-                q.G = c->G;
-                q.D[0] = mesh_buf(c, 0);
-                q.D[1] = mesh_buf(c, 1);
-                launch_step_warp_single(p, c->C, c->sc.sigma > 0.f, c->stream);
-            } else
-                launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, (int)chunk, c->step,
-                            c->geom, c->G, c->sc, Dnext, c->dflag, c->stream);
-        }
-        LAUNCH_CHECK(c);
-        c->cur ^= 1;
-        c->step += chunk;
+        if ((s = advance(c, (int)chunk, fuse)) != HPF_OK) return s;
         left -= chunk;
-        if (fuse) {
-            c->dmesh ^= 1;
-            c->mesh_step = c->step;
-            c->next_zero = false;
-        }
     }
     return HPF_OK;
 }
@@ -1139,6 +1214,251 @@ hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
         batch_advance(b, chunk, fuse);
         left -= chunk;
     }
+    return HPF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ learned propagator driver
+
+namespace {
+
+hpf_status ensure_learned(hpf_ctx* c) {
+    if (c->learned) return HPF_OK;
+    LearnedBufs* L = new LearnedBufs();
+    const size_t M = (size_t)c->geom.nodes, S = (size_t)c->S, xs = S > 4 ? S : 4;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&L->Dbase, sizeof(unsigned long long) * S * M);
+    e = e ? e : cudaMalloc(&L->Dp, sizeof(unsigned long long) * S * M);
+    e = e ? e : cudaMalloc(&L->x, sizeof(float) * xs * M);
+    e = e ? e : cudaMalloc(&L->dphi, sizeof(float) * S * M);
+    e = e ? e : cudaMalloc(&L->snap, sizeof(float) * 6 * (size_t)(c->n > 0 ? c->n : 1));
+    e = e ? e : cudaMalloc(&L->acc, sizeof(double) * (2 + 2 * (size_t)force_error_partials()));
+    e = e ? e : cudaMallocHost(&L->h_acc, sizeof(double) * 2);
+    c->learned = L;  // freed by hpf_destroy, also after a failed allocation
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(L->Dbase);
+        cudaFree(L->Dp);
+        cudaFree(L->x);
+        cudaFree(L->dphi);
+        cudaFree(L->snap);
+        cudaFree(L->acc);
+        cudaFreeHost(L->h_acc);
+        delete L;
+        c->learned = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA,
+                    "learned-propagator buffers: %s", cudaGetErrorString(e));
+    }
+    return HPF_OK;
+}
+
+// eps of the candidate mesh in Dp against the true density of the current
+// positions, which must be the context's mesh.  Leaves the true field in force.
+hpf_status judge_mesh(hpf_ctx* c, double* eps) {
+    LearnedBufs* L = c->learned;
+    hpf_status s;
+    if (c->field_tile < 0 && (s = run_field(c)) != HPF_OK) return s;  // picks the tile
+    if (L->tmap_tile != c->field_tile) {
+        L->tmap_ok = c->S <= 4 && make_mesh_tensor_map(&L->tmap,
+                                                       reinterpret_cast<const long long*>(L->Dp),
+                                                       c->geom, c->S, c->field_tile);
+        L->tmap_tile = c->field_tile;
+    }
+    if ((s = field_from(c, L->Dp, L->tmap, L->tmap_ok, nullptr)) != HPF_OK) return s;
+    const long long n3 = 3ll * c->n;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 1 : 0);
+        launch_forces(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, HPF_FORCE_FIELD,
+                      c->out_f, c->stream);
+    }
+    if ((s = run_field(c)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 2 : 1);
+        launch_forces(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, HPF_FORCE_FIELD,
+                      c->out_f + n3, c->stream);
+        launch_force_error(c->out_f, c->out_f + n3, n3, L->acc, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(L->h_acc, L->acc, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    if ((s = check_flags(c)) != HPF_OK) return s;
+    const double e2 = L->h_acc[0], r2 = L->h_acc[1];
+    *eps = r2 > 0.0 ? sqrt(e2 / r2) : (e2 > 0.0 ? INFINITY : 0.0);
+    return HPF_OK;
+}
+
+// K steps with a true scatter and field refresh at every step (the plain
+// update; the same launches as a context with field_every = 1), no sorting.
+hpf_status plain_window(hpf_ctx* c, int K) {
+    const int fe = c->p.field_every, se = c->p.sort_every;
+    c->p.field_every = 1;
+    c->p.sort_every = 0;
+    hpf_status s = hpf_step(c, K);
+    c->p.field_every = fe;
+    c->p.sort_every = se;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+hpf_status hpf_density_phi(hpf_ctx* c, float* phi) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    if (!phi) return fail(c, HPF_ERR_INVALID, "phi is required");
+    hpf_status s = scatter_current(c);
+    if (s != HPF_OK) return s;
+    const long long n = (long long)mesh_words(c);
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_mesh_to_phi(mesh_buf(c, c->dmesh), n, c->ec.phi_c,
+                           reinterpret_cast<float*>(c->field_stage), c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, phi, c->field_stage, sizeof(float) * n);
+}
+
+hpf_status hpf_judge_density(hpf_ctx* c, const float* phi, double* eps) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!phi || !eps) return fail(c, HPF_ERR_INVALID, "phi and eps are required");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s = ensure_learned(c);
+    if (s != HPF_OK) return s;
+    LearnedBufs* L = c->learned;
+    const long long n = (long long)mesh_words(c);
+    CUDA_TRY(c, cudaMemcpyAsync(L->dphi, phi, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    if ((s = scatter_current(c)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_mesh_predict(nullptr, L->dphi, n, 1.0 / c->ec.phi_c, L->Dp, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return judge_mesh(c, eps);
+}
+
+hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32_t K, double tol,
+                            hpf_learned_stats* stats) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!prop || n_windows < 0 || K < 2 || K > 64 || !(tol >= 0.0))
+        return fail(c, HPF_ERR_INVALID, "need a network, n_windows >= 0, 2 <= K <= 64, tol >= 0");
+    if (c->S != 2) return fail(c, HPF_ERR_INVALID, "the propagator models two species");
+    if (!prop_mesh_is(prop, c->geom))
+        return fail(c, HPF_ERR_INVALID, "the network's mesh differs from the context's");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s = ensure_learned(c);
+    if (s != HPF_OK) return s;
+    LearnedBufs* L = c->learned;
+    hpf_learned_stats st;
+    memset(&st, 0, sizeof st);
+    const long long M = c->geom.nodes, SM = 2 * M;
+    const double inv_phi_c = 1.0 / c->ec.phi_c;
+    for (int w = 0; w < n_windows; ++w) {
+        // the window starts at a true update t: D(t) and its field
+        if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every &&
+            (s = sort_beads(c)) != HPF_OK)
+            return s;
+        if (!(c->field_valid && c->field_step == c->step && c->mesh_step == c->step) &&
+            (s = refresh_field(c)) != HPF_OK)
+            return s;
+        const long long t = c->step;
+        const unsigned long long* Dt = mesh_buf(c, c->dmesh);
+        CUDA_TRY(c, cudaMemcpyAsync(L->Dbase, Dt, sizeof(unsigned long long) * SM,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+        const bool have_hist = L->hist_step >= 0 && L->hist_step == t - K;
+        if (have_hist) {
+            StageScope sc(c, HPF_STAGE_OTHER, 6);
+            launch_mesh_to_phi(Dt, SM, c->ec.phi_c, L->x + SM, c->stream);
+            prop_predict(prop, L->x, L->dphi, c->stream);
+        }
+        LAUNCH_CHECK(c);
+        bool judged = false;
+        double eps = 0.0;
+        if (have_hist && !L->plain_mode) {
+            // learned window: steps t .. t+K-1 on predicted densities
+            CUDA_TRY(c, cudaMemcpyAsync(L->snap, cur_state(c).x, sizeof(float) * 6 * c->n,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            if (L->tmap_tile != c->field_tile) {
+                L->tmap_ok = make_mesh_tensor_map(&L->tmap,
+                                                  reinterpret_cast<const long long*>(L->Dp),
+                                                  c->geom, c->S, c->field_tile);
+                L->tmap_tile = c->field_tile;
+            }
+            if (!c->next_zero) {
+                CUDA_TRY(c, cudaMemsetAsync(mesh_buf(c, c->dmesh ^ 1), 0,
+                                            sizeof(unsigned long long) * SM, c->stream));
+                c->next_zero = true;
+            }
+            for (int j = 0; j < K; ++j) {
+                if (j > 0) {
+                    {
+                        StageScope sc(c, HPF_STAGE_OTHER, 1);
+                        launch_mesh_predict(L->Dbase, L->dphi, SM, (double)j / K * inv_phi_c,
+                                            L->Dp, c->stream);
+                    }
+                    if ((s = field_from(c, L->Dp, L->tmap, L->tmap_ok, nullptr)) != HPF_OK)
+                        return s;
+                }
+                if ((s = advance(c, 1, j == K - 1)) != HPF_OK) return s;
+            }
+            c->field_valid = false;  // the field in force was a predicted one
+            // judge the prediction for t + K against the true scatter there
+            {
+                StageScope sc(c, HPF_STAGE_OTHER, 1);
+                launch_mesh_predict(L->Dbase, L->dphi, SM, inv_phi_c, L->Dp, c->stream);
+            }
+            LAUNCH_CHECK(c);
+            if ((s = judge_mesh(c, &eps)) != HPF_OK) return s;
+            judged = true;
+            if (eps <= tol) {
+                st.learned += 1;
+            } else {
+                // roll back to t and take the plain update instead
+                st.rejected += 1;
+                CUDA_TRY(c, cudaMemcpyAsync(cur_state(c).x, L->snap, sizeof(float) * 6 * c->n,
+                                            cudaMemcpyDeviceToDevice, c->stream));
+                c->step = t;
+                c->field_valid = false;
+                c->mesh_step = -1;
+                c->next_zero = false;
+                if ((s = plain_window(c, K)) != HPF_OK) return s;
+                L->plain_mode = true;
+            }
+        } else {
+            if ((s = plain_window(c, K)) != HPF_OK) return s;
+            st.plain += 1;
+            if (have_hist) {
+                // shadow judge of the prediction made at t
+                if (c->mesh_step != c->step && (s = scatter_current(c)) != HPF_OK) return s;
+                {
+                    StageScope sc(c, HPF_STAGE_OTHER, 1);
+                    launch_mesh_predict(L->Dbase, L->dphi, SM, inv_phi_c, L->Dp, c->stream);
+                }
+                LAUNCH_CHECK(c);
+                if ((s = judge_mesh(c, &eps)) != HPF_OK) return s;
+                judged = true;
+                if (eps <= tol) L->plain_mode = false;
+            }
+        }
+        if (judged) {
+            st.judged += 1;
+            st.eps_last = eps;
+            st.eps_sum += eps;
+            if (eps > st.eps_max) st.eps_max = eps;
+        }
+        // phi(t) becomes the history of the next window
+        {
+            StageScope sc(c, HPF_STAGE_OTHER, 1);
+            launch_mesh_to_phi(L->Dbase, SM, c->ec.phi_c, L->x, c->stream);
+        }
+        LAUNCH_CHECK(c);
+        L->hist_step = t;
+        if ((s = check_flags(c)) != HPF_OK) return s;
+        st.windows += 1;
+        st.steps += K;
+    }
+    if (stats) *stats = st;
     return HPF_OK;
 }
 

@@ -148,7 +148,7 @@ struct BatchFieldRep {
     MeshGeom g;
     const long long* D;
     float4* G;
-    unsigned long long* D_clear;
+    unsigned long long* D_clear;   // mesh cleared by the same launch (NULL: none)
     int blk_begin;  // first block of this replica
 };
 
@@ -165,7 +165,7 @@ struct TiledFieldRep {
     MeshGeom g;
     const long long* D;
     float4* G;
-    unsigned long long* D_clear;
+    unsigned long long* D_clear;   // mesh cleared by the same launch (NULL: none)
     int use_tma;
     int tiles_x, tiles_y;
     int blk_begin;
@@ -406,5 +406,18 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
                           int tile);
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);
 int energy_partials_needed(int n, int nodes);
+
+// learned density propagator (the network lives in k_prop.cu)
+bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);
+void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s);
+void launch_mesh_to_phi(const unsigned long long* D, long long n, double phi_c, float* phi,
+                        cudaStream_t s);
+void launch_mesh_predict(const unsigned long long* D_base, const float* dphi, long long n,
+                         double frac_over_phi_c, unsigned long long* D_out, cudaStream_t s);
+// acc[0] = sum (Fa - Fb)^2, acc[1] = sum Fb^2 over n floats, deterministic;
+// acc holds 2 + 2 force_error_partials() doubles (the tail is scratch)
+void launch_force_error(const float* Fa, const float* Fb, long long n, double* acc,
+                        cudaStream_t s);
+int force_error_partials();
 
 }  // namespace hpf

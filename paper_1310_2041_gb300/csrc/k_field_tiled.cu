@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__
     for (int tz = 0; tz < TZ; ++tz) {
         const int pz = z0 + tz;
         if (pz > g.mz) break;
-        if (px < g.mx && py < g.my && pz < g.mz) {
+        if (r.D_clear && px < g.mx && py < g.my && pz < g.mz) {
             const size_t node = ((size_t)pz * g.my + py) * g.mx + px;
 #pragma unroll
             for (int k = 0; k < S; ++k) r.D_clear[(size_t)k * g.nodes + node] = 0ull;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ Til
     const int px = pnode % g.gx, py = (pnode / g.gx) % (g.my + 1), pz = pnode / g.gxy;
     const int x = px == g.mx ? 0 : px, y = py == g.my ? 0 : py, z = pz == g.mz ? 0 : pz;
     const int node = (z * g.my + y) * g.mx + x;
-    if (px < g.mx && py < g.my && pz < g.mz) {
+    if (r.D_clear && px < g.mx && py < g.my && pz < g.mz) {
 #pragma unroll
         for (int k = 0; k < S; ++k) r.D_clear[(size_t)k * g.nodes + node] = 0ull;
     }

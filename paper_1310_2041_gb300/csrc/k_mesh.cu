@@ -42,7 +42,7 @@ __device__ __forceinline__ void field_node(const long long* __restrict__ D, cons
     const int pz = pnode / g.gxy;
     const int x = px == g.mx ? 0 : px, y = py == g.my ? 0 : py, z = pz == g.mz ? 0 : pz;
     const int node = (z * g.my + y) * g.mx + x;
-    if (px < g.mx && py < g.my && pz < g.mz) {
+    if (D_clear && px < g.mx && py < g.my && pz < g.mz) {
 #pragma unroll
         for (int k = 0; k < S; ++k) D_clear[(size_t)k * g.nodes + node] = 0ull;
     }

@@ -57,6 +57,24 @@ class Params(ctypes.Structure):
     ]
 
 
+class LearnedStats(ctypes.Structure):
+    """Mirror of hpf_learned_stats."""
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("windows", ctypes.c_int32),
+        ("learned", ctypes.c_int32),
+        ("rejected", ctypes.c_int32),
+        ("plain", ctypes.c_int32),
+        ("judged", ctypes.c_int32),
+        ("eps_last", ctypes.c_double),
+        ("eps_max", ctypes.c_double),
+        ("eps_sum", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def load():
     """Load libhpf.so; raises if it has not been built."""
     global _lib
@@ -96,6 +114,27 @@ def load():
         L.hpf_profile.argtypes = [vp, i32]
         L.hpf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]
+        fp, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+        L.hpf_prop_init.argtypes = [ctypes.POINTER(i32), vp, ctypes.POINTER(vp)]
+        L.hpf_prop_destroy.argtypes = [vp]
+        L.hpf_prop_param_count.restype = i32
+        L.hpf_prop_param_count.argtypes = []
+        L.hpf_prop_set_weights.argtypes = [vp, vp]
+        L.hpf_prop_get_weights.argtypes = [vp, vp]
+        L.hpf_prop_forward.argtypes = [vp, vp, vp]
+        L.hpf_prop_backward.argtypes = [vp, vp, vp, vp, dp]
+        L.hpf_prop_adam_step.argtypes = [vp, vp, ctypes.c_float]
+        L.hpf_prop_train_step.argtypes = [vp, vp, vp, ctypes.c_float, dp]
+        L.hpf_density_phi.argtypes = [vp, vp]
+        L.hpf_judge_density.argtypes = [vp, vp, dp]
+        L.hpf_step_learned.argtypes = [vp, vp, i32, i32, ctypes.c_double,
+                                       ctypes.POINTER(LearnedStats)]
+        for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
+                     "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_backward",
+                     "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
+                     "hpf_judge_density", "hpf_step_learned"):
+            getattr(L, name).restype = ctypes.c_int
+        del fp
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
                      "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile",
@@ -286,6 +325,29 @@ class System:
         self._check(self.lib.hpf_energy(self.h, out))
         return np.array(list(out))
 
+    # ---- learned propagator
+    def density_phi(self, out=None):
+        """Volume fractions phi [S][Mz][My][Mx] (FP32) of the current positions."""
+        if out is None:
+            out = np.empty(self.mesh_shape, dtype=np.float32)
+        op, _a = _ptr(out, np.float32, self.mesh_shape, "phi")
+        self._check(self.lib.hpf_density_phi(self.h, op))
+        return out
+
+    def judge_density(self, phi):
+        """Field-force error of candidate volume fractions against the true scatter."""
+        pp, _a = _ptr(phi, np.float32, self.mesh_shape, "phi")
+        eps = ctypes.c_double()
+        self._check(self.lib.hpf_judge_density(self.h, pp, ctypes.byref(eps)))
+        return eps.value
+
+    def step_learned(self, prop, n_windows, K=20, tol=1e-3):
+        """n_windows windows of K steps with the learned propagator; returns the stats dict."""
+        st = LearnedStats()
+        self._check(self.lib.hpf_step_learned(self.h, prop.h, int(n_windows), int(K),
+                                              float(tol), ctypes.byref(st)))
+        return st.as_dict()
+
     # ---- profiling
     def profile(self, enable=True):
         self._check(self.lib.hpf_profile(self.h, 1 if enable else 0))
@@ -348,3 +410,112 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Propagator:
+    """The learned density propagator network (hpf_prop_init ... hpf_prop_destroy).
+
+    Mesh arrays are planar FP32: inputs x [4][Mz][My][Mx] = (phi_A, phi_B at
+    t - K, phi_A, phi_B at t); outputs and targets [2][Mz][My][Mx]."""
+
+    def __init__(self, mesh, stream=None):
+        self.lib = load()
+        m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
+        self.mesh = tuple(int(v) for v in m)
+        if stream is None:
+            stream = current_stream_handle()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        arr = (ctypes.c_int32 * 3)(*self.mesh)
+        h = ctypes.c_void_p()
+        st = self.lib.hpf_prop_init(arr, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if st != 0:
+            raise HPFError(st, self.lib.hpf_status_string(st).decode())
+        self.h = h
+        self.n_params = int(self.lib.hpf_prop_param_count())
+        self.V = self.mesh[0] * self.mesh[1] * self.mesh[2]
+        self.grid = (self.mesh[2], self.mesh[1], self.mesh[0])
+
+    def _check(self, st):
+        if st != 0:
+            raise HPFError(st, self.lib.hpf_status_string(st).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hpf_prop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_weights(self, params):
+        pp, _a = _ptr(params, np.float32, (self.n_params,), "params")
+        self._check(self.lib.hpf_prop_set_weights(self.h, pp))
+
+    def get_weights(self, out=None):
+        if out is None:
+            out = np.empty(self.n_params, dtype=np.float32)
+        op, _a = _ptr(out, np.float32, (self.n_params,), "params")
+        self._check(self.lib.hpf_prop_get_weights(self.h, op))
+        return out
+
+    def forward(self, x, out=None):
+        if out is None:
+            out = np.empty((2,) + self.grid, dtype=np.float32)
+        xp, _a = _ptr(x, np.float32, (4,) + self.grid, "x")
+        op, _b = _ptr(out, np.float32, (2,) + self.grid, "dphi")
+        self._check(self.lib.hpf_prop_forward(self.h, xp, op))
+        return out
+
+    def backward(self, x, phi_next, grads=None):
+        """(loss, gradient vector) of the mean squared error against phi_next - x[2:4]."""
+        if grads is None:
+            grads = np.empty(self.n_params, dtype=np.float32)
+        xp, _a = _ptr(x, np.float32, (4,) + self.grid, "x")
+        tp, _b = _ptr(phi_next, np.float32, (2,) + self.grid, "phi_next")
+        gp, _c = _ptr(grads, np.float32, (self.n_params,), "grads")
+        loss = ctypes.c_double()
+        self._check(self.lib.hpf_prop_backward(self.h, xp, tp, gp, ctypes.byref(loss)))
+        return loss.value, grads
+
+    def adam_step(self, grads, lr):
+        gp, _a = _ptr(grads, np.float32, (self.n_params,), "grads")
+        self._check(self.lib.hpf_prop_adam_step(self.h, gp, float(lr)))
+
+    def train_step(self, x, phi_next, lr, want_loss=False):
+        xp, _a = _ptr(x, np.float32, (4,) + self.grid, "x")
+        tp, _b = _ptr(phi_next, np.float32, (2,) + self.grid, "phi_next")
+        loss = ctypes.c_double()
+        self._check(self.lib.hpf_prop_train_step(self.h, xp, tp, float(lr),
+                                                 ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+
+def pack_params(layers):
+    """[(W [27][Ci][Co], b [Co]) per layer] -> the flat FP32 parameter vector."""
+    return np.concatenate([np.concatenate([np.asarray(W, dtype=np.float32).reshape(-1),
+                                           np.asarray(b, dtype=np.float32).reshape(-1)])
+                           for W, b in layers])
+
+
+def unpack_params(vec, channels=((4, 16), (16, 16), (16, 2))):
+    """Inverse of pack_params."""
+    out, k = [], 0
+    vec = np.asarray(vec)
+    for ci, co in channels:
+        W = vec[k:k + 27 * ci * co].reshape(27, ci, co)
+        k += 27 * ci * co
+        b = vec[k:k + co]
+        k += co
+        out.append((W, b))
+    return out

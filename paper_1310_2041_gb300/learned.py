@@ -1,0 +1,105 @@
+"""Training and evaluation driver of the learned density propagator.
+
+Marshalling and bookkeeping only: densities come from the library's CIC
+scatter (``System.density_phi``), the network runs and trains in the
+library's BF16 tensor-core kernels (``Propagator``), and field-force errors
+are the library's judge (``System.judge_density``).  Snapshot meshes stay in
+device memory (torch tensors) between calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import hpf
+
+
+def collect_snapshots(system: hpf.System, n_snap: int, K: int, out=None):
+    """phi of the current positions, then K steps, n_snap times.
+
+    ``out``: optional preallocated float32 tensor [n_snap, S, Mz, My, Mx] (CUDA
+    for device-resident snapshots).  Returns it."""
+    import torch
+    shape = (n_snap,) + system.mesh_shape
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    for k in range(n_snap):
+        system.density_phi(out[k])
+        if k + 1 < n_snap:
+            system.step(K)
+    return out
+
+
+def triples(n_snap: int):
+    """Indices k with a training example (phi[k-1], phi[k]) -> phi[k+1]."""
+    return list(range(1, n_snap - 1))
+
+
+def train(prop: hpf.Propagator, snaps, iters: int, lr: float = 2e-3, lr_final: float = 2e-4,
+          examples=None, seed: int = 0, log_every: int = 0):
+    """Adam on the mean squared error of the predicted change, one example per
+    step in a seeded random order, learning rate decayed geometrically from lr
+    to lr_final.  Returns the loss log [(iteration, loss)]."""
+    ex = triples(snaps.shape[0]) if examples is None else list(examples)
+    rng = np.random.default_rng(seed)
+    order = []
+    log = []
+    decay = (lr_final / lr) ** (1.0 / max(iters - 1, 1))
+    for it in range(iters):
+        if not order:
+            order = list(rng.permutation(ex))
+        k = int(order.pop())
+        x = snaps[k - 1:k + 1]  # phi(t - K), phi(t): 4 contiguous channels
+        want = bool(log_every) and (it % log_every == 0 or it == iters - 1)
+        loss = prop.train_step(x, snaps[k + 1], lr * decay ** it, want_loss=want)
+        if want:
+            log.append((it, loss))
+    return log
+
+
+def validation_loss(prop: hpf.Propagator, snaps, examples):
+    """Mean loss of the network and of predicting no change over examples."""
+    net, zero = [], []
+    for k in examples:
+        x = snaps[k - 1:k + 1]
+        net.append(prop.backward(x, snaps[k + 1])[0])
+        d = (snaps[k + 1] - snaps[k]).double()
+        zero.append(float((d * d).mean()))
+    return float(np.mean(net)), float(np.mean(zero))
+
+
+def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows: int, K: int,
+                     lags=(1, 2, 5, 10, 20)):
+    """Field-force errors (the judge's eps) of density candidates along a plain
+    trajectory of ``system`` (which should refresh its field every step).
+
+    For every lag L in ``lags``: hold-last phi(t) and linear extrapolation
+    2 phi(t) - phi(t - L), judged at t + L.  With a network (trained for lag
+    K): phi(t) + net(phi(t - K), phi(t)) judged at t + K.  Returns
+    {name: [eps per judged point]}."""
+    import torch
+    H = max(max(lags), 2 * K)
+    hist = torch.empty((H + 1,) + system.mesh_shape, dtype=torch.float32, device="cuda")
+    res = {f"hold_{L}": [] for L in lags}
+    res.update({f"linear_{L}": [] for L in lags})
+    res["net"] = []
+    res["hold_net"] = []
+    n_steps = n_windows * K + H
+    for s in range(n_steps + 1):
+        cur = hist[s % (H + 1)]
+        system.density_phi(cur)
+        if s >= H:
+            for L in lags:
+                if (s - H) % L == 0:
+                    prev = hist[(s - L) % (H + 1)]
+                    prev2 = hist[(s - 2 * L) % (H + 1)]
+                    res[f"hold_{L}"].append(system.judge_density(prev))
+                    res[f"linear_{L}"].append(system.judge_density(2 * prev - prev2))
+            if prop is not None and (s - H) % K == 0:
+                a, b = hist[(s - 2 * K) % (H + 1)], hist[(s - K) % (H + 1)]
+                x = torch.cat([a, b]).contiguous()
+                dphi = prop.forward(x, out=torch.empty_like(b))
+                res["net"].append(system.judge_density(b + dphi))
+                res["hold_net"].append(system.judge_density(b))
+        if s < n_steps:
+            system.step(1)
+    return res

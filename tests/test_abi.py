@@ -66,18 +66,21 @@ def test_library_loads_and_answers_without_a_gpu(lib_path):
     assert L.hpf_init(ctypes.byref(p), None, ctypes.byref(h)) == 1
 
 
-def test_params_struct_layout_matches_header(tmp_path):
-    """Field offsets of the ctypes mirror equal offsetof() of the C header."""
+@pytest.mark.parametrize("mirror,cname", [("Params", "hpf_params"),
+                                           ("LearnedStats", "hpf_learned_stats")])
+def test_struct_layout_matches_header(tmp_path, mirror, cname):
+    """Field offsets of the ctypes mirrors equal offsetof() of the C header."""
     from paper_1310_2041_gb300 import hpf
-    fields = [f for f, _ in hpf.Params._fields_]
+    cls = getattr(hpf, mirror)
+    fields = [f for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'printf("%zu\\n", offsetof(hpf_params, {f}));' for f in fields)
+    body = "".join(f'printf("%zu\\n", offsetof({cname}, {f}));' for f in fields)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hpf.h"\n'
-                   f'int main(void){{ {body} printf("%zu\\n", sizeof(hpf_params)); return 0; }}')
+                   f'int main(void){{ {body} printf("%zu\\n", sizeof({cname})); return 0; }}')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
-    want = [getattr(hpf.Params, f).offset for f in fields] + [ctypes.sizeof(hpf.Params)]
+    want = [getattr(cls, f).offset for f in fields] + [ctypes.sizeof(cls)]
     assert got == want

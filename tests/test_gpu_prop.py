@@ -1,0 +1,274 @@
+"""The learned density propagator on the GPU against its CPU oracle, through the C ABI.
+
+Network kernels (BF16 operands, FP32 accumulation) against the FP64 oracle
+of oracle/propagator.py.  Tolerance: every BF16 rounding (inputs, weights,
+the two hidden activations, the back-propagated gradients) carries a
+relative error of at most 2^-9; through three layers of 27 x 16-term sums
+with mixed signs that is about 1e-2 of an output's norm, so outputs and
+gradients are held to 3e-2 of their norm (and a cosine above 0.999),
+FP32-only quantities (Adam) to FP32 rounding.
+
+The learned MD step is checked by its two exact limits: a network with
+zero weights predicts no change, and the learned window must then equal
+the plain schedule with field_every = K bit for bit; a tolerance of zero
+rejects every prediction, and the run must equal field_every = 1 bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import propagator as P
+from paper_1310_2041_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MESHES = [(13, 10, 5), (8, 8, 2), (3, 2, 2), (24, 16, 9)]
+
+
+def rand_params(seed):
+    rng = np.random.default_rng(seed)
+    params = P.init_params(seed)
+    # a last layer of ordinary size and non-zero biases, so every term matters
+    params = [(W * (10.0 if k == 2 else 1.0), rng.normal(scale=0.2, size=b.shape))
+              for k, (W, b) in enumerate(params)]
+    return params
+
+
+def rand_phi(shape, seed, c=4):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.2, size=(c,) + shape)
+
+
+def grid(mesh):
+    return (mesh[2], mesh[1], mesh[0])
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def cosine(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("mesh", MESHES, ids=lambda m: "x".join(map(str, m)))
+def test_forward_matches_oracle(hpf_gpu, mesh):
+    params = rand_params(1)
+    x = rand_phi(grid(mesh), 2)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        y = net.forward(x.astype(np.float32))
+    yo, _ = P.forward(params, x)
+    assert y.shape == yo.shape
+    assert rel(y, yo) < 3e-2
+    assert cosine(y, yo) > 0.999
+    assert np.max(np.abs(y - yo)) < 0.1 * np.max(np.abs(yo))
+
+
+def test_zero_weights_predict_no_change(hpf_gpu):
+    mesh = (13, 10, 5)
+    with hpf_gpu.Propagator(mesh) as net:
+        y = net.forward(rand_phi(grid(mesh), 3).astype(np.float32))
+    assert np.all(y == 0.0)
+
+
+def test_weights_round_trip(hpf_gpu):
+    vec = hpf_gpu.pack_params(rand_params(4))
+    with hpf_gpu.Propagator((8, 8, 4)) as net:
+        assert net.n_params == vec.size == 9538
+        net.set_weights(vec)
+        assert np.array_equal(net.get_weights(), vec)
+
+
+@pytest.mark.parametrize("mesh", [(13, 10, 5), (24, 16, 9)], ids=lambda m: "x".join(map(str, m)))
+def test_backward_matches_oracle(hpf_gpu, mesh):
+    params = rand_params(5)
+    x = rand_phi(grid(mesh), 6)
+    nxt = rand_phi(grid(mesh), 7, c=2)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        loss, g = net.backward(x.astype(np.float32), nxt.astype(np.float32))
+    target = nxt - x[2:]
+    Lo, go = P.backward(params, x, target)
+    assert loss == pytest.approx(Lo, rel=2e-2)
+    got = hpf_gpu.unpack_params(g)
+    for k, ((gW, gb), (oW, ob)) in enumerate(zip(got, go)):
+        assert rel(gW, oW) < 3e-2, f"layer {k} weights"
+        assert cosine(gW, oW) > 0.999, f"layer {k} weights"
+        assert rel(gb, ob) < 3e-2, f"layer {k} biases"
+
+
+def test_adam_matches_oracle(hpf_gpu):
+    params = rand_params(8)
+    mesh = (8, 8, 4)
+    x = rand_phi(grid(mesh), 9)
+    t = rand_phi(grid(mesh), 10, c=2) - x[2:]
+    state = P.adam_state(params)
+    cur = params
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        for it in range(3):
+            _, grads = P.backward(cur, x, t)  # oracle gradients, given to both sides
+            gvec = hpf_gpu.pack_params(grads)
+            net.adam_step(gvec, 1e-2)
+            cur, state = P.adam_step(cur, [tuple(np.asarray(a, np.float64) for a in gr)
+                                           for gr in hpf_gpu.unpack_params(gvec)],
+                                     state, lr=1e-2)
+        got = net.get_weights()
+    want = hpf_gpu.pack_params(cur)
+    assert np.max(np.abs(got - want)) < 2e-6
+
+
+def test_train_step_is_backward_then_adam(hpf_gpu):
+    params = hpf_gpu.pack_params(rand_params(11))
+    mesh = (13, 10, 5)
+    x = rand_phi(grid(mesh), 12).astype(np.float32)
+    nxt = rand_phi(grid(mesh), 13, c=2).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as a, hpf_gpu.Propagator(mesh) as b:
+        a.set_weights(params)
+        b.set_weights(params)
+        for _ in range(3):
+            la = a.train_step(x, nxt, 1e-3, want_loss=True)
+            lb, g = b.backward(x, nxt)
+            b.adam_step(g, 1e-3)
+            assert la == lb
+        assert np.array_equal(a.get_weights(), b.get_weights())
+
+
+def test_training_on_gpu_fits_a_teacher(hpf_gpu):
+    """A student trained by the GPU kernels learns the map of an oracle teacher network."""
+    mesh = (16, 16, 16)
+    teacher = rand_params(14)
+    xs = [rand_phi(grid(mesh), 20 + k) for k in range(4)]
+    nexts = [x[2:] + P.forward(teacher, x)[0] for x in xs]
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(P.init_params(15)))
+        x32 = [x.astype(np.float32) for x in xs]
+        n32 = [n.astype(np.float32) for n in nexts]
+        first = np.mean([net.backward(x, n)[0] for x, n in zip(x32, n32)])
+        for it in range(400):
+            net.train_step(x32[it % 4], n32[it % 4], 3e-3)
+        last = np.mean([net.backward(x, n)[0] for x, n in zip(x32, n32)])
+    assert last < 0.1 * first
+
+
+# ---------------------------------------------------------------- learned MD step
+
+def melt(hpf, n_chains=400, mesh=10, **over):
+    n = n_chains * 10
+    box = (n / 3.0) ** (1.0 / 3.0)
+    w = W.diblock(n_chains, 5, 5, box, mesh, 1.0, name="learned_melt")
+    pp = w.params()
+    pp.update(over)
+    data = W.generate(w)
+    return w, pp, data
+
+
+def system(hpf, pp, data, step=0):
+    s = hpf.System(hpf.make_params(**pp))
+    s.set_state(data["pos"], data["vel"], data["type"], data["bonds"], step)
+    return s
+
+
+def test_density_phi_is_the_scaled_mesh(hpf_gpu):
+    w, pp, data = melt(hpf_gpu)
+    s = system(hpf_gpu, pp, data)
+    D = s.scatter_density()
+    phi = s.density_phi()
+    h = [np.float64(np.float32(pp["box"][a])) / pp["mesh"][a] for a in range(3)]
+    phi_c = 2.0 ** -39 / (pp["rho0"] * (h[0] * h[1] * h[2]))
+    assert np.array_equal(phi, (D.astype(np.float64) * phi_c).astype(np.float32))
+    # mass conservation: every bead adds 1 / (rho0 h^3) in total
+    vol = h[0] * h[1] * h[2]
+    assert np.sum(phi, dtype=np.float64) * pp["rho0"] * vol == pytest.approx(w.n_beads, rel=1e-6)
+
+
+def test_judge_matches_oracle_forces(hpf_gpu, orc):
+    w, pp, data = melt(hpf_gpu)
+    s = system(hpf_gpu, pp, data)
+    phi = s.density_phi().astype(np.float64)
+    rng = np.random.default_rng(3)
+    cand = np.clip(phi + rng.normal(scale=0.1, size=phi.shape), 0.0, None).astype(np.float32)
+    eps = s.judge_density(cand)
+    assert s.judge_density(phi.astype(np.float32)) < 1e-5
+    # the oracle: field forces of the candidate mesh and of the true mesh
+    op = orc.make_params(**pp)
+    h = [np.float64(np.float32(pp["box"][a])) / pp["mesh"][a] for a in range(3)]
+    inv_phi_c = 1.0 / (2.0 ** -39 / (pp["rho0"] * (h[0] * h[1] * h[2])))
+    Dc = np.maximum(np.rint(cand.astype(np.float64) * inv_phi_c), 0).astype(np.int64)
+    Dt = orc.scatter(op, data["pos"], data["type"])
+    Fc = orc.field_force(op, data["pos"], data["type"], orc.field(op, Dc)[1])
+    Ft = orc.field_force(op, data["pos"], data["type"], orc.field(op, Dt)[1])
+    eo = np.linalg.norm(Fc - Ft) / np.linalg.norm(Ft)
+    assert eps == pytest.approx(eo, rel=1e-3)
+
+
+def test_zero_network_equals_field_every_k(hpf_gpu):
+    """Zero weights predict no change: after the first (plain) window every
+    learned window runs the frozen field of its start, i.e. field_every = K."""
+    K = 5
+    w, pp, data = melt(hpf_gpu, field_every=1)
+    a = system(hpf_gpu, pp, data)
+    with hpf_gpu.Propagator((10, 10, 10)) as net:
+        st = a.step_learned(net, 4, K=K, tol=1e9)
+    assert st["windows"] == 4 and st["plain"] == 1 and st["learned"] == 3
+    assert st["rejected"] == 0 and st["judged"] == 3
+    # reference: K plain steps at field_every = 1, then field_every = K
+    b = system(hpf_gpu, pp, data)
+    b.step(K)
+    pos, vel, step = b.get_state()
+    ppk = dict(pp, field_every=K)
+    c = system(hpf_gpu, ppk, {**data, "pos": pos, "vel": vel}, step)
+    c.step(3 * K)
+    pa, va, sa = a.get_state()
+    pc, vc, sc = c.get_state()
+    assert sa == sc == 4 * K
+    assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+
+
+def test_zero_tolerance_equals_plain(hpf_gpu):
+    """tol = 0 rejects every prediction: the run is field_every = 1 exactly."""
+    K = 4
+    w, pp, data = melt(hpf_gpu, field_every=1, sort_every=7)
+    a = system(hpf_gpu, pp, data)
+    with hpf_gpu.Propagator((10, 10, 10)) as net:
+        net.set_weights(hpf_gpu.pack_params(P.init_params(2)))
+        # window 1 builds history; window 2 is learned, rejected and re-run
+        # plain; windows 3-5 run plain with their predictions judged aside
+        st = a.step_learned(net, 5, K=K, tol=0.0)
+        assert (st["plain"], st["rejected"], st["learned"], st["judged"]) == (4, 1, 0, 4)
+        # a shadow judgement that passes switches back to learned windows ...
+        st = a.step_learned(net, 1, K=K, tol=1e9)
+        assert (st["plain"], st["judged"]) == (1, 1)
+        # ... which a zero tolerance rejects again
+        st = a.step_learned(net, 2, K=K, tol=0.0)
+        assert (st["rejected"], st["plain"], st["learned"]) == (1, 1, 0)
+    b = system(hpf_gpu, pp, data)
+    b.step(8 * K)
+    pa, va, sa = a.get_state()
+    pb, vb, sb = b.get_state()
+    assert sa == sb == 8 * K
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+
+
+def test_learned_window_judges_its_prediction(hpf_gpu):
+    """The eps a learned window reports is the judge's error of D(t) + dphi
+    against the true density at t + K (recomputed here through the ABI)."""
+    K = 5
+    w, pp, data = melt(hpf_gpu, field_every=1)
+    a = system(hpf_gpu, pp, data)
+    params = hpf_gpu.pack_params([(W * 0.3, b) for W, b in P.init_params(4)])
+    with hpf_gpu.Propagator((10, 10, 10)) as net:
+        net.set_weights(params)
+        phi0 = a.density_phi()
+        st = a.step_learned(net, 1, K=K, tol=1e9)       # plain window: history phi(0)
+        assert st["plain"] == 1
+        phiK = a.density_phi()
+        dphi = net.forward(np.concatenate([phi0, phiK]))
+        st = a.step_learned(net, 1, K=K, tol=1e9)       # learned window K .. 2K
+        assert st["learned"] == 1
+        eps = a.judge_density(phiK + dphi)
+    # D(K) + dphi in the fixed point and phi(K) + dphi in FP32 differ by rounding only
+    assert st["eps_last"] == pytest.approx(eps, rel=1e-3)
+    assert 0.0 < eps < 10.0
