@@ -404,12 +404,150 @@ def run_batch(args):
     return 0
 
 
+def run_learned(args):
+    """The 1M-bead A10B10 melt with the learned density propagator (K = 20).
+
+    Untimed set-up: 1000 steps of the plain form, 200 phi snapshots every K
+    steps of a plain run refreshing the field every step, 2000 Adam steps of
+    the network on them (the GPU kernels).  Then the judge's field-force
+    error of hold-last, linear extrapolation and the network, and the timed
+    forms: learned at tol 1e-3 (the value), plain with the field refreshed
+    every step (the plain form that meets 1e-3), learned with every window
+    accepted, and plain at the largest field_every whose frozen-field error
+    does not exceed the network's."""
+    import numpy as np
+    import torch
+    from paper_1310_2041_gb300 import hpf, learned, workloads as W
+
+    torch.cuda.set_device(0)
+    K = 20
+    w = W.a10b10_1m()
+    data = W.generate(w)
+    pp = w.params()
+    pp["sort_every"] = args.sort_every
+    stream = torch.cuda.current_stream()
+    dev = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
+
+    def system(fe, pos, vel, step):
+        s = hpf.System(hpf.make_params(**dict(pp, field_every=fe)), stream=stream)
+        s.set_state(pos, vel, dev["type"], dev["bonds"], step)
+        return s
+
+    s = system(w.field_every, dev["pos"], dev["vel"], 0)
+    s.step(1000)
+    pos, vel, step = s.get_state()
+    s.close()
+    s = system(1, pos, vel, step)
+    snaps = learned.collect_snapshots(s, 200, K)
+    ex = learned.triples(200)
+    train_ex, val_ex = ex[:178], ex[178:]
+    net = hpf.Propagator(pp["mesh"], stream=stream)
+    net.set_weights(learned.init_params(0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    log = learned.train(net, snaps, 2000, lr=2e-3, lr_final=2e-4, examples=train_ex,
+                        log_every=500)
+    torch.cuda.synchronize()
+    train_ms = (time.perf_counter() - t0) * 1e3 / 2000
+    val_net, val_zero = learned.validation_loss(net, snaps, val_ex)
+    # inference time (the 4-channel input already on the device)
+    x = snaps[100:102].contiguous()
+    y = torch.empty_like(snaps[0])
+    for _ in range(3):
+        net.forward(x, out=y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(20):
+        net.forward(x, out=y)
+    b.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b) / 20
+    flops = 2.0 * w.mesh ** 3 * 27 * sum(ci * co for ci, co in ((4, 16), (16, 16), (16, 2)))
+    # the judge's error of the candidates along the continued plain run
+    lags = (1, 2, 5, 10, 15, 20)
+    res = learned.judge_candidates(s, net, 10, K, lags=lags)
+    eps = {k: float(np.mean(v)) for k, v in res.items() if v}
+    pos, vel, step = s.get_state()
+    s.close()
+    fe_equal = max([L for L in lags if eps[f"hold_{L}"] <= eps["net"]] or [1])
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    n_win = max(1, (args.steps + K - 1) // K)
+    warm_win = max(1, (args.warmup + K - 1) // K)
+
+    def timed_windows(run):
+        ms, agg = 0.0, None
+        for _ in range(n_win):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            if isinstance(r, dict):
+                if agg is None:
+                    agg = dict(r)
+                else:
+                    for k, v in r.items():
+                        agg[k] = (max(agg[k], v) if k == "eps_max" else
+                                  v if k == "eps_last" else agg[k] + v)
+        return ms, agg
+
+    forms = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for name, tol in (("learned_tol_1e-3", 1e-3), ("learned_all_accepted", float("inf"))):
+        s = system(1, pos, vel, step)
+        s.step_learned(net, warm_win, K=K, tol=tol)
+        ms, st = timed_windows(lambda: s.step_learned(net, 1, K=K, tol=tol))
+        forms[name] = {"value": w.n_beads * n_win * K / (ms * 1e-3), "stats": st}
+        s.close()
+    for name, fe in (("plain_fe1", 1), (f"plain_fe{fe_equal}", fe_equal), ("plain_fe10", 10)):
+        s = system(fe, pos, vel, step)
+        s.step(warm_win * K)
+        ms, _ = timed_windows(lambda: s.step(K))
+        forms[name] = {"value": w.n_beads * n_win * K / (ms * 1e-3)}
+        s.close()
+    clk = clocks.stop()
+    value = forms["learned_tol_1e-3"]["value"]
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        peak_src = "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 1900.0, "fallback"
+    achieved = flops / (infer_ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": n_win * K, "warmup": warm_win * K,
+            "ms_per_step": 1e3 * w.n_beads / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (network bf16/fp32-acc)", "data": "synthetic",
+            "config": {"workload": "a10b10_1m_learned", "n_beads": w.n_beads, "mesh": w.mesh,
+                       "K": K, "tol": 1e-3, "snapshots": 200, "train_iters": 2000,
+                       "l2": "flushed (256 MB write) before each timed window",
+                       "forms": forms, "eps_mean": eps, "fe_equal_eps": fe_equal,
+                       "val_mse": {"net": val_net, "no_change": val_zero},
+                       "train_ms_per_iter": train_ms, "train_log": log,
+                       "infer_ms": infer_ms},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "kernel": "k_conv (whole forward)",
+                         "algo_flops_per_inference": flops},
+            "cpu_baseline": None, "e2e": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "replicas64":
         return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -13,6 +13,21 @@ import numpy as np
 from . import hpf
 
 
+CHANNELS = ((4, 16), (16, 16), (16, 2))
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Seeded He-uniform initial weights (bound sqrt(6 / fan_in), fan_in = 27 C_in;
+    the last layer scaled by 0.1, biases zero) as the flat FP32 parameter vector."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (ci, co) in enumerate(CHANNELS):
+        bound = np.sqrt(6.0 / (27 * ci)) * (0.1 if k == len(CHANNELS) - 1 else 1.0)
+        parts.append(rng.uniform(-bound, bound, size=27 * ci * co))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def collect_snapshots(system: hpf.System, n_snap: int, K: int, out=None):
     """phi of the current positions, then K steps, n_snap times.
 
@@ -77,7 +92,7 @@ def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows:
     K): phi(t) + net(phi(t - K), phi(t)) judged at t + K.  Returns
     {name: [eps per judged point]}."""
     import torch
-    H = max(max(lags), 2 * K)
+    H = 2 * max(max(lags), K)
     hist = torch.empty((H + 1,) + system.mesh_shape, dtype=torch.float32, device="cuda")
     res = {f"hold_{L}": [] for L in lags}
     res.update({f"linear_{L}": [] for L in lags})

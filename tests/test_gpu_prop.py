@@ -272,3 +272,33 @@ def test_learned_window_judges_its_prediction(hpf_gpu):
     # D(K) + dphi in the fixed point and phi(K) + dphi in FP32 differ by rounding only
     assert st["eps_last"] == pytest.approx(eps, rel=1e-3)
     assert 0.0 < eps < 10.0
+
+
+def test_trained_network_beats_holding_the_last_density(hpf_gpu):
+    """What the network gains over the method without it (holding the density
+    of the last true update, i.e. a frozen field between updates): trained on
+    the GPU on snapshots of a plain run, it predicts held-out density changes
+    with a smaller error than predicting no change, and its field-force error
+    at t + K is below the frozen field's on a continuation of the run."""
+    import torch
+    from paper_1310_2041_gb300 import learned
+    K = 20
+    n_chains = 10000  # 200,000 beads at rho0 = 3
+    box = (20.0 * n_chains / 3.0) ** (1.0 / 3.0)
+    w = W.diblock(n_chains, 10, 10, box, 40, 0.5, name="a10b10_200k")
+    pp = dict(w.params(), field_every=1, sort_every=1000)
+    data = W.generate(w)
+    s = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    s.set_state(data["pos"], data["vel"], data["type"], data["bonds"])
+    s.step(1000)
+    snaps = learned.collect_snapshots(s, 120, K)
+    ex = learned.triples(120)
+    with hpf_gpu.Propagator((40, 40, 40)) as net:
+        net.set_weights(learned.init_params(0))
+        learned.train(net, snaps, 1500, lr=2e-3, lr_final=2e-4, examples=ex[:100])
+        val_net, val_zero = learned.validation_loss(net, snaps, ex[100:])
+        res = learned.judge_candidates(s, net, 8, K, lags=(K,))
+    assert val_net < 0.9 * val_zero
+    assert np.mean(res["net"]) < 0.95 * np.mean(res["hold_net"])
+    assert np.allclose(res["hold_net"], res[f"hold_{K}"][-len(res["hold_net"]):])
+    del torch
