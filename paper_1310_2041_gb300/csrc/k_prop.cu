@@ -23,10 +23,11 @@
 namespace hpf {
 
 constexpr int kPC = 16;                      // padded channels
-constexpr int kTX = 8, kTY = 8, kTZ = 2;     // output tile
+constexpr int kTX = 8, kTY = 8, kTZ = 8;     // output tile: one z-plane of 64 voxels per warp
 constexpr int kBX = kTX + 2, kBY = kTY + 2, kBZ = kTZ + 2;
-constexpr int kBoxVox = kBX * kBY * kBZ;     // 400
-constexpr int kTileVox = kTX * kTY * kTZ;    // 128
+constexpr int kBoxVox = kBX * kBY * kBZ;     // 1000 (32 000 bytes)
+constexpr int kTileVox = kTX * kTY * kTZ;    // 512
+constexpr int kMTiles = kTileVox / 16 / 8;   // 16-voxel MMA row tiles per warp (4)
 constexpr int kOffsets = 27;
 // channels of the three layers: 4 -> 16 -> 16 -> 2
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? 4 : 16; }
@@ -60,6 +61,14 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
                  : "r"(addr));
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
                                          uint32_t a3, uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -80,22 +89,24 @@ __device__ __forceinline__ void tile_origin(const PropGeom& g, int t, int& x0, i
 // ldmatrix phase reads (always eight consecutive rows here) hit distinct banks.
 __device__ __forceinline__ int swz(int row, int half) { return 2 * row + (half ^ ((row >> 2) & 1)); }
 
-// Periodic input box of a tile (all 16 channels), 16-byte vectors.
+// Periodic input box of a tile (all 16 channels), 16-byte asynchronous copies.
 __device__ __forceinline__ void load_box(const __nv_bfloat16* __restrict__ in, const PropGeom& g,
                                          int x0, int y0, int z0, uint4* box) {
+    const uint32_t box_s = saddr(box);
     for (int e = threadIdx.x; e < kBoxVox * 2; e += blockDim.x) {
         const int v = e >> 1, half = e & 1;
         const int bx = v % kBX, by = (v / kBX) % kBY, bz = v / (kBX * kBY);
         const int gx = pwrap(x0 - 1 + bx, g.mx), gy = pwrap(y0 - 1 + by, g.my),
                   gz = pwrap(z0 - 1 + bz, g.mz);
         const size_t gv = ((size_t)gz * g.my + gy) * g.mx + gx;
-        box[swz(v, half)] = __ldg(reinterpret_cast<const uint4*>(in + gv * kPC) + half);
+        cp_async16(box_s + 16 * swz(v, half), in + gv * kPC + 8 * half);
     }
 }
 
-// Voxel r (0..15) of warp w inside the tile: (lx, ly, lz).
-__device__ __forceinline__ void warp_voxel(int w, int r, int& lx, int& ly, int& lz) {
-    const int m = 16 * w + r;
+// Voxel r (0..15) of 16-voxel row tile mt (0..31) of the tile: (lx, ly, lz);
+// row tiles 4w .. 4w + 3 are the z-plane lz = w.
+__device__ __forceinline__ void warp_voxel(int mt, int r, int& lx, int& ly, int& lz) {
+    const int m = 16 * mt + r;
     lx = m % kTX;
     ly = (m / kTX) % kTY;
     lz = m / (kTX * kTY);
@@ -112,10 +123,12 @@ __device__ __forceinline__ int box_row(int lx, int ly, int lz, int o) {
 enum ConvMode { kHidden = 0, kLast = 1, kData = 2 };
 
 // out(n)[co] = sum_offsets sum_ci W[o][co][ci] in(n + d_o)[ci]  (+ bias, SiLU).
-// Persistent CTAs: the weights are staged once, then tiles are taken
-// grid-stride.  kHidden stores the FP32 pre-activation (when z_out is given)
-// and the BF16 SiLU output; kLast and kData store FP32.
-template <int kMode>
+// One CTA per 8 x 8 x 8 tile; warp w computes the 64 voxels of z-plane w as
+// four 16-row MMA tiles against each offset's weight fragment (loaded once
+// per offset and warp).  kN output n-tiles of 8 channels (1 for the
+// two-channel last layer).  kHidden stores the FP32 pre-activation (when
+// z_out is given) and the BF16 SiLU output; kLast and kData store FP32.
+template <int kMode, int kN>
 __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ in,
                                               const __nv_bfloat16* __restrict__ W,
                                               const float* __restrict__ bias,
@@ -125,52 +138,66 @@ __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ 
     __shared__ uint4 box[kBoxVox * 2];
     __shared__ uint4 sw[kOffsets * kPC * 2];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t box_s = saddr(box), sw_s = saddr(sw);
     for (int e = tid; e < kOffsets * kPC * 2; e += blockDim.x)
-        sw[swz(e >> 1, e & 1)] = __ldg(reinterpret_cast<const uint4*>(W) + e);
-    // A rows: lane -> voxel (lane % 16), channel half (lane / 16)
-    int lx, ly, lz;
-    warp_voxel(w, lane & 15, lx, ly, lz);
-    const int ch_half = lane >> 4;
+        cp_async16(sw_s + 16 * swz(e >> 1, e & 1), reinterpret_cast<const uint4*>(W) + e);
+    int x0, y0, z0;
+    tile_origin(g, blockIdx.x, x0, y0, z0);
+    load_box(in, g, x0, y0, z0, box);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // A rows: lane -> voxel (lane % 16) of each row tile, channel half (lane / 16)
+    const int r = lane & 15, ch_half = lane >> 4;
     // B rows: lane -> output channel (lane & 7) + 8 (lane >= 16), input half ((lane >> 3) & 1)
     const int b_n = (lane & 7) + ((lane >> 4) << 3), b_half = (lane >> 3) & 1;
-    const uint32_t box_s = saddr(box), sw_s = saddr(sw);
     const int gq = lane >> 2, q = lane & 3;
-    float b_lo[2] = {0.f, 0.f}, b_hi[2] = {0.f, 0.f};
-    if (kMode != kData) {
-        b_lo[0] = bias[2 * q];
-        b_hi[0] = bias[2 * q + 1];
-        b_lo[1] = bias[8 + 2 * q];
-        b_hi[1] = bias[8 + 2 * q + 1];
-    }
-    for (int t = blockIdx.x; t < g.tiles; t += gridDim.x) {
-        int x0, y0, z0;
-        tile_origin(g, t, x0, y0, z0);
-        __syncthreads();
-        load_box(in, g, x0, y0, z0, box);
-        __syncthreads();
-        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll 3
-        for (int o = 0; o < kOffsets; ++o) {
-            uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
-            ldsm_x4(box_s + 16 * swz(box_row(lx, ly, lz, o), ch_half), a0, a1, a2, a3);
-            ldsm_x4(sw_s + 16 * swz(o * kPC + b_n, b_half), b0, b1, b2, b3);
-            mma_bf16(acc[0], a0, a1, a2, a3, b0, b1);
-            mma_bf16(acc[1], a0, a1, a2, a3, b2, b3);
+    float acc[kMTiles][kN][4];
+#pragma unroll
+    for (int i = 0; i < kMTiles; ++i)
+#pragma unroll
+        for (int j = 0; j < kN; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+    // voxel (lx, ly0 + 2i, w) for row tile i
+    const int lx = r % kTX, ly0 = r / kTX;
+#pragma unroll 1
+    for (int o = 0; o < kOffsets; ++o) {
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4(sw_s + 16 * swz(o * kPC + b_n, b_half), b0, b1, b2, b3);
+        const int row0 = box_row(lx, ly0, w, o);
+#pragma unroll
+        for (int i = 0; i < kMTiles; ++i) {
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(box_s + 16 * swz(row0 + 2 * i * kBX, ch_half), a0, a1, a2, a3);
+            mma_bf16(acc[i][0], a0, a1, a2, a3, b0, b1);
+            if (kN > 1) mma_bf16(acc[i][kN - 1], a0, a1, a2, a3, b2, b3);
         }
-        // epilogue: lane holds voxels gq, gq + 8 and channels 8j + 2q, + 1
+    }
+    float b_lo[kN], b_hi[kN];
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+        b_lo[j] = kMode != kData ? bias[8 * j + 2 * q] : 0.f;
+        b_hi[j] = kMode != kData ? bias[8 * j + 2 * q + 1] : 0.f;
+    }
+    // epilogue: lane holds voxels gq, gq + 8 of each row tile and channels 8j + 2q, + 1
+#pragma unroll
+    for (int i = 0; i < kMTiles; ++i)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             int vx, vy, vz;
-            warp_voxel(w, gq + 8 * half, vx, vy, vz);
+            warp_voxel(kMTiles * w + i, gq + 8 * half, vx, vy, vz);
             const int X = x0 + vx, Y = y0 + vy, Z = z0 + vz;
             if (X >= g.mx || Y >= g.my || Z >= g.mz) continue;
             const size_t gv = ((size_t)Z * g.my + Y) * g.mx + X;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < kN; ++j) {
                 const int ch = 8 * j + 2 * q;
-                const float v0 = acc[j][2 * half] + b_lo[j], v1 = acc[j][2 * half + 1] + b_hi[j];
+                const float v0 = acc[i][j][2 * half] + b_lo[j];
+                const float v1 = acc[i][j][2 * half + 1] + b_hi[j];
                 if (kMode == kHidden) {
-                    if (z_out) *reinterpret_cast<float2*>(z_out + gv * kPC + ch) = make_float2(v0, v1);
+                    if (z_out)
+                        *reinterpret_cast<float2*>(z_out + gv * kPC + ch) = make_float2(v0, v1);
                     const float s0 = v0 / (1.0f + expf(-v0)), s1 = v1 / (1.0f + expf(-v1));
                     *reinterpret_cast<__nv_bfloat162*>(act_out + gv * kPC + ch) =
                         __floats2bfloat162_rn(s0, s1);
@@ -179,7 +206,6 @@ __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ 
                 }
             }
         }
-    }
 }
 
 // dW[o][ci][co] = sum_n in(n + d_o)[ci] gz(n)[co]: a voxel reduction on the
@@ -218,18 +244,19 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
         for (int e = tid; e < kTileVox * 2; e += blockDim.x) {
             const int m = e >> 1, half = e & 1;
             const int X = x0 + m % kTX, Y = y0 + (m / kTX) % kTY, Z = z0 + m / (kTX * kTY);
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);  // voxels outside the mesh add nothing
             if (X < g.mx && Y < g.my && Z < g.mz)
-                v = __ldg(reinterpret_cast<const uint4*>(
-                              gz + (((size_t)Z * g.my + Y) * g.mx + X) * kPC) + half);
-            gt[swz(m, half)] = v;
+                cp_async16(gt_s + 16 * swz(m, half),
+                           gz + (((size_t)Z * g.my + Y) * g.mx + X) * kPC + 8 * half);
+            else
+                gt[swz(m, half)] = make_uint4(0u, 0u, 0u, 0u);  // outside the mesh: adds nothing
         }
+        cp_async_wait_all();
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int o = w + 8 * s;
             if (o >= kOffsets) break;
-#pragma unroll 2
+#pragma unroll 4
             for (int ks = 0; ks < kTileVox / 16; ++ks) {  // 16 voxels per k-step
                 int lx, ly, lz;
                 warp_voxel(ks, r_vox, lx, ly, lz);
@@ -518,7 +545,7 @@ struct hpf_prop {
     float* yout = nullptr;        // planar output [2][V]
     double* loss = nullptr;
     double* h_loss = nullptr;
-    int grid_conv = 0, grid_wgrad = 0;
+    int grid_wgrad = 0;
 };
 
 namespace {
@@ -543,14 +570,15 @@ void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s) {
     const int V = p->g.V, tb = (V + 255) / 256;
     const size_t wl = (size_t)kOffsets * kPC * kPC;
     k_pack_input<<<tb, 256, 0, s>>>(x, V, p->act[0]);
-    k_conv<kHidden><<<p->grid_conv, 256, 0, s>>>(p->act[0], p->wf, p->bias,
-                                                  keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
-                                                  p->g);
-    k_conv<kHidden><<<p->grid_conv, 256, 0, s>>>(p->act[1], p->wf + wl, p->bias + kPC,
-                                                  keep_z ? p->z[1] : nullptr, p->act[2], nullptr,
-                                                  p->g);
-    k_conv<kLast><<<p->grid_conv, 256, 0, s>>>(p->act[2], p->wf + 2 * wl, p->bias + 2 * kPC,
-                                                nullptr, nullptr, p->fbuf, p->g);
+    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[0], p->wf, p->bias,
+                                                   keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
+                                                   p->g);
+    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[1], p->wf + wl, p->bias + kPC,
+                                                   keep_z ? p->z[1] : nullptr, p->act[2], nullptr,
+                                                   p->g);
+    // two output channels: one n-tile (channels 8..15 of fbuf are not written)
+    k_conv<kLast, 1><<<p->g.tiles, 256, 0, s>>>(p->act[2], p->wf + 2 * wl, p->bias + 2 * kPC,
+                                                 nullptr, nullptr, p->fbuf, p->g);
 }
 
 // Loss and packed gradients (p->grads, p->loss) after prop_forward(keep_z) of
@@ -572,8 +600,8 @@ void prop_backward(hpf_prop* p, const float* x, const float* phi_next) {
         k_sum_partials<float><<<1, 32, 0, s>>>(p->bpart, kBiasBlocks, kPC, p->db + layer * kPC);
         if (layer == 0) break;
         // the data gradient of the layer input, then through the SiLU below it
-        k_conv<kData><<<p->grid_conv, 256, 0, s>>>(gbuf, p->wb + layer * wl, nullptr, nullptr,
-                                                    nullptr, p->fbuf, p->g);
+        k_conv<kData, 2><<<p->g.tiles, 256, 0, s>>>(gbuf, p->wb + layer * wl, nullptr, nullptr,
+                                                     nullptr, p->fbuf, p->g);
         k_silu_backward<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(p->fbuf, p->z[layer - 1], nv,
                                                                       gbuf);
     }
@@ -660,7 +688,6 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
     if (sms < 1) sms = 1;
-    p->grid_conv = g.tiles < 6 * sms ? g.tiles : 6 * sms;
     p->grid_wgrad = g.tiles < 2 * sms ? g.tiles : 2 * sms;
     const size_t wl = (size_t)kOffsets * kPC * kPC, Vs = (size_t)g.V;
     cudaError_t e = cudaSuccess;
