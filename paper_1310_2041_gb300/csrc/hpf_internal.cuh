@@ -203,27 +203,18 @@ __device__ __forceinline__ float open_uniform(uint32_t r) {
     return __uint2float_rn(2u * (r >> 9) + 1u) * 5.9604644775390625e-8f;
 }
 
-// ln x for x in [2^-24, 1), by the textbook reduction x = 2^e m, m in
-// [sqrt(1/2), sqrt(2)), and ln m = 2 atanh(t), t = (m - 1) / (m + 1), with the
-// odd series t + t^3/3 + ... + t^9/9 (|t| <= 0.1716: truncation below 1e-9
-// relative).  m - 1 is exact, so the relative accuracy holds as x -> 1, where
-// -ln x is the squared Box-Muller radius and a purely absolute error bound
-// would not do.
-__device__ __forceinline__ float log_unit(float x) {
-    const int bits = __float_as_int(x);
-    int e = (bits >> 23) - 127;
-    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
-    if (m > 1.41421356f) {
-        m *= 0.5f;
-        e += 1;
-    }
-    const float t = __fdividef(m - 1.0f, m + 1.0f);
-    const float t2 = t * t;
-    float p = fmaf(t2, 2.0f / 9.0f, 2.0f / 7.0f);
-    p = fmaf(p, t2, 2.0f / 5.0f);
-    p = fmaf(p, t2, 2.0f / 3.0f);
-    p = fmaf(p, t2, 2.0f);
-    return fmaf((float)e, 0.693147180559945f, t * p);
+// ln u for a uniform u in (0, 1), with the relative accuracy that the
+// Box-Muller radius sqrt(-2 ln u) needs as u -> 1.  With d = 1 - u (exact in
+// FP32 for u >= 1/2): for d <= 2^-6, ln(1 - d) = -d (1 + d/2 + d^2/3) up to a
+// relative d^3/4 <= 2^-20; otherwise the hardware logarithm (__logf: absolute
+// error below 2^-21.4 on [1/2, 1), a few ulp below 1/2), which is below
+// 2.3e-5 relative there since |ln u| >= 0.0157.  Branch-free (both forms are
+// evaluated and one is selected).
+__device__ __forceinline__ float log_unit(float u) {
+    const float d = 1.0f - u;
+    const float series = -d * fmaf(fmaf(d, 1.0f / 3.0f, 0.5f), d, 1.0f);
+    const float hw = __logf(u);
+    return d <= 0.015625f ? series : hw;
 }
 
 // Three standard normals of bead `tag` at step `step` (Box-Muller):
