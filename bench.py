@@ -37,7 +37,9 @@ UNIT = "bead-steps/s"
 # refresh every 10 steps): 50 B per bead-step.
 ALGO_BYTES_PER_BEAD_STEP = 50.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-STEP_SRC = os.path.join(ROOT, "paper_1310_2041_gb300", "csrc", "k_step.cu")
+# the step kernel's sources: its file and the device helpers it inlines
+STEP_SRC = [os.path.join(ROOT, "paper_1310_2041_gb300", "csrc", f)
+            for f in ("k_step.cu", "hpf_internal.cuh")]
 
 
 def parse():
@@ -120,8 +122,10 @@ def traffic_record():
         rec = json.load(open(TRAFFIC_FILE))["k_step"]
     except (OSError, KeyError, ValueError):
         return None
-    sha = hashlib.sha256(open(STEP_SRC, "rb").read()).hexdigest()
-    return rec if rec.get("source_sha256") == sha else None
+    h = hashlib.sha256()
+    for f in STEP_SRC:
+        h.update(open(f, "rb").read())
+    return rec if rec.get("source_sha256") == h.hexdigest() else None
 
 
 def cpu_oracle_rate(w, data, budget_s: float):

@@ -67,10 +67,9 @@ constexpr int kCachePlanes = 6;
 constexpr size_t kStepSmem = sizeof(float4) * kCachePlanes * kStepBlock +
                              sizeof(float) * 3 * 2 * kStepBlock;
 
-__device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
-                                                float flx, float fly, float flz,
-                                                float4* __restrict__ cache, int t,
-                                                int stride = kStepBlock) {
+// Ghosted-array index of the lower corner of cell (flx, fly, flz) (periodic
+// image; see axis_gather for why no fix-up is needed).
+__device__ __forceinline__ int cell_base(const MeshGeom& g, float flx, float fly, float flz) {
     const float fmx = (float)g.mx, fmy = (float)g.my, fmz = (float)g.mz;
     float wx = __fmaf_rn(-fmx, floorf((flx + 0.5f) * g.inv_m[0]), flx);
     float wy = __fmaf_rn(-fmy, floorf((fly + 0.5f) * g.inv_m[1]), fly);
@@ -78,7 +77,14 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
     wx = fminf(fmaxf(wx, 0.0f), fmx - 1.0f);
     wy = fminf(fmaxf(wy, 0.0f), fmy - 1.0f);
     wz = fminf(fmaxf(wz, 0.0f), fmz - 1.0f);
-    const int o00 = (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
+    return (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
+}
+
+__device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
+                                                float flx, float fly, float flz,
+                                                float4* __restrict__ cache, int t,
+                                                int stride = kStepBlock) {
+    const int o00 = cell_base(g, flx, fly, flz);
     const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
     // corner (a, b, c) = offsets (x, y, z) in {0, 1}
     const float4 g000 = __ldg(Gt + o00), g100 = __ldg(Gt + o00 + 1);
@@ -276,12 +282,11 @@ struct Bead {
     float cfx, cfy, cfz;  // cached cell (floor of the mesh coordinate), NaN: none
 };
 
-template <bool kNoise>
-__device__ __forceinline__ void advance_bead(Bead& b, float px, float py, float pz, bool has_p,
-                                             float qx, float qy, float qz, bool has_q,
-                                             const float4* __restrict__ G, const MeshGeom& g,
-                                             const StepConsts& c, long long step,
-                                             float4* __restrict__ cache, int slot) {
+// The bead's cell: refill its cache of the cell polynomial when the bead
+// has entered another cell; returns the offsets inside the cell.
+__device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G, const MeshGeom& g,
+                                           float4* __restrict__ cache, int slot, float& f0,
+                                           float& f1, float& f2) {
     const float s0 = __fmul_rn(b.x, g.inv_h[0]), s1 = __fmul_rn(b.y, g.inv_h[1]),
                 s2 = __fmul_rn(b.z, g.inv_h[2]);
     const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
@@ -292,18 +297,29 @@ __device__ __forceinline__ void advance_bead(Bead& b, float px, float py, float 
         b.cfy = fly;
         b.cfz = flz;
     }
+    f0 = __fsub_rn(s0, flx);
+    f1 = __fsub_rn(s1, fly);
+    f2 = __fsub_rn(s2, flz);
+}
+
+// Kick of one bead: field (cached cell polynomial at offsets f), friction,
+// noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
+// chain neighbours.
+template <bool kNoise>
+__device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
+                                          float ny, float nz, float bx, float by, float bz,
+                                          const StepConsts& c, const float4* __restrict__ cache,
+                                          int slot) {
     float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
-    eval_cell_cache(cache, slot, __fsub_rn(s0, flx), __fsub_rn(s1, fly), __fsub_rn(s2, flz), fx,
-                    fy, fz, 2 * kWarpBlock);
+    eval_cell_cache(cache, slot, f0, f1, f2, fx, fy, fz, 2 * kWarpBlock);
     if (kNoise) {
-        float nx, ny, nz;
-        gauss3(c, b.m & kTagMask, step, nx, ny, nz);
         fx = fmaf(c.sigma, nx, fx);
         fy = fmaf(c.sigma, ny, fy);
         fz = fmaf(c.sigma, nz, fz);
     }
-    bond_force(b.x - px, b.y - py, b.z - pz, has_p ? c.two_k : 0.0f, c.r0, fx, fy, fz);
-    bond_force(b.x - qx, b.y - qy, b.z - qz, has_q ? c.two_k : 0.0f, c.r0, fx, fy, fz);
+    fx += bx;
+    fy += by;
+    fz += bz;
     b.vx = fmaf(c.dt_m, fx, b.vx);
     b.vy = fmaf(c.dt_m, fy, b.vy);
     b.vz = fmaf(c.dt_m, fz, b.vz);
@@ -361,20 +377,34 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
     }
     // whole chains: every flagged neighbour is inside the segment
     const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
-    const bool p1 = (b1.m & kBondPrev) != 0, n1 = (b1.m & kBondNext) != 0;
+    const bool n1 = (b1.m & kBondNext) != 0;  // b1's previous bond is b0's next
     for (int k = 0; k < n_sub; ++k) {
-        // bead 2l - 1 (previous lane's second bead) and bead 2l + 2 (next lane's first)
-        const float ux = __shfl_up_sync(0xffffffffu, b1.x, 1);
-        const float uy = __shfl_up_sync(0xffffffffu, b1.y, 1);
-        const float uz = __shfl_up_sync(0xffffffffu, b1.z, 1);
+        // every bond is evaluated once: bond (2l, 2l + 1) inside the lane, bond
+        // (2l + 1, 2l + 2) with the next lane's first bead, whose share (the
+        // opposite force) goes back up one lane
         const float dx = __shfl_down_sync(0xffffffffu, b0.x, 1);
         const float dy = __shfl_down_sync(0xffffffffu, b0.y, 1);
         const float dz = __shfl_down_sync(0xffffffffu, b0.z, 1);
-        const float x0 = b0.x, y0 = b0.y, z0 = b0.z;
-        advance_bead<kNoise>(b0, ux, uy, uz, p0, b1.x, b1.y, b1.z, n0, G, g, c, step0 + k, wcache,
-                             tid);
-        advance_bead<kNoise>(b1, x0, y0, z0, p1, dx, dy, dz, n1, G, g, c, step0 + k, wcache,
-                             kWarpBlock + tid);
+        float ax = 0.f, ay = 0.f, az = 0.f;  // on bead 2l from bead 2l + 1
+        bond_force(b0.x - b1.x, b0.y - b1.y, b0.z - b1.z, n0 ? c.two_k : 0.0f, c.r0, ax, ay, az);
+        float nx = 0.f, ny = 0.f, nz = 0.f;  // on bead 2l + 1 from bead 2l + 2
+        bond_force(b1.x - dx, b1.y - dy, b1.z - dz, n1 ? c.two_k : 0.0f, c.r0, nx, ny, nz);
+        const float ux = __shfl_up_sync(0xffffffffu, nx, 1);  // previous lane's share
+        const float uy = __shfl_up_sync(0xffffffffu, ny, 1);
+        const float uz = __shfl_up_sync(0xffffffffu, nz, 1);
+        // the two beads' phases side by side, so their independent work interleaves
+        float f00, f01, f02, f10, f11, f12;
+        cell_check(b0, G, g, wcache, tid, f00, f01, f02);
+        cell_check(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
+        float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
+        if (kNoise) {
+            gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
+            gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
+        }
+        kick_bead<kNoise>(b0, f00, f01, f02, g0x, g0y, g0z, p0 ? ax - ux : ax,
+                          p0 ? ay - uy : ay, p0 ? az - uz : az, c, wcache, tid);
+        kick_bead<kNoise>(b1, f10, f11, f12, g1x, g1y, g1z, nx - ax, ny - ay, nz - az, c, wcache,
+                          kWarpBlock + tid);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
         b0.z = fmaf(c.dt, b0.vz, b0.z);
