@@ -519,9 +519,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;  // valid in thread 0
 }
 
+// |d| in FP64 from an FP32 reciprocal-square-root seed and one Newton step
+// y <- y (3 - r2 y^2) / 2 (relative error ~1.5 e0^2 ~ 3e-14 for the FP32
+// seed's e0 ~ 1.4e-7); r2 = 0 gives 0.
+__device__ __forceinline__ double norm_fp64(double r2) {
+    if (!(r2 > 0.0)) return 0.0;
+    double y = (double)rsqrtf((float)r2);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    return r2 * y;
+}
+
 // Per bead: F_n exactly as the step kernel forms it, v_n = v + dt/(2m) F_n in
 // FP64, then kinetic energy, momentum and the bond energy of the bond to the
-// next bead (each bond once).
+// next bead (each bond once).  Each thread accumulates a grid-stride share of
+// the beads in FP64 before the block sums (the FP64 rate of this GPU is low,
+// so the reductions are amortised over many beads).
 __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                                                             const uint32_t* __restrict__ meta,
                                                             int n, MeshGeom g,
@@ -530,9 +542,8 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                                                             EnergyConsts e,
                                                             double* __restrict__ partials) {
     __shared__ double sh[kRedBlock / 32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double ke = 0.0, ub = 0.0, px = 0.0, py = 0.0, pz = 0.0;
-    if (i < n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float x = st.x[i], y = st.y[i], z = st.z[i];
         const float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
         const uint32_t m = meta[i];
@@ -543,8 +554,8 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
             const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
             bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
             const double dx = (double)x - xj, dy = (double)y - yj, dz = (double)z - zj;
-            const double dr = sqrt(dx * dx + dy * dy + dz * dz) - e.r0;
-            ub = e.bond_k * dr * dr;
+            const double dr = norm_fp64(dx * dx + dy * dy + dz * dz) - e.r0;
+            ub += e.bond_k * dr * dr;
         }
         const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
         const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
@@ -564,10 +575,10 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         const double ux = (double)vx + e.half_dt_m * (double)fx;
         const double uy = (double)vy + e.half_dt_m * (double)fy;
         const double uz = (double)vz + e.half_dt_m * (double)fz;
-        ke = 0.5 * e.mass * (ux * ux + uy * uy + uz * uz);
-        px = e.mass * ux;
-        py = e.mass * uy;
-        pz = e.mass * uz;
+        ke += 0.5 * e.mass * (ux * ux + uy * uy + uz * uz);
+        px += e.mass * ux;
+        py += e.mass * uy;
+        pz += e.mass * uz;
     }
     const double vals[kBeadVals] = {ke, ub, px, py, pz};
 #pragma unroll
@@ -582,18 +593,28 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __r
                                                             int nodes, EnergyConsts e,
                                                             double* __restrict__ partials) {
     __shared__ double sh[kRedBlock / 32];
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
     double w = 0.0;
-    if (node < nodes) {
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
+         node += gridDim.x * blockDim.x) {
+        // unrolled over the species bound so phi stays in registers
         double phi[HPF_MAX_SPECIES];
         double tot = 0.0;
-        for (int k = 0; k < e.S; ++k) {
-            phi[k] = e.phi_c * (double)D[(size_t)k * nodes + node];
+#pragma unroll
+        for (int k = 0; k < HPF_MAX_SPECIES; ++k) {
+            phi[k] = k < e.S ? e.phi_c * (double)D[(size_t)k * nodes + node] : 0.0;
             tot += phi[k];
         }
-        for (int k = 0; k < e.S; ++k)
-            for (int kp = 0; kp < e.S; ++kp) w += 0.5 * e.kT * e.chi[k][kp] * phi[k] * phi[kp];
-        w += 0.5 * e.inv_kappa * (tot - 1.0) * (tot - 1.0);
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < HPF_MAX_SPECIES; ++k) {
+            if (k >= e.S) break;
+            double row = 0.0;
+#pragma unroll
+            for (int kp = 0; kp < HPF_MAX_SPECIES; ++kp)
+                if (kp < e.S) row += e.chi[k][kp] * phi[kp];
+            q += phi[k] * row;
+        }
+        w += 0.5 * e.kT * q + 0.5 * e.inv_kappa * (tot - 1.0) * (tot - 1.0);
     }
     const double s = block_sum(w, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -625,17 +646,25 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __rest
     }
 }
 
+static int energy_blocks(int count);
+
 int energy_partials_needed(int n, int nodes) {
-    const int nb = (n + kRedBlock - 1) / kRedBlock;
-    const int nn = (nodes + kRedBlock - 1) / kRedBlock;
-    return nb * kBeadVals + nn + 1;
+    return energy_blocks(n) * kBeadVals + energy_blocks(nodes) + 1;
+}
+
+// Blocks of the energy reductions: each thread takes a grid-stride share (at
+// most 8 beads or nodes per thread on average), independent of the device so
+// the summation order, and with it every FP64 bit, is the same on any GPU.
+static int energy_blocks(int count) {
+    const int per_block = kRedBlock * 8;
+    return (count + per_block - 1) / per_block;
 }
 
 void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, long long step, const long long* D, const EnergyConsts& e,
                    double* partials, double* out6, cudaStream_t s) {
-    const int nb = (n + kRedBlock - 1) / kRedBlock;
-    const int nn = (g.nodes + kRedBlock - 1) / kRedBlock;
+    const int nb = energy_blocks(n);
+    const int nn = energy_blocks(g.nodes);
     double* bead_part = partials;
     double* node_part = partials + (size_t)nb * kBeadVals;
     if (nb > 0) k_energy_beads<<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part);
