@@ -143,17 +143,20 @@ hpf_status hpf_scatter_density(hpf_ctx* ctx, int64_t* D_out);
 hpf_status hpf_field(hpf_ctx* ctx, const int64_t* D_in, float* field_out);
 
 /* The field stencil runs on shared-memory tiles of the mesh, staged by TMA
- * tensor copies when the mesh allows it (Mx even, n_species <= 4).  The tile
- * shape is chosen the first time the field is computed, by timing six
- * candidate shapes on this mesh (that first refresh synchronises once).
- * shape[0..2] = tile (x, y, z) or zeros before the first refresh; *uses_tma =
- * 1 if the tiles are staged by TMA, 0 if by plain loads.  Either pointer may
- * be NULL.  Errors: HPF_ERR_INVALID. */
+ * tensor copies when the mesh allows it (Mx even, n_species <= 4), or untiled
+ * (one ghosted node, or two real nodes, per thread).  The kernel is chosen
+ * the first time the field is computed, by timing the eight candidates on
+ * this mesh (that first refresh synchronises once).  shape[0..2] = tile
+ * (x, y, z); (0, 0, 0) for the one-node untiled kernel (and before the first
+ * refresh), (2, 1, 1) for the node-pair kernel; *uses_tma = 1 if the tiles
+ * are staged by TMA, 0 otherwise.  Either pointer may be NULL.
+ * Errors: HPF_ERR_INVALID. */
 hpf_status hpf_field_tile(const hpf_ctx* ctx, int32_t shape[3], int32_t* uses_tma);
 
-/* Pin the stencil to candidate `tile` (0 .. 6: (32,8,4), (32,8,8), (16,16,4),
- * (64,4,4), (16,16,8), (32,4,8), untiled) instead of autotuning; -1 autotunes
- * again at the next field.  Errors: HPF_ERR_INVALID. */
+/* Pin the stencil to candidate `tile` (0 .. 7: tiles (32,8,4), (32,8,8),
+ * (16,16,4), (64,4,4), (16,16,8), (32,4,8), untiled one node per thread,
+ * untiled node pairs) instead of autotuning; -1 autotunes again at the next
+ * field.  Every candidate computes the same bits.  Errors: HPF_ERR_INVALID. */
 hpf_status hpf_set_field_tile(hpf_ctx* ctx, int32_t tile);
 
 #define HPF_FORCE_FIELD 1

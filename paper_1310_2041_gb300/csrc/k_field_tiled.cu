@@ -19,9 +19,13 @@ namespace hpf {
 // Candidate tiles (x, y, z): a CTA has x * y threads, each computing z nodes
 // along a z column.  Shape {0, 0, 0} is the untiled one-node-per-thread stencil
 // with direct L1/L2 loads, so the autotuner can never pick a slower kernel.
-constexpr int kTileCandidates = 7;
+// Shape {2, 1, 1} is the untiled two-nodes-per-thread stencil (16-byte pair
+// loads, ghost copies written directly).
+constexpr int kTileCandidates = 8;
 constexpr int kTileShapes[kTileCandidates][3] = {
-    {32, 8, 4}, {32, 8, 8}, {16, 16, 4}, {64, 4, 4}, {16, 16, 8}, {32, 4, 8}, {0, 0, 0}};
+    {32, 8, 4}, {32, 8, 8}, {16, 16, 4}, {64, 4, 4}, {16, 16, 8}, {32, 4, 8}, {0, 0, 0},
+    {2, 1, 1}};
+constexpr int kPairTile = 7;
 constexpr unsigned kWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
 
 int field_tile_candidates() { return kTileCandidates; }
@@ -32,11 +36,11 @@ void field_tile_shape(int id, int out[3]) {
 
 size_t field_tile_smem(int id, int S) {
     const int* t = kTileShapes[id];
-    if (t[0] == 0) return 0;
+    if (t[0] == 0 || id == kPairTile) return 0;
     return sizeof(long long) * (size_t)(t[0] + 4) * (t[1] + 2) * (t[2] + 2) * S;
 }
 
-bool field_tile_is_plain(int id) { return kTileShapes[id][0] == 0; }
+bool field_tile_is_plain(int id) { return kTileShapes[id][0] == 0 || id == kPairTile; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -232,6 +236,99 @@ __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ Til
     }
 }
 
+// Two x-adjacent real nodes (x, x + 1) per thread.  With an even x extent
+// every pair starts on a 16-byte boundary and the centre, y +- 1 and z +- 1
+// rows are read as int64 pairs (7 loads per species for two nodes); an odd
+// extent uses scalar loads and a last pair of one node.  Each node writes its
+// ghost copies itself (x = 0 also at x = Mx, and so on), so no ghosted-index
+// arithmetic is needed.  Same arithmetic as the other candidates.
+template <int S>
+__global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ TiledFieldParams p) {
+    int lo = 0, hi = p.R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const TiledFieldRep& r = p.rep[lo];
+    const MeshGeom& g = r.g;
+    const int hx = (g.mx + 1) >> 1;  // pairs per row
+    const int t = ((int)blockIdx.x - r.blk_begin) * 256 + threadIdx.x;
+    if (t >= hx * g.my * g.mz) return;
+    const int x = 2 * (t % hx), y = (t / hx) % g.my, z = t / (hx * g.my);
+    const bool two = x + 1 < g.mx;
+    const int row = (z * g.my + y) * g.mx;
+    const int ym = y == 0 ? g.my - 1 : y - 1, yp = y + 1 == g.my ? 0 : y + 1;
+    const int zm = z == 0 ? g.mz - 1 : z - 1, zp = z + 1 == g.mz ? 0 : z + 1;
+    const int rym = (z * g.my + ym) * g.mx, ryp = (z * g.my + yp) * g.mx;
+    const int rzm = (zm * g.my + y) * g.mx, rzp = (zp * g.my + y) * g.mx;
+    const int xl = x == 0 ? g.mx - 1 : x - 1;
+    const int x1 = two ? x + 1 : x;  // the second node (a repeat of the first if absent)
+    const int xr = x1 + 1 == g.mx ? 0 : x1 + 1;
+    const bool vec = (g.mx & 1) == 0;
+    float ddx[2][S], ddy[2][S], ddz[2][S], dc[2][S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const long long* Dk = r.D + (size_t)k * g.nodes;
+        long long c0, c1, a0, a1, b0, b1, e0, e1, f0, f1;
+        if (vec) {
+            const longlong2 c = __ldg(reinterpret_cast<const longlong2*>(Dk + row + x));
+            const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(Dk + rym + x));
+            const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(Dk + ryp + x));
+            const longlong2 e = __ldg(reinterpret_cast<const longlong2*>(Dk + rzm + x));
+            const longlong2 f = __ldg(reinterpret_cast<const longlong2*>(Dk + rzp + x));
+            c0 = c.x; c1 = c.y; a0 = a.x; a1 = a.y; b0 = b.x; b1 = b.y;
+            e0 = e.x; e1 = e.y; f0 = f.x; f1 = f.y;
+        } else {
+            c0 = __ldg(Dk + row + x); c1 = __ldg(Dk + row + x1);
+            a0 = __ldg(Dk + rym + x); a1 = __ldg(Dk + rym + x1);
+            b0 = __ldg(Dk + ryp + x); b1 = __ldg(Dk + ryp + x1);
+            e0 = __ldg(Dk + rzm + x); e1 = __ldg(Dk + rzm + x1);
+            f0 = __ldg(Dk + rzp + x); f1 = __ldg(Dk + rzp + x1);
+        }
+        const long long l = __ldg(Dk + row + xl), rr = __ldg(Dk + row + xr);
+        ddx[0][k] = (float)((two ? c1 : rr) - l);  // a lone node's right neighbour wraps
+        ddy[0][k] = (float)(b0 - a0);
+        ddz[0][k] = (float)(f0 - e0);
+        dc[0][k] = (float)c0;
+        ddx[1][k] = (float)(rr - c0);
+        ddy[1][k] = (float)(b1 - a1);
+        ddz[1][k] = (float)(f1 - e1);
+        dc[1][k] = (float)c1;
+        if (r.D_clear) {
+            r.D_clear[(size_t)k * g.nodes + row + x] = 0ull;
+            if (two) r.D_clear[(size_t)k * g.nodes + row + x1] = 0ull;
+        }
+    }
+    const FieldCoef& c = p.coef[lo];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (j == 1 && !two) break;
+        const int xx = x + j;
+        // the node and its periodic ghost copies
+        const int nxs = (xx == 0) ? 2 : 1, nys = (y == 0) ? 2 : 1, nzs = (z == 0) ? 2 : 1;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            float gx = 0.f, gy = 0.f, gz = 0.f, vv = c.v0;
+#pragma unroll
+            for (int kp = 0; kp < S; ++kp) {
+                gx = fmaf(c.gx[k][kp], ddx[j][kp], gx);
+                gy = fmaf(c.gy[k][kp], ddy[j][kp], gy);
+                gz = fmaf(c.gz[k][kp], ddz[j][kp], gz);
+                vv = fmaf(c.v[k][kp], dc[j][kp], vv);
+            }
+            const float4 out = make_float4(gx, gy, gz, vv);
+            float4* Gk = r.G + (size_t)k * g.gnodes;
+            for (int iz = 0; iz < nzs; ++iz)
+                for (int iy = 0; iy < nys; ++iy)
+                    for (int ix = 0; ix < nxs; ++ix) {
+                        const int px = ix ? g.mx : xx, py = iy ? g.my : y, pz = iz ? g.mz : z;
+                        Gk[(size_t)pz * g.gxy + (size_t)py * g.gx + px] = out;
+                    }
+        }
+    }
+}
+
 template <int S, int TX, int TY, int TZ>
 static void launch_tile(const TiledFieldParams& p, cudaStream_t s) {
     const size_t smem = sizeof(long long) * (size_t)(TX + 4) * (TY + 2) * (TZ + 2) * S;
@@ -253,6 +350,7 @@ static void launch_for_species(const TiledFieldParams& p, int tile, cudaStream_t
         case 3: launch_tile<S, 64, 4, 4>(p, s); break;
         case 4: launch_tile<S, 16, 16, 8>(p, s); break;
         case 5: launch_tile<S, 32, 4, 8>(p, s); break;
+        case kPairTile: k_field_pair<S><<<p.blocks, 256, 0, s>>>(p); break;
         default: k_field_plain<S><<<p.blocks, 256, 0, s>>>(p); break;
     }
 }
@@ -315,6 +413,12 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
 
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks) {
     const int* t = kTileShapes[tile];
+    if (tile == kPairTile) {  // 256 node pairs of the real mesh per block
+        *tiles_x = 0;
+        *tiles_y = 0;
+        *blocks = (((g.mx + 1) >> 1) * g.my * g.mz + 255) / 256;
+        return;
+    }
     if (t[0] == 0) {  // untiled: 256 nodes of the ghosted array per block
         *tiles_x = 0;
         *tiles_y = 0;

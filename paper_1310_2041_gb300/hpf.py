@@ -291,7 +291,7 @@ class System:
         return tuple(shape), bool(tma.value)
 
     def force_field_tile(self, tile):
-        """Pin the stencil to candidate `tile` (0..6), or -1 to autotune again."""
+        """Pin the stencil to candidate `tile` (0..7), or -1 to autotune again."""
         self._check(self.lib.hpf_set_field_tile(self.h, int(tile)))
 
     # ---- the path
