@@ -108,6 +108,16 @@ const char* hpf_last_error(const hpf_ctx* ctx);
 hpf_status hpf_set_state(hpf_ctx* ctx, const float* pos, const float* vel, const int32_t* type,
                          const int32_t* bonds, int64_t n_bonds, int64_t step);
 
+/* Replace positions and velocities ([n][3] float32 in tag order, host or
+ * device) and set the step, keeping the species, the bonds and the bead order
+ * of the last sort: the light way to continue from modified coordinates
+ * (hpf_set_state reloads the topology and re-sorts).  The density and the
+ * field of the old positions are dropped.  Asynchronous: a non-finite value
+ * is reported by the next synchronising call (HPF_ERR_NONFINITE), and the
+ * caller's buffers must stay unchanged until the stream reaches the call.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_STATE (no hpf_set_state yet), HPF_ERR_CUDA. */
+hpf_status hpf_update_state(hpf_ctx* ctx, const float* pos, const float* vel, int64_t step);
+
 /* Copy the state out in tag order (either pointer may be NULL) and the step
  * number.  Synchronises the stream.
  * Errors: HPF_ERR_STATE, HPF_ERR_NONFINITE (state became non-finite), HPF_ERR_CUDA. */

@@ -725,6 +725,33 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     return HPF_OK;
 }
 
+hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int64_t step) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    if (step < 0) return fail(c, HPF_ERR_INVALID, "step must be >= 0");
+    const int n = c->n;
+    if (n == 0) {
+        c->step = step;
+        c->field_valid = false;
+        c->mesh_step = -1;
+        return HPF_OK;
+    }
+    if (!pos || !vel) return fail(c, HPF_ERR_INVALID, "pos and vel are required");
+    float* spos = (float*)c->stage;
+    float* svel = spos + 3 * (size_t)n;
+    CUDA_TRY(c, cudaMemcpyAsync(spos, pos, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(svel, vel, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_repermute(spos, svel, c->meta, n, cur_state(c), c->dflag, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->step = step;
+    c->field_valid = false;
+    c->mesh_step = -1;
+    return HPF_OK;
+}
+
 hpf_status hpf_get_state(hpf_ctx* c, float* pos, float* vel, int64_t* step) {
     if (!c) return HPF_ERR_INVALID;
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");

@@ -372,6 +372,8 @@ void launch_advance_counter(long long* step, long long by, cudaStream_t s);
 void launch_set_counter(long long* step, long long v, cudaStream_t s);
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,
                       int* flag, cudaStream_t s);
+void launch_repermute(const float* pos_tag, const float* vel_tag, const uint32_t* meta, int n,
+                      StateBuf st, int* flag, cudaStream_t s);
 
 long long sort_key_space(const MeshGeom& g);
 long long scan_scratch_words(long long L);

@@ -68,6 +68,27 @@ __global__ void k_unpermute(StateBuf st, const uint32_t* __restrict__ meta, int 
     }
 }
 
+// New positions and velocities given in tag order, written in storage order
+// (the inverse of k_unpermute); a non-finite value raises the device flag.
+__global__ void k_repermute(const float* __restrict__ pos_tag, const float* __restrict__ vel_tag,
+                            const uint32_t* __restrict__ meta, int n, StateBuf st,
+                            int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t tag = meta[i] & kTagMask;
+    const float x = pos_tag[3 * tag], y = pos_tag[3 * tag + 1], z = pos_tag[3 * tag + 2];
+    const float vx = vel_tag[3 * tag], vy = vel_tag[3 * tag + 1], vz = vel_tag[3 * tag + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
+          isfinite(vz)))
+        atomicOr(flag, kFlagNonFinite);
+    st.x[i] = x;
+    st.y[i] = y;
+    st.z[i] = z;
+    st.vx[i] = vx;
+    st.vy[i] = vy;
+    st.vz[i] = vz;
+}
+
 __global__ void k_order(const uint32_t* __restrict__ meta, int n, int32_t* __restrict__ order) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) order[i] = (int32_t)(meta[i] & kTagMask);
@@ -100,6 +121,12 @@ void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta
                        cudaStream_t s) {
     if (nb <= 0) return;
     k_mark_bonds<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(bonds, nb, n, meta, err);
+}
+
+void launch_repermute(const float* pos_tag, const float* vel_tag, const uint32_t* meta, int n,
+                      StateBuf st, int* flag, cudaStream_t s) {
+    if (n <= 0) return;
+    k_repermute<<<(n + 255) / 256, 256, 0, s>>>(pos_tag, vel_tag, meta, n, st, flag);
 }
 
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,

@@ -94,6 +94,7 @@ def load():
         L.hpf_destroy.argtypes = [vp]
         L.hpf_set_state.argtypes = [vp, vp, vp, vp, vp, i64, i64]
         L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+        L.hpf_update_state.argtypes = [vp, vp, vp, i64]
         L.hpf_get_order.argtypes = [vp, vp]
         L.hpf_field_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hpf_set_field_tile.argtypes = [vp, i32]
@@ -135,7 +136,7 @@ def load():
                      "hpf_judge_density", "hpf_step_learned"):
             getattr(L, name).restype = ctypes.c_int
         del fp
-        for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state",
+        for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state", "hpf_update_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
                      "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile",
                      "hpf_set_field_tile"):
@@ -263,6 +264,12 @@ class System:
             bonds = np.asarray(bonds, dtype=np.int32).reshape(-1, 2)
         bp, _d = _ptr(bonds, np.int32, (nb, 2), "bonds") if nb else (None, None)
         self._check(self.lib.hpf_set_state(self.h, pp, vp, tp, bp, nb, int(step)))
+
+    def update_state(self, pos, vel, step):
+        """New positions and velocities (tag order), same topology and bead order."""
+        pp, _a = _ptr(pos, np.float32, (self.n, 3), "pos")
+        vp, _b = _ptr(vel, np.float32, (self.n, 3), "vel")
+        self._check(self.lib.hpf_update_state(self.h, pp, vp, int(step)))
 
     def get_state(self, pos=None, vel=None):
         if pos is None:

@@ -263,6 +263,33 @@ def test_resume_is_bit_identical(hpf_gpu):
     np.testing.assert_array_equal(va, vc)
 
 
+def test_update_state_equals_a_fresh_load(hpf_gpu):
+    """hpf_update_state (new coordinates, same topology, old bead order) then
+    steps gives the same bits as loading the coordinates into a new context."""
+    w = W.diblock(100, 4, 4, 8.0, 8, 1.0, field_every=5)
+    a, d, pp = make(hpf_gpu, w, sort_every=6)
+    a.step(20)  # re-sorted along the way
+    p1, v1, st = a.get_state()
+    b, _, _ = make(hpf_gpu, w, data=d, sort_every=6)
+    b.step(10)  # a refresh step: the frozen field of b is that of these positions
+    p2, v2, _ = b.get_state()
+    a.update_state(p2, v2, 10)  # rewind a to b's state
+    a.step(10)
+    b.step(10)
+    pa, va, sa = a.get_state()
+    pb, vb, sb = b.get_state()
+    assert sa == sb == 20
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(a.energy(), b.energy())
+    bad = p2.copy()
+    bad[3, 1] = np.nan
+    a.update_state(bad, v2, 10)
+    with pytest.raises(hpf_gpu.HPFError) as e:
+        a.energy()
+    assert e.value.status == 5
+
+
 def expected_order(orc, op, pos, n_chain_beads):
     """Chain order by (brick-major cell key of the first bead, first tag), from the oracle."""
     firsts = np.concatenate([[0], np.cumsum(n_chain_beads)[:-1]])

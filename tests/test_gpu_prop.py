@@ -302,3 +302,48 @@ def test_trained_network_beats_holding_the_last_density(hpf_gpu):
     assert np.mean(res["net"]) < 0.95 * np.mean(res["hold_net"])
     assert np.allclose(res["hold_net"], res[f"hold_{K}"][-len(res["hold_net"]):])
     del torch
+
+
+def test_learned_step_rejects_bad_arguments(hpf_gpu):
+    w, pp, data = melt(hpf_gpu)
+    a = system(hpf_gpu, pp, data)
+    with hpf_gpu.Propagator((10, 10, 12)) as wrong, hpf_gpu.Propagator((10, 10, 10)) as net:
+        calls = [lambda: a.step_learned(wrong, 1, K=4),          # another mesh
+                 lambda: a.step_learned(net, 1, K=1),            # K below 2
+                 lambda: a.step_learned(net, 1, K=65),           # K above 64
+                 lambda: a.step_learned(net, -1, K=4),           # negative count
+                 lambda: a.step_learned(net, 1, K=4, tol=-1.0),
+                 lambda: a.step_learned(net, 1, K=4, tol=float("nan"))]
+        for call in calls:
+            with pytest.raises(hpf_gpu.HPFError) as e:
+                call()
+            assert e.value.status == 1
+        # nothing moved
+        assert a.get_state()[2] == 0
+        st = a.step_learned(net, 0, K=4)
+        assert st["windows"] == 0 and st["steps"] == 0
+
+
+def test_judge_three_species_against_oracle(hpf_gpu, orc):
+    """The judge works for any species count (the learned step needs two)."""
+    w = W.Workload("ternary_small", [(40, [0, 1, 2, 1]), (90, [2])], 7.0, 8, 3,
+                   [[0, 1.2, 0.3], [1.2, 0, 0.8], [0.3, 0.8, 0]], 0.05, 3, 10)
+    pp = w.params()
+    data = W.generate(w)
+    s = system(hpf_gpu, pp, data)
+    phi = s.density_phi().astype(np.float64)
+    assert phi.shape == (3, 8, 8, 8)
+    rng = np.random.default_rng(9)
+    cand = np.clip(phi + rng.normal(scale=0.1, size=phi.shape), 0.0, None).astype(np.float32)
+    eps = s.judge_density(cand)
+    op = orc.make_params(**pp)
+    h = [np.float64(np.float32(pp["box"][a])) / pp["mesh"][a] for a in range(3)]
+    inv_phi_c = 1.0 / (2.0 ** -39 / (pp["rho0"] * (h[0] * h[1] * h[2])))
+    Dc = np.maximum(np.rint(cand.astype(np.float64) * inv_phi_c), 0).astype(np.int64)
+    Dt = orc.scatter(op, data["pos"], data["type"])
+    Fc = orc.field_force(op, data["pos"], data["type"], orc.field(op, Dc)[1])
+    Ft = orc.field_force(op, data["pos"], data["type"], orc.field(op, Dt)[1])
+    assert eps == pytest.approx(np.linalg.norm(Fc - Ft) / np.linalg.norm(Ft), rel=1e-3)
+    with hpf_gpu.Propagator((8, 8, 8)) as net:
+        with pytest.raises(hpf_gpu.HPFError):
+            s.step_learned(net, 1, K=4)
