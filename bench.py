@@ -154,6 +154,35 @@ def cpu_oracle_rate(w, data, budget_s: float):
                       f"{dt:.1f} s of CPU time"}
 
 
+def cpu_oracle_learned_rate(w, data, snap, K: int, budget_s: float):
+    """The oracle of the learned form at tol 1e-3, where every window falls
+    back to the plain update: MD with the field refreshed every step (a bounded
+    sample of the same melt) plus one propagator forward pass (numpy FP64 on
+    the full mesh) per window of K steps, combined in bead-steps/s."""
+    import numpy as np
+    import oracle
+    from oracle import propagator as P
+    oracle.build()
+    pp = dict(w.params(), field_every=1)
+    op = oracle.make_params(**pp)
+    clen = len(w.blocks[0][1])
+    c = max(1, w.blocks[0][0] // 10)
+    n = c * clen
+    t = time.perf_counter()
+    oracle.run(op, data["pos"][:n], data["vel"][:n], data["type"][:n],
+               data["bonds"][: c * (clen - 1)], 0, 2)
+    md_per_bead_step = (time.perf_counter() - t) / (2 * n)
+    t = time.perf_counter()
+    P.forward(P.init_params(0), np.asarray(snap, dtype=np.float64))
+    fwd = time.perf_counter() - t
+    per_step = md_per_bead_step * w.n_beads + fwd / K
+    return {"value": w.n_beads / per_step, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"2 plain steps (field every step) of {n} of the {w.n_beads} beads "
+                      f"({md_per_bead_step * w.n_beads:.2f} s per full step), one propagator "
+                      f"forward on the {w.mesh}^3 mesh ({fwd:.1f} s, once per {K} steps)"}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -523,6 +552,10 @@ def run_learned(args):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 1900.0, "fallback"
     achieved = flops / (infer_ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        x0 = snaps[100:102].reshape((4,) + tuple(snaps.shape[2:])).cpu().numpy()
+        cpu = cpu_oracle_learned_rate(w, data, x0, K, budget_s=12.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": n_win * K, "warmup": warm_win * K,
             "ms_per_step": 1e3 * w.n_beads / value,
@@ -539,7 +572,7 @@ def run_learned(args):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src, "kernel": "k_conv (whole forward)",
                          "algo_flops_per_inference": flops},
-            "cpu_baseline": None, "e2e": None, "clocks": clk}
+            "cpu_baseline": cpu, "e2e": None, "clocks": clk}
     print(json.dumps(line), flush=True)
     net.close()
     return 0
