@@ -21,7 +21,9 @@ from paper_1310_2041_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-MESHES = [(13, 10, 5), (8, 8, 2), (3, 2, 2), (24, 16, 9)]
+# ragged tiles, a mesh smaller than a tile, a mesh wrapping the box several
+# times, and meshes large enough for the one-period wrap of the box copies
+MESHES = [(13, 10, 5), (8, 8, 2), (3, 2, 2), (24, 16, 9), (20, 18, 19), (26, 34, 18)]
 
 
 def rand_params(seed):
@@ -81,7 +83,8 @@ def test_weights_round_trip(hpf_gpu):
         assert np.array_equal(net.get_weights(), vec)
 
 
-@pytest.mark.parametrize("mesh", [(13, 10, 5), (24, 16, 9)], ids=lambda m: "x".join(map(str, m)))
+@pytest.mark.parametrize("mesh", [(13, 10, 5), (24, 16, 9), (20, 18, 19)],
+                         ids=lambda m: "x".join(map(str, m)))
 def test_backward_matches_oracle(hpf_gpu, mesh):
     params = rand_params(5)
     x = rand_phi(grid(mesh), 6)
