@@ -1397,7 +1397,7 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
         if (have_hist) {
             StageScope sc(c, HPF_STAGE_OTHER, 6);
             launch_mesh_to_phi(Dt, SM, c->ec.phi_c, L->x + SM, c->stream);
-            prop_predict(prop, L->x, L->dphi, c->stream, c->dflag);
+            prop_predict(prop, L->x, L->dphi, c->stream);
         }
         LAUNCH_CHECK(c);
         bool judged = false;

@@ -402,8 +402,7 @@ int energy_partials_needed(int n, int nodes);
 
 // learned density propagator (the network lives in k_prop.cu)
 bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);
-// flag: the caller's device flag word, where a timed-out wait is reported
-void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag);
+void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s);
 void launch_mesh_to_phi(const unsigned long long* D, long long n, double phi_c, float* phi,
                         cudaStream_t s);
 void launch_mesh_predict(const unsigned long long* D_base, const float* dphi, long long n,

@@ -284,318 +284,6 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
     }
 }
 
-// ------------------------------------------------------------------ tcgen05 convolution
-//
-// The same convolution on the fifth-generation tensor cores.  A CTA (one
-// warpgroup) works on 8 x 16 x 4 tiles: each z-plane is 128 voxels = the 128
-// rows of one MMA, eight x-consecutive voxels per 8-row core-matrix group, one
-// group per y row, and the four planes are four independent accumulators.
-// The periodic 10 x 18 x 6 input box and the weights are stored as two planes
-// of 8-channel halves (16 bytes per voxel or output channel), which is the
-// canonical K-major layout without swizzle: a core matrix is 8 rows x 16
-// bytes contiguous, the two K halves are one plane apart (leading byte
-// offset), consecutive 8-row groups one box row apart (stride byte offset:
-// 10 voxels for A, 8 channels for B).  Each of the 27 kernel offsets is then
-// one tcgen05.mma per plane (M 128, N 16, K 16, BF16 in, FP32 accumulated in
-// tensor memory) whose A descriptor starts at the shifted box position; one
-// thread issues them, the planes interleaved so four chains are in flight,
-// and commits to an mbarrier; every warp reads its 32 rows of each plane back
-// with tcgen05.ld for the epilogue.
-constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;       // tile: 8 x 16 x 4 voxels, 4 MMA row blocks
-constexpr int kTcBX = kTcX + 2, kTcBY = kTcY + 2, kTcBZ = kTcZ + 2;
-constexpr int kTcPlane = kTcBX * kTcBY;            // box voxels per z-plane
-constexpr int kTcBox = kTcPlane * kTcBZ;           // 1080 voxels per channel half
-constexpr unsigned kTcWaitLimit = 1u << 22;        // mbarrier polls before giving up
-constexpr int kTmemCols = 128;                     // 2 buffers x 4 planes x 16 columns
-constexpr size_t kTcSmem = sizeof(uint4) * (2 * 2 * kTcBox + 2 * 27 * 16) + 64;
-
-// Shared-memory matrix descriptor: start address, leading and stride byte
-// offsets (all in 16-byte units), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// A thread's share of the box copies: element e = tid + 128 k (k < kTcSlots)
-// of the [half][voxel] box, its box coordinates and shared-memory offset,
-// fixed for every tile, so a tile only adds its origin and wraps.
-constexpr int kTcSlots = (kTcBox * 2 + 127) / 128;
-
-struct TcSlots {
-    int c[kTcSlots];        // bx | by << 8 | bz << 16 | half << 24, or -1
-    uint32_t s[kTcSlots];   // byte offset in a box buffer
-};
-
-__device__ __forceinline__ void tc_slots(TcSlots& sl) {
-#pragma unroll
-    for (int k = 0; k < kTcSlots; ++k) {
-        const int e = threadIdx.x + 128 * k;
-        const int v = e >> 1, half = e & 1;
-        const int bx = v % kTcBX, by = (v / kTcBX) % kTcBY, bz = v / (kTcBX * kTcBY);
-        sl.c[k] = e < kTcBox * 2 ? (bx | (by << 8) | (bz << 16) | (half << 24)) : -1;
-        sl.s[k] = (uint32_t)sizeof(uint4) * (uint32_t)(half * kTcBox + v);
-    }
-}
-
-// i in [-1, m + 16]: one period at most when m >= 18 (the box extents), the
-// general remainder otherwise.
-__device__ __forceinline__ int tc_wrap(int i, int m, bool near) {
-    if (near) return i < 0 ? i + m : (i >= m ? i - m : i);
-    return pwrap(i, m);
-}
-
-// Box of the tile with origin (x0, y0, z0) into the buffer at shared address
-// box_s: cp.async of 16-byte channel halves.
-__device__ __forceinline__ void tc_load_box(const __nv_bfloat16* __restrict__ in,
-                                            const PropGeom& g, int x0, int y0, int z0,
-                                            uint32_t box_s, const TcSlots& sl, bool near) {
-#pragma unroll
-    for (int k = 0; k < kTcSlots; ++k) {
-        const int c = sl.c[k];
-        if (c < 0) continue;
-        const int gx = tc_wrap(x0 - 1 + (c & 0xff), g.mx, near);
-        const int gy = tc_wrap(y0 - 1 + ((c >> 8) & 0xff), g.my, near);
-        const int gz = tc_wrap(z0 - 1 + ((c >> 16) & 0xff), g.mz, near);
-        const int gv = (gz * g.my + gy) * g.mx + gx;
-        cp_async16(box_s + sl.s[k], in + (size_t)gv * kPC + 8 * (c >> 24));
-    }
-}
-
-__device__ __forceinline__ void tc_origin(const PropGeom& g, int t, int& x0, int& y0, int& z0) {
-    const int tx = (g.mx + kTcX - 1) / kTcX, ty = (g.my + kTcY - 1) / kTcY;
-    x0 = (t % tx) * kTcX;
-    y0 = ((t / tx) % ty) * kTcY;
-    z0 = (t / (tx * ty)) * kTcZ;
-}
-
-// Epilogue of one tile: the warp's 32 accumulator rows (TMEM lanes 32w ..)
-// from columns col .. col + 15.
-template <int kMode>
-__device__ __forceinline__ void tc_epilogue(uint32_t tmem_col, const PropGeom& g, int x0, int y0,
-                                            int z0, bool ok, const float* __restrict__ bias,
-                                            float* __restrict__ z_out,
-                                            __nv_bfloat16* __restrict__ act_out,
-                                            float* __restrict__ f_out) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float acc[16];
-    {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tmem_col + ((uint32_t)(32 * w) << 16)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = __uint_as_float(r[c]);
-    }
-    // row 32w + lane = voxel (x0 + row % 8, y0 + row / 8, z0)
-    const int row = 32 * w + lane;
-    const int X = x0 + (row & 7), Y = y0 + (row >> 3), Z = z0;
-    if (!ok || X >= g.mx || Y >= g.my || Z >= g.mz) return;
-    const size_t gv = ((size_t)Z * g.my + Y) * g.mx + X;
-    if (kMode != kData) {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] += bias[c];
-    }
-    if (kMode == kHidden) {
-        if (z_out) {
-            float4* zo = reinterpret_cast<float4*>(z_out + gv * kPC);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        }
-        __nv_bfloat162 h[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float a = acc[2 * c], b = acc[2 * c + 1];
-            h[c] = __floats2bfloat162_rn(a / (1.0f + expf(-a)), b / (1.0f + expf(-b)));
-        }
-        uint4* ao = reinterpret_cast<uint4*>(act_out + gv * kPC);
-        ao[0] = reinterpret_cast<uint4*>(h)[0];
-        ao[1] = reinterpret_cast<uint4*>(h)[1];
-    } else {
-        float4* fo = reinterpret_cast<float4*>(f_out + gv * kPC);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            fo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-    }
-}
-
-// Persistent: the weights, the tensor memory (two buffers of four 16-column
-// accumulators) and the barriers are set up once per CTA; tiles are taken
-// grid-stride with two box buffers, so the box of tile i + 1 is loaded and the
-// epilogue of tile i - 1 runs while the tensor cores work on tile i.
-template <int kMode>
-__global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict__ in,
-                                                 const __nv_bfloat16* __restrict__ W,
-                                                 const float* __restrict__ bias,
-                                                 float* __restrict__ z_out,
-                                                 __nv_bfloat16* __restrict__ act_out,
-                                                 float* __restrict__ f_out, PropGeom g,
-                                                 int n_tiles, int* __restrict__ flag) {
-    extern __shared__ __align__(128) uint4 tc_smem[];
-    uint4* boxp = tc_smem;                         // [buffer][channel half][kTcBox]
-    uint4* wp = tc_smem + 2 * 2 * kTcBox;          // [channel half][27 * 16]
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(wp + 2 * kOffsets * kPC);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-    const int tid = threadIdx.x, w = tid >> 5;
-    if (w == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         saddr(tmem_slot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[1])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    for (int e = tid; e < kOffsets * kPC * 2; e += blockDim.x)
-        cp_async16(saddr(&wp[(e & 1) * kOffsets * kPC + (e >> 1)]),
-                   reinterpret_cast<const uint4*>(W) + e);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    TcSlots sl;
-    tc_slots(sl);
-    const bool near = g.mx >= kTcBY && g.my >= kTcBY && g.mz >= kTcBY;
-    constexpr uint32_t idesc = umma_idesc_bf16(128, 16);
-    const uint32_t lbo_a = sizeof(uint4) * kTcBox, sbo_a = sizeof(uint4) * kTcBX;
-    const uint32_t lbo_b = sizeof(uint4) * kOffsets * kPC, sbo_b = sizeof(uint4) * 8;
-    const uint32_t box0 = saddr(boxp), wp0 = saddr(wp);
-    uint32_t phase[2] = {0u, 0u};
-    int px0 = 0, py0 = 0, pz0 = 0;  // origin of the previous tile
-    int i = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
-        const int b = i & 1;
-        int x0, y0, z0;
-        tc_origin(g, t, x0, y0, z0);
-        // buffer b was last read by the MMAs of tile i - 2, whose completion the
-        // epilogue of tile i - 2 waited for
-        const uint32_t boxb = box0 + (uint32_t)(sizeof(uint4) * 2 * kTcBox) * b;
-        tc_load_box(in, g, x0, y0, z0, boxb, sl, near);
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-#pragma unroll 1
-            for (int o = 0; o < kOffsets; ++o) {
-                const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
-                const int v0 = ((1 + dz) * kTcBY + (1 + dy)) * kTcBX + (1 + dx);
-                const uint64_t bd = umma_smem_desc(wp0 + (uint32_t)sizeof(uint4) * o * kPC, lbo_b,
-                                                   sbo_b);
-#pragma unroll
-                for (int zz = 0; zz < kTcZ; ++zz) {
-                    const uint64_t ad = umma_smem_desc(
-                        boxb + (uint32_t)sizeof(uint4) * (v0 + zz * kTcPlane), lbo_a, sbo_a);
-                    const uint32_t d = tmem + 16u * (kTcZ * b + zz);
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.u32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)o)
-                        : "memory");
-                }
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    saddr(&bar[b]))
-                : "memory");
-        }
-        if (i > 0) {
-            // epilogue of the previous tile while this one is on the tensor cores
-            const int pb = b ^ 1;
-            bool done = tc_wait(saddr(&bar[pb]), phase[pb]);
-            if (!done) {
-                atomicOr(flag, kFlagTimeout);
-                done = tc_wait(saddr(&bar[pb]), phase[pb]);
-            }
-            phase[pb] ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int zz = 0; zz < kTcZ; ++zz)
-                tc_epilogue<kMode>(tmem + 16u * (kTcZ * pb + zz), g, px0, py0, pz0 + zz, done,
-                                   bias, z_out, act_out, f_out);
-        }
-        px0 = x0;
-        py0 = y0;
-        pz0 = z0;
-    }
-    if (i > 0) {
-        const int pb = (i - 1) & 1;
-        bool done = tc_wait(saddr(&bar[pb]), phase[pb]);
-        if (!done) {
-            atomicOr(flag, kFlagTimeout);
-            done = tc_wait(saddr(&bar[pb]), phase[pb]);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-        for (int zz = 0; zz < kTcZ; ++zz)
-            tc_epilogue<kMode>(tmem + 16u * (kTcZ * pb + zz), g, px0, py0, pz0 + zz, done, bias,
-                               z_out, act_out, f_out);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (w == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
-                     : "memory");
-}
-
-int conv_tc_tiles(const PropGeom& g) {
-    return ((g.mx + kTcX - 1) / kTcX) * ((g.my + kTcY - 1) / kTcY) * ((g.mz + kTcZ - 1) / kTcZ);
-}
-
-// Persistent grid of the tcgen05 convolution: 2 CTAs per SM (83 KB of shared
-// memory and 128 tensor-memory columns each).
-int conv_tc_grid(const PropGeom& g) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_conv_tc<kHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmem);
-        cudaFuncSetAttribute(k_conv_tc<kLast>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmem);
-        cudaFuncSetAttribute(k_conv_tc<kData>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmem);
-        cudaGetLastError();
-        if (sms < 1) sms = 1;
-    }
-    const int t = conv_tc_tiles(g);
-    return t < 2 * sms ? t : 2 * sms;
-}
-
 // ------------------------------------------------------------------ elementwise
 
 __global__ void k_pack_input(const float* __restrict__ x, int V, __nv_bfloat16* __restrict__ out) {
@@ -857,7 +545,6 @@ struct hpf_prop {
     float* yout = nullptr;        // planar output [2][V]
     double* loss = nullptr;
     double* h_loss = nullptr;
-    int* dflag = nullptr;         // device flags of the tensor-core kernels (bounded waits)
     int grid_wgrad = 0;
 };
 
@@ -879,20 +566,19 @@ hpf_status prop_copy_out(hpf_prop* p, void* dst, const void* src, size_t bytes) 
 
 // Forward pass of planar input x [4][V] (device); leaves the FP32 output in
 // fbuf.  With keep_z the pre-activations are stored for a backward pass.
-// flag: where the tensor-core kernels report a timed-out wait.
-void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s, int* flag) {
+void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s) {
     const int V = p->g.V, tb = (V + 255) / 256;
     const size_t wl = (size_t)kOffsets * kPC * kPC;
-    const int tiles = conv_tc_tiles(p->g), grid = conv_tc_grid(p->g);
     k_pack_input<<<tb, 256, 0, s>>>(x, V, p->act[0]);
-    k_conv_tc<kHidden><<<grid, 128, kTcSmem, s>>>(p->act[0], p->wf, p->bias,
-                                            keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
-                                            p->g, tiles, flag);
-    k_conv_tc<kHidden><<<grid, 128, kTcSmem, s>>>(p->act[1], p->wf + wl, p->bias + kPC,
-                                            keep_z ? p->z[1] : nullptr, p->act[2], nullptr,
-                                            p->g, tiles, flag);
-    k_conv_tc<kLast><<<grid, 128, kTcSmem, s>>>(p->act[2], p->wf + 2 * wl, p->bias + 2 * kPC,
-                                          nullptr, nullptr, p->fbuf, p->g, tiles, flag);
+    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[0], p->wf, p->bias,
+                                                   keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
+                                                   p->g);
+    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[1], p->wf + wl, p->bias + kPC,
+                                                   keep_z ? p->z[1] : nullptr, p->act[2], nullptr,
+                                                   p->g);
+    // two output channels: one n-tile (channels 8..15 of fbuf are not written)
+    k_conv<kLast, 1><<<p->g.tiles, 256, 0, s>>>(p->act[2], p->wf + 2 * wl, p->bias + 2 * kPC,
+                                                 nullptr, nullptr, p->fbuf, p->g);
 }
 
 // Loss and packed gradients (p->grads, p->loss) after prop_forward(keep_z) of
@@ -914,9 +600,8 @@ void prop_backward(hpf_prop* p, const float* x, const float* phi_next) {
         k_sum_partials<float><<<1, 32, 0, s>>>(p->bpart, kBiasBlocks, kPC, p->db + layer * kPC);
         if (layer == 0) break;
         // the data gradient of the layer input, then through the SiLU below it
-        k_conv_tc<kData><<<conv_tc_grid(p->g), 128, kTcSmem, s>>>(gbuf, p->wb + layer * wl, nullptr,
-                                                             nullptr, nullptr, p->fbuf, p->g,
-                                                             conv_tc_tiles(p->g), p->dflag);
+        k_conv<kData, 2><<<p->g.tiles, 256, 0, s>>>(gbuf, p->wb + layer * wl, nullptr, nullptr,
+                                                     nullptr, p->fbuf, p->g);
         k_silu_backward<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(p->fbuf, p->z[layer - 1], nv,
                                                                       gbuf);
     }
@@ -941,18 +626,6 @@ hpf_status prop_stage(hpf_prop* p, float* dst, const float* src, size_t n) {
         return HPF_ERR_CUDA;
     }
     return HPF_OK;
-}
-
-// A timed-out wait of a tensor-core kernel (synchronises).
-hpf_status prop_check(hpf_prop* p) {
-    int h = 0;
-    if (cudaMemcpyAsync(&h, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(p->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return HPF_ERR_CUDA;
-    }
-    return (h & kFlagTimeout) ? HPF_ERR_TIMEOUT : HPF_OK;
 }
 
 hpf_status prop_read_loss(hpf_prop* p, double* loss) {
@@ -980,8 +653,8 @@ bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g) {
     return p && p->g.mx == g.mx && p->g.my == g.my && p->g.mz == g.mz;
 }
 
-void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag) {
-    prop_forward(p, x, false, s, flag);
+void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s) {
+    prop_forward(p, x, false, s);
     k_unpack_output<<<(p->g.V + 255) / 256, 256, 0, s>>>(p->fbuf, p->g.V, dphi);
 }
 
@@ -1038,8 +711,6 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     e = e ? e : cudaMalloc(&p->yout, sizeof(float) * Vs * 2);
     e = e ? e : cudaMalloc(&p->loss, sizeof(double));
     e = e ? e : cudaMallocHost(&p->h_loss, sizeof(double));
-    e = e ? e : cudaMalloc(&p->dflag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream);
     if (e == cudaSuccess) {
         // zero weights until hpf_prop_set_weights: the network predicts no change
         cudaMemsetAsync(p->params, 0, sizeof(float) * p->np, p->stream);
@@ -1081,7 +752,6 @@ hpf_status hpf_prop_destroy(hpf_prop* p) {
     cudaFree(p->yout);
     cudaFree(p->loss);
     cudaFreeHost(p->h_loss);
-    cudaFree(p->dflag);
     cudaGetLastError();
     delete p;
     return HPF_OK;
@@ -1111,10 +781,9 @@ hpf_status hpf_prop_forward(hpf_prop* p, const float* x, float* dphi) {
     if (!p || !dphi) return HPF_ERR_INVALID;
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s != HPF_OK) return s;
-    prop_predict(p, p->xin, p->yout, p->stream, p->dflag);
+    prop_predict(p, p->xin, p->yout, p->stream);
     if ((s = prop_launched(p)) != HPF_OK) return s;
-    if ((s = prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V)) != HPF_OK) return s;
-    return prop_check(p);
+    return prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V);
 }
 
 hpf_status hpf_prop_backward(hpf_prop* p, const float* x, const float* phi_next, float* grads,
@@ -1123,12 +792,11 @@ hpf_status hpf_prop_backward(hpf_prop* p, const float* x, const float* phi_next,
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s == HPF_OK) s = prop_stage(p, p->tin, phi_next, (size_t)p->g.V * 2);
     if (s != HPF_OK) return s;
-    prop_forward(p, p->xin, true, p->stream, p->dflag);
+    prop_forward(p, p->xin, true, p->stream);
     prop_backward(p, p->xin, p->tin);
     if ((s = prop_launched(p)) != HPF_OK) return s;
     if ((s = prop_copy_out(p, grads, p->grads, sizeof(float) * p->np)) != HPF_OK) return s;
-    if ((s = prop_read_loss(p, loss)) != HPF_OK) return s;
-    return prop_check(p);
+    return prop_read_loss(p, loss);
 }
 
 hpf_status hpf_prop_adam_step(hpf_prop* p, const float* grads, float lr) {
@@ -1145,7 +813,7 @@ hpf_status hpf_prop_train_step(hpf_prop* p, const float* x, const float* phi_nex
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s == HPF_OK) s = prop_stage(p, p->tin, phi_next, (size_t)p->g.V * 2);
     if (s != HPF_OK) return s;
-    prop_forward(p, p->xin, true, p->stream, p->dflag);
+    prop_forward(p, p->xin, true, p->stream);
     prop_backward(p, p->xin, p->tin);
     prop_adam(p, p->grads, lr);
     if ((s = prop_launched(p)) != HPF_OK) return s;
