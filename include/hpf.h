@@ -365,9 +365,12 @@ typedef struct {
  * window; otherwise the state at t is restored and the window re-run with a
  * true scatter and field refresh every step (the plain update), and the next
  * windows run plain while their predictions are judged in the shadow, until
- * one meets tol.  The first window of a context runs plain (it builds the
- * phi(t-K) history).  Beads are re-sorted only at window starts.  With zero
- * network weights a learned window equals field_every = K exactly.
+ * one meets tol.  After a rejection or a failed shadow judgement the next
+ * 1, 2, 4, ... (at most 64) plain windows skip the prediction and the judge,
+ * so a network that keeps failing costs little.  The first window of a
+ * context runs plain (it builds the phi(t-K) history).  Beads are re-sorted
+ * only at window starts.  With zero network weights a learned window equals
+ * field_every = K exactly.
  * Synchronises once per window.  stats may be NULL.
  * Errors: HPF_ERR_INVALID, HPF_ERR_STATE, HPF_ERR_CUDA, HPF_ERR_NONFINITE,
  * HPF_ERR_OVERFLOW. */

@@ -79,6 +79,8 @@ struct LearnedBufs {
     double* h_acc = nullptr;
     long long hist_step = -1;  // step whose phi is in x[0:2] (-1: none)
     bool plain_mode = false;   // run plain windows (shadow-judged) until a prediction meets tol
+    int backoff = 0;           // plain windows to skip between shadow judgements (doubles per failure)
+    int skip_left = 0;         // plain windows left before the next shadow judgement
 };
 
 namespace {
@@ -1394,7 +1396,11 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
         CUDA_TRY(c, cudaMemcpyAsync(L->Dbase, Dt, sizeof(unsigned long long) * SM,
                                     cudaMemcpyDeviceToDevice, c->stream));
         const bool have_hist = L->hist_step >= 0 && L->hist_step == t - K;
-        if (have_hist) {
+        // in plain mode after failed judgements, predict (and judge) only every
+        // few windows: the network's cost is not paid while it keeps failing
+        const bool skip = L->plain_mode && L->skip_left > 0;
+        if (skip) L->skip_left -= 1;
+        if (have_hist && !skip) {
             StageScope sc(c, HPF_STAGE_OTHER, 6);
             launch_mesh_to_phi(Dt, SM, c->ec.phi_c, L->x + SM, c->stream);
             prop_predict(prop, L->x, L->dphi, c->stream);
@@ -1402,7 +1408,7 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
         LAUNCH_CHECK(c);
         bool judged = false;
         double eps = 0.0;
-        if (have_hist && !L->plain_mode) {
+        if (have_hist && !skip && !L->plain_mode) {
             // learned window: steps t .. t+K-1 on predicted densities
             CUDA_TRY(c, cudaMemcpyAsync(L->snap, cur_state(c).x, sizeof(float) * 6 * c->n,
                                         cudaMemcpyDeviceToDevice, c->stream));
@@ -1451,11 +1457,13 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
                 c->next_zero = false;
                 if ((s = plain_window(c, K)) != HPF_OK) return s;
                 L->plain_mode = true;
+                L->backoff = 1;
+                L->skip_left = 1;
             }
         } else {
             if ((s = plain_window(c, K)) != HPF_OK) return s;
             st.plain += 1;
-            if (have_hist) {
+            if (have_hist && !skip) {
                 // shadow judge of the prediction made at t
                 if (c->mesh_step != c->step && (s = scatter_current(c)) != HPF_OK) return s;
                 {
@@ -1465,7 +1473,13 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
                 LAUNCH_CHECK(c);
                 if ((s = judge_mesh(c, &eps)) != HPF_OK) return s;
                 judged = true;
-                if (eps <= tol) L->plain_mode = false;
+                if (eps <= tol) {
+                    L->plain_mode = false;
+                    L->backoff = 0;
+                } else {
+                    L->backoff = L->backoff > 0 ? (L->backoff < 32 ? 2 * L->backoff : 64) : 1;
+                    L->skip_left = L->backoff;
+                }
             }
         }
         if (judged) {

@@ -238,20 +238,22 @@ def test_zero_tolerance_equals_plain(hpf_gpu):
     with hpf_gpu.Propagator((10, 10, 10)) as net:
         net.set_weights(hpf_gpu.pack_params(P.init_params(2)))
         # window 1 builds history; window 2 is learned, rejected and re-run
-        # plain; windows 3-5 run plain with their predictions judged aside
+        # plain; window 3 skips the judge (back-off 1), window 4 is judged aside
+        # and fails (back-off 2), window 5 skips
         st = a.step_learned(net, 5, K=K, tol=0.0)
-        assert (st["plain"], st["rejected"], st["learned"], st["judged"]) == (4, 1, 0, 4)
-        # a shadow judgement that passes switches back to learned windows ...
-        st = a.step_learned(net, 1, K=K, tol=1e9)
-        assert (st["plain"], st["judged"]) == (1, 1)
-        # ... which a zero tolerance rejects again
+        assert (st["plain"], st["rejected"], st["learned"], st["judged"]) == (4, 1, 0, 2)
+        # window 6 still skips; window 7's shadow judgement passes and switches
+        # back to learned windows ...
+        st = a.step_learned(net, 2, K=K, tol=1e9)
+        assert (st["plain"], st["judged"], st["learned"]) == (2, 1, 0)
+        # ... which a zero tolerance rejects again (window 8), window 9 skips
         st = a.step_learned(net, 2, K=K, tol=0.0)
-        assert (st["rejected"], st["plain"], st["learned"]) == (1, 1, 0)
+        assert (st["rejected"], st["plain"], st["learned"], st["judged"]) == (1, 1, 0, 1)
     b = system(hpf_gpu, pp, data)
-    b.step(8 * K)
+    b.step(9 * K)
     pa, va, sa = a.get_state()
     pb, vb, sb = b.get_state()
-    assert sa == sb == 8 * K
+    assert sa == sb == 9 * K
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
 
 
