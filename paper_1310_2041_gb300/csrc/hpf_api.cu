@@ -291,7 +291,7 @@ void fill_field_rep(hpf_ctx* c, int tile, int dm, TiledFieldRep& fr, int& blocks
 
 // Time every candidate tile on this launch shape and keep the fastest.  The
 // candidates compute the same field (the last launch leaves it in place).
-template <class Fill>
+template <class Params, class Fill>
 int autotune_tile(cudaStream_t s, int S, Fill fill) {
     if (S > 4) return -1;
     cudaEvent_t a, b;
@@ -302,7 +302,7 @@ int autotune_tile(cudaStream_t s, int S, Fill fill) {
     int best = 0;
     float best_ms = 1e30f;
     for (int t = 0; t < field_tile_candidates(); ++t) {
-        TiledFieldParams p;
+        Params p;
         fill(t, p);
         launch_field_tiled(p, S, t, s);  // warm
         cudaEventRecord(a, s);
@@ -347,16 +347,16 @@ hpf_status run_field(hpf_ctx* c) {
         // the tiled (TMA-staged) stencil with one replica; a batch runs the same
         // kernel, so contexts and batch members agree bit for bit
         if (c->field_tile < 0)
-            c->field_tile = autotune_tile(c->stream, c->S, [&](int t, TiledFieldParams& p) {
-                memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+            c->field_tile = autotune_tile<SingleFieldParams>(c->stream, c->S, [&](int t, SingleFieldParams& p) {
+                memset(&p, 0, sizeof p);
                 p.R = 1;
                 p.coef = c->d_coef;
                 p.flag = c->dflag;
                 fill_field_rep(c, t, c->dmesh, p.rep[0], p.blocks);
             });
         StageScope sc(c, HPF_STAGE_FIELD, 1);
-        TiledFieldParams p;
-        memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+        SingleFieldParams p;
+        memset(&p, 0, sizeof p);
         p.R = 1;
         p.coef = c->d_coef;
         p.flag = c->dflag;
@@ -391,8 +391,8 @@ hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap
     {
         StageScope sc(c, HPF_STAGE_FIELD, 1);
         if (c->S <= 4 && c->field_tile >= 0) {
-            TiledFieldParams p;
-            memset(&p, 0, sizeof(TiledFieldParams) - sizeof(p.rep) + sizeof(p.rep[0]));
+            SingleFieldParams p;
+            memset(&p, 0, sizeof p);
             p.R = 1;
             p.coef = c->d_coef;
             p.flag = c->dflag;
@@ -980,7 +980,7 @@ hpf_status batch_refresh(hpf_batch* b) {
         return HPF_OK;
     }
     if (b->field_tile < 0)
-        b->field_tile = autotune_tile(b->stream, c0->S, [&](int t, TiledFieldParams& p) {
+        b->field_tile = autotune_tile<TiledFieldParams>(b->stream, c0->S, [&](int t, TiledFieldParams& p) {
             fill_batch_field(b, t, 0, p);
         });
     {

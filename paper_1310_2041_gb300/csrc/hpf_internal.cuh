@@ -171,13 +171,18 @@ struct TiledFieldRep {
     int blk_begin;
 };
 
-struct TiledFieldParams {
+// Capacity kCap replicas: a batch passes HPF_MAX_REPLICAS records, a single
+// context one (a 64-record block is ~14 KB of kernel parameters per launch).
+template <int kCap>
+struct TiledFieldParamsT {
     int R;
     int blocks;
     const FieldCoef* coef;  // [R] in device memory
     int* flag;
-    TiledFieldRep rep[HPF_MAX_REPLICAS];
+    TiledFieldRep rep[kCap];
 };
+using TiledFieldParams = TiledFieldParamsT<HPF_MAX_REPLICAS>;
+using SingleFieldParams = TiledFieldParamsT<1>;
 
 // ------------------------------------------------------------------ device helpers
 
@@ -395,6 +400,7 @@ int field_tile_candidates();
 bool field_tile_is_plain(int id);
 void field_tile_shape(int id, int out[3]);
 void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s);
+void launch_field_tiled(const SingleFieldParams& p, int S, int tile, cudaStream_t s);
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile);
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);

@@ -71,8 +71,21 @@ __device__ __forceinline__ int wrap_near(int i, int m) {
     return i;
 }
 
-template <int S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__ TiledFieldParams p) {
+// Replica of block b: the last record with blk_begin <= b.
+template <int kCap>
+__device__ __forceinline__ int field_replica(const TiledFieldParamsT<kCap>& p) {
+    if (kCap == 1) return 0;
+    int lo = 0, hi = p.R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int S, int TX, int TY, int TZ, int kCap>
+__global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__ TiledFieldParamsT<kCap> p) {
     constexpr int BX = TX + 4, BY = TY + 2, BZ = TZ + 2;
     constexpr int BOX = BX * BY * BZ;
     constexpr int NT = TX * TY;
@@ -80,12 +93,7 @@ __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int s_ok;
 
-    int lo = 0, hi = p.R - 1;  // replica of this block
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
+    const int lo = field_replica(p);  // replica of this block
     const TiledFieldRep& r = p.rep[lo];
     const MeshGeom& g = r.g;
     const int t = (int)blockIdx.x - r.blk_begin;
@@ -186,14 +194,9 @@ __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__
 
 // The untiled candidate: one thread per node of the ghosted array, neighbours
 // loaded directly (through L1/L2), same arithmetic as the tiled kernel.
-template <int S>
-__global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ TiledFieldParams p) {
-    int lo = 0, hi = p.R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
+template <int S, int kCap>
+__global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ TiledFieldParamsT<kCap> p) {
+    const int lo = field_replica(p);
     const TiledFieldRep& r = p.rep[lo];
     const MeshGeom& g = r.g;
     const int pnode = ((int)blockIdx.x - r.blk_begin) * 256 + threadIdx.x;
@@ -242,14 +245,9 @@ __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ Til
 // extent uses scalar loads and a last pair of one node.  Each node writes its
 // ghost copies itself (x = 0 also at x = Mx, and so on), so no ghosted-index
 // arithmetic is needed.  Same arithmetic as the other candidates.
-template <int S>
-__global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ TiledFieldParams p) {
-    int lo = 0, hi = p.R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.rep[mid].blk_begin <= (int)blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
+template <int S, int kCap>
+__global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ TiledFieldParamsT<kCap> p) {
+    const int lo = field_replica(p);
     const TiledFieldRep& r = p.rep[lo];
     const MeshGeom& g = r.g;
     const int hx = (g.mx + 1) >> 1;  // pairs per row
@@ -329,20 +327,20 @@ __global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ Tile
     }
 }
 
-template <int S, int TX, int TY, int TZ>
-static void launch_tile(const TiledFieldParams& p, cudaStream_t s) {
+template <int S, int TX, int TY, int TZ, int kCap>
+static void launch_tile(const TiledFieldParamsT<kCap>& p, cudaStream_t s) {
     const size_t smem = sizeof(long long) * (size_t)(TX + 4) * (TY + 2) * (TZ + 2) * S;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_field_tiled<S, TX, TY, TZ>,
+        cudaFuncSetAttribute(k_field_tiled<S, TX, TY, TZ, kCap>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_field_tiled<S, TX, TY, TZ><<<p.blocks, TX * TY, smem, s>>>(p);
+    k_field_tiled<S, TX, TY, TZ, kCap><<<p.blocks, TX * TY, smem, s>>>(p);
 }
 
-template <int S>
-static void launch_for_species(const TiledFieldParams& p, int tile, cudaStream_t s) {
+template <int S, int kCap>
+static void launch_for_species(const TiledFieldParamsT<kCap>& p, int tile, cudaStream_t s) {
     switch (tile) {
         case 0: launch_tile<S, 32, 8, 4>(p, s); break;
         case 1: launch_tile<S, 32, 8, 8>(p, s); break;
@@ -350,12 +348,14 @@ static void launch_for_species(const TiledFieldParams& p, int tile, cudaStream_t
         case 3: launch_tile<S, 64, 4, 4>(p, s); break;
         case 4: launch_tile<S, 16, 16, 8>(p, s); break;
         case 5: launch_tile<S, 32, 4, 8>(p, s); break;
-        case kPairTile: k_field_pair<S><<<p.blocks, 256, 0, s>>>(p); break;
-        default: k_field_plain<S><<<p.blocks, 256, 0, s>>>(p); break;
+        case kPairTile: k_field_pair<S, kCap><<<p.blocks, 256, 0, s>>>(p); break;
+        default: k_field_plain<S, kCap><<<p.blocks, 256, 0, s>>>(p); break;
     }
 }
 
-void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s) {
+template <int kCap>
+static void launch_field_tiled_t(const TiledFieldParamsT<kCap>& p, int S, int tile,
+                                 cudaStream_t s) {
     if (p.blocks <= 0) return;
     switch (S) {
         case 1: launch_for_species<1>(p, tile, s); break;
@@ -363,6 +363,14 @@ void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t
         case 3: launch_for_species<3>(p, tile, s); break;
         default: launch_for_species<4>(p, tile, s); break;
     }
+}
+
+void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s) {
+    launch_field_tiled_t(p, S, tile, s);
+}
+
+void launch_field_tiled(const SingleFieldParams& p, int S, int tile, cudaStream_t s) {
+    launch_field_tiled_t(p, S, tile, s);
 }
 
 // ------------------------------------------------------------------ tensor maps
