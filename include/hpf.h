@@ -74,6 +74,10 @@ typedef struct {
     uint64_t seed;        /* Philox key of the thermostat noise */
     int32_t field_every;  /* refresh the density field when step % field_every == 0 */
     int32_t sort_every;   /* re-sort beads every this many steps (0: only in hpf_set_state) */
+    int32_t force_mode;   /* field force: 0 = the trilinear interpolation of the nodal
+                             central-difference gradient (Algorithm 1, kernels 3-4);
+                             1 = the exact derivative of the CIC field energy (the gradient
+                             of the trilinear interpolant of V; conserves energy) */
 } hpf_params;
 
 /* Text for a status code (static storage). */
@@ -240,7 +244,7 @@ hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
  * at most 64 beads (the warp-segment form); replicas with longer chains make
  * hpf_batch_step fall back to stepping the replicas one after another.
  * Requirements checked by hpf_batch_init (HPF_ERR_INVALID): 1 <= n_replicas
- * <= HPF_MAX_REPLICAS, equal n_species, field_every and sort_every. */
+ * <= HPF_MAX_REPLICAS, equal n_species, field_every, sort_every and force_mode. */
 #define HPF_MAX_REPLICAS 64
 
 typedef struct hpf_batch hpf_batch;
@@ -392,7 +396,8 @@ hpf_status hpf_step_learned(hpf_ctx* ctx, hpf_prop* prop, int32_t n_windows, int
  * The call computes, with no context, the field force that hpf_forces gives
  * with HPF_FORCE_FIELD right after loading these positions: CIC scatter of the
  * beads, V and grad V of that mesh, trilinear gather -grad V_T at every bead.
- * Only n_species, mesh, box, kT, rho0, inv_kappa and chi of `params` are used.
+ * Only n_species, mesh, box, kT, rho0, inv_kappa and chi of `params` are used
+ * (the force is always the interpolated-gradient one, force_mode 0).
  *   pos   [n][3] float32 positions, device memory of the current device
  *   type  [n]    int32 species; a species outside [0, n_species) gets a NaN
  *                force and adds nothing to the density

@@ -184,6 +184,7 @@ hpf_status validate_params(const hpf_params* p) {
             if (!isfinite(a) || a != b) return HPF_ERR_INVALID;  // chi must be symmetric
         }
     if (p->field_every < 1 || p->sort_every < 0) return HPF_ERR_INVALID;
+    if (p->force_mode != 0 && p->force_mode != 1) return HPF_ERR_INVALID;
     return HPF_OK;
 }
 
@@ -230,6 +231,7 @@ void derive_constants(hpf_ctx* c) {
         s.rk0[r] = s.seed_lo + (uint32_t)r * 0x9E3779B9u;
         s.rk1[r] = s.seed_hi + (uint32_t)r * 0xBB67AE85u;
     }
+    s.exact = p.force_mode;
     EnergyConsts& e = c->ec;
     memset(&e, 0, sizeof e);
     e.half_dt_m = 0.5 * p.dt / p.mass;
@@ -1111,7 +1113,8 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
     for (int r = 1; r < n_replicas; ++r)
         if (params[r].n_species != params[0].n_species ||
             params[r].field_every != params[0].field_every ||
-            params[r].sort_every != params[0].sort_every)
+            params[r].sort_every != params[0].sort_every ||
+            params[r].force_mode != params[0].force_mode)
             return HPF_ERR_INVALID;
     hpf_batch* b = new hpf_batch();
     b->R = n_replicas;

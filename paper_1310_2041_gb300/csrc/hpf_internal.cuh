@@ -54,6 +54,7 @@ struct StepConsts {
     float r0;
     uint32_t seed_lo, seed_hi;
     uint32_t rk0[10], rk1[10];  // Philox round keys: seed + r * (Weyl increments)
+    int exact;                  // field force: 0 interpolated gradient, 1 exact energy gradient
 };
 
 // Coefficients of the field stencil: gradient of V_K from integer central
@@ -337,6 +338,34 @@ __device__ __forceinline__ void gather_field(const float4* __restrict__ Gt, cons
     fx -= gx;
     fy -= gy;
     fz -= gz;
+}
+
+// The exact derivative of the CIC field energy at a bead: minus the gradient
+// of the trilinear interpolant of V_T (the .w of the ghosted field array),
+// -sum over the 8 corners of V_c grad w_c with grad w = (+-1/h) per axis.
+__device__ __forceinline__ void gather_field_exact(const float4* __restrict__ Gt,
+                                                   const MeshGeom& g, const AxisCoord& ax,
+                                                   const AxisCoord& ay, const AxisCoord& az,
+                                                   float& fx, float& fy, float& fz) {
+    const float wx1 = ax.f, wx0 = 1.0f - ax.f;
+    const float wy1 = ay.f, wy0 = 1.0f - ay.f;
+    const float wz1 = az.f, wz0 = 1.0f - az.f;
+    const int o00 = az.lo * g.gxy + ay.lo * g.gx + ax.lo;
+    const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
+    const float v000 = __ldg(Gt + o00).w, v100 = __ldg(Gt + o00 + 1).w;
+    const float v010 = __ldg(Gt + o01).w, v110 = __ldg(Gt + o01 + 1).w;
+    const float v001 = __ldg(Gt + o10).w, v101 = __ldg(Gt + o10 + 1).w;
+    const float v011 = __ldg(Gt + o11).w, v111 = __ldg(Gt + o11 + 1).w;
+    // d/dfx, d/dfy, d/dfz of the interpolant
+    const float dx = wz0 * (wy0 * (v100 - v000) + wy1 * (v110 - v010)) +
+                     wz1 * (wy0 * (v101 - v001) + wy1 * (v111 - v011));
+    const float dy = wz0 * (wx0 * (v010 - v000) + wx1 * (v110 - v100)) +
+                     wz1 * (wx0 * (v011 - v001) + wx1 * (v111 - v101));
+    const float dz = wy0 * (wx0 * (v001 - v000) + wx1 * (v101 - v100)) +
+                     wy1 * (wx0 * (v011 - v010) + wx1 * (v111 - v110));
+    fx = fmaf(-g.inv_h[0], dx, fx);
+    fy = fmaf(-g.inv_h[1], dy, fy);
+    fz = fmaf(-g.inv_h[2], dz, fz);
 }
 
 // Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (1 - r0 / r) d, d = x_i - x_j,

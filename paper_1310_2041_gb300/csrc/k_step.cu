@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __r
         const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
         const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
         const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
-        gather_field(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
+        if (c.exact) gather_field_exact(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
+        else gather_field(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
     }
     const uint32_t tag = m & kTagMask;
     F_tag[3 * tag] = fx;
@@ -80,6 +81,9 @@ __device__ __forceinline__ int cell_base(const MeshGeom& g, float flx, float fly
     return (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
 }
 
+// kExact: planes 0 and 1 hold the trilinear polynomial of V instead (the
+// exact-energy-gradient force differentiates it).
+template <bool kExact>
 __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
                                                 float flx, float fly, float flz,
                                                 float4* __restrict__ cache, int t,
@@ -103,9 +107,13 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
         cache[(2 * j) * stride + t] = make_float4(a0, a1, a2, a3);                               \
         cache[(2 * j + 1) * stride + t] = make_float4(a4, a5, a6, a7);                           \
     }
-    HPF_COEF(x, 0)
-    HPF_COEF(y, 1)
-    HPF_COEF(z, 2)
+    if (kExact) {
+        HPF_COEF(w, 0)
+    } else {
+        HPF_COEF(x, 0)
+        HPF_COEF(y, 1)
+        HPF_COEF(z, 2)
+    }
 #undef HPF_COEF
 }
 
@@ -122,12 +130,26 @@ __device__ __forceinline__ float cell_poly(const float4 lo, const float4 hi, flo
     return fmaf(fz, lo.w, v);
 }
 
+template <bool kExact>
 __device__ __forceinline__ void eval_cell_cache(const float4* __restrict__ cache, int t, float fx,
                                                 float fy, float fz, float& Fx, float& Fy,
-                                                float& Fz, int stride = kStepBlock) {
-    Fx -= cell_poly(cache[0 * stride + t], cache[1 * stride + t], fx, fy, fz);
-    Fy -= cell_poly(cache[2 * stride + t], cache[3 * stride + t], fx, fy, fz);
-    Fz -= cell_poly(cache[4 * stride + t], cache[5 * stride + t], fx, fy, fz);
+                                                float& Fz, const MeshGeom& g,
+                                                int stride = kStepBlock) {
+    if (kExact) {
+        // V = a0 + a1 fx + a2 fy + a3 fz + a4 fx fy + a5 fx fz + a6 fy fz + a7 fx fy fz;
+        // F = -(1/h) dV/df per axis
+        const float4 lo = cache[t], hi = cache[stride + t];
+        const float dx = fmaf(fz, fmaf(fy, hi.w, hi.y), fmaf(fy, hi.x, lo.y));
+        const float dy = fmaf(fz, fmaf(fx, hi.w, hi.z), fmaf(fx, hi.x, lo.z));
+        const float dz = fmaf(fy, fmaf(fx, hi.w, hi.z), fmaf(fx, hi.y, lo.w));
+        Fx = fmaf(-g.inv_h[0], dx, Fx);
+        Fy = fmaf(-g.inv_h[1], dy, Fy);
+        Fz = fmaf(-g.inv_h[2], dz, Fz);
+    } else {
+        Fx -= cell_poly(cache[0 * stride + t], cache[1 * stride + t], fx, fy, fz);
+        Fy -= cell_poly(cache[2 * stride + t], cache[3 * stride + t], fx, fy, fz);
+        Fz -= cell_poly(cache[4 * stride + t], cache[5 * stride + t], fx, fy, fz);
+    }
 }
 
 // A warp reads shared positions of its own lanes and of the edge lanes of the
@@ -144,7 +166,7 @@ __device__ __forceinline__ void neighbour_sync(int w) {
     if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
-template <bool kNoise>
+template <bool kNoise, bool kExact>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
                                                         int halo, int n_sub, long long step0,
@@ -188,14 +210,14 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
                     s2 = __fmul_rn(z, g.inv_h[2]);
         const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
         if (flx != cfx || fly != cfy || flz != cfz) {
-            fill_cell_cache(Gt, g, flx, fly, flz, cache, t);
+            fill_cell_cache<kExact>(Gt, g, flx, fly, flz, cache, t);
             cfx = flx;
             cfy = fly;
             cfz = flz;
         }
         float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
-        eval_cell_cache(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly), __fsub_rn(s2, flz), fx,
-                        fy, fz);
+        eval_cell_cache<kExact>(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly),
+                                __fsub_rn(s2, flz), fx, fy, fz, g);
         if (kNoise) {
             float nx, ny, nz;
             gauss3(c, tag, step0 + k, nx, ny, nz);
@@ -239,27 +261,36 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     }
 }
 
-void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
-                 long long step0, MeshGeom g, const float4* G, StepConsts c,
-                 unsigned long long* D_next, int* flag, cudaStream_t s) {
-    if (n <= 0 || n_sub <= 0) return;
+template <bool kNoise, bool kExact>
+static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
+                          long long step0, MeshGeom g, const float4* G, StepConsts c,
+                          unsigned long long* D_next, int* flag, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kStepSmem);
-        cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<kNoise, kExact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kStepSmem);
         attr_set = true;
     }
     const int halo = n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    if (c.sigma > 0.f)
-        k_step<true><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub, step0, g,
-                                                           G, c, D_next, flag);
+    k_step<kNoise, kExact><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub,
+                                                                 step0, g, G, c, D_next, flag);
+}
+
+void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
+                 long long step0, MeshGeom g, const float4* G, StepConsts c,
+                 unsigned long long* D_next, int* flag, cudaStream_t s) {
+    if (n <= 0 || n_sub <= 0) return;
+    const bool noise = c.sigma > 0.f;
+    if (noise && c.exact)
+        launch_step_t<true, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+    else if (noise)
+        launch_step_t<true, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+    else if (c.exact)
+        launch_step_t<false, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     else
-        k_step<false><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub, step0,
-                                                            g, G, c, D_next, flag);
+        launch_step_t<false, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
 }
 
 // ------------------------------------------------------------------ A6, warp form
@@ -284,6 +315,7 @@ struct Bead {
 
 // The bead's cell: refill its cache of the cell polynomial when the bead
 // has entered another cell; returns the offsets inside the cell.
+template <bool kExact>
 __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G, const MeshGeom& g,
                                            float4* __restrict__ cache, int slot, float& f0,
                                            float& f1, float& f2) {
@@ -291,8 +323,8 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
                 s2 = __fmul_rn(b.z, g.inv_h[2]);
     const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
     if (flx != b.cfx || fly != b.cfy || flz != b.cfz) {
-        fill_cell_cache(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx, fly, flz,
-                        cache, slot, 2 * kWarpBlock);
+        fill_cell_cache<kExact>(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx,
+                                fly, flz, cache, slot, 2 * kWarpBlock);
         b.cfx = flx;
         b.cfy = fly;
         b.cfz = flz;
@@ -305,13 +337,13 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
 // Kick of one bead: field (cached cell polynomial at offsets f), friction,
 // noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
 // chain neighbours.
-template <bool kNoise>
+template <bool kNoise, bool kExact>
 __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
                                           float ny, float nz, float bx, float by, float bz,
-                                          const StepConsts& c, const float4* __restrict__ cache,
-                                          int slot) {
+                                          const StepConsts& c, const MeshGeom& g,
+                                          const float4* __restrict__ cache, int slot) {
     float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
-    eval_cell_cache(cache, slot, f0, f1, f2, fx, fy, fz, 2 * kWarpBlock);
+    eval_cell_cache<kExact>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
     if (kNoise) {
         fx = fmaf(c.sigma, nx, fx);
         fy = fmaf(c.sigma, ny, fy);
@@ -349,7 +381,7 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <bool kNoise>
+template <bool kNoise, bool kExact>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -394,17 +426,17 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
         const float uz = __shfl_up_sync(0xffffffffu, nz, 1);
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
-        cell_check(b0, G, g, wcache, tid, f00, f01, f02);
-        cell_check(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
+        cell_check<kExact>(b0, G, g, wcache, tid, f00, f01, f02);
+        cell_check<kExact>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
         float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
         if (kNoise) {
             gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kNoise>(b0, f00, f01, f02, g0x, g0y, g0z, p0 ? ax - ux : ax,
-                          p0 ? ay - uy : ay, p0 ? az - uz : az, c, wcache, tid);
-        kick_bead<kNoise>(b1, f10, f11, f12, g1x, g1y, g1z, nx - ax, ny - ay, nz - az, c, wcache,
-                          kWarpBlock + tid);
+        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, p0 ? ax - ux : ax,
+                                  p0 ? ay - uy : ay, p0 ? az - uz : az, c, g, wcache, tid);
+        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, nx - ax, ny - ay, nz - az, c,
+                                  g, wcache, kWarpBlock + tid);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
         b0.z = fmaf(c.dt, b0.vz, b0.z);
@@ -420,7 +452,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <bool kNoise, int kCap>
+template <bool kNoise, int kCap, bool kExact>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
     extern __shared__ float4 wcache[];
@@ -450,31 +482,50 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
         }
         const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
-        advance_segment<kNoise>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta, rp.seg_start[s],
+        advance_segment<kNoise, kExact>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta, rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
     }
 }
 
+template <int kCap>
+static void warp_attrs() {
+    cudaFuncSetAttribute(k_step_warp_batch<true, kCap, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<false, kCap, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<true, kCap, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<false, kCap, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+}
+
 static int warp_grid_cap() {
     static int cap = 0;
     if (!cap) {
-        cudaFuncSetAttribute(k_step_warp_batch<true, HPF_MAX_REPLICAS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp_batch<false, HPF_MAX_REPLICAS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp_batch<true, 1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-        cudaFuncSetAttribute(k_step_warp_batch<false, 1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+        warp_attrs<HPF_MAX_REPLICAS>();
+        warp_attrs<1>();
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS>, kWarpBlock, kWarpSmem);
+            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS, false>, kWarpBlock, kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     return cap;
+}
+
+template <int kCap>
+static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, bool noise, bool exact,
+                        cudaStream_t s) {
+    if (noise && exact)
+        k_step_warp_batch<true, kCap, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else if (noise)
+        k_step_warp_batch<true, kCap, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else if (exact)
+        k_step_warp_batch<false, kCap, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else
+        k_step_warp_batch<false, kCap, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
@@ -483,10 +534,7 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool no
     const int cap = warp_grid_cap();
     const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    if (noise)
-        k_step_warp_batch<true, HPF_MAX_REPLICAS><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
-    else
-        k_step_warp_batch<false, HPF_MAX_REPLICAS><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    launch_warp(p, blocks, noise, p.rep[0].c.exact != 0, s);  // replicas share the force mode
 }
 
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise,
@@ -495,10 +543,7 @@ void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise,
     const int cap = warp_grid_cap();
     const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    if (noise)
-        k_step_warp_batch<true, 1><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
-    else
-        k_step_warp_batch<false, 1><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    launch_warp(p, blocks, noise, p.rep[0].c.exact != 0, s);
 }
 
 
@@ -560,8 +605,9 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
         const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
         const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
-        gather_field(G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes, g, ax, ay, az, fx,
-                     fy, fz);
+        const float4* Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
+        if (c.exact) gather_field_exact(Gt, g, ax, ay, az, fx, fy, fz);
+        else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
         if (c.sigma > 0.f) {
             float nx, ny, nz;
             gauss3(c, m & kTagMask, step, nx, ny, nz);

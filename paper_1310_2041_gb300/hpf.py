@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("field_every", ctypes.c_int32),
         ("sort_every", ctypes.c_int32),
+        ("force_mode", ctypes.c_int32),
     ]
 
 
@@ -147,7 +148,7 @@ def load():
 
 def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
                 bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
-                sort_every=0, **_ignored) -> Params:
+                sort_every=0, force_mode=0, **_ignored) -> Params:
     p = Params()
     p.n_beads, p.n_species = int(n_beads), int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -166,6 +167,7 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
                                                   float(dt), float(gamma))
     p.seed = int(seed)
     p.field_every, p.sort_every = int(field_every), int(sort_every)
+    p.force_mode = int(force_mode)
     return p
 
 
