@@ -65,6 +65,8 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("field_every", ctypes.c_int32),
         ("force_mode", ctypes.c_int32),
+        ("angle_k", ctypes.c_double),
+        ("angle_cos0", ctypes.c_double),
     ]
 
 
@@ -94,6 +96,9 @@ def lib():
             L.orc_bond_force.argtypes = [pp, i64, P(f64), P(i32), P(i32), P(f64)]
             L.orc_bond_energy.argtypes = [pp, i64, P(f64), P(i32), P(i32)]
             L.orc_bond_energy.restype = f64
+            L.orc_angle_force.argtypes = [pp, i64, P(f64), P(i32), P(i32), P(f64)]
+            L.orc_angle_energy.argtypes = [pp, i64, P(f64), P(i32), P(i32)]
+            L.orc_angle_energy.restype = f64
             L.orc_field_energy.argtypes = [pp, P(i64)]
             L.orc_field_energy.restype = f64
             L.orc_field_force_exact.argtypes = [pp, i64, P(f64), P(i32), P(f64), P(f64)]
@@ -109,7 +114,7 @@ def lib():
 
 def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None, bond_k=4.0,
                 bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1, force_mode=0,
-                **_ignored):
+                angle_k=0.0, angle_cos0=-1.0, **_ignored):
     p = Params()
     p.n_species = int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -129,6 +134,7 @@ def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
     p.seed = int(seed)
     p.field_every = int(field_every)
     p.force_mode = int(force_mode)
+    p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
     return p
 
 
@@ -219,6 +225,22 @@ def bond_force(p: Params, pos, bonds) -> np.ndarray:
     lib().orc_bond_force(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
                          _p(BL, ctypes.c_int32), _p(BN, ctypes.c_int32), _p(F, ctypes.c_double))
     return F
+
+
+def angle_force(p: Params, pos, bonds) -> np.ndarray:
+    pos = _f64(pos, (-1, 3))
+    BL, BN = bond_table(pos.shape[0], bonds)
+    F = np.zeros_like(pos)
+    lib().orc_angle_force(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                          _p(BL, ctypes.c_int32), _p(BN, ctypes.c_int32), _p(F, ctypes.c_double))
+    return F
+
+
+def angle_energy(p: Params, pos, bonds) -> float:
+    pos = _f64(pos, (-1, 3))
+    BL, BN = bond_table(pos.shape[0], bonds)
+    return lib().orc_angle_energy(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                                  _p(BL, ctypes.c_int32), _p(BN, ctypes.c_int32))
 
 
 def bond_energy(p: Params, pos, bonds) -> float:

@@ -349,6 +349,66 @@ void orc_bond_force(const orc_params* p, int64_t n, const double* pos, const int
     }
 }
 
+/* Angles (section "Bonded forces", the cosine form).  With u = x_a - x_j,
+ * w = x_b - x_j and c = u.w / (|u| |w|) = cos theta:
+ *   dc/dx_a = w / (|u| |w|) - c u / |u|^2,  dc/dx_b = u / (|u| |w|) - c w / |w|^2,
+ *   dc/dx_j = -(dc/dx_a + dc/dx_b),
+ * and F = -2 angle_k (c - angle_cos0) dc/dx on each of the three beads. */
+static double angle_cos(const double* pos, int64_t a, int64_t j, int64_t b, double u[3],
+                        double w[3], double* uu, double* ww)
+{
+    double uw = 0.0;
+    *uu = 0.0;
+    *ww = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        u[d] = pos[3 * a + d] - pos[3 * j + d];
+        w[d] = pos[3 * b + d] - pos[3 * j + d];
+        uw += u[d] * w[d];
+        *uu += u[d] * u[d];
+        *ww += w[d] * w[d];
+    }
+    return uw / sqrt(*uu * *ww);
+}
+
+void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                     const int32_t* BN, double* F)
+{
+    for (int64_t i = 0; i < 3 * n; ++i) F[i] = 0.0;
+    if (p->angle_k == 0.0) return;
+    for (int64_t j = 0; j < n; ++j)
+        for (int k1 = 0; k1 < BN[j]; ++k1)
+            for (int k2 = k1 + 1; k2 < BN[j]; ++k2) {
+                const int64_t a = BL[(int64_t)k1 * n + j], b = BL[(int64_t)k2 * n + j];
+                double u[3], w[3], uu, ww;
+                const double c = angle_cos(pos, a, j, b, u, w, &uu, &ww);
+                const double g = -2.0 * p->angle_k * (c - p->angle_cos0);
+                const double inv = 1.0 / sqrt(uu * ww);
+                for (int d = 0; d < 3; ++d) {
+                    const double da = w[d] * inv - c * u[d] / uu;
+                    const double db = u[d] * inv - c * w[d] / ww;
+                    F[3 * a + d] += g * da;
+                    F[3 * b + d] += g * db;
+                    F[3 * j + d] -= g * (da + db);
+                }
+            }
+}
+
+double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                        const int32_t* BN)
+{
+    long double e = 0.0L;
+    if (p->angle_k == 0.0) return 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        for (int k1 = 0; k1 < BN[j]; ++k1)
+            for (int k2 = k1 + 1; k2 < BN[j]; ++k2) {
+                double u[3], w[3], uu, ww;
+                const double c = angle_cos(pos, BL[(int64_t)k1 * n + j], j,
+                                           BL[(int64_t)k2 * n + j], u, w, &uu, &ww);
+                e += (long double)(p->angle_k * (c - p->angle_cos0) * (c - p->angle_cos0));
+            }
+    return (double)e;
+}
+
 double orc_bond_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
                        const int32_t* BN)
 {
@@ -427,6 +487,12 @@ static void conservative_force(const orc_params* p, int64_t n, const double* pos
     else
         orc_field_force(p, n, pos, type, G, Ff);
     orc_bond_force(p, n, pos, BL, BN, Fb);
+    if (p->angle_k != 0.0) {
+        double* Fa = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+        orc_angle_force(p, n, pos, BL, BN, Fa);
+        for (int64_t i = 0; i < 3 * n; ++i) Fb[i] += Fa[i];
+        free(Fa);
+    }
     for (int64_t i = 0; i < 3 * n; ++i) Fc[i] = Ff[i] + Fb[i];
 }
 
@@ -451,7 +517,8 @@ void orc_energy(const orc_params* p, int64_t n, const double* pos, const double*
         }
     orc_scatter(p, n, pos, type, D);
     double w = orc_field_energy(p, D);
-    double ub = orc_bond_energy(p, n, pos, BL, BN);
+    /* the bonded entry: bonds and angles */
+    double ub = orc_bond_energy(p, n, pos, BL, BN) + orc_angle_energy(p, n, pos, BL, BN);
     out[0] = (double)ke;
     out[1] = ub;
     out[2] = w;

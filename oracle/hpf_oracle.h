@@ -50,6 +50,8 @@ typedef struct {
     int32_t field_every;
     int32_t force_mode; /* 0: interpolated central-difference gradient (Algorithm 1);
                            1: exact derivative of the CIC field energy (pinning variant) */
+    double angle_k;     /* U = angle_k (cos theta - angle_cos0)^2 per bonded triplet */
+    double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles */
 } orc_params;
 
 int orc_num_threads(void);
@@ -73,6 +75,13 @@ void orc_field_force(const orc_params* p, int64_t n, const double* pos, const in
 /* Variant force: exact derivative of the CIC field energy for the potential V. */
 void orc_field_force_exact(const orc_params* p, int64_t n, const double* pos, const int32_t* type,
                            const double* V, double* F);
+/* Angle forces and energy: every pair (a, b) of bond partners of a bead j
+ * forms the angle theta at j between x_a - x_j and x_b - x_j (pi for a
+ * straight chain), with U = angle_k (cos theta - angle_cos0)^2. */
+void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                     const int32_t* BN, double* F);
+double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                        const int32_t* BN);
 /* Build the BL / BN bond table from a list of bonded pairs; returns 0 or -1 on overflow. */
 int orc_bond_table(int64_t n, int64_t n_bonds, const int32_t* pairs, int32_t* BL, int32_t* BN);
 /* Harmonic bond force per bead, each bond evaluated from both ends. */
