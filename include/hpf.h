@@ -78,6 +78,9 @@ typedef struct {
                              central-difference gradient (Algorithm 1, kernels 3-4);
                              1 = the exact derivative of the CIC field energy (the gradient
                              of the trilinear interpolant of V; conserves energy) */
+    double angle_k;       /* angle potential U = angle_k (cos theta - angle_cos0)^2 for every */
+    double angle_cos0;    /* bonded triplet (section "Bonded forces", cosine form), theta the
+                             angle at the middle bead (pi for a straight chain); 0: none */
 } hpf_params;
 
 /* Text for a status code (static storage). */
@@ -244,7 +247,10 @@ hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
  * at most 64 beads (the warp-segment form); replicas with longer chains make
  * hpf_batch_step fall back to stepping the replicas one after another.
  * Requirements checked by hpf_batch_init (HPF_ERR_INVALID): 1 <= n_replicas
- * <= HPF_MAX_REPLICAS, equal n_species, field_every, sort_every and force_mode. */
+ * <= HPF_MAX_REPLICAS, equal n_species, field_every, sort_every and force_mode,
+ * and angles in all replicas or in none (their constants may differ): the
+ * batch runs one kernel form for all, and each replica's result is then the
+ * bits of its own context. */
 #define HPF_MAX_REPLICAS 64
 
 typedef struct hpf_batch hpf_batch;

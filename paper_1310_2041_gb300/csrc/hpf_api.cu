@@ -185,6 +185,8 @@ hpf_status validate_params(const hpf_params* p) {
         }
     if (p->field_every < 1 || p->sort_every < 0) return HPF_ERR_INVALID;
     if (p->force_mode != 0 && p->force_mode != 1) return HPF_ERR_INVALID;
+    if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
+        return HPF_ERR_INVALID;
     return HPF_OK;
 }
 
@@ -232,6 +234,8 @@ void derive_constants(hpf_ctx* c) {
         s.rk1[r] = s.seed_hi + (uint32_t)r * 0xBB67AE85u;
     }
     s.exact = p.force_mode;
+    s.two_ka = (float)(2.0 * p.angle_k);
+    s.cos0 = (float)p.angle_cos0;
     EnergyConsts& e = c->ec;
     memset(&e, 0, sizeof e);
     e.half_dt_m = 0.5 * p.dt / p.mass;
@@ -239,6 +243,8 @@ void derive_constants(hpf_ctx* c) {
     e.bond_k = p.bond_k;
     e.r0 = p.bond_r0;
     e.kT = p.kT;
+    e.angle_k = p.angle_k;
+    e.cos0 = p.angle_cos0;
     e.inv_kappa = p.inv_kappa;
     e.phi_c = phi_c;
     e.w_scale = p.rho0 * vol;
@@ -1114,7 +1120,8 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
         if (params[r].n_species != params[0].n_species ||
             params[r].field_every != params[0].field_every ||
             params[r].sort_every != params[0].sort_every ||
-            params[r].force_mode != params[0].force_mode)
+            params[r].force_mode != params[0].force_mode ||
+            (params[r].angle_k != 0.0) != (params[0].angle_k != 0.0))
             return HPF_ERR_INVALID;
     hpf_batch* b = new hpf_batch();
     b->R = n_replicas;

@@ -55,6 +55,8 @@ struct StepConsts {
     uint32_t seed_lo, seed_hi;
     uint32_t rk0[10], rk1[10];  // Philox round keys: seed + r * (Weyl increments)
     int exact;                  // field force: 0 interpolated gradient, 1 exact energy gradient
+    float two_ka;               // 2 * angle_k (0: no angle terms)
+    float cos0;                 // cos of the equilibrium angle
 };
 
 // Coefficients of the field stencil: gradient of V_K from integer central
@@ -81,6 +83,7 @@ struct EnergyConsts {
     double chi[HPF_MAX_SPECIES][HPF_MAX_SPECIES];
     int S;
     int n;
+    double angle_k, cos0;  // angle potential
 };
 
 struct StateBuf {
@@ -380,6 +383,31 @@ __device__ __forceinline__ void bond_force(float dx, float dy, float dz, float t
     fx += s * dx;
     fy += s * dy;
     fz += s * dz;
+}
+
+// Angle U = k (cos theta - cos0)^2 at a middle bead j with u = x_a - x_j,
+// w = x_b - x_j: forces on the end beads a and b (the middle bead takes minus
+// their sum), -2k (c - cos0) dc/dx with dc/dx_a = w / (|u||w|) - c u / |u|^2
+// and dc/dx_b symmetric.  Each arm length is clamped separately, so every
+// intermediate stays finite even for zero vectors (lanes without beads) and
+// two_ka = 0 gives exactly zero.
+__device__ __forceinline__ void angle_force(float ux, float uy, float uz, float wx, float wy,
+                                            float wz, float two_ka, float cos0, float& fax,
+                                            float& fay, float& faz, float& fbx, float& fby,
+                                            float& fbz) {
+    const float uu = fmaxf(ux * ux + uy * uy + uz * uz, 1e-30f);
+    const float ww = fmaxf(wx * wx + wy * wy + wz * wz, 1e-30f);
+    const float uw = ux * wx + uy * wy + uz * wz;
+    const float inv = rsqrtf(uu) * rsqrtf(ww);
+    const float c = uw * inv;
+    const float g = -two_ka * (c - cos0);
+    const float ca = c / uu, cb = c / ww;
+    fax = g * (wx * inv - ca * ux);
+    fay = g * (wy * inv - ca * uy);
+    faz = g * (wz * inv - ca * uz);
+    fbx = g * (ux * inv - cb * wx);
+    fby = g * (uy * inv - cb * wy);
+    fbz = g * (uz * inv - cb * wz);
 }
 
 // ------------------------------------------------------------------ launchers

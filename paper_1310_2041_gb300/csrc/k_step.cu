@@ -11,6 +11,39 @@ int step_halo_max() { return kHaloMax; }
 // ------------------------------------------------------------------ A4 + A5 forces
 //
 // Conservative force at the current positions, written in tag order.
+// The three angles bead i belongs to (centred at i - 1, i and i + 1), read
+// from global memory in storage order (chains are contiguous there).
+__device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32_t* __restrict__ meta,
+                                                int i, uint32_t m, const StepConsts& c, float& fx,
+                                                float& fy, float& fz) {
+    const bool hp = (m & kBondPrev) != 0, hn = (m & kBondNext) != 0;
+    const float x = st.x[i], y = st.y[i], z = st.z[i];
+    float ax, ay, az, bx, by, bz;
+    if (hp && hn) {
+        angle_force(st.x[i - 1] - x, st.y[i - 1] - y, st.z[i - 1] - z, st.x[i + 1] - x,
+                    st.y[i + 1] - y, st.z[i + 1] - z, c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx -= ax + bx;
+        fy -= ay + by;
+        fz -= az + bz;
+    }
+    if (hp && (meta[i - 1] & kBondPrev)) {
+        const float xp = st.x[i - 1], yp = st.y[i - 1], zp = st.z[i - 1];
+        angle_force(st.x[i - 2] - xp, st.y[i - 2] - yp, st.z[i - 2] - zp, x - xp, y - yp, z - zp,
+                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx += bx;
+        fy += by;
+        fz += bz;
+    }
+    if (hn && (meta[i + 1] & kBondNext)) {
+        const float xn = st.x[i + 1], yn = st.y[i + 1], zn = st.z[i + 1];
+        angle_force(x - xn, y - yn, z - zn, st.x[i + 2] - xn, st.y[i + 2] - yn, st.z[i + 2] - zn,
+                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx += ax;
+        fy += ay;
+        fz += az;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __restrict__ meta,
                                                 int n, MeshGeom g, const float4* __restrict__ G,
                                                 StepConsts c, int which,
@@ -25,6 +58,7 @@ __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __r
             bond_force(x - st.x[i - 1], y - st.y[i - 1], z - st.z[i - 1], c.two_k, c.r0, fx, fy, fz);
         if (m & kBondNext)
             bond_force(x - st.x[i + 1], y - st.y[i + 1], z - st.z[i + 1], c.two_k, c.r0, fx, fy, fz);
+        if (c.two_ka != 0.f) angle_forces_of(st, meta, i, m, c, fx, fy, fz);
     }
     if (which & HPF_FORCE_FIELD) {
         const int T = (m >> kTypeShift) & kTypeMask;
@@ -166,7 +200,7 @@ __device__ __forceinline__ void neighbour_sync(int w) {
     if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
-template <bool kNoise, bool kExact>
+template <bool kNoise, bool kExact, bool kAngles>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
                                                         int halo, int n_sub, long long step0,
@@ -197,6 +231,12 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     // out-of-range threads only fill their shared-memory slot
     const bool has_prev = live && (m & kBondPrev) && t > 0;
     const bool has_next = live && (m & kBondNext) && t + 1 < kStepBlock;
+    // bond flags of the whole window, for the angles centred at the neighbours
+    __shared__ unsigned char s_bonds[kStepBlock];
+    if (kAngles) {
+        s_bonds[t] = (unsigned char)((has_prev ? 1 : 0) | (has_next ? 2 : 0));
+        __syncthreads();
+    }
     const uint32_t tag = m & kTagMask;
     const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
     float cfx = __int_as_float(0x7fc00000), cfy = cfx, cfz = cfx;  // cached cell: none
@@ -230,6 +270,39 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
                    z - sz[b * kStepBlock + tp], has_prev ? c.two_k : 0.0f, c.r0, fx, fy, fz);
         bond_force(x - sx[b * kStepBlock + tn], y - sy[b * kStepBlock + tn],
                    z - sz[b * kStepBlock + tn], has_next ? c.two_k : 0.0f, c.r0, fx, fy, fz);
+        if (kAngles) {
+            // the three angles this bead belongs to: centred at t - 1, t and t + 1
+            const int tp2 = (has_prev && t >= 2) ? t - 2 : t;
+            const int tn2 = (has_next && t + 2 < kStepBlock) ? t + 2 : t;
+            const bool left = has_prev && t >= 2 && (s_bonds[t - 1] & 1);
+            const bool right = has_next && t + 2 < kStepBlock && (s_bonds[t + 1] & 2);
+            const float xp = sx[b * kStepBlock + tp], yp = sy[b * kStepBlock + tp],
+                        zp = sz[b * kStepBlock + tp];
+            const float xn = sx[b * kStepBlock + tn], yn = sy[b * kStepBlock + tn],
+                        zn = sz[b * kStepBlock + tn];
+            float ax, ay, az, bx, by, bz;
+            // centred at t: this bead takes minus both end shares
+            angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z,
+                        (has_prev && has_next) ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by,
+                        bz);
+            fx -= ax + bx;
+            fy -= ay + by;
+            fz -= az + bz;
+            // centred at t - 1 (ends t - 2 and t): this bead is end b
+            angle_force(sx[b * kStepBlock + tp2] - xp, sy[b * kStepBlock + tp2] - yp,
+                        sz[b * kStepBlock + tp2] - zp, x - xp, y - yp, z - zp,
+                        left ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by, bz);
+            fx += bx;
+            fy += by;
+            fz += bz;
+            // centred at t + 1 (ends t and t + 2): this bead is end a
+            angle_force(x - xn, y - yn, z - zn, sx[b * kStepBlock + tn2] - xn,
+                        sy[b * kStepBlock + tn2] - yn, sz[b * kStepBlock + tn2] - zn,
+                        right ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by, bz);
+            fx += ax;
+            fy += ay;
+            fz += az;
+        }
         vx = fmaf(c.dt_m, fx, vx);
         vy = fmaf(c.dt_m, fy, vy);
         vz = fmaf(c.dt_m, fz, vz);
@@ -261,21 +334,35 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     }
 }
 
-template <bool kNoise, bool kExact>
+template <bool kNoise, bool kExact, bool kAngles>
 static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_step<kNoise, kExact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kStepSmem);
+        cudaFuncSetAttribute(k_step<kNoise, kExact, kAngles>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
         attr_set = true;
     }
-    const int halo = n_sub;
+    // a bead's update after k sub-steps depends on beads up to k (bonds) or 2k
+    // (angles) places away along its chain
+    const int halo = kAngles ? 2 * n_sub : n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<kNoise, kExact><<<blocks, kStepBlock, kStepSmem, s>>>(in, out, meta, n, halo, n_sub,
-                                                                 step0, g, G, c, D_next, flag);
+    k_step<kNoise, kExact, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
+        in, out, meta, n, halo, n_sub, step0, g, G, c, D_next, flag);
+}
+
+template <bool kNoise, bool kExact>
+static void launch_step_a(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
+                          long long step0, MeshGeom g, const float4* G, StepConsts c,
+                          unsigned long long* D_next, int* flag, cudaStream_t s) {
+    if (c.two_ka != 0.f)
+        launch_step_t<kNoise, kExact, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
+                                            s);
+    else
+        launch_step_t<kNoise, kExact, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
+                                             flag, s);
 }
 
 void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
@@ -284,13 +371,13 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
     if (n <= 0 || n_sub <= 0) return;
     const bool noise = c.sigma > 0.f;
     if (noise && c.exact)
-        launch_step_t<true, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+        launch_step_a<true, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     else if (noise)
-        launch_step_t<true, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+        launch_step_a<true, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     else if (c.exact)
-        launch_step_t<false, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+        launch_step_a<false, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     else
-        launch_step_t<false, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+        launch_step_a<false, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
 }
 
 // ------------------------------------------------------------------ A6, warp form
@@ -381,7 +468,7 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <bool kNoise, bool kExact>
+template <bool kNoise, bool kExact, bool kAngles>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -424,6 +511,34 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
         const float ux = __shfl_up_sync(0xffffffffu, nx, 1);  // previous lane's share
         const float uy = __shfl_up_sync(0xffffffffu, ny, 1);
         const float uz = __shfl_up_sync(0xffffffffu, nz, 1);
+        // angles, each evaluated once by the lane of its middle bead: at bead 2l
+        // (ends 2l - 1, 2l + 1) and at bead 2l + 1 (ends 2l, 2l + 2); the shares
+        // of the end beads held by the neighbouring lanes go there by one shuffle
+        float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
+        if (kAngles) {
+            const float px = __shfl_up_sync(0xffffffffu, b1.x, 1);  // bead 2l - 1
+            const float py = __shfl_up_sync(0xffffffffu, b1.y, 1);
+            const float pz = __shfl_up_sync(0xffffffffu, b1.z, 1);
+            float fpx, fpy, fpz, f1x, f1y, f1z, f0x, f0y, f0z, fdx, fdy, fdz;
+            angle_force(px - b0.x, py - b0.y, pz - b0.z, b1.x - b0.x, b1.y - b0.y, b1.z - b0.z,
+                        (p0 && n0) ? c.two_ka : 0.0f, c.cos0, fpx, fpy, fpz, f1x, f1y, f1z);
+            angle_force(b0.x - b1.x, b0.y - b1.y, b0.z - b1.z, dx - b1.x, dy - b1.y, dz - b1.z,
+                        (n0 && n1) ? c.two_ka : 0.0f, c.cos0, f0x, f0y, f0z, fdx, fdy, fdz);
+            // from lane l - 1: its share on bead 2l; from lane l + 1: its share on bead 2l + 1
+            const float r0x = __shfl_up_sync(0xffffffffu, fdx, 1);
+            const float r0y = __shfl_up_sync(0xffffffffu, fdy, 1);
+            const float r0z = __shfl_up_sync(0xffffffffu, fdz, 1);
+            const float r1x = __shfl_down_sync(0xffffffffu, fpx, 1);
+            const float r1y = __shfl_down_sync(0xffffffffu, fpy, 1);
+            const float r1z = __shfl_down_sync(0xffffffffu, fpz, 1);
+            const bool first = lane == 0, last = lane == 31;
+            q0x = f0x - (fpx + f1x) + (first ? 0.f : r0x);
+            q0y = f0y - (fpy + f1y) + (first ? 0.f : r0y);
+            q0z = f0z - (fpz + f1z) + (first ? 0.f : r0z);
+            q1x = f1x - (f0x + fdx) + (last ? 0.f : r1x);
+            q1y = f1y - (f0y + fdy) + (last ? 0.f : r1y);
+            q1z = f1z - (f0z + fdz) + (last ? 0.f : r1z);
+        }
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
         cell_check<kExact>(b0, G, g, wcache, tid, f00, f01, f02);
@@ -433,10 +548,12 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
             gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, p0 ? ax - ux : ax,
-                                  p0 ? ay - uy : ay, p0 ? az - uz : az, c, g, wcache, tid);
-        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, nx - ax, ny - ay, nz - az, c,
-                                  g, wcache, kWarpBlock + tid);
+        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z,
+                                  (p0 ? ax - ux : ax) + q0x, (p0 ? ay - uy : ay) + q0y,
+                                  (p0 ? az - uz : az) + q0z, c, g, wcache, tid);
+        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, (nx - ax) + q1x,
+                                  (ny - ay) + q1y, (nz - az) + q1z, c, g, wcache,
+                                  kWarpBlock + tid);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
         b0.z = fmaf(c.dt, b0.vz, b0.z);
@@ -452,7 +569,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <bool kNoise, int kCap, bool kExact>
+template <bool kNoise, int kCap, bool kExact, bool kAngles>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
     extern __shared__ float4 wcache[];
@@ -482,22 +599,29 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
         }
         const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
-        advance_segment<kNoise, kExact>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta, rp.seg_start[s],
+        advance_segment<kNoise, kExact, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+                                                 rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
     }
 }
 
+template <int kCap, bool kNoise>
+static void warp_attrs_n() {
+    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+}
+
 template <int kCap>
 static void warp_attrs() {
-    cudaFuncSetAttribute(k_step_warp_batch<true, kCap, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<false, kCap, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<true, kCap, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<false, kCap, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    warp_attrs_n<kCap, true>();
+    warp_attrs_n<kCap, false>();
 }
 
 static int warp_grid_cap() {
@@ -509,23 +633,32 @@ static int warp_grid_cap() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS, false>, kWarpBlock, kWarpSmem);
+            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS, false, false>, kWarpBlock,
+            kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     return cap;
 }
 
+template <int kCap, bool kNoise>
+static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, bool exact, bool angles,
+                          cudaStream_t s) {
+    if (exact && angles)
+        k_step_warp_batch<kNoise, kCap, true, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else if (exact)
+        k_step_warp_batch<kNoise, kCap, true, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else if (angles)
+        k_step_warp_batch<kNoise, kCap, false, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    else
+        k_step_warp_batch<kNoise, kCap, false, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+}
+
 template <int kCap>
 static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, bool noise, bool exact,
                         cudaStream_t s) {
-    if (noise && exact)
-        k_step_warp_batch<true, kCap, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
-    else if (noise)
-        k_step_warp_batch<true, kCap, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
-    else if (exact)
-        k_step_warp_batch<false, kCap, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
-    else
-        k_step_warp_batch<false, kCap, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+    const bool angles = p.rep[0].c.two_ka != 0.f;  // all replicas alike (checked at init)
+    if (noise) launch_warp_n<kCap, true>(p, blocks, exact, angles, s);
+    else launch_warp_n<kCap, false>(p, blocks, exact, angles, s);
 }
 
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
@@ -601,6 +734,19 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
             const double dx = (double)x - xj, dy = (double)y - yj, dz = (double)z - zj;
             const double dr = norm_fp64(dx * dx + dy * dy + dz * dz) - e.r0;
             ub += e.bond_k * dr * dr;
+        }
+        if (c.two_ka != 0.f) {
+            angle_forces_of(st, meta, i, m, c, fx, fy, fz);
+            if ((m & kBondPrev) && (m & kBondNext)) {
+                // the angle centred here, once, in FP64 from the FP32 positions
+                const double ux = (double)st.x[i - 1] - x, uy = (double)st.y[i - 1] - y,
+                             uz = (double)st.z[i - 1] - z;
+                const double wx = (double)st.x[i + 1] - x, wy = (double)st.y[i + 1] - y,
+                             wz = (double)st.z[i + 1] - z;
+                const double uu = ux * ux + uy * uy + uz * uz, ww = wx * wx + wy * wy + wz * wz;
+                const double cth = (ux * wx + uy * wy + uz * wz) / norm_fp64(uu * ww);
+                ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
+            }
         }
         const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
         const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);

@@ -55,6 +55,8 @@ class Params(ctypes.Structure):
         ("field_every", ctypes.c_int32),
         ("sort_every", ctypes.c_int32),
         ("force_mode", ctypes.c_int32),
+        ("angle_k", ctypes.c_double),
+        ("angle_cos0", ctypes.c_double),
     ]
 
 
@@ -148,7 +150,7 @@ def load():
 
 def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
                 bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
-                sort_every=0, force_mode=0, **_ignored) -> Params:
+                sort_every=0, force_mode=0, angle_k=0.0, angle_cos0=-1.0, **_ignored) -> Params:
     p = Params()
     p.n_beads, p.n_species = int(n_beads), int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -168,6 +170,7 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
     p.seed = int(seed)
     p.field_every, p.sort_every = int(field_every), int(sort_every)
     p.force_mode = int(force_mode)
+    p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
     return p
 
 
