@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--net-lags", default="",
+                    help="learned workload: also train and judge a network at these lags "
+                         "(comma-separated step counts)")
     return ap.parse_args()
 
 
@@ -477,13 +480,14 @@ def run_learned(args):
     train_ex, val_ex = ex[:178], ex[178:]
     net = hpf.Propagator(pp["mesh"], stream=stream)
     net.set_weights(learned.init_params(0))
+    net.scale = learned.change_scale(snaps, train_ex)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     log = learned.train(net, snaps, 2000, lr=2e-3, lr_final=2e-4, examples=train_ex,
                         log_every=500)
     torch.cuda.synchronize()
     train_ms = (time.perf_counter() - t0) * 1e3 / 2000
-    val_net, val_zero = learned.validation_loss(net, snaps, val_ex)
+    val_net, val_zero, val_lin = learned.validation_loss(net, snaps, val_ex)
     # inference time (the 4-channel input already on the device)
     x = snaps[100:102].contiguous()
     y = torch.empty_like(snaps[0])
@@ -546,6 +550,24 @@ def run_learned(args):
         s.close()
     clk = clocks.stop()
     value = forms["learned_tol_1e-3"]["value"]
+    # the accuracy study at other lags: one network per lag, trained on 200
+    # snapshots of that spacing, judged on the continuation of the run
+    by_lag = {}
+    for L in [int(v) for v in args.net_lags.split(",") if v.strip()]:
+        sl = system(1, pos, vel, step)
+        sn = learned.collect_snapshots(sl, 200, L)
+        nl = hpf.Propagator(pp["mesh"], stream=stream)
+        nl.set_weights(learned.init_params(0))
+        nl.scale = learned.change_scale(sn, ex[:178])
+        learned.train(nl, sn, 2000, lr=2e-3, lr_final=2e-4, examples=ex[:178])
+        vn, vz, vl = learned.validation_loss(nl, sn, ex[178:])
+        rl = learned.judge_candidates(sl, nl, 10, L, lags=(L,))
+        by_lag[L] = {"net": float(np.mean(rl["net"])), "hold": float(np.mean(rl[f"hold_{L}"])),
+                     "linear": float(np.mean(rl[f"linear_{L}"])),
+                     "scale": nl.scale,
+                     "val_mse": {"net": vn, "no_change": vz, "linear": vl}}
+        nl.close()
+        sl.close()
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
         peak_src = "measured"
@@ -565,9 +587,10 @@ def run_learned(args):
                        "K": K, "tol": 1e-3, "snapshots": 200, "train_iters": 2000,
                        "l2": "flushed (256 MB write) before each timed window",
                        "forms": forms, "eps_mean": eps, "fe_equal_eps": fe_equal,
-                       "val_mse": {"net": val_net, "no_change": val_zero},
+                       "val_mse": {"net": val_net, "no_change": val_zero, "linear": val_lin},
+                       "change_scale": net.scale,
                        "train_ms_per_iter": train_ms, "train_log": log,
-                       "infer_ms": infer_ms},
+                       "infer_ms": infer_ms, "net_by_lag": by_lag},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src, "kernel": "k_conv (whole forward)",

@@ -288,9 +288,14 @@ hpf_status hpf_batch_destroy(hpf_batch* batch);
  * the field can still be refreshed every step from predicted densities.
  *
  * Network (two species only): input x = (phi_A, phi_B at step t - K, phi_A,
- * phi_B at step t), 4 channels on the periodic Mx x My x Mz mesh; three
- * 3x3x3 periodic convolutions (cross-correlation) 4 -> 16 -> 16 -> 2 channels
- * with SiLU after the first two; output dphi = predicted phi(t + K) - phi(t).
+ * phi_B at step t), 4 channels on the periodic Mx x My x Mz mesh, whose input
+ * channels are formed in FP32 as (s (phi(t) - phi(t - K)), phi(t)) per
+ * species before the BF16 rounding, s the handle's change scale; three 3x3x3
+ * periodic convolutions (cross-correlation) 4 -> 16 -> 16 -> 2 channels
+ * with SiLU after the first two; output dphi = (last layer) / s = predicted
+ * phi(t + K) - phi(t).  The scale s brings density changes (about 1e-2 per
+ * step) to order one in the network's units, so the weights that read them
+ * need not be far larger than their initial values.
  * A convolution computes out[co](n) = b[co] + sum_d sum_ci W[d][ci][co]
  * in[ci](n + d) over the 27 offsets d = (dz, dy, dx) in {-1, 0, 1}^3, z-major.
  * Weights and activations are BF16 on the tensor cores with FP32
@@ -310,6 +315,12 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out);
 hpf_status hpf_prop_destroy(hpf_prop* prop); /* NULL is a no-op */
 int32_t hpf_prop_param_count(void);
 
+/* The change scale s (default 1): > 0 and finite, else HPF_ERR_INVALID.  It
+ * is not part of the parameter vector; set it before training and keep it
+ * with the weights. */
+hpf_status hpf_prop_set_scale(hpf_prop* prop, float scale);
+hpf_status hpf_prop_get_scale(const hpf_prop* prop, float* scale);
+
 /* Load [param_count] FP32 parameters (and reset Adam); synchronises. */
 hpf_status hpf_prop_set_weights(hpf_prop* prop, const float* params);
 /* Copy the FP32 parameters out (synchronises for a host destination). */
@@ -319,7 +330,8 @@ hpf_status hpf_prop_get_weights(hpf_prop* prop, float* params);
  * host destination. */
 hpf_status hpf_prop_forward(hpf_prop* prop, const float* x, float* dphi);
 
-/* Loss L = mean over the 2 x M outputs of (network(x) - (phi_next - x[2:4]))^2
+/* Loss L = mean over the 2 x M outputs of (s network(x) - s (phi_next - x[2:4]))^2,
+ * i.e. s^2 times the mean squared error of the predicted change,
  * and its gradient with respect to the parameter vector (back-propagation
  * through the same BF16 kernels: data gradients with flipped, transposed
  * weights, weight gradients as tensor-core voxel reductions).  phi_next is

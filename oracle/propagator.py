@@ -1,18 +1,21 @@
 """CPU oracle of the learned density propagator (test infrastructure only).
 
 The network maps the per-species density meshes at the last two true field
-refreshes, (phi_A, phi_B)(t - K) and (phi_A, phi_B)(t) -- 4 channels on the
-periodic mesh -- to the change (phi_A, phi_B)(t + K) - (phi_A, phi_B)(t):
+refreshes, x = ((phi_A, phi_B)(t - K), (phi_A, phi_B)(t)) -- 4 channels on the
+periodic mesh -- to the change (phi_A, phi_B)(t + K) - (phi_A, phi_B)(t).  Its
+input channels are features(x) = (s (phi(t) - phi(t - K)), phi(t)) per
+species, s a fixed change scale:
 
-    h1 = SiLU(conv(x, W1) + b1)      4 -> 16 channels
+    h1 = SiLU(conv(features(x), W1) + b1)      4 -> 16 channels
     h2 = SiLU(conv(h1, W2) + b2)    16 -> 16
-    y  = conv(h2, W3) + b3          16 ->  2
+    y  = (conv(h2, W3) + b3) / s    16 ->  2
 
 conv is a 3x3x3 periodic convolution (cross-correlation, as in deep-learning
 libraries): out[co](n) = sum_ci sum_d W[d][ci][co] in[ci](n + d), with the
 27 offsets d = (dz, dy, dx) in {-1, 0, 1}^3 in z-major order.  Meshes are
-[C][Mz][My][Mx].  FP64 throughout; the loss is the mean squared error over
-all voxels and output channels.
+[C][Mz][My][Mx].  FP64 throughout; the loss is s^2 times the mean squared
+error of y over all voxels and output channels (the error of the last
+layer's output against the scaled change).
 
 Parity status: conv, SiLU and the whole network forward are pinned by closed
 forms (delta kernels shift the input, periodic wrap, linearity, SiLU values);
@@ -78,27 +81,34 @@ def init_params(seed=0):
     return params
 
 
-def forward(params, x):
-    """Returns the output and the per-layer (input, pre-activation) cache."""
+def features(x, scale=1.0):
+    """The network's input channels from x = (phi_A, phi_B at t - K, phi_A, phi_B
+    at t): the scaled changes scale * (phi(t) - phi(t - K)) and the current
+    phi(t), per species, formed in full precision before any rounding."""
+    return np.stack([scale * (x[2] - x[0]), scale * (x[3] - x[1]), x[2], x[3]])
+
+
+def forward(params, x, scale=1.0):
+    """Returns the predicted change y and the per-layer (input, pre-activation) cache."""
     cache = []
-    h = x
+    h = features(x, scale)
     for (W, b), (_, _, act) in zip(params, LAYERS):
         z = conv(h, W, b)
         cache.append((h, z))
         h = silu(z) if act else z
-    return h, cache
+    return h / scale, cache
 
 
-def loss(params, x, target):
-    y, _ = forward(params, x)
-    return float(np.mean((y - target) ** 2))
+def loss(params, x, target, scale=1.0):
+    y, _ = forward(params, x, scale)
+    return float(np.mean((scale * y - scale * target) ** 2))
 
 
-def backward(params, x, target):
+def backward(params, x, target, scale=1.0):
     """Loss and its gradients [(gW, gb) per layer] by back-propagation."""
-    y, cache = forward(params, x)
-    L = float(np.mean((y - target) ** 2))
-    g = 2.0 * (y - target) / y.size
+    y, cache = forward(params, x, scale)
+    L = float(np.mean((scale * y - scale * target) ** 2))
+    g = 2.0 * (scale * y - scale * target) / y.size
     grads = [None] * len(params)
     for li in reversed(range(len(params))):
         h, z = cache[li]

@@ -286,28 +286,40 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
 
 // ------------------------------------------------------------------ elementwise
 
-__global__ void k_pack_input(const float* __restrict__ x, int V, __nv_bfloat16* __restrict__ out) {
+// The network's input channels from x = (phi_A, phi_B at t - K, phi_A, phi_B
+// at t), planar FP32: the scaled changes scale * (phi(t) - phi(t - K)) and the
+// current phi(t) per species, formed in FP32 before the BF16 rounding (a
+// one-step change of about 1e-2 is far below the BF16 spacing of phi ~ 0.5),
+// zero-padded to 16.
+__global__ void k_pack_input(const float* __restrict__ x, int V, float scale,
+                             __nv_bfloat16* __restrict__ out) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
+    const float a0 = x[v], b0 = x[(size_t)V + v];
+    const float a1 = x[(size_t)2 * V + v], b1 = x[(size_t)3 * V + v];
+    const float f[4] = {scale * (a1 - a0), scale * (b1 - b0), a1, b1};
     __nv_bfloat16 vals[kPC];
 #pragma unroll
-    for (int c = 0; c < kPC; ++c) vals[c] = __float2bfloat16_rn(c < 4 ? x[(size_t)c * V + v] : 0.f);
+    for (int c = 0; c < kPC; ++c) vals[c] = __float2bfloat16_rn(c < 4 ? f[c] : 0.f);
     reinterpret_cast<uint4*>(out + (size_t)v * kPC)[0] = reinterpret_cast<uint4*>(vals)[0];
     reinterpret_cast<uint4*>(out + (size_t)v * kPC)[1] = reinterpret_cast<uint4*>(vals)[1];
 }
 
-__global__ void k_unpack_output(const float* __restrict__ y, int V, float* __restrict__ out) {
+// The predicted change: the network's two output channels divided by scale.
+__global__ void k_unpack_output(const float* __restrict__ y, int V, float scale,
+                                float* __restrict__ out) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    out[v] = y[(size_t)v * kPC];
-    out[(size_t)V + v] = y[(size_t)v * kPC + 1];
+    out[v] = y[(size_t)v * kPC] / scale;
+    out[(size_t)V + v] = y[(size_t)v * kPC + 1] / scale;
 }
 
-// Mean squared error of the predicted change y against phi_next - phi_cur
-// (planar [2][V] each) and its gradient 2 (y - target) / (2V) in BF16.
+// Mean squared error of the network output y against scale * (phi_next -
+// phi_cur) (planar [2][V] each) and its gradient 2 (y - target) / (2V) in BF16.
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
                                               const float* __restrict__ phi_cur,
                                               const float* __restrict__ phi_next, int V,
+                                              float scale,
                                               __nv_bfloat16* __restrict__ gy,
                                               double* __restrict__ loss_part) {
     __shared__ double sh[8];
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const size_t k = (size_t)c * V + v;
-            const float d = y[(size_t)v * kPC + c] - (phi_next[k] - phi_cur[k]);
+            const float d = y[(size_t)v * kPC + c] - scale * (phi_next[k] - phi_cur[k]);
             l += (double)d * d;
             vals[c] = __float2bfloat16_rn(d / (float)V);
         }
@@ -523,6 +535,7 @@ using namespace hpf;
 struct hpf_prop {
     cudaStream_t stream = nullptr;
     PropGeom g{};
+    float scale = 1.f;  // change-channel scale (input times, output divided by)
     int np = 0;
     float* params = nullptr;  // FP32 master [np]
     float* grads = nullptr;
@@ -569,7 +582,7 @@ hpf_status prop_copy_out(hpf_prop* p, void* dst, const void* src, size_t bytes) 
 void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s) {
     const int V = p->g.V, tb = (V + 255) / 256;
     const size_t wl = (size_t)kOffsets * kPC * kPC;
-    k_pack_input<<<tb, 256, 0, s>>>(x, V, p->act[0]);
+    k_pack_input<<<tb, 256, 0, s>>>(x, V, p->scale, p->act[0]);
     k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[0], p->wf, p->bias,
                                                    keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
                                                    p->g);
@@ -590,7 +603,7 @@ void prop_backward(hpf_prop* p, const float* x, const float* phi_next) {
     cudaStream_t s = p->stream;
     __nv_bfloat16* gbuf = p->act[3];
     // the last layer has no activation: its gz is dL/dy
-    k_loss<<<tb, 256, 0, s>>>(p->fbuf, x + 2 * (size_t)V, phi_next, V, gbuf, p->lpart);
+    k_loss<<<tb, 256, 0, s>>>(p->fbuf, x + 2 * (size_t)V, phi_next, V, p->scale, gbuf, p->lpart);
     k_sum_partials<double><<<1, 32, 0, s>>>(p->lpart, tb, 1, p->loss);
     for (int layer = 2; layer >= 0; --layer) {
         k_conv_wgrad<<<p->grid_wgrad, 256, 0, s>>>(p->act[layer], gbuf, p->wpart, p->g);
@@ -655,7 +668,7 @@ bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g) {
 
 void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s) {
     prop_forward(p, x, false, s);
-    k_unpack_output<<<(p->g.V + 255) / 256, 256, 0, s>>>(p->fbuf, p->g.V, dphi);
+    k_unpack_output<<<(p->g.V + 255) / 256, 256, 0, s>>>(p->fbuf, p->g.V, p->scale, dphi);
 }
 
 }  // namespace hpf
@@ -775,6 +788,18 @@ hpf_status hpf_prop_set_weights(hpf_prop* p, const float* params) {
 hpf_status hpf_prop_get_weights(hpf_prop* p, float* params) {
     if (!p || !params) return HPF_ERR_INVALID;
     return prop_copy_out(p, params, p->params, sizeof(float) * p->np);
+}
+
+hpf_status hpf_prop_set_scale(hpf_prop* p, float scale) {
+    if (!p || !(scale > 0.f) || !(scale < 3.0e38f)) return HPF_ERR_INVALID;
+    p->scale = scale;
+    return HPF_OK;
+}
+
+hpf_status hpf_prop_get_scale(const hpf_prop* p, float* scale) {
+    if (!p || !scale) return HPF_ERR_INVALID;
+    *scale = p->scale;
+    return HPF_OK;
 }
 
 hpf_status hpf_prop_forward(hpf_prop* p, const float* x, float* dphi) {

@@ -125,6 +125,8 @@ def load():
         L.hpf_prop_param_count.argtypes = []
         L.hpf_prop_set_weights.argtypes = [vp, vp]
         L.hpf_prop_get_weights.argtypes = [vp, vp]
+        L.hpf_prop_set_scale.argtypes = [vp, ctypes.c_float]
+        L.hpf_prop_get_scale.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.hpf_prop_forward.argtypes = [vp, vp, vp]
         L.hpf_prop_backward.argtypes = [vp, vp, vp, vp, dp]
         L.hpf_prop_adam_step.argtypes = [vp, vp, ctypes.c_float]
@@ -134,6 +136,7 @@ def load():
         L.hpf_step_learned.argtypes = [vp, vp, i32, i32, ctypes.c_double,
                                        ctypes.POINTER(LearnedStats)]
         for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
+                     "hpf_prop_set_scale", "hpf_prop_get_scale",
                      "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_backward",
                      "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
                      "hpf_judge_density", "hpf_step_learned"):
@@ -428,7 +431,9 @@ class Propagator:
     """The learned density propagator network (hpf_prop_init ... hpf_prop_destroy).
 
     Mesh arrays are planar FP32: inputs x [4][Mz][My][Mx] = (phi_A, phi_B at
-    t - K, phi_A, phi_B at t); outputs and targets [2][Mz][My][Mx]."""
+    t - K, phi_A, phi_B at t); outputs and targets [2][Mz][My][Mx].  ``scale``
+    is the change scale s (input change channels times s, output divided by
+    s; the training loss is s^2 times the mean squared error)."""
 
     def __init__(self, mesh, stream=None):
         self.lib = load()
@@ -469,6 +474,16 @@ class Propagator:
 
     def __exit__(self, *exc):
         self.close()
+
+    @property
+    def scale(self) -> float:
+        v = ctypes.c_float()
+        self._check(self.lib.hpf_prop_get_scale(self.h, ctypes.byref(v)))
+        return float(v.value)
+
+    @scale.setter
+    def scale(self, value: float):
+        self._check(self.lib.hpf_prop_set_scale(self.h, float(value)))
 
     def set_weights(self, params):
         pp, _a = _ptr(params, np.float32, (self.n_params,), "params")

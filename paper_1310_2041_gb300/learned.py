@@ -49,6 +49,16 @@ def triples(n_snap: int):
     return list(range(1, n_snap - 1))
 
 
+def change_scale(snaps, examples=None) -> float:
+    """The change scale s for a network trained on ``snaps``: the inverse RMS
+    of the input changes phi[k] - phi[k - 1] over the examples, so that the
+    network reads and writes changes of order one."""
+    ex = triples(snaps.shape[0]) if examples is None else list(examples)
+    ms = [float(((snaps[k] - snaps[k - 1]).double() ** 2).mean()) for k in ex]
+    rms = float(np.sqrt(np.mean(ms)))
+    return 1.0 / rms if rms > 0.0 else 1.0
+
+
 def train(prop: hpf.Propagator, snaps, iters: int, lr: float = 2e-3, lr_final: float = 2e-4,
           examples=None, seed: int = 0, log_every: int = 0):
     """Adam on the mean squared error of the predicted change, one example per
@@ -72,14 +82,19 @@ def train(prop: hpf.Propagator, snaps, iters: int, lr: float = 2e-3, lr_final: f
 
 
 def validation_loss(prop: hpf.Propagator, snaps, examples):
-    """Mean loss of the network and of predicting no change over examples."""
-    net, zero = [], []
+    """Mean squared error of the predicted change over examples: of the
+    network, of predicting no change, and of linear extrapolation
+    (phi[k] - phi[k - 1])."""
+    net, zero, lin = [], [], []
+    s2 = prop.scale ** 2
     for k in examples:
         x = snaps[k - 1:k + 1]
-        net.append(prop.backward(x, snaps[k + 1])[0])
+        net.append(prop.backward(x, snaps[k + 1])[0] / s2)
         d = (snaps[k + 1] - snaps[k]).double()
         zero.append(float((d * d).mean()))
-    return float(np.mean(net)), float(np.mean(zero))
+        e = d - (snaps[k] - snaps[k - 1]).double()
+        lin.append(float((e * e).mean()))
+    return float(np.mean(net)), float(np.mean(zero)), float(np.mean(lin))
 
 
 def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows: int, K: int,

@@ -102,6 +102,38 @@ def test_backward_matches_oracle(hpf_gpu, mesh):
         assert rel(gb, ob) < 3e-2, f"layer {k} biases"
 
 
+def test_scaled_network_matches_oracle(hpf_gpu):
+    """With a change scale s the change channels enter times s and the
+    prediction leaves divided by s; the loss is s^2 times the squared error.
+    Inputs with changes of the size one MD step makes (about 1e-2)."""
+    mesh = (24, 16, 9)
+    s = 25.0
+    params = rand_params(21)
+    rng = np.random.default_rng(22)
+    x = rand_phi(grid(mesh), 23)
+    x[:2] = x[2:] - rng.uniform(-0.04, 0.04, size=x[2:].shape)
+    nxt = x[2:] + rng.uniform(-0.04, 0.04, size=x[2:].shape)
+    with hpf_gpu.Propagator(mesh) as net:
+        assert net.scale == 1.0
+        net.scale = s
+        assert net.scale == s
+        net.set_weights(hpf_gpu.pack_params(params))
+        assert net.scale == s  # loading weights keeps the scale
+        y = net.forward(x.astype(np.float32))
+        loss, g = net.backward(x.astype(np.float32), nxt.astype(np.float32))
+        for bad in (0.0, -1.0, float("inf"), float("nan")):
+            with pytest.raises(hpf_gpu.HPFError):
+                net.scale = bad
+        assert net.scale == s
+    yo, _ = P.forward(params, x, s)
+    assert rel(y, yo) < 3e-2 and cosine(y, yo) > 0.999
+    Lo, go = P.backward(params, x, nxt - x[2:], s)
+    assert loss == pytest.approx(Lo, rel=2e-2)
+    for k, ((gW, gb), (oW, ob)) in enumerate(zip(hpf_gpu.unpack_params(g), go)):
+        assert rel(gW, oW) < 3e-2 and cosine(gW, oW) > 0.999, f"layer {k} weights"
+        assert rel(gb, ob) < 3e-2, f"layer {k} biases"
+
+
 def test_adam_matches_oracle(hpf_gpu):
     params = rand_params(8)
     mesh = (8, 8, 4)
@@ -300,13 +332,42 @@ def test_trained_network_beats_holding_the_last_density(hpf_gpu):
     ex = learned.triples(120)
     with hpf_gpu.Propagator((40, 40, 40)) as net:
         net.set_weights(learned.init_params(0))
+        net.scale = learned.change_scale(snaps, ex[:100])
         learned.train(net, snaps, 1500, lr=2e-3, lr_final=2e-4, examples=ex[:100])
-        val_net, val_zero = learned.validation_loss(net, snaps, ex[100:])
+        val_net, val_zero, val_lin = learned.validation_loss(net, snaps, ex[100:])
         res = learned.judge_candidates(s, net, 8, K, lags=(K,))
-    assert val_net < 0.9 * val_zero
+    # at this lag linear extrapolation overshoots and is worse than holding
+    assert val_net < 0.9 * min(val_zero, val_lin)
     assert np.mean(res["net"]) < 0.95 * np.mean(res["hold_net"])
+    assert np.mean(res["net"]) < 0.95 * np.mean(res[f"linear_{K}"])
     assert np.allclose(res["hold_net"], res[f"hold_{K}"][-len(res["hold_net"]):])
     del torch
+
+
+def test_scaled_network_learns_short_lag_extrapolation(hpf_gpu):
+    """At a lag of 2 steps the density change is nearly linear in time; with
+    the change scale the trained network reaches the accuracy of linear
+    extrapolation (and far beats holding the last density)."""
+    from paper_1310_2041_gb300 import learned
+    K = 2
+    n_chains = 10000
+    box = (20.0 * n_chains / 3.0) ** (1.0 / 3.0)
+    w = W.diblock(n_chains, 10, 10, box, 40, 0.5, name="a10b10_200k")
+    pp = dict(w.params(), field_every=1, sort_every=1000)
+    data = W.generate(w)
+    s = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    s.set_state(data["pos"], data["vel"], data["type"], data["bonds"])
+    s.step(1000)
+    snaps = learned.collect_snapshots(s, 120, K)
+    ex = learned.triples(120)
+    with hpf_gpu.Propagator((40, 40, 40)) as net:
+        net.set_weights(learned.init_params(0))
+        net.scale = learned.change_scale(snaps, ex[:100])
+        assert 20.0 < net.scale < 500.0
+        learned.train(net, snaps, 1500, lr=2e-3, lr_final=2e-4, examples=ex[:100])
+        val_net, val_zero, val_lin = learned.validation_loss(net, snaps, ex[100:])
+    assert val_net < 1.1 * val_lin
+    assert val_net < 0.3 * val_zero
 
 
 def test_learned_step_rejects_bad_arguments(hpf_gpu):

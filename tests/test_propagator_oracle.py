@@ -53,14 +53,16 @@ def test_silu_closed_form():
     assert P.silu(np.array(40.0)) == pytest.approx(40.0)
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("scale", [1.0, 37.0])
+def test_backward_matches_finite_differences(scale):
     rng = np.random.default_rng(3)
     params = P.init_params(seed=4)
     params = [(W * 3.0, rng.normal(scale=0.1, size=b.shape)) for W, b in params]
     x = rng.normal(size=(4, 4, 3, 5))
-    t = rng.normal(scale=0.1, size=(2, 4, 3, 5))
-    L, grads = P.backward(params, x, t)
-    assert L == pytest.approx(P.loss(params, x, t), rel=1e-14)
+    x[:2] = x[2:] - rng.normal(scale=1.0 / scale, size=(2, 4, 3, 5))
+    t = rng.normal(scale=0.1 / scale, size=(2, 4, 3, 5))
+    L, grads = P.backward(params, x, t, scale)
+    assert L == pytest.approx(P.loss(params, x, t, scale), rel=1e-14)
     h = 1e-6
     for li in range(3):
         W, b = params[li]
@@ -70,7 +72,7 @@ def test_backward_matches_finite_differences():
             Wm[idx] -= h
             pp = list(params); pp[li] = (Wp, b)
             pm = list(params); pm[li] = (Wm, b)
-            fd = (P.loss(pp, x, t) - P.loss(pm, x, t)) / (2 * h)
+            fd = (P.loss(pp, x, t, scale) - P.loss(pm, x, t, scale)) / (2 * h)
             assert grads[li][0][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
         for j in (0, b.shape[0] - 1):
             bp, bm = b.copy(), b.copy()
@@ -78,7 +80,7 @@ def test_backward_matches_finite_differences():
             bm[j] -= h
             pp = list(params); pp[li] = (W, bp)
             pm = list(params); pm[li] = (W, bm)
-            fd = (P.loss(pp, x, t) - P.loss(pm, x, t)) / (2 * h)
+            fd = (P.loss(pp, x, t, scale) - P.loss(pm, x, t, scale)) / (2 * h)
             assert grads[li][1][j] == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
@@ -90,3 +92,48 @@ def test_first_adam_step_closed_form():
     assert new[0][0][0, 0, 0] == pytest.approx(0.5 - 0.01 * 2.0 / (2.0 + 1e-8))
     assert new[0][1][0] == pytest.approx(1.0 + 0.01 * 3.0 / (3.0 + 1e-8))
     assert state[0] == 1
+
+
+def test_features_are_the_change_and_the_current_density():
+    rng = np.random.default_rng(9)
+    x = rng.uniform(size=(4, 3, 4, 5))
+    f = P.features(x)
+    np.testing.assert_array_equal(f[0], x[2] - x[0])
+    np.testing.assert_array_equal(f[1], x[3] - x[1])
+    np.testing.assert_array_equal(f[2:], x[2:])
+    # the forward pass starts from the features: a first layer that copies the
+    # change channel of species A into every output shows it
+    params = P.init_params(1)
+    W1 = np.zeros((27, 4, 16))
+    W1[13, 0, :] = 1.0  # centre offset, channel 0
+    y, cache = P.forward([(W1, np.zeros(16))] + params[1:], x)
+    np.testing.assert_array_equal(cache[0][0], f)
+    np.testing.assert_allclose(cache[0][1][5], x[2] - x[0], rtol=1e-15)
+
+
+def test_change_scale_enters_the_change_channels_and_the_output_only():
+    """Scaling the change channels by s and dividing the output by s is a
+    reparametrisation: dividing the first layer's change-channel weights by s
+    and multiplying the last layer by s gives the same predictions at s as
+    the original weights at s = 1; the loss is s^2 times the mean squared error."""
+    rng = np.random.default_rng(11)
+    params = P.init_params(5)
+    params = [(W * 2.0, rng.normal(scale=0.1, size=b.shape)) for W, b in params]
+    x = rng.uniform(0.2, 1.0, size=(4, 5, 4, 3))
+    t = rng.normal(scale=0.05, size=(2, 5, 4, 3))
+    s = 23.0
+    (W1, b1), mid, (W3, b3) = params
+    W1s = W1.copy()
+    W1s[:, :2, :] /= s
+    rep = [(W1s, b1), mid, (W3 * s, b3 * s)]
+    y1, _ = P.forward(params, x)
+    ys, _ = P.forward(rep, x, s)
+    np.testing.assert_allclose(ys, y1, rtol=1e-12, atol=1e-14)
+    assert P.loss(rep, x, t, s) == pytest.approx(s * s * np.mean((ys - t) ** 2), rel=1e-12)
+    # the phi(t) channels are not scaled: a first layer reading only them
+    # gives predictions that scale as 1 / s
+    W1p = W1.copy()
+    W1p[:, :2, :] = 0.0
+    yp1, _ = P.forward([(W1p, b1), mid, (W3, b3)], x)
+    yps, _ = P.forward([(W1p, b1), mid, (W3, b3)], x, s)
+    np.testing.assert_allclose(yps * s, yp1, rtol=1e-12, atol=1e-14)
