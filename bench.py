@@ -566,6 +566,10 @@ def run_learned(args):
                      "linear": float(np.mean(rl[f"linear_{L}"])),
                      "scale": nl.scale,
                      "val_mse": {"net": vn, "no_change": vz, "linear": vl}}
+        if L == 1:
+            # the lag-1 network used autoregressively over K steps
+            by_lag[L]["rollout"] = {K2: float(np.mean(learned.judge_rollout(sl, nl, 8, K2)))
+                                    for K2 in (2, 5, 10, 20)}
         nl.close()
         sl.close()
     try:

@@ -133,3 +133,42 @@ def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows:
         if s < n_steps:
             system.step(1)
     return res
+
+
+def rollout(prop: hpf.Propagator, prev, cur, K: int):
+    """Autoregressive use of a network trained at lag 1: from phi(t - 1) = prev
+    and phi(t) = cur, predict phi(t + 1) = phi(t) + net(phi(t - 1), phi(t)),
+    then feed the prediction back, K times.  Returns the predicted phi(t + K)."""
+    import torch
+    a, b = prev, cur
+    x = torch.empty((4,) + tuple(cur.shape[1:]), dtype=torch.float32, device=cur.device)
+    d = torch.empty_like(cur)
+    for _ in range(K):
+        x[:2].copy_(a)
+        x[2:].copy_(b)
+        prop.forward(x, out=d)
+        a, b = b, b + d
+    return b
+
+
+def judge_rollout(system: hpf.System, prop: hpf.Propagator, n_windows: int, K: int):
+    """The judge's eps of K-step autoregressive rollouts of a lag-1 network
+    along a plain trajectory of ``system`` (which should refresh its field
+    every step): each window starts from the true phi(t - 1), phi(t) and is
+    judged at t + K.  Returns [eps per window]."""
+    import torch
+    shape = system.mesh_shape
+    prev = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cur = torch.empty_like(prev)
+    system.density_phi(prev)
+    system.step(1)
+    system.density_phi(cur)
+    res = []
+    for _ in range(n_windows):
+        pred = rollout(prop, prev, cur, K)
+        system.step(K - 1)
+        system.density_phi(prev)
+        system.step(1)
+        system.density_phi(cur)
+        res.append(system.judge_density(pred))
+    return res

@@ -413,3 +413,39 @@ def test_judge_three_species_against_oracle(hpf_gpu, orc):
     with hpf_gpu.Propagator((8, 8, 8)) as net:
         with pytest.raises(hpf_gpu.HPFError):
             s.step_learned(net, 1, K=4)
+
+
+def test_autoregressive_rollout(hpf_gpu):
+    """The K-step rollout feeds each prediction back: its first step is one
+    forward pass, its second a forward pass on (phi(t), prediction); a network
+    with zero weights holds phi(t), so its judged error is the error of the
+    held density at t + K (recomputed on an identical trajectory)."""
+    import torch
+    from paper_1310_2041_gb300 import learned
+    w, pp, data = melt(hpf_gpu, field_every=1)
+    a = system(hpf_gpu, pp, data)
+    prev = torch.from_numpy(a.density_phi()).cuda()
+    a.step(1)
+    cur = torch.from_numpy(a.density_phi()).cuda()
+    with hpf_gpu.Propagator((10, 10, 10)) as net:
+        net.set_weights(hpf_gpu.pack_params([(W * 0.3, b) for W, b in P.init_params(6)]))
+        net.scale = 40.0
+        d1 = net.forward(torch.cat([prev, cur]).contiguous(), out=torch.empty_like(cur))
+        p1 = cur + d1
+        d2 = net.forward(torch.cat([cur, p1]).contiguous(), out=torch.empty_like(cur))
+        assert torch.equal(learned.rollout(net, prev, cur, 1), p1)
+        assert torch.equal(learned.rollout(net, prev, cur, 2), p1 + d2)
+    K, n = 3, 4
+    b = system(hpf_gpu, pp, data)
+    with hpf_gpu.Propagator((10, 10, 10)) as zero:
+        assert torch.equal(learned.rollout(zero, prev, cur, K), cur)
+        eps = learned.judge_rollout(b, zero, n, K)
+    assert len(eps) == n and all(np.isfinite(eps))
+    c = system(hpf_gpu, pp, data)
+    c.step(1)
+    want = []
+    for _ in range(n):
+        held = c.density_phi()
+        c.step(K)
+        want.append(c.judge_density(held))
+    assert eps == pytest.approx(want, rel=1e-12)
