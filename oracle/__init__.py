@@ -16,6 +16,8 @@ with the CUDA library.  Parity status per function:
                  by moments of the normals
   energy         pinned (kinetic energy of known velocities, bond closed form,
                  field energy derivative equals the potential)
+  run_nh         pinned (NVE limit, free-particle thermostat ODE, extended-energy
+                 conservation, mean temperature)
 """
 from __future__ import annotations
 
@@ -67,6 +69,8 @@ class Params(ctypes.Structure):
         ("force_mode", ctypes.c_int32),
         ("angle_k", ctypes.c_double),
         ("angle_cos0", ctypes.c_double),
+        ("thermostat", ctypes.c_int32),
+        ("nh_tau", ctypes.c_double),
     ]
 
 
@@ -106,6 +110,9 @@ def lib():
                                      P(f64), i64, P(f64)]
             L.orc_run.argtypes = [pp, i64, P(f64), P(f64), P(i32), i64, P(i32), i64, i32, P(f64)]
             L.orc_run.restype = ctypes.c_int
+            L.orc_run_nh.argtypes = [pp, i64, P(f64), P(f64), P(i32), i64, P(i32), i64, i32,
+                                     P(f64), P(f64)]
+            L.orc_run_nh.restype = ctypes.c_int
             L.orc_cell_key.argtypes = [pp, P(f64), i32]
             L.orc_cell_key.restype = i64
             _lib = L
@@ -114,7 +121,7 @@ def lib():
 
 def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None, bond_k=4.0,
                 bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1, force_mode=0,
-                angle_k=0.0, angle_cos0=-1.0, **_ignored):
+                angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0, **_ignored):
     p = Params()
     p.n_species = int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -135,6 +142,7 @@ def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
     p.field_every = int(field_every)
     p.force_mode = int(force_mode)
     p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
+    p.thermostat, p.nh_tau = int(thermostat), float(nh_tau)
     return p
 
 
@@ -295,6 +303,26 @@ def run(p: Params, pos, vel, types, bonds, step0, n_steps, energies=False):
     if rc != 0:
         raise ValueError("oracle rejected the input")
     return pos, vel, E
+
+
+def run_nh(p: Params, pos, vel, types, bonds, step0, n_steps, xe=(0.0, 0.0), energies=False):
+    """Nose-Hoover NVT (``orc_run_nh``).  Returns (pos, vel, (xi, eta), energies
+    or None); vel is v_{n-1/2}, (xi, eta) the thermostat at the middle of the
+    last step, energies [n_steps + 1][7] (kinetic, bonded, field, total, |P|,
+    T, extended energy)."""
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    types = _i32(types)
+    bonds = _i32(np.asarray(bonds).reshape(-1, 2))
+    x = np.array(xe, dtype=np.float64)
+    E = np.zeros((n_steps + 1, 7)) if energies else None
+    rc = lib().orc_run_nh(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                          _p(vel, ctypes.c_double), _p(types, ctypes.c_int32), bonds.shape[0],
+                          _p(bonds, ctypes.c_int32), int(step0), int(n_steps),
+                          _p(x, ctypes.c_double), _p(E, ctypes.c_double) if E is not None else None)
+    if rc != 0:
+        raise ValueError("oracle rejected the input")
+    return pos, vel, (float(x[0]), float(x[1])), E
 
 
 def cell_key(p: Params, x, brick: int) -> int:

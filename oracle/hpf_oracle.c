@@ -579,6 +579,105 @@ int orc_run(const orc_params* p, int64_t n, double* pos, double* vel, const int3
     return 0;
 }
 
+/* ------------------------------------------------------------ Nose-Hoover NVT */
+
+static double nh_dof(int64_t n)
+{
+    return n > 1 ? 3.0 * (double)(n - 1) : 3.0 * (double)n;
+}
+
+static double nh_g(const orc_params* p, double dof, double K)
+{
+    if (dof <= 0.0) return 0.0;
+    return (2.0 * K / (dof * p->kT) - 1.0) / (p->nh_tau * p->nh_tau);
+}
+
+/* One thermostat half step T(h) of the scheme above; returns the velocity
+ * scale and updates xi, eta and the kinetic energy K. */
+static double nh_half(const orc_params* p, double dof, double h, double* xi, double* eta,
+                      double* K)
+{
+    *xi += 0.5 * h * nh_g(p, dof, *K);
+    const double s = exp(-*xi * h);
+    *K *= s * s;
+    *eta += *xi * h;
+    *xi += 0.5 * h * nh_g(p, dof, *K);
+    return s;
+}
+
+int orc_run_nh(const orc_params* p, int64_t n, double* pos, double* vel, const int32_t* type,
+               int64_t n_bonds, const int32_t* pairs, int64_t step0, int32_t n_steps,
+               double xe[2], double* energies)
+{
+    if (p->field_every < 1 || p->n_species < 1 || p->n_species > ORC_MAX_SPECIES || n < 0 ||
+        p->force_mode < 0 || p->force_mode > 1 || !(p->nh_tau > 0.0) || !xe)
+        return -1;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    const int64_t M = n_nodes(p);
+    int32_t* BL = (int32_t*)malloc(sizeof(int32_t) * ORC_MAX_BONDS * nn);
+    int32_t* BN = (int32_t*)malloc(sizeof(int32_t) * nn);
+    if (orc_bond_table(n, n_bonds, pairs, BL, BN) != 0) {
+        free(BL); free(BN);
+        return -1;
+    }
+    int64_t* D = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M * p->n_species));
+    double* V = (double*)malloc(sizeof(double) * (size_t)(M * p->n_species));
+    double* G = (double*)malloc(sizeof(double) * 3 * (size_t)(M * p->n_species));
+    double* Ff = (double*)malloc(sizeof(double) * 3 * nn);
+    double* Fb = (double*)malloc(sizeof(double) * 3 * nn);
+    double* Fc = (double*)malloc(sizeof(double) * 3 * nn);
+    double* vE = (double*)malloc(sizeof(double) * 3 * nn);
+    const double dof = nh_dof(n), h = 0.5 * p->dt, hm = 0.5 * p->dt / p->mass;
+    double xi = xe[0], eta = xe[1];
+    for (int32_t k = 0; k <= n_steps; ++k) {
+        int64_t step = step0 + k;
+        if (k == 0 || step % p->field_every == 0) {
+            orc_scatter(p, n, pos, type, D);
+            orc_field(p, D, V, G);
+        }
+        conservative_force(p, n, pos, type, BL, BN, V, G, Ff, Fb, Fc);
+        long double ke = 0.0L;
+        for (int64_t i = 0; i < 3 * n; ++i) {
+            vE[i] = vel[i] + hm * Fc[i];
+            ke += (long double)(0.5 * p->mass * vE[i] * vE[i]);
+        }
+        double K = (double)ke;
+        /* the end of step n - 1 (on copies: the last record's half step is not
+           part of the state, which keeps xi, eta at the middle of a step) */
+        double xi1 = xi, eta1 = eta;
+        const double s1 = nh_half(p, dof, h, &xi1, &eta1, &K);
+        if (energies) {
+            double* e = energies + 7 * (size_t)k;
+            long double mom[3] = {0.0L, 0.0L, 0.0L};
+            for (int64_t i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) mom[a] += (long double)(p->mass * s1 * vE[3 * i + a]);
+            orc_scatter(p, n, pos, type, D);
+            const double w = orc_field_energy(p, D);
+            const double ub = orc_bond_energy(p, n, pos, BL, BN) + orc_angle_energy(p, n, pos, BL, BN);
+            e[0] = K;
+            e[1] = ub;
+            e[2] = w;
+            e[3] = K + ub + w;
+            e[4] = sqrt((double)(mom[0] * mom[0] + mom[1] * mom[1] + mom[2] * mom[2]));
+            e[5] = n > 0 ? 2.0 * K / (3.0 * (double)n) : 0.0;
+            e[6] = e[3] + dof * p->kT * (0.5 * p->nh_tau * p->nh_tau * xi1 * xi1 + eta1);
+        }
+        if (k == n_steps) break;
+        xi = xi1;
+        eta = eta1;
+        /* the start of step n */
+        const double s2 = nh_half(p, dof, h, &xi, &eta, &K);
+        for (int64_t i = 0; i < 3 * n; ++i) {
+            vel[i] = s2 * (s1 * vE[i]) + hm * Fc[i];
+            pos[i] += p->dt * vel[i];
+        }
+    }
+    xe[0] = xi;
+    xe[1] = eta;
+    free(BL); free(BN); free(D); free(V); free(G); free(Ff); free(Fb); free(Fc); free(vE);
+    return 0;
+}
+
 /* ------------------------------------------------------------ A1: order */
 
 /* Sort key of a chain: the cell of its first bead, numbered brick by brick

@@ -52,6 +52,9 @@ typedef struct {
                            1: exact derivative of the CIC field energy (pinning variant) */
     double angle_k;     /* U = angle_k (cos theta - angle_cos0)^2 per bonded triplet */
     double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles */
+    int32_t thermostat; /* 0: Langevin (gamma); 1: Nose-Hoover (section "MD methods and
+                           algorithms" names it for NVT; orc_run_nh) */
+    double nh_tau;      /* Nose-Hoover relaxation time tau (> 0) */
 } orc_params;
 
 int orc_num_threads(void);
@@ -108,6 +111,26 @@ int orc_run(const orc_params* p, int64_t n, double* pos, double* vel, const int3
 
 /* Chain order used by the bead sort: key of each chain (first bead's cell in
  * brick-major order, bricks of `brick` cells per axis). */
+/* Nose-Hoover NVT (section "MD methods and algorithms" names the thermostat;
+ * the equations are Hoover's): dv/dt = F/m - xi v, dxi/dt = (2 K / (g kT) - 1) / tau^2,
+ * deta/dt = xi, g = 3 (n - 1) kinetic degrees of freedom (3 for n = 1); the
+ * extended energy E + g kT (tau^2 xi^2 / 2 + eta) is conserved.  State
+ * (x_n, v_{n-1/2}, xi, eta) with xi, eta at the middle of step n - 1.  Each
+ * step n: refresh the field if due; F_n; v^E = v + dt/(2m) F_n (the on-step
+ * velocity before the thermostat); two thermostat half steps T(dt/2) (the end
+ * of step n - 1 and the start of step n), each
+ *   xi += (h/2) G(K); v *= exp(-xi h); K *= exp(-2 xi h); eta += xi h;
+ *   xi += (h/2) G(K),      G(K) = (2 K / (g kT) - 1) / tau^2, h = dt/2;
+ * then v <- v + dt/(2m) F_n; x <- x + dt v.  xe = (xi, eta) in and out.
+ * energies (optional): [n_steps + 1][7] records at each step before its
+ * update: kinetic (on-step, after the pending half step), bonded, field,
+ * total, |P|, T, and the extended energy.  Returns 0, or -1 on bad input.
+ * Parity: pinned (NVE limit, free-particle thermostat ODE, extended-energy
+ * conservation, mean temperature). */
+int orc_run_nh(const orc_params* p, int64_t n, double* pos, double* vel, const int32_t* type,
+               int64_t n_bonds, const int32_t* pairs, int64_t step0, int32_t n_steps,
+               double xe[2], double* energies);
+
 int64_t orc_cell_key(const orc_params* p, const double* x, int32_t brick);
 
 #ifdef __cplusplus
