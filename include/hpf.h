@@ -81,6 +81,9 @@ typedef struct {
     double angle_k;       /* angle potential U = angle_k (cos theta - angle_cos0)^2 for every */
     double angle_cos0;    /* bonded triplet (section "Bonded forces", cosine form), theta the
                              angle at the middle bead (pi for a straight chain); 0: none */
+    int32_t thermostat;   /* 0: Langevin (gamma, seed); 1: Nose-Hoover NVT (nh_tau; gamma and
+                             seed unused), see hpf_get_thermostat */
+    double nh_tau;        /* Nose-Hoover relaxation time tau (> 0 when thermostat == 1) */
 } hpf_params;
 
 /* Text for a status code (static storage). */
@@ -197,8 +200,10 @@ hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
  * key = (seed lo, seed hi)), uniforms u = (2 (r >> 9) + 1) 2^-24; x, y from
  * (u0, u1) and z from (u2, u3).  The field is refreshed from the positions
  * when n % field_every == 0 (or when no field is valid) and held fixed in
- * between, as in the MD-SCF section.
- * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
+ * between, as in the MD-SCF section.  With thermostat == 1 the step is the
+ * Nose-Hoover scheme below instead (no friction or noise).
+ * Errors: HPF_ERR_INVALID (n_steps < 0; Nose-Hoover with chains longer than
+ * 64 beads), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
 
 /* Observables at the current step, reduced in FP64 (synchronises):
@@ -209,6 +214,34 @@ hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
  * out[4] |total momentum| of v_n, out[5] kinetic temperature 2 KE / (3 N).
  * Errors: HPF_ERR_INVALID (out NULL), HPF_ERR_STATE, HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
 hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
+
+/* Nose-Hoover NVT (thermostat == 1; the section "MD methods and algorithms"
+ * names the thermostat for the canonical ensemble, with Hoover's equations
+ *   dv/dt = F/m - xi v,  dxi/dt = (2K / (g kT) - 1) / tau^2,  deta/dt = xi,
+ * g = 3 (n - 1) kinetic degrees of freedom (3 for n = 1)).  The state is
+ * (x_n, v_{n-1/2}, xi, eta) with xi, eta at the middle of step n - 1.  Each
+ * step n of hpf_step: the field refresh when due; F_n; v^E = v + dt/(2m) F_n;
+ * two thermostat half steps T(dt/2) (the end of step n - 1, the start of step
+ * n) on the kinetic energy K of v^E, each
+ *   xi += (h/2) G(K); v *= exp(-xi h); K *= exp(-2 xi h); eta += xi h; xi += (h/2) G(K),
+ *   G(K) = (2K / (g kT) - 1) / tau^2, h = dt/2;
+ * then v <- v + dt/(2m) F_n; x <- x + dt v.  K is summed in FP64 over the
+ * beads in a fixed order.  hpf_energy reports the step's on-step quantities
+ * after the pending half step (kinetic energy, |P| and T of s v^E).  Needs
+ * chains of at most 64 beads (HPF_ERR_INVALID from hpf_step otherwise); not
+ * available in batches or learned windows.
+ *
+ * xi, eta of the state (out[2]); hpf_set_state resets them to zero.
+ * Synchronises.  Errors: HPF_ERR_INVALID (no Nose-Hoover thermostat), HPF_ERR_CUDA. */
+hpf_status hpf_get_thermostat(hpf_ctx* ctx, double out[2]);
+/* Restore xi, eta (in[2], finite), e.g. with hpf_set_state from a checkpoint.
+ * Synchronises.  Errors: HPF_ERR_INVALID, HPF_ERR_CUDA. */
+hpf_status hpf_set_thermostat(hpf_ctx* ctx, const double in[2]);
+/* The extended energy conserved by the Nose-Hoover equations at the current
+ * step: the total energy of hpf_energy + g kT (tau^2 xi^2 / 2 + eta), with
+ * xi, eta advanced by the pending half step.  Synchronises.
+ * Errors: as hpf_energy, HPF_ERR_INVALID (no Nose-Hoover thermostat). */
+hpf_status hpf_nh_conserved(hpf_ctx* ctx, double* H);
 
 /* Stage profiling.  Every kernel launch of a context is counted by stage;
  * while profiling is enabled, CUDA events recorded on the context's stream

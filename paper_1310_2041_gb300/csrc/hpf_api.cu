@@ -63,6 +63,11 @@ struct hpf_ctx {
     std::vector<cudaEvent_t> ev_free;
     std::string err;
     struct LearnedBufs* learned = nullptr;  // learned-propagator buffers (allocated on first use)
+    // Nose-Hoover (thermostat == 1): device state, constants, grid, host mirror
+    NhDev* nh = nullptr;
+    NhConsts nhc{};
+    int nh_blocks = 0;
+    double* h_nh = nullptr;  // pinned [2]: xi, eta
 };
 
 // Buffers of the learned-propagator driver and the density judge.
@@ -187,6 +192,8 @@ hpf_status validate_params(const hpf_params* p) {
     if (p->force_mode != 0 && p->force_mode != 1) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
         return HPF_ERR_INVALID;
+    if (p->thermostat != 0 && p->thermostat != 1) return HPF_ERR_INVALID;
+    if (p->thermostat == 1 && !(p->nh_tau > 0.0 && isfinite(p->nh_tau))) return HPF_ERR_INVALID;
     return HPF_OK;
 }
 
@@ -223,8 +230,10 @@ void derive_constants(hpf_ctx* c) {
     StepConsts& s = c->sc;
     s.dt = (float)p.dt;
     s.dt_m = (float)(p.dt / p.mass);
-    s.fric = (float)(p.gamma * p.mass);
-    s.sigma = (float)sqrt(2.0 * p.gamma * p.mass * p.kT / p.dt);
+    // Nose-Hoover replaces the Langevin friction and noise
+    const double gamma = p.thermostat == 1 ? 0.0 : p.gamma;
+    s.fric = (float)(gamma * p.mass);
+    s.sigma = (float)sqrt(2.0 * gamma * p.mass * p.kT / p.dt);
     s.two_k = (float)(2.0 * p.bond_k);
     s.r0 = (float)p.bond_r0;
     s.seed_lo = (uint32_t)p.seed;
@@ -252,6 +261,11 @@ void derive_constants(hpf_ctx* c) {
         for (int j = 0; j < p.n_species; ++j) e.chi[k][j] = p.chi[k * HPF_MAX_SPECIES + j];
     e.S = p.n_species;
     e.n = p.n_beads;
+    NhConsts& t = c->nhc;
+    t.h = 0.5 * p.dt;
+    t.dof_kT = (p.n_beads > 1 ? 3.0 * (p.n_beads - 1) : 3.0 * p.n_beads) * p.kT;
+    t.inv_tau2 = p.thermostat == 1 ? 1.0 / (p.nh_tau * p.nh_tau) : 0.0;
+    t.mass = p.mass;
 }
 
 size_t stage_bytes(int n) {
@@ -505,6 +519,63 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse) {
     return HPF_OK;
 }
 
+// Nose-Hoover: `chunk` steps on the field in force (one launch per step plus
+// one, see k_nh.cu); with fuse the last launch deposits its positions into
+// the other mesh (which must be zero).
+hpf_status advance_nh(hpf_ctx* c, int chunk, bool fuse) {
+    {
+        StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? chunk + 1 : 0);
+        if (c->n > 0) {
+            NhParams p;
+            memset(&p, 0, sizeof p);
+            p.st = c->st[c->cur];
+            p.meta = c->meta;
+            p.seg_start = c->sb.seg_start;
+            p.seg_count = c->sb.seg_count;
+            p.n_seg = c->sb.n_seg;
+            p.g = c->geom;
+            p.G = c->G;
+            p.c = c->sc;
+            p.t = c->nhc;
+            p.nh = c->nh;
+            p.flag = c->dflag;
+            // F_n and the thermostat at the first step (after a refresh or a call boundary)
+            p.kick_drift = 0;
+            p.force_kick = 1;
+            launch_nh_step(p, c->nh_blocks, c->stream);
+            for (int j = 0; j < chunk; ++j) {
+                const bool last = j == chunk - 1;
+                p.kick_drift = 1;
+                p.force_kick = last ? 0 : 1;
+                p.D_next = (last && fuse) ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
+                launch_nh_step(p, c->nh_blocks, c->stream);
+            }
+        }
+    }
+    LAUNCH_CHECK(c);
+    c->step += chunk;
+    if (fuse) {
+        c->dmesh ^= 1;
+        c->mesh_step = c->step;
+        c->next_zero = false;
+    }
+    return HPF_OK;
+}
+
+// The pending thermostat half step of the current step (the end of the last
+// one) applied on the host to the on-step quantities of the state: returns
+// the velocity scale and advances copies of xi, eta and K.
+double nh_pending_half(const hpf_ctx* c, double& xi, double& eta, double& K) {
+    const NhConsts& t = c->nhc;
+    auto rate = [&](double k) { return t.dof_kT > 0.0 ? (2.0 * k / t.dof_kT - 1.0) * t.inv_tau2 : 0.0; };
+    xi += 0.5 * t.h * rate(K);
+    const double s = exp(-xi * t.h);
+    K *= s * s;
+    eta += xi * t.h;
+    xi += 0.5 * t.h * rate(K);
+    return s;
+}
+
 hpf_status check_flags(hpf_ctx* c) {
     CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
                                 c->stream));
@@ -575,6 +646,11 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
                            sizeof(double) * energy_partials_needed(c->n, c->geom.nodes));
     e = e ? e : cudaMalloc(&c->d_out6, sizeof(double) * 8);
     e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
+    if (params->thermostat == 1) {
+        e = e ? e : cudaMalloc(&c->nh, sizeof(NhDev));
+        e = e ? e : cudaMallocHost(&c->h_nh, sizeof(double) * 2);
+        e = e ? e : cudaMemsetAsync(c->nh, 0, sizeof(NhDev), c->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cleanup(e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA);
@@ -641,6 +717,8 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->d_out6);
     cudaFreeHost(c->h_out6);
+    cudaFree(c->nh);
+    cudaFreeHost(c->h_nh);
     if (LearnedBufs* L = c->learned) {
         cudaFree(L->Dbase);
         cudaFree(L->Dp);
@@ -731,6 +809,11 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     if (s2 != HPF_OK) return s2;
     c->step = step;
     c->field_step = -1;
+    if (c->nh) {
+        // a loaded state starts with the thermostat at rest (hpf_set_thermostat restores one)
+        CUDA_TRY(c, cudaMemsetAsync(c->nh, 0, sizeof(NhDev), c->stream));
+        c->nh_blocks = nh_grid(c->C);
+    }
     c->has_state = true;
     return HPF_OK;
 }
@@ -843,6 +926,23 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
     const long long fe = c->p.field_every;
     long long left = n_steps;
+    if (c->nh) {
+        if (c->n > 0 && !c->warp_mode)
+            return fail(c, HPF_ERR_INVALID, "Nose-Hoover steps need chains of at most 64 beads");
+        while (left > 0) {
+            hpf_status s = ensure_field(c);
+            if (s != HPF_OK) return s;
+            long long chunk = fe - (c->step % fe);
+            if (chunk > left) chunk = left;
+            if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
+                if ((s = sort_beads(c)) != HPF_OK) return s;
+            }
+            const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
+            if ((s = advance_nh(c, (int)chunk, fuse)) != HPF_OK) return s;
+            left -= chunk;
+        }
+        return HPF_OK;
+    }
     while (left > 0) {
         hpf_status s = ensure_field(c);
         if (s != HPF_OK) return s;
@@ -878,8 +978,58 @@ hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     LAUNCH_CHECK(c);
     CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,
                                 c->stream));
+    if (c->nh)
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                                    c->stream));
     if ((s = check_flags(c)) != HPF_OK) return s;
     memcpy(out, c->h_out6, sizeof(double) * 6);
+    if (c->nh) {
+        // the kernels give the on-step velocity before the pending thermostat half step
+        double xi = c->h_nh[0], eta = c->h_nh[1], K = out[0];
+        const double sc = nh_pending_half(c, xi, eta, K);
+        out[0] = K;
+        out[3] = K + out[1] + out[2];
+        out[4] *= sc;
+        out[5] *= sc * sc;
+    }
+    return HPF_OK;
+}
+
+hpf_status hpf_get_thermostat(hpf_ctx* c, double out[2]) {
+    if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
+    if (!c->nh) return fail(c, HPF_ERR_INVALID, "the context has no Nose-Hoover thermostat");
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out[0] = c->h_nh[0];
+    out[1] = c->h_nh[1];
+    return HPF_OK;
+}
+
+hpf_status hpf_set_thermostat(hpf_ctx* c, const double in[2]) {
+    if (!c || !in) return fail(c, HPF_ERR_INVALID, "in is required");
+    if (!c->nh) return fail(c, HPF_ERR_INVALID, "the context has no Nose-Hoover thermostat");
+    if (!isfinite(in[0]) || !isfinite(in[1])) return fail(c, HPF_ERR_INVALID, "non-finite xi or eta");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the pinned mirror may still be in use
+    c->h_nh[0] = in[0];
+    c->h_nh[1] = in[1];
+    CUDA_TRY(c, cudaMemcpyAsync(c->nh, c->h_nh, sizeof(double) * 2, cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return HPF_OK;
+}
+
+hpf_status hpf_nh_conserved(hpf_ctx* c, double* H) {
+    if (!c || !H) return fail(c, HPF_ERR_INVALID, "H is required");
+    if (!c->nh) return fail(c, HPF_ERR_INVALID, "the context has no Nose-Hoover thermostat");
+    double e[6];
+    hpf_status s = hpf_energy(c, e);
+    if (s != HPF_OK) return s;
+    // hpf_energy left the state's xi, eta in the pinned mirror and the kinetic
+    // energy before the pending half step in the energy mirror
+    double xi = c->h_nh[0], eta = c->h_nh[1], K = c->h_out6[0];
+    nh_pending_half(c, xi, eta, K);
+    *H = e[3] + c->nhc.dof_kT * (0.5 * c->p.nh_tau * c->p.nh_tau * xi * xi + eta);
     return HPF_OK;
 }
 
@@ -1123,6 +1273,8 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
             params[r].force_mode != params[0].force_mode ||
             (params[r].angle_k != 0.0) != (params[0].angle_k != 0.0))
             return HPF_ERR_INVALID;
+    for (int r = 0; r < n_replicas; ++r)
+        if (params[r].thermostat != 0) return HPF_ERR_INVALID;  // batches run Langevin
     hpf_batch* b = new hpf_batch();
     b->R = n_replicas;
     b->stream = (cudaStream_t)stream;
@@ -1383,6 +1535,7 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
     if (!prop || n_windows < 0 || K < 2 || K > 64 || !(tol >= 0.0))
         return fail(c, HPF_ERR_INVALID, "need a network, n_windows >= 0, 2 <= K <= 64, tol >= 0");
     if (c->S != 2) return fail(c, HPF_ERR_INVALID, "the propagator models two species");
+    if (c->nh) return fail(c, HPF_ERR_INVALID, "learned windows run the Langevin thermostat");
     if (!prop_mesh_is(prop, c->geom))
         return fail(c, HPF_ERR_INVALID, "the network's mesh differs from the context's");
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");

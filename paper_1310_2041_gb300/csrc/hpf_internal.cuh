@@ -410,6 +410,97 @@ __device__ __forceinline__ void angle_force(float ux, float uy, float uz, float 
     fbz = g * (uz * inv - cb * wz);
 }
 
+// Bonded forces of one warp segment of whole chains: lane l holds beads 2l
+// and 2l + 1 at (x0, y0, z0) and (x1, y1, z1); p0, n0: bead 2l is bonded to
+// its previous / next bead, n1: bead 2l + 1 to its next.  Returns the summed
+// bond (and, with kAngles, angle) forces on the lane's two beads.
+template <bool kAngles>
+__device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0, float x1, float y1,
+                                                   float z1, bool p0, bool n0, bool n1,
+                                                   const StepConsts& c, int lane, float& w0x,
+                                                   float& w0y, float& w0z, float& w1x,
+                                                   float& w1y, float& w1z) {
+    // every bond is evaluated once: bond (2l, 2l + 1) inside the lane, bond
+    // (2l + 1, 2l + 2) with the next lane's first bead, whose share (the
+    // opposite force) goes back up one lane
+    const float dx = __shfl_down_sync(0xffffffffu, x0, 1);
+    const float dy = __shfl_down_sync(0xffffffffu, y0, 1);
+    const float dz = __shfl_down_sync(0xffffffffu, z0, 1);
+    float ax = 0.f, ay = 0.f, az = 0.f;  // on bead 2l from bead 2l + 1
+    bond_force(x0 - x1, y0 - y1, z0 - z1, n0 ? c.two_k : 0.0f, c.r0, ax, ay, az);
+    float nx = 0.f, ny = 0.f, nz = 0.f;  // on bead 2l + 1 from bead 2l + 2
+    bond_force(x1 - dx, y1 - dy, z1 - dz, n1 ? c.two_k : 0.0f, c.r0, nx, ny, nz);
+    const float ux = __shfl_up_sync(0xffffffffu, nx, 1);  // previous lane's share
+    const float uy = __shfl_up_sync(0xffffffffu, ny, 1);
+    const float uz = __shfl_up_sync(0xffffffffu, nz, 1);
+    // angles, each evaluated once by the lane of its middle bead: at bead 2l
+    // (ends 2l - 1, 2l + 1) and at bead 2l + 1 (ends 2l, 2l + 2); the shares
+    // of the end beads held by the neighbouring lanes go there by one shuffle
+    float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
+    if (kAngles) {
+        const float px = __shfl_up_sync(0xffffffffu, x1, 1);  // bead 2l - 1
+        const float py = __shfl_up_sync(0xffffffffu, y1, 1);
+        const float pz = __shfl_up_sync(0xffffffffu, z1, 1);
+        float fpx, fpy, fpz, f1x, f1y, f1z, f0x, f0y, f0z, fdx, fdy, fdz;
+        angle_force(px - x0, py - y0, pz - z0, x1 - x0, y1 - y0, z1 - z0,
+                    (p0 && n0) ? c.two_ka : 0.0f, c.cos0, fpx, fpy, fpz, f1x, f1y, f1z);
+        angle_force(x0 - x1, y0 - y1, z0 - z1, dx - x1, dy - y1, dz - z1,
+                    (n0 && n1) ? c.two_ka : 0.0f, c.cos0, f0x, f0y, f0z, fdx, fdy, fdz);
+        // from lane l - 1: its share on bead 2l; from lane l + 1: its share on bead 2l + 1
+        const float r0x = __shfl_up_sync(0xffffffffu, fdx, 1);
+        const float r0y = __shfl_up_sync(0xffffffffu, fdy, 1);
+        const float r0z = __shfl_up_sync(0xffffffffu, fdz, 1);
+        const float r1x = __shfl_down_sync(0xffffffffu, fpx, 1);
+        const float r1y = __shfl_down_sync(0xffffffffu, fpy, 1);
+        const float r1z = __shfl_down_sync(0xffffffffu, fpz, 1);
+        const bool first = lane == 0, last = lane == 31;
+        q0x = f0x - (fpx + f1x) + (first ? 0.f : r0x);
+        q0y = f0y - (fpy + f1y) + (first ? 0.f : r0y);
+        q0z = f0z - (fpz + f1z) + (first ? 0.f : r0z);
+        q1x = f1x - (f0x + fdx) + (last ? 0.f : r1x);
+        q1y = f1y - (f0y + fdy) + (last ? 0.f : r1y);
+        q1z = f1z - (f0z + fdz) + (last ? 0.f : r1z);
+    }
+    w0x = (p0 ? ax - ux : ax) + q0x;
+    w0y = (p0 ? ay - uy : ay) + q0y;
+    w0z = (p0 ? az - uz : az) + q0z;
+    w1x = (nx - ax) + q1x;
+    w1y = (ny - ay) + q1y;
+    w1z = (nz - az) + q1z;
+}
+
+// Nose-Hoover thermostat: device-resident state of one context.
+constexpr int kNhMaxBlocks = 2048;
+struct NhDev {
+    double xi, eta;       // at the middle of the last step
+    double ke;            // kinetic energy of the last reduction (v^E, before the half steps)
+    float s1, s2;         // velocity scales of the last two thermostat half steps
+    unsigned int ticket;  // blocks done with the current reduction
+    double part[kNhMaxBlocks];
+};
+struct NhConsts {
+    double h;         // dt / 2
+    double dof_kT;    // g kT, g = 3 (n - 1) kinetic degrees of freedom (3 for n = 1)
+    double inv_tau2;  // 1 / tau^2
+    double mass;
+};
+struct NhParams {
+    StateBuf st;  // advanced in place
+    const uint32_t* meta;
+    const int* seg_start;
+    const int* seg_count;
+    const int* n_seg;
+    MeshGeom g;
+    const float4* G;
+    StepConsts c;
+    NhConsts t;
+    NhDev* nh;
+    unsigned long long* D_next;  // deposit the final positions (kick_drift-only launches)
+    int* flag;
+    int kick_drift;  // v = s2 (s1 v) + dt/(2m) F; x += dt v
+    int force_kick;  // v += dt/(2m) F at the (new) positions; K; thermostat half steps
+};
+
 // ------------------------------------------------------------------ launchers
 
 void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
@@ -418,6 +509,8 @@ void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta
                        cudaStream_t s);
 void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g,
                     unsigned long long* D, cudaStream_t s);
+int nh_grid(int max_seg);
+void launch_nh_step(const NhParams& p, int blocks, cudaStream_t s);
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
                   unsigned long long* D_clear, cudaStream_t s);
 void launch_unpad_field(const float4* G, MeshGeom g, int S, float4* out, cudaStream_t s);

@@ -498,47 +498,9 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
     const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
     const bool n1 = (b1.m & kBondNext) != 0;  // b1's previous bond is b0's next
     for (int k = 0; k < n_sub; ++k) {
-        // every bond is evaluated once: bond (2l, 2l + 1) inside the lane, bond
-        // (2l + 1, 2l + 2) with the next lane's first bead, whose share (the
-        // opposite force) goes back up one lane
-        const float dx = __shfl_down_sync(0xffffffffu, b0.x, 1);
-        const float dy = __shfl_down_sync(0xffffffffu, b0.y, 1);
-        const float dz = __shfl_down_sync(0xffffffffu, b0.z, 1);
-        float ax = 0.f, ay = 0.f, az = 0.f;  // on bead 2l from bead 2l + 1
-        bond_force(b0.x - b1.x, b0.y - b1.y, b0.z - b1.z, n0 ? c.two_k : 0.0f, c.r0, ax, ay, az);
-        float nx = 0.f, ny = 0.f, nz = 0.f;  // on bead 2l + 1 from bead 2l + 2
-        bond_force(b1.x - dx, b1.y - dy, b1.z - dz, n1 ? c.two_k : 0.0f, c.r0, nx, ny, nz);
-        const float ux = __shfl_up_sync(0xffffffffu, nx, 1);  // previous lane's share
-        const float uy = __shfl_up_sync(0xffffffffu, ny, 1);
-        const float uz = __shfl_up_sync(0xffffffffu, nz, 1);
-        // angles, each evaluated once by the lane of its middle bead: at bead 2l
-        // (ends 2l - 1, 2l + 1) and at bead 2l + 1 (ends 2l, 2l + 2); the shares
-        // of the end beads held by the neighbouring lanes go there by one shuffle
-        float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
-        if (kAngles) {
-            const float px = __shfl_up_sync(0xffffffffu, b1.x, 1);  // bead 2l - 1
-            const float py = __shfl_up_sync(0xffffffffu, b1.y, 1);
-            const float pz = __shfl_up_sync(0xffffffffu, b1.z, 1);
-            float fpx, fpy, fpz, f1x, f1y, f1z, f0x, f0y, f0z, fdx, fdy, fdz;
-            angle_force(px - b0.x, py - b0.y, pz - b0.z, b1.x - b0.x, b1.y - b0.y, b1.z - b0.z,
-                        (p0 && n0) ? c.two_ka : 0.0f, c.cos0, fpx, fpy, fpz, f1x, f1y, f1z);
-            angle_force(b0.x - b1.x, b0.y - b1.y, b0.z - b1.z, dx - b1.x, dy - b1.y, dz - b1.z,
-                        (n0 && n1) ? c.two_ka : 0.0f, c.cos0, f0x, f0y, f0z, fdx, fdy, fdz);
-            // from lane l - 1: its share on bead 2l; from lane l + 1: its share on bead 2l + 1
-            const float r0x = __shfl_up_sync(0xffffffffu, fdx, 1);
-            const float r0y = __shfl_up_sync(0xffffffffu, fdy, 1);
-            const float r0z = __shfl_up_sync(0xffffffffu, fdz, 1);
-            const float r1x = __shfl_down_sync(0xffffffffu, fpx, 1);
-            const float r1y = __shfl_down_sync(0xffffffffu, fpy, 1);
-            const float r1z = __shfl_down_sync(0xffffffffu, fpz, 1);
-            const bool first = lane == 0, last = lane == 31;
-            q0x = f0x - (fpx + f1x) + (first ? 0.f : r0x);
-            q0y = f0y - (fpy + f1y) + (first ? 0.f : r0y);
-            q0z = f0z - (fpz + f1z) + (first ? 0.f : r0z);
-            q1x = f1x - (f0x + fdx) + (last ? 0.f : r1x);
-            q1y = f1y - (f0y + fdy) + (last ? 0.f : r1y);
-            q1z = f1z - (f0z + fdz) + (last ? 0.f : r1z);
-        }
+        float w0x, w0y, w0z, w1x, w1y, w1z;  // bonded forces on the lane's two beads
+        warp_bonded_forces<kAngles>(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, p0, n0, n1, c, lane, w0x,
+                                    w0y, w0z, w1x, w1y, w1z);
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
         cell_check<kExact>(b0, G, g, wcache, tid, f00, f01, f02);
@@ -548,11 +510,9 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
             gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z,
-                                  (p0 ? ax - ux : ax) + q0x, (p0 ? ay - uy : ay) + q0y,
-                                  (p0 ? az - uz : az) + q0z, c, g, wcache, tid);
-        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, (nx - ax) + q1x,
-                                  (ny - ay) + q1y, (nz - az) + q1z, c, g, wcache,
+        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
+                                  tid);
+        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
                                   kWarpBlock + tid);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);

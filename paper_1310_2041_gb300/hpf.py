@@ -57,6 +57,8 @@ class Params(ctypes.Structure):
         ("force_mode", ctypes.c_int32),
         ("angle_k", ctypes.c_double),
         ("angle_cos0", ctypes.c_double),
+        ("thermostat", ctypes.c_int32),
+        ("nh_tau", ctypes.c_double),
     ]
 
 
@@ -106,6 +108,9 @@ def load():
         L.hpf_forces.argtypes = [vp, vp, i32]
         L.hpf_step.argtypes = [vp, i32]
         L.hpf_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_get_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_set_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_nh_conserved.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_batch_init.argtypes = [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
         L.hpf_batch_replica.argtypes = [vp, i32]
         L.hpf_batch_replica.restype = vp
@@ -145,7 +150,8 @@ def load():
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state", "hpf_update_state",
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
                      "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile",
-                     "hpf_set_field_tile"):
+                     "hpf_set_field_tile", "hpf_get_thermostat", "hpf_set_thermostat",
+                     "hpf_nh_conserved"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib
@@ -153,7 +159,8 @@ def load():
 
 def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
                 bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
-                sort_every=0, force_mode=0, angle_k=0.0, angle_cos0=-1.0, **_ignored) -> Params:
+                sort_every=0, force_mode=0, angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0,
+                **_ignored) -> Params:
     p = Params()
     p.n_beads, p.n_species = int(n_beads), int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -174,6 +181,7 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
     p.field_every, p.sort_every = int(field_every), int(sort_every)
     p.force_mode = int(force_mode)
     p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
+    p.thermostat, p.nh_tau = int(thermostat), float(nh_tau)
     return p
 
 
@@ -339,6 +347,23 @@ class System:
         out = (ctypes.c_double * 6)()
         self._check(self.lib.hpf_energy(self.h, out))
         return np.array(list(out))
+
+    # ---- Nose-Hoover thermostat (thermostat == 1)
+    def get_thermostat(self):
+        """(xi, eta) of the state, at the middle of the last step."""
+        out = (ctypes.c_double * 2)()
+        self._check(self.lib.hpf_get_thermostat(self.h, out))
+        return float(out[0]), float(out[1])
+
+    def set_thermostat(self, xi, eta):
+        arr = (ctypes.c_double * 2)(float(xi), float(eta))
+        self._check(self.lib.hpf_set_thermostat(self.h, arr))
+
+    def nh_conserved(self):
+        """The extended energy conserved by the Nose-Hoover equations."""
+        v = ctypes.c_double()
+        self._check(self.lib.hpf_nh_conserved(self.h, ctypes.byref(v)))
+        return v.value
 
     # ---- learned propagator
     def density_phi(self, out=None):
