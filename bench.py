@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--thermostat", default="langevin", choices=["langevin", "nh"],
+                    help="plain workloads: Langevin (the default) or Nose-Hoover NVT")
+    ap.add_argument("--nh-tau", type=float, default=1.0)
     ap.add_argument("--net-lags", default="",
                     help="learned workload: also train and judge a network at these lags "
                          "(comma-separated step counts)")
@@ -131,25 +134,31 @@ def traffic_record():
     return rec if rec.get("source_sha256") == h.hexdigest() else None
 
 
-def cpu_oracle_rate(w, data, budget_s: float):
+def cpu_oracle_rate(w, data, budget_s: float, over=None):
     """Oracle bead-steps/s on the full workload, whole field periods until about
     budget_s of CPU work (a 2 %-of-chains calibration sizes the sample)."""
     import oracle
     oracle.build()
-    op = oracle.make_params(**w.params())
+    pp = dict(w.params(), **(over or {}))
+    op = oracle.make_params(**pp)
+    if pp.get("thermostat", 0) == 1:
+        def run(p, pos, vel, types, bonds, step0, n_steps):
+            return oracle.run_nh(p, pos, vel, types, bonds, step0, n_steps)
+    else:
+        run = oracle.run
     n_chains_total = w.blocks[0][0]
     clen = len(w.blocks[0][1])
     c0 = max(1, n_chains_total // 50)
     n0 = c0 * clen
     t = time.perf_counter()
-    oracle.run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
-               data["bonds"][: c0 * (clen - 1)], 0, w.field_every)
+    run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
+        data["bonds"][: c0 * (clen - 1)], 0, w.field_every)
     per_bead_step = (time.perf_counter() - t) / (w.field_every * n0)
     n = w.n_beads
     periods = int(max(1, min(50, budget_s / (per_bead_step * n * w.field_every))))
     steps = periods * w.field_every
     t = time.perf_counter()
-    oracle.run(op, data["pos"], data["vel"], data["type"], data["bonds"], 0, steps)
+    run(op, data["pos"], data["vel"], data["type"], data["bonds"], 0, steps)
     dt = time.perf_counter() - t
     return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
@@ -198,15 +207,25 @@ def run_reference(args):
     w = W.WORKLOADS[args.workload]()
     data = W.generate(w)
     oracle.build()
-    op = oracle.make_params(**w.params())
+    nh = args.thermostat == "nh"
+    op = oracle.make_params(**dict(w.params(), **({"thermostat": 1, "nh_tau": args.nh_tau}
+                                                  if nh else {})))
+
+    def run(p, pos, vel, types, bonds, step0, n_steps, xe=(0.0, 0.0)):
+        if nh:
+            po, vo, xo, _ = oracle.run_nh(p, pos, vel, types, bonds, step0, n_steps, xe)
+            return po, vo, xo
+        po, vo, _ = oracle.run(p, pos, vel, types, bonds, step0, n_steps)
+        return po, vo, xe
+
     n_chains_total = w.blocks[0][0]
     clen = len(w.blocks[0][1])
     # calibrate, then size every step's sample so the run takes about 90 s
     c0 = max(1, n_chains_total // 50)
     n0 = c0 * clen
     t = time.perf_counter()
-    oracle.run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
-               data["bonds"][: c0 * (clen - 1)], 0, 1)
+    run(op, data["pos"][:n0], data["vel"][:n0], data["type"][:n0],
+        data["bonds"][: c0 * (clen - 1)], 0, 1)
     per_bead_step = time.perf_counter() - t
     per_bead_step /= n0
     total = max(1, args.steps + args.warmup)
@@ -214,10 +233,11 @@ def run_reference(args):
     n = chains * clen
     pos, vel = data["pos"][:n].astype(np.float64), data["vel"][:n].astype(np.float64)
     types, bonds = data["type"][:n], data["bonds"][: chains * (clen - 1)]
+    xe = (0.0, 0.0)
     if args.warmup > 0:
-        pos, vel, _e = oracle.run(op, pos, vel, types, bonds, 0, args.warmup)
+        pos, vel, xe = run(op, pos, vel, types, bonds, 0, args.warmup)
     t = time.perf_counter()
-    pos, vel, _e = oracle.run(op, pos, vel, types, bonds, args.warmup, args.steps)
+    pos, vel, xe = run(op, pos, vel, types, bonds, args.warmup, args.steps, xe)
     dt = time.perf_counter() - t
     value = n * args.steps / dt
     sample = (f"each step: one MD step (field refreshed every {w.field_every}) of the first "
@@ -226,7 +246,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_beads": w.n_beads, "sample_beads": n},
+            "config": {"workload": w.name, "n_beads": w.n_beads, "sample_beads": n,
+                       "thermostat": f"nose-hoover tau={args.nh_tau}" if nh else "langevin"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -252,6 +273,9 @@ def run_ours(args):
     data = W.generate(w, seed=w.seed + rank)
     pp = w.params()
     pp["sort_every"] = args.sort_every
+    nh = args.thermostat == "nh"
+    therm = {"thermostat": 1, "nh_tau": args.nh_tau} if nh else {}
+    pp.update(therm)
     stream = torch.cuda.current_stream()
     sysm = hpf.System(hpf.make_params(**pp), stream=stream)
     dev = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
@@ -299,7 +323,8 @@ def run_ours(args):
     dev_ms = float(t_max.item())
     value = w.n_beads * args.steps * world / (dev_ms * 1e-3)
 
-    # dominant kernel: the fused step kernel (one launch per field period)
+    # dominant kernel: the fused step kernel (one launch per field period;
+    # Nose-Hoover: one per step plus one per period)
     step_ms, step_launches = prof["step"]
     avg_launch_s = step_ms * 1e-3 / max(step_launches, 1)
     bead_steps_per_launch = w.n_beads * args.steps / max(step_launches, 1)
@@ -310,13 +335,14 @@ def run_ours(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    tr = traffic_record()
+    tr = None if nh else traffic_record()
     traffic = None
     if tr:
         traffic = tr["dram_bytes_per_launch"] * bead_steps_per_launch / tr["bead_steps_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                "kernel": "k_step_warp_batch", "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
+                "kernel": "k_nh_step" if nh else "k_step_warp_batch",
+                "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
                 "avg_launch_us": avg_launch_s * 1e6,
                 "stage_ms": {k: round(v[0], 4) for k, v in prof.items()}}
     launches = int(sum(v[1] for v in prof.values()))
@@ -346,7 +372,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(w, data, budget_s=12.0)
+        cpu = cpu_oracle_rate(w, data, budget_s=12.0, over=therm)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -356,6 +382,8 @@ def run_ours(args):
                 "config": {"workload": w.name, "n_beads": w.n_beads, "mesh": w.mesh,
                            "species": w.n_species, "field_every": fe,
                            "sort_every": args.sort_every, "parallelism": f"replicas{world}",
+                           "thermostat": (f"nose-hoover tau={args.nh_tau}" if nh else
+                                          f"langevin gamma={pp['gamma']}"),
                            "l2": "flushed (256 MB write) before each timed field period",
                            "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "hpf_internal.cuh"
+#include "nh_internal.cuh"
 
 using namespace hpf;
 
@@ -63,10 +64,13 @@ struct hpf_ctx {
     std::vector<cudaEvent_t> ev_free;
     std::string err;
     struct LearnedBufs* learned = nullptr;  // learned-propagator buffers (allocated on first use)
-    // Nose-Hoover (thermostat == 1): device state, constants, grid, host mirror
+    // Nose-Hoover (thermostat == 1): device state and partials, the stored
+    // force (two buffers of [3][n]), constants, host mirror
     NhDev* nh = nullptr;
+    double* nh_part = nullptr;
+    float* nh_F = nullptr;
+    int nh_f = 0;  // force buffer written last
     NhConsts nhc{};
-    int nh_blocks = 0;
     double* h_nh = nullptr;  // pinned [2]: xi, eta
 };
 
@@ -264,6 +268,7 @@ void derive_constants(hpf_ctx* c) {
     NhConsts& t = c->nhc;
     t.h = 0.5 * p.dt;
     t.dof_kT = (p.n_beads > 1 ? 3.0 * (p.n_beads - 1) : 3.0 * p.n_beads) * p.kT;
+    t.two_over_dof_kT = t.dof_kT > 0.0 ? 2.0 / t.dof_kT : 0.0;
     t.inv_tau2 = p.thermostat == 1 ? 1.0 / (p.nh_tau * p.nh_tau) : 0.0;
     t.mass = p.mass;
 }
@@ -526,29 +531,38 @@ hpf_status advance_nh(hpf_ctx* c, int chunk, bool fuse) {
     {
         StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? chunk + 1 : 0);
         if (c->n > 0) {
+            const size_t n = (size_t)c->n;
             NhParams p;
             memset(&p, 0, sizeof p);
-            p.st = c->st[c->cur];
             p.meta = c->meta;
-            p.seg_start = c->sb.seg_start;
-            p.seg_count = c->sb.seg_count;
-            p.n_seg = c->sb.n_seg;
+            p.n = c->n;
             p.g = c->geom;
             p.G = c->G;
             p.c = c->sc;
             p.t = c->nhc;
             p.nh = c->nh;
+            p.part = c->nh_part;
             p.flag = c->dflag;
+            // one launch; the state and (after a force evaluation) the force buffers swap
+            auto launch = [&](bool kick_drift, bool force_kick, unsigned long long* D_next) {
+                p.in = c->st[c->cur];
+                p.out = c->st[c->cur ^ 1];
+                for (int a = 0; a < 3; ++a) {
+                    p.Fin[a] = c->nh_F + ((size_t)c->nh_f * 3 + a) * n;
+                    p.Fout[a] = c->nh_F + ((size_t)(c->nh_f ^ 1) * 3 + a) * n;
+                }
+                p.kick_drift = kick_drift ? 1 : 0;
+                p.force_kick = force_kick ? 1 : 0;
+                p.D_next = D_next;
+                launch_nh_step(p, c->stream);
+                c->cur ^= 1;
+                if (force_kick) c->nh_f ^= 1;
+            };
             // F_n and the thermostat at the first step (after a refresh or a call boundary)
-            p.kick_drift = 0;
-            p.force_kick = 1;
-            launch_nh_step(p, c->nh_blocks, c->stream);
+            launch(false, true, nullptr);
             for (int j = 0; j < chunk; ++j) {
                 const bool last = j == chunk - 1;
-                p.kick_drift = 1;
-                p.force_kick = last ? 0 : 1;
-                p.D_next = (last && fuse) ? mesh_buf(c, c->dmesh ^ 1) : nullptr;
-                launch_nh_step(p, c->nh_blocks, c->stream);
+                launch(true, !last, (last && fuse) ? mesh_buf(c, c->dmesh ^ 1) : nullptr);
             }
         }
     }
@@ -648,6 +662,8 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
     if (params->thermostat == 1) {
         e = e ? e : cudaMalloc(&c->nh, sizeof(NhDev));
+        e = e ? e : cudaMalloc(&c->nh_part, sizeof(double) * (nh_blocks((int)n) + 1));
+        e = e ? e : cudaMalloc(&c->nh_F, sizeof(float) * 6 * n);
         e = e ? e : cudaMallocHost(&c->h_nh, sizeof(double) * 2);
         e = e ? e : cudaMemsetAsync(c->nh, 0, sizeof(NhDev), c->stream);
     }
@@ -718,6 +734,8 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->d_out6);
     cudaFreeHost(c->h_out6);
     cudaFree(c->nh);
+    cudaFree(c->nh_part);
+    cudaFree(c->nh_F);
     cudaFreeHost(c->h_nh);
     if (LearnedBufs* L = c->learned) {
         cudaFree(L->Dbase);
@@ -812,7 +830,6 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     if (c->nh) {
         // a loaded state starts with the thermostat at rest (hpf_set_thermostat restores one)
         CUDA_TRY(c, cudaMemsetAsync(c->nh, 0, sizeof(NhDev), c->stream));
-        c->nh_blocks = nh_grid(c->C);
     }
     c->has_state = true;
     return HPF_OK;
@@ -927,8 +944,6 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
     const long long fe = c->p.field_every;
     long long left = n_steps;
     if (c->nh) {
-        if (c->n > 0 && !c->warp_mode)
-            return fail(c, HPF_ERR_INVALID, "Nose-Hoover steps need chains of at most 64 beads");
         while (left > 0) {
             hpf_status s = ensure_field(c);
             if (s != HPF_OK) return s;

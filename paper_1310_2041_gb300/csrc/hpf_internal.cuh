@@ -469,38 +469,6 @@ __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0,
     w1z = (nz - az) + q1z;
 }
 
-// Nose-Hoover thermostat: device-resident state of one context.
-constexpr int kNhMaxBlocks = 2048;
-struct NhDev {
-    double xi, eta;       // at the middle of the last step
-    double ke;            // kinetic energy of the last reduction (v^E, before the half steps)
-    float s1, s2;         // velocity scales of the last two thermostat half steps
-    unsigned int ticket;  // blocks done with the current reduction
-    double part[kNhMaxBlocks];
-};
-struct NhConsts {
-    double h;         // dt / 2
-    double dof_kT;    // g kT, g = 3 (n - 1) kinetic degrees of freedom (3 for n = 1)
-    double inv_tau2;  // 1 / tau^2
-    double mass;
-};
-struct NhParams {
-    StateBuf st;  // advanced in place
-    const uint32_t* meta;
-    const int* seg_start;
-    const int* seg_count;
-    const int* n_seg;
-    MeshGeom g;
-    const float4* G;
-    StepConsts c;
-    NhConsts t;
-    NhDev* nh;
-    unsigned long long* D_next;  // deposit the final positions (kick_drift-only launches)
-    int* flag;
-    int kick_drift;  // v = s2 (s1 v) + dt/(2m) F; x += dt v
-    int force_kick;  // v += dt/(2m) F at the (new) positions; K; thermostat half steps
-};
-
 // ------------------------------------------------------------------ launchers
 
 void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
@@ -509,8 +477,6 @@ void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta
                        cudaStream_t s);
 void launch_scatter(StateBuf st, const uint32_t* meta, int n, MeshGeom g,
                     unsigned long long* D, cudaStream_t s);
-int nh_grid(int max_seg);
-void launch_nh_step(const NhParams& p, int blocks, cudaStream_t s);
 void launch_field(const long long* D, MeshGeom g, const FieldCoef& coef, float4* G,
                   unsigned long long* D_clear, cudaStream_t s);
 void launch_unpad_field(const float4* G, MeshGeom g, int S, float4* out, cudaStream_t s);

@@ -5,64 +5,123 @@
 // Every step couples all beads through the kinetic energy K, so a step
 // cannot run on chip for a whole field period like the Langevin kernel.  The
 // step is split where K is needed:
-//   force_kick : F_n at the current positions; v^E = v + dt/(2m) F_n; the
-//                kinetic energy of v^E is summed (FP64, per-block partials in a
-//                fixed order) and the last block to finish applies the two
-//                thermostat half steps T(dt/2) (the end of step n - 1, the
-//                start of step n), writing the velocity scales s1, s2 and xi, eta;
-//   kick_drift : v = s2 (s1 v^E) + dt/(2m) F_n (F_n recomputed from the same
-//                positions and field, so the bits agree); x += dt v.
+//   force_kick : F_n at the current positions (stored for the next launch);
+//                v^E = v + dt/(2m) F_n; the kinetic energy of v^E is summed
+//                (FP32 over each thread's few beads, FP64 from the warp sums
+//                on, block partials added in a fixed order) and the last
+//                block to finish applies the two thermostat half steps T(dt/2)
+//                (the end of step n - 1, the start of step n), writing the
+//                velocity scales s1, s2 and xi, eta;
+//   kick_drift : v = s2 (s1 v^E) + dt/(2m) F_n with the stored F_n; x += dt v.
 // One launch does kick_drift of step n and force_kick of step n + 1 when no
 // field refresh lies between them; a refresh splits them (kick_drift, which
 // also deposits the positions into the next density mesh, then the refresh,
-// then force_kick).  Beads are advanced in place, one warp per segment of
-// whole chains (two beads per lane, bonded neighbours by shuffles), so the
-// result does not depend on how the steps are split into calls.
-#include "hpf_internal.cuh"
+// then force_kick).
+//
+// A fixed grid (at most kNhGrid blocks, set by n alone, so the summation
+// order is the same on every GPU) whose threads loop over the beads; the
+// state and the stored force are read from one buffer and written to the
+// other.  A bead's bonded force after the drift
+// needs its chain neighbours' new positions (two beads each way with angles);
+// each thread recomputes those drifts from the neighbours' old state with the
+// same arithmetic as the neighbours' own threads, so no grid synchronisation
+// is needed and every bit agrees.  Any chain length works.
+#include "nh_internal.cuh"
 
 namespace hpf {
 
 namespace {
 
 constexpr int kNhBlock = 256;
+constexpr int kNhGrid = 1024;  // at most this many blocks, each thread loops over beads
 
-struct NhBead {
-    float x, y, z, vx, vy, vz;
-    uint32_t m;
+struct Drift {
+    float s1, s2, hdt_m, dt;
+    bool on;  // kick_drift launch
 };
 
-template <bool kExact>
-__device__ __forceinline__ void field_force_at(const NhBead& b, const MeshGeom& g,
-                                               const float4* __restrict__ G, float& fx, float& fy,
-                                               float& fz) {
-    const float4* Gt = G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes;
-    const AxisCoord ax = axis_gather(b.x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
-    const AxisCoord ay = axis_gather(b.y, g.inv_h[1], (float)g.my, g.inv_m[1]);
-    const AxisCoord az = axis_gather(b.z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
-    if (kExact) gather_field_exact(Gt, g, ax, ay, az, fx, fy, fz);
-    else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
+// Position (and velocity) of bead j after this launch's kick and drift (or
+// the stored one when the launch does not drift).
+__device__ __forceinline__ void moved(const NhParams& p, const Drift& d, int j, float& x, float& y,
+                                      float& z, float& vx, float& vy, float& vz) {
+    x = p.in.x[j];
+    y = p.in.y[j];
+    z = p.in.z[j];
+    vx = p.in.vx[j];
+    vy = p.in.vy[j];
+    vz = p.in.vz[j];
+    if (d.on) {
+        vx = fmaf(d.hdt_m, p.Fin[0][j], d.s2 * (d.s1 * vx));
+        vy = fmaf(d.hdt_m, p.Fin[1][j], d.s2 * (d.s1 * vy));
+        vz = fmaf(d.hdt_m, p.Fin[2][j], d.s2 * (d.s1 * vz));
+        x = fmaf(d.dt, vx, x);
+        y = fmaf(d.dt, vy, y);
+        z = fmaf(d.dt, vz, z);
+    }
 }
 
-// Conservative forces on the lane's two beads (bonded terms by shuffles: the
-// whole warp must call this).
-template <bool kExact, bool kAngles>
-__device__ __forceinline__ void pair_forces(const NhBead& b0, const NhBead& b1, bool p0, bool n0,
-                                            bool n1, const NhParams& p, int lane, float* F) {
-    warp_bonded_forces<kAngles>(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, p0, n0, n1, p.c, lane, F[0],
-                                F[1], F[2], F[3], F[4], F[5]);
-    field_force_at<kExact>(b0, p.g, p.G, F[0], F[1], F[2]);
-    field_force_at<kExact>(b1, p.g, p.G, F[3], F[4], F[5]);
+__device__ __forceinline__ void moved_pos(const NhParams& p, const Drift& d, int j, float& x,
+                                          float& y, float& z) {
+    float vx, vy, vz;
+    moved(p, d, j, x, y, z, vx, vy, vz);
+}
+
+// Bonded force on bead i at (x, y, z): its bonds, and with kAngles the three
+// angles it belongs to (centred at i - 1, i and i + 1).
+template <bool kAngles>
+__device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int i, uint32_t m,
+                                          float x, float y, float z, float& fx, float& fy,
+                                          float& fz) {
+    const bool hp = (m & kBondPrev) != 0, hn = (m & kBondNext) != 0;
+    float xp = 0.f, yp = 0.f, zp = 0.f, xn = 0.f, yn = 0.f, zn = 0.f;
+    if (hp) {
+        moved_pos(p, d, i - 1, xp, yp, zp);
+        bond_force(x - xp, y - yp, z - zp, p.c.two_k, p.c.r0, fx, fy, fz);
+    }
+    if (hn) {
+        moved_pos(p, d, i + 1, xn, yn, zn);
+        bond_force(x - xn, y - yn, z - zn, p.c.two_k, p.c.r0, fx, fy, fz);
+    }
+    if (!kAngles) return;
+    float ax, ay, az, bx, by, bz;
+    if (hp && hn) {
+        angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z, p.c.two_ka, p.c.cos0, ax, ay,
+                    az, bx, by, bz);
+        fx -= ax + bx;
+        fy -= ay + by;
+        fz -= az + bz;
+    }
+    if (hp && (p.meta[i - 1] & kBondPrev)) {
+        float xq, yq, zq;
+        moved_pos(p, d, i - 2, xq, yq, zq);
+        angle_force(xq - xp, yq - yp, zq - zp, x - xp, y - yp, z - zp, p.c.two_ka, p.c.cos0, ax,
+                    ay, az, bx, by, bz);
+        fx += bx;
+        fy += by;
+        fz += bz;
+    }
+    if (hn && (p.meta[i + 1] & kBondNext)) {
+        float xq, yq, zq;
+        moved_pos(p, d, i + 2, xq, yq, zq);
+        angle_force(x - xn, y - yn, z - zn, xq - xn, yq - yn, zq - zn, p.c.two_ka, p.c.cos0, ax,
+                    ay, az, bx, by, bz);
+        fx += ax;
+        fy += ay;
+        fz += az;
+    }
 }
 
 __device__ __forceinline__ double nh_rate(const NhConsts& t, double K) {
-    return t.dof_kT > 0.0 ? (2.0 * K / t.dof_kT - 1.0) * t.inv_tau2 : 0.0;
+    return t.dof_kT > 0.0 ? fma(K, t.two_over_dof_kT, -1.0) * t.inv_tau2 : 0.0;
 }
 
 // One thermostat half step T(h) (h = dt/2): xi += (h/2) G(K); s = exp(-xi h);
-// K *= s^2; eta += xi h; xi += (h/2) G(K).  Returns s.
+// K *= s^2; eta += xi h; xi += (h/2) G(K).  Returns s.  The scale is taken in
+// FP32 (it multiplies FP32 velocities); this GPU's FP64 rate is low and the
+// step waits for this one thread.
 __device__ __forceinline__ double nh_half(const NhConsts& t, double& xi, double& eta, double& K) {
     xi += 0.5 * t.h * nh_rate(t, K);
-    const double s = exp(-xi * t.h);
+    const double s = (double)expf((float)(-xi * t.h));
     K *= s * s;
     eta += xi * t.h;
     xi += 0.5 * t.h * nh_rate(t, K);
@@ -74,102 +133,82 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
     __shared__ double s_ke[kNhBlock / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31;
-    const float hdt_m = 0.5f * p.c.dt_m;
-    float s1 = 1.0f, s2 = 1.0f;
-    if (p.kick_drift) {
-        s1 = p.nh->s1;
-        s2 = p.nh->s2;
-    }
-    double ke = 0.0;  // sum of |v^E|^2 over this thread's beads
-    const int n_seg = *p.n_seg;
-    const int warps_total = gridDim.x * (kNhBlock / 32);
-    for (int w = blockIdx.x * (kNhBlock / 32) + (tid >> 5); w < n_seg; w += warps_total) {
-        const int base = p.seg_start[w], cnt = p.seg_count[w];
-        const int j0 = 2 * lane, j1 = j0 + 1;
-        const bool a0 = j0 < cnt, a1 = j1 < cnt;
-        NhBead b0{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u}, b1 = b0;
-        if (a0) {
-            const long long i = (long long)base + j0;
-            b0 = NhBead{p.st.x[i], p.st.y[i], p.st.z[i], p.st.vx[i], p.st.vy[i], p.st.vz[i],
-                        p.meta[i]};
-        }
-        if (a1) {
-            const long long i = (long long)base + j1;
-            b1 = NhBead{p.st.x[i], p.st.y[i], p.st.z[i], p.st.vx[i], p.st.vy[i], p.st.vz[i],
-                        p.meta[i]};
-        }
-        const bool p0 = (b0.m & kBondPrev) != 0, n0 = (b0.m & kBondNext) != 0;
-        const bool n1 = (b1.m & kBondNext) != 0;
-        float F[6];
-        if (p.kick_drift) {
-            pair_forces<kExact, kAngles>(b0, b1, p0, n0, n1, p, lane, F);
-            b0.vx = fmaf(hdt_m, F[0], s2 * (s1 * b0.vx));
-            b0.vy = fmaf(hdt_m, F[1], s2 * (s1 * b0.vy));
-            b0.vz = fmaf(hdt_m, F[2], s2 * (s1 * b0.vz));
-            b1.vx = fmaf(hdt_m, F[3], s2 * (s1 * b1.vx));
-            b1.vy = fmaf(hdt_m, F[4], s2 * (s1 * b1.vy));
-            b1.vz = fmaf(hdt_m, F[5], s2 * (s1 * b1.vz));
-            b0.x = fmaf(p.c.dt, b0.vx, b0.x);
-            b0.y = fmaf(p.c.dt, b0.vy, b0.y);
-            b0.z = fmaf(p.c.dt, b0.vz, b0.z);
-            b1.x = fmaf(p.c.dt, b1.vx, b1.x);
-            b1.y = fmaf(p.c.dt, b1.vy, b1.y);
-            b1.z = fmaf(p.c.dt, b1.vz, b1.z);
-        }
+    Drift d;
+    d.on = p.kick_drift != 0;
+    d.s1 = d.on ? p.nh->s1 : 1.0f;
+    d.s2 = d.on ? p.nh->s2 : 1.0f;
+    d.hdt_m = 0.5f * p.c.dt_m;
+    d.dt = p.c.dt;
+    float ke = 0.0f;  // this thread's beads, FP32 (a few beads); FP64 from the warp sum up
+#pragma unroll 2
+    for (int i = blockIdx.x * kNhBlock + tid; i < p.n; i += gridDim.x * kNhBlock) {
+        const uint32_t m = p.meta[i];
+        float x, y, z, vx, vy, vz;
+        moved(p, d, i, x, y, z, vx, vy, vz);
         if (p.force_kick) {
-            pair_forces<kExact, kAngles>(b0, b1, p0, n0, n1, p, lane, F);
-            b0.vx = fmaf(hdt_m, F[0], b0.vx);
-            b0.vy = fmaf(hdt_m, F[1], b0.vy);
-            b0.vz = fmaf(hdt_m, F[2], b0.vz);
-            b1.vx = fmaf(hdt_m, F[3], b1.vx);
-            b1.vy = fmaf(hdt_m, F[4], b1.vy);
-            b1.vz = fmaf(hdt_m, F[5], b1.vz);
-            if (a0) ke += (double)fmaf(b0.vx, b0.vx, fmaf(b0.vy, b0.vy, b0.vz * b0.vz));
-            if (a1) ke += (double)fmaf(b1.vx, b1.vx, fmaf(b1.vy, b1.vy, b1.vz * b1.vz));
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            bonded_of<kAngles>(p, d, i, m, x, y, z, fx, fy, fz);
+            const float4* Gt = p.G + (size_t)((m >> kTypeShift) & kTypeMask) * p.g.gnodes;
+            const AxisCoord ax = axis_gather(x, p.g.inv_h[0], (float)p.g.mx, p.g.inv_m[0]);
+            const AxisCoord ay = axis_gather(y, p.g.inv_h[1], (float)p.g.my, p.g.inv_m[1]);
+            const AxisCoord az = axis_gather(z, p.g.inv_h[2], (float)p.g.mz, p.g.inv_m[2]);
+            if (kExact) gather_field_exact(Gt, p.g, ax, ay, az, fx, fy, fz);
+            else gather_field(Gt, p.g, ax, ay, az, fx, fy, fz);
+            p.Fout[0][i] = fx;
+            p.Fout[1][i] = fy;
+            p.Fout[2][i] = fz;
+            vx = fmaf(d.hdt_m, fx, vx);
+            vy = fmaf(d.hdt_m, fy, vy);
+            vz = fmaf(d.hdt_m, fz, vz);
+            ke += fmaf(vx, vx, fmaf(vy, vy, vz * vz));
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (!(k ? a1 : a0)) continue;
-            const NhBead& b = k ? b1 : b0;
-            const long long i = (long long)base + (k ? j1 : j0);
-            p.st.x[i] = b.x;
-            p.st.y[i] = b.y;
-            p.st.z[i] = b.z;
-            p.st.vx[i] = b.vx;
-            p.st.vy[i] = b.vy;
-            p.st.vz[i] = b.vz;
-            const bool finite = isfinite(b.x) && isfinite(b.y) && isfinite(b.z) &&
-                                isfinite(b.vx) && isfinite(b.vy) && isfinite(b.vz);
-            if (!finite) atomicOr(p.flag, kFlagNonFinite);
-            else if (!(coord_in_range(b.x, p.g.inv_h[0]) && coord_in_range(b.y, p.g.inv_h[1]) &&
-                       coord_in_range(b.z, p.g.inv_h[2])))
-                atomicOr(p.flag, kFlagRange);
-            else if (p.D_next) {
-                const AxisCoord ax = axis_coord(b.x, p.g.inv_h[0], p.g.mx, p.g.inv_m[0]);
-                const AxisCoord ay = axis_coord(b.y, p.g.inv_h[1], p.g.my, p.g.inv_m[1]);
-                const AxisCoord az = axis_coord(b.z, p.g.inv_h[2], p.g.mz, p.g.inv_m[2]);
-                scatter_bead(p.D_next + (size_t)((b.m >> kTypeShift) & kTypeMask) * p.g.nodes,
-                             p.g, ax, ay, az);
-            }
+        p.out.x[i] = x;
+        p.out.y[i] = y;
+        p.out.z[i] = z;
+        p.out.vx[i] = vx;
+        p.out.vy[i] = vy;
+        p.out.vz[i] = vz;
+        const bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) &&
+                            isfinite(vy) && isfinite(vz);
+        if (!finite) atomicOr(p.flag, kFlagNonFinite);
+        else if (!(coord_in_range(x, p.g.inv_h[0]) && coord_in_range(y, p.g.inv_h[1]) &&
+                   coord_in_range(z, p.g.inv_h[2])))
+            atomicOr(p.flag, kFlagRange);
+        else if (p.D_next) {
+            const AxisCoord ax = axis_coord(x, p.g.inv_h[0], p.g.mx, p.g.inv_m[0]);
+            const AxisCoord ay = axis_coord(y, p.g.inv_h[1], p.g.my, p.g.inv_m[1]);
+            const AxisCoord az = axis_coord(z, p.g.inv_h[2], p.g.mz, p.g.inv_m[2]);
+            scatter_bead(p.D_next + (size_t)((m >> kTypeShift) & kTypeMask) * p.g.nodes, p.g,
+                         ax, ay, az);
         }
     }
     if (!p.force_kick) return;
     // the kinetic-energy sum: warp, block, then the blocks' partials in order
-    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
-    if (lane == 0) s_ke[tid >> 5] = ke;
+    double kd = (double)ke;
+    for (int o = 16; o > 0; o >>= 1) kd += __shfl_down_sync(0xffffffffu, kd, o);
+    if (lane == 0) s_ke[tid >> 5] = kd;
     __syncthreads();
     if (tid == 0) {
         double b = 0.0;
         for (int k = 0; k < kNhBlock / 32; ++k) b += s_ke[k];
-        p.nh->part[blockIdx.x] = b;
+        p.part[blockIdx.x] = b;
         __threadfence();
         s_last = atomicAdd(&p.nh->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last) return;
+    // the last block sums the partials in a fixed order (strided per thread,
+    // then the same shuffle tree and warp order as above)
     __threadfence();
+    double v = 0.0;
+    for (int k = tid; k < (int)gridDim.x; k += kNhBlock) v += __ldcg(&p.part[k]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) s_ke[tid >> 5] = v;
+    __syncthreads();
+    if (tid != 0) return;
     double sum = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) sum += __ldcg(&p.nh->part[k]);
+    for (int k = 0; k < kNhBlock / 32; ++k) sum += s_ke[k];
     double K = 0.5 * p.t.mass * sum;
     double xi = p.nh->xi, eta = p.nh->eta;
     p.nh->ke = K;
@@ -183,30 +222,26 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
 }
 
 template <bool kExact>
-void launch_nh_e(const NhParams& p, int blocks, bool angles, cudaStream_t s) {
+void launch_nh_e(const NhParams& p, bool angles, cudaStream_t s) {
+    const int blocks = nh_blocks(p.n);
     if (angles) k_nh_step<kExact, true><<<blocks, kNhBlock, 0, s>>>(p);
     else k_nh_step<kExact, false><<<blocks, kNhBlock, 0, s>>>(p);
 }
 
 }  // namespace
 
-int nh_grid(int max_seg) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nh_step<false, false>, kNhBlock, 0);
-    cudaGetLastError();
-    int cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    if (cap > kNhMaxBlocks) cap = kNhMaxBlocks;
-    const int need = (max_seg + kNhBlock / 32 - 1) / (kNhBlock / 32);
-    const int blocks = need < cap ? need : cap;
-    return blocks > 0 ? blocks : 1;
+int nh_blocks(int n) {
+    // a fixed grid (it depends only on n): the summation order of the kinetic
+    // energy is the same on every GPU
+    const int b = (n + kNhBlock - 1) / kNhBlock;
+    return b < kNhGrid ? b : kNhGrid;
 }
 
-void launch_nh_step(const NhParams& p, int blocks, cudaStream_t s) {
+void launch_nh_step(const NhParams& p, cudaStream_t s) {
+    if (p.n <= 0) return;
     const bool angles = p.c.two_ka != 0.f;
-    if (p.c.exact) launch_nh_e<true>(p, blocks, angles, s);
-    else launch_nh_e<false>(p, blocks, angles, s);
+    if (p.c.exact) launch_nh_e<true>(p, angles, s);
+    else launch_nh_e<false>(p, angles, s);
 }
 
 }  // namespace hpf

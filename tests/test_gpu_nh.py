@@ -7,6 +7,7 @@ observables within 2e-6 relative (1e-5 for the potential energies, whose
 positions have drifted by FP32 rounding); the extended energy conserved to FP32
 rounding on the GPU.  How the steps are split into calls does not change a
 bit, and a checkpoint (state + xi, eta) resumes the run bit for bit.
+Chains of any length (one thread per bead; neighbours' drifts recomputed).
 """
 import numpy as np
 import pytest
@@ -166,12 +167,20 @@ def test_set_state_resets_and_invalid_uses_fail(hpf_gpu):
             hpf_gpu.System(hpf_gpu.make_params(**dict(pp, nh_tau=bad)))
     with pytest.raises(hpf_gpu.HPFError):
         hpf_gpu.Batch([hpf_gpu.make_params(**pp)] * 2)
-    # chains longer than 64 beads: the warp form is required
-    wl = W.diblock(4, 40, 40, 6.0, 6, 1.0)
-    dl = W.generate(wl)
-    sl, _ = make(hpf_gpu, wl, dl)
-    with pytest.raises(hpf_gpu.HPFError):
-        sl.step(1)
+
+
+def test_long_chains_with_angles_match_oracle(hpf_gpu, orc):
+    """Chains of 80 beads (longer than a warp segment) with angles."""
+    w = W.diblock(8, 40, 40, 6.0, 6, 1.0, name="long_640")
+    d = hot(W.generate(w))
+    s, pp = make(hpf_gpu, w, d, angle_k=1.5, angle_cos0=-0.8, field_every=3)
+    s.step(10)
+    pos, vel, _ = s.get_state()
+    xi, eta = s.get_thermostat()
+    po, vo, (xo, eo), _ = orc.run_nh(orc.make_params(**pp), d["pos"], d["vel"], d["type"],
+                                     d["bonds"], 0, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4 and np.max(np.abs(vel - vo)) <= 1e-4
+    assert abs(xi - xo) <= 1e-5 and abs(eta - eo) <= 1e-5
 
 
 def test_empty_system_steps(hpf_gpu):
