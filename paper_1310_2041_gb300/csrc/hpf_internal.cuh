@@ -410,6 +410,39 @@ __device__ __forceinline__ void angle_force(float ux, float uy, float uz, float 
     fbz = g * (uz * inv - cb * wz);
 }
 
+// The three angles bead i belongs to (centred at i - 1, i and i + 1), read
+// from global memory in storage order (chains are contiguous there).
+__device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32_t* __restrict__ meta,
+                                                int i, uint32_t m, const StepConsts& c, float& fx,
+                                                float& fy, float& fz) {
+    const bool hp = (m & kBondPrev) != 0, hn = (m & kBondNext) != 0;
+    const float x = st.x[i], y = st.y[i], z = st.z[i];
+    float ax, ay, az, bx, by, bz;
+    if (hp && hn) {
+        angle_force(st.x[i - 1] - x, st.y[i - 1] - y, st.z[i - 1] - z, st.x[i + 1] - x,
+                    st.y[i + 1] - y, st.z[i + 1] - z, c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx -= ax + bx;
+        fy -= ay + by;
+        fz -= az + bz;
+    }
+    if (hp && (meta[i - 1] & kBondPrev)) {
+        const float xp = st.x[i - 1], yp = st.y[i - 1], zp = st.z[i - 1];
+        angle_force(st.x[i - 2] - xp, st.y[i - 2] - yp, st.z[i - 2] - zp, x - xp, y - yp, z - zp,
+                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx += bx;
+        fy += by;
+        fz += bz;
+    }
+    if (hn && (meta[i + 1] & kBondNext)) {
+        const float xn = st.x[i + 1], yn = st.y[i + 1], zn = st.z[i + 1];
+        angle_force(x - xn, y - yn, z - zn, st.x[i + 2] - xn, st.y[i + 2] - yn, st.z[i + 2] - zn,
+                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+        fx += ax;
+        fy += ay;
+        fz += az;
+    }
+}
+
 // Bonded forces of one warp segment of whole chains: lane l holds beads 2l
 // and 2l + 1 at (x0, y0, z0) and (x1, y1, z1); p0, n0: bead 2l is bonded to
 // its previous / next bead, n1: bead 2l + 1 to its next.  Returns the summed

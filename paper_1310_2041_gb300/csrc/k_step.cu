@@ -1,4 +1,4 @@
-// k_step.cu -- field gather, bonds, Langevin velocity-Verlet, FP64 observables.
+// k_step.cu -- field gather, bonds, Langevin velocity-Verlet (the fused field-period kernels).
 #include "hpf_internal.cuh"
 
 namespace hpf {
@@ -11,39 +11,6 @@ int step_halo_max() { return kHaloMax; }
 // ------------------------------------------------------------------ A4 + A5 forces
 //
 // Conservative force at the current positions, written in tag order.
-// The three angles bead i belongs to (centred at i - 1, i and i + 1), read
-// from global memory in storage order (chains are contiguous there).
-__device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32_t* __restrict__ meta,
-                                                int i, uint32_t m, const StepConsts& c, float& fx,
-                                                float& fy, float& fz) {
-    const bool hp = (m & kBondPrev) != 0, hn = (m & kBondNext) != 0;
-    const float x = st.x[i], y = st.y[i], z = st.z[i];
-    float ax, ay, az, bx, by, bz;
-    if (hp && hn) {
-        angle_force(st.x[i - 1] - x, st.y[i - 1] - y, st.z[i - 1] - z, st.x[i + 1] - x,
-                    st.y[i + 1] - y, st.z[i + 1] - z, c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
-        fx -= ax + bx;
-        fy -= ay + by;
-        fz -= az + bz;
-    }
-    if (hp && (meta[i - 1] & kBondPrev)) {
-        const float xp = st.x[i - 1], yp = st.y[i - 1], zp = st.z[i - 1];
-        angle_force(st.x[i - 2] - xp, st.y[i - 2] - yp, st.z[i - 2] - zp, x - xp, y - yp, z - zp,
-                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
-        fx += bx;
-        fy += by;
-        fz += bz;
-    }
-    if (hn && (meta[i + 1] & kBondNext)) {
-        const float xn = st.x[i + 1], yn = st.y[i + 1], zn = st.z[i + 1];
-        angle_force(x - xn, y - yn, z - zn, st.x[i + 2] - xn, st.y[i + 2] - yn, st.z[i + 2] - zn,
-                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
-        fx += ax;
-        fy += ay;
-        fz += az;
-    }
-}
-
 __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __restrict__ meta,
                                                 int n, MeshGeom g, const float4* __restrict__ G,
                                                 StepConsts c, int which,
@@ -639,189 +606,5 @@ void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise,
     launch_warp(p, blocks, noise, p.rep[0].c.exact != 0, s);
 }
 
-
-// ------------------------------------------------------------------ A7 FP64 observables
-
-constexpr int kRedBlock = 256;
-constexpr int kBeadVals = 5;  // kinetic, bond, px, py, pz
-
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-    return r;  // valid in thread 0
-}
-
-// |d| in FP64 from an FP32 reciprocal-square-root seed and one Newton step
-// y <- y (3 - r2 y^2) / 2 (relative error ~1.5 e0^2 ~ 3e-14 for the FP32
-// seed's e0 ~ 1.4e-7); r2 = 0 gives 0.
-__device__ __forceinline__ double norm_fp64(double r2) {
-    if (!(r2 > 0.0)) return 0.0;
-    double y = (double)rsqrtf((float)r2);
-    y = y * fma(-0.5 * r2, y * y, 1.5);
-    return r2 * y;
-}
-
-// Per bead: F_n exactly as the step kernel forms it, v_n = v + dt/(2m) F_n in
-// FP64, then kinetic energy, momentum and the bond energy of the bond to the
-// next bead (each bond once).  Each thread accumulates a grid-stride share of
-// the beads in FP64 before the block sums (the FP64 rate of this GPU is low,
-// so the reductions are amortised over many beads).
-__global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
-                                                            const uint32_t* __restrict__ meta,
-                                                            int n, MeshGeom g,
-                                                            const float4* __restrict__ G,
-                                                            StepConsts c, long long step,
-                                                            EnergyConsts e,
-                                                            double* __restrict__ partials) {
-    __shared__ double sh[kRedBlock / 32];
-    double ke = 0.0, ub = 0.0, px = 0.0, py = 0.0, pz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float x = st.x[i], y = st.y[i], z = st.z[i];
-        const float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
-        const uint32_t m = meta[i];
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        if (m & kBondPrev)
-            bond_force(x - st.x[i - 1], y - st.y[i - 1], z - st.z[i - 1], c.two_k, c.r0, fx, fy, fz);
-        if (m & kBondNext) {
-            const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
-            bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
-            const double dx = (double)x - xj, dy = (double)y - yj, dz = (double)z - zj;
-            const double dr = norm_fp64(dx * dx + dy * dy + dz * dz) - e.r0;
-            ub += e.bond_k * dr * dr;
-        }
-        if (c.two_ka != 0.f) {
-            angle_forces_of(st, meta, i, m, c, fx, fy, fz);
-            if ((m & kBondPrev) && (m & kBondNext)) {
-                // the angle centred here, once, in FP64 from the FP32 positions
-                const double ux = (double)st.x[i - 1] - x, uy = (double)st.y[i - 1] - y,
-                             uz = (double)st.z[i - 1] - z;
-                const double wx = (double)st.x[i + 1] - x, wy = (double)st.y[i + 1] - y,
-                             wz = (double)st.z[i + 1] - z;
-                const double uu = ux * ux + uy * uy + uz * uz, ww = wx * wx + wy * wy + wz * wz;
-                const double cth = (ux * wx + uy * wy + uz * wz) / norm_fp64(uu * ww);
-                ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
-            }
-        }
-        const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
-        const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
-        const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
-        const float4* Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
-        if (c.exact) gather_field_exact(Gt, g, ax, ay, az, fx, fy, fz);
-        else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
-        if (c.sigma > 0.f) {
-            float nx, ny, nz;
-            gauss3(c, m & kTagMask, step, nx, ny, nz);
-            fx += c.sigma * nx;
-            fy += c.sigma * ny;
-            fz += c.sigma * nz;
-        }
-        fx -= c.fric * vx;
-        fy -= c.fric * vy;
-        fz -= c.fric * vz;
-        const double ux = (double)vx + e.half_dt_m * (double)fx;
-        const double uy = (double)vy + e.half_dt_m * (double)fy;
-        const double uz = (double)vz + e.half_dt_m * (double)fz;
-        ke += 0.5 * e.mass * (ux * ux + uy * uy + uz * uz);
-        px += e.mass * ux;
-        py += e.mass * uy;
-        pz += e.mass * uz;
-    }
-    const double vals[kBeadVals] = {ke, ub, px, py, pz};
-#pragma unroll
-    for (int k = 0; k < kBeadVals; ++k) {
-        const double s = block_sum(vals[k], sh);
-        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kBeadVals + k] = s;
-    }
-}
-
-// Per node: the field-energy density of the mesh D (FP64 from exact integers).
-__global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __restrict__ D,
-                                                            int nodes, EnergyConsts e,
-                                                            double* __restrict__ partials) {
-    __shared__ double sh[kRedBlock / 32];
-    double w = 0.0;
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
-         node += gridDim.x * blockDim.x) {
-        // unrolled over the species bound so phi stays in registers
-        double phi[HPF_MAX_SPECIES];
-        double tot = 0.0;
-#pragma unroll
-        for (int k = 0; k < HPF_MAX_SPECIES; ++k) {
-            phi[k] = k < e.S ? e.phi_c * (double)D[(size_t)k * nodes + node] : 0.0;
-            tot += phi[k];
-        }
-        double q = 0.0;
-#pragma unroll
-        for (int k = 0; k < HPF_MAX_SPECIES; ++k) {
-            if (k >= e.S) break;
-            double row = 0.0;
-#pragma unroll
-            for (int kp = 0; kp < HPF_MAX_SPECIES; ++kp)
-                if (kp < e.S) row += e.chi[k][kp] * phi[kp];
-            q += phi[k] * row;
-        }
-        w += 0.5 * e.kT * q + 0.5 * e.inv_kappa * (tot - 1.0) * (tot - 1.0);
-    }
-    const double s = block_sum(w, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-// Fixed-order final sums -> out6 = {KE, U_bond, W, total, |P|, T}.
-__global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __restrict__ bead_part,
-                                                            int nb, const double* __restrict__ node_part,
-                                                            int nn, EnergyConsts e,
-                                                            double* __restrict__ out6) {
-    __shared__ double sh[kRedBlock / 32];
-    double acc[kBeadVals + 1];
-    for (int k = 0; k < kBeadVals; ++k) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) v += bead_part[(size_t)b * kBeadVals + k];
-        acc[k] = block_sum(v, sh);
-    }
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nn; b += blockDim.x) v += node_part[b];
-    acc[kBeadVals] = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        const double ke = acc[0], ub = acc[1], w = acc[5] * e.w_scale;
-        out6[0] = ke;
-        out6[1] = ub;
-        out6[2] = w;
-        out6[3] = ke + ub + w;
-        out6[4] = sqrt(acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4]);
-        out6[5] = e.n > 0 ? 2.0 * ke / (3.0 * (double)e.n) : 0.0;
-    }
-}
-
-static int energy_blocks(int count);
-
-int energy_partials_needed(int n, int nodes) {
-    return energy_blocks(n) * kBeadVals + energy_blocks(nodes) + 1;
-}
-
-// Blocks of the energy reductions: each thread takes a grid-stride share (at
-// most 8 beads or nodes per thread on average), independent of the device so
-// the summation order, and with it every FP64 bit, is the same on any GPU.
-static int energy_blocks(int count) {
-    const int per_block = kRedBlock * 8;
-    return (count + per_block - 1) / per_block;
-}
-
-void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
-                   StepConsts c, long long step, const long long* D, const EnergyConsts& e,
-                   double* partials, double* out6, cudaStream_t s) {
-    const int nb = energy_blocks(n);
-    const int nn = energy_blocks(g.nodes);
-    double* bead_part = partials;
-    double* node_part = partials + (size_t)nb * kBeadVals;
-    if (nb > 0) k_energy_beads<<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part);
-    k_energy_nodes<<<nn, kRedBlock, 0, s>>>(D, g.nodes, e, node_part);
-    k_energy_final<<<1, kRedBlock, 0, s>>>(bead_part, nb, node_part, nn, e, out6);
-}
 
 }  // namespace hpf
