@@ -305,6 +305,12 @@ hpf_ctx* hpf_batch_replica(hpf_batch* batch, int32_t r);
  * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_batch_step(hpf_batch* batch, int32_t n_steps);
 
+/* Observables of every replica at its current step (hpf_energy's six values
+ * each, out[n_replicas][6], replica order): all replicas' kernels are queued
+ * on the batch's stream and the call synchronises once.  Errors: as
+ * hpf_energy (the first failing replica's). */
+hpf_status hpf_batch_energy(hpf_batch* batch, double* out);
+
 /* Use CUDA graphs for steady-state periods (1, default) or plain launches (0). */
 hpf_status hpf_batch_use_graphs(hpf_batch* batch, int32_t enable);
 

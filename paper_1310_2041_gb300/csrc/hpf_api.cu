@@ -602,6 +602,44 @@ hpf_status check_flags(hpf_ctx* c) {
     return HPF_OK;
 }
 
+// The observables of the current step: kernels and the copies of the six
+// sums (and the Nose-Hoover state) to the context's pinned mirrors, all
+// asynchronous on the context's stream.
+hpf_status energy_launch(hpf_ctx* c) {
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s = ensure_field(c);
+    if (s != HPF_OK) return s;
+    // the mesh of the current positions for the field energy
+    if ((s = scatter_current(c)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_ENERGY, c->n > 0 ? 3 : 2);
+        launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
+                      reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->ec,
+                      c->partials, c->d_out6, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (c->nh)
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                                    c->stream));
+    return HPF_OK;
+}
+
+// After the stream has reached energy_launch's copies: the six values.
+void energy_finish(const hpf_ctx* c, double out[6]) {
+    memcpy(out, c->h_out6, sizeof(double) * 6);
+    if (c->nh) {
+        // the kernels give the on-step velocity before the pending thermostat half step
+        double xi = c->h_nh[0], eta = c->h_nh[1], K = out[0];
+        const double sc = nh_pending_half(c, xi, eta, K);
+        out[0] = K;
+        out[3] = K + out[1] + out[2];
+        out[4] *= sc;
+        out[5] *= sc * sc;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -979,34 +1017,10 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
 
 hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
-    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
-    hpf_status s = ensure_field(c);
+    hpf_status s = energy_launch(c);
     if (s != HPF_OK) return s;
-    // the mesh of the current positions for the field energy
-    if ((s = scatter_current(c)) != HPF_OK) return s;
-    {
-        StageScope sc(c, HPF_STAGE_ENERGY, c->n > 0 ? 3 : 2);
-        launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
-                      reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->ec,
-                      c->partials, c->d_out6, c->stream);
-    }
-    LAUNCH_CHECK(c);
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,
-                                c->stream));
-    if (c->nh)
-        CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
-                                    c->stream));
     if ((s = check_flags(c)) != HPF_OK) return s;
-    memcpy(out, c->h_out6, sizeof(double) * 6);
-    if (c->nh) {
-        // the kernels give the on-step velocity before the pending thermostat half step
-        double xi = c->h_nh[0], eta = c->h_nh[1], K = out[0];
-        const double sc = nh_pending_half(c, xi, eta, K);
-        out[0] = K;
-        out[3] = K + out[1] + out[2];
-        out[4] *= sc;
-        out[5] *= sc * sc;
-    }
+    energy_finish(c, out);
     return HPF_OK;
 }
 
@@ -1323,6 +1337,21 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
 hpf_ctx* hpf_batch_replica(hpf_batch* b, int32_t r) {
     if (!b || r < 0 || r >= b->R) return nullptr;
     return b->rep[r];
+}
+
+hpf_status hpf_batch_energy(hpf_batch* b, double* out) {
+    if (!b || !out) return HPF_ERR_INVALID;
+    // every replica's kernels and copies first, one synchronisation after
+    for (hpf_ctx* c : b->rep) {
+        hpf_status s = energy_launch(c);
+        if (s != HPF_OK) return s;
+    }
+    for (hpf_ctx* c : b->rep) {
+        hpf_status s = check_flags(c);
+        if (s != HPF_OK) return s;
+    }
+    for (size_t r = 0; r < b->rep.size(); ++r) energy_finish(b->rep[r], out + 6 * r);
+    return HPF_OK;
 }
 
 hpf_status hpf_batch_use_graphs(hpf_batch* b, int32_t enable) {

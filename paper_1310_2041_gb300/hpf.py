@@ -116,9 +116,10 @@ def load():
         L.hpf_batch_replica.restype = vp
         L.hpf_batch_step.argtypes = [vp, i32]
         L.hpf_batch_use_graphs.argtypes = [vp, i32]
+        L.hpf_batch_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_batch_destroy.argtypes = [vp]
         for name in ("hpf_batch_init", "hpf_batch_step", "hpf_batch_use_graphs",
-                     "hpf_batch_destroy"):
+                     "hpf_batch_destroy", "hpf_batch_energy"):
             getattr(L, name).restype = ctypes.c_int
         L.hpf_profile.argtypes = [vp, i32]
         L.hpf_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -428,6 +429,14 @@ class Batch:
         if st != 0:
             msg = self.lib.hpf_last_error(self.replicas[0].h).decode()
             raise HPFError(st, msg or self.lib.hpf_status_string(st).decode())
+
+    def energy(self):
+        """hpf_energy's six observables of every replica, [R][6]."""
+        out = (ctypes.c_double * (6 * len(self.params)))()
+        st = self.lib.hpf_batch_energy(self.h, out)
+        if st != 0:
+            raise HPFError(st, self.lib.hpf_status_string(st).decode())
+        return np.array(list(out)).reshape(len(self.params), 6)
 
     def use_graphs(self, enable=True):
         self.lib.hpf_batch_use_graphs(self.h, 1 if enable else 0)

@@ -104,3 +104,25 @@ def test_batch_with_long_chains_falls_back(hpf_gpu):
         np.testing.assert_array_equal(pos, pi)
         np.testing.assert_array_equal(vel, vi)
     b.close()
+
+
+def test_batch_energy_is_every_replicas_energy(hpf_gpu, orc):
+    """hpf_batch_energy gives each replica's hpf_energy bit for bit (one
+    synchronisation for all), and each agrees with the oracle's observables."""
+    ws = replica_workloads()
+    b, data, params, stream = make_batch(hpf_gpu, ws)
+    b.step(7)
+    E = b.energy()
+    assert E.shape == (len(ws), 6)
+    for r, (w, d) in enumerate(zip(ws, data)):
+        assert np.array_equal(E[r], b.replica(r).energy())
+        pos, vel, _ = b.replica(r).get_state()
+        op = orc.make_params(**w.params())
+        # the field in force at step 7 is the one refreshed at step 5
+        pos5, vel5, _ = independent(hpf_gpu, w, d, 5)
+        V5, G5 = orc.field(op, orc.scatter(op, pos5, d["type"]))
+        eo = orc.energy(op, pos, vel, d["type"], d["bonds"], V5, G5, 7)
+        assert E[r][1] == pytest.approx(eo[1], rel=1e-12)
+        assert E[r][2] == pytest.approx(eo[2], rel=1e-12)
+        assert E[r][0] == pytest.approx(eo[0], rel=1e-6)
+    b.close()
