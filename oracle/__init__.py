@@ -16,6 +16,8 @@ with the CUDA library.  Parity status per function:
                  by moments of the normals
   energy         pinned (kinetic energy of known velocities, bond closed form,
                  field energy derivative equals the potential)
+  run (Andersen) pinned (nu = 0 is NVE, force-free velocity autocorrelation
+                 (1 - nu dt)^n, collision rate, mean temperature)
   run_nh         pinned (NVE limit, free-particle thermostat ODE, extended-energy
                  conservation, mean temperature)
 """
@@ -71,6 +73,7 @@ class Params(ctypes.Structure):
         ("angle_cos0", ctypes.c_double),
         ("thermostat", ctypes.c_int32),
         ("nh_tau", ctypes.c_double),
+        ("andersen_nu", ctypes.c_double),
     ]
 
 
@@ -113,6 +116,8 @@ def lib():
             L.orc_run_nh.argtypes = [pp, i64, P(f64), P(f64), P(i32), i64, P(i32), i64, i32,
                                      P(f64), P(f64)]
             L.orc_run_nh.restype = ctypes.c_int
+            L.orc_andersen_collides.argtypes = [pp, u32, i64]
+            L.orc_andersen_collides.restype = ctypes.c_int
             L.orc_cell_key.argtypes = [pp, P(f64), i32]
             L.orc_cell_key.restype = i64
             _lib = L
@@ -121,7 +126,8 @@ def lib():
 
 def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None, bond_k=4.0,
                 bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1, force_mode=0,
-                angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0, **_ignored):
+                angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0, andersen_nu=0.0,
+                **_ignored):
     p = Params()
     p.n_species = int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -143,6 +149,7 @@ def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
     p.force_mode = int(force_mode)
     p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
     p.thermostat, p.nh_tau = int(thermostat), float(nh_tau)
+    p.andersen_nu = float(andersen_nu)
     return p
 
 
@@ -323,6 +330,10 @@ def run_nh(p: Params, pos, vel, types, bonds, step0, n_steps, xe=(0.0, 0.0), ene
     if rc != 0:
         raise ValueError("oracle rejected the input")
     return pos, vel, (float(x[0]), float(x[1])), E
+
+
+def andersen_collides(p: Params, tag: int, step: int) -> bool:
+    return bool(lib().orc_andersen_collides(ctypes.byref(p), int(tag), int(step)))
 
 
 def cell_key(p: Params, x, brick: int) -> int:

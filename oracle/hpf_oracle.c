@@ -107,6 +107,17 @@ void orc_gauss3(uint64_t seed, uint32_t tag, int64_t step, double xi[3])
     xi[2] = b * cos(two_pi * u3);
 }
 
+int orc_andersen_collides(const orc_params* p, uint32_t tag, int64_t step)
+{
+    uint64_t us = (uint64_t)step;
+    uint32_t ctr[4] = {tag, (uint32_t)us, (uint32_t)(us >> 32), 1u};
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    const float u = (float)uniform_open(r[0]);
+    return u < (float)(p->andersen_nu * p->dt);
+}
+
 /* ------------------------------------------------------------ mesh helpers */
 
 float orc_inv_h(const orc_params* p, int axis)
@@ -457,9 +468,29 @@ double orc_field_energy(const orc_params* p, const int64_t* D)
     return (double)(w * (long double)(p->rho0 * vol));
 }
 
+/* Langevin friction coefficient gamma m and noise amplitude; both zero for
+ * the other thermostats (Andersen acts on the velocity instead). */
+static double friction(const orc_params* p)
+{
+    return p->thermostat == 0 ? p->gamma * p->mass : 0.0;
+}
+
 static double noise_sigma(const orc_params* p)
 {
-    return sqrt(2.0 * p->gamma * p->mass * p->kT / p->dt);
+    return p->thermostat == 0 ? sqrt(2.0 * p->gamma * p->mass * p->kT / p->dt) : 0.0;
+}
+
+/* Andersen (thermostat 2): the on-step velocity v_n = v + dt/(2m) F_n of a
+ * bead that collides at step n is replaced by sqrt(kT/m) xi, xi the three
+ * normals of orc_gauss3 at (tag, n).  Returns 1 and writes u[3] if it does. */
+static int andersen_velocity(const orc_params* p, int64_t i, int64_t step, double u[3])
+{
+    if (p->thermostat != 2 || !orc_andersen_collides(p, (uint32_t)i, step)) return 0;
+    double xi[3];
+    orc_gauss3(p->seed, (uint32_t)i, step, xi);
+    const double sv = sqrt(p->kT / p->mass);
+    for (int a = 0; a < 3; ++a) u[a] = sv * xi[a];
+    return 1;
 }
 
 /* Total force at step n on the state (x_n, v_{n-1/2}): conservative part plus
@@ -473,7 +504,7 @@ static void total_force(const orc_params* p, int64_t n, const double* vel, const
         double xi[3] = {0.0, 0.0, 0.0};
         if (sigma > 0.0) orc_gauss3(p->seed, (uint32_t)i, step, xi);
         for (int a = 0; a < 3; ++a)
-            F[3 * i + a] = Fc[3 * i + a] - p->gamma * p->mass * vel[3 * i + a] + sigma * xi[a];
+            F[3 * i + a] = Fc[3 * i + a] - friction(p) * vel[3 * i + a] + sigma * xi[a];
     }
 }
 
@@ -509,12 +540,15 @@ void orc_energy(const orc_params* p, int64_t n, const double* pos, const double*
     total_force(p, n, vel, Fc, step, F);
     /* On-step velocity v_n = v_{n-1/2} + dt/(2m) F_n (mean of the two half steps). */
     long double ke = 0.0L, mom[3] = {0.0L, 0.0L, 0.0L};
-    for (int64_t i = 0; i < n; ++i)
+    for (int64_t i = 0; i < n; ++i) {
+        double u[3];
+        const int coll = andersen_velocity(p, i, step, u);
         for (int a = 0; a < 3; ++a) {
-            double v = vel[3 * i + a] + 0.5 * p->dt / p->mass * F[3 * i + a];
+            double v = coll ? u[a] : vel[3 * i + a] + 0.5 * p->dt / p->mass * F[3 * i + a];
             ke += (long double)(0.5 * p->mass * v * v);
             mom[a] += (long double)(p->mass * v);
         }
+    }
     orc_scatter(p, n, pos, type, D);
     double w = orc_field_energy(p, D);
     /* the bonded entry: bonds and angles */
@@ -537,13 +571,19 @@ void orc_energy(const orc_params* p, int64_t n, const double* pos, const double*
  * MD-SCF section).  Each step, with v the half-step velocity:
  *   F = F_field(x) + F_bond(x) - gamma m v + sqrt(2 gamma m kT / dt) xi(tag, n)
  *   v <- v + dt F / m
- *   x <- x + dt v                                                         */
+ *   x <- x + dt v
+ * With the Andersen thermostat (thermostat 2) there is no friction or noise
+ * force; a bead that collides at step n (orc_andersen_collides) takes
+ *   v <- sqrt(kT/m) xi(tag, n) + dt/(2m) F
+ * instead (its on-step velocity redrawn from the Maxwell distribution).
+ * Nose-Hoover (thermostat 1) runs through orc_run_nh.                     */
 int orc_run(const orc_params* p, int64_t n, double* pos, double* vel, const int32_t* type,
             int64_t n_bonds, const int32_t* pairs, int64_t step0, int32_t n_steps,
             double* energies)
 {
     if (p->field_every < 1 || p->n_species < 1 || p->n_species > ORC_MAX_SPECIES || n < 0 ||
-        p->force_mode < 0 || p->force_mode > 1)
+        p->force_mode < 0 || p->force_mode > 1 || p->thermostat == 1 ||
+        (p->thermostat == 2 && !(p->andersen_nu >= 0.0)))
         return -1;
     size_t nn = (size_t)(n > 0 ? n : 1);
     const int64_t M = n_nodes(p);
@@ -570,9 +610,15 @@ int orc_run(const orc_params* p, int64_t n, double* pos, double* vel, const int3
         if (k == n_steps) break;
         conservative_force(p, n, pos, type, BL, BN, V, G, Ff, Fb, Fc);
         total_force(p, n, vel, Fc, step, F);
-        for (int64_t i = 0; i < 3 * n; ++i) {
-            vel[i] += p->dt * F[i] / p->mass;
-            pos[i] += p->dt * vel[i];
+        for (int64_t i = 0; i < n; ++i) {
+            double u[3];
+            const int coll = andersen_velocity(p, i, step, u);
+            for (int a = 0; a < 3; ++a) {
+                const int64_t k = 3 * i + a;
+                if (coll) vel[k] = u[a] + 0.5 * p->dt * F[k] / p->mass;
+                else vel[k] += p->dt * F[k] / p->mass;
+                pos[k] += p->dt * vel[k];
+            }
         }
     }
     free(BL); free(BN); free(D); free(V); free(G); free(Ff); free(Fb); free(Fc); free(F);

@@ -53,8 +53,10 @@ typedef struct {
     double angle_k;     /* U = angle_k (cos theta - angle_cos0)^2 per bonded triplet */
     double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles */
     int32_t thermostat; /* 0: Langevin (gamma); 1: Nose-Hoover (section "MD methods and
-                           algorithms" names it for NVT; orc_run_nh) */
+                           algorithms" names it for NVT; orc_run_nh); 2: Andersen
+                           (named there too; orc_run) */
     double nh_tau;      /* Nose-Hoover relaxation time tau (> 0) */
+    double andersen_nu; /* Andersen collision frequency nu (>= 0) */
 } orc_params;
 
 int orc_num_threads(void);
@@ -63,6 +65,10 @@ int orc_num_threads(void);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* Three standard normals for bead `tag` at step `step` (Box-Muller). */
 void orc_gauss3(uint64_t seed, uint32_t tag, int64_t step, double xi[3]);
+/* Andersen collision of bead `tag` at step `step`: the uniform u of word 0 of
+ * Philox4x32-10(counter = (tag, step lo, step hi, 1), key = seed), compared in
+ * FP32 (both exact there): u < fl32(nu dt).  Returns 1 for a collision. */
+int orc_andersen_collides(const orc_params* p, uint32_t tag, int64_t step);
 
 /* Inverse mesh spacing per axis, fl32(M / L). */
 float orc_inv_h(const orc_params* p, int axis);
