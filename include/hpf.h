@@ -82,8 +82,10 @@ typedef struct {
     double angle_cos0;    /* bonded triplet (section "Bonded forces", cosine form), theta the
                              angle at the middle bead (pi for a straight chain); 0: none */
     int32_t thermostat;   /* 0: Langevin (gamma, seed); 1: Nose-Hoover NVT (nh_tau; gamma and
-                             seed unused), see hpf_get_thermostat */
+                             seed unused), see hpf_get_thermostat; 2: Andersen NVT
+                             (andersen_nu, seed; gamma unused), see hpf_step */
     double nh_tau;        /* Nose-Hoover relaxation time tau (> 0 when thermostat == 1) */
+    double andersen_nu;   /* Andersen collision frequency nu (>= 0 when thermostat == 2) */
 } hpf_params;
 
 /* Text for a status code (static storage). */
@@ -201,13 +203,19 @@ hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
  * (u0, u1) and z from (u2, u3).  The field is refreshed from the positions
  * when n % field_every == 0 (or when no field is valid) and held fixed in
  * between, as in the MD-SCF section.  With thermostat == 1 the step is the
- * Nose-Hoover scheme below instead (no friction or noise).
+ * Nose-Hoover scheme below instead (no friction or noise).  With thermostat
+ * == 2 (Andersen, the section "MD methods and algorithms") there is no
+ * friction or noise force; a bead collides at step n when the uniform of word
+ * 0 of Philox4x32-10(counter = (tag, n lo, n hi, 1)) is below fl32(nu dt),
+ * and then takes v <- sqrt(kT/m) xi + dt/(2m) F (xi as above): its on-step
+ * velocity redrawn from the Maxwell distribution.
  * Errors: HPF_ERR_INVALID (n_steps < 0; Nose-Hoover with chains longer than
  * 64 beads), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
 
 /* Observables at the current step, reduced in FP64 (synchronises):
- * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step),
+ * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step;
+ *   with Andersen, a bead colliding at step n counts its redrawn velocity),
  * out[1] bond energy sum k (r - r0)^2, out[2] field energy
  *   W = rho0 h^3 sum_nodes [1/2 kT sum_KK' chi phi_K phi_K' + 1/2 inv_kappa (sum phi - 1)^2]
  *   of a fresh scatter of the current positions, out[3] = out[0]+out[1]+out[2],

@@ -2,6 +2,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -196,7 +197,9 @@ hpf_status validate_params(const hpf_params* p) {
     if (p->force_mode != 0 && p->force_mode != 1) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
         return HPF_ERR_INVALID;
-    if (p->thermostat != 0 && p->thermostat != 1) return HPF_ERR_INVALID;
+    if (p->thermostat < 0 || p->thermostat > 2) return HPF_ERR_INVALID;
+    if (p->thermostat == 2 && !(p->andersen_nu >= 0.0 && isfinite(p->andersen_nu)))
+        return HPF_ERR_INVALID;
     if (p->thermostat == 1 && !(p->nh_tau > 0.0 && isfinite(p->nh_tau))) return HPF_ERR_INVALID;
     return HPF_OK;
 }
@@ -234,8 +237,8 @@ void derive_constants(hpf_ctx* c) {
     StepConsts& s = c->sc;
     s.dt = (float)p.dt;
     s.dt_m = (float)(p.dt / p.mass);
-    // Nose-Hoover replaces the Langevin friction and noise
-    const double gamma = p.thermostat == 1 ? 0.0 : p.gamma;
+    // Nose-Hoover and Andersen replace the Langevin friction and noise
+    const double gamma = p.thermostat == 0 ? p.gamma : 0.0;
     s.fric = (float)(gamma * p.mass);
     s.sigma = (float)sqrt(2.0 * gamma * p.mass * p.kT / p.dt);
     s.two_k = (float)(2.0 * p.bond_k);
@@ -249,6 +252,8 @@ void derive_constants(hpf_ctx* c) {
     s.exact = p.force_mode;
     s.two_ka = (float)(2.0 * p.angle_k);
     s.cos0 = (float)p.angle_cos0;
+    s.p_coll = p.thermostat == 2 ? (float)(p.andersen_nu * p.dt) : 0.0f;
+    s.sig_v = (float)sqrt(p.kT / p.mass);
     EnergyConsts& e = c->ec;
     memset(&e, 0, sizeof e);
     e.half_dt_m = 0.5 * p.dt / p.mass;
@@ -507,7 +512,7 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse) {
             q.G = c->G;
             q.D[0] = mesh_buf(c, 0);
             q.D[1] = mesh_buf(c, 1);
-            launch_step_warp_single(p, c->C, c->sc.sigma > 0.f, c->stream);
+            launch_step_warp_single(p, c->C, step_thermostat(c->sc), c->stream);
         } else
             launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, chunk, c->step, c->geom,
                         c->G, c->sc, fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr, c->dflag,
@@ -1219,10 +1224,13 @@ int batch_max_segments(hpf_batch* b) {
     return m;
 }
 
-bool batch_noise(hpf_batch* b) {
-    for (auto* c : b->rep)
-        if (c->sc.sigma > 0.f) return true;
-    return false;
+// The step kernels' thermostat for all replicas (they share the thermostat
+// kind; a replica without friction or collisions adds zero noise or never
+// collides under the kind's instantiation).
+int batch_thermostat(hpf_batch* b) {
+    int t = 0;
+    for (auto* c : b->rep) t = std::max(t, step_thermostat(c->sc));
+    return t;
 }
 
 void batch_advance(hpf_batch* b, long long chunk, bool fuse) {
@@ -1267,7 +1275,7 @@ hpf_status batch_capture(hpf_batch* b) {
         sp.cur = c0->cur ^ half;
         sp.dnext = c0->dmesh ^ half ^ 1;
         sp.step_dev = b->d_step;
-        launch_step_warp_batch(sp, batch_max_segments(b), batch_noise(b), b->stream);
+        launch_step_warp_batch(sp, batch_max_segments(b), batch_thermostat(b), b->stream);
         launch_advance_counter(b->d_step, fe, b->stream);
     }
     cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
@@ -1303,7 +1311,8 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
             (params[r].angle_k != 0.0) != (params[0].angle_k != 0.0))
             return HPF_ERR_INVALID;
     for (int r = 0; r < n_replicas; ++r)
-        if (params[r].thermostat != 0) return HPF_ERR_INVALID;  // batches run Langevin
+        if (params[r].thermostat == 1 || params[r].thermostat != params[0].thermostat)
+            return HPF_ERR_INVALID;  // Langevin or Andersen, the same for every replica
     hpf_batch* b = new hpf_batch();
     b->R = n_replicas;
     b->stream = (cudaStream_t)stream;
@@ -1443,7 +1452,7 @@ hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
         fill_step_params(b, p, (int)chunk, fuse);
         {
             StageScope sc(c0, HPF_STAGE_STEP, 1);
-            launch_step_warp_batch(p, batch_max_segments(b), batch_noise(b), b->stream);
+            launch_step_warp_batch(p, batch_max_segments(b), batch_thermostat(b), b->stream);
         }
         LAUNCH_CHECK(c0);
         batch_advance(b, chunk, fuse);

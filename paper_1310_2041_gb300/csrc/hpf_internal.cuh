@@ -57,7 +57,14 @@ struct StepConsts {
     int exact;                  // field force: 0 interpolated gradient, 1 exact energy gradient
     float two_ka;               // 2 * angle_k (0: no angle terms)
     float cos0;                 // cos of the equilibrium angle
+    float p_coll;               // Andersen collision probability per step fl32(nu dt) (0: none)
+    float sig_v;                // sqrt(kT / m): the Maxwell velocity scale
 };
+
+// Thermostat of the step kernels: 0 none (NVE), 1 Langevin noise, 2 Andersen.
+inline int step_thermostat(const StepConsts& c) {
+    return c.sigma > 0.f ? 1 : (c.p_coll > 0.f ? 2 : 0);
+}
 
 // Coefficients of the field stencil: gradient of V_K from integer central
 // differences of D_K', and V_K from D_K'.
@@ -244,6 +251,17 @@ __device__ __forceinline__ void gauss3(const StepConsts& c, uint32_t tag, long l
     gx = -a * k1;
     gy = -a * s1;
     gz = -b * __cosf(6.28318530717958648f * (open_uniform(c3) - 0.5f));
+}
+
+// Andersen collision of bead `tag` at step `step`: the uniform of word 0 of
+// Philox4x32-10(counter = (tag, step lo, step hi, 1)) below p_coll.  Both are
+// exact in FP32, so the decision is the same as an FP64 comparison of them.
+__device__ __forceinline__ bool andersen_collides(const StepConsts& c, uint32_t tag,
+                                                  long long step) {
+    uint32_t c0 = tag, c1 = (uint32_t)step, c2 = (uint32_t)((unsigned long long)step >> 32),
+             c3 = 1u;
+    philox4x32_10(c0, c1, c2, c3, c.rk0, c.rk1);
+    return open_uniform(c0) < c.p_coll;
 }
 
 // Mesh coordinate of one component.  t = floor(2^13 s) is exact in FP32, so
@@ -541,9 +559,9 @@ int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* me
                 uint32_t* meta_out, int n, int C, MeshGeom g, cudaStream_t s);
 
 int step_halo_max();
-void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
+void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,
                             cudaStream_t s);
-void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise, cudaStream_t s);
+void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm, cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
 int field_tile_candidates();
 bool field_tile_is_plain(int id);

@@ -92,7 +92,15 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         fy -= c.fric * vy;
         fz -= c.fric * vz;
         const float hf = (float)e.half_dt_m;
-        const float ux = fmaf(hf, fx, vx), uy = fmaf(hf, fy, vy), uz = fmaf(hf, fz, vz);
+        float ux = fmaf(hf, fx, vx), uy = fmaf(hf, fy, vy), uz = fmaf(hf, fz, vz);
+        if (c.p_coll > 0.f && andersen_collides(c, m & kTagMask, step)) {
+            // Andersen: this step's collision redraws the on-step velocity
+            float nx, ny, nz;
+            gauss3(c, m & kTagMask, step, nx, ny, nz);
+            ux = c.sig_v * nx;
+            uy = c.sig_v * ny;
+            uz = c.sig_v * nz;
+        }
         kf = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, kf)));
         pfx += ux;
         pfy += uy;

@@ -167,7 +167,7 @@ __device__ __forceinline__ void neighbour_sync(int w) {
     if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
-template <bool kNoise, bool kExact, bool kAngles>
+template <int kTherm, bool kExact, bool kAngles>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
                                                         int halo, int n_sub, long long step0,
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
         float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
         eval_cell_cache<kExact>(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly),
                                 __fsub_rn(s2, flz), fx, fy, fz, g);
-        if (kNoise) {
+        if (kTherm == 1) {
             float nx, ny, nz;
             gauss3(c, tag, step0 + k, nx, ny, nz);
             fx = fmaf(c.sigma, nx, fx);
@@ -270,9 +270,19 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
             fy += ay;
             fz += az;
         }
-        vx = fmaf(c.dt_m, fx, vx);
-        vy = fmaf(c.dt_m, fy, vy);
-        vz = fmaf(c.dt_m, fz, vz);
+        if (kTherm == 2 && andersen_collides(c, tag, step0 + k)) {
+            // the on-step velocity redrawn, then the second half kick
+            float nx, ny, nz;
+            gauss3(c, tag, step0 + k, nx, ny, nz);
+            const float h = 0.5f * c.dt_m;
+            vx = fmaf(h, fx, c.sig_v * nx);
+            vy = fmaf(h, fy, c.sig_v * ny);
+            vz = fmaf(h, fz, c.sig_v * nz);
+        } else {
+            vx = fmaf(c.dt_m, fx, vx);
+            vy = fmaf(c.dt_m, fy, vy);
+            vz = fmaf(c.dt_m, fz, vz);
+        }
         x = fmaf(c.dt, vx, x);
         y = fmaf(c.dt, vy, y);
         z = fmaf(c.dt, vz, z);
@@ -301,13 +311,13 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     }
 }
 
-template <bool kNoise, bool kExact, bool kAngles>
+template <int kTherm, bool kExact, bool kAngles>
 static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_step<kNoise, kExact, kAngles>,
+        cudaFuncSetAttribute(k_step<kTherm, kExact, kAngles>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
         attr_set = true;
     }
@@ -316,19 +326,19 @@ static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n
     const int halo = kAngles ? 2 * n_sub : n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<kNoise, kExact, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
+    k_step<kTherm, kExact, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
         in, out, meta, n, halo, n_sub, step0, g, G, c, D_next, flag);
 }
 
-template <bool kNoise, bool kExact>
+template <int kTherm, bool kExact>
 static void launch_step_a(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (c.two_ka != 0.f)
-        launch_step_t<kNoise, kExact, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
+        launch_step_t<kTherm, kExact, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
                                             s);
     else
-        launch_step_t<kNoise, kExact, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
+        launch_step_t<kTherm, kExact, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
                                              flag, s);
 }
 
@@ -336,15 +346,18 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
                  long long step0, MeshGeom g, const float4* G, StepConsts c,
                  unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (n <= 0 || n_sub <= 0) return;
-    const bool noise = c.sigma > 0.f;
-    if (noise && c.exact)
-        launch_step_a<true, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
-    else if (noise)
-        launch_step_a<true, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
-    else if (c.exact)
-        launch_step_a<false, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
-    else
-        launch_step_a<false, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+    const int therm = step_thermostat(c);
+#define HPF_HALO(T)                                                                          \
+    if (c.exact) launch_step_a<T, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s); \
+    else launch_step_a<T, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+    if (therm == 1) {
+        HPF_HALO(1)
+    } else if (therm == 2) {
+        HPF_HALO(2)
+    } else {
+        HPF_HALO(0)
+    }
+#undef HPF_HALO
 }
 
 // ------------------------------------------------------------------ A6, warp form
@@ -390,15 +403,17 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
 
 // Kick of one bead: field (cached cell polynomial at offsets f), friction,
 // noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
-// chain neighbours.
-template <bool kNoise, bool kExact>
+// chain neighbours.  Andersen (kTherm 2): a colliding bead's on-step velocity
+// is sqrt(kT/m) (nx, ny, nz) before the second half kick.
+template <int kTherm, bool kExact>
 __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
                                           float ny, float nz, float bx, float by, float bz,
                                           const StepConsts& c, const MeshGeom& g,
-                                          const float4* __restrict__ cache, int slot) {
+                                          const float4* __restrict__ cache, int slot,
+                                          bool coll) {
     float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
     eval_cell_cache<kExact>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
-    if (kNoise) {
+    if (kTherm == 1) {
         fx = fmaf(c.sigma, nx, fx);
         fy = fmaf(c.sigma, ny, fy);
         fz = fmaf(c.sigma, nz, fz);
@@ -406,9 +421,16 @@ __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2,
     fx += bx;
     fy += by;
     fz += bz;
-    b.vx = fmaf(c.dt_m, fx, b.vx);
-    b.vy = fmaf(c.dt_m, fy, b.vy);
-    b.vz = fmaf(c.dt_m, fz, b.vz);
+    if (kTherm == 2 && coll) {
+        const float h = 0.5f * c.dt_m;
+        b.vx = fmaf(h, fx, c.sig_v * nx);
+        b.vy = fmaf(h, fy, c.sig_v * ny);
+        b.vz = fmaf(h, fz, c.sig_v * nz);
+    } else {
+        b.vx = fmaf(c.dt_m, fx, b.vx);
+        b.vy = fmaf(c.dt_m, fy, b.vy);
+        b.vz = fmaf(c.dt_m, fz, b.vz);
+    }
 }
 
 __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf out,
@@ -435,7 +457,7 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <bool kNoise, bool kExact, bool kAngles>
+template <int kTherm, bool kExact, bool kAngles>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -473,14 +495,21 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
         cell_check<kExact>(b0, G, g, wcache, tid, f00, f01, f02);
         cell_check<kExact>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
         float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
-        if (kNoise) {
+        bool coll0 = false, coll1 = false;
+        if (kTherm == 1) {
             gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kNoise, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
-                                  tid);
-        kick_bead<kNoise, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
-                                  kWarpBlock + tid);
+        if (kTherm == 2) {
+            coll0 = andersen_collides(c, b0.m & kTagMask, step0 + k);
+            coll1 = andersen_collides(c, b1.m & kTagMask, step0 + k);
+            if (coll0) gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
+            if (coll1) gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
+        }
+        kick_bead<kTherm, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
+                                  tid, coll0);
+        kick_bead<kTherm, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
+                                  kWarpBlock + tid, coll1);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
         b0.z = fmaf(c.dt, b0.vz, b0.z);
@@ -496,7 +525,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <bool kNoise, int kCap, bool kExact, bool kAngles>
+template <int kTherm, int kCap, bool kExact, bool kAngles>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
     extern __shared__ float4 wcache[];
@@ -526,29 +555,30 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
         }
         const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
-        advance_segment<kNoise, kExact, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+        advance_segment<kTherm, kExact, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
                                                  rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
     }
 }
 
-template <int kCap, bool kNoise>
+template <int kCap, int kTherm>
 static void warp_attrs_n() {
-    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, false, false>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, false, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, true, false>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, true, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, false, true>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, false, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kNoise, kCap, true, true>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, true, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
 }
 
 template <int kCap>
 static void warp_attrs() {
-    warp_attrs_n<kCap, true>();
-    warp_attrs_n<kCap, false>();
+    warp_attrs_n<kCap, 0>();
+    warp_attrs_n<kCap, 1>();
+    warp_attrs_n<kCap, 2>();
 }
 
 static int warp_grid_cap() {
@@ -560,50 +590,51 @@ static int warp_grid_cap() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_step_warp_batch<true, HPF_MAX_REPLICAS, false, false>, kWarpBlock,
+            &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, false, false>, kWarpBlock,
             kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     return cap;
 }
 
-template <int kCap, bool kNoise>
+template <int kCap, int kTherm>
 static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, bool exact, bool angles,
                           cudaStream_t s) {
     if (exact && angles)
-        k_step_warp_batch<kNoise, kCap, true, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<kTherm, kCap, true, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
     else if (exact)
-        k_step_warp_batch<kNoise, kCap, true, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<kTherm, kCap, true, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
     else if (angles)
-        k_step_warp_batch<kNoise, kCap, false, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<kTherm, kCap, false, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
     else
-        k_step_warp_batch<kNoise, kCap, false, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        k_step_warp_batch<kTherm, kCap, false, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
 template <int kCap>
-static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, bool noise, bool exact,
+static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, int therm, bool exact,
                         cudaStream_t s) {
     const bool angles = p.rep[0].c.two_ka != 0.f;  // all replicas alike (checked at init)
-    if (noise) launch_warp_n<kCap, true>(p, blocks, exact, angles, s);
-    else launch_warp_n<kCap, false>(p, blocks, exact, angles, s);
+    if (therm == 1) launch_warp_n<kCap, 1>(p, blocks, exact, angles, s);
+    else if (therm == 2) launch_warp_n<kCap, 2>(p, blocks, exact, angles, s);
+    else launch_warp_n<kCap, 0>(p, blocks, exact, angles, s);
 }
 
-void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, bool noise,
+void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,
                             cudaStream_t s) {
     if (max_seg_total <= 0 || p.n_sub <= 0) return;
     const int cap = warp_grid_cap();
     const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    launch_warp(p, blocks, noise, p.rep[0].c.exact != 0, s);  // replicas share the force mode
+    launch_warp(p, blocks, therm, p.rep[0].c.exact != 0, s);  // replicas share the force mode
 }
 
-void launch_step_warp_single(const SingleStepParams& p, int max_seg, bool noise,
+void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm,
                              cudaStream_t s) {
     if (max_seg <= 0 || p.n_sub <= 0) return;
     const int cap = warp_grid_cap();
     const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    launch_warp(p, blocks, noise, p.rep[0].c.exact != 0, s);
+    launch_warp(p, blocks, therm, p.rep[0].c.exact != 0, s);
 }
 
 
