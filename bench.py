@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
-    ap.add_argument("--thermostat", default="langevin", choices=["langevin", "nh"],
-                    help="plain workloads: Langevin (the default) or Nose-Hoover NVT")
+    ap.add_argument("--thermostat", default="langevin", choices=["langevin", "nh", "andersen"],
+                    help="plain workloads: Langevin (the default), Nose-Hoover or Andersen NVT")
     ap.add_argument("--nh-tau", type=float, default=1.0)
+    ap.add_argument("--andersen-nu", type=float, default=1.0)
     ap.add_argument("--net-lags", default="",
                     help="learned workload: also train and judge a network at these lags "
                          "(comma-separated step counts)")
@@ -134,6 +135,22 @@ def traffic_record():
     return rec if rec.get("source_sha256") == h.hexdigest() else None
 
 
+def thermostat_params(args):
+    if args.thermostat == "nh":
+        return {"thermostat": 1, "nh_tau": args.nh_tau}
+    if args.thermostat == "andersen":
+        return {"thermostat": 2, "andersen_nu": args.andersen_nu}
+    return {}
+
+
+def thermostat_name(args, pp):
+    if args.thermostat == "nh":
+        return f"nose-hoover tau={args.nh_tau}"
+    if args.thermostat == "andersen":
+        return f"andersen nu={args.andersen_nu}"
+    return f"langevin gamma={pp['gamma']}"
+
+
 def cpu_oracle_rate(w, data, budget_s: float, over=None):
     """Oracle bead-steps/s on the full workload, whole field periods until about
     budget_s of CPU work (a 2 %-of-chains calibration sizes the sample)."""
@@ -208,8 +225,7 @@ def run_reference(args):
     data = W.generate(w)
     oracle.build()
     nh = args.thermostat == "nh"
-    op = oracle.make_params(**dict(w.params(), **({"thermostat": 1, "nh_tau": args.nh_tau}
-                                                  if nh else {})))
+    op = oracle.make_params(**dict(w.params(), **thermostat_params(args)))
 
     def run(p, pos, vel, types, bonds, step0, n_steps, xe=(0.0, 0.0)):
         if nh:
@@ -247,7 +263,7 @@ def run_reference(args):
             "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_beads": w.n_beads, "sample_beads": n,
-                       "thermostat": f"nose-hoover tau={args.nh_tau}" if nh else "langevin"},
+                       "thermostat": thermostat_name(args, w.params())},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -274,7 +290,7 @@ def run_ours(args):
     pp = w.params()
     pp["sort_every"] = args.sort_every
     nh = args.thermostat == "nh"
-    therm = {"thermostat": 1, "nh_tau": args.nh_tau} if nh else {}
+    therm = thermostat_params(args)
     pp.update(therm)
     stream = torch.cuda.current_stream()
     sysm = hpf.System(hpf.make_params(**pp), stream=stream)
@@ -382,8 +398,7 @@ def run_ours(args):
                 "config": {"workload": w.name, "n_beads": w.n_beads, "mesh": w.mesh,
                            "species": w.n_species, "field_every": fe,
                            "sort_every": args.sort_every, "parallelism": f"replicas{world}",
-                           "thermostat": (f"nose-hoover tau={args.nh_tau}" if nh else
-                                          f"langevin gamma={pp['gamma']}"),
+                           "thermostat": thermostat_name(args, pp),
                            "l2": "flushed (256 MB write) before each timed field period",
                            "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
