@@ -195,6 +195,37 @@ struct TiledFieldParamsT {
 using TiledFieldParams = TiledFieldParamsT<HPF_MAX_REPLICAS>;
 using SingleFieldParams = TiledFieldParamsT<1>;
 
+// ------------------------------------------------------------------ dependent launch
+//
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// launch_pdl may be scheduled while its predecessor on the stream is still
+// running, so launch latency overlaps the predecessor's tail.  Every such
+// kernel executes griddep_wait() before its first global-memory access, which
+// returns once the predecessor grid has completed and its writes are visible:
+// the ordering is that of the plain stream.  griddep_launch_dependents() lets
+// the next kernel be scheduled early (it waits in turn).  Both are no-ops for
+// kernels launched without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------------ device helpers
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products

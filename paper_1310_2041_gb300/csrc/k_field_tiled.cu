@@ -86,6 +86,8 @@ __device__ __forceinline__ int field_replica(const TiledFieldParamsT<kCap>& p) {
 
 template <int S, int TX, int TY, int TZ, int kCap>
 __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__ TiledFieldParamsT<kCap> p) {
+    griddep_wait();
+    griddep_launch_dependents();
     constexpr int BX = TX + 4, BY = TY + 2, BZ = TZ + 2;
     constexpr int BOX = BX * BY * BZ;
     constexpr int NT = TX * TY;
@@ -196,6 +198,8 @@ __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__
 // loaded directly (through L1/L2), same arithmetic as the tiled kernel.
 template <int S, int kCap>
 __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ TiledFieldParamsT<kCap> p) {
+    griddep_wait();
+    griddep_launch_dependents();
     const int lo = field_replica(p);
     const TiledFieldRep& r = p.rep[lo];
     const MeshGeom& g = r.g;
@@ -247,6 +251,8 @@ __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ Til
 // arithmetic is needed.  Same arithmetic as the other candidates.
 template <int S, int kCap>
 __global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ TiledFieldParamsT<kCap> p) {
+    griddep_wait();
+    griddep_launch_dependents();
     const int lo = field_replica(p);
     const TiledFieldRep& r = p.rep[lo];
     const MeshGeom& g = r.g;
@@ -336,7 +342,8 @@ static void launch_tile(const TiledFieldParamsT<kCap>& p, cudaStream_t s) {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_field_tiled<S, TX, TY, TZ, kCap><<<p.blocks, TX * TY, smem, s>>>(p);
+    if (kCap == 1) launch_pdl(k_field_tiled<S, TX, TY, TZ, kCap>, p.blocks, TX * TY, smem, s, p);
+    else k_field_tiled<S, TX, TY, TZ, kCap><<<p.blocks, TX * TY, smem, s>>>(p);
 }
 
 template <int S, int kCap>
@@ -348,8 +355,14 @@ static void launch_for_species(const TiledFieldParamsT<kCap>& p, int tile, cudaS
         case 3: launch_tile<S, 64, 4, 4>(p, s); break;
         case 4: launch_tile<S, 16, 16, 8>(p, s); break;
         case 5: launch_tile<S, 32, 4, 8>(p, s); break;
-        case kPairTile: k_field_pair<S, kCap><<<p.blocks, 256, 0, s>>>(p); break;
-        default: k_field_plain<S, kCap><<<p.blocks, 256, 0, s>>>(p); break;
+        case kPairTile:
+            if (kCap == 1) launch_pdl(k_field_pair<S, kCap>, p.blocks, 256, 0, s, p);
+            else k_field_pair<S, kCap><<<p.blocks, 256, 0, s>>>(p);
+            break;
+        default:
+            if (kCap == 1) launch_pdl(k_field_plain<S, kCap>, p.blocks, 256, 0, s, p);
+            else k_field_plain<S, kCap><<<p.blocks, 256, 0, s>>>(p);
+            break;
     }
 }
 

@@ -528,6 +528,8 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 template <int kTherm, int kCap, bool kExact, bool kAngles>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
+    griddep_wait();
+    griddep_launch_dependents();
     extern __shared__ float4 wcache[];
     __shared__ int s_off[kCap + 1];
     const int tid = threadIdx.x;
@@ -597,17 +599,26 @@ static int warp_grid_cap() {
     return cap;
 }
 
+// A context's launches use dependent launch; a batch's are captured into
+// graphs and launched plainly.
+template <int kCap>
+static void launch_warp_k(void (*k)(const BatchStepParamsT<kCap>), const BatchStepParamsT<kCap>& p,
+                          int blocks, cudaStream_t s) {
+    if (kCap == 1) launch_pdl(k, blocks, kWarpBlock, kWarpSmem, s, p);
+    else k<<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+}
+
 template <int kCap, int kTherm>
 static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, bool exact, bool angles,
                           cudaStream_t s) {
     if (exact && angles)
-        k_step_warp_batch<kTherm, kCap, true, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        launch_warp_k(k_step_warp_batch<kTherm, kCap, true, true>, p, blocks, s);
     else if (exact)
-        k_step_warp_batch<kTherm, kCap, true, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        launch_warp_k(k_step_warp_batch<kTherm, kCap, true, false>, p, blocks, s);
     else if (angles)
-        k_step_warp_batch<kTherm, kCap, false, true><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        launch_warp_k(k_step_warp_batch<kTherm, kCap, false, true>, p, blocks, s);
     else
-        k_step_warp_batch<kTherm, kCap, false, false><<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
+        launch_warp_k(k_step_warp_batch<kTherm, kCap, false, false>, p, blocks, s);
 }
 
 template <int kCap>
