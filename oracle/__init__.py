@@ -18,6 +18,8 @@ with the CUDA library.  Parity status per function:
                  field energy derivative equals the potential)
   run (Andersen) pinned (nu = 0 is NVE, force-free velocity autocorrelation
                  (1 - nu dt)^n, collision rate, mean temperature)
+  field_force_staggered  pinned (quadratic fields exact, central difference on
+                 a vertex, continuity between vertices, sinusoid closed form)
   run_nh         pinned (NVE limit, free-particle thermostat ODE, extended-energy
                  conservation, mean temperature)
 """
@@ -109,6 +111,7 @@ def lib():
             L.orc_field_energy.argtypes = [pp, P(i64)]
             L.orc_field_energy.restype = f64
             L.orc_field_force_exact.argtypes = [pp, i64, P(f64), P(i32), P(f64), P(f64)]
+            L.orc_field_force_staggered.argtypes = [pp, i64, P(f64), P(i32), P(f64), P(f64)]
             L.orc_energy.argtypes = [pp, i64, P(f64), P(f64), P(i32), P(i32), P(i32), P(f64),
                                      P(f64), i64, P(f64)]
             L.orc_run.argtypes = [pp, i64, P(f64), P(f64), P(i32), i64, P(i32), i64, i32, P(f64)]
@@ -278,6 +281,18 @@ def field_force_exact(p: Params, pos, types, V) -> np.ndarray:
     lib().orc_field_force_exact(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
                                 _p(types, ctypes.c_int32), _p(V, ctypes.c_double),
                                 _p(F, ctypes.c_double))
+    return F
+
+
+def field_force_staggered(p: Params, pos, types, V) -> np.ndarray:
+    """Algorithm 1's staggered field force (force_mode 2) from the potential V."""
+    pos = _f64(pos, (-1, 3))
+    types = _i32(types)
+    V = _f64(V)
+    F = np.zeros_like(pos)
+    lib().orc_field_force_staggered(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                                    _p(types, ctypes.c_int32), _p(V, ctypes.c_double),
+                                    _p(F, ctypes.c_double))
     return F
 
 

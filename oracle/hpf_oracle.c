@@ -319,6 +319,47 @@ void orc_field_force_exact(const orc_params* p, int64_t n, const double* pos, co
     }
 }
 
+/* The field force of Algorithm 1, kernels 3-4, read literally (force_mode 2).
+ * Kernel 3 keeps, per vertex and axis, the backward and forward differences
+ * of the density (here of V, into which kernel 4's chi sum folds), which sit
+ * half a mesh spacing below and above the vertex; kernel 4 blends them with
+ * "fraction ratios" at the bead's vertex.  Reading: the vertex is the one
+ * nearest the bead, c = floor(s + 1/2) per axis (s the FP32 mesh coordinate),
+ * and the fractions are the linear interpolation weights between the two
+ * half-points, xf1 = 1/2 - d and xf2 = 1/2 + d with d = s - c in [-1/2, 1/2):
+ *   F_a = -(1/h_a) [xf1 (V(c) - V(c - e_a)) + xf2 (V(c + e_a) - V(c))],
+ * only the vertex's own grid line entering each component.  Parity: pinned
+ * (quadratic fields exact, central difference on a vertex, continuity between
+ * vertices, the sinusoid closed form). */
+void orc_field_force_staggered(const orc_params* p, int64_t n, const double* pos,
+                               const int32_t* type, const double* V, double* F)
+{
+    const int64_t M = n_nodes(p);
+    double inv_h[3];
+    for (int a = 0; a < 3; ++a) inv_h[a] = (double)p->mesh[a] / (double)p->box[a];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c[3];
+        double d[3];
+        for (int a = 0; a < 3; ++a) {
+            const float s = (float)pos[3 * i + a] * orc_inv_h(p, a); /* as mesh_coord */
+            const double r = floor((double)s + 0.5);
+            d[a] = (double)s - r;
+            c[a] = wrap((int64_t)r, p->mesh[a]);
+        }
+        const double* Vk = V + (int64_t)type[i] * M;
+        const double vc = Vk[node_index(p, c[0], c[1], c[2])];
+        for (int a = 0; a < 3; ++a) {
+            int64_t m[3] = {c[0], c[1], c[2]}, q[3] = {c[0], c[1], c[2]};
+            m[a] = wrap(c[a] - 1, p->mesh[a]);
+            q[a] = wrap(c[a] + 1, p->mesh[a]);
+            const double vm = Vk[node_index(p, m[0], m[1], m[2])];
+            const double vp = Vk[node_index(p, q[0], q[1], q[2])];
+            F[3 * i + a] = -inv_h[a] * ((0.5 - d[a]) * (vc - vm) + (0.5 + d[a]) * (vp - vc));
+        }
+    }
+}
+
 /* ------------------------------------------------------------ A5: bonds */
 
 int orc_bond_table(int64_t n, int64_t n_bonds, const int32_t* pairs, int32_t* BL, int32_t* BN)
@@ -515,6 +556,8 @@ static void conservative_force(const orc_params* p, int64_t n, const double* pos
 {
     if (p->force_mode == 1)
         orc_field_force_exact(p, n, pos, type, V, Ff);
+    else if (p->force_mode == 2)
+        orc_field_force_staggered(p, n, pos, type, V, Ff);
     else
         orc_field_force(p, n, pos, type, G, Ff);
     orc_bond_force(p, n, pos, BL, BN, Fb);
@@ -582,7 +625,7 @@ int orc_run(const orc_params* p, int64_t n, double* pos, double* vel, const int3
             double* energies)
 {
     if (p->field_every < 1 || p->n_species < 1 || p->n_species > ORC_MAX_SPECIES || n < 0 ||
-        p->force_mode < 0 || p->force_mode > 1 || p->thermostat == 1 ||
+        p->force_mode < 0 || p->force_mode > 2 || p->thermostat == 1 ||
         (p->thermostat == 2 && !(p->andersen_nu >= 0.0)))
         return -1;
     size_t nn = (size_t)(n > 0 ? n : 1);
@@ -656,7 +699,7 @@ int orc_run_nh(const orc_params* p, int64_t n, double* pos, double* vel, const i
                double xe[2], double* energies)
 {
     if (p->field_every < 1 || p->n_species < 1 || p->n_species > ORC_MAX_SPECIES || n < 0 ||
-        p->force_mode < 0 || p->force_mode > 1 || !(p->nh_tau > 0.0) || !xe)
+        p->force_mode < 0 || p->force_mode > 2 || !(p->nh_tau > 0.0) || !xe)
         return -1;
     size_t nn = (size_t)(n > 0 ? n : 1);
     const int64_t M = n_nodes(p);

@@ -49,7 +49,9 @@ typedef struct {
     uint64_t seed;
     int32_t field_every;
     int32_t force_mode; /* 0: interpolated central-difference gradient (Algorithm 1);
-                           1: exact derivative of the CIC field energy (pinning variant) */
+                           1: exact derivative of the CIC field energy (pinning variant);
+                           2: Algorithm 1's staggered differences blended at the
+                              nearest vertex (orc_field_force_staggered) */
     double angle_k;     /* U = angle_k (cos theta - angle_cos0)^2 per bonded triplet */
     double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles */
     int32_t thermostat; /* 0: Langevin (gamma); 1: Nose-Hoover (section "MD methods and
@@ -92,6 +94,8 @@ void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const in
 double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
                         const int32_t* BN);
 /* Build the BL / BN bond table from a list of bonded pairs; returns 0 or -1 on overflow. */
+void orc_field_force_staggered(const orc_params* p, int64_t n, const double* pos,
+                               const int32_t* type, const double* V, double* F);
 int orc_bond_table(int64_t n, int64_t n_bonds, const int32_t* pairs, int32_t* BL, int32_t* BN);
 /* Harmonic bond force per bead, each bond evaluated from both ends. */
 void orc_bond_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
