@@ -194,7 +194,7 @@ hpf_status validate_params(const hpf_params* p) {
             if (!isfinite(a) || a != b) return HPF_ERR_INVALID;  // chi must be symmetric
         }
     if (p->field_every < 1 || p->sort_every < 0) return HPF_ERR_INVALID;
-    if (p->force_mode != 0 && p->force_mode != 1) return HPF_ERR_INVALID;
+    if (p->force_mode < 0 || p->force_mode > 2) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
         return HPF_ERR_INVALID;
     if (p->thermostat < 0 || p->thermostat > 2) return HPF_ERR_INVALID;
@@ -249,7 +249,7 @@ void derive_constants(hpf_ctx* c) {
         s.rk0[r] = s.seed_lo + (uint32_t)r * 0x9E3779B9u;
         s.rk1[r] = s.seed_hi + (uint32_t)r * 0xBB67AE85u;
     }
-    s.exact = p.force_mode;
+    s.force_mode = p.force_mode;
     s.two_ka = (float)(2.0 * p.angle_k);
     s.cos0 = (float)p.angle_cos0;
     s.p_coll = p.thermostat == 2 ? (float)(p.andersen_nu * p.dt) : 0.0f;

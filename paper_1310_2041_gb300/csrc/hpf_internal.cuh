@@ -54,7 +54,8 @@ struct StepConsts {
     float r0;
     uint32_t seed_lo, seed_hi;
     uint32_t rk0[10], rk1[10];  // Philox round keys: seed + r * (Weyl increments)
-    int exact;                  // field force: 0 interpolated gradient, 1 exact energy gradient
+    int force_mode;             // field force: 0 interpolated gradient, 1 exact energy gradient,
+                                // 2 staggered differences at the nearest vertex
     float two_ka;               // 2 * angle_k (0: no angle terms)
     float cos0;                 // cos of the equilibrium angle
     float p_coll;               // Andersen collision probability per step fl32(nu dt) (0: none)
@@ -418,6 +419,79 @@ __device__ __forceinline__ void gather_field_exact(const float4* __restrict__ Gt
     fx = fmaf(-g.inv_h[0], dx, fx);
     fy = fmaf(-g.inv_h[1], dy, fy);
     fz = fmaf(-g.inv_h[2], dz, fz);
+}
+
+// Algorithm 1's staggered field force (kernels 3-4 read literally): along each
+// axis the backward and forward differences of V at the vertex c nearest the
+// bead are blended with the linear fractions 1/2 - d and 1/2 + d, d = s - c:
+//   F_a = -(1/h_a) [g0 + d g1],  g0 = (V(c+1) - V(c-1)) / 2,  g1 = V(c+1) - 2 V(c) + V(c-1)
+// (the derivative of the quadratic through the three values on the vertex's
+// grid line).  stag_coefs and the final fma are shared by the direct gather
+// and the per-bead cache of the step kernels, so both give the same bits.
+__device__ __forceinline__ float stag_vertex(float s) { return floorf(s + 0.5f); }
+
+// Periodic image of a vertex coordinate (an integer-valued float) in [0, m).
+__device__ __forceinline__ float vertex_wrap(float k, float m, float inv_m) {
+    const float w = __fmaf_rn(-m, floorf((k + 0.5f) * inv_m), k);
+    return fminf(fmaxf(w, 0.0f), m - 1.0f);
+}
+
+__device__ __forceinline__ void stag_coefs(float vm, float vc, float vp, float& g0, float& g1) {
+    g0 = 0.5f * (vp - vm);
+    g1 = (vp - vc) - (vc - vm);
+}
+
+// The six coefficients (g0, g1 per axis) of the bead's nearest vertex
+// (kx, ky, kz) from the V components of the ghosted field array.
+__device__ __forceinline__ void stag_vertex_coefs(const float4* __restrict__ Gt, const MeshGeom& g,
+                                                  float kx, float ky, float kz, float (&c)[6]) {
+    const float wx = vertex_wrap(kx, (float)g.mx, g.inv_m[0]);
+    const float wy = vertex_wrap(ky, (float)g.my, g.inv_m[1]);
+    const float wz = vertex_wrap(kz, (float)g.mz, g.inv_m[2]);
+    const int ix = (int)wx, iy = (int)wy, iz = (int)wz;
+    const int o = iz * g.gxy + iy * g.gx + ix;
+    // the upper neighbours may be ghost entries; the lower ones wrap
+    const int oxm = ix == 0 ? o + (g.mx - 1) : o - 1;
+    const int oym = iy == 0 ? o + (g.my - 1) * g.gx : o - g.gx;
+    const int ozm = iz == 0 ? o + (g.mz - 1) * g.gxy : o - g.gxy;
+    const float vc = __ldg(Gt + o).w;
+    stag_coefs(__ldg(Gt + oxm).w, vc, __ldg(Gt + o + 1).w, c[0], c[1]);
+    stag_coefs(__ldg(Gt + oym).w, vc, __ldg(Gt + o + g.gx).w, c[2], c[3]);
+    stag_coefs(__ldg(Gt + ozm).w, vc, __ldg(Gt + o + g.gxy).w, c[4], c[5]);
+}
+
+__device__ __forceinline__ void stag_force(const float (&c)[6], float dx, float dy, float dz,
+                                           const MeshGeom& g, float& fx, float& fy, float& fz) {
+    fx = fmaf(-g.inv_h[0], fmaf(dx, c[1], c[0]), fx);
+    fy = fmaf(-g.inv_h[1], fmaf(dy, c[3], c[2]), fy);
+    fz = fmaf(-g.inv_h[2], fmaf(dz, c[5], c[4]), fz);
+}
+
+// The staggered field force at position (x, y, z), gathered directly.
+__device__ __forceinline__ void gather_field_staggered(const float4* __restrict__ Gt,
+                                                       const MeshGeom& g, float x, float y,
+                                                       float z, float& fx, float& fy, float& fz) {
+    const float sx = __fmul_rn(x, g.inv_h[0]), sy = __fmul_rn(y, g.inv_h[1]),
+                sz = __fmul_rn(z, g.inv_h[2]);
+    const float kx = stag_vertex(sx), ky = stag_vertex(sy), kz = stag_vertex(sz);
+    float c[6];
+    stag_vertex_coefs(Gt, g, kx, ky, kz, c);
+    stag_force(c, __fsub_rn(sx, kx), __fsub_rn(sy, ky), __fsub_rn(sz, kz), g, fx, fy, fz);
+}
+
+// Field force of mode 0, 1 or 2 at (x, y, z), gathered directly.
+__device__ __forceinline__ void gather_field_mode(const float4* __restrict__ Gt, const MeshGeom& g,
+                                                  int mode, float x, float y, float z, float& fx,
+                                                  float& fy, float& fz) {
+    if (mode == 2) {
+        gather_field_staggered(Gt, g, x, y, z, fx, fy, fz);
+        return;
+    }
+    const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
+    const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
+    const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
+    if (mode == 1) gather_field_exact(Gt, g, ax, ay, az, fx, fy, fz);
+    else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
 }
 
 // Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (1 - r0 / r) d, d = x_i - x_j,

@@ -75,12 +75,8 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                 ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
             }
         }
-        const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
-        const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
-        const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
         const float4* Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
-        if (c.exact) gather_field_exact(Gt, g, ax, ay, az, fx, fy, fz);
-        else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
+        gather_field_mode(Gt, g, c.force_mode, x, y, z, fx, fy, fz);
         if (c.sigma > 0.f) {
             float nx, ny, nz;
             gauss3(c, m & kTagMask, step, nx, ny, nz);

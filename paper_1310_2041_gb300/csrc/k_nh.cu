@@ -128,7 +128,7 @@ __device__ __forceinline__ double nh_half(const NhConsts& t, double& xi, double&
     return s;
 }
 
-template <bool kExact, bool kAngles>
+template <int kForce, bool kAngles>
 __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ NhParams p) {
     __shared__ double s_ke[kNhBlock / 32];
     __shared__ bool s_last;
@@ -149,11 +149,7 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
             float fx = 0.f, fy = 0.f, fz = 0.f;
             bonded_of<kAngles>(p, d, i, m, x, y, z, fx, fy, fz);
             const float4* Gt = p.G + (size_t)((m >> kTypeShift) & kTypeMask) * p.g.gnodes;
-            const AxisCoord ax = axis_gather(x, p.g.inv_h[0], (float)p.g.mx, p.g.inv_m[0]);
-            const AxisCoord ay = axis_gather(y, p.g.inv_h[1], (float)p.g.my, p.g.inv_m[1]);
-            const AxisCoord az = axis_gather(z, p.g.inv_h[2], (float)p.g.mz, p.g.inv_m[2]);
-            if (kExact) gather_field_exact(Gt, p.g, ax, ay, az, fx, fy, fz);
-            else gather_field(Gt, p.g, ax, ay, az, fx, fy, fz);
+            gather_field_mode(Gt, p.g, kForce, x, y, z, fx, fy, fz);
             p.Fout[0][i] = fx;
             p.Fout[1][i] = fy;
             p.Fout[2][i] = fz;
@@ -221,11 +217,11 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
     p.nh->ticket = 0u;
 }
 
-template <bool kExact>
+template <int kForce>
 void launch_nh_e(const NhParams& p, bool angles, cudaStream_t s) {
     const int blocks = nh_blocks(p.n);
-    if (angles) k_nh_step<kExact, true><<<blocks, kNhBlock, 0, s>>>(p);
-    else k_nh_step<kExact, false><<<blocks, kNhBlock, 0, s>>>(p);
+    if (angles) k_nh_step<kForce, true><<<blocks, kNhBlock, 0, s>>>(p);
+    else k_nh_step<kForce, false><<<blocks, kNhBlock, 0, s>>>(p);
 }
 
 }  // namespace
@@ -240,8 +236,9 @@ int nh_blocks(int n) {
 void launch_nh_step(const NhParams& p, cudaStream_t s) {
     if (p.n <= 0) return;
     const bool angles = p.c.two_ka != 0.f;
-    if (p.c.exact) launch_nh_e<true>(p, angles, s);
-    else launch_nh_e<false>(p, angles, s);
+    if (p.c.force_mode == 2) launch_nh_e<2>(p, angles, s);
+    else if (p.c.force_mode == 1) launch_nh_e<1>(p, angles, s);
+    else launch_nh_e<0>(p, angles, s);
 }
 
 }  // namespace hpf

@@ -29,11 +29,7 @@ __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __r
     }
     if (which & HPF_FORCE_FIELD) {
         const int T = (m >> kTypeShift) & kTypeMask;
-        const AxisCoord ax = axis_gather(x, g.inv_h[0], (float)g.mx, g.inv_m[0]);
-        const AxisCoord ay = axis_gather(y, g.inv_h[1], (float)g.my, g.inv_m[1]);
-        const AxisCoord az = axis_gather(z, g.inv_h[2], (float)g.mz, g.inv_m[2]);
-        if (c.exact) gather_field_exact(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
-        else gather_field(G + (size_t)T * g.gnodes, g, ax, ay, az, fx, fy, fz);
+        gather_field_mode(G + (size_t)T * g.gnodes, g, c.force_mode, x, y, z, fx, fy, fz);
     }
     const uint32_t tag = m & kTagMask;
     F_tag[3 * tag] = fx;
@@ -82,13 +78,21 @@ __device__ __forceinline__ int cell_base(const MeshGeom& g, float flx, float fly
     return (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
 }
 
-// kExact: planes 0 and 1 hold the trilinear polynomial of V instead (the
-// exact-energy-gradient force differentiates it).
-template <bool kExact>
+// kForce 1: planes 0 and 1 hold the trilinear polynomial of V instead (the
+// exact-energy-gradient force differentiates it).  kForce 2: the key is the
+// nearest vertex and planes 0 and 1 hold its six staggered coefficients.
+template <int kForce>
 __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, const MeshGeom& g,
                                                 float flx, float fly, float flz,
                                                 float4* __restrict__ cache, int t,
                                                 int stride = kStepBlock) {
+    if (kForce == 2) {
+        float c[6];
+        stag_vertex_coefs(Gt, g, flx, fly, flz, c);
+        cache[t] = make_float4(c[0], c[1], c[2], c[3]);
+        cache[stride + t] = make_float4(c[4], c[5], 0.f, 0.f);
+        return;
+    }
     const int o00 = cell_base(g, flx, fly, flz);
     const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
     // corner (a, b, c) = offsets (x, y, z) in {0, 1}
@@ -108,7 +112,7 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
         cache[(2 * j) * stride + t] = make_float4(a0, a1, a2, a3);                               \
         cache[(2 * j + 1) * stride + t] = make_float4(a4, a5, a6, a7);                           \
     }
-    if (kExact) {
+    if (kForce == 1) {
         HPF_COEF(w, 0)
     } else {
         HPF_COEF(x, 0)
@@ -116,6 +120,13 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
         HPF_COEF(z, 2)
     }
 #undef HPF_COEF
+}
+
+// The cache key of a mesh coordinate: its cell (floor), or its nearest
+// vertex for the staggered force.
+template <int kForce>
+__device__ __forceinline__ float cache_key(float s) {
+    return kForce == 2 ? stag_vertex(s) : floorf(s);
 }
 
 // -(trilinear polynomial) of the cached cell at offset (fx, fy, fz).
@@ -131,12 +142,16 @@ __device__ __forceinline__ float cell_poly(const float4 lo, const float4 hi, flo
     return fmaf(fz, lo.w, v);
 }
 
-template <bool kExact>
+template <int kForce>
 __device__ __forceinline__ void eval_cell_cache(const float4* __restrict__ cache, int t, float fx,
                                                 float fy, float fz, float& Fx, float& Fy,
                                                 float& Fz, const MeshGeom& g,
                                                 int stride = kStepBlock) {
-    if (kExact) {
+    if (kForce == 2) {
+        const float4 lo = cache[t], hi = cache[stride + t];
+        const float c[6] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y};
+        stag_force(c, fx, fy, fz, g, Fx, Fy, Fz);
+    } else if (kForce == 1) {
         // V = a0 + a1 fx + a2 fy + a3 fz + a4 fx fy + a5 fx fz + a6 fy fz + a7 fx fy fz;
         // F = -(1/h) dV/df per axis
         const float4 lo = cache[t], hi = cache[stride + t];
@@ -167,7 +182,7 @@ __device__ __forceinline__ void neighbour_sync(int w) {
     if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
-template <int kTherm, bool kExact, bool kAngles>
+template <int kTherm, int kForce, bool kAngles>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
                                                         int halo, int n_sub, long long step0,
@@ -215,15 +230,16 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
         neighbour_sync(t >> 5);
         const float s0 = __fmul_rn(x, g.inv_h[0]), s1 = __fmul_rn(y, g.inv_h[1]),
                     s2 = __fmul_rn(z, g.inv_h[2]);
-        const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
+        const float flx = cache_key<kForce>(s0), fly = cache_key<kForce>(s1),
+                    flz = cache_key<kForce>(s2);
         if (flx != cfx || fly != cfy || flz != cfz) {
-            fill_cell_cache<kExact>(Gt, g, flx, fly, flz, cache, t);
+            fill_cell_cache<kForce>(Gt, g, flx, fly, flz, cache, t);
             cfx = flx;
             cfy = fly;
             cfz = flz;
         }
         float fx = -c.fric * vx, fy = -c.fric * vy, fz = -c.fric * vz;
-        eval_cell_cache<kExact>(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly),
+        eval_cell_cache<kForce>(cache, t, __fsub_rn(s0, flx), __fsub_rn(s1, fly),
                                 __fsub_rn(s2, flz), fx, fy, fz, g);
         if (kTherm == 1) {
             float nx, ny, nz;
@@ -311,13 +327,13 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     }
 }
 
-template <int kTherm, bool kExact, bool kAngles>
+template <int kTherm, int kForce, bool kAngles>
 static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_step<kTherm, kExact, kAngles>,
+        cudaFuncSetAttribute(k_step<kTherm, kForce, kAngles>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
         attr_set = true;
     }
@@ -326,19 +342,19 @@ static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n
     const int halo = kAngles ? 2 * n_sub : n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<kTherm, kExact, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
+    k_step<kTherm, kForce, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
         in, out, meta, n, halo, n_sub, step0, g, G, c, D_next, flag);
 }
 
-template <int kTherm, bool kExact>
+template <int kTherm, int kForce>
 static void launch_step_a(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (c.two_ka != 0.f)
-        launch_step_t<kTherm, kExact, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
+        launch_step_t<kTherm, kForce, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
                                             s);
     else
-        launch_step_t<kTherm, kExact, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
+        launch_step_t<kTherm, kForce, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
                                              flag, s);
 }
 
@@ -347,9 +363,13 @@ void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_s
                  unsigned long long* D_next, int* flag, cudaStream_t s) {
     if (n <= 0 || n_sub <= 0) return;
     const int therm = step_thermostat(c);
-#define HPF_HALO(T)                                                                          \
-    if (c.exact) launch_step_a<T, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s); \
-    else launch_step_a<T, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+#define HPF_HALO(T)                                                                        \
+    if (c.force_mode == 2)                                                                   \
+        launch_step_a<T, 2>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);       \
+    else if (c.force_mode == 1)                                                              \
+        launch_step_a<T, 1>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);       \
+    else                                                                                     \
+        launch_step_a<T, 0>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     if (therm == 1) {
         HPF_HALO(1)
     } else if (therm == 2) {
@@ -382,15 +402,16 @@ struct Bead {
 
 // The bead's cell: refill its cache of the cell polynomial when the bead
 // has entered another cell; returns the offsets inside the cell.
-template <bool kExact>
+template <int kForce>
 __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G, const MeshGeom& g,
                                            float4* __restrict__ cache, int slot, float& f0,
                                            float& f1, float& f2) {
     const float s0 = __fmul_rn(b.x, g.inv_h[0]), s1 = __fmul_rn(b.y, g.inv_h[1]),
                 s2 = __fmul_rn(b.z, g.inv_h[2]);
-    const float flx = floorf(s0), fly = floorf(s1), flz = floorf(s2);
+    const float flx = cache_key<kForce>(s0), fly = cache_key<kForce>(s1),
+                flz = cache_key<kForce>(s2);
     if (flx != b.cfx || fly != b.cfy || flz != b.cfz) {
-        fill_cell_cache<kExact>(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx,
+        fill_cell_cache<kForce>(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx,
                                 fly, flz, cache, slot, 2 * kWarpBlock);
         b.cfx = flx;
         b.cfy = fly;
@@ -405,14 +426,14 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
 // noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
 // chain neighbours.  Andersen (kTherm 2): a colliding bead's on-step velocity
 // is sqrt(kT/m) (nx, ny, nz) before the second half kick.
-template <int kTherm, bool kExact>
+template <int kTherm, int kForce>
 __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
                                           float ny, float nz, float bx, float by, float bz,
                                           const StepConsts& c, const MeshGeom& g,
                                           const float4* __restrict__ cache, int slot,
                                           bool coll) {
     float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
-    eval_cell_cache<kExact>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
+    eval_cell_cache<kForce>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
     if (kTherm == 1) {
         fx = fmaf(c.sigma, nx, fx);
         fy = fmaf(c.sigma, ny, fy);
@@ -457,7 +478,7 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <int kTherm, bool kExact, bool kAngles>
+template <int kTherm, int kForce, bool kAngles>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -492,8 +513,8 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
                                     w0y, w0z, w1x, w1y, w1z);
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
-        cell_check<kExact>(b0, G, g, wcache, tid, f00, f01, f02);
-        cell_check<kExact>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
+        cell_check<kForce>(b0, G, g, wcache, tid, f00, f01, f02);
+        cell_check<kForce>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
         float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
         bool coll0 = false, coll1 = false;
         if (kTherm == 1) {
@@ -506,9 +527,9 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
             if (coll0) gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             if (coll1) gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kTherm, kExact>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
+        kick_bead<kTherm, kForce>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
                                   tid, coll0);
-        kick_bead<kTherm, kExact>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
+        kick_bead<kTherm, kForce>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
                                   kWarpBlock + tid, coll1);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
@@ -525,7 +546,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <int kTherm, int kCap, bool kExact, bool kAngles>
+template <int kTherm, int kCap, int kForce, bool kAngles>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
     griddep_wait();
@@ -557,23 +578,26 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
         }
         const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
-        advance_segment<kTherm, kExact, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+        advance_segment<kTherm, kForce, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
                                                  rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
     }
 }
 
+template <int kCap, int kTherm, int kForce>
+static void warp_attrs_f() {
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+}
+
 template <int kCap, int kTherm>
 static void warp_attrs_n() {
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    warp_attrs_f<kCap, kTherm, 0>();
+    warp_attrs_f<kCap, kTherm, 1>();
+    warp_attrs_f<kCap, kTherm, 2>();
 }
 
 template <int kCap>
@@ -592,7 +616,7 @@ static int warp_grid_cap() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, false, false>, kWarpBlock,
+            &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, 0, false>, kWarpBlock,
             kWarpSmem);
         cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
@@ -608,26 +632,28 @@ static void launch_warp_k(void (*k)(const BatchStepParamsT<kCap>), const BatchSt
     else k<<<blocks, kWarpBlock, kWarpSmem, s>>>(p);
 }
 
-template <int kCap, int kTherm>
-static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, bool exact, bool angles,
+template <int kCap, int kTherm, int kForce>
+static void launch_warp_f(const BatchStepParamsT<kCap>& p, int blocks, bool angles,
                           cudaStream_t s) {
-    if (exact && angles)
-        launch_warp_k(k_step_warp_batch<kTherm, kCap, true, true>, p, blocks, s);
-    else if (exact)
-        launch_warp_k(k_step_warp_batch<kTherm, kCap, true, false>, p, blocks, s);
-    else if (angles)
-        launch_warp_k(k_step_warp_batch<kTherm, kCap, false, true>, p, blocks, s);
-    else
-        launch_warp_k(k_step_warp_batch<kTherm, kCap, false, false>, p, blocks, s);
+    if (angles) launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, true>, p, blocks, s);
+    else launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, false>, p, blocks, s);
+}
+
+template <int kCap, int kTherm>
+static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, int force, bool angles,
+                          cudaStream_t s) {
+    if (force == 2) launch_warp_f<kCap, kTherm, 2>(p, blocks, angles, s);
+    else if (force == 1) launch_warp_f<kCap, kTherm, 1>(p, blocks, angles, s);
+    else launch_warp_f<kCap, kTherm, 0>(p, blocks, angles, s);
 }
 
 template <int kCap>
-static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, int therm, bool exact,
+static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, int therm, int force,
                         cudaStream_t s) {
     const bool angles = p.rep[0].c.two_ka != 0.f;  // all replicas alike (checked at init)
-    if (therm == 1) launch_warp_n<kCap, 1>(p, blocks, exact, angles, s);
-    else if (therm == 2) launch_warp_n<kCap, 2>(p, blocks, exact, angles, s);
-    else launch_warp_n<kCap, 0>(p, blocks, exact, angles, s);
+    if (therm == 1) launch_warp_n<kCap, 1>(p, blocks, force, angles, s);
+    else if (therm == 2) launch_warp_n<kCap, 2>(p, blocks, force, angles, s);
+    else launch_warp_n<kCap, 0>(p, blocks, force, angles, s);
 }
 
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,
@@ -636,7 +662,7 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int the
     const int cap = warp_grid_cap();
     const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    launch_warp(p, blocks, therm, p.rep[0].c.exact != 0, s);  // replicas share the force mode
+    launch_warp(p, blocks, therm, p.rep[0].c.force_mode, s);  // replicas share the force mode
 }
 
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm,
@@ -645,7 +671,7 @@ void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm,
     const int cap = warp_grid_cap();
     const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
-    launch_warp(p, blocks, therm, p.rep[0].c.exact != 0, s);
+    launch_warp(p, blocks, therm, p.rep[0].c.force_mode, s);
 }
 
 
