@@ -77,7 +77,11 @@ typedef struct {
     int32_t force_mode;   /* field force: 0 = the trilinear interpolation of the nodal
                              central-difference gradient (Algorithm 1, kernels 3-4);
                              1 = the exact derivative of the CIC field energy (the gradient
-                             of the trilinear interpolant of V; conserves energy) */
+                             of the trilinear interpolant of V; conserves energy);
+                             2 = Algorithm 1, kernels 3-4 read literally: per axis the
+                             backward and forward differences of V at the vertex c nearest
+                             the bead blended by (1/2 - d, 1/2 + d), d = s - c in [-1/2, 1/2)
+                             (s the mesh coordinate), only c's grid line entering */
     double angle_k;       /* angle potential U = angle_k (cos theta - angle_cos0)^2 for every */
     double angle_cos0;    /* bonded triplet (section "Bonded forces", cosine form), theta the
                              angle at the middle bead (pi for a straight chain); 0: none */
