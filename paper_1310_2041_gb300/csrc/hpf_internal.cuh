@@ -16,7 +16,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include "hpf.h"
 
@@ -195,6 +197,15 @@ struct TiledFieldParamsT {
 };
 using TiledFieldParams = TiledFieldParamsT<HPF_MAX_REPLICAS>;
 using SingleFieldParams = TiledFieldParamsT<1>;
+
+// Run `f` once per device (ordinals taken modulo 64) for set-up that CUDA
+// keeps per device, such as kernel attributes; thread-safe.
+template <typename F>
+inline void once_per_device(std::once_flag (&flags)[64], F&& f) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(flags[dev & 63], std::forward<F>(f));
+}
 
 // ------------------------------------------------------------------ dependent launch
 //

@@ -336,12 +336,11 @@ __global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ Tile
 template <int S, int TX, int TY, int TZ, int kCap>
 static void launch_tile(const TiledFieldParamsT<kCap>& p, cudaStream_t s) {
     const size_t smem = sizeof(long long) * (size_t)(TX + 4) * (TY + 2) * (TZ + 2) * S;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr[64];
+    once_per_device(attr, [smem] {
         cudaFuncSetAttribute(k_field_tiled<S, TX, TY, TZ, kCap>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    });
     if (kCap == 1) launch_pdl(k_field_tiled<S, TX, TY, TZ, kCap>, p.blocks, TX * TY, smem, s, p);
     else k_field_tiled<S, TX, TY, TZ, kCap><<<p.blocks, TX * TY, smem, s>>>(p);
 }
@@ -395,9 +394,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 static EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* f = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
@@ -406,7 +404,7 @@ static EncodeTiledFn encode_fn() {
             fn = reinterpret_cast<EncodeTiledFn>(f);
         else
             cudaGetLastError();
-    }
+    });
     return fn;
 }
 

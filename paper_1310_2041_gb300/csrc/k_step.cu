@@ -331,12 +331,11 @@ template <int kTherm, int kForce, bool kAngles>
 static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr[64];
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_step<kTherm, kForce, kAngles>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
-        attr_set = true;
-    }
+    });
     // a bead's update after k sub-steps depends on beads up to k (bonds) or 2k
     // (angles) places away along its chain
     const int halo = kAngles ? 2 * n_sub : n_sub;
@@ -607,20 +606,25 @@ static void warp_attrs() {
     warp_attrs_n<kCap, 2>();
 }
 
+// The persistent grid of the current device (its SM count times the
+// resident CTAs per SM), with the kernels' attributes set on first use.
 static int warp_grid_cap() {
-    static int cap = 0;
-    if (!cap) {
+    static std::once_flag once[64];
+    static int cap[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    once_per_device(once, [dev] {
         warp_attrs<HPF_MAX_REPLICAS>();
         warp_attrs<1>();
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+        int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, 0, false>, kWarpBlock,
             kWarpSmem);
-        cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
-    return cap;
+        cudaGetLastError();
+        cap[dev & 63] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    });
+    return cap[dev & 63];
 }
 
 // A context's launches use dependent launch; a batch's are captured into
