@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ 
             for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
     // voxel (lx, ly0 + 2i, w) for row tile i
     const int lx = r % kTX, ly0 = r / kTX;
-#pragma unroll 1
+#pragma unroll 9
     for (int o = 0; o < kOffsets; ++o) {
         uint32_t b0, b1, b2, b3;
         ldsm_x4(sw_s + 16 * swz(o * kPC + b_n, b_half), b0, b1, b2, b3);
