@@ -168,6 +168,15 @@ hpf_status hpf_scatter_density(hpf_ctx* ctx, int64_t* D_out);
  * Errors: HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_field(hpf_ctx* ctx, const int64_t* D_in, float* field_out);
 
+/* Self-test of the device-side wait bound: one kernel waits on a barrier that
+ * nothing completes, which must give up after its limit (0.2 s), raise the
+ * context's timeout flag and return.  The flag is cleared again, so the
+ * context stays usable; *seconds (may be NULL) is the host-measured time.
+ * Returns HPF_ERR_TIMEOUT when the wait gave up as designed, HPF_OK if it
+ * completed (the bound did not act).  Synchronises.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_CUDA. */
+hpf_status hpf_selftest_timeout(hpf_ctx* ctx, double* seconds);
+
 /* The field stencil runs on shared-memory tiles of the mesh, staged by TMA
  * tensor copies when the mesh allows it (Mx even, n_species <= 4), or untiled
  * (one ghosted node, or two real nodes, per thread).  The kernel is chosen

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -1065,6 +1066,29 @@ hpf_status hpf_nh_conserved(hpf_ctx* c, double* H) {
     nh_pending_half(c, xi, eta, K);
     *H = e[3] + c->nhc.dof_kT * (0.5 * c->p.nh_tau * c->p.nh_tau * xi * xi + eta);
     return HPF_OK;
+}
+
+hpf_status hpf_selftest_timeout(hpf_ctx* c, double* seconds) {
+    if (!c) return HPF_ERR_INVALID;
+    CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int before = c->hflag[0];
+    const auto t0 = std::chrono::steady_clock::now();
+    launch_wait_selftest(c->dflag, c->stream);
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const auto t1 = std::chrono::steady_clock::now();
+    const int after = c->hflag[0];
+    // the flag word as it was: the self-test is its only writer meanwhile
+    c->hflag[0] = before;
+    CUDA_TRY(c, cudaMemcpyAsync(c->dflag, c->hflag, sizeof(int), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (seconds) *seconds = std::chrono::duration<double>(t1 - t0).count();
+    return (after & kFlagTimeout) ? HPF_ERR_TIMEOUT : HPF_OK;
 }
 
 hpf_status hpf_field_tile(const hpf_ctx* c, int32_t shape[3], int32_t* uses_tma) {

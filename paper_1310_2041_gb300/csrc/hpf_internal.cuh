@@ -683,6 +683,7 @@ int field_tile_candidates();
 bool field_tile_is_plain(int id);
 void field_tile_shape(int id, int out[3]);
 void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s);
+void launch_wait_selftest(int* flag, cudaStream_t s);
 void launch_field_tiled(const SingleFieldParams& p, int S, int tile, cudaStream_t s);
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile);

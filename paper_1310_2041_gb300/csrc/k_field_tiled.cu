@@ -26,7 +26,8 @@ constexpr int kTileShapes[kTileCandidates][3] = {
     {32, 8, 4}, {32, 8, 8}, {16, 16, 4}, {64, 4, 4}, {16, 16, 8}, {32, 4, 8}, {0, 0, 0},
     {2, 1, 1}};
 constexpr int kPairTile = 7;
-constexpr unsigned kWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
+constexpr unsigned kWaitLimit = 1u << 22;          // polls of an mbarrier before giving up
+constexpr unsigned long long kWaitNs = 200000000ull;  // or 0.2 s, whichever comes first
 
 int field_tile_candidates() { return kTileCandidates; }
 
@@ -46,8 +47,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Returns false if the barrier did not complete within kWaitLimit polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false if the barrier did not complete within kWaitLimit polls or
+// kWaitNs nanoseconds (a tensor copy completes within microseconds).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitLimit; ++it) {
         uint32_t done;
         asm volatile(
@@ -58,8 +67,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
+}
+
+// Self-test of the bounded wait: an mbarrier nothing ever arrives on (no
+// copy is issued), so the wait must give up, raise the timeout flag and
+// return.
+__global__ void k_wait_selftest(int* flag) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(b, 0)) atomicOr(flag, kFlagTimeout);
 }
 
 // Periodic image of an index that is at most one period outside [0, m) (the
@@ -376,6 +400,8 @@ static void launch_field_tiled_t(const TiledFieldParamsT<kCap>& p, int S, int ti
         default: launch_for_species<4>(p, tile, s); break;
     }
 }
+
+void launch_wait_selftest(int* flag, cudaStream_t s) { k_wait_selftest<<<1, 32, 0, s>>>(flag); }
 
 void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s) {
     launch_field_tiled_t(p, S, tile, s);

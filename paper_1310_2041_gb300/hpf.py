@@ -112,6 +112,8 @@ def load():
         L.hpf_get_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_set_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_nh_conserved.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_selftest_timeout.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.hpf_selftest_timeout.restype = ctypes.c_int
         L.hpf_batch_init.argtypes = [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
         L.hpf_batch_replica.argtypes = [vp, i32]
         L.hpf_batch_replica.restype = vp
@@ -361,6 +363,13 @@ class System:
     def set_thermostat(self, xi, eta):
         arr = (ctypes.c_double * 2)(float(xi), float(eta))
         self._check(self.lib.hpf_set_thermostat(self.h, arr))
+
+    def selftest_timeout(self):
+        """Run the bounded-wait self-test: (status, seconds); status 6
+        (HPF_ERR_TIMEOUT) when the wait gave up as designed."""
+        t = ctypes.c_double()
+        st = self.lib.hpf_selftest_timeout(self.h, ctypes.byref(t))
+        return int(st), t.value
 
     def nh_conserved(self):
         """The extended energy conserved by the Nose-Hoover equations."""

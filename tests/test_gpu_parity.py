@@ -407,3 +407,19 @@ def test_full_size_ternary_blend(hpf_gpu, orc):
     Fo = orc.field_force(op, d["pos"], d["type"], Go) + orc.bond_force(op, d["pos"], d["bonds"])
     ok, worst = force_ok(s.forces(), Fo)
     assert ok, worst
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(hpf_gpu, orc):
+    """Failure detection without a fault: a device wait that nothing completes
+    gives up within its limit, the host reads HPF_ERR_TIMEOUT, and the same
+    context then steps and matches the oracle."""
+    w = W.diblock(60, 4, 6, 9.3, 8, 1.0, name="ragged_600")
+    s, d, pp = make(hpf_gpu, w)
+    status, seconds = s.selftest_timeout()
+    assert status == 6  # HPF_ERR_TIMEOUT
+    assert 0.1 <= seconds < 2.0
+    s.step(10)
+    pos, vel, step = s.get_state()  # no stale timeout reported
+    po, vo, _ = orc.run(oparams(orc, pp), d["pos"], d["vel"], d["type"], d["bonds"], 0, 10)
+    assert step == 10
+    assert np.max(np.abs(pos - po)) <= 1e-4 and np.max(np.abs(vel - vo)) <= 1e-4
