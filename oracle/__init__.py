@@ -20,6 +20,8 @@ with the CUDA library.  Parity status per function:
                  (1 - nu dt)^n, collision rate, mean temperature)
   field_force_staggered  pinned (quadratic fields exact, central difference on
                  a vertex, continuity between vertices, sinusoid closed form)
+  dihedral_force / dihedral_energy  pinned (closed forms in phi, minus the
+                 numerical energy derivative, zero net force and torque)
   run_nh         pinned (NVE limit, free-particle thermostat ODE, extended-energy
                  conservation, mean temperature)
 """
@@ -76,6 +78,9 @@ class Params(ctypes.Structure):
         ("thermostat", ctypes.c_int32),
         ("nh_tau", ctypes.c_double),
         ("andersen_nu", ctypes.c_double),
+        ("dihedral_k", ctypes.c_double),
+        ("dihedral_n", ctypes.c_int32),
+        ("dihedral_delta", ctypes.c_double),
     ]
 
 
@@ -108,6 +113,9 @@ def lib():
             L.orc_angle_force.argtypes = [pp, i64, P(f64), P(i32), P(i32), P(f64)]
             L.orc_angle_energy.argtypes = [pp, i64, P(f64), P(i32), P(i32)]
             L.orc_angle_energy.restype = f64
+            L.orc_dihedral_force.argtypes = [pp, i64, P(f64), P(i32), P(i32), P(f64)]
+            L.orc_dihedral_energy.argtypes = [pp, i64, P(f64), P(i32), P(i32)]
+            L.orc_dihedral_energy.restype = f64
             L.orc_field_energy.argtypes = [pp, P(i64)]
             L.orc_field_energy.restype = f64
             L.orc_field_force_exact.argtypes = [pp, i64, P(f64), P(i32), P(f64), P(f64)]
@@ -130,7 +138,7 @@ def lib():
 def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None, bond_k=4.0,
                 bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1, force_mode=0,
                 angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0, andersen_nu=0.0,
-                **_ignored):
+                dihedral_k=0.0, dihedral_n=1, dihedral_delta=0.0, **_ignored):
     p = Params()
     p.n_species = int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -153,6 +161,8 @@ def make_params(n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
     p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
     p.thermostat, p.nh_tau = int(thermostat), float(nh_tau)
     p.andersen_nu = float(andersen_nu)
+    p.dihedral_k, p.dihedral_n, p.dihedral_delta = (float(dihedral_k), int(dihedral_n),
+                                                    float(dihedral_delta))
     return p
 
 
@@ -294,6 +304,22 @@ def field_force_staggered(p: Params, pos, types, V) -> np.ndarray:
                                     _p(types, ctypes.c_int32), _p(V, ctypes.c_double),
                                     _p(F, ctypes.c_double))
     return F
+
+
+def dihedral_force(p: Params, pos, bonds) -> np.ndarray:
+    pos = _f64(pos, (-1, 3))
+    BL, BN = bond_table(pos.shape[0], bonds)
+    F = np.zeros_like(pos)
+    lib().orc_dihedral_force(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                             _p(BL, ctypes.c_int32), _p(BN, ctypes.c_int32), _p(F, ctypes.c_double))
+    return F
+
+
+def dihedral_energy(p: Params, pos, bonds) -> float:
+    pos = _f64(pos, (-1, 3))
+    BL, BN = bond_table(pos.shape[0], bonds)
+    return lib().orc_dihedral_energy(ctypes.byref(p), pos.shape[0], _p(pos, ctypes.c_double),
+                                     _p(BL, ctypes.c_int32), _p(BN, ctypes.c_int32))
 
 
 def energy(p: Params, pos, vel, types, bonds, V, G, step) -> np.ndarray:

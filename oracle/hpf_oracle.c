@@ -461,6 +461,116 @@ double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const
     return (double)e;
 }
 
+/* The dihedral of the bonded quadruplet (a, j, k, b) and the vectors its
+ * force needs (the convention of the header). */
+typedef struct {
+    double rij[3], rkj[3], rkl[3], m[3], nv[3];
+    double phi;
+} dihedral_geom;
+
+static void cross3(const double x[3], const double y[3], double z[3])
+{
+    z[0] = x[1] * y[2] - x[2] * y[1];
+    z[1] = x[2] * y[0] - x[0] * y[2];
+    z[2] = x[0] * y[1] - x[1] * y[0];
+}
+
+static double dot3(const double x[3], const double y[3])
+{
+    return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+}
+
+static dihedral_geom dihedral_of(const double* pos, int64_t a, int64_t j, int64_t k, int64_t b)
+{
+    dihedral_geom q;
+    for (int d = 0; d < 3; ++d) {
+        q.rij[d] = pos[3 * a + d] - pos[3 * j + d];
+        q.rkj[d] = pos[3 * k + d] - pos[3 * j + d];
+        q.rkl[d] = pos[3 * k + d] - pos[3 * b + d];
+    }
+    cross3(q.rij, q.rkj, q.m);
+    cross3(q.rkj, q.rkl, q.nv);
+    q.phi = atan2(sqrt(dot3(q.rkj, q.rkj)) * dot3(q.rij, q.nv), dot3(q.m, q.nv));
+    return q;
+}
+
+/* Every bonded quadruplet (a, j, k, b) once: the bond j-k with j < k, a
+ * another neighbour of j, b another neighbour of k (b != a).  Returns the
+ * count; *out (malloc'd, 4 indices each) holds them. */
+static int64_t dihedral_list(int64_t n, const int32_t* BL, const int32_t* BN, int64_t** out)
+{
+    int64_t cap = 16, cnt = 0;
+    int64_t* q = (int64_t*)malloc(sizeof(int64_t) * 4 * (size_t)cap);
+    for (int64_t j = 0; j < n; ++j)
+        for (int kj = 0; kj < BN[j]; ++kj) {
+            const int64_t k = BL[(int64_t)kj * n + j];
+            if (k <= j) continue;
+            for (int ka = 0; ka < BN[j]; ++ka) {
+                const int64_t a = BL[(int64_t)ka * n + j];
+                if (a == k) continue;
+                for (int kb = 0; kb < BN[k]; ++kb) {
+                    const int64_t b = BL[(int64_t)kb * n + k];
+                    if (b == j || b == a) continue;
+                    if (cnt == cap) {
+                        cap *= 2;
+                        q = (int64_t*)realloc(q, sizeof(int64_t) * 4 * (size_t)cap);
+                    }
+                    q[4 * cnt] = a;
+                    q[4 * cnt + 1] = j;
+                    q[4 * cnt + 2] = k;
+                    q[4 * cnt + 3] = b;
+                    ++cnt;
+                }
+            }
+        }
+    *out = q;
+    return cnt;
+}
+
+void orc_dihedral_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                        const int32_t* BN, double* F)
+{
+    for (int64_t i = 0; i < 3 * n; ++i) F[i] = 0.0;
+    if (p->dihedral_k == 0.0) return;
+    int64_t* q4 = NULL;
+    const int64_t cnt = dihedral_list(n, BL, BN, &q4);
+    for (int64_t t = 0; t < cnt; ++t) {
+        const int64_t a = q4[4 * t], j = q4[4 * t + 1], k = q4[4 * t + 2], b = q4[4 * t + 3];
+        const dihedral_geom q = dihedral_of(pos, a, j, k, b);
+        /* dU/dphi */
+        const double g = -p->dihedral_k * p->dihedral_n *
+                         sin(p->dihedral_n * q.phi - p->dihedral_delta);
+        const double rkj2 = dot3(q.rkj, q.rkj), rkj = sqrt(rkj2);
+        const double mm = dot3(q.m, q.m), nn = dot3(q.nv, q.nv);
+        const double pa = dot3(q.rij, q.rkj) / rkj2, pb = dot3(q.rkl, q.rkj) / rkj2;
+        for (int d = 0; d < 3; ++d) {
+            const double fa = -g * rkj / mm * q.m[d];
+            const double fb = g * rkj / nn * q.nv[d];
+            F[3 * a + d] += fa;
+            F[3 * b + d] += fb;
+            F[3 * j + d] += -fa + pa * fa - pb * fb;
+            F[3 * k + d] += -fb - pa * fa + pb * fb;
+        }
+    }
+    free(q4);
+}
+
+double orc_dihedral_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                           const int32_t* BN)
+{
+    if (p->dihedral_k == 0.0) return 0.0;
+    int64_t* q4 = NULL;
+    const int64_t cnt = dihedral_list(n, BL, BN, &q4);
+    long double e = 0.0L;
+    for (int64_t t = 0; t < cnt; ++t) {
+        const dihedral_geom q = dihedral_of(pos, q4[4 * t], q4[4 * t + 1], q4[4 * t + 2],
+                                            q4[4 * t + 3]);
+        e += (long double)(p->dihedral_k * (1.0 + cos(p->dihedral_n * q.phi - p->dihedral_delta)));
+    }
+    free(q4);
+    return (double)e;
+}
+
 double orc_bond_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
                        const int32_t* BN)
 {
@@ -561,10 +671,16 @@ static void conservative_force(const orc_params* p, int64_t n, const double* pos
     else
         orc_field_force(p, n, pos, type, G, Ff);
     orc_bond_force(p, n, pos, BL, BN, Fb);
-    if (p->angle_k != 0.0) {
+    if (p->angle_k != 0.0 || p->dihedral_k != 0.0) {
         double* Fa = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-        orc_angle_force(p, n, pos, BL, BN, Fa);
-        for (int64_t i = 0; i < 3 * n; ++i) Fb[i] += Fa[i];
+        if (p->angle_k != 0.0) {
+            orc_angle_force(p, n, pos, BL, BN, Fa);
+            for (int64_t i = 0; i < 3 * n; ++i) Fb[i] += Fa[i];
+        }
+        if (p->dihedral_k != 0.0) {
+            orc_dihedral_force(p, n, pos, BL, BN, Fa);
+            for (int64_t i = 0; i < 3 * n; ++i) Fb[i] += Fa[i];
+        }
         free(Fa);
     }
     for (int64_t i = 0; i < 3 * n; ++i) Fc[i] = Ff[i] + Fb[i];
@@ -594,8 +710,9 @@ void orc_energy(const orc_params* p, int64_t n, const double* pos, const double*
     }
     orc_scatter(p, n, pos, type, D);
     double w = orc_field_energy(p, D);
-    /* the bonded entry: bonds and angles */
-    double ub = orc_bond_energy(p, n, pos, BL, BN) + orc_angle_energy(p, n, pos, BL, BN);
+    /* the bonded entry: bonds, angles and dihedrals */
+    double ub = orc_bond_energy(p, n, pos, BL, BN) + orc_angle_energy(p, n, pos, BL, BN) +
+                orc_dihedral_energy(p, n, pos, BL, BN);
     out[0] = (double)ke;
     out[1] = ub;
     out[2] = w;
@@ -742,7 +859,9 @@ int orc_run_nh(const orc_params* p, int64_t n, double* pos, double* vel, const i
                 for (int a = 0; a < 3; ++a) mom[a] += (long double)(p->mass * s1 * vE[3 * i + a]);
             orc_scatter(p, n, pos, type, D);
             const double w = orc_field_energy(p, D);
-            const double ub = orc_bond_energy(p, n, pos, BL, BN) + orc_angle_energy(p, n, pos, BL, BN);
+            const double ub = orc_bond_energy(p, n, pos, BL, BN) +
+                              orc_angle_energy(p, n, pos, BL, BN) +
+                              orc_dihedral_energy(p, n, pos, BL, BN);
             e[0] = K;
             e[1] = ub;
             e[2] = w;

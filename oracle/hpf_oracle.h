@@ -59,6 +59,9 @@ typedef struct {
                            (named there too; orc_run) */
     double nh_tau;      /* Nose-Hoover relaxation time tau (> 0) */
     double andersen_nu; /* Andersen collision frequency nu (>= 0) */
+    double dihedral_k;  /* U = dihedral_k [1 + cos(dihedral_n phi - dihedral_delta)] per */
+    int32_t dihedral_n; /* bonded quadruplet (section "Bonded forces"); 0: none */
+    double dihedral_delta;
 } orc_params;
 
 int orc_num_threads(void);
@@ -96,6 +99,16 @@ double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const
 /* Build the BL / BN bond table from a list of bonded pairs; returns 0 or -1 on overflow. */
 void orc_field_force_staggered(const orc_params* p, int64_t n, const double* pos,
                                const int32_t* type, const double* V, double* F);
+/* Dihedrals (orc_dihedral_force / orc_dihedral_energy): every bonded
+ * quadruplet (a, j, k, b), phi the angle between the planes (a, j, k) and
+ * (j, k, b): with r_ij = x_a - x_j, r_kj = x_k - x_j, r_kl = x_k - x_b,
+ * m = r_ij x r_kj, n = r_kj x r_kl, phi = atan2(|r_kj| (r_ij . n), m . n)
+ * (trans +-pi, cis 0).  Parity: pinned (closed forms in phi, minus the
+ * numerical energy derivative, zero net force and torque). */
+void orc_dihedral_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                        const int32_t* BN, double* F);
+double orc_dihedral_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
+                           const int32_t* BN);
 int orc_bond_table(int64_t n, int64_t n_bonds, const int32_t* pairs, int32_t* BL, int32_t* BN);
 /* Harmonic bond force per bead, each bond evaluated from both ends. */
 void orc_bond_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,

@@ -181,3 +181,40 @@ def generate(w: Workload, seed: int | None = None) -> dict:
              else np.zeros((0, 2), dtype=np.int32))
     return dict(pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel.astype(np.float32)),
                 type=types, bonds=np.ascontiguousarray(bonds))
+
+
+def with_bond_angles(w: Workload, data: dict, theta_deg=(100.0, 140.0), seed: int = 0) -> dict:
+    """The same melt with every chain rebuilt bead by bead from its first
+    bead: bond length walk_step, each bond angle drawn uniformly in
+    theta_deg (degrees) and each torsion uniformly, so no three consecutive
+    beads start near collinear (where a dihedral is undefined).  Types,
+    bonds and velocities are kept."""
+    rng = np.random.Generator(np.random.Philox(key=seed + 7))
+    pos = data["pos"].astype(np.float64).copy()
+    b = w.walk_step
+    base = 0
+    for n_chains, seq in w.blocks:
+        clen = len(seq)
+        for c in range(n_chains):
+            s = base + c * clen
+            if clen < 2:
+                continue
+            v = _unit_vectors(rng, (1,))[0]
+            pos[s + 1] = pos[s] + b * v
+            u = _unit_vectors(rng, (1,))[0]
+            u -= np.dot(u, v) * v
+            u /= np.linalg.norm(u)
+            for k in range(2, clen):
+                th = np.radians(rng.uniform(*theta_deg))
+                ph = rng.uniform(-np.pi, np.pi)
+                t = (pos[s + k - 1] - pos[s + k - 2]) / b
+                n1 = np.cross(t, u)
+                n1 /= np.linalg.norm(n1)
+                m1 = np.cross(n1, t)
+                d = -np.cos(th) * t + np.sin(th) * (np.cos(ph) * m1 + np.sin(ph) * n1)
+                pos[s + k] = pos[s + k - 1] + b * d
+                u = t
+        base += n_chains * clen
+    out = dict(data)
+    out["pos"] = np.ascontiguousarray(pos.astype(np.float32))
+    return out
