@@ -90,6 +90,13 @@ typedef struct {
                              (andersen_nu, seed; gamma unused), see hpf_step */
     double nh_tau;        /* Nose-Hoover relaxation time tau (> 0 when thermostat == 1) */
     double andersen_nu;   /* Andersen collision frequency nu (>= 0 when thermostat == 2) */
+    double dihedral_k;    /* dihedral potential U = dihedral_k [1 + cos(n phi - dihedral_delta)]
+                             for every run of three consecutive bonds i-j, j-k, k-l along a
+                             chain (section "Bonded forces"); phi the angle between the planes
+                             (i, j, k) and (j, k, l), signed by the right-hand rule about j -> k,
+                             pi for trans and 0 for cis; 0: none */
+    int32_t dihedral_n;   /* multiplicity n, 1 .. 6 (checked only when dihedral_k != 0) */
+    double dihedral_delta; /* phase delta in radians */
 } hpf_params;
 
 /* Text for a status code (static storage). */
@@ -302,7 +309,8 @@ hpf_status hpf_profile_read(hpf_ctx* ctx, double ms[HPF_STAGE_COUNT],
  * hpf_batch_step fall back to stepping the replicas one after another.
  * Requirements checked by hpf_batch_init (HPF_ERR_INVALID): 1 <= n_replicas
  * <= HPF_MAX_REPLICAS, equal n_species, field_every, sort_every and force_mode,
- * and angles in all replicas or in none (their constants may differ): the
+ * angles in all replicas or in none, and dihedrals in all or in none (their
+ * constants may differ), and one thermostat, Langevin or Andersen, for all: the
  * batch runs one kernel form for all, and each replica's result is then the
  * bits of its own context. */
 #define HPF_MAX_REPLICAS 64

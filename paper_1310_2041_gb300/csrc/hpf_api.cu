@@ -198,6 +198,9 @@ hpf_status validate_params(const hpf_params* p) {
     if (p->force_mode < 0 || p->force_mode > 2) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
         return HPF_ERR_INVALID;
+    if (!isfinite(p->dihedral_k) || !isfinite(p->dihedral_delta) ||
+        (p->dihedral_k != 0.0 && (p->dihedral_n < 1 || p->dihedral_n > 6)))
+        return HPF_ERR_INVALID;
     if (p->thermostat < 0 || p->thermostat > 2) return HPF_ERR_INVALID;
     if (p->thermostat == 2 && !(p->andersen_nu >= 0.0 && isfinite(p->andersen_nu)))
         return HPF_ERR_INVALID;
@@ -255,6 +258,10 @@ void derive_constants(hpf_ctx* c) {
     s.cos0 = (float)p.angle_cos0;
     s.p_coll = p.thermostat == 2 ? (float)(p.andersen_nu * p.dt) : 0.0f;
     s.sig_v = (float)sqrt(p.kT / p.mass);
+    s.kd = (float)p.dihedral_k;
+    s.nd = p.dihedral_k != 0.0 ? p.dihedral_n : 1;
+    s.cd = (float)cos(p.dihedral_delta);
+    s.sd = (float)sin(p.dihedral_delta);
     EnergyConsts& e = c->ec;
     memset(&e, 0, sizeof e);
     e.half_dt_m = 0.5 * p.dt / p.mass;
@@ -264,6 +271,10 @@ void derive_constants(hpf_ctx* c) {
     e.kT = p.kT;
     e.angle_k = p.angle_k;
     e.cos0 = p.angle_cos0;
+    e.dih_k = p.dihedral_k;
+    e.dih_n = p.dihedral_k != 0.0 ? p.dihedral_n : 1;
+    e.dih_cd = cos(p.dihedral_delta);
+    e.dih_sd = sin(p.dihedral_delta);
     e.inv_kappa = p.inv_kappa;
     e.phi_c = phi_c;
     e.w_scale = p.rho0 * vol;
@@ -1332,7 +1343,8 @@ hpf_status hpf_batch_init(const hpf_params* params, int32_t n_replicas, void* st
             params[r].field_every != params[0].field_every ||
             params[r].sort_every != params[0].sort_every ||
             params[r].force_mode != params[0].force_mode ||
-            (params[r].angle_k != 0.0) != (params[0].angle_k != 0.0))
+            (params[r].angle_k != 0.0) != (params[0].angle_k != 0.0) ||
+            (params[r].dihedral_k != 0.0) != (params[0].dihedral_k != 0.0))
             return HPF_ERR_INVALID;
     for (int r = 0; r < n_replicas; ++r)
         if (params[r].thermostat == 1 || params[r].thermostat != params[0].thermostat)

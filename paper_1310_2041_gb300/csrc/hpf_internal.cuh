@@ -62,7 +62,16 @@ struct StepConsts {
     float cos0;                 // cos of the equilibrium angle
     float p_coll;               // Andersen collision probability per step fl32(nu dt) (0: none)
     float sig_v;                // sqrt(kT / m): the Maxwell velocity scale
+    float kd;                   // dihedral_k (0: no dihedral terms)
+    int nd;                     // dihedral multiplicity n
+    float cd, sd;               // cos and sin of the dihedral phase delta
 };
+
+// Bonded terms the step kernels evaluate: 0 bonds, 1 bonds and angles,
+// 2 bonds, angles and dihedrals (angle_k may be 0 there).
+inline int bonded_level(const StepConsts& c) {
+    return c.kd != 0.f ? 2 : (c.two_ka != 0.f ? 1 : 0);
+}
 
 // Thermostat of the step kernels: 0 none (NVE), 1 Langevin noise, 2 Andersen.
 inline int step_thermostat(const StepConsts& c) {
@@ -94,6 +103,9 @@ struct EnergyConsts {
     int S;
     int n;
     double angle_k, cos0;  // angle potential
+    double dih_k;          // dihedral potential k [1 + cos(n phi - delta)]
+    int dih_n;
+    double dih_cd, dih_sd; // cos delta, sin delta
 };
 
 struct StateBuf {
@@ -577,11 +589,106 @@ __device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32
     }
 }
 
+__device__ __forceinline__ float3 f3_sub(float3 a, float3 b) {
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 f3_cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float f3_dot(float3 a, float3 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+
+// Dihedral U = k [1 + cos(n phi - delta)] of the bonded quadruplet 0-1-2-3
+// from its bond vectors b1 = x1 - x0, b2 = x2 - x1, b3 = x3 - x2.  With
+// A = b1 x b2 and B = b2 x b3: cos phi = A.B / (|A||B|), sin phi =
+// |b2| b1.B / (|A||B|) (trans pi, cis 0), and cos(n phi), sin(n phi) are the
+// n-th power of cos phi + i sin phi, so no angle is formed.  With
+// g = dU/dphi = -k n sin(n phi - delta) the end beads take F0 = g |b2| A / |A|^2
+// and F3 = -g |b2| B / |B|^2, the middle ones F1 = S - F0 and F2 = -(F3 + S),
+// S = pa F0 - pb F3, pa = -b1.b2 / |b2|^2, pb = -b3.b2 / |b2|^2 (no net force
+// or torque).  Squared norms are clamped, so for any finite vectors every
+// intermediate stays finite (|cos phi|, |sin phi| <= 1 up to rounding) and a
+// masked quadruplet (kd = 0) gives exactly zero.
+__device__ __forceinline__ void dihedral_force(float3 b1, float3 b2, float3 b3, float kd,
+                                               const StepConsts& c, float3& f0, float3& f1,
+                                               float3& f2, float3& f3) {
+    const float3 A = f3_cross(b1, b2), B = f3_cross(b2, b3);
+    const float AA = fmaxf(f3_dot(A, A), 1e-30f), BB = fmaxf(f3_dot(B, B), 1e-30f);
+    const float b22 = fmaxf(f3_dot(b2, b2), 1e-30f);
+    const float ib = rsqrtf(b22);
+    const float L = b22 * ib;  // |b2|
+    const float inv = rsqrtf(AA) * rsqrtf(BB);
+    const float cp = f3_dot(A, B) * inv, sp = L * f3_dot(b1, B) * inv;
+    float cn = cp, sn = sp;
+    for (int k = 1; k < c.nd; ++k) {
+        const float t = fmaf(cn, cp, -sn * sp);
+        sn = fmaf(sn, cp, cn * sp);
+        cn = t;
+    }
+    const float g = -kd * (float)c.nd * fmaf(sn, c.cd, -cn * c.sd);
+    const float a0 = g * L / AA, a3 = -g * L / BB;
+    f0 = make_float3(a0 * A.x, a0 * A.y, a0 * A.z);
+    f3 = make_float3(a3 * B.x, a3 * B.y, a3 * B.z);
+    const float ib2 = ib * ib;
+    const float pa = -f3_dot(b1, b2) * ib2, pb = -f3_dot(b3, b2) * ib2;
+    const float3 S = make_float3(fmaf(pa, f0.x, -pb * f3.x), fmaf(pa, f0.y, -pb * f3.y),
+                                 fmaf(pa, f0.z, -pb * f3.z));
+    f1 = f3_sub(S, f0);
+    f2 = make_float3(-(f3.x + S.x), -(f3.y + S.y), -(f3.z + S.z));
+}
+
+// How many consecutive bonds lead from bead i backwards (back) and forwards
+// (fwd) along its chain, each capped at 3; chains are contiguous in storage.
+__device__ __forceinline__ void chain_reach(const uint32_t* __restrict__ meta, int i, uint32_t m,
+                                            int& back, int& fwd) {
+    back = 0;
+    fwd = 0;
+    if (m & kBondPrev) {
+        back = 1;
+        if (meta[i - 1] & kBondPrev) {
+            back = 2;
+            if (meta[i - 2] & kBondPrev) back = 3;
+        }
+    }
+    if (m & kBondNext) {
+        fwd = 1;
+        if (meta[i + 1] & kBondNext) {
+            fwd = 2;
+            if (meta[i + 2] & kBondNext) fwd = 3;
+        }
+    }
+}
+
+// Dihedral forces on one bead from the (up to four) quadruplets it belongs
+// to, which start 3, 2, 1 and 0 beads before it; back / fwd as chain_reach,
+// pos(d) the position of the bead d places along the chain (-back <= d <= fwd).
+template <class Pos>
+__device__ __forceinline__ void dihedral_forces_of(Pos pos, int back, int fwd, const StepConsts& c,
+                                                   float& fx, float& fy, float& fz) {
+    float3 P[7];
+#pragma unroll
+    for (int d = -3; d <= 3; ++d)
+        P[d + 3] = (d >= -back && d <= fwd) ? pos(d) : make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // the quadruplet starting q beads back: this bead is its q-th
+        if (back >= q && fwd >= 3 - q) {
+            float3 f[4];
+            dihedral_force(f3_sub(P[4 - q], P[3 - q]), f3_sub(P[5 - q], P[4 - q]),
+                           f3_sub(P[6 - q], P[5 - q]), c.kd, c, f[0], f[1], f[2], f[3]);
+            fx += f[q].x;
+            fy += f[q].y;
+            fz += f[q].z;
+        }
+    }
+}
+
 // Bonded forces of one warp segment of whole chains: lane l holds beads 2l
 // and 2l + 1 at (x0, y0, z0) and (x1, y1, z1); p0, n0: bead 2l is bonded to
 // its previous / next bead, n1: bead 2l + 1 to its next.  Returns the summed
-// bond (and, with kAngles, angle) forces on the lane's two beads.
-template <bool kAngles>
+// bond forces on the lane's two beads, with kBonded >= 1 the angle forces
+// and with kBonded == 2 the dihedral forces.
+template <int kBonded>
 __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0, float x1, float y1,
                                                    float z1, bool p0, bool n0, bool n1,
                                                    const StepConsts& c, int lane, float& w0x,
@@ -604,7 +711,7 @@ __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0,
     // (ends 2l - 1, 2l + 1) and at bead 2l + 1 (ends 2l, 2l + 2); the shares
     // of the end beads held by the neighbouring lanes go there by one shuffle
     float q0x = 0.f, q0y = 0.f, q0z = 0.f, q1x = 0.f, q1y = 0.f, q1z = 0.f;
-    if (kAngles) {
+    if (kBonded >= 1) {
         const float px = __shfl_up_sync(0xffffffffu, x1, 1);  // bead 2l - 1
         const float py = __shfl_up_sync(0xffffffffu, y1, 1);
         const float pz = __shfl_up_sync(0xffffffffu, z1, 1);
@@ -634,6 +741,46 @@ __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0,
     w1x = (nx - ax) + q1x;
     w1y = (ny - ay) + q1y;
     w1z = (nz - az) + q1z;
+    if (kBonded == 2) {
+        // dihedrals, each evaluated once by the lane of its first bead: Q0 =
+        // (2l .. 2l + 3) and Q1 = (2l + 1 .. 2l + 4).  Their shares on beads
+        // 2l + 2 and 2l + 3 go up one lane, Q1's share on bead 2l + 4 two
+        // lanes.  The last bead of a segment has no next bond, so no valid
+        // quadruplet reaches past lane 31.
+        const float3 r0 = make_float3(x0, y0, z0), r1 = make_float3(x1, y1, z1);
+        const float3 r2 = make_float3(dx, dy, dz);  // bead 2l + 2
+        const float3 r3 = make_float3(__shfl_down_sync(0xffffffffu, x1, 1),
+                                      __shfl_down_sync(0xffffffffu, y1, 1),
+                                      __shfl_down_sync(0xffffffffu, z1, 1));
+        const float3 r4 = make_float3(__shfl_down_sync(0xffffffffu, x0, 2),
+                                      __shfl_down_sync(0xffffffffu, y0, 2),
+                                      __shfl_down_sync(0xffffffffu, z0, 2));
+        const bool n2 = __shfl_down_sync(0xffffffffu, (int)n0, 1) != 0;  // bond 2l+2 -> 2l+3
+        const bool n3 = __shfl_down_sync(0xffffffffu, (int)n1, 1) != 0;  // bond 2l+3 -> 2l+4
+        const float3 b01 = f3_sub(r1, r0), b12 = f3_sub(r2, r1), b23 = f3_sub(r3, r2),
+                     b34 = f3_sub(r4, r3);
+        float3 e0, e1, e2, e3, h1, h2, h3, h4;
+        dihedral_force(b01, b12, b23, (n0 && n1 && n2) ? c.kd : 0.0f, c, e0, e1, e2, e3);
+        dihedral_force(b12, b23, b34, (n1 && n2 && n3) ? c.kd : 0.0f, c, h1, h2, h3, h4);
+        const float u0x = e2.x + h2.x, u0y = e2.y + h2.y, u0z = e2.z + h2.z;  // to lane l+1, bead 0
+        const float u1x = e3.x + h3.x, u1y = e3.y + h3.y, u1z = e3.z + h3.z;  // to lane l+1, bead 1
+        const float v0x = __shfl_up_sync(0xffffffffu, u0x, 1);
+        const float v0y = __shfl_up_sync(0xffffffffu, u0y, 1);
+        const float v0z = __shfl_up_sync(0xffffffffu, u0z, 1);
+        const float v1x = __shfl_up_sync(0xffffffffu, u1x, 1);
+        const float v1y = __shfl_up_sync(0xffffffffu, u1y, 1);
+        const float v1z = __shfl_up_sync(0xffffffffu, u1z, 1);
+        const float v2x = __shfl_up_sync(0xffffffffu, h4.x, 2);
+        const float v2y = __shfl_up_sync(0xffffffffu, h4.y, 2);
+        const float v2z = __shfl_up_sync(0xffffffffu, h4.z, 2);
+        const bool up1 = lane >= 1, up2 = lane >= 2;
+        w0x += e0.x + (up1 ? v0x : 0.f) + (up2 ? v2x : 0.f);
+        w0y += e0.y + (up1 ? v0y : 0.f) + (up2 ? v2y : 0.f);
+        w0z += e0.z + (up1 ? v0z : 0.f) + (up2 ? v2z : 0.f);
+        w1x += (e1.x + h1.x) + (up1 ? v1x : 0.f);
+        w1y += (e1.y + h1.y) + (up1 ? v1y : 0.f);
+        w1z += (e1.z + h1.z) + (up1 ? v1z : 0.f);
+    }
 }
 
 // ------------------------------------------------------------------ launchers

@@ -31,6 +31,41 @@ __device__ __forceinline__ double norm_fp64(double r2) {
     return r2 * y;
 }
 
+// Dihedral energy k [1 + cos(n phi - delta)] of the quadruplet i .. i + 3 in
+// FP64 from the FP32 positions: cos phi = A.B / (|A||B|), sin phi =
+// |b2| b1.B / (|A||B|) with A = b1 x b2, B = b2 x b3, and cos(n phi),
+// sin(n phi) by the n-th power of cos phi + i sin phi.
+__device__ __forceinline__ double dihedral_energy_fp64(const StateBuf& st, int i,
+                                                       const EnergyConsts& e) {
+    double b[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        b[k][0] = (double)st.x[i + k + 1] - st.x[i + k];
+        b[k][1] = (double)st.y[i + k + 1] - st.y[i + k];
+        b[k][2] = (double)st.z[i + k + 1] - st.z[i + k];
+    }
+    double A[3], B[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int u = (a + 1) % 3, v = (a + 2) % 3;
+        A[a] = b[0][u] * b[1][v] - b[0][v] * b[1][u];
+        B[a] = b[1][u] * b[2][v] - b[1][v] * b[2][u];
+    }
+    const double AA = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+    const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double L = norm_fp64(b[1][0] * b[1][0] + b[1][1] * b[1][1] + b[1][2] * b[1][2]);
+    const double den = norm_fp64(AA) * norm_fp64(BB);
+    const double cp = (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) / den;
+    const double sp = L * (b[0][0] * B[0] + b[0][1] * B[1] + b[0][2] * B[2]) / den;
+    double cn = cp, sn = sp;
+    for (int k = 1; k < e.dih_n; ++k) {
+        const double t = cn * cp - sn * sp;
+        sn = sn * cp + cn * sp;
+        cn = t;
+    }
+    return e.dih_k * (1.0 + cn * e.dih_cd + sn * e.dih_sd);
+}
+
 // Per bead: F_n exactly as the step kernel forms it, the on-step velocity
 // v_n = v + dt/(2m) F_n, then kinetic energy, momentum and the bond energy of
 // the bond to the next bead (each bond once).  The bond and angle energies
@@ -74,6 +109,14 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                 const double cth = (ux * wx + uy * wy + uz * wz) / norm_fp64(uu * ww);
                 ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
             }
+        }
+        if (c.kd != 0.f) {
+            int back, fwd;
+            chain_reach(meta, i, m, back, fwd);
+            dihedral_forces_of(
+                [&](int d) { return make_float3(st.x[i + d], st.y[i + d], st.z[i + d]); }, back,
+                fwd, c, fx, fy, fz);
+            if (fwd == 3) ub += dihedral_energy_fp64(st, i, e);  // the one starting here, once
         }
         const float4* Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
         gather_field_mode(Gt, g, c.force_mode, x, y, z, fx, fy, fz);

@@ -22,7 +22,8 @@
 // order is the same on every GPU) whose threads loop over the beads; the
 // state and the stored force are read from one buffer and written to the
 // other.  A bead's bonded force after the drift
-// needs its chain neighbours' new positions (two beads each way with angles);
+// needs its chain neighbours' new positions (two beads each way with angles,
+// three with dihedrals);
 // each thread recomputes those drifts from the neighbours' old state with the
 // same arithmetic as the neighbours' own threads, so no grid synchronisation
 // is needed and every bit agrees.  Any chain length works.
@@ -66,9 +67,10 @@ __device__ __forceinline__ void moved_pos(const NhParams& p, const Drift& d, int
     moved(p, d, j, x, y, z, vx, vy, vz);
 }
 
-// Bonded force on bead i at (x, y, z): its bonds, and with kAngles the three
-// angles it belongs to (centred at i - 1, i and i + 1).
-template <bool kAngles>
+// Bonded force on bead i at (x, y, z): its bonds, with kBonded >= 1 the three
+// angles it belongs to (centred at i - 1, i and i + 1) and with kBonded == 2
+// the four dihedrals (starting at i - 3 .. i).
+template <int kBonded>
 __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int i, uint32_t m,
                                           float x, float y, float z, float& fx, float& fy,
                                           float& fz) {
@@ -82,7 +84,7 @@ __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int
         moved_pos(p, d, i + 1, xn, yn, zn);
         bond_force(x - xn, y - yn, z - zn, p.c.two_k, p.c.r0, fx, fy, fz);
     }
-    if (!kAngles) return;
+    if (kBonded == 0) return;
     float ax, ay, az, bx, by, bz;
     if (hp && hn) {
         angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z, p.c.two_ka, p.c.cos0, ax, ay,
@@ -109,6 +111,17 @@ __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int
         fy += ay;
         fz += az;
     }
+    if (kBonded == 2) {
+        int back, fwd;
+        chain_reach(p.meta, i, m, back, fwd);
+        dihedral_forces_of(
+            [&](int dd) {
+                float3 r = make_float3(x, y, z);
+                if (dd != 0) moved_pos(p, d, i + dd, r.x, r.y, r.z);
+                return r;
+            },
+            back, fwd, p.c, fx, fy, fz);
+    }
 }
 
 __device__ __forceinline__ double nh_rate(const NhConsts& t, double K) {
@@ -128,7 +141,7 @@ __device__ __forceinline__ double nh_half(const NhConsts& t, double& xi, double&
     return s;
 }
 
-template <int kForce, bool kAngles>
+template <int kForce, int kBonded>
 __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ NhParams p) {
     __shared__ double s_ke[kNhBlock / 32];
     __shared__ bool s_last;
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
         moved(p, d, i, x, y, z, vx, vy, vz);
         if (p.force_kick) {
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            bonded_of<kAngles>(p, d, i, m, x, y, z, fx, fy, fz);
+            bonded_of<kBonded>(p, d, i, m, x, y, z, fx, fy, fz);
             const float4* Gt = p.G + (size_t)((m >> kTypeShift) & kTypeMask) * p.g.gnodes;
             gather_field_mode(Gt, p.g, kForce, x, y, z, fx, fy, fz);
             p.Fout[0][i] = fx;
@@ -218,10 +231,11 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
 }
 
 template <int kForce>
-void launch_nh_e(const NhParams& p, bool angles, cudaStream_t s) {
+void launch_nh_e(const NhParams& p, int bonded, cudaStream_t s) {
     const int blocks = nh_blocks(p.n);
-    if (angles) k_nh_step<kForce, true><<<blocks, kNhBlock, 0, s>>>(p);
-    else k_nh_step<kForce, false><<<blocks, kNhBlock, 0, s>>>(p);
+    if (bonded == 2) k_nh_step<kForce, 2><<<blocks, kNhBlock, 0, s>>>(p);
+    else if (bonded == 1) k_nh_step<kForce, 1><<<blocks, kNhBlock, 0, s>>>(p);
+    else k_nh_step<kForce, 0><<<blocks, kNhBlock, 0, s>>>(p);
 }
 
 }  // namespace
@@ -235,10 +249,10 @@ int nh_blocks(int n) {
 
 void launch_nh_step(const NhParams& p, cudaStream_t s) {
     if (p.n <= 0) return;
-    const bool angles = p.c.two_ka != 0.f;
-    if (p.c.force_mode == 2) launch_nh_e<2>(p, angles, s);
-    else if (p.c.force_mode == 1) launch_nh_e<1>(p, angles, s);
-    else launch_nh_e<0>(p, angles, s);
+    const int bonded = bonded_level(p.c);
+    if (p.c.force_mode == 2) launch_nh_e<2>(p, bonded, s);
+    else if (p.c.force_mode == 1) launch_nh_e<1>(p, bonded, s);
+    else launch_nh_e<0>(p, bonded, s);
 }
 
 }  // namespace hpf

@@ -26,6 +26,12 @@ __global__ void __launch_bounds__(256) k_forces(StateBuf st, const uint32_t* __r
         if (m & kBondNext)
             bond_force(x - st.x[i + 1], y - st.y[i + 1], z - st.z[i + 1], c.two_k, c.r0, fx, fy, fz);
         if (c.two_ka != 0.f) angle_forces_of(st, meta, i, m, c, fx, fy, fz);
+        if (c.kd != 0.f) {
+            int back, fwd;
+            chain_reach(meta, i, m, back, fwd);
+            dihedral_forces_of([&](int d) { return make_float3(st.x[i + d], st.y[i + d], st.z[i + d]); },
+                               back, fwd, c, fx, fy, fz);
+        }
     }
     if (which & HPF_FORCE_FIELD) {
         const int T = (m >> kTypeShift) & kTypeMask;
@@ -182,7 +188,7 @@ __device__ __forceinline__ void neighbour_sync(int w) {
     if (w + 1 < kWarps) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
 }
 
-template <int kTherm, int kForce, bool kAngles>
+template <int kTherm, int kForce, int kBonded>
 __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf out,
                                                         const uint32_t* __restrict__ meta, int n,
                                                         int halo, int n_sub, long long step0,
@@ -214,10 +220,28 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     const bool has_prev = live && (m & kBondPrev) && t > 0;
     const bool has_next = live && (m & kBondNext) && t + 1 < kStepBlock;
     // bond flags of the whole window, for the angles centred at the neighbours
+    // and the dihedrals through them
     __shared__ unsigned char s_bonds[kStepBlock];
-    if (kAngles) {
+    int back = 0, fwd = 0;  // consecutive bonds backwards / forwards inside the window (<= 3)
+    if (kBonded >= 1) {
         s_bonds[t] = (unsigned char)((has_prev ? 1 : 0) | (has_next ? 2 : 0));
         __syncthreads();
+    }
+    if (kBonded == 2) {
+        if (has_prev) {
+            back = 1;
+            if (s_bonds[t - 1] & 1) {
+                back = 2;
+                if (s_bonds[t - 2] & 1) back = 3;
+            }
+        }
+        if (has_next) {
+            fwd = 1;
+            if (s_bonds[t + 1] & 2) {
+                fwd = 2;
+                if (s_bonds[t + 2] & 2) fwd = 3;
+            }
+        }
     }
     const uint32_t tag = m & kTagMask;
     const float4* __restrict__ Gt = G + (size_t)((m >> kTypeShift) & kTypeMask) * g.gnodes;
@@ -253,7 +277,7 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
                    z - sz[b * kStepBlock + tp], has_prev ? c.two_k : 0.0f, c.r0, fx, fy, fz);
         bond_force(x - sx[b * kStepBlock + tn], y - sy[b * kStepBlock + tn],
                    z - sz[b * kStepBlock + tn], has_next ? c.two_k : 0.0f, c.r0, fx, fy, fz);
-        if (kAngles) {
+        if (kBonded >= 1) {
             // the three angles this bead belongs to: centred at t - 1, t and t + 1
             const int tp2 = (has_prev && t >= 2) ? t - 2 : t;
             const int tn2 = (has_next && t + 2 < kStepBlock) ? t + 2 : t;
@@ -285,6 +309,12 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
             fx += ax;
             fy += ay;
             fz += az;
+        }
+        if (kBonded == 2) {
+            const int o = b * kStepBlock + t;
+            dihedral_forces_of(
+                [&](int d) { return make_float3(sx[o + d], sy[o + d], sz[o + d]); }, back, fwd, c,
+                fx, fy, fz);
         }
         if (kTherm == 2 && andersen_collides(c, tag, step0 + k)) {
             // the on-step velocity redrawn, then the second half kick
@@ -327,21 +357,21 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
     }
 }
 
-template <int kTherm, int kForce, bool kAngles>
+template <int kTherm, int kForce, int kBonded>
 static void launch_step_t(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
     static std::once_flag attr[64];
     once_per_device(attr, [] {
-        cudaFuncSetAttribute(k_step<kTherm, kForce, kAngles>,
+        cudaFuncSetAttribute(k_step<kTherm, kForce, kBonded>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
     });
-    // a bead's update after k sub-steps depends on beads up to k (bonds) or 2k
-    // (angles) places away along its chain
-    const int halo = kAngles ? 2 * n_sub : n_sub;
+    // a bead's update after k sub-steps depends on beads up to k (bonds), 2k
+    // (angles) or 3k (dihedrals) places away along its chain
+    const int halo = (kBonded + 1) * n_sub;
     const int payload = kStepBlock - 2 * halo;
     const int blocks = (n + payload - 1) / payload;
-    k_step<kTherm, kForce, kAngles><<<blocks, kStepBlock, kStepSmem, s>>>(
+    k_step<kTherm, kForce, kBonded><<<blocks, kStepBlock, kStepSmem, s>>>(
         in, out, meta, n, halo, n_sub, step0, g, G, c, D_next, flag);
 }
 
@@ -349,12 +379,13 @@ template <int kTherm, int kForce>
 static void launch_step_a(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
                           long long step0, MeshGeom g, const float4* G, StepConsts c,
                           unsigned long long* D_next, int* flag, cudaStream_t s) {
-    if (c.two_ka != 0.f)
-        launch_step_t<kTherm, kForce, true>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag,
-                                            s);
+    const int bonded = bonded_level(c);
+    if (bonded == 2)
+        launch_step_t<kTherm, kForce, 2>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
+    else if (bonded == 1)
+        launch_step_t<kTherm, kForce, 1>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
     else
-        launch_step_t<kTherm, kForce, false>(in, out, meta, n, n_sub, step0, g, G, c, D_next,
-                                             flag, s);
+        launch_step_t<kTherm, kForce, 0>(in, out, meta, n, n_sub, step0, g, G, c, D_next, flag, s);
 }
 
 void launch_step(StateBuf in, StateBuf out, const uint32_t* meta, int n, int n_sub,
@@ -477,7 +508,7 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <int kTherm, int kForce, bool kAngles>
+template <int kTherm, int kForce, int kBonded>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -508,7 +539,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
     const bool n1 = (b1.m & kBondNext) != 0;  // b1's previous bond is b0's next
     for (int k = 0; k < n_sub; ++k) {
         float w0x, w0y, w0z, w1x, w1y, w1z;  // bonded forces on the lane's two beads
-        warp_bonded_forces<kAngles>(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, p0, n0, n1, c, lane, w0x,
+        warp_bonded_forces<kBonded>(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, p0, n0, n1, c, lane, w0x,
                                     w0y, w0z, w1x, w1y, w1z);
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
@@ -545,7 +576,7 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
 // batch of one): the warps walk the concatenated segment lists; each
 // segment's replica (warp-uniform) selects its record in the kernel parameter
 // block.
-template <int kTherm, int kCap, int kForce, bool kAngles>
+template <int kTherm, int kCap, int kForce, int kBonded>
 __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
     const __grid_constant__ BatchStepParamsT<kCap> p) {
     griddep_wait();
@@ -577,7 +608,7 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
         }
         const BatchStepRep& rp = p.rep[kCap > 1 ? lo : 0];
         const int s = w - s_off[lo];
-        advance_segment<kTherm, kForce, kAngles>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+        advance_segment<kTherm, kForce, kBonded>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
                                                  rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
@@ -586,9 +617,11 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
 
 template <int kCap, int kTherm, int kForce>
 static void warp_attrs_f() {
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, false>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, 0>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
-    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, true>,
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
+    cudaFuncSetAttribute(k_step_warp_batch<kTherm, kCap, kForce, 2>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmem);
 }
 
@@ -619,7 +652,7 @@ static int warp_grid_cap() {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, 0, false>, kWarpBlock,
+            &per_sm, k_step_warp_batch<1, HPF_MAX_REPLICAS, 0, 0>, kWarpBlock,
             kWarpSmem);
         cudaGetLastError();
         cap[dev & 63] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
@@ -637,27 +670,28 @@ static void launch_warp_k(void (*k)(const BatchStepParamsT<kCap>), const BatchSt
 }
 
 template <int kCap, int kTherm, int kForce>
-static void launch_warp_f(const BatchStepParamsT<kCap>& p, int blocks, bool angles,
+static void launch_warp_f(const BatchStepParamsT<kCap>& p, int blocks, int bonded,
                           cudaStream_t s) {
-    if (angles) launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, true>, p, blocks, s);
-    else launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, false>, p, blocks, s);
+    if (bonded == 2) launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, 2>, p, blocks, s);
+    else if (bonded == 1) launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, 1>, p, blocks, s);
+    else launch_warp_k(k_step_warp_batch<kTherm, kCap, kForce, 0>, p, blocks, s);
 }
 
 template <int kCap, int kTherm>
-static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, int force, bool angles,
+static void launch_warp_n(const BatchStepParamsT<kCap>& p, int blocks, int force, int bonded,
                           cudaStream_t s) {
-    if (force == 2) launch_warp_f<kCap, kTherm, 2>(p, blocks, angles, s);
-    else if (force == 1) launch_warp_f<kCap, kTherm, 1>(p, blocks, angles, s);
-    else launch_warp_f<kCap, kTherm, 0>(p, blocks, angles, s);
+    if (force == 2) launch_warp_f<kCap, kTherm, 2>(p, blocks, bonded, s);
+    else if (force == 1) launch_warp_f<kCap, kTherm, 1>(p, blocks, bonded, s);
+    else launch_warp_f<kCap, kTherm, 0>(p, blocks, bonded, s);
 }
 
 template <int kCap>
 static void launch_warp(const BatchStepParamsT<kCap>& p, int blocks, int therm, int force,
                         cudaStream_t s) {
-    const bool angles = p.rep[0].c.two_ka != 0.f;  // all replicas alike (checked at init)
-    if (therm == 1) launch_warp_n<kCap, 1>(p, blocks, force, angles, s);
-    else if (therm == 2) launch_warp_n<kCap, 2>(p, blocks, force, angles, s);
-    else launch_warp_n<kCap, 0>(p, blocks, force, angles, s);
+    const int bonded = bonded_level(p.rep[0].c);  // all replicas alike (checked at init)
+    if (therm == 1) launch_warp_n<kCap, 1>(p, blocks, force, bonded, s);
+    else if (therm == 2) launch_warp_n<kCap, 2>(p, blocks, force, bonded, s);
+    else launch_warp_n<kCap, 0>(p, blocks, force, bonded, s);
 }
 
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,

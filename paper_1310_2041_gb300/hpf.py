@@ -60,6 +60,9 @@ class Params(ctypes.Structure):
         ("thermostat", ctypes.c_int32),
         ("nh_tau", ctypes.c_double),
         ("andersen_nu", ctypes.c_double),
+        ("dihedral_k", ctypes.c_double),
+        ("dihedral_n", ctypes.c_int32),
+        ("dihedral_delta", ctypes.c_double),
     ]
 
 
@@ -164,7 +167,8 @@ def load():
 def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, chi=None,
                 bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
                 sort_every=0, force_mode=0, angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0,
-                andersen_nu=0.0, **_ignored) -> Params:
+                andersen_nu=0.0, dihedral_k=0.0, dihedral_n=1, dihedral_delta=0.0,
+                **_ignored) -> Params:
     p = Params()
     p.n_beads, p.n_species = int(n_beads), int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -187,6 +191,8 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
     p.angle_k, p.angle_cos0 = float(angle_k), float(angle_cos0)
     p.thermostat, p.nh_tau = int(thermostat), float(nh_tau)
     p.andersen_nu = float(andersen_nu)
+    p.dihedral_k, p.dihedral_n = float(dihedral_k), int(dihedral_n)
+    p.dihedral_delta = float(dihedral_delta)
     return p
 
 
