@@ -401,11 +401,15 @@ void orc_bond_force(const orc_params* p, int64_t n, const double* pos, const int
     }
 }
 
-/* Angles (section "Bonded forces", the cosine form).  With u = x_a - x_j,
+/* Angles (section "Bonded forces", both forms).  With u = x_a - x_j,
  * w = x_b - x_j and c = u.w / (|u| |w|) = cos theta:
  *   dc/dx_a = w / (|u| |w|) - c u / |u|^2,  dc/dx_b = u / (|u| |w|) - c w / |w|^2,
- *   dc/dx_j = -(dc/dx_a + dc/dx_b),
- * and F = -2 angle_k (c - angle_cos0) dc/dx on each of the three beads. */
+ *   dc/dx_j = -(dc/dx_a + dc/dx_b).
+ * Cosine form, U = k (c - cos0)^2: F = -2k (c - cos0) dc/dx on each bead.
+ * Harmonic form, U = k (theta - theta0)^2 with theta = atan2(|u x w|, u.w) in
+ * [0, pi]: dtheta/dx = -(1 / sin theta) dc/dx, so F = 2k (theta - theta0) /
+ * sin theta dc/dx; at sin theta = 0 the factor is taken as 0 (the straight
+ * chain, where dc/dx vanishes too). */
 static double angle_cos(const double* pos, int64_t a, int64_t j, int64_t b, double u[3],
                         double w[3], double* uu, double* ww)
 {
@@ -422,6 +426,22 @@ static double angle_cos(const double* pos, int64_t a, int64_t j, int64_t b, doub
     return uw / sqrt(*uu * *ww);
 }
 
+/* theta = atan2(|u x w|, u.w) of the vectors angle_cos returned. */
+static double angle_theta(const double u[3], const double w[3])
+{
+    const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2],
+                 cz = u[0] * w[1] - u[1] * w[0];
+    return atan2(sqrt(cx * cx + cy * cy + cz * cz), u[0] * w[0] + u[1] * w[1] + u[2] * w[2]);
+}
+
+/* -dU/dc of one angle: the factor of dc/dx in its forces. */
+static double angle_factor(const orc_params* p, double c, const double u[3], const double w[3])
+{
+    if (p->angle_form != 1) return -2.0 * p->angle_k * (c - p->angle_cos0);
+    const double th = angle_theta(u, w), s = sin(th);
+    return s > 0.0 ? 2.0 * p->angle_k * (th - p->angle_theta0) / s : 0.0;
+}
+
 void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
                      const int32_t* BN, double* F)
 {
@@ -433,7 +453,7 @@ void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const in
                 const int64_t a = BL[(int64_t)k1 * n + j], b = BL[(int64_t)k2 * n + j];
                 double u[3], w[3], uu, ww;
                 const double c = angle_cos(pos, a, j, b, u, w, &uu, &ww);
-                const double g = -2.0 * p->angle_k * (c - p->angle_cos0);
+                const double g = angle_factor(p, c, u, w);
                 const double inv = 1.0 / sqrt(uu * ww);
                 for (int d = 0; d < 3; ++d) {
                     const double da = w[d] * inv - c * u[d] / uu;
@@ -456,7 +476,12 @@ double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const
                 double u[3], w[3], uu, ww;
                 const double c = angle_cos(pos, BL[(int64_t)k1 * n + j], j,
                                            BL[(int64_t)k2 * n + j], u, w, &uu, &ww);
-                e += (long double)(p->angle_k * (c - p->angle_cos0) * (c - p->angle_cos0));
+                if (p->angle_form == 1) {
+                    const double d = angle_theta(u, w) - p->angle_theta0;
+                    e += (long double)(p->angle_k * d * d);
+                } else {
+                    e += (long double)(p->angle_k * (c - p->angle_cos0) * (c - p->angle_cos0));
+                }
             }
     return (double)e;
 }

@@ -53,7 +53,8 @@ typedef struct {
                            2: Algorithm 1's staggered differences blended at the
                               nearest vertex (orc_field_force_staggered) */
     double angle_k;     /* U = angle_k (cos theta - angle_cos0)^2 per bonded triplet */
-    double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles */
+    double angle_cos0;  /* (section "Bonded forces", the cosine form); 0: no angles;
+                           with angle_form 1 U = angle_k (theta - angle_theta0)^2 */
     int32_t thermostat; /* 0: Langevin (gamma); 1: Nose-Hoover (section "MD methods and
                            algorithms" names it for NVT; orc_run_nh); 2: Andersen
                            (named there too; orc_run) */
@@ -62,6 +63,8 @@ typedef struct {
     double dihedral_k;  /* U = dihedral_k [1 + cos(dihedral_n phi - dihedral_delta)] per */
     int32_t dihedral_n; /* bonded quadruplet (section "Bonded forces"); 0: none */
     double dihedral_delta;
+    int32_t angle_form;  /* 0: the cosine form; 1: the harmonic form in theta (radians) */
+    double angle_theta0;
 } orc_params;
 
 int orc_num_threads(void);
@@ -91,7 +94,8 @@ void orc_field_force_exact(const orc_params* p, int64_t n, const double* pos, co
                            const double* V, double* F);
 /* Angle forces and energy: every pair (a, b) of bond partners of a bead j
  * forms the angle theta at j between x_a - x_j and x_b - x_j (pi for a
- * straight chain), with U = angle_k (cos theta - angle_cos0)^2. */
+ * straight chain), with U = angle_k (cos theta - angle_cos0)^2, or with
+ * angle_form 1 U = angle_k (theta - angle_theta0)^2. */
 void orc_angle_force(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
                      const int32_t* BN, double* F);
 double orc_angle_energy(const orc_params* p, int64_t n, const double* pos, const int32_t* BL,
