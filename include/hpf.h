@@ -97,6 +97,10 @@ typedef struct {
                              pi for trans and 0 for cis; 0: none */
     int32_t dihedral_n;   /* multiplicity n, 1 .. 6 (checked only when dihedral_k != 0) */
     double dihedral_delta; /* phase delta in radians */
+    int32_t angle_form;   /* 0: the cosine form above; 1: the harmonic form of the same
+                             section, U = angle_k (theta - angle_theta0)^2, theta in radians
+                             from atan2(|u x w|, u.w) (angle_cos0 unused) */
+    double angle_theta0;  /* equilibrium angle of the harmonic form, 0 .. pi */
 } hpf_params;
 
 /* Text for a status code (static storage). */

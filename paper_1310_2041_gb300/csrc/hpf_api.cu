@@ -198,6 +198,9 @@ hpf_status validate_params(const hpf_params* p) {
     if (p->force_mode < 0 || p->force_mode > 2) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
         return HPF_ERR_INVALID;
+    if (p->angle_form < 0 || p->angle_form > 1 ||
+        (p->angle_form == 1 && !(p->angle_theta0 >= 0.0 && p->angle_theta0 <= M_PI)))
+        return HPF_ERR_INVALID;
     if (!isfinite(p->dihedral_k) || !isfinite(p->dihedral_delta) ||
         (p->dihedral_k != 0.0 && (p->dihedral_n < 1 || p->dihedral_n > 6)))
         return HPF_ERR_INVALID;
@@ -256,6 +259,8 @@ void derive_constants(hpf_ctx* c) {
     s.force_mode = p.force_mode;
     s.two_ka = (float)(2.0 * p.angle_k);
     s.cos0 = (float)p.angle_cos0;
+    s.angle_form = p.angle_form;
+    s.th0 = (float)p.angle_theta0;
     s.p_coll = p.thermostat == 2 ? (float)(p.andersen_nu * p.dt) : 0.0f;
     s.sig_v = (float)sqrt(p.kT / p.mass);
     s.kd = (float)p.dihedral_k;
@@ -271,6 +276,8 @@ void derive_constants(hpf_ctx* c) {
     e.kT = p.kT;
     e.angle_k = p.angle_k;
     e.cos0 = p.angle_cos0;
+    e.angle_form = p.angle_form;
+    e.theta0 = p.angle_theta0;
     e.dih_k = p.dihedral_k;
     e.dih_n = p.dihedral_k != 0.0 ? p.dihedral_n : 1;
     e.dih_cd = cos(p.dihedral_delta);

@@ -60,6 +60,8 @@ struct StepConsts {
                                 // 2 staggered differences at the nearest vertex
     float two_ka;               // 2 * angle_k (0: no angle terms)
     float cos0;                 // cos of the equilibrium angle
+    int angle_form;             // 0 cosine form, 1 harmonic form in theta
+    float th0;                  // equilibrium angle of the harmonic form (radians)
     float p_coll;               // Andersen collision probability per step fl32(nu dt) (0: none)
     float sig_v;                // sqrt(kT / m): the Maxwell velocity scale
     float kd;                   // dihedral_k (0: no dihedral terms)
@@ -103,6 +105,8 @@ struct EnergyConsts {
     int S;
     int n;
     double angle_k, cos0;  // angle potential
+    int angle_form;        // 0 cosine, 1 harmonic (theta0)
+    double theta0;
     double dih_k;          // dihedral potential k [1 + cos(n phi - delta)]
     int dih_n;
     double dih_cd, dih_sd; // cos delta, sin delta
@@ -531,22 +535,32 @@ __device__ __forceinline__ void bond_force(float dx, float dy, float dz, float t
     fz += s * dz;
 }
 
-// Angle U = k (cos theta - cos0)^2 at a middle bead j with u = x_a - x_j,
-// w = x_b - x_j: forces on the end beads a and b (the middle bead takes minus
-// their sum), -2k (c - cos0) dc/dx with dc/dx_a = w / (|u||w|) - c u / |u|^2
-// and dc/dx_b symmetric.  Each arm length is clamped separately, so every
-// intermediate stays finite even for zero vectors (lanes without beads) and
-// two_ka = 0 gives exactly zero.
+// Angle at a middle bead j with u = x_a - x_j, w = x_b - x_j: forces on the
+// end beads a and b (the middle bead takes minus their sum), g dc/dx with
+// c = cos theta, dc/dx_a = w / (|u||w|) - c u / |u|^2 and dc/dx_b symmetric.
+// Cosine form U = k (c - cos0)^2: g = -2k (c - cos0).  Harmonic form
+// U = k (theta - theta0)^2, theta = atan2(|u x w|, u.w): dtheta/dx =
+// -(1 / sin theta) dc/dx, so g = 2k (theta - theta0) / sin theta.  Lengths and
+// sin theta are clamped, so every intermediate stays finite even for zero
+// vectors (lanes without beads) and two_ka = 0 gives exactly zero.
 __device__ __forceinline__ void angle_force(float ux, float uy, float uz, float wx, float wy,
-                                            float wz, float two_ka, float cos0, float& fax,
-                                            float& fay, float& faz, float& fbx, float& fby,
-                                            float& fbz) {
+                                            float wz, float two_ka, const StepConsts& sc,
+                                            float& fax, float& fay, float& faz, float& fbx,
+                                            float& fby, float& fbz) {
     const float uu = fmaxf(ux * ux + uy * uy + uz * uz, 1e-30f);
     const float ww = fmaxf(wx * wx + wy * wy + wz * wz, 1e-30f);
     const float uw = ux * wx + uy * wy + uz * wz;
     const float inv = rsqrtf(uu) * rsqrtf(ww);
     const float c = uw * inv;
-    const float g = -two_ka * (c - cos0);
+    float g;
+    if (sc.angle_form == 1) {
+        const float qx = uy * wz - uz * wy, qy = uz * wx - ux * wz, qz = ux * wy - uy * wx;
+        const float q = sqrtf(qx * qx + qy * qy + qz * qz);  // |u x w|
+        const float th = atan2f(q, uw);
+        g = two_ka * (th - sc.th0) / fmaxf(q * inv, 1e-30f);
+    } else {
+        g = -two_ka * (c - sc.cos0);
+    }
     const float ca = c / uu, cb = c / ww;
     fax = g * (wx * inv - ca * ux);
     fay = g * (wy * inv - ca * uy);
@@ -566,7 +580,7 @@ __device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32
     float ax, ay, az, bx, by, bz;
     if (hp && hn) {
         angle_force(st.x[i - 1] - x, st.y[i - 1] - y, st.z[i - 1] - z, st.x[i + 1] - x,
-                    st.y[i + 1] - y, st.z[i + 1] - z, c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+                    st.y[i + 1] - y, st.z[i + 1] - z, c.two_ka, c, ax, ay, az, bx, by, bz);
         fx -= ax + bx;
         fy -= ay + by;
         fz -= az + bz;
@@ -574,7 +588,7 @@ __device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32
     if (hp && (meta[i - 1] & kBondPrev)) {
         const float xp = st.x[i - 1], yp = st.y[i - 1], zp = st.z[i - 1];
         angle_force(st.x[i - 2] - xp, st.y[i - 2] - yp, st.z[i - 2] - zp, x - xp, y - yp, z - zp,
-                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+                    c.two_ka, c, ax, ay, az, bx, by, bz);
         fx += bx;
         fy += by;
         fz += bz;
@@ -582,7 +596,7 @@ __device__ __forceinline__ void angle_forces_of(const StateBuf& st, const uint32
     if (hn && (meta[i + 1] & kBondNext)) {
         const float xn = st.x[i + 1], yn = st.y[i + 1], zn = st.z[i + 1];
         angle_force(x - xn, y - yn, z - zn, st.x[i + 2] - xn, st.y[i + 2] - yn, st.z[i + 2] - zn,
-                    c.two_ka, c.cos0, ax, ay, az, bx, by, bz);
+                    c.two_ka, c, ax, ay, az, bx, by, bz);
         fx += ax;
         fy += ay;
         fz += az;
@@ -717,9 +731,9 @@ __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0,
         const float pz = __shfl_up_sync(0xffffffffu, z1, 1);
         float fpx, fpy, fpz, f1x, f1y, f1z, f0x, f0y, f0z, fdx, fdy, fdz;
         angle_force(px - x0, py - y0, pz - z0, x1 - x0, y1 - y0, z1 - z0,
-                    (p0 && n0) ? c.two_ka : 0.0f, c.cos0, fpx, fpy, fpz, f1x, f1y, f1z);
+                    (p0 && n0) ? c.two_ka : 0.0f, c, fpx, fpy, fpz, f1x, f1y, f1z);
         angle_force(x0 - x1, y0 - y1, z0 - z1, dx - x1, dy - y1, dz - z1,
-                    (n0 && n1) ? c.two_ka : 0.0f, c.cos0, f0x, f0y, f0z, fdx, fdy, fdz);
+                    (n0 && n1) ? c.two_ka : 0.0f, c, f0x, f0y, f0z, fdx, fdy, fdz);
         // from lane l - 1: its share on bead 2l; from lane l + 1: its share on bead 2l + 1
         const float r0x = __shfl_up_sync(0xffffffffu, fdx, 1);
         const float r0y = __shfl_up_sync(0xffffffffu, fdy, 1);

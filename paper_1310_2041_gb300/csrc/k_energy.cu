@@ -106,8 +106,17 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                 const double wx = (double)st.x[i + 1] - x, wy = (double)st.y[i + 1] - y,
                              wz = (double)st.z[i + 1] - z;
                 const double uu = ux * ux + uy * uy + uz * uz, ww = wx * wx + wy * wy + wz * wz;
-                const double cth = (ux * wx + uy * wy + uz * wz) / norm_fp64(uu * ww);
-                ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
+                const double uw = ux * wx + uy * wy + uz * wz;
+                if (e.angle_form == 1) {
+                    // harmonic: theta = atan2(|u x w|, u.w)
+                    const double qx = uy * wz - uz * wy, qy = uz * wx - ux * wz,
+                                 qz = ux * wy - uy * wx;
+                    const double d = atan2(norm_fp64(qx * qx + qy * qy + qz * qz), uw) - e.theta0;
+                    ub += e.angle_k * d * d;
+                } else {
+                    const double cth = uw / norm_fp64(uu * ww);
+                    ub += e.angle_k * (cth - e.cos0) * (cth - e.cos0);
+                }
             }
         }
         if (c.kd != 0.f) {

@@ -87,7 +87,7 @@ __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int
     if (kBonded == 0) return;
     float ax, ay, az, bx, by, bz;
     if (hp && hn) {
-        angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z, p.c.two_ka, p.c.cos0, ax, ay,
+        angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z, p.c.two_ka, p.c, ax, ay,
                     az, bx, by, bz);
         fx -= ax + bx;
         fy -= ay + by;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int
     if (hp && (p.meta[i - 1] & kBondPrev)) {
         float xq, yq, zq;
         moved_pos(p, d, i - 2, xq, yq, zq);
-        angle_force(xq - xp, yq - yp, zq - zp, x - xp, y - yp, z - zp, p.c.two_ka, p.c.cos0, ax,
+        angle_force(xq - xp, yq - yp, zq - zp, x - xp, y - yp, z - zp, p.c.two_ka, p.c, ax,
                     ay, az, bx, by, bz);
         fx += bx;
         fy += by;
@@ -105,7 +105,7 @@ __device__ __forceinline__ void bonded_of(const NhParams& p, const Drift& d, int
     if (hn && (p.meta[i + 1] & kBondNext)) {
         float xq, yq, zq;
         moved_pos(p, d, i + 2, xq, yq, zq);
-        angle_force(x - xn, y - yn, z - zn, xq - xn, yq - yn, zq - zn, p.c.two_ka, p.c.cos0, ax,
+        angle_force(x - xn, y - yn, z - zn, xq - xn, yq - yn, zq - zn, p.c.two_ka, p.c, ax,
                     ay, az, bx, by, bz);
         fx += ax;
         fy += ay;

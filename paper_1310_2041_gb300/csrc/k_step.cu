@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
             float ax, ay, az, bx, by, bz;
             // centred at t: this bead takes minus both end shares
             angle_force(xp - x, yp - y, zp - z, xn - x, yn - y, zn - z,
-                        (has_prev && has_next) ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by,
+                        (has_prev && has_next) ? c.two_ka : 0.0f, c, ax, ay, az, bx, by,
                         bz);
             fx -= ax + bx;
             fy -= ay + by;
@@ -298,14 +298,14 @@ __global__ void __launch_bounds__(kStepBlock, 2) k_step(StateBuf in, StateBuf ou
             // centred at t - 1 (ends t - 2 and t): this bead is end b
             angle_force(sx[b * kStepBlock + tp2] - xp, sy[b * kStepBlock + tp2] - yp,
                         sz[b * kStepBlock + tp2] - zp, x - xp, y - yp, z - zp,
-                        left ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by, bz);
+                        left ? c.two_ka : 0.0f, c, ax, ay, az, bx, by, bz);
             fx += bx;
             fy += by;
             fz += bz;
             // centred at t + 1 (ends t and t + 2): this bead is end a
             angle_force(x - xn, y - yn, z - zn, sx[b * kStepBlock + tn2] - xn,
                         sy[b * kStepBlock + tn2] - yn, sz[b * kStepBlock + tn2] - zn,
-                        right ? c.two_ka : 0.0f, c.cos0, ax, ay, az, bx, by, bz);
+                        right ? c.two_ka : 0.0f, c, ax, ay, az, bx, by, bz);
             fx += ax;
             fy += ay;
             fz += az;

@@ -63,6 +63,8 @@ class Params(ctypes.Structure):
         ("dihedral_k", ctypes.c_double),
         ("dihedral_n", ctypes.c_int32),
         ("dihedral_delta", ctypes.c_double),
+        ("angle_form", ctypes.c_int32),
+        ("angle_theta0", ctypes.c_double),
     ]
 
 
@@ -168,7 +170,7 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
                 bond_k=4.0, bond_r0=0.7, mass=1.0, dt=0.01, gamma=1.0, seed=42, field_every=1,
                 sort_every=0, force_mode=0, angle_k=0.0, angle_cos0=-1.0, thermostat=0, nh_tau=1.0,
                 andersen_nu=0.0, dihedral_k=0.0, dihedral_n=1, dihedral_delta=0.0,
-                **_ignored) -> Params:
+                angle_form=0, angle_theta0=np.pi, **_ignored) -> Params:
     p = Params()
     p.n_beads, p.n_species = int(n_beads), int(n_species)
     m = (mesh,) * 3 if np.isscalar(mesh) else tuple(mesh)
@@ -193,6 +195,7 @@ def make_params(n_beads, n_species, mesh, box, kT=1.0, rho0=3.0, inv_kappa=0.1, 
     p.andersen_nu = float(andersen_nu)
     p.dihedral_k, p.dihedral_n = float(dihedral_k), int(dihedral_n)
     p.dihedral_delta = float(dihedral_delta)
+    p.angle_form, p.angle_theta0 = int(angle_form), float(angle_theta0)
     return p
 
 
