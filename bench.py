@@ -57,6 +57,17 @@ def parse():
                     help="plain workloads: Langevin (the default), Nose-Hoover or Andersen NVT")
     ap.add_argument("--nh-tau", type=float, default=1.0)
     ap.add_argument("--andersen-nu", type=float, default=1.0)
+    ap.add_argument("--angle-k", type=float, default=0.0,
+                    help="plain workloads: angle potential constant (0: bonds only)")
+    ap.add_argument("--angle-form", default="cos", choices=["cos", "harmonic"])
+    ap.add_argument("--angle-cos0", type=float, default=-0.5)
+    ap.add_argument("--angle-theta0", type=float, default=2.0)
+    ap.add_argument("--dihedral-k", type=float, default=0.0,
+                    help="plain workloads: dihedral constant (0: none); n = --dihedral-n, "
+                         "delta = --dihedral-delta; chains then start with bond angles "
+                         "in 100..140 degrees")
+    ap.add_argument("--dihedral-n", type=int, default=3)
+    ap.add_argument("--dihedral-delta", type=float, default=0.0)
     ap.add_argument("--net-lags", default="",
                     help="learned workload: also train and judge a network at these lags "
                          "(comma-separated step counts)")
@@ -143,6 +154,44 @@ def thermostat_params(args):
     return {}
 
 
+def bonded_params(args):
+    out = {}
+    if args.angle_k:
+        out.update(angle_k=args.angle_k, angle_form=1 if args.angle_form == "harmonic" else 0,
+                   angle_cos0=args.angle_cos0, angle_theta0=args.angle_theta0)
+    if args.dihedral_k:
+        out.update(dihedral_k=args.dihedral_k, dihedral_n=args.dihedral_n,
+                   dihedral_delta=args.dihedral_delta)
+    return out
+
+
+def model_params(args):
+    return dict(thermostat_params(args), **bonded_params(args))
+
+
+def bonded_name(args):
+    parts = ["bonds"]
+    if args.angle_k:
+        parts.append(f"harmonic angles k={args.angle_k} theta0={args.angle_theta0}"
+                     if args.angle_form == "harmonic" else
+                     f"cosine angles k={args.angle_k} cos0={args.angle_cos0}")
+    if args.dihedral_k:
+        parts.append(f"dihedrals k={args.dihedral_k} n={args.dihedral_n} "
+                     f"delta={args.dihedral_delta}")
+    return " + ".join(parts)
+
+
+def bench_data(w, args, seed=None):
+    """The seeded melt; with angle or dihedral terms its chains start with
+    bond angles in 100..140 degrees (a random walk has near-collinear
+    triples, where a dihedral is undefined)."""
+    from paper_1310_2041_gb300 import workloads as W
+    data = W.generate(w, seed=seed)
+    if args.angle_k or args.dihedral_k:
+        data = W.with_bond_angles(w, data)
+    return data
+
+
 def thermostat_name(args, pp):
     if args.thermostat == "nh":
         return f"nose-hoover tau={args.nh_tau}"
@@ -222,10 +271,10 @@ def run_reference(args):
     import oracle
     from paper_1310_2041_gb300 import workloads as W
     w = W.WORKLOADS[args.workload]()
-    data = W.generate(w)
+    data = bench_data(w, args)
     oracle.build()
     nh = args.thermostat == "nh"
-    op = oracle.make_params(**dict(w.params(), **thermostat_params(args)))
+    op = oracle.make_params(**dict(w.params(), **model_params(args)))
 
     def run(p, pos, vel, types, bonds, step0, n_steps, xe=(0.0, 0.0)):
         if nh:
@@ -263,7 +312,8 @@ def run_reference(args):
             "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_beads": w.n_beads, "sample_beads": n,
-                       "thermostat": thermostat_name(args, w.params())},
+                       "thermostat": thermostat_name(args, w.params()),
+                       "bonded": bonded_name(args)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -286,11 +336,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = W.WORKLOADS[args.workload]()
-    data = W.generate(w, seed=w.seed + rank)
+    data = bench_data(w, args, seed=w.seed + rank)
     pp = w.params()
     pp["sort_every"] = args.sort_every
     nh = args.thermostat == "nh"
-    therm = thermostat_params(args)
+    therm = model_params(args)
     pp.update(therm)
     stream = torch.cuda.current_stream()
     sysm = hpf.System(hpf.make_params(**pp), stream=stream)
@@ -362,7 +412,8 @@ def run_ours(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    tr = None if nh else traffic_record()
+    # the record is the bonds-only step kernel's, on the default workload
+    tr = None if (nh or bonded_params(args)) else traffic_record()
     traffic = None
     if tr:
         traffic = tr["dram_bytes_per_launch"] * bead_steps_per_launch / tr["bead_steps_per_launch"]
@@ -411,6 +462,7 @@ def run_ours(args):
                            "species": w.n_species, "field_every": fe,
                            "sort_every": args.sort_every, "parallelism": f"replicas{world}",
                            "thermostat": thermostat_name(args, pp),
+                           "bonded": bonded_name(args),
                            "l2": "flushed (256 MB write) before each timed field period",
                            "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -550,18 +550,21 @@ __device__ __forceinline__ void angle_force(float ux, float uy, float uz, float 
     const float uu = fmaxf(ux * ux + uy * uy + uz * uz, 1e-30f);
     const float ww = fmaxf(wx * wx + wy * wy + wz * wz, 1e-30f);
     const float uw = ux * wx + uy * wy + uz * wz;
-    const float inv = rsqrtf(uu) * rsqrtf(ww);
+    const float ru = rsqrtf(uu), rw = rsqrtf(ww);  // 1/|u|, 1/|w|: no divisions below
+    const float inv = ru * rw;
     const float c = uw * inv;
     float g;
     if (sc.angle_form == 1) {
         const float qx = uy * wz - uz * wy, qy = uz * wx - ux * wz, qz = ux * wy - uy * wx;
-        const float q = sqrtf(qx * qx + qy * qy + qz * qz);  // |u x w|
-        const float th = atan2f(q, uw);
-        g = two_ka * (th - sc.th0) / fmaxf(q * inv, 1e-30f);
+        const float qq = fmaxf(qx * qx + qy * qy + qz * qz, 1e-30f);  // |u x w|^2
+        const float rq = rsqrtf(qq);
+        const float th = atan2f(qq * rq, uw);
+        // 1 / sin theta = |u||w| / |u x w|
+        g = two_ka * (th - sc.th0) * rq * ((uu * ru) * (ww * rw));
     } else {
         g = -two_ka * (c - sc.cos0);
     }
-    const float ca = c / uu, cb = c / ww;
+    const float ca = c * (ru * ru), cb = c * (rw * rw);
     fax = g * (wx * inv - ca * ux);
     fay = g * (wy * inv - ca * uy);
     faz = g * (wz * inv - ca * uz);
@@ -632,7 +635,8 @@ __device__ __forceinline__ void dihedral_force(float3 b1, float3 b2, float3 b3, 
     const float b22 = fmaxf(f3_dot(b2, b2), 1e-30f);
     const float ib = rsqrtf(b22);
     const float L = b22 * ib;  // |b2|
-    const float inv = rsqrtf(AA) * rsqrtf(BB);
+    const float rA = rsqrtf(AA), rB = rsqrtf(BB);  // no divisions below
+    const float inv = rA * rB;
     const float cp = f3_dot(A, B) * inv, sp = L * f3_dot(b1, B) * inv;
     float cn = cp, sn = sp;
     for (int k = 1; k < c.nd; ++k) {
@@ -641,7 +645,7 @@ __device__ __forceinline__ void dihedral_force(float3 b1, float3 b2, float3 b3, 
         cn = t;
     }
     const float g = -kd * (float)c.nd * fmaf(sn, c.cd, -cn * c.sd);
-    const float a0 = g * L / AA, a3 = -g * L / BB;
+    const float a0 = g * L * (rA * rA), a3 = -g * L * (rB * rB);
     f0 = make_float3(a0 * A.x, a0 * A.y, a0 * A.z);
     f3 = make_float3(a3 * B.x, a3 * B.y, a3 * B.z);
     const float ib2 = ib * ib;

@@ -193,27 +193,28 @@ def with_bond_angles(w: Workload, data: dict, theta_deg=(100.0, 140.0), seed: in
     pos = data["pos"].astype(np.float64).copy()
     b = w.walk_step
     base = 0
+
+    def unit(v):
+        return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
     for n_chains, seq in w.blocks:
         clen = len(seq)
-        for c in range(n_chains):
-            s = base + c * clen
-            if clen < 2:
-                continue
-            v = _unit_vectors(rng, (1,))[0]
-            pos[s + 1] = pos[s] + b * v
-            u = _unit_vectors(rng, (1,))[0]
-            u -= np.dot(u, v) * v
-            u /= np.linalg.norm(u)
+        if clen >= 2:
+            x = pos[base:base + n_chains * clen].reshape(n_chains, clen, 3)
+            v = _unit_vectors(rng, (n_chains,))
+            x[:, 1] = x[:, 0] + b * v
+            u = _unit_vectors(rng, (n_chains,))
+            u = unit(u - np.sum(u * v, axis=1, keepdims=True) * v)
             for k in range(2, clen):
-                th = np.radians(rng.uniform(*theta_deg))
-                ph = rng.uniform(-np.pi, np.pi)
-                t = (pos[s + k - 1] - pos[s + k - 2]) / b
-                n1 = np.cross(t, u)
-                n1 /= np.linalg.norm(n1)
+                th = np.radians(rng.uniform(theta_deg[0], theta_deg[1], size=(n_chains, 1)))
+                ph = rng.uniform(-np.pi, np.pi, size=(n_chains, 1))
+                t = unit(x[:, k - 1] - x[:, k - 2])
+                n1 = unit(np.cross(t, u))
                 m1 = np.cross(n1, t)
                 d = -np.cos(th) * t + np.sin(th) * (np.cos(ph) * m1 + np.sin(ph) * n1)
-                pos[s + k] = pos[s + k - 1] + b * d
+                x[:, k] = x[:, k - 1] + b * d
                 u = t
+            pos[base:base + n_chains * clen] = x.reshape(-1, 3)
         base += n_chains * clen
     out = dict(data)
     out["pos"] = np.ascontiguousarray(pos.astype(np.float32))

@@ -6,7 +6,7 @@ contexts), and parameter checks.  Chains start with bond angles in
 100..140 degrees (workloads.with_bond_angles): the form's force changes
 direction abruptly where a chain passes through straight, and on random-walk
 chains the oracle itself, fed positions perturbed at the FP32 rounding level,
-moves by 2.3e-4 in ten steps on the 10k melt, against at most 3.4e-5 on the
+moves by 2.3e-4 in ten steps on the 10k melt, against at most 3.8e-5 on the
 chains used here.  Bars as for the cosine form."""
 import numpy as np
 import pytest

@@ -34,10 +34,11 @@ def chains(w):
     return W.with_bond_angles(w, W.generate(w))
 
 
-def run_both(hpf, orc, w, n_steps, **over):
+def run_both(hpf, orc, w, n_steps, chunks=None, **over):
     d = chains(w)
     s, d, pp = make(hpf, w, data=d, **over)
-    s.step(n_steps)
+    for c in (chunks or [n_steps]):
+        s.step(c)
     pos, vel, step = s.get_state()
     op = oparams(orc, pp)
     if pp.get("thermostat", 0) == 1:
@@ -85,6 +86,18 @@ def test_long_chains_with_dihedrals_in_the_halo_kernel(hpf_gpu, orc, fe, steps):
     step (48 at 16 steps per launch, the most one launch fuses)."""
     w = W.diblock(30, 50, 50, 10.0, 10, 1.0, field_every=fe)
     pos, vel, po, vo = run_both(hpf_gpu, orc, w, steps, **TRAJ)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_dihedrals_do_not_depend_on_sorting(hpf_gpu, orc, form):
+    """Re-sorting at every launch moves chains between warp segments and
+    lanes (a bead's dihedral shares then add up in another order): the
+    trajectory is still the oracle's, with either angle form."""
+    w = W.diblock(150, 5, 5, 8.0, 8, 1.0, field_every=2)
+    pos, vel, po, vo = run_both(hpf_gpu, orc, w, 10, chunks=[3, 3, 4], sort_every=1,
+                                **dict(TRAJ, angle_form=form, angle_theta0=2.0))
     assert np.max(np.abs(pos - po)) <= 1e-4
     assert np.max(np.abs(vel - vo)) <= 1e-4
 
@@ -153,11 +166,11 @@ def test_batch_rejects_replicas_with_and_without_dihedrals(hpf_gpu):
 
 
 def test_nve_with_dihedrals_conserves_energy(hpf_gpu):
-    """The oracle's NVE pin on the GPU: bonds, a stiff angle term and
-    dihedrals, no field, no thermostat, dt = 0.00125, 1600 steps."""
+    """The oracle's NVE pin on the GPU: bonds, a stiff angle term (angle_k
+    16) and dihedrals, no field, no thermostat, dt = 0.00125, 1600 steps."""
     w = W.diblock(100, 5, 5, 7.0, 7, 1.0)
     s, d, pp = make(hpf_gpu, w, data=chains(w), gamma=0.0, dt=0.00125, chi=np.zeros((2, 2)),
-                    inv_kappa=0.0, angle_k=8.0, angle_cos0=-0.5, dihedral_k=0.5, dihedral_n=3,
+                    inv_kappa=0.0, angle_k=16.0, angle_cos0=-0.5, dihedral_k=0.5, dihedral_n=3,
                     dihedral_delta=0.0)
     E = [s.energy()]
     for _ in range(8):

@@ -112,12 +112,14 @@ def test_nve_conservation_with_dihedrals(orc):
     """Bonds, a stiff angle term and dihedrals, no field and no thermostat, on
     chains whose bond angles start in 100..140 degrees: the total energy is
     conserved (dihedral forces grow without bound as three beads become
-    collinear, which the angle term keeps them away from)."""
+    collinear, which the angle term keeps them away from: with angle_k 8
+    some seeded chains come close enough in 1600 steps to drift by 1e-3 per
+    bead; with 16, five seeds drift by 2e-5 to 6e-5)."""
     w = W.diblock(100, 5, 5, 7.0, 7, 1.0)
     d = W.with_bond_angles(w, W.generate(w))
     pp = dict(w.params(), gamma=0.0, dt=0.00125, chi=np.zeros((2, 2)), inv_kappa=0.0,
-              angle_k=8.0, angle_cos0=-0.5, dihedral_k=0.5, dihedral_n=3, dihedral_delta=0.0)
+              angle_k=16.0, angle_cos0=-0.5, dihedral_k=0.5, dihedral_n=3, dihedral_delta=0.0)
     p = orc.make_params(**pp)
     _, _, E = orc.run(p, d["pos"], d["vel"], d["type"], d["bonds"], 0, 1600, energies=True)
     assert np.ptp(E[:, 1]) / w.n_beads > 0.05      # the bonded energy moves
-    assert np.max(np.abs(E[:, 3] - E[0, 3])) / w.n_beads < 1e-3
+    assert np.max(np.abs(E[:, 3] - E[0, 3])) / w.n_beads < 5e-4
