@@ -143,6 +143,10 @@ __device__ __forceinline__ double nh_half(const NhConsts& t, double& xi, double&
 
 template <int kForce, int kBonded>
 __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ NhParams p) {
+    // dependent launch: the previous launch's state, force and velocity
+    // scales are read only after it has completed
+    griddep_wait();
+    griddep_launch_dependents();
     __shared__ double s_ke[kNhBlock / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -233,9 +237,9 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
 template <int kForce>
 void launch_nh_e(const NhParams& p, int bonded, cudaStream_t s) {
     const int blocks = nh_blocks(p.n);
-    if (bonded == 2) k_nh_step<kForce, 2><<<blocks, kNhBlock, 0, s>>>(p);
-    else if (bonded == 1) k_nh_step<kForce, 1><<<blocks, kNhBlock, 0, s>>>(p);
-    else k_nh_step<kForce, 0><<<blocks, kNhBlock, 0, s>>>(p);
+    if (bonded == 2) launch_pdl(k_nh_step<kForce, 2>, blocks, kNhBlock, 0, s, p);
+    else if (bonded == 1) launch_pdl(k_nh_step<kForce, 1>, blocks, kNhBlock, 0, s, p);
+    else launch_pdl(k_nh_step<kForce, 0>, blocks, kNhBlock, 0, s, p);
 }
 
 }  // namespace
