@@ -273,6 +273,8 @@ void derive_constants(hpf_ctx* c) {
     e.mass = p.mass;
     e.bond_k = p.bond_k;
     e.r0 = p.bond_r0;
+    e.r0_hi = (float)p.bond_r0;
+    e.r0_lo = (float)(p.bond_r0 - (double)e.r0_hi);
     e.kT = p.kT;
     e.angle_k = p.angle_k;
     e.cos0 = p.angle_cos0;
@@ -719,7 +721,8 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     e = e ? e : cudaMalloc(&c->dflag, sizeof(int) * 8);
     e = e ? e : cudaMallocHost(&c->hflag, sizeof(int) * 8);
     e = e ? e : cudaMalloc(&c->partials,
-                           sizeof(double) * energy_partials_needed(c->n, c->geom.nodes));
+                           sizeof(double) * energy_partials_needed(c->n, c->geom.nodes,
+                                                                   c->p.n_species));
     e = e ? e : cudaMalloc(&c->d_out6, sizeof(double) * 8);
     e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
     if (params->thermostat == 1) {

@@ -97,6 +97,7 @@ struct EnergyConsts {
     double mass;
     double bond_k;
     double r0;
+    float r0_hi, r0_lo;  // r0 as a float-float pair
     double kT;
     double inv_kappa;
     double phi_c;       // phi per fixed-point unit: 2^-39 / (rho0 h^3)
@@ -853,7 +854,7 @@ void launch_field_tiled(const SingleFieldParams& p, int S, int tile, cudaStream_
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile);
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);
-int energy_partials_needed(int n, int nodes);
+int energy_partials_needed(int n, int nodes, int S);
 
 // learned density propagator (the network lives in k_prop.cu)
 bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);

@@ -8,6 +8,8 @@ namespace hpf {
 
 constexpr int kRedBlock = 256;
 constexpr int kBeadVals = 5;  // kinetic, bond, px, py, pz
+constexpr int kBeadsPerThread = 8;  // grid-stride share of a thread (on average)
+constexpr int kNodesPerThread = 8;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -18,6 +20,80 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     double r = 0.0;
     if (threadIdx.x == 0)
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+    return r;  // valid in thread 0
+}
+
+// Knuth's two-sum: s + t == a + b exactly (round-to-nearest, no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    t = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// The bond energy k (|d| - r0)^2 of d = x_i - x_j in float-float arithmetic
+// (pairs of FP32 numbers): each component of d exactly by two-sum, |d|^2 with
+// the exact error of each square (FMA) to about 2^-46, |d| from the
+// correctly rounded square root plus its residual, |d| - r0 against
+// r0 = r0_hi + r0_lo, and only the square of that in FP64.  Accurate to about
+// 1e-14 of |d|, like an FP64 evaluation, at a small part of its cost on a
+// GPU whose FP64 rate is low.
+__device__ __forceinline__ double bond_energy_ff(float xi, float yi, float zi, float xj, float yj,
+                                                 float zj, const EnergyConsts& e) {
+    float hx, lx, hy, ly, hz, lz;
+    two_sum(xi, -xj, hx, lx);
+    two_sum(yi, -yj, hy, ly);
+    two_sum(zi, -zj, hz, lz);
+    float H = 0.f, L = 0.f;
+    const float hs[3] = {hx, hy, hz}, ls[3] = {lx, ly, lz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float p = __fmul_rn(hs[a], hs[a]);
+        const float pe = fmaf(hs[a], hs[a], -p);                        // exact error of h^2
+        const float rest = fmaf(2.0f * hs[a], ls[a], fmaf(ls[a], ls[a], pe));  // 2hl + l^2 + pe
+        float t;
+        two_sum(H, p, H, t);
+        L = __fadd_rn(L, __fadd_rn(t, rest));
+    }
+    const float H2 = __fadd_rn(H, L);
+    const float L2 = __fsub_rn(L, __fsub_rn(H2, H));
+    if (!(H2 > 0.f)) return e.bond_k * e.r0 * e.r0;
+    const float r = sqrtf(H2);
+    const float res = __fadd_rn(fmaf(-r, r, H2), L2);  // H2 - r^2 is exact
+    const float r_lo = 0.5f * res * rsqrtf(H2);
+    float a, b;
+    two_sum(r, -e.r0_hi, a, b);
+    b = __fadd_rn(b, __fsub_rn(r_lo, e.r0_lo));
+    const double dr = (double)a + (double)b;
+    return e.bond_k * dr * dr;
+}
+
+// Exact unsigned 128-bit sums (the field energy's node sums).
+struct U128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ void u128_add(U128& a, const U128& b) {
+    const unsigned long long lo = a.lo + b.lo;
+    a.hi += b.hi + (lo < a.lo ? 1ull : 0ull);
+    a.lo = lo;
+}
+__device__ __forceinline__ U128 u128_mul(unsigned long long a, unsigned long long b) {
+    return U128{a * b, __umul64hi(a, b)};
+}
+__device__ __forceinline__ double u128_to_double(const U128& v) {
+    return (double)v.hi * 18446744073709551616.0 + (double)v.lo;
+}
+__device__ __forceinline__ U128 block_sum_u128(U128 v, U128* sh) {
+    for (int o = 16; o > 0; o >>= 1)
+        u128_add(v, U128{__shfl_down_sync(0xffffffffu, v.lo, o),
+                         __shfl_down_sync(0xffffffffu, v.hi, o)});
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    U128 r{0ull, 0ull};
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u128_add(r, sh[k]);
     return r;  // valid in thread 0
 }
 
@@ -68,8 +144,9 @@ __device__ __forceinline__ double dihedral_energy_fp64(const StateBuf& st, int i
 
 // Per bead: F_n exactly as the step kernel forms it, the on-step velocity
 // v_n = v + dt/(2m) F_n, then kinetic energy, momentum and the bond energy of
-// the bond to the next bead (each bond once).  The bond and angle energies
-// are formed in FP64 from the FP32 positions (exact differences); v_n and its
+// the bond to the next bead (each bond once).  The bond energy is formed in
+// float-float (bond_energy_ff), the angle and dihedral energies in FP64, all
+// from the FP32 positions with exact differences; v_n and its
 // squares are FP32 (the FP32 force already limits them to ~1e-7) and are
 // summed in FP32 over each thread's few beads (at most 8 on average), FP64
 // from the block sums on: this GPU's FP64 rate is low.
@@ -93,9 +170,7 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         if (m & kBondNext) {
             const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
             bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
-            const double dx = (double)x - xj, dy = (double)y - yj, dz = (double)z - zj;
-            const double dr = norm_fp64(dx * dx + dy * dy + dz * dz) - e.r0;
-            ub += e.bond_k * dr * dr;
+            ub += bond_energy_ff(x, y, z, xj, yj, zj, e);
         }
         if (c.two_ka != 0.f) {
             angle_forces_of(st, meta, i, m, c, fx, fy, fz);
@@ -166,52 +241,92 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
 // Per node: the field-energy density of the mesh D (FP64 from exact integers).
 // Instantiated per species count: this GPU's FP64 rate is low, and loops to
 // the species bound would issue predicated FP64 work for absent species.
+// The field energy from exact integer sums.  With phi_K = phi_c D_K (D the
+// int64 fixed-point density, non-negative) and T = sum_K D_K per node,
+//   W / (rho0 h^3) = 1/2 kT phi_c^2 sum_KK' chi_KK' S_KK'
+//                  + 1/2 inv_kappa (phi_c^2 sum T^2 - 2 phi_c sum T + nodes),
+// S_KK' = sum over nodes of D_K D_K'.  Every product is below 2^126 and so is
+// every sum (at most (sum D_K)(sum D_K') < 2^126), so the node sums are exact
+// unsigned 128-bit integers, independent of order; FP64 enters only in the
+// final combination.  Per block: the kS (kS + 1) / 2 pair sums (K <= K'),
+// sum T^2 and sum T, each as (lo, hi).
 template <int kS>
 __global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __restrict__ D,
-                                                            int nodes, EnergyConsts e,
-                                                            double* __restrict__ partials) {
-    __shared__ double sh[kRedBlock / 32];
-    double w = 0.0;
+                                                            int nodes,
+                                                            unsigned long long* __restrict__ part) {
+    constexpr int kP = kS * (kS + 1) / 2;
+    __shared__ U128 sh[kRedBlock / 32];
+    U128 acc[kP + 2];
+#pragma unroll
+    for (int q = 0; q < kP + 2; ++q) acc[q] = U128{0ull, 0ull};
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
          node += gridDim.x * blockDim.x) {
-        double phi[kS];
-        double tot = 0.0;
+        unsigned long long d[kS];
+        unsigned long long T = 0ull;
 #pragma unroll
         for (int k = 0; k < kS; ++k) {
-            phi[k] = e.phi_c * (double)D[(size_t)k * nodes + node];
-            tot += phi[k];
+            d[k] = (unsigned long long)D[(size_t)k * nodes + node];
+            T += d[k];
         }
-        double q = 0.0;
+        int q = 0;
 #pragma unroll
-        for (int k = 0; k < kS; ++k) {
-            double row = 0.0;
+        for (int k = 0; k < kS; ++k)
 #pragma unroll
-            for (int kp = 0; kp < kS; ++kp) row += e.chi[k][kp] * phi[kp];
-            q += phi[k] * row;
-        }
-        w += 0.5 * e.kT * q + 0.5 * e.inv_kappa * (tot - 1.0) * (tot - 1.0);
+            for (int kp = k; kp < kS; ++kp) u128_add(acc[q++], u128_mul(d[k], d[kp]));
+        u128_add(acc[kP], u128_mul(T, T));
+        u128_add(acc[kP + 1], U128{T, 0ull});
     }
-    const double s = block_sum(w, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+#pragma unroll
+    for (int q = 0; q < kP + 2; ++q) {
+        const U128 v = block_sum_u128(acc[q], sh);
+        if (threadIdx.x == 0) {
+            part[((size_t)blockIdx.x * (kP + 2) + q) * 2] = v.lo;
+            part[((size_t)blockIdx.x * (kP + 2) + q) * 2 + 1] = v.hi;
+        }
+    }
 }
 
-// Fixed-order final sums -> out6 = {KE, U_bond, W, total, |P|, T}.
 __global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __restrict__ bead_part,
-                                                            int nb, const double* __restrict__ node_part,
-                                                            int nn, EnergyConsts e,
+                                                            int nb,
+                                                            const unsigned long long* __restrict__ node_part,
+                                                            int nn, int nodes, EnergyConsts e,
                                                             double* __restrict__ out6) {
     __shared__ double sh[kRedBlock / 32];
-    double acc[kBeadVals + 1];
+    __shared__ U128 shu[kRedBlock / 32];
+    __shared__ double s_field;
+    double acc[kBeadVals];
     for (int k = 0; k < kBeadVals; ++k) {
         double v = 0.0;
         for (int b = threadIdx.x; b < nb; b += blockDim.x) v += bead_part[(size_t)b * kBeadVals + k];
         acc[k] = block_sum(v, sh);
     }
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nn; b += blockDim.x) v += node_part[b];
-    acc[kBeadVals] = block_sum(v, sh);
+    // the field energy's exact sums, then their combination
+    const int nq = e.S * (e.S + 1) / 2 + 2;
+    double q_chi = 0.0, t2 = 0.0, t1 = 0.0;
+    int k = 0, kp = 0;
+    for (int q = 0; q < nq; ++q) {
+        U128 v{0ull, 0ull};
+        for (int b = threadIdx.x; b < nn; b += blockDim.x)
+            u128_add(v, U128{node_part[((size_t)b * nq + q) * 2],
+                             node_part[((size_t)b * nq + q) * 2 + 1]});
+        const U128 tot = block_sum_u128(v, shu);
+        if (threadIdx.x == 0) {
+            const double val = u128_to_double(tot);
+            if (q < nq - 2) {
+                q_chi += (k == kp ? 1.0 : 2.0) * e.chi[k][kp] * val;
+                if (++kp == e.S) kp = ++k;
+            } else if (q == nq - 2) {
+                t2 = val;
+            } else {
+                t1 = val;
+            }
+        }
+    }
     if (threadIdx.x == 0) {
-        const double ke = acc[0], ub = acc[1], w = acc[5] * e.w_scale;
+        const double pc = e.phi_c;
+        s_field = e.w_scale * (0.5 * e.kT * pc * pc * q_chi +
+                               0.5 * e.inv_kappa * (pc * pc * t2 - 2.0 * pc * t1 + (double)nodes));
+        const double ke = acc[0], ub = acc[1], w = s_field;
         out6[0] = ke;
         out6[1] = ub;
         out6[2] = w;
@@ -221,36 +336,39 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __rest
     }
 }
 
-static int energy_blocks(int count);
+static int energy_blocks(int count, int per_thread);
 
-int energy_partials_needed(int n, int nodes) {
-    return energy_blocks(n) * kBeadVals + energy_blocks(nodes) + 1;
+int energy_partials_needed(int n, int nodes, int S) {
+    // bead partials (doubles), then per node block (S (S + 1) / 2 + 2) sums of two words
+    return energy_blocks(n, kBeadsPerThread) * kBeadVals +
+           energy_blocks(nodes, kNodesPerThread) * 2 * (S * (S + 1) / 2 + 2) + 1;
 }
 
 // Blocks of the energy reductions: each thread takes a grid-stride share (at
 // most 8 beads or nodes per thread on average), independent of the device so
 // the summation order, and with it every FP64 bit, is the same on any GPU.
-static int energy_blocks(int count) {
-    const int per_block = kRedBlock * 8;
+static int energy_blocks(int count, int per_thread) {
+    const int per_block = kRedBlock * per_thread;
     return (count + per_block - 1) / per_block;
 }
 
 void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const float4* G,
                    StepConsts c, long long step, const long long* D, const EnergyConsts& e,
                    double* partials, double* out6, cudaStream_t s) {
-    const int nb = energy_blocks(n);
-    const int nn = energy_blocks(g.nodes);
+    const int nb = energy_blocks(n, kBeadsPerThread);
+    const int nn = energy_blocks(g.nodes, kNodesPerThread);
     double* bead_part = partials;
-    double* node_part = partials + (size_t)nb * kBeadVals;
+    unsigned long long* node_part =
+        reinterpret_cast<unsigned long long*>(partials + (size_t)nb * kBeadVals);
     if (nb > 0) k_energy_beads<<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part);
     switch (e.S) {
 #define HPF_NODES(k) \
-    case k: k_energy_nodes<k><<<nn, kRedBlock, 0, s>>>(D, g.nodes, e, node_part); break;
+    case k: k_energy_nodes<k><<<nn, kRedBlock, 0, s>>>(D, g.nodes, node_part); break;
         HPF_NODES(1) HPF_NODES(2) HPF_NODES(3) HPF_NODES(4)
         HPF_NODES(5) HPF_NODES(6) HPF_NODES(7) HPF_NODES(8)
 #undef HPF_NODES
     }
-    k_energy_final<<<1, kRedBlock, 0, s>>>(bead_part, nb, node_part, nn, e, out6);
+    k_energy_final<<<1, kRedBlock, 0, s>>>(bead_part, nb, node_part, nn, g.nodes, e, out6);
 }
 
 }  // namespace hpf
