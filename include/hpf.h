@@ -233,16 +233,20 @@ hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
  * 0 of Philox4x32-10(counter = (tag, n lo, n hi, 1)) is below fl32(nu dt),
  * and then takes v <- sqrt(kT/m) xi + dt/(2m) F (xi as above): its on-step
  * velocity redrawn from the Maxwell distribution.
- * Errors: HPF_ERR_INVALID (n_steps < 0; Nose-Hoover with chains longer than
- * 64 beads), HPF_ERR_STATE, HPF_ERR_CUDA. */
+ * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
 
-/* Observables at the current step, reduced in FP64 (synchronises):
+/* Observables at the current step, reduced in a fixed order (synchronises;
+ * the values do not depend on the GPU):
  * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step;
  *   with Andersen, a bead colliding at step n counts its redrawn velocity),
- * out[1] bond energy sum k (r - r0)^2, out[2] field energy
+ * out[1] bonded energy: bonds sum k (r - r0)^2 (float-float, ~1e-14 relative
+ *   per bond), angles and dihedrals when set (FP64 per term),
+ * out[2] field energy
  *   W = rho0 h^3 sum_nodes [1/2 kT sum_KK' chi phi_K phi_K' + 1/2 inv_kappa (sum phi - 1)^2]
- *   of a fresh scatter of the current positions, out[3] = out[0]+out[1]+out[2],
+ *   of a fresh scatter of the current positions, from exact 128-bit integer
+ *   sums of the fixed-point densities over the nodes, combined once in FP64,
+ * out[3] = out[0]+out[1]+out[2],
  * out[4] |total momentum| of v_n, out[5] kinetic temperature 2 KE / (3 N).
  * Errors: HPF_ERR_INVALID (out NULL), HPF_ERR_STATE, HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
 hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
@@ -259,9 +263,8 @@ hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
  *   G(K) = (2K / (g kT) - 1) / tau^2, h = dt/2;
  * then v <- v + dt/(2m) F_n; x <- x + dt v.  K is summed in FP64 over the
  * beads in a fixed order.  hpf_energy reports the step's on-step quantities
- * after the pending half step (kinetic energy, |P| and T of s v^E).  Needs
- * chains of at most 64 beads (HPF_ERR_INVALID from hpf_step otherwise); not
- * available in batches or learned windows.
+ * after the pending half step (kinetic energy, |P| and T of s v^E).  Chains
+ * of any length; not available in batches or learned windows.
  *
  * xi, eta of the state (out[2]); hpf_set_state resets them to zero.
  * Synchronises.  Errors: HPF_ERR_INVALID (no Nose-Hoover thermostat), HPF_ERR_CUDA. */
