@@ -148,6 +148,24 @@ hpf_status hpf_update_state(hpf_ctx* ctx, const float* pos, const float* vel, in
 /* Copy the state out in tag order (either pointer may be NULL) and the step
  * number.  Synchronises the stream.
  * Errors: HPF_ERR_STATE, HPF_ERR_NONFINITE (state became non-finite), HPF_ERR_CUDA. */
+/* Pipelined replacement of positions and velocities, for callers that feed
+ * a new state every few steps and want its upload to overlap the GPU work of
+ * the previous one (double buffering).  hpf_upload_state starts the copy of
+ * pos and vel (tag order, [n][3] FP32, host or device; for an overlapped copy
+ * from the host, pinned memory) into one of two context-owned staging slots
+ * on the context's own copy stream and returns at once.  The caller keeps
+ * both arrays valid and unchanged until the copy has run, which is certain
+ * once a later synchronising call on this context (hpf_energy_finish,
+ * hpf_energy, hpf_get_state) has returned after hpf_apply_state.
+ * hpf_apply_state makes the context's stream wait for that copy and then
+ * replaces the state as hpf_update_state(pos, vel, step) does; a slot is
+ * reused only after the permutation that read it has run.  One upload may be
+ * pending at a time.  Errors: HPF_ERR_INVALID (NULL arrays with n > 0,
+ * step < 0), HPF_ERR_STATE (no state; an upload already pending for
+ * hpf_upload_state, none for hpf_apply_state), HPF_ERR_CUDA. */
+hpf_status hpf_upload_state(hpf_ctx* ctx, const float* pos, const float* vel);
+hpf_status hpf_apply_state(hpf_ctx* ctx, int64_t step);
+
 hpf_status hpf_get_state(hpf_ctx* ctx, float* pos, float* vel, int64_t* step);
 
 /* The library's storage order: order[i] is the tag of storage slot i.
@@ -250,6 +268,16 @@ hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
  * out[4] |total momentum| of v_n, out[5] kinetic temperature 2 KE / (3 N).
  * Errors: HPF_ERR_INVALID (out NULL), HPF_ERR_STATE, HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
 hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
+/* hpf_energy in two halves: hpf_energy_start enqueues the kernels and the
+ * copy of the six values to a pinned mirror on the context's stream and
+ * returns; hpf_energy_finish synchronises the stream and returns the values
+ * of the step at which hpf_energy_start was called (work enqueued between the
+ * two, e.g. hpf_apply_state and hpf_step of the next step, runs before it
+ * returns).  While a start is pending, hpf_energy, hpf_nh_conserved,
+ * hpf_batch_energy and a second hpf_energy_start return HPF_ERR_STATE.
+ * Errors: as hpf_energy; HPF_ERR_STATE (hpf_energy_finish without a start). */
+hpf_status hpf_energy_start(hpf_ctx* ctx);
+hpf_status hpf_energy_finish(hpf_ctx* ctx, double out[6]);
 
 /* Nose-Hoover NVT (thermostat == 1; the section "MD methods and algorithms"
  * names the thermostat for the canonical ensemble, with Hoover's equations

@@ -74,6 +74,16 @@ struct hpf_ctx {
     int nh_f = 0;  // force buffer written last
     NhConsts nhc{};
     double* h_nh = nullptr;  // pinned [2]: xi, eta
+    // pipelined uploads (hpf_upload_state / hpf_apply_state): two staging
+    // slots of [6n] floats, the context's copy stream, and per slot the event
+    // of its copy and the event of the permutation that last read it
+    float* up_stage[2] = {nullptr, nullptr};
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_done[2] = {nullptr, nullptr};
+    cudaEvent_t up_free[2] = {nullptr, nullptr};
+    int up_slot = 0;
+    bool up_pending = false;
+    bool energy_pending = false;  // hpf_energy_start issued, hpf_energy_finish not yet
 };
 
 // Buffers of the learned-propagator driver and the density judge.
@@ -802,6 +812,15 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->nh_part);
     cudaFree(c->nh_F);
     cudaFreeHost(c->h_nh);
+    if (c->up_stream) {
+        cudaStreamSynchronize(c->up_stream);
+        cudaStreamDestroy(c->up_stream);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (c->up_done[k]) cudaEventDestroy(c->up_done[k]);
+        if (c->up_free[k]) cudaEventDestroy(c->up_free[k]);
+        cudaFree(c->up_stage[k]);
+    }
     if (LearnedBufs* L = c->learned) {
         cudaFree(L->Dbase);
         cudaFree(L->Dp);
@@ -927,6 +946,61 @@ hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int6
     return HPF_OK;
 }
 
+hpf_status hpf_upload_state(hpf_ctx* c, const float* pos, const float* vel) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    if (c->up_pending) return fail(c, HPF_ERR_STATE, "an upload is pending (hpf_apply_state first)");
+    const int n = c->n;
+    if (n > 0) {
+        if (!pos || !vel) return fail(c, HPF_ERR_INVALID, "pos and vel are required");
+        if (!c->up_stream) {
+            CUDA_TRY(c, cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
+            for (int k = 0; k < 2; ++k) {
+                CUDA_TRY(c, cudaEventCreateWithFlags(&c->up_done[k], cudaEventDisableTiming));
+                CUDA_TRY(c, cudaEventCreateWithFlags(&c->up_free[k], cudaEventDisableTiming));
+                CUDA_TRY(c, cudaMalloc(&c->up_stage[k], sizeof(float) * 6 * (size_t)n));
+            }
+        }
+        const int k = c->up_slot;
+        float* spos = c->up_stage[k];
+        float* svel = spos + 3 * (size_t)n;
+        // the slot is free once the permutation that last read it has run
+        CUDA_TRY(c, cudaStreamWaitEvent(c->up_stream, c->up_free[k], 0));
+        CUDA_TRY(c, cudaMemcpyAsync(spos, pos, sizeof(float) * 3 * n, cudaMemcpyDefault,
+                                    c->up_stream));
+        CUDA_TRY(c, cudaMemcpyAsync(svel, vel, sizeof(float) * 3 * n, cudaMemcpyDefault,
+                                    c->up_stream));
+        CUDA_TRY(c, cudaEventRecord(c->up_done[k], c->up_stream));
+    }
+    c->up_pending = true;
+    return HPF_OK;
+}
+
+hpf_status hpf_apply_state(hpf_ctx* c, int64_t step) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    if (!c->up_pending) return fail(c, HPF_ERR_STATE, "no upload pending (hpf_upload_state first)");
+    if (step < 0) return fail(c, HPF_ERR_INVALID, "step must be >= 0");
+    const int n = c->n;
+    if (n > 0) {
+        const int k = c->up_slot;
+        CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->up_done[k], 0));
+        {
+            StageScope sc(c, HPF_STAGE_OTHER, 1);
+            launch_repermute(c->up_stage[k], c->up_stage[k] + 3 * (size_t)n, c->meta, n,
+                             cur_state(c), c->dflag, c->stream);
+        }
+        LAUNCH_CHECK(c);
+        CUDA_TRY(c, cudaEventRecord(c->up_free[k], c->stream));
+        c->up_slot ^= 1;
+    }
+    c->up_pending = false;
+    c->step = step;
+    c->field_valid = false;
+    c->mesh_step = -1;
+    return HPF_OK;
+}
+
 hpf_status hpf_get_state(hpf_ctx* c, float* pos, float* vel, int64_t* step) {
     if (!c) return HPF_ERR_INVALID;
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
@@ -1044,9 +1118,29 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
 
 hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
+    if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
     hpf_status s = energy_launch(c);
     if (s != HPF_OK) return s;
     if ((s = check_flags(c)) != HPF_OK) return s;
+    energy_finish(c, out);
+    return HPF_OK;
+}
+
+hpf_status hpf_energy_start(hpf_ctx* c) {
+    if (!c) return HPF_ERR_INVALID;
+    if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
+    const hpf_status s = energy_launch(c);
+    if (s != HPF_OK) return s;
+    c->energy_pending = true;
+    return HPF_OK;
+}
+
+hpf_status hpf_energy_finish(hpf_ctx* c, double out[6]) {
+    if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
+    if (!c->energy_pending) return fail(c, HPF_ERR_STATE, "no hpf_energy_start pending");
+    c->energy_pending = false;
+    const hpf_status s = check_flags(c);
+    if (s != HPF_OK) return s;
     energy_finish(c, out);
     return HPF_OK;
 }
@@ -1396,6 +1490,8 @@ hpf_ctx* hpf_batch_replica(hpf_batch* b, int32_t r) {
 
 hpf_status hpf_batch_energy(hpf_batch* b, double* out) {
     if (!b || !out) return HPF_ERR_INVALID;
+    for (hpf_ctx* c : b->rep)
+        if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
     // every replica's kernels and copies first, one synchronisation after
     for (hpf_ctx* c : b->rep) {
         hpf_status s = energy_launch(c);

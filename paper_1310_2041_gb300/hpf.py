@@ -106,6 +106,10 @@ def load():
         L.hpf_set_state.argtypes = [vp, vp, vp, vp, vp, i64, i64]
         L.hpf_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
         L.hpf_update_state.argtypes = [vp, vp, vp, i64]
+        L.hpf_upload_state.argtypes = [vp, vp, vp]
+        L.hpf_apply_state.argtypes = [vp, i64]
+        L.hpf_energy_start.argtypes = [vp]
+        L.hpf_energy_finish.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_get_order.argtypes = [vp, vp]
         L.hpf_field_tile.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hpf_set_field_tile.argtypes = [vp, i32]
@@ -301,6 +305,42 @@ class System:
         vp, _b = _ptr(vel, np.float32, (self.n, 3), "vel")
         self._check(self.lib.hpf_update_state(self.h, pp, vp, int(step)))
 
+    # ---- pipelined state upload (double-buffered staging, own copy stream)
+    def upload_state(self, pos, vel):
+        """Start copying new positions and velocities (tag order); returns at
+        once.  The arrays are kept referenced here until a synchronising call
+        after apply_state (energy_finish, energy, get_state)."""
+        pp, a = _ptr(pos, np.float32, (self.n, 3), "pos")
+        vp, b = _ptr(vel, np.float32, (self.n, 3), "vel")
+        self._check(self.lib.hpf_upload_state(self.h, pp, vp))
+        self._uploads().append([(pos, vel, a, b), False])
+
+    def apply_state(self, step):
+        """Replace the state with the pending upload (the stream waits for its copy)."""
+        self._check(self.lib.hpf_apply_state(self.h, int(step)))
+        for u in self._uploads():
+            u[1] = True
+
+    def _uploads(self):
+        if not hasattr(self, "_up"):
+            self._up = []
+        return self._up
+
+    def _synced(self):
+        # uploads applied before a synchronising call have been copied
+        self._up = [u for u in self._uploads() if not u[1]]
+
+    def energy_start(self):
+        """Enqueue the observables of the current step (see energy_finish)."""
+        self._check(self.lib.hpf_energy_start(self.h))
+
+    def energy_finish(self):
+        """The six observables of the step energy_start was called at."""
+        out = (ctypes.c_double * 6)()
+        self._check(self.lib.hpf_energy_finish(self.h, out))
+        self._synced()
+        return np.array(list(out))
+
     def get_state(self, pos=None, vel=None):
         if pos is None:
             pos = np.empty((self.n, 3), dtype=np.float32)
@@ -310,6 +350,7 @@ class System:
         pp, _a = _ptr(pos, np.float32, (self.n, 3), "pos")
         vp, _b = _ptr(vel, np.float32, (self.n, 3), "vel")
         self._check(self.lib.hpf_get_state(self.h, pp, vp, ctypes.byref(step)))
+        self._synced()
         return pos, vel, step.value
 
     def order(self, out=None):
@@ -360,6 +401,7 @@ class System:
     def energy(self):
         out = (ctypes.c_double * 6)()
         self._check(self.lib.hpf_energy(self.h, out))
+        self._synced()
         return np.array(list(out))
 
     # ---- Nose-Hoover thermostat (thermostat == 1)
