@@ -157,7 +157,10 @@ hpf_status hpf_update_state(hpf_ctx* ctx, const float* pos, const float* vel, in
  * both arrays valid and unchanged until the copy has run, which is certain
  * once a later synchronising call on this context (hpf_energy_finish,
  * hpf_energy, hpf_get_state) has returned after hpf_apply_state.
- * hpf_apply_state makes the context's stream wait for that copy and then
+ * The copy is ordered after no other work (it runs on a non-blocking stream
+ * so that it can overlap the context's): device-resident inputs must be
+ * complete when hpf_upload_state is called (their producer's stream
+ * synchronised).  hpf_apply_state makes the context's stream wait for that copy and then
  * replaces the state as hpf_update_state(pos, vel, step) does; a slot is
  * reused only after the permutation that read it has run.  One upload may be
  * pending at a time.  Errors: HPF_ERR_INVALID (NULL arrays with n > 0,

@@ -308,8 +308,10 @@ class System:
     # ---- pipelined state upload (double-buffered staging, own copy stream)
     def upload_state(self, pos, vel):
         """Start copying new positions and velocities (tag order); returns at
-        once.  The arrays are kept referenced here until a synchronising call
-        after apply_state (energy_finish, energy, get_state)."""
+        once.  The copy is not ordered after other GPU work: device arrays
+        must be complete when this is called.  The arrays are kept referenced
+        here until a synchronising call after apply_state (energy_finish,
+        energy, get_state)."""
         pp, a = _ptr(pos, np.float32, (self.n, 3), "pos")
         vp, b = _ptr(vel, np.float32, (self.n, 3), "vel")
         self._check(self.lib.hpf_upload_state(self.h, pp, vp))
