@@ -41,3 +41,24 @@ def test_ternary_blend_layout():
     assert d["type"].tolist().count(2) == 30
     assert d["bonds"].shape[0] == 6 * 19
     assert np.all(d["bonds"][:, 1] == d["bonds"][:, 0] + 1)
+
+
+def test_chains_with_bounded_bond_angles():
+    """with_bond_angles: bonds of walk_step, every bond angle in 100..140
+    degrees, the same draw for the same seed, topology and velocities kept."""
+    w = W.diblock(50, 6, 4, 8.0, 8, 1.0)
+    d = W.generate(w)
+    a = W.with_bond_angles(w, d)
+    b = W.with_bond_angles(w, d)
+    assert np.array_equal(a["pos"], b["pos"])
+    assert not np.array_equal(a["pos"], W.with_bond_angles(w, d, seed=1)["pos"])
+    for k in ("vel", "type", "bonds"):
+        assert np.array_equal(a[k], d[k])
+    x = a["pos"].astype(np.float64).reshape(50, 10, 3)
+    assert np.array_equal(x[:, 0], d["pos"].astype(np.float64).reshape(50, 10, 3)[:, 0])
+    r = np.linalg.norm(x[:, 1:] - x[:, :-1], axis=-1)
+    np.testing.assert_allclose(r, w.walk_step, rtol=1e-5)
+    u, v = x[:, :-2] - x[:, 1:-1], x[:, 2:] - x[:, 1:-1]
+    c = np.sum(u * v, -1) / np.linalg.norm(u, axis=-1) / np.linalg.norm(v, axis=-1)
+    theta = np.degrees(np.arccos(np.clip(c, -1, 1)))
+    assert theta.min() >= 100.0 - 1e-3 and theta.max() <= 140.0 + 1e-3
