@@ -257,6 +257,41 @@ hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
  * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
 
+/* ---- Chain-partitioned runs ------------------------------------------------
+ *
+ * One system split into parts by whole chains, each part a context (for
+ * example one per GPU).  The MD-SCF section drives every bead by one field of
+ * the density of all beads, so at each refresh the parts' partial int64
+ * meshes are summed (an exact, order-independent integer sum) and every part
+ * computes the same field from the total; between refreshes the parts are
+ * independent (bonds never cross parts, the field is frozen).
+ *
+ * hpf_set_tag_base: the part's beads are beads tag_base .. tag_base + n - 1
+ * of the whole system; their noise counters (hpf_step) use those global tags,
+ * so the parts draw the same noise as one context holding every chain.
+ * Results stay indexed by the part's own tags 0 .. n - 1.  Any time after
+ * hpf_init; tag_base >= 0 and tag_base + n_beads <= 2^24.
+ * Errors: HPF_ERR_INVALID. */
+hpf_status hpf_set_tag_base(hpf_ctx* ctx, int64_t tag_base);
+
+/* hpf_step for one part: advances like hpf_step but returns where a field
+ * refresh is due, with *steps_done the steps it ran and *mesh the device
+ * address of the context's mesh ([S][Mz][My][Mx] int64, library-owned, valid
+ * until the next call on the context) holding this part's own density of the
+ * current positions.  The caller adds every other part's mesh into it (in
+ * place, e.g. an all-reduce sum over the parts, ordered after the context's
+ * stream and before the next call) and calls again: that call computes the
+ * field from the mesh as it then stands and continues.  *mesh is NULL when the
+ * call ran all n_steps before a refresh was due.  Sorting, bonds, angles,
+ * dihedrals, the Langevin and Andersen thermostats and the fused deposit work
+ * as in hpf_step, so parts driven this way with tag bases reproduce one
+ * context's run bit for bit.  hpf_energy on a part gives its own beads'
+ * kinetic and bonded terms and |P| and T of its beads; its field term is that
+ * of the part's own density.  Asynchronous.
+ * Errors: HPF_ERR_INVALID (n_steps < 0, NULL outputs, a Nose-Hoover context:
+ * its thermostat couples every bead at every step), HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_step_partial(hpf_ctx* ctx, int32_t n_steps, int32_t* steps_done, int64_t** mesh);
+
 /* Observables at the current step, reduced in a fixed order (synchronises;
  * the values do not depend on the GPU):
  * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step;
@@ -277,7 +312,8 @@ hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
  * of the step at which hpf_energy_start was called (work enqueued between the
  * two, e.g. hpf_apply_state and hpf_step of the next step, runs before it
  * returns).  While a start is pending, hpf_energy, hpf_nh_conserved,
- * hpf_batch_energy and a second hpf_energy_start return HPF_ERR_STATE.
+ * hpf_get_thermostat, hpf_set_thermostat, hpf_batch_energy and a second
+ * hpf_energy_start return HPF_ERR_STATE.
  * Errors: as hpf_energy; HPF_ERR_STATE (hpf_energy_finish without a start). */
 hpf_status hpf_energy_start(hpf_ctx* ctx);
 hpf_status hpf_energy_finish(hpf_ctx* ctx, double out[6]);
@@ -512,8 +548,8 @@ hpf_status hpf_step_learned(hpf_ctx* ctx, hpf_prop* prop, int32_t n_windows, int
  * whose own memory pool has already reserved nearly all of the device, or a
  * program that must not pay the device-wide synchronisation that cudaMalloc
  * and cudaFree can cause in the middle of its work.  Such a caller owns every
- * buffer it passes; the library's own working memory (one int64 density mesh,
- * a spare mesh and the float4 field) is a single file-scope static __device__
+ * buffer it passes; the library's own working memory (one int64 density mesh
+ * and the float4 field) is a single file-scope static __device__
  * array of HPF_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads this
  * library holds until the process exits.
  *
@@ -535,10 +571,11 @@ hpf_status hpf_step_learned(hpf_ctx* ctx, hpf_prop* prop, int32_t n_windows, int
  * density mesh it needs itself): calls that overlap on the GPU (two streams
  * or threads without ordering between them) race and give wrong forces, so
  * order them, for instance on one stream.
- * Errors: HPF_ERR_INVALID (bad parameter, n outside [0, HPF_MAX_BEADS], a
- * NULL or host pointer with n > 0), HPF_ERR_SCRATCH (the mesh needs more than
+ * Errors: HPF_ERR_INVALID (a field parameter hpf_init would refuse, n outside
+ * [0, HPF_MAX_BEADS], or with n > 0 a NULL pointer, a host pointer or one to
+ * another GPU's memory), HPF_ERR_SCRATCH (the mesh needs more than
  * HPF_NOALLOC_SCRATCH_BYTES; see hpf_noalloc_scratch_bytes), HPF_ERR_CUDA. */
-#define HPF_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB: fits a 70^3 two-species mesh */
+#define HPF_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB: fits a 70^3 mesh of up to 3 species */
 
 /* Scratch bytes hpf_field_forces_noalloc needs for these parameters (0 if the
  * species count or mesh is invalid). */

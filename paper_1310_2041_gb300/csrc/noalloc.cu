@@ -20,9 +20,8 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-// Device scratch shared by every call on a device: [D | D_spare | G], each part
-// 256-byte aligned.  D_spare only absorbs the field kernel's clearing of a
-// second mesh.
+// Device scratch shared by every call on a device: [D | G], each part 256-byte
+// aligned.
 __device__ __align__(256) unsigned char g_noalloc_scratch[HPF_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_addr_mutex;
@@ -65,13 +64,21 @@ __global__ void k_na_gather(const float* __restrict__ pos, const int32_t* __rest
     F[3 * i + 2] = fz;
 }
 
+// Device memory of the current device (or managed memory): a buffer on
+// another GPU would fault in the kernels instead of being refused here.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device address of the scratch on the current device (looked up once per device).
@@ -103,24 +110,15 @@ extern "C" size_t hpf_noalloc_scratch_bytes(const hpf_params* p) {
     const size_t nodes = (size_t)p->mesh[0] * p->mesh[1] * p->mesh[2];
     const size_t gnodes = (size_t)(p->mesh[0] + 1) * (p->mesh[1] + 1) * (p->mesh[2] + 1);
     const size_t d = align256(sizeof(unsigned long long) * nodes * p->n_species);
-    return 2 * d + align256(sizeof(float4) * gnodes * p->n_species);
+    return d + align256(sizeof(float4) * gnodes * p->n_species);
 }
 
 extern "C" hpf_status hpf_field_forces_noalloc(const hpf_params* p, const float* pos,
                                                const int32_t* type, int32_t n, float* F_out,
                                                void* stream) {
     if (!p || n < 0 || n > HPF_MAX_BEADS) return HPF_ERR_INVALID;
-    if (p->n_species < 1 || p->n_species > HPF_MAX_SPECIES || !(p->rho0 > 0) ||
-        !isfinite(p->kT) || !isfinite(p->inv_kappa))
-        return HPF_ERR_INVALID;
-    for (int a = 0; a < 3; ++a)
-        if (p->mesh[a] < 2 || p->mesh[a] > 4096 || !(p->box[a] > 0.0f) || !isfinite(p->box[a]))
-            return HPF_ERR_INVALID;
-    for (int k = 0; k < p->n_species; ++k)
-        for (int j = 0; j < p->n_species; ++j) {
-            const double a = p->chi[k * HPF_MAX_SPECIES + j], b = p->chi[j * HPF_MAX_SPECIES + k];
-            if (!isfinite(a) || a != b) return HPF_ERR_INVALID;
-        }
+    // the same field parameters hpf_init accepts
+    if (validate_field_params(p) != HPF_OK) return HPF_ERR_INVALID;
     const size_t need = hpf_noalloc_scratch_bytes(p);
     if (need > (size_t)HPF_NOALLOC_SCRATCH_BYTES) return HPF_ERR_SCRATCH;
     if (n > 0 && (!pos || !type || !F_out || !on_device(pos) || !on_device(type) ||
@@ -165,8 +163,7 @@ extern "C" hpf_status hpf_field_forces_noalloc(const hpf_params* p, const float*
     }
     const size_t dbytes = sizeof(unsigned long long) * (size_t)g.nodes * f.S;
     unsigned long long* D = (unsigned long long*)base;
-    unsigned long long* D_spare = (unsigned long long*)((char*)base + align256(dbytes));
-    float4* G = (float4*)((char*)base + 2 * align256(dbytes));
+    float4* G = (float4*)((char*)base + align256(dbytes));
 
     // the scratch keeps the previous call's contents: clear the mesh first
     if (cudaMemsetAsync(D, 0, dbytes, s) != cudaSuccess) {
@@ -174,7 +171,7 @@ extern "C" hpf_status hpf_field_forces_noalloc(const hpf_params* p, const float*
         return HPF_ERR_CUDA;
     }
     if (n > 0) k_na_scatter<<<(n + 255) / 256, 256, 0, s>>>(pos, type, n, f.S, g, D);
-    launch_field(reinterpret_cast<const long long*>(D), g, f, G, D_spare, s);
+    launch_field(reinterpret_cast<const long long*>(D), g, f, G, nullptr, s);
     if (n > 0) k_na_gather<<<(n + 255) / 256, 256, 0, s>>>(pos, type, n, f.S, g, G, F_out);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HPF_OK : HPF_ERR_CUDA;

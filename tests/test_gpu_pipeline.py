@@ -87,3 +87,25 @@ def test_pipeline_misuse_is_an_error(hpf_gpu):
     e1 = s.energy_finish()
     np.testing.assert_array_equal(e1, s.energy())
     s.close()
+
+
+def test_nose_hoover_observables_survive_thermostat_calls_while_pending(hpf_gpu):
+    """hpf_energy_finish applies the pending Nose-Hoover half step with the
+    thermostat state in the pinned mirror that hpf_get_thermostat and
+    hpf_set_thermostat write: both are refused while a start is pending, so
+    the split observables equal hpf_energy's even after such a call."""
+    w = W.diblock(300, 5, 5, 9.4, 9, 1.0, field_every=2)
+    d = W.generate(w)
+    pp = dict(w.params(), thermostat=1, nh_tau=0.5)
+    s = hpf_gpu.System(hpf_gpu.make_params(**pp))
+    s.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+    s.step(3)
+    ref = s.energy()
+    s.energy_start()
+    s.step(2)                                   # moves xi, eta on the device
+    with pytest.raises(hpf_gpu.HPFError):
+        s.get_thermostat()
+    with pytest.raises(hpf_gpu.HPFError):
+        s.set_thermostat(0.3, 0.1)
+    np.testing.assert_array_equal(s.energy_finish(), ref)
+    s.close()

@@ -92,3 +92,10 @@ def test_noalloc_rejects_oversize_meshes_and_host_pointers():
     host = np.zeros((10, 3), dtype=np.float32)
     assert L.hpf_field_forces_noalloc(ctypes.byref(ok), host.ctypes.data, typ.data_ptr(), 10,
                                       dev.data_ptr(), None) == HPF_ERR_INVALID
+    # field parameters that hpf_init refuses are refused here too (no launch)
+    neg = hpf.make_params(10, 2, 8, 8.0, kT=-1.0)
+    assert L.hpf_field_forces_noalloc(ctypes.byref(neg), dev.data_ptr(), typ.data_ptr(), 10,
+                                      dev.data_ptr(), None) == HPF_ERR_INVALID
+    # the 70^3 mesh of three species fits the scratch (density and field only)
+    tern = hpf.make_params(10, 3, 70, 69.3)
+    assert 0 < L.hpf_noalloc_scratch_bytes(ctypes.byref(tern)) <= 32 << 20
