@@ -37,6 +37,7 @@ struct hpf_ctx {
     int dmesh = 0;                    // which one is the context's mesh
     long long mesh_step = -1;         // step whose positions it holds (-1: none / injected)
     bool next_zero = false;           // the other mesh is known to be all zero
+    long long part_step = -1;         // step whose partial mesh hpf_step_partial handed out
     float4* G = nullptr;              // field mesh (ghosted)
     float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
     FieldCoef* d_coef = nullptr;      // the stencil coefficients in device memory
@@ -82,6 +83,7 @@ struct hpf_ctx {
     cudaEvent_t up_done[2] = {nullptr, nullptr};
     cudaEvent_t up_free[2] = {nullptr, nullptr};
     int up_slot = 0;
+    bool up_ready = false;    // stream, events and both slots exist
     bool up_pending = false;
     bool energy_pending = false;  // hpf_energy_start issued, hpf_energy_finish not yet
 };
@@ -183,10 +185,11 @@ hpf_status copy_out(hpf_ctx* c, void* dst, const void* src, size_t bytes) {
     return HPF_OK;
 }
 
-hpf_status validate_params(const hpf_params* p) {
+}  // namespace
+
+// The mesh and field parameters (shared with the allocation-free entry point).
+hpf_status hpf::validate_field_params(const hpf_params* p) {
     if (!p) return HPF_ERR_INVALID;
-    if (p->n_beads < 0) return HPF_ERR_INVALID;
-    if (p->n_beads > HPF_MAX_BEADS) return HPF_ERR_OVERFLOW;
     if (p->n_species < 1 || p->n_species > HPF_MAX_SPECIES) return HPF_ERR_INVALID;
     for (int a = 0; a < 3; ++a) {
         if (p->mesh[a] < 2 || p->mesh[a] > 4096) return HPF_ERR_INVALID;
@@ -195,15 +198,26 @@ hpf_status validate_params(const hpf_params* p) {
     if ((long long)(p->mesh[0] + 1) * (p->mesh[1] + 1) * (p->mesh[2] + 1) * p->n_species >
         (1LL << 31) - 1)
         return HPF_ERR_INVALID;
-    if (!(p->rho0 > 0) || !(p->mass > 0) || !(p->dt > 0) || !(p->gamma >= 0) || !(p->kT >= 0))
-        return HPF_ERR_INVALID;
-    if (!isfinite(p->inv_kappa) || !isfinite(p->bond_k) || !isfinite(p->bond_r0))
+    if (!(p->rho0 > 0) || !(p->kT >= 0) || !isfinite(p->kT) || !isfinite(p->inv_kappa))
         return HPF_ERR_INVALID;
     for (int k = 0; k < p->n_species; ++k)
         for (int j = 0; j < p->n_species; ++j) {
             const double a = p->chi[k * HPF_MAX_SPECIES + j], b = p->chi[j * HPF_MAX_SPECIES + k];
             if (!isfinite(a) || a != b) return HPF_ERR_INVALID;  // chi must be symmetric
         }
+    return HPF_OK;
+}
+
+namespace {
+
+hpf_status validate_params(const hpf_params* p) {
+    if (!p) return HPF_ERR_INVALID;
+    if (p->n_beads < 0) return HPF_ERR_INVALID;
+    if (p->n_beads > HPF_MAX_BEADS) return HPF_ERR_OVERFLOW;
+    const hpf_status f = validate_field_params(p);
+    if (f != HPF_OK) return f;
+    if (!(p->mass > 0) || !(p->dt > 0) || !(p->gamma >= 0)) return HPF_ERR_INVALID;
+    if (!isfinite(p->bond_k) || !isfinite(p->bond_r0)) return HPF_ERR_INVALID;
     if (p->field_every < 1 || p->sort_every < 0) return HPF_ERR_INVALID;
     if (p->force_mode < 0 || p->force_mode > 2) return HPF_ERR_INVALID;
     if (!isfinite(p->angle_k) || !(p->angle_cos0 >= -1.0 && p->angle_cos0 <= 1.0))
@@ -907,6 +921,7 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     c->warp_mode = n > 0 && c->max_chain <= 64;
     c->step = step;
     c->mesh_step = -1;
+    c->part_step = -1;
     hpf_status s2 = sort_beads(c);
     if (s2 != HPF_OK) return s2;
     c->step = step;
@@ -928,6 +943,7 @@ hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int6
         c->step = step;
         c->field_valid = false;
         c->mesh_step = -1;
+        c->part_step = -1;
         return HPF_OK;
     }
     if (!pos || !vel) return fail(c, HPF_ERR_INVALID, "pos and vel are required");
@@ -943,7 +959,36 @@ hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int6
     c->step = step;
     c->field_valid = false;
     c->mesh_step = -1;
+    c->part_step = -1;
     return HPF_OK;
+}
+
+// The copy stream, events and staging slots of pipelined uploads, made on
+// first use.  up_ready is set only once all of them exist; a failure part way
+// releases what was made, so a later call starts over.
+static hpf_status upload_setup(hpf_ctx* c) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&c->up_done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->up_free[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&c->up_stage[k], sizeof(float) * 6 * (size_t)c->n);
+    }
+    if (e == cudaSuccess) {
+        c->up_ready = true;
+        return HPF_OK;
+    }
+    cudaGetLastError();
+    for (int k = 0; k < 2; ++k) {
+        if (c->up_done[k]) cudaEventDestroy(c->up_done[k]);
+        if (c->up_free[k]) cudaEventDestroy(c->up_free[k]);
+        cudaFree(c->up_stage[k]);
+        c->up_done[k] = c->up_free[k] = nullptr;
+        c->up_stage[k] = nullptr;
+    }
+    if (c->up_stream) cudaStreamDestroy(c->up_stream);
+    c->up_stream = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA,
+                "upload set-up: %s", cudaGetErrorString(e));
 }
 
 hpf_status hpf_upload_state(hpf_ctx* c, const float* pos, const float* vel) {
@@ -953,13 +998,9 @@ hpf_status hpf_upload_state(hpf_ctx* c, const float* pos, const float* vel) {
     const int n = c->n;
     if (n > 0) {
         if (!pos || !vel) return fail(c, HPF_ERR_INVALID, "pos and vel are required");
-        if (!c->up_stream) {
-            CUDA_TRY(c, cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
-            for (int k = 0; k < 2; ++k) {
-                CUDA_TRY(c, cudaEventCreateWithFlags(&c->up_done[k], cudaEventDisableTiming));
-                CUDA_TRY(c, cudaEventCreateWithFlags(&c->up_free[k], cudaEventDisableTiming));
-                CUDA_TRY(c, cudaMalloc(&c->up_stage[k], sizeof(float) * 6 * (size_t)n));
-            }
+        if (!c->up_ready) {
+            const hpf_status s = upload_setup(c);
+            if (s != HPF_OK) return s;
         }
         const int k = c->up_slot;
         float* spos = c->up_stage[k];
@@ -998,6 +1039,7 @@ hpf_status hpf_apply_state(hpf_ctx* c, int64_t step) {
     c->step = step;
     c->field_valid = false;
     c->mesh_step = -1;
+    c->part_step = -1;
     return HPF_OK;
 }
 
@@ -1047,6 +1089,7 @@ hpf_status hpf_field(hpf_ctx* c, const int64_t* D_in, float* field_out) {
                                     c->stream));
         c->dmesh ^= 1;
         c->mesh_step = -1;  // an injected mesh is not the density of the positions
+        c->part_step = -1;
         c->next_zero = false;
     }
     hpf_status s = run_field(c);
@@ -1116,6 +1159,58 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
     return HPF_OK;
 }
 
+hpf_status hpf_set_tag_base(hpf_ctx* c, int64_t tag_base) {
+    if (!c) return HPF_ERR_INVALID;
+    if (tag_base < 0 || tag_base + (int64_t)c->n > (int64_t)HPF_MAX_BEADS + 1)
+        return fail(c, HPF_ERR_INVALID, "tag_base + n_beads must stay within 2^24");
+    c->sc.tag_base = (uint32_t)tag_base;
+    return HPF_OK;
+}
+
+// hpf_step that stops where a refresh is due: the first call there hands out
+// the part's own density of the current positions (deposited by the last
+// launch, or scattered now) for the caller to sum over all parts; the next
+// call takes the mesh as it then stands for the field.
+hpf_status hpf_step_partial(hpf_ctx* c, int32_t n_steps, int32_t* steps_done, int64_t** mesh) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!steps_done || !mesh) return fail(c, HPF_ERR_INVALID, "steps_done and mesh are required");
+    *steps_done = 0;
+    *mesh = nullptr;
+    if (n_steps < 0) return fail(c, HPF_ERR_INVALID, "n_steps must be >= 0");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    if (c->nh)
+        return fail(c, HPF_ERR_INVALID, "Nose-Hoover couples every bead each step: no partial steps");
+    const long long fe = c->p.field_every;
+    long long left = n_steps;
+    for (;;) {
+        hpf_status s;
+        const bool due = !c->field_valid || (c->step % fe == 0 && c->field_step != c->step);
+        if (due) {
+            if (c->part_step != c->step) {
+                if ((s = scatter_current(c)) != HPF_OK) return s;
+                c->part_step = c->step;
+                *mesh = reinterpret_cast<int64_t*>(mesh_buf(c, c->dmesh));
+                return HPF_OK;
+            }
+            // the mesh holds the sum over the parts now, not this part's density
+            if ((s = run_field(c)) != HPF_OK) return s;
+            c->mesh_step = -1;
+        }
+        if (left == 0) return HPF_OK;
+        long long chunk = fe - (c->step % fe);
+        if (chunk > left) chunk = left;
+        if (chunk > (c->warp_mode ? 64 : step_halo_max()))
+            chunk = c->warp_mode ? 64 : step_halo_max();
+        if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
+            if ((s = sort_beads(c)) != HPF_OK) return s;
+        }
+        const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
+        if ((s = advance(c, (int)chunk, fuse)) != HPF_OK) return s;
+        left -= chunk;
+        *steps_done += (int32_t)chunk;
+    }
+}
+
 hpf_status hpf_energy(hpf_ctx* c, double out[6]) {
     if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
     if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
@@ -1148,6 +1243,8 @@ hpf_status hpf_energy_finish(hpf_ctx* c, double out[6]) {
 hpf_status hpf_get_thermostat(hpf_ctx* c, double out[2]) {
     if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
     if (!c->nh) return fail(c, HPF_ERR_INVALID, "the context has no Nose-Hoover thermostat");
+    // hpf_energy_finish reads the pinned mirror the copy below would overwrite
+    if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
     CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1160,6 +1257,7 @@ hpf_status hpf_set_thermostat(hpf_ctx* c, const double in[2]) {
     if (!c || !in) return fail(c, HPF_ERR_INVALID, "in is required");
     if (!c->nh) return fail(c, HPF_ERR_INVALID, "the context has no Nose-Hoover thermostat");
     if (!isfinite(in[0]) || !isfinite(in[1])) return fail(c, HPF_ERR_INVALID, "non-finite xi or eta");
+    if (c->energy_pending) return fail(c, HPF_ERR_STATE, "hpf_energy_start is pending");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the pinned mirror may still be in use
     c->h_nh[0] = in[0];
     c->h_nh[1] = in[1];
@@ -1812,6 +1910,7 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
                 c->step = t;
                 c->field_valid = false;
                 c->mesh_step = -1;
+                c->part_step = -1;
                 c->next_zero = false;
                 if ((s = plain_window(c, K)) != HPF_OK) return s;
                 L->plain_mode = true;

@@ -67,6 +67,7 @@ struct StepConsts {
     float kd;                   // dihedral_k (0: no dihedral terms)
     int nd;                     // dihedral multiplicity n
     float cd, sd;               // cos and sin of the dihedral phase delta
+    uint32_t tag_base;          // added to a bead's tag in its noise counter (parts of a system)
 };
 
 // Bonded terms the step kernels evaluate: 0 bonds, 1 bonds and angles,
@@ -293,14 +294,15 @@ __device__ __forceinline__ float log_unit(float u) {
     return d <= 0.015625f ? series : hw;
 }
 
-// Three standard normals of bead `tag` at step `step` (Box-Muller):
+// Three standard normals of bead `tag` (its global tag is tag + c.tag_base)
+// at step `step` (Box-Muller):
 // x, y = sqrt(-2 ln u0) (cos, sin)(2 pi u1); z = sqrt(-2 ln u2) cos(2 pi u3).
 // The angle is taken as 2 pi (u - 1/2) + pi, inside (-pi, pi) for the
 // hardware sine and cosine.
 __device__ __forceinline__ void gauss3(const StepConsts& c, uint32_t tag, long long step,
                                        float& gx, float& gy, float& gz) {
-    uint32_t c0 = tag, c1 = (uint32_t)step, c2 = (uint32_t)((unsigned long long)step >> 32),
-             c3 = 0u;
+    uint32_t c0 = tag + c.tag_base, c1 = (uint32_t)step,
+             c2 = (uint32_t)((unsigned long long)step >> 32), c3 = 0u;
     philox4x32_10(c0, c1, c2, c3, c.rk0, c.rk1);
     const float L0 = -2.0f * log_unit(open_uniform(c0));
     const float L2 = -2.0f * log_unit(open_uniform(c2));
@@ -318,8 +320,8 @@ __device__ __forceinline__ void gauss3(const StepConsts& c, uint32_t tag, long l
 // exact in FP32, so the decision is the same as an FP64 comparison of them.
 __device__ __forceinline__ bool andersen_collides(const StepConsts& c, uint32_t tag,
                                                   long long step) {
-    uint32_t c0 = tag, c1 = (uint32_t)step, c2 = (uint32_t)((unsigned long long)step >> 32),
-             c3 = 1u;
+    uint32_t c0 = tag + c.tag_base, c1 = (uint32_t)step,
+             c2 = (uint32_t)((unsigned long long)step >> 32), c3 = 1u;
     philox4x32_10(c0, c1, c2, c3, c.rk0, c.rk1);
     return open_uniform(c0) < c.p_coll;
 }
@@ -803,6 +805,10 @@ __device__ __forceinline__ void warp_bonded_forces(float x0, float y0, float z0,
 }
 
 // ------------------------------------------------------------------ launchers
+
+// Mesh, box, species, rho0, kT, 1/kappa and chi of a parameter block:
+// HPF_OK or HPF_ERR_INVALID.
+hpf_status validate_field_params(const hpf_params* p);
 
 void launch_stage_state(const float* pos, const float* vel, const int32_t* type, int n, int S,
                         StateBuf st, uint32_t* meta, int* err, cudaStream_t s);

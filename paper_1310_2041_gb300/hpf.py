@@ -117,6 +117,8 @@ def load():
         L.hpf_field.argtypes = [vp, vp, vp]
         L.hpf_forces.argtypes = [vp, vp, i32]
         L.hpf_step.argtypes = [vp, i32]
+        L.hpf_set_tag_base.argtypes = [vp, i64]
+        L.hpf_step_partial.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(vp)]
         L.hpf_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_get_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.hpf_set_thermostat.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -164,7 +166,7 @@ def load():
                      "hpf_scatter_density", "hpf_field", "hpf_forces", "hpf_step", "hpf_energy",
                      "hpf_profile", "hpf_profile_read", "hpf_get_order", "hpf_field_tile",
                      "hpf_set_field_tile", "hpf_get_thermostat", "hpf_set_thermostat",
-                     "hpf_nh_conserved"):
+                     "hpf_nh_conserved", "hpf_set_tag_base", "hpf_step_partial"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib
@@ -221,6 +223,22 @@ def _ptr(a, dtype, shape=None, name="array"):
     if shape is not None and a.numel() != int(np.prod(shape)):
         raise ValueError(f"{name}: expected {shape}, got {tuple(a.shape)}")
     return a.data_ptr(), a
+
+
+class _CudaArray:
+    """A device buffer described by __cuda_array_interface__ (version 3)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape),
+                                         "typestr": typestr, "data": (int(ptr), False),
+                                         "strides": None, "version": 3}
+
+
+def device_view(ptr, shape, typestr):
+    """A torch tensor over library-owned device memory (no copy; the library
+    keeps ownership)."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
 
 
 def current_stream_handle():
@@ -399,6 +417,22 @@ class System:
 
     def step(self, n_steps=1):
         self._check(self.lib.hpf_step(self.h, int(n_steps)))
+
+    # ---- chain-partitioned runs
+    def set_tag_base(self, tag_base):
+        """This part's beads are tags tag_base .. tag_base + n - 1 of the system."""
+        self._check(self.lib.hpf_set_tag_base(self.h, int(tag_base)))
+
+    def step_partial(self, n_steps):
+        """hpf_step_partial: (steps run, mesh) with mesh None, or a torch int64
+        tensor [S][Mz][My][Mx] viewing the library's mesh (no copy) that holds
+        this part's density; sum the other parts into it before the next call."""
+        done, mesh = ctypes.c_int32(0), ctypes.c_void_p(0)
+        self._check(self.lib.hpf_step_partial(self.h, int(n_steps), ctypes.byref(done),
+                                              ctypes.byref(mesh)))
+        if not mesh.value:
+            return done.value, None
+        return done.value, device_view(mesh.value, self.mesh_shape, "<i8")
 
     def energy(self):
         out = (ctypes.c_double * 6)()
