@@ -1,8 +1,23 @@
 """The learned density propagator on the GPU against its CPU oracle, through the C ABI.
 
 Network kernels (BF16 operands, FP32 accumulation) against the FP64 oracle
-of oracle/propagator.py.  Tolerance: every BF16 rounding (inputs, weights,
-the two hidden activations, the back-propagated gradients) carries a
+of oracle/propagator.py, twice.
+
+First against the oracle fed what the kernels consume (tests/prop_bf16.py:
+the oracle's conv, SiLU and their derivatives with the GPU's BF16 roundings
+applied in between -- input features formed in FP32, weights, hidden
+activations, loss and back-propagated gradients).  What is left is the FP32
+accumulation order (about 1e-6 of a 432-term sum) and the rare hidden value
+whose FP32 pre-activation lies on the other side of a BF16 rounding boundary
+than the FP64 one: it moves by one BF16 step (2^-8 relative), so no output
+or gradient element can move by more than 2^-8 of the largest one through a
+single such flip, and their few random flips keep the norm error near
+sqrt(p) 2^-8 ~ 1e-4.  Held to 5e-4 of the norm per output and per layer's
+weight and bias gradients, 2^-8 of the largest element element-wise, the
+loss to 5e-5.  A wrong bias, a swapped channel or a SiLU rounded the wrong
+way fails these.
+
+Second against the unrounded FP64 oracle: every BF16 rounding carries a
 relative error of at most 2^-9; through three layers of 27 x 16-term sums
 with mixed signs that is about 1e-2 of an output's norm, so outputs and
 gradients are held to 3e-2 of their norm (and a cosine above 0.999),
@@ -16,6 +31,7 @@ rejects every prediction, and the run must equal field_every = 1 bit for bit.
 import numpy as np
 import pytest
 
+import prop_bf16 as E
 from oracle import propagator as P
 from paper_1310_2041_gb300 import workloads as W
 
@@ -48,6 +64,19 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+# bars against the BF16-emulated oracle (module docstring)
+EMU_NORM = 5e-4
+EMU_ELEM = 2.0 ** -8
+EMU_LOSS = 5e-5
+
+
+def within_emulated(got, ref, what):
+    got = np.asarray(got, np.float64)
+    assert rel(got, ref) < EMU_NORM, f"{what}: norm error {rel(got, ref):.2e}"
+    err = np.max(np.abs(got - ref))
+    assert err <= EMU_ELEM * np.max(np.abs(ref)), f"{what}: element error {err:.2e}"
+
+
 def cosine(a, b):
     a = np.asarray(a, np.float64).ravel()
     b = np.asarray(b, np.float64).ravel()
@@ -61,6 +90,8 @@ def test_forward_matches_oracle(hpf_gpu, mesh):
     with hpf_gpu.Propagator(mesh) as net:
         net.set_weights(hpf_gpu.pack_params(params))
         y = net.forward(x.astype(np.float32))
+    ye, _, _, _ = E.forward(params, x)
+    within_emulated(y, ye, "output")
     yo, _ = P.forward(params, x)
     assert y.shape == yo.shape
     assert rel(y, yo) < 3e-2
@@ -93,9 +124,14 @@ def test_backward_matches_oracle(hpf_gpu, mesh):
         net.set_weights(hpf_gpu.pack_params(params))
         loss, g = net.backward(x.astype(np.float32), nxt.astype(np.float32))
     target = nxt - x[2:]
+    Le, ge = E.backward(params, x, nxt)
+    assert loss == pytest.approx(Le, rel=EMU_LOSS)
+    got = hpf_gpu.unpack_params(g)
+    for k, ((gW, gb), (eW, eb)) in enumerate(zip(got, ge)):
+        within_emulated(gW, eW, f"layer {k} weight gradient")
+        within_emulated(gb, eb, f"layer {k} bias gradient")
     Lo, go = P.backward(params, x, target)
     assert loss == pytest.approx(Lo, rel=2e-2)
-    got = hpf_gpu.unpack_params(g)
     for k, ((gW, gb), (oW, ob)) in enumerate(zip(got, go)):
         assert rel(gW, oW) < 3e-2, f"layer {k} weights"
         assert cosine(gW, oW) > 0.999, f"layer {k} weights"
@@ -125,6 +161,13 @@ def test_scaled_network_matches_oracle(hpf_gpu):
             with pytest.raises(hpf_gpu.HPFError):
                 net.scale = bad
         assert net.scale == s
+    ye, _, _, _ = E.forward(params, x, s)
+    within_emulated(y, ye, "scaled output")
+    Le, ge = E.backward(params, x, nxt, s)
+    assert loss == pytest.approx(Le, rel=EMU_LOSS)
+    for k, ((gW, gb), (eW, eb)) in enumerate(zip(hpf_gpu.unpack_params(g), ge)):
+        within_emulated(gW, eW, f"layer {k} weight gradient (scaled)")
+        within_emulated(gb, eb, f"layer {k} bias gradient (scaled)")
     yo, _ = P.forward(params, x, s)
     assert rel(y, yo) < 3e-2 and cosine(y, yo) > 0.999
     Lo, go = P.backward(params, x, nxt - x[2:], s)
