@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="a10b10_1m")
     ap.add_argument("--sort-every", type=int, default=1000)
+    ap.add_argument("--parallel", default="chains", choices=["chains", "replicas"],
+                    help="with --gpus N > 1: split one system by whole chains (NCCL mesh "
+                         "all-reduce at every refresh, strong scaling) or run N replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
@@ -336,64 +339,95 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = W.WORKLOADS[args.workload]()
-    data = bench_data(w, args, seed=w.seed + rank)
+    chains = world > 1 and args.parallel == "chains"
     pp = w.params()
     pp["sort_every"] = args.sort_every
     nh = args.thermostat == "nh"
     therm = model_params(args)
     pp.update(therm)
+    if chains and nh:
+        raise SystemExit("Nose-Hoover couples every bead each step: use --parallel replicas")
     stream = torch.cuda.current_stream()
-    sysm = hpf.System(hpf.make_params(**pp), stream=stream)
+    if chains:
+        # one system split by whole chains; the partial meshes are summed by an
+        # NCCL all-reduce at every field refresh
+        from paper_1310_2041_gb300 import partition as PT
+        data_all = bench_data(w, args)
+        tag_base, data = PT.split_chains(data_all, world)[rank]
+        del data_all
+        pp["n_beads"] = len(data["type"])
+        sysm = hpf.System(hpf.make_params(**pp), stream=stream)
+        sysm.set_tag_base(tag_base)
+
+        def reduce(mesh):
+            dist.all_reduce(mesh, op=dist.ReduceOp.SUM)
+
+        def advance(n):
+            PT.step_part(sysm, n, reduce)
+    else:
+        data = bench_data(w, args, seed=w.seed + rank)
+        sysm = hpf.System(hpf.make_params(**pp), stream=stream)
+
+        def advance(n):
+            sysm.step(n)
+    n_total = w.n_beads if chains else w.n_beads * world
     dev = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
     sysm.set_state(dev["pos"], dev["vel"], dev["type"], dev["bonds"])
     fe = w.field_every
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    # warm-up (untimed)
-    sysm.step(args.warmup)
+    # warm-up (untimed): at least W steps, continued to the next field refresh,
+    # so that the timed window starts on a refresh step as every period of a
+    # long run does
+    warm = args.warmup + (-args.warmup) % fe
+    advance(warm)
     torch.cuda.synchronize()
     sysm.profile_read()
 
     # timed region: K steps in field periods, L2 flushed before each period
     chunks, left = [], args.steps
     while left > 0:
-        c = min(fe - (args.warmup + args.steps - left) % fe, left)
+        c = min(fe, left)
         chunks.append(c)
         left -= c
-    starts = [torch.cuda.Event(enable_timing=True) for _ in chunks]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in chunks]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+
+    def window(profile: bool):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, a, b in zip(chunks, starts, ends):
+            flush.zero_()
+            sysm.profile(profile)
+            a.record(stream)
+            advance(c)
+            b.record(stream)
+        sysm.profile(False)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), t1
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    # the library's per-stage CUDA events (which time the step kernel for the
-    # roofline) are recorded in a sample of the timed periods only: each event
-    # pair between kernels costs about 1 us per step in stream serialisation
-    prof_every = max(1, len(chunks) // 8)
-    profiled = [k % prof_every == 0 for k in range(len(chunks))]
-    wall0 = time.perf_counter()
-    for c, a, b, on in zip(chunks, starts, ends, profiled):
-        flush.zero_()
-        sysm.profile(on)
-        a.record(stream)
-        sysm.step(c)
-        b.record(stream)
-    sysm.profile(False)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if dist:
-        dist.barrier()
+    dev_ms, wall = window(False)
     clk = clocks.stop()
-    prof = sysm.profile_read()
-    sysm.profile(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     t_max = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     dev_ms = float(t_max.item())
-    value = w.n_beads * args.steps * world / (dev_ms * 1e-3)
+    value = n_total * args.steps / (dev_ms * 1e-3)
+    # the kernel window: the same K steps again (continuing the run) with the
+    # library's per-stage CUDA events on its stream; events between kernels
+    # break the dependent-launch overlap, so the throughput window has none
+    sysm.profile_read()
+    window(True)
+    prof = sysm.profile_read()
+    profiled = [True] * len(chunks)
 
     # dominant kernel: the fused step kernel (one launch per field period;
     # Nose-Hoover: one per step plus one per period).  Achieved bandwidth: the
@@ -401,11 +435,12 @@ def run_ours(args):
     # kernel's event time in those periods (the sum over their launches of
     # bytes per launch / launch duration, weighted by duration).
     step_ms, step_launches = prof["step"]
+    n_local = sysm.n   # this rank's beads
     prof_steps = sum(c for c, on in zip(chunks, profiled) if on)
     prof_launches = sum((c + 1 if nh else 1) for c, on in zip(chunks, profiled) if on)
     avg_launch_s = step_ms * 1e-3 / max(prof_launches, 1)
-    bead_steps_per_launch = w.n_beads * prof_steps / max(prof_launches, 1)
-    achieved = ALGO_BYTES_PER_BEAD_STEP * w.n_beads * prof_steps / (step_ms * 1e-3) / 1e9
+    bead_steps_per_launch = n_local * prof_steps / max(prof_launches, 1)
+    achieved = ALGO_BYTES_PER_BEAD_STEP * n_local * prof_steps / (step_ms * 1e-3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -422,7 +457,8 @@ def run_ours(args):
                 "kernel": "k_nh_step" if nh else "k_step_warp_batch",
                 "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
                 "avg_launch_us": avg_launch_s * 1e6,
-                "timed_periods": f"{sum(profiled)} of {len(chunks)} (stage events)",
+                "kernel_window": f"step-kernel events over a second window of the same "
+                                 f"{args.steps} steps ({len(chunks)} periods)",
                 "stage_ms": {k: round(v[0], 4) for k, v in prof.items()}}
     launches = int(sum(v[1] for v in prof.values()))
 
@@ -433,14 +469,14 @@ def run_ours(args):
         host = {k: torch.from_numpy(v).pin_memory() for k, v in data.items()}
         h2d = sum(host[k].numel() * host[k].element_size() for k in ("pos", "vel"))
         sysm.set_state(host["pos"], host["vel"], host["type"], host["bonds"])
-        sysm.step(1)
+        advance(1)
         sysm.energy()
         torch.cuda.synchronize()
         # serial: each step's upload, step and observables one after another
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             sysm.update_state(host["pos"], host["vel"], 0)
-            sysm.step(1)
+            advance(1)
             sysm.energy()
         torch.cuda.synchronize()
         te_serial = time.perf_counter() - t0
@@ -450,28 +486,28 @@ def run_ours(args):
         for _ in range(2):
             sysm.upload_state(host["pos"], host["vel"])
             sysm.apply_state(0)
-            sysm.step(1)
+            advance(1)
             sysm.energy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sysm.upload_state(host["pos"], host["vel"])
         for k in range(args.e2e_steps):
             sysm.apply_state(0)
-            sysm.step(1)
+            advance(1)
             sysm.energy_start()
             if k + 1 < args.e2e_steps:
                 sysm.upload_state(host["pos"], host["vel"])
             sysm.energy_finish()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": w.n_beads * args.e2e_steps * world / te, "unit": UNIT,
+        e2e = {"value": n_total * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 6 * 8,
                "steps": args.e2e_steps,
                "path": "per step: hpf_upload_state(positions and velocities from pinned "
                        "host, double-buffered, issued while the previous step runs) + "
                        "hpf_apply_state + hpf_step(1) + hpf_energy_start/finish (to host); "
                        "topology loaded once",
-               "serial_value": w.n_beads * args.e2e_steps * world / te_serial,
+               "serial_value": n_total * args.e2e_steps / te_serial,
                "serial_path": "hpf_update_state + hpf_step(1) + hpf_energy per step"}
 
     cpu = None
@@ -482,12 +518,18 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "strong" if chains else "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "n_beads": w.n_beads, "mesh": w.mesh,
                            "species": w.n_species, "field_every": fe,
-                           "sort_every": args.sort_every, "parallelism": f"replicas{world}",
+                           "sort_every": args.sort_every,
+                           "parallelism": (f"chains{world} (NCCL int64 mesh all-reduce per "
+                                           f"refresh)" if chains else f"replicas{world}"),
                            "thermostat": thermostat_name(args, pp),
                            "bonded": bonded_name(args),
+                           "window": f"untimed warm-up of {warm} steps (W continued to the "
+                                     f"next field refresh), then {len(chunks)} field "
+                                     f"periods",
                            "l2": "flushed (256 MB write) before each timed field period",
                            "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
