@@ -348,6 +348,7 @@ void ensure_tmaps(hpf_ctx* c, int tile) {
 void fill_field_rep_mesh(hpf_ctx* c, int tile, const unsigned long long* D, const CUtensorMap& tm,
                          bool tm_ok, unsigned long long* D_clear, TiledFieldRep& fr, int& blocks) {
     fr.tmap = tm;
+    fr.coef = c->d_coef;
     fr.g = c->geom;
     fr.D = reinterpret_cast<const long long*>(D);
     fr.G = c->G;
@@ -427,7 +428,6 @@ hpf_status run_field(hpf_ctx* c) {
             c->field_tile = autotune_tile<SingleFieldParams>(c->stream, c->S, [&](int t, SingleFieldParams& p) {
                 memset(&p, 0, sizeof p);
                 p.R = 1;
-                p.coef = c->d_coef;
                 p.flag = c->dflag;
                 fill_field_rep(c, t, c->dmesh, p.rep[0], p.blocks);
             });
@@ -435,7 +435,6 @@ hpf_status run_field(hpf_ctx* c) {
         SingleFieldParams p;
         memset(&p, 0, sizeof p);
         p.R = 1;
-        p.coef = c->d_coef;
         p.flag = c->dflag;
         fill_field_rep(c, c->field_tile, c->dmesh, p.rep[0], p.blocks);
         launch_field_tiled(p, c->S, c->field_tile, c->stream);
@@ -471,7 +470,6 @@ hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap
             SingleFieldParams p;
             memset(&p, 0, sizeof p);
             p.R = 1;
-            p.coef = c->d_coef;
             p.flag = c->dflag;
             fill_field_rep_mesh(c, c->field_tile, D, tm, tm_ok, D_clear, p.rep[0], p.blocks);
             launch_field_tiled(p, c->S, c->field_tile, c->stream);
@@ -1360,7 +1358,7 @@ struct hpf_batch {
     long long* d_step = nullptr;  // step counter read by graph replays
     cudaGraphExec_t gexec = nullptr;
     std::vector<const void*> graph_key;  // buffers the captured graph refers to
-    int field_tile = -1;                 // stencil tile shape chosen for the whole batch
+    std::vector<int> rep_tile;           // stencil tile shape chosen per replica mesh (empty: not yet)
     std::string err;
 };
 
@@ -1371,15 +1369,39 @@ hpf_status bfail(hpf_batch* b, hpf_status s, const char* msg) {
     return s;
 }
 
-// The batched stencil over all replicas, each reading its mesh buffer dm_r.
-void fill_batch_field(hpf_batch* b, int tile, int flip, TiledFieldParams& p) {
-    memset(&p, 0, sizeof p);
-    p.R = b->R;
-    p.coef = b->d_coef;
-    p.flag = b->rep[0]->dflag;
+// The batched stencil over all replicas, each reading its mesh buffer
+// dmesh ^ flip: one tiled launch per distinct tile shape among the replicas
+// (each replica keeps the shape the autotuner picked for its mesh).
+void launch_batch_fields(hpf_batch* b, int flip) {
+    const int S = b->rep[0]->S;
+    std::vector<int> shapes;
+    for (int t : b->rep_tile)
+        if (std::find(shapes.begin(), shapes.end(), t) == shapes.end()) shapes.push_back(t);
+    for (int t : shapes) {
+        TiledFieldParams p;
+        memset(&p, 0, sizeof p);
+        p.flag = b->rep[0]->dflag;
+        for (int r = 0; r < b->R; ++r) {
+            if (b->rep_tile[r] != t) continue;
+            hpf_ctx* c = b->rep[r];
+            fill_field_rep(c, t, c->dmesh ^ flip, p.rep[p.R++], p.blocks);
+        }
+        launch_field_tiled(p, S, t, b->stream);
+    }
+}
+
+// Tile shape per replica: every candidate timed on the replica's own mesh.
+void batch_autotune(hpf_batch* b) {
+    const int S = b->rep[0]->S;
+    b->rep_tile.assign(b->R, 0);
     for (int r = 0; r < b->R; ++r) {
         hpf_ctx* c = b->rep[r];
-        fill_field_rep(c, tile, c->dmesh ^ flip, p.rep[r], p.blocks);
+        b->rep_tile[r] = autotune_tile<TiledFieldParams>(b->stream, S, [&](int t, TiledFieldParams& p) {
+            memset(&p, 0, sizeof p);
+            p.flag = c->dflag;
+            p.R = 1;
+            fill_field_rep(c, t, c->dmesh, p.rep[0], p.blocks);
+        });
     }
 }
 
@@ -1408,15 +1430,10 @@ hpf_status batch_refresh(hpf_batch* b) {
         }
         return HPF_OK;
     }
-    if (b->field_tile < 0)
-        b->field_tile = autotune_tile<TiledFieldParams>(b->stream, c0->S, [&](int t, TiledFieldParams& p) {
-            fill_batch_field(b, t, 0, p);
-        });
+    if (b->rep_tile.empty()) batch_autotune(b);
     {
         StageScope sc(c0, HPF_STAGE_FIELD, 1);
-        TiledFieldParams p;
-        fill_batch_field(b, b->field_tile, 0, p);
-        launch_field_tiled(p, c0->S, b->field_tile, b->stream);
+        launch_batch_fields(b, 0);
     }
     LAUNCH_CHECK(c0);
     for (auto* c : b->rep) {
@@ -1504,9 +1521,7 @@ hpf_status batch_capture(hpf_batch* b) {
     cudaGraph_t graph = nullptr;
     CUDA_TRY(c0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     for (int half = 0; half < 2; ++half) {
-        TiledFieldParams fp;
-        fill_batch_field(b, b->field_tile, half, fp);
-        launch_field_tiled(fp, c0->S, b->field_tile, b->stream);
+        launch_batch_fields(b, half);
         BatchStepParams sp;
         fill_step_params(b, sp, fe, true);
         sp.cur = c0->cur ^ half;
@@ -1646,7 +1661,7 @@ hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
     while (left > 0) {
         // steady state: replay two captured periods at a time
         const bool aligned = c0->step % fe == 0 && fe <= 64;
-        bool steady = aligned && b->use_graphs && left >= 2 * fe && b->field_tile >= 0;
+        bool steady = aligned && b->use_graphs && left >= 2 * fe && !b->rep_tile.empty();
         for (auto* c : b->rep)
             steady = steady && c->mesh_step == c->step && c->field_step != c->step &&
                      c->cur == c0->cur && c->dmesh == c0->dmesh;
@@ -1859,7 +1874,7 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
         if (have_hist && !skip) {
             StageScope sc(c, HPF_STAGE_OTHER, 6);
             launch_mesh_to_phi(Dt, SM, c->ec.phi_c, L->x + SM, c->stream);
-            prop_predict(prop, L->x, L->dphi, c->stream);
+            prop_predict(prop, L->x, L->dphi, c->stream, c->dflag);
         }
         LAUNCH_CHECK(c);
         bool judged = false;

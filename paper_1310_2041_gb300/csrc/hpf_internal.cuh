@@ -194,6 +194,7 @@ struct BatchFieldParams {
 // Tiled field stencil: one record per replica (a context is a batch of one).
 struct TiledFieldRep {
     CUtensorMap tmap;  // over D (valid when use_tma)
+    const FieldCoef* coef;  // this replica's stencil coefficients (device memory)
     MeshGeom g;
     const long long* D;
     float4* G;
@@ -209,7 +210,6 @@ template <int kCap>
 struct TiledFieldParamsT {
     int R;
     int blocks;
-    const FieldCoef* coef;  // [R] in device memory
     int* flag;
     TiledFieldRep rep[kCap];
 };
@@ -864,7 +864,8 @@ int energy_partials_needed(int n, int nodes, int S);
 
 // learned density propagator (the network lives in k_prop.cu)
 bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);
-void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s);
+// flag: device status word for a tensor-core wait that gives up (kFlagTimeout)
+void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag);
 void launch_mesh_to_phi(const unsigned long long* D, long long n, double phi_c, float* phi,
                         cudaStream_t s);
 void launch_mesh_predict(const unsigned long long* D_base, const float* dphi, long long n,

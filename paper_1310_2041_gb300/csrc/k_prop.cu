@@ -2,16 +2,14 @@
 // (4 -> 16 -> 16 -> 2 channels, 3x3x3 kernels, SiLU) on BF16 tensor cores.
 //
 // Activations are channels-last BF16 [V][16] (channels padded to 16 with
-// zeros; V = Mz My Mx, x fastest).  A convolution is an implicit GEMM: a CTA
-// owns a 8 x 8 x 2 tile of 128 output voxels, stages the periodic
-// 10 x 10 x 4 input box in shared memory, and for each of the 27 kernel
-// offsets multiplies the box shifted by that offset (16 voxels x 16 input
-// channels per warp, read with ldmatrix) by the offset's 16 x 16 weight block
-// with mma.sync m16n8k16 (BF16 in, FP32 accumulate).  The data-gradient pass
-// is the same kernel with flipped and transposed weights; the weight
-// gradient reduces over voxels on the tensor cores (ldmatrix.trans operands)
-// and accumulates in registers over many tiles before one FP32 atomic add
-// per weight and CTA.
+// zeros; V = Mz My Mx, x fastest).  The forward and data-gradient
+// convolutions run on the fifth-generation tensor cores (k_conv_tc: tcgen05
+// MMAs from shared-memory descriptors into tensor-memory accumulators, one
+// MMA per input plane and in-plane offset feeding three output planes); the
+// first layer's four input channels enter as an x-im2col, so its three x
+// offsets share one K = 16 step.  The weight gradient reduces over voxels with
+// warp-level MMAs (ldmatrix.trans operands), accumulating in registers over
+// many tiles before writing one partial block per CTA.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -27,7 +25,6 @@ constexpr int kTX = 8, kTY = 8, kTZ = 8;     // output tile: one z-plane of 64 v
 constexpr int kBX = kTX + 2, kBY = kTY + 2, kBZ = kTZ + 2;
 constexpr int kBoxVox = kBX * kBY * kBZ;     // 1000 (32 000 bytes)
 constexpr int kTileVox = kTX * kTY * kTZ;    // 512
-constexpr int kMTiles = kTileVox / 16 / 8;   // 16-voxel MMA row tiles per warp (4)
 constexpr int kOffsets = 27;
 // channels of the three layers: 4 -> 16 -> 16 -> 2
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? 4 : 16; }
@@ -122,90 +119,469 @@ __device__ __forceinline__ int box_row(int lx, int ly, int lz, int o) {
 
 enum ConvMode { kHidden = 0, kLast = 1, kData = 2 };
 
-// out(n)[co] = sum_offsets sum_ci W[o][co][ci] in(n + d_o)[ci]  (+ bias, SiLU).
-// One CTA per 8 x 8 x 8 tile; warp w computes the 64 voxels of z-plane w as
-// four 16-row MMA tiles against each offset's weight fragment (loaded once
-// per offset and warp).  kN output n-tiles of 8 channels (1 for the
-// two-channel last layer).  kHidden stores the FP32 pre-activation (when
-// z_out is given) and the BF16 SiLU output; kLast and kData store FP32.
-template <int kMode, int kN>
-__global__ void __launch_bounds__(256) k_conv(const __nv_bfloat16* __restrict__ in,
-                                              const __nv_bfloat16* __restrict__ W,
-                                              const float* __restrict__ bias,
-                                              float* __restrict__ z_out,
-                                              __nv_bfloat16* __restrict__ act_out,
-                                              float* __restrict__ f_out, PropGeom g) {
-    __shared__ uint4 box[kBoxVox * 2];
-    __shared__ uint4 sw[kOffsets * kPC * 2];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t box_s = saddr(box), sw_s = saddr(sw);
-    for (int e = tid; e < kOffsets * kPC * 2; e += blockDim.x)
-        cp_async16(sw_s + 16 * swz(e >> 1, e & 1), reinterpret_cast<const uint4*>(W) + e);
-    int x0, y0, z0;
-    tile_origin(g, blockIdx.x, x0, y0, z0);
-    load_box(in, g, x0, y0, z0, box);
-    cp_async_wait_all();
-    __syncthreads();
+// ------------------------------------------------------------------ tcgen05 convolution
+//
+// The forward and data-gradient convolutions on the fifth-generation tensor
+// cores.  A CTA (one warpgroup) works on tiles of 8 x 16 x 4 voxels; a
+// z-plane of a tile is 128 voxels = the 128 rows of one MMA (eight
+// x-consecutive voxels per 8-row core-matrix group, one group per y row).
+// The periodic 10 x 18 x 6 input box sits in shared memory as two planes of
+// 8-channel halves (16 bytes per voxel): the canonical K-major layout without
+// swizzle, so the box shifted by any in-plane offset (dy, dx) is a matrix
+// descriptor that starts at the shifted voxel (K halves one plane apart,
+// 8-row groups one box row apart).
+//
+// Each input plane z (box planes -1 .. 4 of the tile) feeds the output planes
+// z + 1, z and z - 1 through the kernel offsets dz = -1, 0, +1 (an output
+// voxel n sums W[d] in(n + d)).  So the weights of one in-plane offset are
+// stacked for the three dz values as N = 3 x 16 columns, and the accumulators
+// of the four output planes sit in tensor memory in reverse order, 16 columns
+// each: the three planes an input plane feeds are then 48 consecutive columns,
+// and one tcgen05.mma (M 128, N 48, K 16, BF16 in, FP32 accumulate) per input
+// plane and in-plane offset updates all three; at the tile's first and last
+// input planes fewer planes exist (N = 16 or 32).  That is 6 x 9 MMAs per
+// tile instead of 27 x 4 of width 16, and every MMA reads its A operand once
+// for three output planes.  The two-channel last layer keeps 2 columns per
+// plane and N = 16: its weight rows past the 6 real ones are zero, so the
+// columns an MMA spills into are only added zeros.  The accumulators are
+// cleared by tcgen05.st before the tile's MMAs, which then all accumulate.
+//
+// One thread issues the MMAs and commits them to an mbarrier; the box of
+// the next tile is loaded and the epilogue of the previous tile (tcgen05.ld,
+// bias, SiLU, BF16 or FP32 stores) runs meanwhile: two box buffers and two
+// tensor-memory accumulator sets.  Waits are bounded (kTcWaitLimit polls);
+// a wait that gives up sets kFlagTimeout and the CTA stops after releasing
+// its tensor memory.
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;
+constexpr int kTcBX = kTcX + 2, kTcBY = kTcY + 2, kTcBZ = kTcZ + 2;
+constexpr int kTcPlane = kTcBX * kTcBY;   // box voxels per z-plane
+constexpr int kTcBox = kTcPlane * kTcBZ;  // 1080 voxels per channel half
+constexpr int kTcInPlane = 9;             // in-plane offsets (dy, dx)
+constexpr int kTcRows16 = 48;             // B rows per in-plane offset: (dz, co)
+constexpr int kTcRows2 = 24;              // 6 real rows (dz, co < 2), then zeros
+constexpr int kTcCols = 64;               // accumulator columns per set: 4 planes x 16
+constexpr unsigned kTcWaitLimit = 1u << 22;
+constexpr int kTcThreads = 256;          // two warps per tensor-memory lane quarter
+constexpr int kTcWCopies = 8;            // replicas of each packed weight image (spread L2 reads)
+// shared memory of a CTA with kBuf box buffers (and kBuf accumulator sets)
+constexpr size_t tc_smem_bytes(int kBuf) {
+    return sizeof(uint4) * ((size_t)kBuf * 2 * kTcBox + 2 * kTcInPlane * kTcRows16) + 64;
+}
 
-    // A rows: lane -> voxel (lane % 16) of each row tile, channel half (lane / 16)
-    const int r = lane & 15, ch_half = lane >> 4;
-    // B rows: lane -> output channel (lane & 7) + 8 (lane >= 16), input half ((lane >> 3) & 1)
-    const int b_n = (lane & 7) + ((lane >> 4) << 3), b_half = (lane >> 3) & 1;
-    const int gq = lane >> 2, q = lane & 3;
-    float acc[kMTiles][kN][4];
+// The weight images of the tensor-core convolutions, [copy][half][in-plane
+// offset][B row]: 0 first layer (x-im2col, kIP 3), 1 second layer, 2 last
+// layer (kCB 2), 3 and 4 the data gradients of the second and last layers.
+constexpr int kTcImages = 5;
+__host__ __device__ constexpr int tc_image_cb(int k) { return k == 2 ? 2 : 16; }
+__host__ __device__ constexpr int tc_image_ip(int k) { return k == 0 ? 3 : 9; }
+__host__ __device__ constexpr int tc_image_words(int k) {   // uint4 per copy
+    return 2 * tc_image_ip(k) * (tc_image_cb(k) == 16 ? kTcRows16 : kTcRows2);
+}
+__host__ __device__ constexpr int tc_image_offset(int k) {  // uint4, all copies
+    return k == 0 ? 0 : tc_image_offset(k - 1) + kTcWCopies * tc_image_words(k - 1);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all in 16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_origin(const PropGeom& g, int t, int& x0, int& y0, int& z0) {
+    const int tx = (g.mx + kTcX - 1) / kTcX, ty = (g.my + kTcY - 1) / kTcY;
+    x0 = (t % tx) * kTcX;
+    y0 = ((t / tx) % ty) * kTcY;
+    z0 = (t / (tx * ty)) * kTcZ;
+}
+
+// Box of the tile at (x0, y0, z0) into the buffer at shared address box_s:
+// 16-byte asynchronous copies of channel halves, [half][voxel].
+// i in [-1, m + box extent]: one period at most when m spans the box extent
+// (near), the general remainder otherwise.
+__device__ __forceinline__ int tc_wrap(int i, int m, bool near) {
+    if (near) return i < 0 ? i + m : (i >= m ? i - m : i);
+    return pwrap(i, m);
+}
+
+// A thread's share of the box copies: elements e = tid + kTcThreads k of the
+// [voxel][half] order, their box coordinates and shared-memory offsets, the
+// same for every tile.
+constexpr int kTcSlots = (kTcBox * 2 + kTcThreads - 1) / kTcThreads;
+
+struct TcSlots {
+    int c[kTcSlots];       // bx | by << 8 | bz << 16 | half << 24, or -1
+    uint32_t s[kTcSlots];  // byte offset in a box buffer
+};
+
+__device__ __forceinline__ void tc_slots(TcSlots& sl) {
 #pragma unroll
-    for (int i = 0; i < kMTiles; ++i)
+    for (int k = 0; k < kTcSlots; ++k) {
+        const int e = threadIdx.x + kTcThreads * k;
+        const int v = e >> 1, half = e & 1;
+        const int bx = v % kTcBX, by = (v / kTcBX) % kTcBY, bz = v / kTcPlane;
+        sl.c[k] = e < kTcBox * 2 ? (bx | (by << 8) | (bz << 16) | (half << 24)) : -1;
+        sl.s[k] = (uint32_t)sizeof(uint4) * (uint32_t)(half * kTcBox + v);
+    }
+}
+
+__device__ __forceinline__ void tc_load_box(const __nv_bfloat16* __restrict__ in,
+                                            const PropGeom& g, int x0, int y0, int z0,
+                                            uint32_t box_s, const TcSlots& sl, bool near) {
 #pragma unroll
-        for (int j = 0; j < kN; ++j)
+    for (int k = 0; k < kTcSlots; ++k) {
+        const int c = sl.c[k];
+        if (c < 0) continue;
+        const int gx = tc_wrap(x0 - 1 + (c & 0xff), g.mx, near);
+        const int gy = tc_wrap(y0 - 1 + ((c >> 8) & 0xff), g.my, near);
+        const int gz = tc_wrap(z0 - 1 + ((c >> 16) & 0xff), g.mz, near);
+        const int gv = (gz * g.my + gy) * g.mx + gx;
+        cp_async16(box_s + sl.s[k], in + (size_t)gv * kPC + 8 * (c >> 24));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_zero_cols16(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+
+// Epilogue of one output plane: the warp's 32 accumulator rows (lanes 32w ..)
+// from columns col .. col + kCB - 1, voxel (x0 + row % 8, y0 + row / 8, z).
+template <int kMode, int kCB>
+__device__ __forceinline__ void tc_epilogue(uint32_t tcol, const PropGeom& g, int x0, int y0,
+                                            int z, const float* __restrict__ bias,
+                                            float* __restrict__ z_out,
+                                            __nv_bfloat16* __restrict__ act_out,
+                                            float* __restrict__ f_out) {
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 3;  // lane quarter
+    const uint32_t taddr = tcol + ((uint32_t)(32 * w) << 16);
+    float acc[16];
+    if (kCB == 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-    // voxel (lx, ly0 + 2i, w) for row tile i
-    const int lx = r % kTX, ly0 = r / kTX;
-#pragma unroll 9
-    for (int o = 0; o < kOffsets; ++o) {
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4(sw_s + 16 * swz(o * kPC + b_n, b_half), b0, b1, b2, b3);
-        const int row0 = box_row(lx, ly0, w, o);
+        for (int c = 0; c < 16; ++c) acc[c] = __uint_as_float(r[c]);
+    } else {
+        uint32_t r0, r1;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                     : "=r"(r0), "=r"(r1)
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        acc[0] = __uint_as_float(r0);
+        acc[1] = __uint_as_float(r1);
+    }
+    const int row = 32 * w + lane;
+    const int X = x0 + (row & 7), Y = y0 + (row >> 3);
+    if (X >= g.mx || Y >= g.my || z >= g.mz) return;
+    const size_t gv = ((size_t)z * g.my + Y) * g.mx + X;
+    if (kMode != kData) {
 #pragma unroll
-        for (int i = 0; i < kMTiles; ++i) {
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4(box_s + 16 * swz(row0 + 2 * i * kBX, ch_half), a0, a1, a2, a3);
-            mma_bf16(acc[i][0], a0, a1, a2, a3, b0, b1);
-            if (kN > 1) mma_bf16(acc[i][kN - 1], a0, a1, a2, a3, b2, b3);
+        for (int c = 0; c < kCB; ++c) acc[c] += bias[c];
+    }
+    if (kMode == kHidden) {
+        if (z_out) {
+            float4* zo = reinterpret_cast<float4*>(z_out + gv * kPC);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
+        __nv_bfloat162 h[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float a = acc[2 * c], b = acc[2 * c + 1];
+            h[c] = __floats2bfloat162_rn(__fdividef(a, 1.0f + __expf(-a)),
+                                         __fdividef(b, 1.0f + __expf(-b)));
+        }
+        uint4* ao = reinterpret_cast<uint4*>(act_out + gv * kPC);
+        ao[0] = reinterpret_cast<uint4*>(h)[0];
+        ao[1] = reinterpret_cast<uint4*>(h)[1];
+    } else if (kCB == 2) {
+        *reinterpret_cast<float2*>(f_out + gv * kPC) = make_float2(acc[0], acc[1]);
+    } else {
+        float4* fo = reinterpret_cast<float4*>(f_out + gv * kPC);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            fo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
-    float b_lo[kN], b_hi[kN];
-#pragma unroll
-    for (int j = 0; j < kN; ++j) {
-        b_lo[j] = kMode != kData ? bias[8 * j + 2 * q] : 0.f;
-        b_hi[j] = kMode != kData ? bias[8 * j + 2 * q + 1] : 0.f;
+}
+
+// W: the layer's padded BF16 weights [3 kIP][16 out][16 in] (forward or data
+// gradient), offset index dz_index * kIP + in-plane offset; kCB output
+// channels per plane (16, or 2 for the last layer).  kIP = 9: in-plane
+// offsets (dy, dx), K = 16 input channels.  kIP = 3: in-plane offsets dy only;
+// the input is the x-im2col of a 4-channel layer (K index (dx + 1) * 4 + ci,
+// see k_pack_input) and the weights follow that K order.
+template <int kMode, int kCB, int kIP, int kBuf>
+__global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1) k_conv_tc(const __nv_bfloat16* __restrict__ in,
+                                                 const uint4* __restrict__ Wp,
+                                                 const float* __restrict__ bias,
+                                                 float* __restrict__ z_out,
+                                                 __nv_bfloat16* __restrict__ act_out,
+                                                 float* __restrict__ f_out, PropGeom g,
+                                                 int n_tiles, int* __restrict__ flag) {
+    constexpr int kRows = kCB == 16 ? kTcRows16 : kTcRows2;
+    extern __shared__ __align__(128) uint4 tc_smem[];
+    uint4* boxp = tc_smem;                    // [buffer][channel half][kTcBox]
+    uint4* wp = tc_smem + kBuf * 2 * kTcBox;  // [channel half][in-plane offset][kRows]
+    unsigned long long* bar =
+        reinterpret_cast<unsigned long long*>(wp + 2 * kTcInPlane * kTcRows16);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 3);
+    const int tid = threadIdx.x, w = tid >> 5;
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tmem_slot)),
+                     "r"(kBuf * kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // epilogue: lane holds voxels gq, gq + 8 of each row tile and channels 8j + 2q, + 1
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[1])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[2])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // B, pre-packed in its shared-memory layout (tc_pack_weights): one bulk
+    // copy from one of kTcWCopies replicas of the image in global memory
+    constexpr uint32_t kWBytes = (uint32_t)sizeof(uint4) * 2 * kIP * kRows;
+    if (tid == 0) {
+        const uint4* src = Wp + (size_t)(blockIdx.x % kTcWCopies) * (kWBytes / sizeof(uint4));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         saddr(&bar[2])),
+                     "r"(kWBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(saddr(wp)),
+            "l"(src), "r"(kWBytes), "r"(saddr(&bar[2]))
+            : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t lbo_a = sizeof(uint4) * kTcBox, sbo_a = sizeof(uint4) * kTcBX;
+    const uint32_t lbo_b = sizeof(uint4) * kIP * kRows, sbo_b = sizeof(uint4) * 8;
+    const uint32_t box0 = saddr(boxp), wp0 = saddr(wp);
+    const bool near = g.mx >= kTcBY && g.my >= kTcBY && g.mz >= kTcBY;
+    TcSlots sl;
+    tc_slots(sl);
+    uint32_t phase[2] = {0u, 0u};
+    int px0 = 0, py0 = 0, pz0 = 0;  // origin of the previous tile
+    int i = 0;
+    bool failed = false;
+    bool w_ok = true;  // the weights arrived (thread 0)
+    // the box of a tile is loaded one iteration ahead, into the buffer that the
+    // MMAs of the tile before the previous one have finished reading
+    int t = blockIdx.x;
+    if (t < n_tiles) {
+        int x0, y0, z0;
+        tc_origin(g, t, x0, y0, z0);
+        tc_load_box(in, g, x0, y0, z0, box0, sl, near);
+    }
+    for (; t < n_tiles; t += gridDim.x, ++i) {
+        if (kBuf == 1 && i > 0) break;  // one tile per CTA (the grid covers the tiles)
+        const int b = kBuf == 1 ? 0 : (i & 1);
+        int x0, y0, z0;
+        tc_origin(g, t, x0, y0, z0);
+        if (i > 0) {
+            // the MMAs of the previous tile: done before its box buffer is refilled
+            // and before its epilogue
+            const bool ok = tc_wait(saddr(&bar[b ^ 1]), phase[b ^ 1]);
+            if (__syncthreads_or(!ok)) {  // every thread takes the same branch
+                if (tid == 0) atomicOr(flag, kFlagTimeout);
+                failed = true;
+                break;
+            }
+            phase[b ^ 1] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const int tn = t + (int)gridDim.x;
+        if (kBuf > 1 && tn < n_tiles) {
+            int xn, yn, zn;
+            tc_origin(g, tn, xn, yn, zn);
+            tc_load_box(in, g, xn, yn, zn,
+                        box0 + (uint32_t)(sizeof(uint4) * 2 * kTcBox) * (b ^ 1), sl, near);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        const uint32_t boxb = box0 + (uint32_t)(sizeof(uint4) * 2 * kTcBox) * b;
+        // accumulator set b was last read by the epilogue of tile i - 2
+        const uint32_t accb = tmem + (uint32_t)(kTcCols * b);
 #pragma unroll
-    for (int i = 0; i < kMTiles; ++i)
+        for (int c = 0; c < kTcCols / 2; c += 16)
+            tc_zero_cols16(accb + (w >> 2) * (kTcCols / 2) + c + ((uint32_t)(32 * (w & 3)) << 16));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0 && i == 0) {
+            // the bulk copy of the weights (issued in the prologue)
+            w_ok = tc_wait(saddr(&bar[2]), 0u);
+            if (!w_ok) atomicOr(flag, kFlagTimeout);
+        }
+        if (tid == 0 && w_ok) {
+            // descriptors: the start-address field is the low 14 bits (16-byte
+            // units); offsets inside shared memory are added to it directly
+            const uint64_t a0 = umma_smem_desc(boxb, lbo_a, sbo_a);
+            const uint64_t b0 = umma_smem_desc(wp0, lbo_b, sbo_b);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            int vx, vy, vz;
-            warp_voxel(kMTiles * w + i, gq + 8 * half, vx, vy, vz);
-            const int X = x0 + vx, Y = y0 + vy, Z = z0 + vz;
-            if (X >= g.mx || Y >= g.my || Z >= g.mz) continue;
-            const size_t gv = ((size_t)Z * g.my + Y) * g.mx + X;
+            for (int z = -1; z <= kTcZ; ++z) {
+                const int pf = z + 1 < kTcZ - 1 ? z + 1 : kTcZ - 1;  // first plane fed
+                const int pl = z - 1 > 0 ? z - 1 : 0;                 // last plane fed
+                const int N = kCB == 16 ? 16 * (pf - pl + 1) : 16;
+                const uint32_t idesc = umma_idesc_bf16(128, N);
+                const uint32_t d = accb + (uint32_t)(kCB * (kTcZ - 1 - pf));
+                const int row0 = kCB * (z - pf + 1);  // B row of the first plane's dz
 #pragma unroll
-            for (int j = 0; j < kN; ++j) {
-                const int ch = 8 * j + 2 * q;
-                const float v0 = acc[i][j][2 * half] + b_lo[j];
-                const float v1 = acc[i][j][2 * half + 1] + b_hi[j];
-                if (kMode == kHidden) {
-                    if (z_out)
-                        *reinterpret_cast<float2*>(z_out + gv * kPC + ch) = make_float2(v0, v1);
-                    const float s0 = v0 / (1.0f + expf(-v0)), s1 = v1 / (1.0f + expf(-v1));
-                    *reinterpret_cast<__nv_bfloat162*>(act_out + gv * kPC + ch) =
-                        __floats2bfloat162_rn(s0, s1);
-                } else {
-                    *reinterpret_cast<float2*>(f_out + gv * kPC + ch) = make_float2(v0, v1);
+                for (int o9 = 0; o9 < kIP; ++o9) {
+                    const int dy = kIP == 9 ? o9 / 3 - 1 : o9 - 1;
+                    const int dx = kIP == 9 ? o9 % 3 - 1 : 0;
+                    const int v0 = ((z + 1) * kTcBY + (1 + dy)) * kTcBX + (1 + dx);
+                    const uint64_t ad = a0 + (uint64_t)v0;
+                    const uint64_t bd = b0 + (uint64_t)(o9 * kRows + row0);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.u32 p, 1, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(idesc)
+                        : "memory");
                 }
             }
         }
+        if (tid == 0)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    saddr(&bar[b]))
+                : "memory");
+        if (i > 0) {
+            // epilogue of the previous tile while this one is on the tensor cores
+            const uint32_t accp = tmem + (uint32_t)(kTcCols * (b ^ 1));
+#pragma unroll 1
+            for (int p = 2 * (w >> 2); p < 2 * (w >> 2) + 2; ++p)
+                tc_epilogue<kMode, kCB>(accp + (uint32_t)(kCB * (kTcZ - 1 - p)), g, px0, py0,
+                                        pz0 + p, bias, z_out, act_out, f_out);
+        }
+        px0 = x0;
+        py0 = y0;
+        pz0 = z0;
+    }
+    if (!failed && i > 0) {
+        const int pb = (i - 1) & 1;
+        const bool ok = tc_wait(saddr(&bar[pb]), phase[pb]);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(flag, kFlagTimeout);
+            failed = true;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t accp = tmem + (uint32_t)(kTcCols * pb);
+#pragma unroll 1
+            for (int p = 2 * (w >> 2); p < 2 * (w >> 2) + 2; ++p)
+                tc_epilogue<kMode, kCB>(accp + (uint32_t)(kCB * (kTcZ - 1 - p)), g, px0, py0,
+                                        pz0 + p, bias, z_out, act_out, f_out);
+        }
+    }
+    if (failed) {
+        // MMAs of the last tiles may still be in flight: one more bounded wait on
+        // each accumulator set before the tensor memory is released
+        tc_wait(saddr(&bar[0]), phase[0]);
+        if (kBuf > 1) tc_wait(saddr(&bar[1]), phase[1]);
+    }
+    if (tid == 0 && (!w_ok || i == 0)) tc_wait(saddr(&bar[2]), 0u);  // the weights' bulk copy
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kBuf * kTcCols)
+                     : "memory");
+}
+
+int conv_tc_tiles(const PropGeom& g) {
+    return ((g.mx + kTcX - 1) / kTcX) * ((g.my + kTcY - 1) / kTcY) * ((g.mz + kTcZ - 1) / kTcZ);
+}
+
+template <int kMode, int kCB, int kIP>
+void set_tc_attr() {
+    cudaFuncSetAttribute(k_conv_tc<kMode, kCB, kIP, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(1));
+}
+
+// One tile per CTA, single-buffered (48 KB of shared memory and 64
+// tensor-memory columns per CTA, four CTAs per SM overlap one another's box
+// loads, MMAs and epilogues); attributes set once per device.
+void conv_tc_setup() {
+    static std::once_flag once[64];
+    once_per_device(once, [] {
+        set_tc_attr<kHidden, 16, 3>();
+        set_tc_attr<kHidden, 16, 9>();
+        set_tc_attr<kLast, 2, 9>();
+        set_tc_attr<kData, 16, 9>();
+        cudaGetLastError();
+    });
+}
+
+// Convolution with weight image k of the packed images tcw (tc_pack_weights).
+template <int kMode, int kCB, int kIP = 9>
+void launch_conv_tc(const __nv_bfloat16* in, const uint4* tcw, int k, const float* bias,
+                    float* z_out, __nv_bfloat16* act_out, float* f_out, const PropGeom& g,
+                    int* flag, cudaStream_t s) {
+    conv_tc_setup();
+    const int n = conv_tc_tiles(g);
+    k_conv_tc<kMode, kCB, kIP, 1><<<n, kTcThreads, tc_smem_bytes(1), s>>>(
+        in, tcw + tc_image_offset(k), bias, z_out, act_out, f_out, g, n, flag);
+}
+
+// Weight image k in the B layout of k_conv_tc, kTcWCopies times: from the
+// padded BF16 weights W [3 kIP][16 out][16 in] (offset dz_index * kIP +
+// in-plane offset), row n = dz_index * kCB + out channel, zeros past 3 kCB.
+__global__ void k_pack_tc_image(const __nv_bfloat16* __restrict__ W, int k,
+                                uint4* __restrict__ tcw) {
+    const int cb = tc_image_cb(k), ip = tc_image_ip(k), rows = cb == 16 ? kTcRows16 : kTcRows2;
+    const int per = tc_image_words(k);
+    const uint4* W4 = reinterpret_cast<const uint4*>(W);
+    uint4* out = tcw + tc_image_offset(k);
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        const int half = e / (ip * rows), rest = e % (ip * rows);
+        const int o9 = rest / rows, n = rest % rows;
+        const uint4 v = n < 3 * cb ? W4[(((n / cb) * ip + o9) * kPC + n % cb) * 2 + half]
+                                   : make_uint4(0u, 0u, 0u, 0u);
+        for (int c = 0; c < kTcWCopies; ++c) out[c * per + e] = v;
+    }
 }
 
 // dW[o][ci][co] = sum_n in(n + d_o)[ci] gz(n)[co]: a voxel reduction on the
@@ -291,18 +667,40 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
 // current phi(t) per species, formed in FP32 before the BF16 rounding (a
 // one-step change of about 1e-2 is far below the BF16 spacing of phi ~ 0.5),
 // zero-padded to 16.
-__global__ void k_pack_input(const float* __restrict__ x, int V, float scale,
-                             __nv_bfloat16* __restrict__ out) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
+//
+// out_x: the same four channels as the x-im2col input of the first layer's
+// tensor-core convolution, K index (dx + 1) * 4 + ci holding channel ci of
+// voxel (x + dx, y, z) (periodic in x) for dx = -1, 0, 1, zeros from 12 on.
+__device__ __forceinline__ void input_features(const float* __restrict__ x, int V, int v,
+                                               float scale, float (&f)[4]) {
     const float a0 = x[v], b0 = x[(size_t)V + v];
     const float a1 = x[(size_t)2 * V + v], b1 = x[(size_t)3 * V + v];
-    const float f[4] = {scale * (a1 - a0), scale * (b1 - b0), a1, b1};
-    __nv_bfloat16 vals[kPC];
+    f[0] = scale * (a1 - a0);
+    f[1] = scale * (b1 - b0);
+    f[2] = a1;
+    f[3] = b1;
+}
+
+__global__ void k_pack_input(const float* __restrict__ x, int V, int mx, float scale,
+                             __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_x) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int xi = v % mx;
+    const int vm = v - xi + (xi == 0 ? mx - 1 : xi - 1), vp = v - xi + (xi == mx - 1 ? 0 : xi + 1);
+    float f[3][4];
+    input_features(x, V, vm, scale, f[0]);
+    input_features(x, V, v, scale, f[1]);
+    input_features(x, V, vp, scale, f[2]);
+    __nv_bfloat16 vals[kPC], cols[kPC];
 #pragma unroll
-    for (int c = 0; c < kPC; ++c) vals[c] = __float2bfloat16_rn(c < 4 ? f[c] : 0.f);
+    for (int c = 0; c < kPC; ++c) {
+        vals[c] = __float2bfloat16_rn(c < 4 ? f[1][c] : 0.f);
+        cols[c] = __float2bfloat16_rn(c < 12 ? f[c >> 2][c & 3] : 0.f);
+    }
     reinterpret_cast<uint4*>(out + (size_t)v * kPC)[0] = reinterpret_cast<uint4*>(vals)[0];
     reinterpret_cast<uint4*>(out + (size_t)v * kPC)[1] = reinterpret_cast<uint4*>(vals)[1];
+    reinterpret_cast<uint4*>(out_x + (size_t)v * kPC)[0] = reinterpret_cast<uint4*>(cols)[0];
+    reinterpret_cast<uint4*>(out_x + (size_t)v * kPC)[1] = reinterpret_cast<uint4*>(cols)[1];
 }
 
 // The predicted change: the network's two output channels divided by scale.
@@ -389,8 +787,11 @@ __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restri
 
 // Packed FP32 parameters -> padded BF16 forward weights [o][co][ci], data-
 // gradient weights [o'][ci][co] (o' = the opposite offset) and FP32 biases.
+// wx: the first layer's weights for its x-im2col input, [dz_index * 3 + dy_index]
+// [co][K = (dx + 1) * 4 + ci], zeros from K = 12 on.
 __global__ void k_pack_weights(const float* __restrict__ params, __nv_bfloat16* __restrict__ wf,
-                               __nv_bfloat16* __restrict__ wb, float* __restrict__ bias) {
+                               __nv_bfloat16* __restrict__ wb, float* __restrict__ bias,
+                               __nv_bfloat16* __restrict__ wx) {
     const int layer = blockIdx.x;
     const int ci_n = layer_in(layer), co_n = layer_out(layer);
     int off = 0;
@@ -410,6 +811,14 @@ __global__ void k_pack_weights(const float* __restrict__ params, __nv_bfloat16* 
         b[e] = __float2bfloat16_rn(vb);
     }
     if (threadIdx.x < kPC) bias[layer * kPC + threadIdx.x] = threadIdx.x < co_n ? bl[threadIdx.x] : 0.f;
+    if (layer == 0) {
+        for (int e = threadIdx.x; e < 9 * kPC * kPC; e += blockDim.x) {
+            const int o = e / (kPC * kPC), co = (e / kPC) % kPC, k = e % kPC;
+            const int dzi = o / 3, dyi = o % 3, dxi = k >> 2, ci = k & 3;
+            const float v = k < 12 ? Wl[((dzi * 9 + dyi * 3 + dxi) * ci_n + ci) * co_n + co] : 0.f;
+            wx[e] = __float2bfloat16_rn(v);
+        }
+    }
 }
 
 // Padded weight / bias gradients -> packed gradient vector.
@@ -551,6 +960,9 @@ struct hpf_prop {
     float* bpart = nullptr;       // bias-gradient partials [152][16]
     double* lpart = nullptr;      // loss partials [ceil(V / 256)]
     __nv_bfloat16* act[4] = {};   // input, h1, h2, and a gradient buffer [V][16]
+    __nv_bfloat16* act_x = nullptr;  // the input as x-im2col [V][16] (first layer)
+    __nv_bfloat16* wx = nullptr;     // first-layer weights for it [9][16][16]
+    uint4* tcw = nullptr;            // packed weight images of the tensor-core convolutions
     float* z[2] = {};             // pre-activations of layers 1, 2 [V][16]
     float* fbuf = nullptr;        // FP32 [V][16]: output / data gradient
     float* xin = nullptr;         // staging of the planar input [4][V]
@@ -558,6 +970,8 @@ struct hpf_prop {
     float* yout = nullptr;        // planar output [2][V]
     double* loss = nullptr;
     double* h_loss = nullptr;
+    int* flag = nullptr;          // device status bits of the tensor-core waits
+    int* h_flag = nullptr;        // pinned mirror
     int grid_wgrad = 0;
 };
 
@@ -577,21 +991,31 @@ hpf_status prop_copy_out(hpf_prop* p, void* dst, const void* src, size_t bytes) 
     return HPF_OK;
 }
 
+// The padded BF16 weights, biases and the tensor-core weight images from the
+// FP32 parameters.
+void pack_all_weights(hpf_prop* p, cudaStream_t s) {
+    const size_t wl = (size_t)kOffsets * kPC * kPC;
+    k_pack_weights<<<3, 256, 0, s>>>(p->params, p->wf, p->wb, p->bias, p->wx);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wx, 0, p->tcw);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wf + wl, 1, p->tcw);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wf + 2 * wl, 2, p->tcw);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + wl, 3, p->tcw);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + 2 * wl, 4, p->tcw);
+}
+
 // Forward pass of planar input x [4][V] (device); leaves the FP32 output in
 // fbuf.  With keep_z the pre-activations are stored for a backward pass.
-void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s) {
+void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s, int* flag) {
     const int V = p->g.V, tb = (V + 255) / 256;
-    const size_t wl = (size_t)kOffsets * kPC * kPC;
-    k_pack_input<<<tb, 256, 0, s>>>(x, V, p->scale, p->act[0]);
-    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[0], p->wf, p->bias,
-                                                   keep_z ? p->z[0] : nullptr, p->act[1], nullptr,
-                                                   p->g);
-    k_conv<kHidden, 2><<<p->g.tiles, 256, 0, s>>>(p->act[1], p->wf + wl, p->bias + kPC,
-                                                   keep_z ? p->z[1] : nullptr, p->act[2], nullptr,
-                                                   p->g);
-    // two output channels: one n-tile (channels 8..15 of fbuf are not written)
-    k_conv<kLast, 1><<<p->g.tiles, 256, 0, s>>>(p->act[2], p->wf + 2 * wl, p->bias + 2 * kPC,
-                                                 nullptr, nullptr, p->fbuf, p->g);
+    k_pack_input<<<tb, 256, 0, s>>>(x, V, p->g.mx, p->scale, p->act[0], p->act_x);
+    // first layer: three in-plane offsets over the x-im2col input
+    launch_conv_tc<kHidden, 16, 3>(p->act_x, p->tcw, 0, p->bias, keep_z ? p->z[0] : nullptr,
+                                   p->act[1], nullptr, p->g, flag, s);
+    launch_conv_tc<kHidden, 16>(p->act[1], p->tcw, 1, p->bias + kPC,
+                                keep_z ? p->z[1] : nullptr, p->act[2], nullptr, p->g, flag, s);
+    // two output channels (channels 2..15 of fbuf are not written)
+    launch_conv_tc<kLast, 2>(p->act[2], p->tcw, 2, p->bias + 2 * kPC, nullptr, nullptr,
+                             p->fbuf, p->g, flag, s);
 }
 
 // Loss and packed gradients (p->grads, p->loss) after prop_forward(keep_z) of
@@ -613,8 +1037,8 @@ void prop_backward(hpf_prop* p, const float* x, const float* phi_next) {
         k_sum_partials<float><<<1, 32, 0, s>>>(p->bpart, kBiasBlocks, kPC, p->db + layer * kPC);
         if (layer == 0) break;
         // the data gradient of the layer input, then through the SiLU below it
-        k_conv<kData, 2><<<p->g.tiles, 256, 0, s>>>(gbuf, p->wb + layer * wl, nullptr, nullptr,
-                                                     nullptr, p->fbuf, p->g);
+        launch_conv_tc<kData, 16>(gbuf, p->tcw, layer + 2, nullptr, nullptr, nullptr, p->fbuf,
+                                  p->g, p->flag, s);
         k_silu_backward<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(p->fbuf, p->z[layer - 1], nv,
                                                                       gbuf);
     }
@@ -628,7 +1052,7 @@ void prop_adam(hpf_prop* p, const float* grads, float lr) {
     const float c2 = (float)(1.0 - pow(0.999, (double)p->adam_t));
     k_adam<<<(p->np + 255) / 256, 256, 0, p->stream>>>(p->params, grads, p->adam_m, p->adam_v,
                                                       p->np, lr, b1, b2, 1e-8f, c1, c2);
-    k_pack_weights<<<3, 256, 0, p->stream>>>(p->params, p->wf, p->wb, p->bias);
+    pack_all_weights(p, p->stream);
 }
 
 // Planar inputs are staged into library buffers (host or device sources).
@@ -641,21 +1065,45 @@ hpf_status prop_stage(hpf_prop* p, float* dst, const float* src, size_t n) {
     return HPF_OK;
 }
 
+// The loss of the last backward pass (synchronises), with the status of the
+// tensor-core waits: HPF_ERR_TIMEOUT once if a wait gave up.
 hpf_status prop_read_loss(hpf_prop* p, double* loss) {
     if (!loss) return HPF_OK;
     if (cudaMemcpyAsync(p->h_loss, p->loss, sizeof(double), cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(p->h_flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(p->stream) != cudaSuccess) {
         cudaGetLastError();
         return HPF_ERR_CUDA;
     }
     *loss = *p->h_loss;
+    if (*p->h_flag & kFlagTimeout) {
+        cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
+        return HPF_ERR_TIMEOUT;
+    }
     return HPF_OK;
 }
 
 hpf_status prop_launched(hpf_prop* p) {
     (void)p;
     return cudaGetLastError() == cudaSuccess ? HPF_OK : HPF_ERR_CUDA;
+}
+
+// Status of the tensor-core waits of the work enqueued so far (synchronises):
+// HPF_ERR_TIMEOUT once if a wait gave up.
+hpf_status prop_flag_status(hpf_prop* p) {
+    if (cudaMemcpyAsync(p->h_flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return HPF_ERR_CUDA;
+    }
+    if (*p->h_flag & kFlagTimeout) {
+        cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
+        return HPF_ERR_TIMEOUT;
+    }
+    return HPF_OK;
 }
 
 }  // namespace
@@ -666,8 +1114,8 @@ bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g) {
     return p && p->g.mx == g.mx && p->g.my == g.my && p->g.mz == g.mz;
 }
 
-void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s) {
-    prop_forward(p, x, false, s);
+void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag) {
+    prop_forward(p, x, false, s, flag ? flag : p->flag);
     k_unpack_output<<<(p->g.V + 255) / 256, 256, 0, s>>>(p->fbuf, p->g.V, p->scale, dphi);
 }
 
@@ -724,12 +1172,18 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     e = e ? e : cudaMalloc(&p->yout, sizeof(float) * Vs * 2);
     e = e ? e : cudaMalloc(&p->loss, sizeof(double));
     e = e ? e : cudaMallocHost(&p->h_loss, sizeof(double));
+    e = e ? e : cudaMalloc(&p->flag, sizeof(int));
+    e = e ? e : cudaMalloc(&p->act_x, sizeof(__nv_bfloat16) * Vs * kPC);
+    e = e ? e : cudaMalloc(&p->wx, sizeof(__nv_bfloat16) * 9 * kPC * kPC);
+    e = e ? e : cudaMalloc(&p->tcw, sizeof(uint4) * tc_image_offset(kTcImages));
+    e = e ? e : cudaMallocHost(&p->h_flag, sizeof(int));
     if (e == cudaSuccess) {
+        cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
         // zero weights until hpf_prop_set_weights: the network predicts no change
         cudaMemsetAsync(p->params, 0, sizeof(float) * p->np, p->stream);
         cudaMemsetAsync(p->adam_m, 0, sizeof(float) * p->np, p->stream);
         cudaMemsetAsync(p->adam_v, 0, sizeof(float) * p->np, p->stream);
-        k_pack_weights<<<3, 256, 0, p->stream>>>(p->params, p->wf, p->wb, p->bias);
+        pack_all_weights(p, p->stream);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     }
@@ -765,6 +1219,11 @@ hpf_status hpf_prop_destroy(hpf_prop* p) {
     cudaFree(p->yout);
     cudaFree(p->loss);
     cudaFreeHost(p->h_loss);
+    cudaFree(p->flag);
+    cudaFreeHost(p->h_flag);
+    cudaFree(p->act_x);
+    cudaFree(p->wx);
+    cudaFree(p->tcw);
     cudaGetLastError();
     delete p;
     return HPF_OK;
@@ -779,7 +1238,7 @@ hpf_status hpf_prop_set_weights(hpf_prop* p, const float* params) {
     cudaMemsetAsync(p->adam_m, 0, sizeof(float) * p->np, p->stream);
     cudaMemsetAsync(p->adam_v, 0, sizeof(float) * p->np, p->stream);
     p->adam_t = 0;
-    k_pack_weights<<<3, 256, 0, p->stream>>>(p->params, p->wf, p->wb, p->bias);
+    pack_all_weights(p, p->stream);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess)
         return HPF_ERR_CUDA;
     return HPF_OK;
@@ -806,9 +1265,10 @@ hpf_status hpf_prop_forward(hpf_prop* p, const float* x, float* dphi) {
     if (!p || !dphi) return HPF_ERR_INVALID;
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s != HPF_OK) return s;
-    prop_predict(p, p->xin, p->yout, p->stream);
+    prop_predict(p, p->xin, p->yout, p->stream, p->flag);
     if ((s = prop_launched(p)) != HPF_OK) return s;
-    return prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V);
+    if ((s = prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V)) != HPF_OK) return s;
+    return prop_flag_status(p);
 }
 
 hpf_status hpf_prop_backward(hpf_prop* p, const float* x, const float* phi_next, float* grads,
@@ -817,7 +1277,7 @@ hpf_status hpf_prop_backward(hpf_prop* p, const float* x, const float* phi_next,
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s == HPF_OK) s = prop_stage(p, p->tin, phi_next, (size_t)p->g.V * 2);
     if (s != HPF_OK) return s;
-    prop_forward(p, p->xin, true, p->stream);
+    prop_forward(p, p->xin, true, p->stream, p->flag);
     prop_backward(p, p->xin, p->tin);
     if ((s = prop_launched(p)) != HPF_OK) return s;
     if ((s = prop_copy_out(p, grads, p->grads, sizeof(float) * p->np)) != HPF_OK) return s;
@@ -838,7 +1298,7 @@ hpf_status hpf_prop_train_step(hpf_prop* p, const float* x, const float* phi_nex
     hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
     if (s == HPF_OK) s = prop_stage(p, p->tin, phi_next, (size_t)p->g.V * 2);
     if (s != HPF_OK) return s;
-    prop_forward(p, p->xin, true, p->stream);
+    prop_forward(p, p->xin, true, p->stream, p->flag);
     prop_backward(p, p->xin, p->tin);
     prop_adam(p, p->grads, lr);
     if ((s = prop_launched(p)) != HPF_OK) return s;
