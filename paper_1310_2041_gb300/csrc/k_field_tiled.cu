@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TX * TY) k_field_tiled(const __grid_constant__
     const int tx = tid % TX, ty = tid / TX;
     const int px = x0 + tx, py = y0 + ty;
     if (px > g.mx || py > g.my) return;
-    const FieldCoef& c = p.coef[lo];
+    const FieldCoef& c = *r.coef;
     const int u = tx + 2, v = ty + 1;
 #pragma unroll 1
     for (int tz = 0; tz < TZ; ++tz) {
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_field_plain(const __grid_constant__ Til
     const int ym = node + ((y == 0) ? (g.my - 1) * sy : -sy);
     const int zp = node + ((z + 1 == g.mz) ? (1 - g.mz) * sz : sz);
     const int zm = node + ((z == 0) ? (g.mz - 1) * sz : -sz);
-    const FieldCoef& c = p.coef[lo];
+    const FieldCoef& c = *r.coef;
     float ddx[S], ddy[S], ddz[S], dc[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256) k_field_pair(const __grid_constant__ Tile
             if (two) r.D_clear[(size_t)k * g.nodes + row + x1] = 0ull;
         }
     }
-    const FieldCoef& c = p.coef[lo];
+    const FieldCoef& c = *r.coef;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         if (j == 1 && !two) break;
