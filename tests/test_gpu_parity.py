@@ -247,6 +247,26 @@ def test_energy_matches_oracle(hpf_gpu, orc, w):
     assert E[5] == pytest.approx(Eo[5], rel=1e-7)
 
 
+def test_kT_other_than_one_follows_the_oracle(hpf_gpu, orc):
+    """At kT = 2.5 (chi in kT units, 1/kappa in energy units, so only the chi
+    terms scale) the field forces, the field energy and a 10-step trajectory
+    follow the oracle at the usual bars."""
+    w = SMALL[2]
+    d = thermal(W.generate(w))
+    s, d, pp = make(hpf_gpu, w, data=d, kT=2.5)
+    op = oparams(orc, pp)
+    Vo, Go = orc.field(op, orc.scatter(op, d["pos"], d["type"]))
+    ok, worst = force_ok(s.forces(1), orc.field_force(op, d["pos"], d["type"], Go))
+    assert ok, worst
+    Eo = orc.energy(op, d["pos"], d["vel"], d["type"], d["bonds"], Vo, Go, 0)
+    assert s.energy()[2] == pytest.approx(Eo[2], rel=1e-12)
+    s.step(10)
+    pos, vel, _ = s.get_state()
+    po, vo, _ = orc.run(op, d["pos"], d["vel"], d["type"], d["bonds"], 0, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+
+
 def test_resume_is_bit_identical(hpf_gpu):
     w = W.diblock(100, 4, 4, 8.0, 8, 1.0, field_every=5)
     a, d, pp = make(hpf_gpu, w)

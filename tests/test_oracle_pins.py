@@ -341,6 +341,26 @@ def test_field_energy_closed_form_uniform_mix(orc):
     assert orc.field_energy(p, D) == pytest.approx(2.0 * 64 * 1.6 / 4, rel=1e-14)
 
 
+def test_field_energy_and_potential_at_kT_2_scale_only_the_chi_terms(orc):
+    """Reading of the MD-SCF potential V_K = kT sum chi phi + (1/kappa)(sum phi - 1)
+    with chi in kT units and 1/kappa in energy units: at kT = 2.5 only the chi
+    terms scale.  Uniform phi_A = phi_B = 0.6 (1.2 beads of each per unit cell),
+    chi_AB = 0.5, 1/kappa = 1.5: W = rho0 vol [kT chi phiA phiB + (1/kappa)/2
+    (phiA + phiB - 1)^2] = 128 (0.45 + 0.03) and V_A = kT chi phiB + (1/kappa)
+    (phiA + phiB - 1) = 0.75 + 0.3; kT multiplying 1/kappa too would give
+    W = 128 (0.45 + 0.075) and V_A = 1.5."""
+    p = unit_params(orc, mesh=(4, 4, 4), chi=[[0, 0.5], [0.5, 0]], inv_kappa=1.5, rho0=2.0,
+                    kT=2.5)
+    D = np.full((2, 4, 4, 4), 12 * BEAD // 10, dtype=np.int64)
+    phi = (12 * BEAD // 10) / BEAD / 2.0
+    W = 2.0 * 64 * (2.5 * 0.5 * phi * phi + 0.5 * 1.5 * (2 * phi - 1) ** 2)
+    assert orc.field_energy(p, D) == pytest.approx(W, rel=1e-12)
+    assert W == pytest.approx(128 * 0.48, rel=1e-9)
+    V, _ = orc.field(p, D)
+    assert V[0, 2, 1, 3] == pytest.approx(2.5 * 0.5 * phi + 1.5 * (2 * phi - 1), rel=1e-12)
+    assert V[1, 0, 3, 2] == pytest.approx(1.05, rel=1e-9)
+
+
 def test_energy_observables_of_known_state(orc):
     # no field, no friction, no noise: v_n = v_{n-1/2} + dt/(2m) F_bond with the
     # two-bead closed form F_0 = -2k(r-r0)(x0-x1)/r = (1.44, 1.92, 0) = -F_1
