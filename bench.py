@@ -136,17 +136,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
-def traffic_record():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+def traffic_record(workload: str):
+    """DRAM bytes per launch of the step kernel on `workload` from the committed
+    ncu summary, valid only while the kernel source is unchanged since the
+    capture."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))["k_step"]
+        recs = json.load(open(TRAFFIC_FILE))["k_step"]
     except (OSError, KeyError, ValueError):
         return None
+    if isinstance(recs, dict):
+        recs = [recs]
     h = hashlib.sha256()
     for f in STEP_SRC:
         h.update(open(f, "rb").read())
-    return rec if rec.get("source_sha256") == h.hexdigest() else None
+    for rec in recs:
+        if rec.get("workload") == workload and rec.get("source_sha256") == h.hexdigest():
+            return rec
+    return None
 
 
 def thermostat_params(args):
@@ -262,6 +268,35 @@ def cpu_oracle_learned_rate(w, data, snap, K: int, budget_s: float):
             "sample": f"2 plain steps (field every step) of {n} of the {w.n_beads} beads "
                       f"({md_per_bead_step * w.n_beads:.2f} s per full step), one propagator "
                       f"forward on the {w.mesh}^3 mesh ({fwd:.1f} s, once per {K} steps)"}
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_replicas_rate(ws, data, budget_s: float):
+    """Oracle bead-steps/s on the replica set: whole field periods of replicas
+    taken in order until about budget_s of CPU work."""
+    import oracle
+    oracle.build()
+    done_beads, t_total, used = 0, 0.0, 0
+    for w, d in zip(ws, data):
+        op = oracle.make_params(**w.params())
+        t = time.perf_counter()
+        oracle.run(op, d["pos"], d["vel"], d["type"], d["bonds"], 0, w.field_every)
+        t_total += time.perf_counter() - t
+        done_beads += w.n_beads * w.field_every
+        used += 1
+        if t_total >= budget_s:
+            break
+    return {"value": done_beads / t_total, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"one field period ({ws[0].field_every} steps) of each of the first "
+                      f"{used} of {len(ws)} replicas, {t_total:.1f} s of CPU time"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -448,7 +483,7 @@ def run_ours(args):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     # the record is the bonds-only step kernel's, on the default workload
-    tr = None if (nh or bonded_params(args)) else traffic_record()
+    tr = None if (nh or bonded_params(args)) else traffic_record(w.name)
     traffic = None
     if tr:
         traffic = tr["dram_bytes_per_launch"] * bead_steps_per_launch / tr["bead_steps_per_launch"]
@@ -572,15 +607,25 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
+    warm = args.warmup + (-args.warmup) % fe  # the timed window starts on a refresh
     with torch.cuda.stream(stream):
         batch = hpf.Batch(params, stream=stream)
         load(batch.replicas)
-        batch.step(args.warmup)
+        batch.step(warm)
         clocks = ClockSampler(0)
         clocks.start()
         time.sleep(0.3)
         ms_batch = timed(batch.step, args.steps)
         clk = clocks.stop()
+        # kernel window: the same steps again with plain launches (no graph
+        # replays) and the library's stage events, for the step kernel's time
+        r0 = batch.replica(0)
+        batch.use_graphs(False)
+        r0.profile_read()
+        r0.profile(True)
+        batch.step(args.steps)
+        r0.profile(False)
+        prof = r0.profile_read()
         batch.close()
         plain = [hpf.System(p, stream=stream) for p in params]
         load(plain)
@@ -599,6 +644,18 @@ def run_batch(args):
             s.close()
     value = n_total * args.steps / (ms_batch * 1e-3)
     plain_value = n_total * args.steps / (ms_plain * 1e-3)
+    step_ms, step_launches = prof["step"]
+    achieved = ALGO_BYTES_PER_BEAD_STEP * n_total * args.steps / (step_ms * 1e-3) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "kernel": "k_step_warp_batch (all replicas, one launch per period)",
+                "algo_bytes_per_bead_step": ALGO_BYTES_PER_BEAD_STEP,
+                "avg_launch_us": 1e3 * step_ms / max(step_launches, 1),
+                "kernel_window": f"step-kernel events over a second window of the same "
+                                 f"{args.steps} steps, plain launches",
+                "stage_ms": {k: round(v[0], 4) for k, v in prof.items()}}
+    cpu = None if args.no_cpu_baseline else cpu_oracle_replicas_rate(ws, data, budget_s=10.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_batch / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -606,11 +663,13 @@ def run_batch(args):
             "config": {"workload": "replicas64_a8b12", "n_beads": n_total, "replicas": len(ws),
                        "field_every": fe, "sort_every": args.sort_every,
                        "l2": "state of all replicas (~200 MB) larger than L2, no flush",
+                       "window": f"untimed warm-up of {warm} steps, then {args.steps} steps",
                        "form": "one batched field + persistent step launch per period, CUDA "
                                "graph replays",
                        "plain_value": plain_value, "plain_form": "64 contexts, hpf_step each",
                        "speedup_vs_plain": value / plain_value},
-            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk}
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
+            "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
