@@ -734,6 +734,11 @@ def run_learned(args):
     torch.cuda.synchronize()
     infer_ms = a.elapsed_time(b) / 20
     flops = 2.0 * w.mesh ** 3 * 27 * sum(ci * co for ci, co in ((4, 16), (16, 16), (16, 2)))
+    # memory side of the same inference, layer by layer: the 4-channel FP32
+    # input read, the two 16-channel BF16 hidden activations written and read
+    # once each, the 2-channel FP32 output written
+    V = w.mesh ** 3
+    infer_bytes = V * (4 * 4 + 2 * (2 * 16 * 2) + 2 * 4)
     # the judge's error of the candidates along the continued plain run
     lags = (1, 2, 5, 10, 15, 20)
     res = learned.judge_candidates(s, net, 10, K, lags=lags)
@@ -811,6 +816,7 @@ def run_learned(args):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 1900.0, "fallback"
     achieved = flops / (infer_ms * 1e-3) / 1e12
+    hbm_peak, hbm_src = measured_hbm_peak()
     cpu = None
     if not args.no_cpu_baseline:
         x0 = snaps[100:102].reshape((4,) + tuple(snaps.shape[2:])).cpu().numpy()
@@ -830,11 +836,82 @@ def run_learned(args):
                        "infer_ms": infer_ms, "net_by_lag": by_lag},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_src, "kernel": "k_conv (whole forward)",
+                         "peak_source": peak_src,
+                         "kernel": "k_conv_tc (three layers, whole forward)",
                          "algo_flops_per_inference": flops},
+            "roofline_hbm": {"bound": "hbm", "achieved": infer_bytes / (infer_ms * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": infer_bytes / (infer_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_source": hbm_src, "algo_bytes_per_inference": infer_bytes},
             "cpu_baseline": cpu, "e2e": None, "clocks": clk}
     print(json.dumps(line), flush=True)
     net.close()
+    return 0
+
+
+def run_propagator(args):
+    """The learned density propagator's inference alone on the 70^3 mesh of the
+    1M-bead melt: He-initialised weights (the arithmetic does not depend on
+    the values), a seeded 4-channel input on the device, K timed forwards
+    (CUDA events on the handle's stream), L2 flushed before each.  Reports the
+    tensor roofline (6.52 GFLOP per inference) and the memory-side one."""
+    import numpy as np
+    import torch
+    from paper_1310_2041_gb300 import hpf, learned
+
+    torch.cuda.set_device(0)
+    M = 70
+    V = M ** 3
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.uniform(0.0, 1.2, size=(4, M, M, M)).astype(np.float32)).cuda()
+    y = torch.empty((2, M, M, M), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flops = 2.0 * V * 27 * sum(ci * co for ci, co in ((4, 16), (16, 16), (16, 2)))
+    infer_bytes = V * (4 * 4 + 2 * (2 * 16 * 2) + 2 * 4)
+    with hpf.Propagator((M, M, M), stream=stream) as net:
+        net.set_weights(learned.init_params(1))
+        for _ in range(max(3, args.warmup)):
+            net.forward(x, out=y)
+        torch.cuda.synchronize()
+        ms = []
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.forward(x, out=y)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        clk = clocks.stop()
+    infer_ms = statistics.median(ms)
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        peak_src = "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 1900.0, "fallback"
+    hbm_peak, hbm_src = measured_hbm_peak()
+    achieved = flops / (infer_ms * 1e-3) / 1e12
+    line = {"metric": "propagator inferences/s, 70^3 mesh (4->16->16->2, 3x3x3, BF16)",
+            "value": 1e3 / infer_ms, "unit": "inferences/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": infer_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "propagator_70", "mesh": M,
+                       "l2": "flushed (256 MB write) before each timed inference"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "kernel": "k_conv_tc (three layers)",
+                         "algo_flops_per_inference": flops},
+            "roofline_hbm": {"bound": "hbm", "achieved": infer_bytes / (infer_ms * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": infer_bytes / (infer_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_source": hbm_src, "algo_bytes_per_inference": infer_bytes},
+            "cpu_baseline": None, "e2e": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -846,6 +923,8 @@ def main():
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "propagator":
+        return run_propagator(args)
     return run_ours(args)
 
 

@@ -441,7 +441,10 @@ hpf_status hpf_batch_destroy(hpf_batch* batch);
  * A convolution computes out[co](n) = b[co] + sum_d sum_ci W[d][ci][co]
  * in[ci](n + d) over the 27 offsets d = (dz, dy, dx) in {-1, 0, 1}^3, z-major.
  * Weights and activations are BF16 on the tensor cores with FP32
- * accumulation; the master parameters and Adam state are FP32.
+ * accumulation (forward and data gradients on tcgen05 with tensor-memory
+ * accumulators); the master parameters and Adam state are FP32.  The
+ * tensor-core waits are bounded: one that gives up makes the next call that
+ * synchronises return HPF_ERR_TIMEOUT (once).
  *
  * Parameter vector (hpf_prop_param_count() floats): for each layer in order,
  * W [27][C_in][C_out] then b [C_out].  Mesh arrays are planar FP32,
@@ -469,8 +472,18 @@ hpf_status hpf_prop_set_weights(hpf_prop* prop, const float* params);
 hpf_status hpf_prop_get_weights(hpf_prop* prop, float* params);
 
 /* dphi [2][Mz][My][Mx] = network(x [4][Mz][My][Mx]).  Synchronises for a
- * host destination. */
+ * host destination (and then reports HPF_ERR_TIMEOUT as above); with a
+ * device destination it returns without waiting. */
 hpf_status hpf_prop_forward(hpf_prop* prop, const float* x, float* dphi);
+
+/* Autoregressive use of a network trained at lag 1 (the per-step variant of
+ * the propagator): from x = (phi(t - 1), phi(t)) [4][Mz][My][Mx], steps times
+ * phi(t + 1) = phi(t) + network(phi(t - 1), phi(t)), each prediction fed
+ * back as the next input (FP32 sums); phi_out [2][Mz][My][Mx] = the predicted
+ * phi(t + steps).  With a network trained at lag L and steps = 1 it is that
+ * network's prediction phi(t) + dphi.  Synchronises for a host destination.
+ * Errors: HPF_ERR_INVALID (steps < 1, NULL), HPF_ERR_CUDA, HPF_ERR_TIMEOUT. */
+hpf_status hpf_prop_rollout(hpf_prop* prop, const float* x, int32_t steps, float* phi_out);
 
 /* Loss L = mean over the 2 x M outputs of (s network(x) - s (phi_next - x[2:4]))^2,
  * i.e. s^2 times the mean squared error of the predicted change,

@@ -1390,19 +1390,48 @@ void launch_batch_fields(hpf_batch* b, int flip) {
     }
 }
 
-// Tile shape per replica: every candidate timed on the replica's own mesh.
+// Tile shapes: every candidate timed on each replica's own mesh gives a shape
+// per replica; the grouped launches this needs (one per distinct shape) are
+// then timed against the best single shape for all replicas in one launch,
+// and the faster of the two is kept.
 void batch_autotune(hpf_batch* b) {
     const int S = b->rep[0]->S;
-    b->rep_tile.assign(b->R, 0);
+    std::vector<int> per(b->R, 0);
     for (int r = 0; r < b->R; ++r) {
         hpf_ctx* c = b->rep[r];
-        b->rep_tile[r] = autotune_tile<TiledFieldParams>(b->stream, S, [&](int t, TiledFieldParams& p) {
+        per[r] = autotune_tile<TiledFieldParams>(b->stream, S, [&](int t, TiledFieldParams& p) {
             memset(&p, 0, sizeof p);
             p.flag = c->dflag;
             p.R = 1;
             fill_field_rep(c, t, c->dmesh, p.rep[0], p.blocks);
         });
     }
+    const int uni = autotune_tile<TiledFieldParams>(b->stream, S, [&](int t, TiledFieldParams& p) {
+        memset(&p, 0, sizeof p);
+        p.flag = b->rep[0]->dflag;
+        for (int r = 0; r < b->R; ++r) {
+            hpf_ctx* c = b->rep[r];
+            fill_field_rep(c, t, c->dmesh, p.rep[p.R++], p.blocks);
+        }
+    });
+    cudaEvent_t e0, e1;
+    float ms[2] = {0.f, 0.f};
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        for (int k = 0; k < 2; ++k) {
+            b->rep_tile = k == 0 ? per : std::vector<int>(b->R, uni);
+            launch_batch_fields(b, 0);  // warm
+            cudaEventRecord(e0, b->stream);
+            for (int rep = 0; rep < 3; ++rep) launch_batch_fields(b, 0);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms[k], e0, e1) != cudaSuccess)
+                ms[k] = 0.f;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    cudaGetLastError();
+    b->rep_tile = (ms[0] > 0.f && ms[0] < ms[1]) ? per : std::vector<int>(b->R, uni);
 }
 
 // Batched refresh of the replicas whose field is due (all of them in steady state).

@@ -712,6 +712,19 @@ __global__ void k_unpack_output(const float* __restrict__ y, int V, float scale,
     out[(size_t)V + v] = y[(size_t)v * kPC + 1] / scale;
 }
 
+// One autoregressive step on the planar input x [4][V] = (phi(t - 1), phi(t))
+// with the predicted change dphi [2][V]: x becomes (phi(t), phi(t) + dphi).
+__global__ void k_rollout_shift(float* __restrict__ x, const float* __restrict__ dphi, int V) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float cur = x[(size_t)(2 + c) * V + v];
+        x[(size_t)c * V + v] = cur;
+        x[(size_t)(2 + c) * V + v] = cur + dphi[(size_t)c * V + v];
+    }
+}
+
 // Mean squared error of the network output y against scale * (phi_next -
 // phi_cur) (planar [2][V] each) and its gradient 2 (y - target) / (2V) in BF16.
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
@@ -1268,7 +1281,32 @@ hpf_status hpf_prop_forward(hpf_prop* p, const float* x, float* dphi) {
     prop_predict(p, p->xin, p->yout, p->stream, p->flag);
     if ((s = prop_launched(p)) != HPF_OK) return s;
     if ((s = prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V)) != HPF_OK) return s;
-    return prop_flag_status(p);
+    // a host destination has synchronised the stream: the wait status is known;
+    // for a device destination it is reported by the next synchronising call
+    cudaPointerAttributes a;
+    const bool dev = cudaPointerGetAttributes(&a, dphi) == cudaSuccess &&
+                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return dev ? HPF_OK : prop_flag_status(p);
+}
+
+hpf_status hpf_prop_rollout(hpf_prop* p, const float* x, int32_t steps, float* phi_out) {
+    if (!p || !phi_out || steps < 1) return HPF_ERR_INVALID;
+    const int V = p->g.V;
+    hpf_status s = prop_stage(p, p->xin, x, (size_t)V * 4);
+    if (s != HPF_OK) return s;
+    for (int k = 0; k < steps; ++k) {
+        prop_predict(p, p->xin, p->yout, p->stream, p->flag);
+        k_rollout_shift<<<(V + 255) / 256, 256, 0, p->stream>>>(p->xin, p->yout, V);
+    }
+    if ((s = prop_launched(p)) != HPF_OK) return s;
+    if ((s = prop_copy_out(p, phi_out, p->xin + 2 * (size_t)V, sizeof(float) * 2 * V)) != HPF_OK)
+        return s;
+    cudaPointerAttributes a;
+    const bool dev = cudaPointerGetAttributes(&a, phi_out) == cudaSuccess &&
+                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return dev ? HPF_OK : prop_flag_status(p);
 }
 
 hpf_status hpf_prop_backward(hpf_prop* p, const float* x, const float* phi_next, float* grads,

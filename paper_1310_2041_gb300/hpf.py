@@ -148,6 +148,7 @@ def load():
         L.hpf_prop_set_scale.argtypes = [vp, ctypes.c_float]
         L.hpf_prop_get_scale.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.hpf_prop_forward.argtypes = [vp, vp, vp]
+        L.hpf_prop_rollout.argtypes = [vp, vp, i32, vp]
         L.hpf_prop_backward.argtypes = [vp, vp, vp, vp, dp]
         L.hpf_prop_adam_step.argtypes = [vp, vp, ctypes.c_float]
         L.hpf_prop_train_step.argtypes = [vp, vp, vp, ctypes.c_float, dp]
@@ -157,7 +158,8 @@ def load():
                                        ctypes.POINTER(LearnedStats)]
         for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
                      "hpf_prop_set_scale", "hpf_prop_get_scale",
-                     "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_backward",
+                     "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_rollout",
+                     "hpf_prop_backward",
                      "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
                      "hpf_judge_density", "hpf_step_learned"):
             getattr(L, name).restype = ctypes.c_int
@@ -634,6 +636,16 @@ class Propagator:
         xp, _a = _ptr(x, np.float32, (4,) + self.grid, "x")
         op, _b = _ptr(out, np.float32, (2,) + self.grid, "dphi")
         self._check(self.lib.hpf_prop_forward(self.h, xp, op))
+        return out
+
+    def rollout(self, x, steps, out=None):
+        """hpf_prop_rollout: phi(t + steps) from x = (phi(t - 1), phi(t)), each
+        prediction phi + network(phi_prev, phi) fed back as the next input."""
+        if out is None:
+            out = np.empty((2,) + self.grid, dtype=np.float32)
+        xp, _a = _ptr(x, np.float32, (4,) + self.grid, "x")
+        op, _b = _ptr(out, np.float32, (2,) + self.grid, "phi_out")
+        self._check(self.lib.hpf_prop_rollout(self.h, xp, int(steps), op))
         return out
 
     def backward(self, x, phi_next, grads=None):

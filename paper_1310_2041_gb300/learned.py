@@ -127,8 +127,8 @@ def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows:
             if prop is not None and (s - H) % K == 0:
                 a, b = hist[(s - 2 * K) % (H + 1)], hist[(s - K) % (H + 1)]
                 x = torch.cat([a, b]).contiguous()
-                dphi = prop.forward(x, out=torch.empty_like(b))
-                res["net"].append(system.judge_density(b + dphi))
+                pred = prop.rollout(x, 1, out=torch.empty_like(b))   # phi(t) + net(...)
+                res["net"].append(system.judge_density(pred))
                 res["hold_net"].append(system.judge_density(b))
         if s < n_steps:
             system.step(1)
@@ -138,17 +138,11 @@ def judge_candidates(system: hpf.System, prop: hpf.Propagator | None, n_windows:
 def rollout(prop: hpf.Propagator, prev, cur, K: int):
     """Autoregressive use of a network trained at lag 1: from phi(t - 1) = prev
     and phi(t) = cur, predict phi(t + 1) = phi(t) + net(phi(t - 1), phi(t)),
-    then feed the prediction back, K times.  Returns the predicted phi(t + K)."""
+    then feed the prediction back, K times (hpf_prop_rollout).  Returns the
+    predicted phi(t + K)."""
     import torch
-    a, b = prev, cur
-    x = torch.empty((4,) + tuple(cur.shape[1:]), dtype=torch.float32, device=cur.device)
-    d = torch.empty_like(cur)
-    for _ in range(K):
-        x[:2].copy_(a)
-        x[2:].copy_(b)
-        prop.forward(x, out=d)
-        a, b = b, b + d
-    return b
+    x = torch.cat([prev, cur]).contiguous()
+    return prop.rollout(x, K, out=torch.empty_like(cur))
 
 
 def judge_rollout(system: hpf.System, prop: hpf.Propagator, n_windows: int, K: int):

@@ -492,3 +492,29 @@ def test_autoregressive_rollout(hpf_gpu):
         c.step(K)
         want.append(c.judge_density(held))
     assert eps == pytest.approx(want, rel=1e-12)
+
+
+def test_rollout_feeds_predictions_back(hpf_gpu):
+    """hpf_prop_rollout: K autoregressive steps in the library give the same
+    bits as K forward passes with the sum phi + dphi done in FP32 outside, and
+    one step is the network's prediction phi(t) + dphi at the emulated bars."""
+    mesh = (13, 10, 5)
+    params = rand_params(31)
+    rng = np.random.default_rng(32)
+    cur = rand_phi(grid(mesh), 33, c=2)
+    prev = cur + rng.uniform(-0.03, 0.03, size=cur.shape)
+    x = np.concatenate([prev, cur]).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.scale = 20.0
+        net.set_weights(hpf_gpu.pack_params(params))
+        got = net.rollout(x, 3)
+        a, b = x[:2].copy(), x[2:].copy()
+        for _ in range(3):
+            d = net.forward(np.concatenate([a, b]))
+            a, b = b, (b + d).astype(np.float32)
+        one = net.rollout(x, 1)
+        with pytest.raises(hpf_gpu.HPFError):
+            net.rollout(x, 0)
+    np.testing.assert_array_equal(got, b)
+    ye, _, _, _ = E.forward(params, x.astype(np.float64), 20.0)
+    within_emulated(one - x[2:], ye, "one rollout step")
