@@ -71,6 +71,12 @@ def parse():
                          "in 100..140 degrees")
     ap.add_argument("--dihedral-n", type=int, default=3)
     ap.add_argument("--dihedral-delta", type=float, default=0.0)
+    ap.add_argument("--smooth-passes", default="",
+                    help="learned workload: also run the smoothed-density study with these "
+                         "binomial-filter pass counts (comma-separated)")
+    ap.add_argument("--smooth-lags", default="",
+                    help="smoothed-density study: train and judge a network at each of these "
+                         "lags (default: K = 20)")
     ap.add_argument("--net-lags", default="",
                     help="learned workload: also train and judge a network at these lags "
                          "(comma-separated step counts)")
@@ -810,6 +816,27 @@ def run_learned(args):
                                     for K2 in (2, 5, 10, 20)}
         nl.close()
         sl.close()
+    # smoothed-density variant: every density (the true one included) through
+    # the binomial filter before its field is formed; a network trained on
+    # smoothed snapshots; the same judge
+    smoothed = {}
+    s_lags = [int(v) for v in args.smooth_lags.split(",") if v.strip()] or [K]
+    for P in [int(v) for v in args.smooth_passes.split(",") if v.strip()]:
+        smoothed[P] = {}
+        for L in s_lags:
+            ss = system(1, pos, vel, step)
+            snaps_s = learned.collect_smoothed(ss, 200, L, P)
+            ns = hpf.Propagator(pp["mesh"], stream=stream)
+            ns.set_weights(learned.init_params(0))
+            ns.scale = learned.change_scale(snaps_s, train_ex)
+            learned.train(ns, snaps_s, 2000, lr=2e-3, lr_final=2e-4, examples=train_ex)
+            vn, vz, vl = learned.validation_loss(ns, snaps_s, val_ex)
+            res_s = learned.judge_smoothed(ss, P, ns, 10, L, lags=sorted({1, 2, 5, L}))
+            smoothed[P][L] = {"eps_mean": {k: float(np.mean(v)) for k, v in res_s.items() if v},
+                              "val_mse": {"net": vn, "no_change": vz, "linear": vl},
+                              "scale": ns.scale}
+            ns.close()
+            ss.close()
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
         peak_src = "measured"
@@ -833,7 +860,8 @@ def run_learned(args):
                        "val_mse": {"net": val_net, "no_change": val_zero, "linear": val_lin},
                        "change_scale": net.scale,
                        "train_ms_per_iter": train_ms, "train_log": log,
-                       "infer_ms": infer_ms, "net_by_lag": by_lag},
+                       "infer_ms": infer_ms, "net_by_lag": by_lag,
+                       "smoothed": smoothed},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src,

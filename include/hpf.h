@@ -518,6 +518,36 @@ hpf_status hpf_density_phi(hpf_ctx* ctx, float* phi);
  * Errors: HPF_ERR_INVALID, HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_judge_density(hpf_ctx* ctx, const float* phi, double* eps);
 
+/* The smoothed-density study (the propagator's accuracy question of the
+ * learned part; the paper has no counterpart): a periodic binomial filter of
+ * phi meshes and a judge between two densities.
+ *
+ * hpf_smooth_phi: phi_out = the filter (1/4, 1/2, 1/4) applied along x, y and
+ * z in turn, `passes` times (0..64; variance passes/2 cells^2 per axis), to
+ * phi_in [n_species][Mz][My][Mx] FP32 (periodic; host or device; phi_out may
+ * equal phi_in).  Synchronises for a host destination.
+ * hpf_judge_density_pair: eps = || F(phi_cand) - F(phi_ref) ||_2 /
+ * || F(phi_ref) ||_2, the field forces (trilinear gather of the
+ * central-difference gradient, as the judge of hpf_step_learned) of the two
+ * densities at the current positions, each taken to the mesh's fixed point
+ * (negative values count as zero).  Leaves the field of the true density in
+ * force.  Synchronises.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_STATE, HPF_ERR_CUDA. */
+hpf_status hpf_smooth_phi(hpf_ctx* ctx, const float* phi_in, float* phi_out, int32_t passes);
+hpf_status hpf_judge_density_pair(hpf_ctx* ctx, const float* phi_cand, const float* phi_ref,
+                                  double* eps);
+
+/* How hpf_step_learned runs an accepted-form (learned) window.  in_launch = 1
+ * (the default): one step-kernel launch for the whole window, the field at
+ * window step j being (1 - j/K) F(D(t)) + (j/K) F(D(t) + dphi), F the field of
+ * a mesh -- the field of D(t) + (j/K) dphi, since the field is linear in the
+ * density -- with both cells' polynomials cached per bead (contexts whose
+ * chains fit warp segments and with force_mode 0; others run per step).
+ * in_launch = 0: one launch per step on the field of the integer mesh
+ * D(t) + (j/K) dphi (in the mesh's fixed point) refreshed every step.  The two
+ * agree to FP32 rounding.  Errors: HPF_ERR_INVALID, HPF_ERR_NOMEM. */
+hpf_status hpf_learned_mode(hpf_ctx* ctx, int32_t in_launch);
+
 /* Outcome of hpf_step_learned (totals of the call). */
 typedef struct {
     int64_t steps;    /* steps advanced */

@@ -140,3 +140,14 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 def adam_state(params):
     return (0, [[np.zeros_like(W), np.zeros_like(b)] for W, b in params],
             [[np.zeros_like(W), np.zeros_like(b)] for W, b in params])
+
+
+def smooth(phi, passes):
+    """The periodic binomial filter (1/4, 1/2, 1/4) along x, y and z in turn,
+    passes times, of a [..., Mz, My, Mx] mesh (the smoothed-density variant of
+    the propagator study)."""
+    out = np.asarray(phi, dtype=np.float64).copy()
+    for _ in range(passes):
+        for axis in (-1, -2, -3):
+            out = 0.25 * (np.roll(out, 1, axis=axis) + np.roll(out, -1, axis=axis)) + 0.5 * out
+    return out

@@ -104,6 +104,8 @@ struct LearnedBufs {
     bool plain_mode = false;   // run plain windows (shadow-judged) until a prediction meets tol
     int backoff = 0;           // plain windows to skip between shadow judgements (doubles per failure)
     int skip_left = 0;         // plain windows left before the next shadow judgement
+    float4* G2 = nullptr;      // field of the window's predicted end density (ghosted)
+    bool in_launch = true;     // a learned window in one launch (interpolated fields)
 };
 
 namespace {
@@ -463,7 +465,8 @@ hpf_status run_field(hpf_ctx* c) {
 // field buffer, clearing D_clear when given.  The tile must have been chosen
 // (run_field ran before).  The context's mesh bookkeeping is not changed.
 hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap& tm, bool tm_ok,
-                      unsigned long long* D_clear) {
+                      unsigned long long* D_clear, float4* G_out = nullptr) {
+    float4* G = G_out ? G_out : c->G;
     {
         StageScope sc(c, HPF_STAGE_FIELD, 1);
         if (c->S <= 4 && c->field_tile >= 0) {
@@ -472,6 +475,7 @@ hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap
             p.R = 1;
             p.flag = c->dflag;
             fill_field_rep_mesh(c, c->field_tile, D, tm, tm_ok, D_clear, p.rep[0], p.blocks);
+            p.rep[0].G = G;
             launch_field_tiled(p, c->S, c->field_tile, c->stream);
         } else {
             BatchFieldParams fp;
@@ -480,7 +484,7 @@ hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap
             fp.coef = c->d_coef;
             fp.rep[0].g = c->geom;
             fp.rep[0].D = reinterpret_cast<const long long*>(D);
-            fp.rep[0].G = c->G;
+            fp.rep[0].G = G;
             fp.rep[0].D_clear = D_clear;
             fp.rep[0].blk_begin = 0;
             fp.blocks = (c->geom.gnodes + 255) / 256;
@@ -528,7 +532,11 @@ hpf_status sort_beads(hpf_ctx* c) {
 
 // Launch `chunk` steps on the field in force; with fuse the last sub-step
 // also scatters its positions into the other mesh (which must be zero).
-hpf_status advance(hpf_ctx* c, int chunk, bool fuse) {
+// lerp_G2: a learned window in one launch (warp form, force_mode 0): the
+// field (1 - j/K) G + (j/K) lerp_G2 at window step j, lerp_j0 at the first
+// sub-step, lerp_inv_k = 1/K.
+hpf_status advance(hpf_ctx* c, int chunk, bool fuse, const float4* lerp_G2 = nullptr,
+                   int lerp_j0 = 0, float lerp_inv_k = 0.f) {
     {
         StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
         if (c->warp_mode) {
@@ -555,7 +563,11 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse) {
             q.G = c->G;
             q.D[0] = mesh_buf(c, 0);
             q.D[1] = mesh_buf(c, 1);
-            launch_step_warp_single(p, c->C, step_thermostat(c->sc), c->stream);
+            if (lerp_G2)
+                launch_step_warp_lerp(p, lerp_G2, lerp_j0, lerp_inv_k, c->C,
+                                      step_thermostat(c->sc), c->stream);
+            else
+                launch_step_warp_single(p, c->C, step_thermostat(c->sc), c->stream);
         } else
             launch_step(c->st[c->cur], c->st[c->cur ^ 1], c->meta, c->n, chunk, c->step, c->geom,
                         c->G, c->sc, fuse ? mesh_buf(c, c->dmesh ^ 1) : nullptr, c->dflag,
@@ -841,6 +853,7 @@ hpf_status hpf_destroy(hpf_ctx* c) {
         cudaFree(L->snap);
         cudaFree(L->acc);
         cudaFreeHost(L->h_acc);
+        cudaFree(L->G2);
         delete L;
     }
     cudaGetLastError();
@@ -1763,6 +1776,7 @@ hpf_status ensure_learned(hpf_ctx* c) {
     e = e ? e : cudaMalloc(&L->snap, sizeof(float) * 6 * (size_t)(c->n > 0 ? c->n : 1));
     e = e ? e : cudaMalloc(&L->acc, sizeof(double) * (2 + 2 * (size_t)force_error_partials()));
     e = e ? e : cudaMallocHost(&L->h_acc, sizeof(double) * 2);
+    e = e ? e : cudaMalloc(&L->G2, sizeof(float4) * S * (size_t)c->geom.gnodes);
     c->learned = L;  // freed by hpf_destroy, also after a failed allocation
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1773,6 +1787,7 @@ hpf_status ensure_learned(hpf_ctx* c) {
         cudaFree(L->snap);
         cudaFree(L->acc);
         cudaFreeHost(L->h_acc);
+        cudaFree(L->G2);
         delete L;
         c->learned = nullptr;
         return fail(c, e == cudaErrorMemoryAllocation ? HPF_ERR_NOMEM : HPF_ERR_CUDA,
@@ -1866,6 +1881,83 @@ hpf_status hpf_judge_density(hpf_ctx* c, const float* phi, double* eps) {
     return judge_mesh(c, eps);
 }
 
+hpf_status hpf_learned_mode(hpf_ctx* c, int32_t in_launch) {
+    if (!c) return HPF_ERR_INVALID;
+    if (in_launch < 0 || in_launch > 1) return fail(c, HPF_ERR_INVALID, "in_launch must be 0 or 1");
+    hpf_status s = ensure_learned(c);
+    if (s != HPF_OK) return s;
+    c->learned->in_launch = in_launch != 0;
+    return HPF_OK;
+}
+
+hpf_status hpf_smooth_phi(hpf_ctx* c, const float* phi_in, float* phi_out, int32_t passes) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!phi_in || !phi_out || passes < 0 || passes > 64)
+        return fail(c, HPF_ERR_INVALID, "phi_in, phi_out and 0 <= passes <= 64 are required");
+    const long long n = (long long)mesh_words(c);
+    // work and scratch meshes in the field staging buffer (4 n floats)
+    float* a = reinterpret_cast<float*>(c->field_stage);
+    float* tmp = a + n;
+    CUDA_TRY(c, cudaMemcpyAsync(a, phi_in, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 3 * passes);
+        launch_smooth_phi(a, a, tmp, c->geom.mx, c->geom.my, c->geom.mz, c->S, passes, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    return copy_out(c, phi_out, a, sizeof(float) * n);
+}
+
+hpf_status hpf_judge_density_pair(hpf_ctx* c, const float* phi_cand, const float* phi_ref,
+                                  double* eps) {
+    if (!c) return HPF_ERR_INVALID;
+    if (!phi_cand || !phi_ref || !eps)
+        return fail(c, HPF_ERR_INVALID, "phi_cand, phi_ref and eps are required");
+    if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
+    hpf_status s = ensure_learned(c);
+    if (s != HPF_OK) return s;
+    LearnedBufs* L = c->learned;
+    const long long n = (long long)mesh_words(c), n3 = 3ll * c->n;
+    if ((s = scatter_current(c)) != HPF_OK) return s;
+    if (c->field_tile < 0 && (s = run_field(c)) != HPF_OK) return s;  // picks the tile
+    CUDA_TRY(c, cudaMemcpyAsync(L->dphi, phi_cand, sizeof(float) * n, cudaMemcpyDefault,
+                                c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_mesh_predict(nullptr, L->dphi, n, 1.0 / c->ec.phi_c, L->Dp, c->stream);
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(L->dphi, phi_ref, sizeof(float) * n, cudaMemcpyDefault,
+                                c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_mesh_predict(nullptr, L->dphi, n, 1.0 / c->ec.phi_c, L->Dbase, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    CUtensorMap none;
+    memset(&none, 0, sizeof none);
+    if ((s = field_from(c, L->Dp, none, false, nullptr)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 1 : 0);
+        launch_forces(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, HPF_FORCE_FIELD,
+                      c->out_f, c->stream);
+    }
+    if ((s = field_from(c, L->Dbase, none, false, nullptr)) != HPF_OK) return s;
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, c->n > 0 ? 2 : 1);
+        launch_forces(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, HPF_FORCE_FIELD,
+                      c->out_f + n3, c->stream);
+        launch_force_error(c->out_f, c->out_f + n3, n3, L->acc, c->stream);
+    }
+    LAUNCH_CHECK(c);
+    // the field of the true density back in force
+    if ((s = run_field(c)) != HPF_OK) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(L->h_acc, L->acc, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    if ((s = check_flags(c)) != HPF_OK) return s;
+    const double e2 = L->h_acc[0], r2 = L->h_acc[1];
+    *eps = r2 > 0.0 ? sqrt(e2 / r2) : (e2 > 0.0 ? INFINITY : 0.0);
+    return HPF_OK;
+}
+
 hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32_t K, double tol,
                             hpf_learned_stats* stats) {
     if (!c) return HPF_ERR_INVALID;
@@ -1923,17 +2015,29 @@ hpf_status hpf_step_learned(hpf_ctx* c, hpf_prop* prop, int32_t n_windows, int32
                                             sizeof(unsigned long long) * SM, c->stream));
                 c->next_zero = true;
             }
-            for (int j = 0; j < K; ++j) {
-                if (j > 0) {
-                    {
-                        StageScope sc(c, HPF_STAGE_OTHER, 1);
-                        launch_mesh_predict(L->Dbase, L->dphi, SM, (double)j / K * inv_phi_c,
-                                            L->Dp, c->stream);
-                    }
-                    if ((s = field_from(c, L->Dp, L->tmap, L->tmap_ok, nullptr)) != HPF_OK)
-                        return s;
+            if (L->in_launch && c->warp_mode && c->sc.force_mode == 0) {
+                // one launch: the field of the predicted end density D(t) + dphi in
+                // G2, interpolated with the field of D(t) in the step kernel
+                {
+                    StageScope sc(c, HPF_STAGE_OTHER, 1);
+                    launch_mesh_predict(L->Dbase, L->dphi, SM, inv_phi_c, L->Dp, c->stream);
                 }
-                if ((s = advance(c, 1, j == K - 1)) != HPF_OK) return s;
+                if ((s = field_from(c, L->Dp, L->tmap, L->tmap_ok, nullptr, L->G2)) != HPF_OK)
+                    return s;
+                if ((s = advance(c, K, true, L->G2, 0, 1.0f / (float)K)) != HPF_OK) return s;
+            } else {
+                for (int j = 0; j < K; ++j) {
+                    if (j > 0) {
+                        {
+                            StageScope sc(c, HPF_STAGE_OTHER, 1);
+                            launch_mesh_predict(L->Dbase, L->dphi, SM, (double)j / K * inv_phi_c,
+                                                L->Dp, c->stream);
+                        }
+                        if ((s = field_from(c, L->Dp, L->tmap, L->tmap_ok, nullptr)) != HPF_OK)
+                            return s;
+                    }
+                    if ((s = advance(c, 1, j == K - 1)) != HPF_OK) return s;
+                }
             }
             c->field_valid = false;  // the field in force was a predicted one
             // judge the prediction for t + K against the true scatter there

@@ -850,6 +850,10 @@ int step_halo_max();
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,
                             cudaStream_t s);
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm, cudaStream_t s);
+// A learned window: the field (1 - j/K) G + j/K G2 at window step j (j0 at the
+// launch's first sub-step, inv_k = 1/K); a single context, force_mode 0.
+void launch_step_warp_lerp(const SingleStepParams& p, const float4* G2, int j0, float inv_k,
+                           int max_seg, int therm, cudaStream_t s);
 void launch_field_batch(const BatchFieldParams& p, int S, cudaStream_t s);
 int field_tile_candidates();
 bool field_tile_is_plain(int id);
@@ -868,6 +872,8 @@ bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);
 void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag);
 void launch_mesh_to_phi(const unsigned long long* D, long long n, double phi_c, float* phi,
                         cudaStream_t s);
+void launch_smooth_phi(const float* in, float* out, float* tmp, int mx, int my, int mz, int C,
+                       int passes, cudaStream_t s);
 void launch_mesh_predict(const unsigned long long* D_base, const float* dphi, long long n,
                          double frac_over_phi_c, unsigned long long* D_out, cudaStream_t s);
 // acc[0] = sum (Fa - Fb)^2, acc[1] = sum Fb^2 over n floats, deterministic;

@@ -919,6 +919,57 @@ __global__ void __launch_bounds__(256) k_force_error(const float* __restrict__ F
     }
 }
 
+// One pass of the periodic binomial filter (1/4, 1/2, 1/4) along one axis of
+// C channels of an FP32 [C][Mz][My][Mx] mesh: out(n) = (in(n - e) + 2 in(n) +
+// in(n + e)) / 4 with the neighbours e along the axis (periodic).
+__global__ void k_binomial_pass(const float* __restrict__ in, float* __restrict__ out, int mx,
+                                int my, int mz, int C, int axis) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)C * mx * my * mz;
+    if (i >= n) return;
+    const int x = (int)(i % mx), y = (int)((i / mx) % my), z = (int)((i / ((long long)mx * my)) % mz);
+    long long lo, hi;
+    if (axis == 0) {
+        lo = i - x + (x == 0 ? mx - 1 : x - 1);
+        hi = i - x + (x == mx - 1 ? 0 : x + 1);
+    } else if (axis == 1) {
+        const long long r = (long long)mx;
+        lo = i + (long long)((y == 0 ? my - 1 : y - 1) - y) * r;
+        hi = i + (long long)((y == my - 1 ? 0 : y + 1) - y) * r;
+    } else {
+        const long long r = (long long)mx * my;
+        lo = i + (long long)((z == 0 ? mz - 1 : z - 1) - z) * r;
+        hi = i + (long long)((z == mz - 1 ? 0 : z + 1) - z) * r;
+    }
+    out[i] = 0.25f * (in[lo] + in[hi]) + 0.5f * in[i];
+}
+
+// passes x 3 axes of the binomial filter from in to out, ping-ponging between
+// out and tmp (same size, distinct from out) so that the last pass writes out;
+// in may equal out.
+void launch_smooth_phi(const float* in, float* out, float* tmp, int mx, int my, int mz, int C,
+                       int passes, cudaStream_t s) {
+    const long long n = (long long)C * mx * my * mz;
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const int total = 3 * (passes > 0 ? passes : 0);
+    if (total == 0) {
+        if (in != out) cudaMemcpyAsync(out, in, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    const float* src = in;
+    for (int k = 0; k < total; ++k) {
+        float* dst = ((total - 1 - k) % 2 == 0) ? out : tmp;
+        if (dst == src) {  // only at the first pass, when in is the target buffer
+            float* other = dst == out ? tmp : out;
+            cudaMemcpyAsync(other, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+            src = other;
+        }
+        k_binomial_pass<<<blocks, 256, 0, s>>>(src, dst, mx, my, mz, C, k % 3);
+        src = dst;
+    }
+}
+
 void launch_mesh_to_phi(const unsigned long long* D, long long n, double phi_c, float* phi,
                         cudaStream_t s) {
     if (n > 0) k_mesh_to_phi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, n, phi_c, phi);

@@ -84,6 +84,54 @@ __device__ __forceinline__ int cell_base(const MeshGeom& g, float flx, float fly
     return (int)wz * g.gxy + (int)wy * g.gx + (int)wx;
 }
 
+// The eight corners (x, y, z offsets in {0, 1}) of cell (flx, fly, flz).
+struct Corners {
+    float4 g000, g100, g010, g110, g001, g101, g011, g111;
+};
+
+__device__ __forceinline__ Corners load_corners(const float4* __restrict__ Gt, const MeshGeom& g,
+                                                float flx, float fly, float flz) {
+    const int o00 = cell_base(g, flx, fly, flz);
+    const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
+    Corners k;
+    k.g000 = __ldg(Gt + o00);
+    k.g100 = __ldg(Gt + o00 + 1);
+    k.g010 = __ldg(Gt + o01);
+    k.g110 = __ldg(Gt + o01 + 1);
+    k.g001 = __ldg(Gt + o10);
+    k.g101 = __ldg(Gt + o10 + 1);
+    k.g011 = __ldg(Gt + o11);
+    k.g111 = __ldg(Gt + o11 + 1);
+    return k;
+}
+
+// The cell polynomial's coefficients from its corners into cache slot t
+// (component-major: planes 2j, 2j + 1 hold c0..c7 of component j; kForce 1:
+// planes 0 and 1 hold the polynomial of V).
+template <int kForce>
+__device__ __forceinline__ void store_cell_coefs(const Corners& k, float4* __restrict__ cache, int t,
+                                                 int stride) {
+#define HPF_COEF(comp, j)                                                                        \
+    {                                                                                            \
+        const float a0 = k.g000.comp, a1 = k.g100.comp - k.g000.comp;                            \
+        const float a2 = k.g010.comp - k.g000.comp, a3 = k.g001.comp - k.g000.comp;              \
+        const float a4 = (k.g110.comp - k.g100.comp) - a2;                                       \
+        const float a5 = (k.g101.comp - k.g100.comp) - a3;                                       \
+        const float a6 = (k.g011.comp - k.g010.comp) - a3;                                       \
+        const float a7 = ((k.g111.comp - k.g110.comp) - (k.g101.comp - k.g100.comp)) - a6;       \
+        cache[(2 * j) * stride + t] = make_float4(a0, a1, a2, a3);                               \
+        cache[(2 * j + 1) * stride + t] = make_float4(a4, a5, a6, a7);                           \
+    }
+    if (kForce == 1) {
+        HPF_COEF(w, 0)
+    } else {
+        HPF_COEF(x, 0)
+        HPF_COEF(y, 1)
+        HPF_COEF(z, 2)
+    }
+#undef HPF_COEF
+}
+
 // kForce 1: planes 0 and 1 hold the trilinear polynomial of V instead (the
 // exact-energy-gradient force differentiates it).  kForce 2: the key is the
 // nearest vertex and planes 0 and 1 hold its six staggered coefficients.
@@ -99,33 +147,7 @@ __device__ __forceinline__ void fill_cell_cache(const float4* __restrict__ Gt, c
         cache[stride + t] = make_float4(c[4], c[5], 0.f, 0.f);
         return;
     }
-    const int o00 = cell_base(g, flx, fly, flz);
-    const int o01 = o00 + g.gx, o10 = o00 + g.gxy, o11 = o10 + g.gx;
-    // corner (a, b, c) = offsets (x, y, z) in {0, 1}
-    const float4 g000 = __ldg(Gt + o00), g100 = __ldg(Gt + o00 + 1);
-    const float4 g010 = __ldg(Gt + o01), g110 = __ldg(Gt + o01 + 1);
-    const float4 g001 = __ldg(Gt + o10), g101 = __ldg(Gt + o10 + 1);
-    const float4 g011 = __ldg(Gt + o11), g111 = __ldg(Gt + o11 + 1);
-    // component-major: planes 2j, 2j+1 hold c0..c7 of component j
-#define HPF_COEF(comp, j)                                                                        \
-    {                                                                                            \
-        const float a0 = g000.comp, a1 = g100.comp - g000.comp, a2 = g010.comp - g000.comp;      \
-        const float a3 = g001.comp - g000.comp;                                                  \
-        const float a4 = (g110.comp - g100.comp) - a2;                                           \
-        const float a5 = (g101.comp - g100.comp) - a3;                                           \
-        const float a6 = (g011.comp - g010.comp) - a3;                                           \
-        const float a7 = ((g111.comp - g110.comp) - (g101.comp - g100.comp)) - a6;               \
-        cache[(2 * j) * stride + t] = make_float4(a0, a1, a2, a3);                               \
-        cache[(2 * j + 1) * stride + t] = make_float4(a4, a5, a6, a7);                           \
-    }
-    if (kForce == 1) {
-        HPF_COEF(w, 0)
-    } else {
-        HPF_COEF(x, 0)
-        HPF_COEF(y, 1)
-        HPF_COEF(z, 2)
-    }
-#undef HPF_COEF
+    store_cell_coefs<kForce>(load_corners(Gt, g, flx, fly, flz), cache, t, stride);
 }
 
 // The cache key of a mesh coordinate: its cell (floor), or its nearest
@@ -432,16 +454,23 @@ struct Bead {
 
 // The bead's cell: refill its cache of the cell polynomial when the bead
 // has entered another cell; returns the offsets inside the cell.
-template <int kForce>
+template <int kForce, int kLerp = 0>
 __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G, const MeshGeom& g,
                                            float4* __restrict__ cache, int slot, float& f0,
-                                           float& f1, float& f2) {
+                                           float& f1, float& f2,
+                                           const float4* __restrict__ G2 = nullptr) {
     const float s0 = __fmul_rn(b.x, g.inv_h[0]), s1 = __fmul_rn(b.y, g.inv_h[1]),
                 s2 = __fmul_rn(b.z, g.inv_h[2]);
     const float flx = cache_key<kForce>(s0), fly = cache_key<kForce>(s1),
                 flz = cache_key<kForce>(s2);
     if (flx != b.cfx || fly != b.cfy || flz != b.cfz) {
-        fill_cell_cache<kForce>(G + (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes, g, flx,
+        const size_t off = (size_t)((b.m >> kTypeShift) & kTypeMask) * g.gnodes;
+        if (kLerp) {
+            // the window's second field: its polynomial in planes 6..11
+            store_cell_coefs<0>(load_corners(G2 + off, g, flx, fly, flz),
+                                cache + kCachePlanes * 2 * kWarpBlock, slot, 2 * kWarpBlock);
+        }
+        fill_cell_cache<kForce>(G + off, g, flx,
                                 fly, flz, cache, slot, 2 * kWarpBlock);
         b.cfx = flx;
         b.cfy = fly;
@@ -456,14 +485,29 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
 // noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
 // chain neighbours.  Andersen (kTherm 2): a colliding bead's on-step velocity
 // is sqrt(kT/m) (nx, ny, nz) before the second half kick.
-template <int kTherm, int kForce>
+template <int kTherm, int kForce, int kLerp = 0>
 __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
                                           float ny, float nz, float bx, float by, float bz,
                                           const StepConsts& c, const MeshGeom& g,
                                           const float4* __restrict__ cache, int slot,
-                                          bool coll) {
+                                          bool coll, float a = 0.f) {
     float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
-    eval_cell_cache<kForce>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
+    if (kLerp) {
+        // the field (1 - a) G0 + a G2: P0 + a (P2 - P0) of the two cached polynomials
+        constexpr int st = 2 * kWarpBlock;
+        const float4* c2 = cache + kCachePlanes * st;
+        const float p0x = cell_poly(cache[0 * st + slot], cache[1 * st + slot], f0, f1, f2);
+        const float p0y = cell_poly(cache[2 * st + slot], cache[3 * st + slot], f0, f1, f2);
+        const float p0z = cell_poly(cache[4 * st + slot], cache[5 * st + slot], f0, f1, f2);
+        const float p2x = cell_poly(c2[0 * st + slot], c2[1 * st + slot], f0, f1, f2);
+        const float p2y = cell_poly(c2[2 * st + slot], c2[3 * st + slot], f0, f1, f2);
+        const float p2z = cell_poly(c2[4 * st + slot], c2[5 * st + slot], f0, f1, f2);
+        fx -= fmaf(a, p2x - p0x, p0x);
+        fy -= fmaf(a, p2y - p0y, p0y);
+        fz -= fmaf(a, p2z - p0z, p0z);
+    } else {
+        eval_cell_cache<kForce>(cache, slot, f0, f1, f2, fx, fy, fz, g, 2 * kWarpBlock);
+    }
     if (kTherm == 1) {
         fx = fmaf(c.sigma, nx, fx);
         fy = fmaf(c.sigma, ny, fy);
@@ -508,14 +552,16 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
 }
 
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <int kTherm, int kForce, int kBonded>
+template <int kTherm, int kForce, int kBonded, int kLerp = 0>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
                                                 const MeshGeom& g, const float4* __restrict__ G,
                                                 const StepConsts& c,
                                                 unsigned long long* __restrict__ D_next,
-                                                int* __restrict__ flag, float4* wcache, int tid) {
+                                                int* __restrict__ flag, float4* wcache, int tid,
+                                                const float4* __restrict__ G2 = nullptr,
+                                                int lerp_j0 = 0, float lerp_inv_k = 0.f) {
     const int lane = tid & 31;
     const float nan = __int_as_float(0x7fc00000);
     const int j0 = 2 * lane, j1 = j0 + 1;
@@ -543,8 +589,8 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
                                     w0y, w0z, w1x, w1y, w1z);
         // the two beads' phases side by side, so their independent work interleaves
         float f00, f01, f02, f10, f11, f12;
-        cell_check<kForce>(b0, G, g, wcache, tid, f00, f01, f02);
-        cell_check<kForce>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
+        cell_check<kForce, kLerp>(b0, G, g, wcache, tid, f00, f01, f02, G2);
+        cell_check<kForce, kLerp>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12, G2);
         float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
         bool coll0 = false, coll1 = false;
         if (kTherm == 1) {
@@ -557,10 +603,12 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
             if (coll0) gauss3(c, b0.m & kTagMask, step0 + k, g0x, g0y, g0z);
             if (coll1) gauss3(c, b1.m & kTagMask, step0 + k, g1x, g1y, g1z);
         }
-        kick_bead<kTherm, kForce>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache,
-                                  tid, coll0);
-        kick_bead<kTherm, kForce>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
-                                  kWarpBlock + tid, coll1);
+        // window fraction of this sub-step (the learned field's interpolation)
+        const float a = kLerp ? (float)(lerp_j0 + k) * lerp_inv_k : 0.f;
+        kick_bead<kTherm, kForce, kLerp>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g,
+                                         wcache, tid, coll0, a);
+        kick_bead<kTherm, kForce, kLerp>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g,
+                                         wcache, kWarpBlock + tid, coll1, a);
         b0.x = fmaf(c.dt, b0.vx, b0.x);
         b0.y = fmaf(c.dt, b0.vy, b0.y);
         b0.z = fmaf(c.dt, b0.vz, b0.z);
@@ -613,6 +661,45 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
     }
+}
+
+// A learned window in one launch (a single context, interpolated-gradient
+// force): the field at window step j is (1 - j/K) G0 + (j/K) G2, G0 the field
+// of the true density at the window start and G2 that of the predicted
+// density at its end -- the field of D(t) + (j/K) dphi, since the field is
+// linear in the density.  Each bead caches both cells' polynomials (twelve
+// planes); the launch's first sub-step is window step j0.
+constexpr size_t kWarpSmemLerp = 2 * sizeof(float4) * kCachePlanes * 2 * kWarpBlock;
+
+template <int kTherm, int kBonded>
+__global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_lerp(
+    const __grid_constant__ SingleStepParams p, const float4* __restrict__ G2, int j0,
+    float inv_k) {
+    griddep_wait();
+    griddep_launch_dependents();
+    extern __shared__ float4 wcache[];
+    const int tid = threadIdx.x;
+    const BatchStepRep& rp = p.rep[0];
+    const int total = *rp.n_seg;
+    const int warps_total = gridDim.x * (kWarpBlock / 32);
+    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < total; w += warps_total)
+        advance_segment<kTherm, 0, kBonded, 1>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+                                               rp.seg_start[w], rp.seg_count[w], p.n_sub,
+                                               p.step0, rp.g, rp.G, rp.c,
+                                               p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache,
+                                               tid, G2, j0, inv_k);
+}
+
+template <int kTherm, int kBonded>
+static void launch_lerp_k(const SingleStepParams& p, const float4* G2, int j0, float inv_k,
+                          int blocks, cudaStream_t s) {
+    static std::once_flag once[64];
+    once_per_device(once, [] {
+        cudaFuncSetAttribute(k_step_warp_lerp<kTherm, kBonded>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpSmemLerp);
+    });
+    launch_pdl(k_step_warp_lerp<kTherm, kBonded>, blocks, kWarpBlock, kWarpSmemLerp, s, p, G2, j0,
+               inv_k);
 }
 
 template <int kCap, int kTherm, int kForce>
@@ -701,6 +788,28 @@ void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int the
     const int need = (max_seg_total + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
     const int blocks = need < cap ? need : cap;
     launch_warp(p, blocks, therm, p.rep[0].c.force_mode, s);  // replicas share the force mode
+}
+
+void launch_step_warp_lerp(const SingleStepParams& p, const float4* G2, int j0, float inv_k,
+                           int max_seg, int therm, cudaStream_t s) {
+    if (max_seg <= 0 || p.n_sub <= 0) return;
+    const int cap = warp_grid_cap();
+    const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+    const int blocks = need < cap ? need : cap;
+    const int bonded = bonded_level(p.rep[0].c);
+    if (therm == 1) {
+        if (bonded == 2) launch_lerp_k<1, 2>(p, G2, j0, inv_k, blocks, s);
+        else if (bonded == 1) launch_lerp_k<1, 1>(p, G2, j0, inv_k, blocks, s);
+        else launch_lerp_k<1, 0>(p, G2, j0, inv_k, blocks, s);
+    } else if (therm == 2) {
+        if (bonded == 2) launch_lerp_k<2, 2>(p, G2, j0, inv_k, blocks, s);
+        else if (bonded == 1) launch_lerp_k<2, 1>(p, G2, j0, inv_k, blocks, s);
+        else launch_lerp_k<2, 0>(p, G2, j0, inv_k, blocks, s);
+    } else {
+        if (bonded == 2) launch_lerp_k<0, 2>(p, G2, j0, inv_k, blocks, s);
+        else if (bonded == 1) launch_lerp_k<0, 1>(p, G2, j0, inv_k, blocks, s);
+        else launch_lerp_k<0, 0>(p, G2, j0, inv_k, blocks, s);
+    }
 }
 
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm,

@@ -154,6 +154,9 @@ def load():
         L.hpf_prop_train_step.argtypes = [vp, vp, vp, ctypes.c_float, dp]
         L.hpf_density_phi.argtypes = [vp, vp]
         L.hpf_judge_density.argtypes = [vp, vp, dp]
+        L.hpf_smooth_phi.argtypes = [vp, vp, vp, i32]
+        L.hpf_learned_mode.argtypes = [vp, i32]
+        L.hpf_judge_density_pair.argtypes = [vp, vp, vp, dp]
         L.hpf_step_learned.argtypes = [vp, vp, i32, i32, ctypes.c_double,
                                        ctypes.POINTER(LearnedStats)]
         for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
@@ -161,7 +164,8 @@ def load():
                      "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_rollout",
                      "hpf_prop_backward",
                      "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
-                     "hpf_judge_density", "hpf_step_learned"):
+                     "hpf_judge_density", "hpf_step_learned", "hpf_smooth_phi", "hpf_learned_mode",
+                     "hpf_judge_density_pair"):
             getattr(L, name).restype = ctypes.c_int
         del fp
         for name in ("hpf_init", "hpf_destroy", "hpf_set_state", "hpf_get_state", "hpf_update_state",
@@ -481,6 +485,28 @@ class System:
         eps = ctypes.c_double()
         self._check(self.lib.hpf_judge_density(self.h, pp, ctypes.byref(eps)))
         return eps.value
+
+    def learned_mode(self, in_launch=True):
+        """hpf_learned_mode: learned windows in one launch (True) or per step."""
+        self._check(self.lib.hpf_learned_mode(self.h, 1 if in_launch else 0))
+
+    def smooth_phi(self, phi, passes, out=None):
+        """hpf_smooth_phi: the periodic binomial filter, passes times per axis."""
+        if out is None:
+            out = np.empty(self.mesh_shape, dtype=np.float32)
+        ip, _a = _ptr(phi, np.float32, self.mesh_shape, "phi_in")
+        op, _b = _ptr(out, np.float32, self.mesh_shape, "phi_out")
+        self._check(self.lib.hpf_smooth_phi(self.h, ip, op, int(passes)))
+        return out
+
+    def judge_density_pair(self, phi_cand, phi_ref):
+        """hpf_judge_density_pair: eps of the candidate's field force against
+        the reference density's, at the current positions."""
+        cp, _a = _ptr(phi_cand, np.float32, self.mesh_shape, "phi_cand")
+        rp, _b = _ptr(phi_ref, np.float32, self.mesh_shape, "phi_ref")
+        eps = ctypes.c_double()
+        self._check(self.lib.hpf_judge_density_pair(self.h, cp, rp, ctypes.byref(eps)))
+        return float(eps.value)
 
     def step_learned(self, prop, n_windows, K=20, tol=1e-3):
         """n_windows windows of K steps with the learned propagator; returns the stats dict."""

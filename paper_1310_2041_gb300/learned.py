@@ -166,3 +166,49 @@ def judge_rollout(system: hpf.System, prop: hpf.Propagator, n_windows: int, K: i
         system.density_phi(cur)
         res.append(system.judge_density(pred))
     return res
+
+
+def collect_smoothed(system: hpf.System, n_snap: int, K: int, passes: int):
+    """collect_snapshots with every phi passed through the binomial filter
+    (hpf_smooth_phi) in place."""
+    snaps = collect_snapshots(system, n_snap, K)
+    for k in range(n_snap):
+        system.smooth_phi(snaps[k], passes, out=snaps[k])
+    return snaps
+
+
+def judge_smoothed(system: hpf.System, passes: int, prop: hpf.Propagator | None,
+                   n_windows: int, K: int, lags=(1, 2, 5, 10, 20)):
+    """The smoothed-density variant of judge_candidates: every density, the
+    true one included, passes through the binomial filter before its field is
+    formed (hpf_smooth_phi), and eps compares a candidate's field force with
+    that of the smoothed true density at the same positions
+    (hpf_judge_density_pair).  Candidates: hold-last s(t - L), linear
+    extrapolation 2 s(t - L) - s(t - 2 L), and with a network trained on
+    smoothed snapshots at lag K its prediction from (s(t - 2K), s(t - K)).
+    ``system`` should refresh its field every step.  Returns {name: [eps]}."""
+    import torch
+    H = 2 * max(max(lags), K)
+    hist = torch.empty((H + 1,) + system.mesh_shape, dtype=torch.float32, device="cuda")
+    res = {f"hold_{L}": [] for L in lags}
+    res.update({f"linear_{L}": [] for L in lags})
+    res["net"] = []
+    n_steps = n_windows * K + H
+    for s in range(n_steps + 1):
+        cur = hist[s % (H + 1)]
+        system.density_phi(cur)
+        system.smooth_phi(cur, passes, out=cur)
+        if s >= H:
+            for L in lags:
+                if (s - H) % L == 0:
+                    prev = hist[(s - L) % (H + 1)]
+                    prev2 = hist[(s - 2 * L) % (H + 1)]
+                    res[f"hold_{L}"].append(system.judge_density_pair(prev, cur))
+                    res[f"linear_{L}"].append(system.judge_density_pair(2 * prev - prev2, cur))
+            if prop is not None and (s - H) % K == 0:
+                a, b = hist[(s - 2 * K) % (H + 1)], hist[(s - K) % (H + 1)]
+                pred = prop.rollout(torch.cat([a, b]).contiguous(), 1, out=torch.empty_like(b))
+                res["net"].append(system.judge_density_pair(pred, cur))
+        if s < n_steps:
+            system.step(1)
+    return res

@@ -354,6 +354,31 @@ def test_learned_window_judges_its_prediction(hpf_gpu):
     assert 0.0 < eps < 10.0
 
 
+def test_learned_window_in_one_launch_matches_per_step(hpf_gpu):
+    """hpf_learned_mode: a learned window in one launch (the step kernel
+    interpolating the fields of D(t) and D(t) + dphi) against one launch per
+    step on the refreshed fixed-point meshes D(t) + (j/K) dphi.  The field is
+    linear in the density, so the two differ by rounding only: the same
+    windows accepted, the same judged eps to 1e-3, trajectories within the
+    trajectory bar (1e-4)."""
+    K = 6
+    w, pp, data = melt(hpf_gpu, field_every=1)
+    params = hpf_gpu.pack_params([(W * 0.3, b) for W, b in P.init_params(4)])
+    out = []
+    for in_launch in (True, False):
+        a = system(hpf_gpu, pp, data)
+        a.learned_mode(in_launch)
+        with hpf_gpu.Propagator((10, 10, 10)) as net:
+            net.set_weights(params)
+            st = a.step_learned(net, 4, K=K, tol=1e9)
+        out.append((st, a.get_state()))
+        a.close()
+    (s1, (p1, v1, t1)), (s2, (p2, v2, t2)) = out
+    assert s1["learned"] == s2["learned"] == 3 and t1 == t2 == 4 * K
+    assert np.max(np.abs(p1 - p2)) <= 1e-4 and np.max(np.abs(v1 - v2)) <= 1e-4
+    assert s1["eps_last"] == pytest.approx(s2["eps_last"], rel=1e-3)
+
+
 def test_trained_network_beats_holding_the_last_density(hpf_gpu):
     """What the network gains over the method without it (holding the density
     of the last true update, i.e. a frozen field between updates): trained on
@@ -518,3 +543,42 @@ def test_rollout_feeds_predictions_back(hpf_gpu):
     np.testing.assert_array_equal(got, b)
     ye, _, _, _ = E.forward(params, x.astype(np.float64), 20.0)
     within_emulated(one - x[2:], ye, "one rollout step")
+
+
+def test_smooth_phi_matches_oracle(hpf_gpu):
+    """hpf_smooth_phi (FP32) against the oracle's binomial filter (FP64) on a
+    ragged mesh, in place and out of place."""
+    w = W.diblock(300, 5, 5, 11.0, 11, 1.0)
+    d = W.generate(w)
+    pp = w.params()
+    pp["mesh"] = (13, 10, 5)
+    rng = np.random.default_rng(41)
+    phi = rng.uniform(0.0, 1.2, size=(2, 5, 10, 13)).astype(np.float32)
+    with hpf_gpu.System(hpf_gpu.make_params(**pp)) as s:
+        s.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+        for passes in (0, 1, 4):
+            got = s.smooth_phi(phi, passes)
+            ref = P.smooth(phi.astype(np.float64), passes)
+            assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref)), passes
+        import torch
+        t = torch.from_numpy(phi).cuda()
+        s.smooth_phi(t, 3, out=t)
+        np.testing.assert_allclose(t.cpu().numpy(), P.smooth(phi.astype(np.float64), 3),
+                                   rtol=0, atol=1e-6)
+
+
+def test_judge_density_pair(hpf_gpu):
+    """eps of a density against itself is zero; against the true density it
+    is hpf_judge_density's eps (the reference taken through FP32 phi)."""
+    w = W.diblock(400, 5, 5, 10.0, 10, 1.0)
+    d = W.generate(w)
+    with hpf_gpu.System(hpf_gpu.make_params(**w.params())) as s:
+        s.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+        true = s.density_phi()
+        rng = np.random.default_rng(43)
+        cand = (true + rng.normal(0.0, 0.02, true.shape)).astype(np.float32)
+        assert s.judge_density_pair(cand, cand) == 0.0
+        e_pair = s.judge_density_pair(cand, true)
+        e_true = s.judge_density(cand)
+        assert e_true > 1e-3
+        assert abs(e_pair - e_true) <= 1e-5 * e_true + 1e-7

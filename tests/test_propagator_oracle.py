@@ -137,3 +137,37 @@ def test_change_scale_enters_the_change_channels_and_the_output_only():
     yp1, _ = P.forward([(W1p, b1), mid, (W3, b3)], x)
     yps, _ = P.forward([(W1p, b1), mid, (W3, b3)], x, s)
     np.testing.assert_allclose(yps * s, yp1, rtol=1e-12, atol=1e-14)
+
+
+# ---- the binomial filter of the smoothed-density variant
+
+def test_smooth_keeps_constants_and_the_total():
+    rng = np.random.default_rng(7)
+    c = np.full((2, 6, 5, 7), 0.37)
+    np.testing.assert_allclose(P.smooth(c, 3), c, rtol=0, atol=1e-15)
+    a = rng.uniform(0.0, 1.0, size=(2, 6, 5, 7))
+    np.testing.assert_allclose(P.smooth(a, 4).sum(axis=(1, 2, 3)), a.sum(axis=(1, 2, 3)),
+                               rtol=1e-13)
+
+
+def test_smooth_spike_is_the_binomial_distribution():
+    """A unit spike on a mesh wider than the filter's reach becomes, per axis,
+    C(2p, k) / 4^p at offsets k - p (p passes), the product over the axes."""
+    from math import comb
+    p, M = 3, 15
+    a = np.zeros((1, M, M, M))
+    a[0, 7, 7, 7] = 1.0
+    got = P.smooth(a, p)
+    w = np.zeros(M)
+    for k in range(2 * p + 1):
+        w[7 - p + k] = comb(2 * p, k) / 4.0 ** p
+    np.testing.assert_allclose(got[0], np.einsum("i,j,k->ijk", w, w, w), rtol=0, atol=1e-15)
+
+
+def test_smooth_attenuates_a_sinusoid_by_the_closed_form():
+    """sin(2 pi m x / M) along x: each pass multiplies it by cos^2(pi m / M)."""
+    M, m, p = 16, 3, 5
+    x = np.arange(M)
+    a = np.broadcast_to(np.sin(2 * np.pi * m * x / M), (1, 4, 3, M)).copy()
+    f = np.cos(np.pi * m / M) ** (2 * p)
+    np.testing.assert_allclose(P.smooth(a, p), f * a, rtol=0, atol=1e-13)
