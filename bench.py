@@ -865,7 +865,7 @@ def run_learned(args):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src,
-                         "kernel": "k_conv_tc (three layers, whole forward)",
+                         "kernel": "k_conv_sweep (three layers, whole forward)",
                          "algo_flops_per_inference": flops},
             "roofline_hbm": {"bound": "hbm", "achieved": infer_bytes / (infer_ms * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
@@ -932,7 +932,7 @@ def run_propagator(args):
                        "l2": "flushed (256 MB write) before each timed inference"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_src, "kernel": "k_conv_tc (three layers)",
+                         "peak_source": peak_src, "kernel": "k_conv_sweep (three layers)",
                          "algo_flops_per_inference": flops},
             "roofline_hbm": {"bound": "hbm", "achieved": infer_bytes / (infer_ms * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",

@@ -442,7 +442,9 @@ hpf_status hpf_batch_destroy(hpf_batch* batch);
  * in[ci](n + d) over the 27 offsets d = (dz, dy, dx) in {-1, 0, 1}^3, z-major.
  * Weights and activations are BF16 on the tensor cores with FP32
  * accumulation (forward and data gradients on tcgen05 with tensor-memory
- * accumulators); the master parameters and Adam state are FP32.  The
+ * accumulators; the forward convolutions are persistent, one CTA per SM
+ * sweeping columns of the mesh along z); the master parameters and Adam
+ * state are FP32.  The
  * tensor-core waits are bounded: one that gives up makes the next call that
  * synchronises return HPF_ERR_TIMEOUT (once).
  *
@@ -465,6 +467,11 @@ int32_t hpf_prop_param_count(void);
  * with the weights. */
 hpf_status hpf_prop_set_scale(hpf_prop* prop, float scale);
 hpf_status hpf_prop_get_scale(const hpf_prop* prop, float* scale);
+
+/* At most ctas CTAs for the persistent forward convolutions (the output
+ * planes are split evenly over them); 0 restores one CTA per SM.  Results do
+ * not depend on it.  Errors: HPF_ERR_INVALID (ctas < 0). */
+hpf_status hpf_prop_set_ctas(hpf_prop* prop, int32_t ctas);
 
 /* Load [param_count] FP32 parameters (and reset Adam); synchronises. */
 hpf_status hpf_prop_set_weights(hpf_prop* prop, const float* params);

@@ -861,6 +861,11 @@ void field_tile_shape(int id, int out[3]);
 void launch_field_tiled(const TiledFieldParams& p, int S, int tile, cudaStream_t s);
 void launch_wait_selftest(int* flag, cudaStream_t s);
 void launch_field_tiled(const SingleFieldParams& p, int S, int tile, cudaStream_t s);
+// cuTensorMapEncodeTiled through the runtime's driver entry point: unit element
+// strides, no interleave, no swizzle, 128-byte L2 promotion, zero fill out of
+// range.  False when the entry point is missing or the encoding is refused.
+bool encode_tiled_map(CUtensorMap* map, CUtensorMapDataType type, int rank, void* base,
+                      const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box);
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile);
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);

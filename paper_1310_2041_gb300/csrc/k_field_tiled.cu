@@ -434,14 +434,23 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
+bool encode_tiled_map(CUtensorMap* map, CUtensorMapDataType type, int rank, void* base,
+                      const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, type, (cuuint32_t)rank, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 // A tensor map over the int64 mesh D [S][Mz][My][Mx] with the box of `tile`.
 // False when TMA cannot be used (odd Mx, unaligned base, no driver entry point).
 bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& g, int S,
                           int tile) {
     if (field_tile_is_plain(tile)) return false;
     if (g.mx % 2 != 0 || (reinterpret_cast<uintptr_t>(D) & 15u) != 0 || S > 4) return false;
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
     const int* t = kTileShapes[tile];
     const cuuint64_t dims[4] = {(cuuint64_t)g.mx, (cuuint64_t)g.my, (cuuint64_t)g.mz,
                                 (cuuint64_t)S};
@@ -449,11 +458,8 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
                                    (cuuint64_t)g.mx * g.my * g.mz * 8};
     const cuuint32_t box[4] = {(cuuint32_t)(t[0] + 4), (cuuint32_t)(t[1] + 2),
                                (cuuint32_t)(t[2] + 2), (cuuint32_t)S};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<long long*>(D), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
+    return encode_tiled_map(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<long long*>(D),
+                            dims, strides, box);
 }
 
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks) {

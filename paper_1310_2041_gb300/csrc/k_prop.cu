@@ -1,13 +1,16 @@
 // k_prop.cu -- the learned density propagator: a 3-D periodic conv net
 // (4 -> 16 -> 16 -> 2 channels, 3x3x3 kernels, SiLU) on BF16 tensor cores.
 //
-// Activations are channels-last BF16 [V][16] (channels padded to 16 with
-// zeros; V = Mz My Mx, x fastest).  The forward and data-gradient
-// convolutions run on the fifth-generation tensor cores (k_conv_tc: tcgen05
-// MMAs from shared-memory descriptors into tensor-memory accumulators, one
-// MMA per input plane and in-plane offset feeding three output planes); the
-// first layer's four input channels enter as an x-im2col, so its three x
-// offsets share one K = 16 step.  The weight gradient reduces over voxels with
+// Forward convolutions (k_conv_sweep): persistent, warp-specialised kernels
+// that sweep columns of the mesh along z -- TMA loads of padded activation
+// planes, tcgen05 MMAs with tensor-memory accumulators in a ring of output
+// planes, an epilogue that gathers the x offsets from neighbouring lanes.
+// Activations between the forward layers live in a periodically padded
+// layout [2][Mz + 2][PY][PX][8] (channel halves planar); the first layer's
+// four input channels enter as an x-im2col, so its three x offsets share one
+// K = 16 step.  Training keeps the plain channels-last layout [V][16] for the
+// back-propagated gradients: the data-gradient convolutions run on a tiled
+// tcgen05 kernel (k_conv_tc), the weight gradient reduces over voxels with
 // warp-level MMAs (ldmatrix.trans operands), accumulating in registers over
 // many tiles before writing one partial block per CTA.
 #include <cuda_bf16.h>
@@ -86,17 +89,27 @@ __device__ __forceinline__ void tile_origin(const PropGeom& g, int t, int& x0, i
 // ldmatrix phase reads (always eight consecutive rows here) hit distinct banks.
 __device__ __forceinline__ int swz(int row, int half) { return 2 * row + (half ^ ((row >> 2) & 1)); }
 
+// Where the voxels of an activation buffer live: channel half h (8 channels)
+// of voxel (x, y, z) at element (((z + off) ly + y + off) lx + x + off) vs +
+// h hs -- the plain layout [V][16] (lx = Mx, ly = My, off = 0, vs = 16, hs =
+// 8) or the padded one of the forward convolutions [2][Mz + 2][PY][PX][8]
+// (off = 1, vs = 8, hs = (Mz + 2) PY PX 8).
+struct ActLayout {
+    int lx, ly, off;
+    long long vs, hs;
+};
+
 // Periodic input box of a tile (all 16 channels), 16-byte asynchronous copies.
 __device__ __forceinline__ void load_box(const __nv_bfloat16* __restrict__ in, const PropGeom& g,
-                                         int x0, int y0, int z0, uint4* box) {
+                                         const ActLayout& L, int x0, int y0, int z0, uint4* box) {
     const uint32_t box_s = saddr(box);
     for (int e = threadIdx.x; e < kBoxVox * 2; e += blockDim.x) {
         const int v = e >> 1, half = e & 1;
         const int bx = v % kBX, by = (v / kBX) % kBY, bz = v / (kBX * kBY);
         const int gx = pwrap(x0 - 1 + bx, g.mx), gy = pwrap(y0 - 1 + by, g.my),
                   gz = pwrap(z0 - 1 + bz, g.mz);
-        const size_t gv = ((size_t)gz * g.my + gy) * g.mx + gx;
-        cp_async16(box_s + 16 * swz(v, half), in + gv * kPC + 8 * half);
+        const size_t gv = ((size_t)(gz + L.off) * L.ly + gy + L.off) * L.lx + gx + L.off;
+        cp_async16(box_s + 16 * swz(v, half), in + gv * L.vs + half * L.hs);
     }
 }
 
@@ -115,14 +128,12 @@ __device__ __forceinline__ int box_row(int lx, int ly, int lz, int o) {
     return ((lz + 1 + dz) * kBY + (ly + 1 + dy)) * kBX + (lx + 1 + dx);
 }
 
-// ------------------------------------------------------------------ convolution
-
-enum ConvMode { kHidden = 0, kLast = 1, kData = 2 };
-
-// ------------------------------------------------------------------ tcgen05 convolution
+// ------------------------------------------------------------------ tcgen05 data gradients
 //
-// The forward and data-gradient convolutions on the fifth-generation tensor
-// cores.  A CTA (one warpgroup) works on tiles of 8 x 16 x 4 voxels; a
+// The data-gradient convolutions of training (a convolution of the back-
+// propagated gradient with flipped, transposed weights, no bias, FP32 out) on
+// the fifth-generation tensor cores.  A CTA (one warpgroup) works on tiles of
+// 8 x 16 x 4 voxels of the plain channels-last layout [V][16]; a
 // z-plane of a tile is 128 voxels = the 128 rows of one MMA (eight
 // x-consecutive voxels per 8-row core-matrix group, one group per y row).
 // The periodic 10 x 18 x 6 input box sits in shared memory as two planes of
@@ -141,15 +152,12 @@ enum ConvMode { kHidden = 0, kLast = 1, kData = 2 };
 // plane and in-plane offset updates all three; at the tile's first and last
 // input planes fewer planes exist (N = 16 or 32).  That is 6 x 9 MMAs per
 // tile instead of 27 x 4 of width 16, and every MMA reads its A operand once
-// for three output planes.  The two-channel last layer keeps 2 columns per
-// plane and N = 16: its weight rows past the 6 real ones are zero, so the
-// columns an MMA spills into are only added zeros.  The accumulators are
-// cleared by tcgen05.st before the tile's MMAs, which then all accumulate.
+// for three output planes.  The accumulators are cleared by tcgen05.st
+// before the tile's MMAs, which then all accumulate.
 //
-// One thread issues the MMAs and commits them to an mbarrier; the box of
-// the next tile is loaded and the epilogue of the previous tile (tcgen05.ld,
-// bias, SiLU, BF16 or FP32 stores) runs meanwhile: two box buffers and two
-// tensor-memory accumulator sets.  Waits are bounded (kTcWaitLimit polls);
+// One thread issues the MMAs and commits them to an mbarrier; all eight warps
+// then read the accumulators back (tcgen05.ld) for the FP32 stores.  Waits are
+// bounded (kTcWaitLimit polls);
 // a wait that gives up sets kFlagTimeout and the CTA stops after releasing
 // its tensor memory.
 constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;
@@ -158,7 +166,6 @@ constexpr int kTcPlane = kTcBX * kTcBY;   // box voxels per z-plane
 constexpr int kTcBox = kTcPlane * kTcBZ;  // 1080 voxels per channel half
 constexpr int kTcInPlane = 9;             // in-plane offsets (dy, dx)
 constexpr int kTcRows16 = 48;             // B rows per in-plane offset: (dz, co)
-constexpr int kTcRows2 = 24;              // 6 real rows (dz, co < 2), then zeros
 constexpr int kTcCols = 64;               // accumulator columns per set: 4 planes x 16
 constexpr unsigned kTcWaitLimit = 1u << 22;
 constexpr int kTcThreads = 256;          // two warps per tensor-memory lane quarter
@@ -168,17 +175,12 @@ constexpr size_t tc_smem_bytes(int kBuf) {
     return sizeof(uint4) * ((size_t)kBuf * 2 * kTcBox + 2 * kTcInPlane * kTcRows16) + 64;
 }
 
-// The weight images of the tensor-core convolutions, [copy][half][in-plane
-// offset][B row]: 0 first layer (x-im2col, kIP 3), 1 second layer, 2 last
-// layer (kCB 2), 3 and 4 the data gradients of the second and last layers.
-constexpr int kTcImages = 5;
-__host__ __device__ constexpr int tc_image_cb(int k) { return k == 2 ? 2 : 16; }
-__host__ __device__ constexpr int tc_image_ip(int k) { return k == 0 ? 3 : 9; }
-__host__ __device__ constexpr int tc_image_words(int k) {   // uint4 per copy
-    return 2 * tc_image_ip(k) * (tc_image_cb(k) == 16 ? kTcRows16 : kTcRows2);
-}
+// The weight images of the data-gradient convolutions, [copy][half][in-plane
+// offset][B row]: 0 the second layer's, 1 the last layer's.
+constexpr int kTcImages = 2;
+constexpr int kTcImageWords = 2 * kTcInPlane * kTcRows16;  // uint4 per copy
 __host__ __device__ constexpr int tc_image_offset(int k) {  // uint4, all copies
-    return k == 0 ? 0 : tc_image_offset(k - 1) + kTcWCopies * tc_image_words(k - 1);
+    return k * kTcWCopies * kTcImageWords;
 }
 
 // Shared-memory matrix descriptor: start address, leading and stride byte
@@ -272,87 +274,41 @@ __device__ __forceinline__ void tc_zero_cols16(uint32_t taddr) {
 }
 
 // Epilogue of one output plane: the warp's 32 accumulator rows (lanes 32w ..)
-// from columns col .. col + kCB - 1, voxel (x0 + row % 8, y0 + row / 8, z).
-template <int kMode, int kCB>
+// from columns col .. col + 15, voxel (x0 + row % 8, y0 + row / 8, z), FP32.
 __device__ __forceinline__ void tc_epilogue(uint32_t tcol, const PropGeom& g, int x0, int y0,
-                                            int z, const float* __restrict__ bias,
-                                            float* __restrict__ z_out,
-                                            __nv_bfloat16* __restrict__ act_out,
-                                            float* __restrict__ f_out) {
+                                            int z, float* __restrict__ f_out) {
     const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 3;  // lane quarter
     const uint32_t taddr = tcol + ((uint32_t)(32 * w) << 16);
     float acc[16];
-    if (kCB == 16) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = __uint_as_float(r[c]);
-    } else {
-        uint32_t r0, r1;
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                     : "=r"(r0), "=r"(r1)
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        acc[0] = __uint_as_float(r0);
-        acc[1] = __uint_as_float(r1);
-    }
+    for (int c = 0; c < 16; ++c) acc[c] = __uint_as_float(r[c]);
     const int row = 32 * w + lane;
     const int X = x0 + (row & 7), Y = y0 + (row >> 3);
     if (X >= g.mx || Y >= g.my || z >= g.mz) return;
     const size_t gv = ((size_t)z * g.my + Y) * g.mx + X;
-    if (kMode != kData) {
+    float4* fo = reinterpret_cast<float4*>(f_out + gv * kPC);
 #pragma unroll
-        for (int c = 0; c < kCB; ++c) acc[c] += bias[c];
-    }
-    if (kMode == kHidden) {
-        if (z_out) {
-            float4* zo = reinterpret_cast<float4*>(z_out + gv * kPC);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        }
-        __nv_bfloat162 h[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float a = acc[2 * c], b = acc[2 * c + 1];
-            h[c] = __floats2bfloat162_rn(__fdividef(a, 1.0f + __expf(-a)),
-                                         __fdividef(b, 1.0f + __expf(-b)));
-        }
-        uint4* ao = reinterpret_cast<uint4*>(act_out + gv * kPC);
-        ao[0] = reinterpret_cast<uint4*>(h)[0];
-        ao[1] = reinterpret_cast<uint4*>(h)[1];
-    } else if (kCB == 2) {
-        *reinterpret_cast<float2*>(f_out + gv * kPC) = make_float2(acc[0], acc[1]);
-    } else {
-        float4* fo = reinterpret_cast<float4*>(f_out + gv * kPC);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            fo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-    }
+    for (int q = 0; q < 4; ++q)
+        fo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
-// W: the layer's padded BF16 weights [3 kIP][16 out][16 in] (forward or data
-// gradient), offset index dz_index * kIP + in-plane offset; kCB output
-// channels per plane (16, or 2 for the last layer).  kIP = 9: in-plane
-// offsets (dy, dx), K = 16 input channels.  kIP = 3: in-plane offsets dy only;
-// the input is the x-im2col of a 4-channel layer (K index (dx + 1) * 4 + ci,
-// see k_pack_input) and the weights follow that K order.
-template <int kMode, int kCB, int kIP, int kBuf>
-__global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1) k_conv_tc(const __nv_bfloat16* __restrict__ in,
-                                                 const uint4* __restrict__ Wp,
-                                                 const float* __restrict__ bias,
-                                                 float* __restrict__ z_out,
-                                                 __nv_bfloat16* __restrict__ act_out,
-                                                 float* __restrict__ f_out, PropGeom g,
-                                                 int n_tiles, int* __restrict__ flag) {
-    constexpr int kRows = kCB == 16 ? kTcRows16 : kTcRows2;
+// Wp: a packed weight image (k_pack_tc_image) of the data-gradient weights
+// [27][16 out][16 in], offset index 9 dz_index + in-plane offset (dy, dx);
+// K = 16 input channels of the plain layout [V][16].
+template <int kBuf>
+__global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1)
+    k_conv_tc(const __nv_bfloat16* __restrict__ in, const uint4* __restrict__ Wp,
+              float* __restrict__ f_out, PropGeom g, int n_tiles, int* __restrict__ flag) {
+    constexpr int kRows = kTcRows16, kIP = kTcInPlane;
     extern __shared__ __align__(128) uint4 tc_smem[];
     uint4* boxp = tc_smem;                    // [buffer][channel half][kTcBox]
     uint4* wp = tc_smem + kBuf * 2 * kTcBox;  // [channel half][in-plane offset][kRows]
@@ -463,14 +419,13 @@ __global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1) k_conv_tc(const
             for (int z = -1; z <= kTcZ; ++z) {
                 const int pf = z + 1 < kTcZ - 1 ? z + 1 : kTcZ - 1;  // first plane fed
                 const int pl = z - 1 > 0 ? z - 1 : 0;                 // last plane fed
-                const int N = kCB == 16 ? 16 * (pf - pl + 1) : 16;
+                const int N = 16 * (pf - pl + 1);
                 const uint32_t idesc = umma_idesc_bf16(128, N);
-                const uint32_t d = accb + (uint32_t)(kCB * (kTcZ - 1 - pf));
-                const int row0 = kCB * (z - pf + 1);  // B row of the first plane's dz
+                const uint32_t d = accb + (uint32_t)(16 * (kTcZ - 1 - pf));
+                const int row0 = 16 * (z - pf + 1);  // B row of the first plane's dz
 #pragma unroll
                 for (int o9 = 0; o9 < kIP; ++o9) {
-                    const int dy = kIP == 9 ? o9 / 3 - 1 : o9 - 1;
-                    const int dx = kIP == 9 ? o9 % 3 - 1 : 0;
+                    const int dy = o9 / 3 - 1, dx = o9 % 3 - 1;
                     const int v0 = ((z + 1) * kTcBY + (1 + dy)) * kTcBX + (1 + dx);
                     const uint64_t ad = a0 + (uint64_t)v0;
                     const uint64_t bd = b0 + (uint64_t)(o9 * kRows + row0);
@@ -493,8 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1) k_conv_tc(const
             const uint32_t accp = tmem + (uint32_t)(kTcCols * (b ^ 1));
 #pragma unroll 1
             for (int p = 2 * (w >> 2); p < 2 * (w >> 2) + 2; ++p)
-                tc_epilogue<kMode, kCB>(accp + (uint32_t)(kCB * (kTcZ - 1 - p)), g, px0, py0,
-                                        pz0 + p, bias, z_out, act_out, f_out);
+                tc_epilogue(accp + (uint32_t)(16 * (kTcZ - 1 - p)), g, px0, py0, pz0 + p, f_out);
         }
         px0 = x0;
         py0 = y0;
@@ -511,8 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, kBuf == 1 ? 4 : 1) k_conv_tc(const
             const uint32_t accp = tmem + (uint32_t)(kTcCols * pb);
 #pragma unroll 1
             for (int p = 2 * (w >> 2); p < 2 * (w >> 2) + 2; ++p)
-                tc_epilogue<kMode, kCB>(accp + (uint32_t)(kCB * (kTcZ - 1 - p)), g, px0, py0,
-                                        pz0 + p, bias, z_out, act_out, f_out);
+                tc_epilogue(accp + (uint32_t)(16 * (kTcZ - 1 - p)), g, px0, py0, pz0 + p, f_out);
         }
     }
     if (failed) {
@@ -535,52 +488,710 @@ int conv_tc_tiles(const PropGeom& g) {
     return ((g.mx + kTcX - 1) / kTcX) * ((g.my + kTcY - 1) / kTcY) * ((g.mz + kTcZ - 1) / kTcZ);
 }
 
-template <int kMode, int kCB, int kIP>
-void set_tc_attr() {
-    cudaFuncSetAttribute(k_conv_tc<kMode, kCB, kIP, 1>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(1));
-}
-
 // One tile per CTA, single-buffered (48 KB of shared memory and 64
 // tensor-memory columns per CTA, four CTAs per SM overlap one another's box
-// loads, MMAs and epilogues); attributes set once per device.
+// loads, MMAs and epilogues); the attribute is set once per device.
 void conv_tc_setup() {
     static std::once_flag once[64];
     once_per_device(once, [] {
-        set_tc_attr<kHidden, 16, 3>();
-        set_tc_attr<kHidden, 16, 9>();
-        set_tc_attr<kLast, 2, 9>();
-        set_tc_attr<kData, 16, 9>();
+        cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem_bytes(1));
         cudaGetLastError();
     });
 }
 
-// Convolution with weight image k of the packed images tcw (tc_pack_weights).
-template <int kMode, int kCB, int kIP = 9>
-void launch_conv_tc(const __nv_bfloat16* in, const uint4* tcw, int k, const float* bias,
-                    float* z_out, __nv_bfloat16* act_out, float* f_out, const PropGeom& g,
-                    int* flag, cudaStream_t s) {
+// Data-gradient convolution of in [V][16] with weight image k of tcw into
+// f_out [V][16] FP32.
+void launch_conv_tc(const __nv_bfloat16* in, const uint4* tcw, int k, float* f_out,
+                    const PropGeom& g, int* flag, cudaStream_t s) {
     conv_tc_setup();
     const int n = conv_tc_tiles(g);
-    k_conv_tc<kMode, kCB, kIP, 1><<<n, kTcThreads, tc_smem_bytes(1), s>>>(
-        in, tcw + tc_image_offset(k), bias, z_out, act_out, f_out, g, n, flag);
+    k_conv_tc<1><<<n, kTcThreads, tc_smem_bytes(1), s>>>(in, tcw + tc_image_offset(k), f_out, g,
+                                                         n, flag);
 }
 
 // Weight image k in the B layout of k_conv_tc, kTcWCopies times: from the
-// padded BF16 weights W [3 kIP][16 out][16 in] (offset dz_index * kIP +
-// in-plane offset), row n = dz_index * kCB + out channel, zeros past 3 kCB.
+// padded BF16 weights W [27][16 out][16 in] (offset 9 dz_index + in-plane
+// offset), row n = dz_index 16 + out channel.
 __global__ void k_pack_tc_image(const __nv_bfloat16* __restrict__ W, int k,
                                 uint4* __restrict__ tcw) {
-    const int cb = tc_image_cb(k), ip = tc_image_ip(k), rows = cb == 16 ? kTcRows16 : kTcRows2;
-    const int per = tc_image_words(k);
+    const int per = kTcImageWords, rows = kTcRows16, ip = kTcInPlane;
     const uint4* W4 = reinterpret_cast<const uint4*>(W);
     uint4* out = tcw + tc_image_offset(k);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
         const int half = e / (ip * rows), rest = e % (ip * rows);
         const int o9 = rest / rows, n = rest % rows;
-        const uint4 v = n < 3 * cb ? W4[(((n / cb) * ip + o9) * kPC + n % cb) * 2 + half]
-                                   : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 v = W4[(((n / 16) * ip + o9) * kPC + n % 16) * 2 + half];
         for (int c = 0; c < kTcWCopies; ++c) out[c * per + e] = v;
+    }
+}
+
+// ------------------------------------------------------------------ z-sweep convolution
+//
+// The forward convolutions: persistent and warp-specialised.  The mesh is cut
+// into columns of 14 x 8 output voxels (x, y) through the whole z extent; the
+// output planes of all columns, in column-major order (column, z), are split
+// evenly over the CTAs (one per SM), and a CTA sweeps its share plane by plane.
+//
+// Activations live in a periodically padded layout [2][Mz + 2][PY][PX][8] BF16
+// (channel halves planar; one halo voxel on each side in x, y and z holding
+// the opposite face; PX >= Mx + 2, PY >= My + 2), so the 16 x 10 voxel boxes
+// of two consecutive input planes -- the column's 14 x 8 voxels with their x
+// and y neighbours -- are one TMA box of twenty 256-byte rows per channel half
+// (x and channel form the innermost dimension of the tensor map).  A stage
+// holds two input planes.  In shared memory a plane's box is the canonical
+// K-major layout without swizzle (8 channels = 16 bytes per voxel, core
+// matrices of 8 x-consecutive voxels, the channel halves 5120 bytes apart),
+// and its 128 voxels from box row dy + 1 on are the A operand
+// (M = 128: 8 rows of 16) of the in-plane offset dy, a descriptor into the
+// same box for every dy.
+//
+// For each dy, N stacks the weights of the three dz and, in the 16 -> 16
+// layer, of the three dx as well.  An output voxel n sums W[d] in(n + d):
+// input plane zi feeds output planes zi + 1, zi, zi - 1 (dz = -1, 0, +1), and
+// the dx block of the product at box voxel u belongs to the output voxel
+// u - dx, which the epilogue gathers from the neighbouring tensor-memory lanes
+// with warp shuffles (a 16-voxel box row keeps x - 1 and x + 1 of each of its
+// 14 interior voxels in the same warp).  So an input plane costs three MMAs
+// (one per dy) of N up to 3 x 48 = 144 that read the box three times, not
+// nine.  The first layer's x-im2col input (K index (dx + 1) 4 + ci) needs no
+// dx block (N up to 48); the two-channel last layer keeps 16 columns per
+// plane, 6 of them used (zero weight rows behind).
+//
+// Output planes accumulate in a ring of kSwRing tensor-memory slots in
+// reverse column order, so the planes an input plane feeds are adjacent
+// columns except where the ring wraps (the MMA is split there).  A slot
+// starts at the bias (dx = 0 block) or zero and every MMA accumulates; the
+// epilogue reads a finished plane, resets its slot and hands it back before
+// its own arithmetic and stores.
+//
+// Warp 0: TMA producer (a ring of kSwStages plane boxes); warp 1: owner of
+// the tensor memory and MMA issuer; warps 2..5: epilogue, one tensor-memory
+// lane quarter each.  Every wait is bounded; one that gives up raises
+// kFlagTimeout and a shared abort word that ends every role's loop, after
+// which the CTA waits (bounded) for its copies and MMAs in flight and
+// releases its tensor memory.
+constexpr int kSwOX = 14;                                // output voxels of a column along x
+constexpr int kSwBX = 16, kSwY = 8, kSwBY = 10;          // box: x with halo, output rows, rows
+constexpr uint32_t kSwPlaneBytes = 16u * kSwBX * kSwBY;  // one channel half of a plane box
+constexpr uint32_t kSwHalfBytes = 2u * kSwPlaneBytes;    // one channel half of a stage
+constexpr uint32_t kSwStageBytes = 2u * kSwHalfBytes;    // two input planes
+constexpr int kSwStages = 9;
+constexpr int kSwRingMax = 10;
+constexpr int kSwEpiWarps = 4;
+constexpr int kSwThreads = 32 * (2 + kSwEpiWarps);
+constexpr int kSwPerSM = 2;                              // CTAs (sweeps) per SM
+constexpr size_t kSwSmemFloor = 80 * 1024;               // at most two CTAs per SM
+
+// layer kL: 0 first (x-im2col input), 1 second (16 -> 16), 2 last (16 -> 2)
+__host__ __device__ constexpr int sw_cols(int L) { return L == 1 ? 48 : 16; }  // per plane
+__host__ __device__ constexpr int sw_rows(int L) { return 3 * sw_cols(L); }    // B rows per dy
+__host__ __device__ constexpr int sw_image_words(int L) { return 2 * 3 * sw_rows(L); }
+__host__ __device__ constexpr int sw_image_offset(int L) {
+    return L == 0 ? 0 : sw_image_offset(L - 1) + kTcWCopies * sw_image_words(L - 1);
+}
+// accumulator slots: 5 x 48 or 10 x 16 columns, 256 allocated (two CTAs per SM)
+__host__ __device__ constexpr int sw_ring(int L) { return L == 1 ? 5 : 10; }
+__host__ __device__ constexpr uint32_t sw_tmem_cols(int L) { return 256u; }
+constexpr int kSwBars = 2 * kSwStages + kSwRingMax + 2;  // full, empty, acc full, weights, done
+constexpr size_t sw_smem_bytes(int L) {
+    return (size_t)1024 + (size_t)kSwStages * kSwStageBytes + 16 * (size_t)sw_image_words(L) +
+                   8 * (size_t)kSwBars + 64 <
+                   kSwSmemFloor
+               ? kSwSmemFloor
+               : (size_t)1024 + (size_t)kSwStages * kSwStageBytes +
+                     16 * (size_t)sw_image_words(L) + 8 * (size_t)kSwBars + 64;
+}
+
+struct SweepArgs {
+    const uint4* w;            // packed weight image of the layer (kTcWCopies replicas)
+    const float* bias;         // [16]
+    float* z_out;              // hidden: pre-activations [V][16] FP32 (optional)
+    __nv_bfloat16* act_out;    // hidden: SiLU output, padded layout [2][Mz + 2][PY][PX][8]
+    float* f_out;              // last: [V][16] FP32, channels 0 and 1 (optional)
+    float* y_out;              // last: planar [2][V], times inv_scale (optional)
+    float inv_scale;
+    int* flag;
+    int mx, my, mz, px, py;    // mesh and padded pitches
+    int ncx, total;            // columns along x; output planes of all columns
+};
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool sw_wait(uint32_t bar, uint32_t parity, volatile int* abort_w,
+                                        int* flag) {
+    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_w) return false;
+    }
+    *abort_w = 1;
+    atomicOr(flag, kFlagTimeout);
+    return false;
+}
+
+// Each epilogue warp counts the accumulator slots it has released (a release
+// add after its tensor-memory reads and resets); a slot is free once every
+// warp's count has passed it (acquire loads before the MMAs that reuse it).
+// One count per warp: the warps drift apart by a few planes, and a sum could
+// pass a plane that a slow warp has not read yet.
+__device__ __forceinline__ void count_release(uint32_t addr) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ uint32_t count_acquire(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool mbar_test_now(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void count_publish(uint32_t addr, uint32_t v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target,
+                                              volatile int* abort_w, int* flag) {
+    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        if (count_acquire(addr) >= target) return true;
+        if (*abort_w) return false;
+    }
+    *abort_w = 1;
+    atomicOr(flag, kFlagTimeout);
+    return false;
+}
+
+__device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target,
+                                                 volatile int* abort_w, int* flag) {
+    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        uint32_t m = count_acquire(addr);
+#pragma unroll
+        for (int w = 1; w < kSwEpiWarps; ++w) {
+            const uint32_t c = count_acquire(addr + 4u * w);
+            m = c < m ? c : m;
+        }
+        if (m >= target) return true;
+        if (*abort_w) return false;
+    }
+    *abort_w = 1;
+    atomicOr(flag, kFlagTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, 1, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// Initial value of a slot for this warp's lanes: the bias in the dx = 0 block
+// (channels 0..15 of the first layer, columns 16..31 of the second, columns
+// 2 and 3 of the last), zero elsewhere.
+template <int kL>
+__device__ __forceinline__ void sw_reset_slot(uint32_t taddr, const float (&binit)[16]) {
+    float zero[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) zero[c] = 0.f;
+    if (kL == 1) {
+        tmem_st16(taddr, zero);
+        tmem_st16(taddr + 16, binit);
+        tmem_st16(taddr + 32, zero);
+    } else {
+        tmem_st16(taddr, binit);
+    }
+}
+
+// A voxel's two channel halves to the padded layout, with its periodic
+// copies in the halo when it lies on a face (up to eight at a corner).
+__device__ __forceinline__ void sw_store_act(__nv_bfloat16* __restrict__ act, const SweepArgs& a,
+                                             int X, int Y, int Z, uint4 lo, uint4 hi) {
+    const int xs[2] = {X + 1, X == 0 ? a.mx + 1 : (X == a.mx - 1 ? 0 : -1)};
+    const int ys[2] = {Y + 1, Y == 0 ? a.my + 1 : (Y == a.my - 1 ? 0 : -1)};
+    const int zs[2] = {Z + 1, Z == 0 ? a.mz + 1 : (Z == a.mz - 1 ? 0 : -1)};
+    const size_t hs = (size_t)(a.mz + 2) * a.py * a.px;  // voxels per half
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (zs[k] < 0) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (ys[j] < 0) continue;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (xs[i] < 0) continue;
+                uint4* o = reinterpret_cast<uint4*>(act) +
+                           ((size_t)zs[k] * a.py + ys[j]) * a.px + xs[i];
+                o[0] = lo;
+                o[hs] = hi;
+            }
+        }
+    }
+}
+
+// The output planes [q0, q1) of this CTA in the order q = column Mz + z.
+__device__ __forceinline__ void sw_share(const SweepArgs& a, long long& q0, long long& q1) {
+    q0 = (long long)a.total * blockIdx.x / gridDim.x;
+    q1 = (long long)a.total * (blockIdx.x + 1) / gridDim.x;
+}
+
+// The run of output planes [zs, ze) of one column starting at q.
+__device__ __forceinline__ void sw_chunk(const SweepArgs& a, long long q, long long q1, int& x0,
+                                         int& y0, int& zs, int& ze) {
+    const int col = (int)(q / a.mz);
+    zs = (int)(q % a.mz);
+    const long long left = q1 - q;
+    ze = zs + (int)(left < (long long)(a.mz - zs) ? left : (long long)(a.mz - zs));
+    x0 = (col % a.ncx) * kSwOX;
+    y0 = (col / a.ncx) * kSwY;
+}
+
+// The stages of a CTA in order: each run of input planes zs - 1 .. ze of a
+// column, two planes per stage (an odd run ends with a padding plane that no
+// MMA reads).  zi: the stage's first input plane.
+struct SwStages {
+    long long q, q1;
+    int x0, y0, zs, ze, zi;
+    __device__ __forceinline__ void begin(const SweepArgs& a, long long q0, long long q1_) {
+        q = q0;
+        q1 = q1_;
+        if (q < q1) {
+            sw_chunk(a, q, q1, x0, y0, zs, ze);
+            zi = zs - 1;
+        }
+    }
+    __device__ __forceinline__ void next(const SweepArgs& a) {
+        zi += 2;
+        if (zi > ze) {
+            q += ze - zs;
+            if (q < q1) {
+                sw_chunk(a, q, q1, x0, y0, zs, ze);
+                zi = zs - 1;
+            }
+        }
+    }
+};
+
+template <int kL>
+__global__ void __launch_bounds__(kSwThreads, kSwPerSM)
+    k_conv_sweep(const __grid_constant__ CUtensorMap tmap, const SweepArgs a) {
+    constexpr int C = sw_cols(kL), RW = sw_rows(kL), kSwRing = sw_ring(kL);
+    constexpr uint32_t kWBytes = 16u * sw_image_words(kL);
+    extern __shared__ __align__(1024) uint8_t sw_raw[];
+    const uint32_t raw_s = saddr(sw_raw);
+    const uint32_t stage_s = (raw_s + 1023u) & ~1023u;  // TMA boxes, 1024-byte aligned
+    uint8_t* base = sw_raw + (stage_s - raw_s);
+    const uint32_t w_s = stage_s + kSwStages * kSwStageBytes;
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(base + kSwStages * kSwStageBytes + kWBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kSwBars);
+    volatile int* abort_w = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint32_t* released = tmem_slot + 2;  // [kSwEpiWarps] slot releases per epilogue warp
+    uint32_t* loaded = released + kSwEpiWarps;  // input planes landed in shared memory
+    const uint32_t rel_s = saddr(released), loaded_s = saddr(loaded);
+    const uint32_t bar0 = saddr(bars);
+    // barrier k at bar0 + 8 k: full [0, S), empty [S, 2S), acc full [2S, 2S + R),
+    // weights, done
+    const uint32_t full_b = bar0, empty_b = bar0 + 8 * kSwStages;
+    const uint32_t accf_b = bar0 + 16 * kSwStages;
+    const uint32_t w_b = accf_b + 8 * kSwRingMax, done_b = w_b + 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int k = 0; k < kSwBars; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k) : "memory");
+        *abort_w = 0;
+        for (int w = 0; w < kSwEpiWarps; ++w) released[w] = 0;
+        *loaded = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tmem_slot)),
+                     "r"(sw_tmem_cols(kL))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    float binit[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) binit[c] = 0.f;
+    if (kL == 2) {
+        binit[2] = a.bias[0];
+        binit[3] = a.bias[1];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) binit[c] = a.bias[c];
+    }
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    if (warp >= 2) {
+#pragma unroll 1
+        for (int s = 0; s < kSwRing; ++s)
+            sw_reset_slot<kL>(tmem + (uint32_t)((kSwRing - 1 - s) * C) + lane_off, binit);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    long long q0, q1;
+    sw_share(a, q0, q1);
+    int n_stages = 0;  // every run of input planes zs - 1 .. ze, padded to an even count
+    for (long long q = q0; q < q1;) {
+        int x0, y0, zs, ze;
+        sw_chunk(a, q, q1, x0, y0, zs, ze);
+        n_stages += (ze - zs + 3) / 2;
+        q += ze - zs;
+    }
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------------- producer
+        const uint4* src = a.w + (size_t)(blockIdx.x % kTcWCopies) * sw_image_words(kL);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(w_b),
+                     "r"(kWBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(w_s),
+            "l"(src), "r"(kWBytes), "r"(w_b)
+            : "memory");
+        // Stages run up to kSwStages ahead (a stage is reused once the MMAs that
+        // read it are done); between issues the producer watches the copies
+        // land, in order, and publishes their count, so that the MMA thread
+        // polls one word instead of a barrier per stage.
+        SwStages in;
+        in.begin(a, q0, q1);
+        int si = 0, pub = 0;
+        unsigned idle = 0;
+        while (si < n_stages || pub < si) {
+            bool progress = false;
+            const int st = si % kSwStages;
+            if (si < n_stages && mbar_test_now(empty_b + 8 * st, ((si / kSwStages) & 1) ^ 1)) {
+                const uint32_t dst = stage_s + st * kSwStageBytes, fb = full_b + 8 * st;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                             "r"(kSwStageBytes)
+                             : "memory");
+                // planes zi, zi + 1 at padded z = zi + 1 (0 .. Mz + 1): one box per
+                // channel half; x0 8 elements = 16 x0 bytes keeps the copy aligned
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::"
+                        "bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst + h * kSwHalfBytes),
+                        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(8 * in.x0), "r"(in.y0),
+                        "r"(in.zi + 1), "r"(h), "r"(fb)
+                        : "memory");
+                in.next(a);
+                ++si;
+                progress = true;
+            }
+            if (pub < si &&
+                mbar_test_now(full_b + 8 * (pub % kSwStages), (pub / kSwStages) & 1)) {
+                ++pub;
+                count_publish(loaded_s, (uint32_t)pub);
+                progress = true;
+            }
+            if (progress) {
+                idle = 0;
+            } else if (*abort_w) {
+                break;
+            } else if (++idle >= kTcWaitLimit) {
+                *abort_w = 1;
+                atomicOr(a.flag, kFlagTimeout);
+                break;
+            }
+        }
+        // every copy issued lands before the CTA ends (the last phase of each
+        // stage is the one to wait for)
+        const int used = si < kSwStages ? si : kSwStages;
+        for (int st = 0; st < used; ++st) {
+            const int j = si - 1 - ((si - 1 - st) % kSwStages);
+            for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(full_b + 8 * st, (j / kSwStages) & 1); ++k) {
+            }
+        }
+        for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(w_b, 0); ++k) {
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        // A single thread: descriptors are formed once and offset per MMA (the
+        // start-address field, in 16-byte units, is the low bits).
+        bool ok = sw_wait(w_b, 0, abort_w, a.flag);
+        const uint64_t adesc0 = umma_smem_desc(stage_s, kSwHalfBytes, 128u);
+        const uint64_t bdesc0 = umma_smem_desc(w_s, 16u * 3 * RW, 128u);
+        const uint32_t idesc0 = umma_idesc_bf16(128, 0);
+        SwStages in;
+        in.begin(a, q0, q1);
+        int kb = 0;       // ring index of the run's first plane
+        int s_first = 0;  // its slot
+        for (int si = 0; si < n_stages && ok; ++si) {
+            if (!sw_wait_count(loaded_s, (uint32_t)(si + 1), abort_w, a.flag)) {
+                ok = false;
+                break;
+            }
+            const int st = si % kSwStages;
+            const int zs = in.zs, ze = in.ze;
+            if (in.zi == zs - 1) s_first = kb % kSwRing;
+#pragma unroll 1
+            for (int pl = 0; pl < 2; ++pl) {
+                const int zi = in.zi + pl;
+                if (zi > ze) break;  // the padding plane of an odd run
+                const int hi = zi + 1 < ze - 1 ? zi + 1 : ze - 1;
+                const int lo = zi - 1 > zs ? zi - 1 : zs;
+                const int khi = kb + hi - zs;
+                if (zi + 1 < ze && khi >= kSwRing) {
+                    // plane khi is first fed now: its slot was released with plane khi - R
+                    if (!sw_wait_released(rel_s, (uint32_t)(khi - kSwRing + 1), abort_w, a.flag)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                int slot = s_first + (hi - zs);
+                while (slot >= kSwRing) slot -= kSwRing;
+                const uint64_t a_pl =
+                    adesc0 + (uint64_t)((st * kSwStageBytes + pl * kSwPlaneBytes) >> 4);
+                int dzi = zi - hi + 1;
+                for (int left = hi - lo + 1; left > 0;) {
+                    const int n = left < slot + 1 ? left : slot + 1;  // adjacent columns
+                    const uint32_t d = tmem + (uint32_t)((kSwRing - 1 - slot) * C);
+                    const uint32_t idesc = idesc0 + ((uint32_t)(n * C) >> 3 << 17);
+                    const uint64_t b_run = bdesc0 + (uint64_t)(dzi * C);
+#pragma unroll
+                    for (int dyi = 0; dyi < 3; ++dyi)
+                        umma_bf16(d, a_pl + (uint64_t)(16 * dyi), b_run + (uint64_t)(dyi * RW),
+                                  idesc);
+                    left -= n;
+                    dzi += n;
+                    slot = kSwRing - 1;
+                }
+                if (zi - 1 >= zs) {  // plane zi - 1 has all its inputs
+                    int s1 = s_first + (zi - 1 - zs);
+                    while (s1 >= kSwRing) s1 -= kSwRing;
+                    umma_commit(accf_b + 8 * s1);
+                }
+            }
+            if (!ok) break;
+            umma_commit(empty_b + 8 * st);  // the stage is read once these MMAs are done
+            if (in.zi + 2 > ze) kb += ze - zs;  // the run's last stage
+            in.next(a);
+        }
+        umma_commit(done_b);
+        for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(done_b, 0); ++k) {
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------------- epilogue
+        const int r = 32 * (warp & 3) + lane, bx = r & 15, by = r >> 4;
+        int k = 0;
+        bool ok = true;
+        for (long long q = q0; q < q1 && ok;) {
+            int x0, y0, zs, ze;
+            sw_chunk(a, q, q1, x0, y0, zs, ze);
+            const int X = x0 - 1 + bx, Y = y0 + by;
+            const bool valid = bx >= 1 && bx <= kSwOX && X < a.mx && Y < a.my;
+            for (int zo = zs; zo < ze; ++zo, ++k) {
+                const int slot = k % kSwRing;
+                int got = 1;
+                if (lane == 0) got = sw_wait(accf_b + 8 * slot, (k / kSwRing) & 1, abort_w, a.flag);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t taddr = tmem + (uint32_t)((kSwRing - 1 - slot) * C) + lane_off;
+                float v[C];
+#pragma unroll
+                for (int c = 0; c < C; c += 16) tmem_ld16(taddr + c, v + c);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                sw_reset_slot<kL>(taddr, binit);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) count_release(rel_s + 4u * (warp - 2));
+                const size_t gv = ((size_t)zo * a.my + Y) * a.mx + X;
+                if (kL == 2) {
+                    float o[2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+                        o[c] = __shfl_up_sync(0xffffffffu, v[c], 1) + v[2 + c] +
+                               __shfl_down_sync(0xffffffffu, v[4 + c], 1);
+                    if (valid) {
+                        if (a.f_out)
+                            *reinterpret_cast<float2*>(a.f_out + gv * kPC) = make_float2(o[0], o[1]);
+                        if (a.y_out) {
+                            const size_t V = (size_t)a.mx * a.my * a.mz;
+                            a.y_out[gv] = o[0] * a.inv_scale;
+                            a.y_out[V + gv] = o[1] * a.inv_scale;
+                        }
+                    }
+                } else {
+                    float o[16];
+                    if (kL == 1) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            o[c] = __shfl_up_sync(0xffffffffu, v[c], 1) + v[16 + c] +
+                                   __shfl_down_sync(0xffffffffu, v[32 + c], 1);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) o[c] = v[c];
+                    }
+                    if (valid) {
+                        if (a.z_out) {
+                            float4* zo4 = reinterpret_cast<float4*>(a.z_out + gv * kPC);
+#pragma unroll
+                            for (int c4 = 0; c4 < 4; ++c4)
+                                zo4[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2],
+                                                      o[4 * c4 + 3]);
+                        }
+                        __nv_bfloat162 h[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float u = o[2 * c], w = o[2 * c + 1];
+                            h[c] = __floats2bfloat162_rn(__fdividef(u, 1.0f + __expf(-u)),
+                                                         __fdividef(w, 1.0f + __expf(-w)));
+                        }
+                        sw_store_act(a.act_out, a, X, Y, zo, reinterpret_cast<uint4*>(h)[0],
+                                     reinterpret_cast<uint4*>(h)[1]);
+                    }
+                }
+            }
+            q += ze - zs;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(sw_tmem_cols(kL))
+                     : "memory");
+    }
+}
+
+template <int kL>
+void sweep_attr() {
+    cudaFuncSetAttribute(k_conv_sweep<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sw_smem_bytes(kL));
+}
+
+void conv_sweep_setup() {
+    static std::once_flag once[64];
+    once_per_device(once, [] {
+        sweep_attr<0>();
+        sweep_attr<1>();
+        sweep_attr<2>();
+        cudaGetLastError();
+    });
+}
+
+// The padded-activation geometry of a mesh: pitches PX, PY (at least one box).
+void sweep_pitches(const PropGeom& g, int& px, int& py) {
+    px = g.mx + 2 > kSwBX ? g.mx + 2 : kSwBX;
+    py = g.my + 2 > kSwBY ? g.my + 2 : kSwBY;
+}
+
+// Tensor map of a padded activation buffer [2 halves][Mz + 2][PY][PX][8] with
+// x and channel folded into one innermost dimension of 8 PX elements, so that
+// a box row (16 voxels x 8 channels, 256 bytes) is one contiguous TMA row; the
+// box is one channel half of the 16 x 10 voxel boxes of two planes.
+bool make_act_tensor_map(CUtensorMap* map, __nv_bfloat16* act, const PropGeom& g) {
+    int px, py;
+    sweep_pitches(g, px, py);
+    const cuuint64_t pz = (cuuint64_t)g.mz + 2;
+    const cuuint64_t dims[4] = {8ull * px, (cuuint64_t)py, pz, 2};
+    const cuuint64_t strides[3] = {16ull * px, 16ull * px * py, 16ull * px * py * pz};
+    const cuuint32_t box[4] = {8 * kSwBX, (cuuint32_t)kSwBY, 2, 1};
+    return encode_tiled_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, act, dims, strides, box);
+}
+
+template <int kL>
+void launch_conv_sweep(const CUtensorMap& tmap, const SweepArgs& a, int ctas, cudaStream_t s) {
+    conv_sweep_setup();
+    const int grid = a.total < ctas ? a.total : ctas;
+    if (grid > 0) k_conv_sweep<kL><<<grid, kSwThreads, sw_smem_bytes(kL), s>>>(tmap, a);
+}
+
+// Weight image of layer kL in the B layout of k_conv_sweep, kTcWCopies times:
+// [half][dy index][row][8 channels], row = dz index C + column, column = co
+// (first layer), dx index 16 + co (second), dx index 2 + co < 6 (last); from
+// the forward weights wf [o][co][ci] (o = 9 dz index + 3 dy index + dx index)
+// or, for the first layer, wx [3 dz index + dy index][co][K].
+__global__ void k_pack_sweep_images(const __nv_bfloat16* __restrict__ wf,
+                                    const __nv_bfloat16* __restrict__ wx, uint4* __restrict__ out) {
+    const int L = blockIdx.x;
+    const int C = sw_cols(L), RW = sw_rows(L), per = sw_image_words(L);
+    const uint4* wf4 = reinterpret_cast<const uint4*>(wf + (size_t)L * kOffsets * kPC * kPC);
+    const uint4* wx4 = reinterpret_cast<const uint4*>(wx);
+    uint4* o = out + sw_image_offset(L);
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        const int half = e / (3 * RW), dyi = (e / RW) % 3, row = e % RW;
+        const int dzi = row / C, c = row % C;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (L == 0) {
+            v = wx4[((dzi * 3 + dyi) * kPC + c) * 2 + half];
+        } else if (L == 1) {
+            const int dxi = c / 16, co = c % 16;
+            v = wf4[((dzi * 9 + dyi * 3 + dxi) * kPC + co) * 2 + half];
+        } else if (c < 6) {
+            const int dxi = c / 2, co = c % 2;
+            v = wf4[((dzi * 9 + dyi * 3 + dxi) * kPC + co) * 2 + half];
+        }
+        for (int k = 0; k < kTcWCopies; ++k) o[k * per + e] = v;
     }
 }
 
@@ -591,7 +1202,8 @@ __global__ void k_pack_tc_image(const __nv_bfloat16* __restrict__ W, int k,
 // fixed order, so the gradient is deterministic.
 __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restrict__ in,
                                                     const __nv_bfloat16* __restrict__ gz,
-                                                    float* __restrict__ part, PropGeom g) {
+                                                    float* __restrict__ part, PropGeom g,
+                                                    ActLayout L) {
     __shared__ uint4 box[kBoxVox * 2];
     __shared__ uint4 gt[kTileVox * 2];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -616,7 +1228,7 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
         int x0, y0, z0;
         tile_origin(g, t, x0, y0, z0);
         __syncthreads();
-        load_box(in, g, x0, y0, z0, box);
+        load_box(in, g, L, x0, y0, z0, box);
         for (int e = tid; e < kTileVox * 2; e += blockDim.x) {
             const int m = e >> 1, half = e & 1;
             const int X = x0 + m % kTX, Y = y0 + (m / kTX) % kTY, Z = z0 + m / (kTX * kTY);
@@ -681,35 +1293,39 @@ __device__ __forceinline__ void input_features(const float* __restrict__ x, int 
     f[3] = b1;
 }
 
-__global__ void k_pack_input(const float* __restrict__ x, int V, int mx, float scale,
+// One thread per voxel of the padded array [Mz + 2][My + 2][Mx + 2] (halo
+// included, each halo voxel a copy of the opposite face): out_x in the padded
+// layout of the forward convolutions [2][Mz + 2][py][px][8]; out (optional, for the
+// weight gradient): the plain four channels [V][16] at the interior voxels.
+__global__ void k_pack_input(const float* __restrict__ x, PropGeom g, int px, int py, float scale,
                              __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_x) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    const int xi = v % mx;
-    const int vm = v - xi + (xi == 0 ? mx - 1 : xi - 1), vp = v - xi + (xi == mx - 1 ? 0 : xi + 1);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int wx = g.mx + 2, wy = g.my + 2, wz = g.mz + 2;
+    if (i >= (long long)wx * wy * wz) return;
+    const int hx = (int)(i % wx), hy = (int)((i / wx) % wy), hz = (int)(i / ((long long)wx * wy));
+    const int xi = hx == 0 ? g.mx - 1 : (hx == g.mx + 1 ? 0 : hx - 1);
+    const int yi = hy == 0 ? g.my - 1 : (hy == g.my + 1 ? 0 : hy - 1);
+    const int z = hz == 0 ? g.mz - 1 : (hz == g.mz + 1 ? 0 : hz - 1);
+    const int row = (z * g.my + yi) * g.mx;
+    const int xm = xi == 0 ? g.mx - 1 : xi - 1, xp = xi == g.mx - 1 ? 0 : xi + 1;
     float f[3][4];
-    input_features(x, V, vm, scale, f[0]);
-    input_features(x, V, v, scale, f[1]);
-    input_features(x, V, vp, scale, f[2]);
+    input_features(x, g.V, row + xm, scale, f[0]);
+    input_features(x, g.V, row + xi, scale, f[1]);
+    input_features(x, g.V, row + xp, scale, f[2]);
     __nv_bfloat16 vals[kPC], cols[kPC];
 #pragma unroll
     for (int c = 0; c < kPC; ++c) {
         vals[c] = __float2bfloat16_rn(c < 4 ? f[1][c] : 0.f);
         cols[c] = __float2bfloat16_rn(c < 12 ? f[c >> 2][c & 3] : 0.f);
     }
-    reinterpret_cast<uint4*>(out + (size_t)v * kPC)[0] = reinterpret_cast<uint4*>(vals)[0];
-    reinterpret_cast<uint4*>(out + (size_t)v * kPC)[1] = reinterpret_cast<uint4*>(vals)[1];
-    reinterpret_cast<uint4*>(out_x + (size_t)v * kPC)[0] = reinterpret_cast<uint4*>(cols)[0];
-    reinterpret_cast<uint4*>(out_x + (size_t)v * kPC)[1] = reinterpret_cast<uint4*>(cols)[1];
-}
-
-// The predicted change: the network's two output channels divided by scale.
-__global__ void k_unpack_output(const float* __restrict__ y, int V, float scale,
-                                float* __restrict__ out) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    out[v] = y[(size_t)v * kPC] / scale;
-    out[(size_t)V + v] = y[(size_t)v * kPC + 1] / scale;
+    uint4* ox = reinterpret_cast<uint4*>(out_x) + ((size_t)hz * py + hy) * px + hx;
+    ox[0] = reinterpret_cast<uint4*>(cols)[0];
+    ox[(size_t)wz * py * px] = reinterpret_cast<uint4*>(cols)[1];
+    if (out && hx >= 1 && hx <= g.mx && hy >= 1 && hy <= g.my && hz >= 1 && hz <= g.mz) {
+        uint4* o = reinterpret_cast<uint4*>(out + (size_t)(row + xi) * kPC);
+        o[0] = reinterpret_cast<uint4*>(vals)[0];
+        o[1] = reinterpret_cast<uint4*>(vals)[1];
+    }
 }
 
 // One autoregressive step on the planar input x [4][V] = (phi(t - 1), phi(t))
@@ -1023,10 +1639,17 @@ struct hpf_prop {
     float* wpart = nullptr;       // weight-gradient partials [grid_wgrad][27][16][16]
     float* bpart = nullptr;       // bias-gradient partials [152][16]
     double* lpart = nullptr;      // loss partials [ceil(V / 256)]
-    __nv_bfloat16* act[4] = {};   // input, h1, h2, and a gradient buffer [V][16]
-    __nv_bfloat16* act_x = nullptr;  // the input as x-im2col [V][16] (first layer)
+    // act[0]: the plain input [V][16] (training only); act[1], act[2]: the
+    // hidden activations in the padded layout [2][Mz + 2][py][px][8]; act[3]:
+    // a gradient buffer [V][16]
+    __nv_bfloat16* act[4] = {};
+    __nv_bfloat16* act_x = nullptr;  // the input as x-im2col, padded layout
     __nv_bfloat16* wx = nullptr;     // first-layer weights for it [9][16][16]
-    uint4* tcw = nullptr;            // packed weight images of the tensor-core convolutions
+    uint4* tcw = nullptr;            // packed weight images of the data-gradient convolutions
+    uint4* sww = nullptr;            // packed weight images of the forward convolutions
+    CUtensorMap tmap[3];             // act_x, act[1], act[2]
+    int px = 0, py = 0;              // padded pitches
+    int ctas = 1;                    // CTAs of the persistent convolutions (kSwPerSM per SM)
     float* z[2] = {};             // pre-activations of layers 1, 2 [V][16]
     float* fbuf = nullptr;        // FP32 [V][16]: output / data gradient
     float* xin = nullptr;         // staging of the planar input [4][V]
@@ -1060,26 +1683,48 @@ hpf_status prop_copy_out(hpf_prop* p, void* dst, const void* src, size_t bytes) 
 void pack_all_weights(hpf_prop* p, cudaStream_t s) {
     const size_t wl = (size_t)kOffsets * kPC * kPC;
     k_pack_weights<<<3, 256, 0, s>>>(p->params, p->wf, p->wb, p->bias, p->wx);
-    k_pack_tc_image<<<1, 256, 0, s>>>(p->wx, 0, p->tcw);
-    k_pack_tc_image<<<1, 256, 0, s>>>(p->wf + wl, 1, p->tcw);
-    k_pack_tc_image<<<1, 256, 0, s>>>(p->wf + 2 * wl, 2, p->tcw);
-    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + wl, 3, p->tcw);
-    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + 2 * wl, 4, p->tcw);
+    k_pack_sweep_images<<<3, 256, 0, s>>>(p->wf, p->wx, p->sww);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + wl, 0, p->tcw);
+    k_pack_tc_image<<<1, 256, 0, s>>>(p->wb + 2 * wl, 1, p->tcw);
 }
 
-// Forward pass of planar input x [4][V] (device); leaves the FP32 output in
-// fbuf.  With keep_z the pre-activations are stored for a backward pass.
-void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s, int* flag) {
-    const int V = p->g.V, tb = (V + 255) / 256;
-    k_pack_input<<<tb, 256, 0, s>>>(x, V, p->g.mx, p->scale, p->act[0], p->act_x);
-    // first layer: three in-plane offsets over the x-im2col input
-    launch_conv_tc<kHidden, 16, 3>(p->act_x, p->tcw, 0, p->bias, keep_z ? p->z[0] : nullptr,
-                                   p->act[1], nullptr, p->g, flag, s);
-    launch_conv_tc<kHidden, 16>(p->act[1], p->tcw, 1, p->bias + kPC,
-                                keep_z ? p->z[1] : nullptr, p->act[2], nullptr, p->g, flag, s);
-    // two output channels (channels 2..15 of fbuf are not written)
-    launch_conv_tc<kLast, 2>(p->act[2], p->tcw, 2, p->bias + 2 * kPC, nullptr, nullptr,
-                             p->fbuf, p->g, flag, s);
+SweepArgs sweep_args(const hpf_prop* p, int layer, int* flag) {
+    SweepArgs a{};
+    a.w = p->sww + sw_image_offset(layer);
+    a.bias = p->bias + layer * kPC;
+    a.inv_scale = 1.0f / p->scale;
+    a.flag = flag;
+    a.mx = p->g.mx;
+    a.my = p->g.my;
+    a.mz = p->g.mz;
+    a.px = p->px;
+    a.py = p->py;
+    a.ncx = (p->g.mx + kSwOX - 1) / kSwOX;
+    a.total = a.ncx * ((p->g.my + kSwY - 1) / kSwY) * p->g.mz;
+    return a;
+}
+
+// Forward pass of planar input x [4][V] (device).  keep_z: the pre-activations
+// and the plain input are stored and the FP32 output goes to fbuf [V][16] for
+// a backward pass; y_planar (optional): the predicted change [2][V] (the
+// output divided by scale).
+void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s, int* flag,
+                  float* y_planar = nullptr) {
+    const long long hv = (long long)(p->g.mx + 2) * (p->g.my + 2) * (p->g.mz + 2);
+    k_pack_input<<<(unsigned)((hv + 255) / 256), 256, 0, s>>>(
+        x, p->g, p->px, p->py, p->scale, keep_z ? p->act[0] : nullptr, p->act_x);
+    SweepArgs a = sweep_args(p, 0, flag);
+    a.z_out = keep_z ? p->z[0] : nullptr;
+    a.act_out = p->act[1];
+    launch_conv_sweep<0>(p->tmap[0], a, p->ctas, s);
+    a = sweep_args(p, 1, flag);
+    a.z_out = keep_z ? p->z[1] : nullptr;
+    a.act_out = p->act[2];
+    launch_conv_sweep<1>(p->tmap[1], a, p->ctas, s);
+    a = sweep_args(p, 2, flag);
+    a.f_out = keep_z ? p->fbuf : nullptr;
+    a.y_out = y_planar;
+    launch_conv_sweep<2>(p->tmap[2], a, p->ctas, s);
 }
 
 // Loss and packed gradients (p->grads, p->loss) after prop_forward(keep_z) of
@@ -1094,15 +1739,17 @@ void prop_backward(hpf_prop* p, const float* x, const float* phi_next) {
     k_loss<<<tb, 256, 0, s>>>(p->fbuf, x + 2 * (size_t)V, phi_next, V, p->scale, gbuf, p->lpart);
     k_sum_partials<double><<<1, 32, 0, s>>>(p->lpart, tb, 1, p->loss);
     for (int layer = 2; layer >= 0; --layer) {
-        k_conv_wgrad<<<p->grid_wgrad, 256, 0, s>>>(p->act[layer], gbuf, p->wpart, p->g);
+        const ActLayout lay =
+            layer == 0 ? ActLayout{p->g.mx, p->g.my, 0, kPC, 8}
+                       : ActLayout{p->px, p->py, 1, 8, 8ll * (p->g.mz + 2) * p->py * p->px};
+        k_conv_wgrad<<<p->grid_wgrad, 256, 0, s>>>(p->act[layer], gbuf, p->wpart, p->g, lay);
         k_sum_partials<float><<<(unsigned)((wl + 255) / 256), 256, 0, s>>>(
             p->wpart, p->grid_wgrad, (int)wl, p->dW + layer * wl);
         k_bias_grad<<<kBiasBlocks, 256, 0, s>>>(gbuf, V, p->bpart);
         k_sum_partials<float><<<1, 32, 0, s>>>(p->bpart, kBiasBlocks, kPC, p->db + layer * kPC);
         if (layer == 0) break;
         // the data gradient of the layer input, then through the SiLU below it
-        launch_conv_tc<kData, 16>(gbuf, p->tcw, layer + 2, nullptr, nullptr, nullptr, p->fbuf,
-                                  p->g, p->flag, s);
+        launch_conv_tc(gbuf, p->tcw, layer - 1, p->fbuf, p->g, p->flag, s);
         k_silu_backward<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(p->fbuf, p->z[layer - 1], nv,
                                                                       gbuf);
     }
@@ -1149,6 +1796,16 @@ hpf_status prop_read_loss(hpf_prop* p, double* loss) {
     return HPF_OK;
 }
 
+// A device (or managed) array of the current device.
+bool prop_on_device(const void* ptr) {
+    cudaPointerAttributes a;
+    int dev = -1;
+    const bool ok = cudaPointerGetAttributes(&a, ptr) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+                    (a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev));
+    cudaGetLastError();
+    return ok;
+}
+
 hpf_status prop_launched(hpf_prop* p) {
     (void)p;
     return cudaGetLastError() == cudaSuccess ? HPF_OK : HPF_ERR_CUDA;
@@ -1179,8 +1836,7 @@ bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g) {
 }
 
 void prop_predict(hpf_prop* p, const float* x, float* dphi, cudaStream_t s, int* flag) {
-    prop_forward(p, x, false, s, flag ? flag : p->flag);
-    k_unpack_output<<<(p->g.V + 255) / 256, 256, 0, s>>>(p->fbuf, p->g.V, p->scale, dphi);
+    prop_forward(p, x, false, s, flag ? flag : p->flag, dphi);
 }
 
 }  // namespace hpf
@@ -1214,6 +1870,9 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     cudaGetLastError();
     if (sms < 1) sms = 1;
     p->grid_wgrad = g.tiles < 2 * sms ? g.tiles : 2 * sms;
+    p->ctas = kSwPerSM * sms;
+    sweep_pitches(g, p->px, p->py);
+    const size_t Vp = (size_t)(g.mz + 2) * p->py * p->px;  // padded voxels
     const size_t wl = (size_t)kOffsets * kPC * kPC, Vs = (size_t)g.V;
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMalloc(&p->params, sizeof(float) * p->np);
@@ -1228,7 +1887,8 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     e = e ? e : cudaMalloc(&p->wpart, sizeof(float) * (size_t)p->grid_wgrad * wl);
     e = e ? e : cudaMalloc(&p->bpart, sizeof(float) * kBiasBlocks * kPC);
     e = e ? e : cudaMalloc(&p->lpart, sizeof(double) * ((Vs + 255) / 256));
-    for (int k = 0; k < 4; ++k) e = e ? e : cudaMalloc(&p->act[k], sizeof(__nv_bfloat16) * Vs * kPC);
+    for (int k = 0; k < 4; ++k)
+        e = e ? e : cudaMalloc(&p->act[k], sizeof(__nv_bfloat16) * (k == 1 || k == 2 ? Vp : Vs) * kPC);
     for (int k = 0; k < 2; ++k) e = e ? e : cudaMalloc(&p->z[k], sizeof(float) * Vs * kPC);
     e = e ? e : cudaMalloc(&p->fbuf, sizeof(float) * Vs * kPC);
     e = e ? e : cudaMalloc(&p->xin, sizeof(float) * Vs * 4);
@@ -1237,10 +1897,22 @@ hpf_status hpf_prop_init(const int32_t mesh[3], void* stream, hpf_prop** out) {
     e = e ? e : cudaMalloc(&p->loss, sizeof(double));
     e = e ? e : cudaMallocHost(&p->h_loss, sizeof(double));
     e = e ? e : cudaMalloc(&p->flag, sizeof(int));
-    e = e ? e : cudaMalloc(&p->act_x, sizeof(__nv_bfloat16) * Vs * kPC);
+    e = e ? e : cudaMalloc(&p->act_x, sizeof(__nv_bfloat16) * Vp * kPC);
+    e = e ? e : cudaMalloc(&p->sww, sizeof(uint4) * sw_image_offset(3));
     e = e ? e : cudaMalloc(&p->wx, sizeof(__nv_bfloat16) * 9 * kPC * kPC);
     e = e ? e : cudaMalloc(&p->tcw, sizeof(uint4) * tc_image_offset(kTcImages));
     e = e ? e : cudaMallocHost(&p->h_flag, sizeof(int));
+    if (e == cudaSuccess) {
+        // padded buffers: the pitch beyond the halo (meshes narrower than a box)
+        // is read by the box copies and stays zero
+        cudaMemsetAsync(p->act_x, 0, sizeof(__nv_bfloat16) * Vp * kPC, p->stream);
+        cudaMemsetAsync(p->act[1], 0, sizeof(__nv_bfloat16) * Vp * kPC, p->stream);
+        cudaMemsetAsync(p->act[2], 0, sizeof(__nv_bfloat16) * Vp * kPC, p->stream);
+        if (!make_act_tensor_map(&p->tmap[0], p->act_x, g) ||
+            !make_act_tensor_map(&p->tmap[1], p->act[1], g) ||
+            !make_act_tensor_map(&p->tmap[2], p->act[2], g))
+            e = cudaErrorNotSupported;
+    }
     if (e == cudaSuccess) {
         cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream);
         // zero weights until hpf_prop_set_weights: the network predicts no change
@@ -1288,6 +1960,7 @@ hpf_status hpf_prop_destroy(hpf_prop* p) {
     cudaFree(p->act_x);
     cudaFree(p->wx);
     cudaFree(p->tcw);
+    cudaFree(p->sww);
     cudaGetLastError();
     delete p;
     return HPF_OK;
@@ -1313,6 +1986,19 @@ hpf_status hpf_prop_get_weights(hpf_prop* p, float* params) {
     return prop_copy_out(p, params, p->params, sizeof(float) * p->np);
 }
 
+hpf_status hpf_prop_set_ctas(hpf_prop* p, int32_t ctas) {
+    if (!p || ctas < 0) return HPF_ERR_INVALID;
+    if (ctas == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        ctas = kSwPerSM * (sms > 0 ? sms : 1);
+    }
+    p->ctas = ctas;
+    return HPF_OK;
+}
+
 hpf_status hpf_prop_set_scale(hpf_prop* p, float scale) {
     if (!p || !(scale > 0.f) || !(scale < 3.0e38f)) return HPF_ERR_INVALID;
     p->scale = scale;
@@ -1326,19 +2012,18 @@ hpf_status hpf_prop_get_scale(const hpf_prop* p, float* scale) {
 }
 
 hpf_status hpf_prop_forward(hpf_prop* p, const float* x, float* dphi) {
-    if (!p || !dphi) return HPF_ERR_INVALID;
-    hpf_status s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4);
-    if (s != HPF_OK) return s;
-    prop_predict(p, p->xin, p->yout, p->stream, p->flag);
+    if (!p || !dphi || !x) return HPF_ERR_INVALID;
+    // device arrays of the current device are read and written in place (the
+    // input is consumed by the first kernel, so x may even alias dphi); host
+    // arrays go through the handle's staging buffers
+    const bool dev_in = prop_on_device(x), dev_out = prop_on_device(dphi);
+    hpf_status s = HPF_OK;
+    if (!dev_in && (s = prop_stage(p, p->xin, x, (size_t)p->g.V * 4)) != HPF_OK) return s;
+    prop_predict(p, dev_in ? x : p->xin, dev_out ? dphi : p->yout, p->stream, p->flag);
     if ((s = prop_launched(p)) != HPF_OK) return s;
+    if (dev_out) return HPF_OK;  // the wait status comes with the next synchronising call
     if ((s = prop_copy_out(p, dphi, p->yout, sizeof(float) * 2 * p->g.V)) != HPF_OK) return s;
-    // a host destination has synchronised the stream: the wait status is known;
-    // for a device destination it is reported by the next synchronising call
-    cudaPointerAttributes a;
-    const bool dev = cudaPointerGetAttributes(&a, dphi) == cudaSuccess &&
-                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
-    return dev ? HPF_OK : prop_flag_status(p);
+    return prop_flag_status(p);  // the host copy has synchronised: the status is known
 }
 
 hpf_status hpf_prop_rollout(hpf_prop* p, const float* x, int32_t steps, float* phi_out) {

@@ -147,6 +147,7 @@ def load():
         L.hpf_prop_get_weights.argtypes = [vp, vp]
         L.hpf_prop_set_scale.argtypes = [vp, ctypes.c_float]
         L.hpf_prop_get_scale.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.hpf_prop_set_ctas.argtypes = [vp, i32]
         L.hpf_prop_forward.argtypes = [vp, vp, vp]
         L.hpf_prop_rollout.argtypes = [vp, vp, i32, vp]
         L.hpf_prop_backward.argtypes = [vp, vp, vp, vp, dp]
@@ -160,7 +161,7 @@ def load():
         L.hpf_step_learned.argtypes = [vp, vp, i32, i32, ctypes.c_double,
                                        ctypes.POINTER(LearnedStats)]
         for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
-                     "hpf_prop_set_scale", "hpf_prop_get_scale",
+                     "hpf_prop_set_scale", "hpf_prop_get_scale", "hpf_prop_set_ctas",
                      "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_rollout",
                      "hpf_prop_backward",
                      "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
@@ -644,6 +645,10 @@ class Propagator:
     @scale.setter
     def scale(self, value: float):
         self._check(self.lib.hpf_prop_set_scale(self.h, float(value)))
+
+    def set_ctas(self, ctas: int):
+        """At most ctas CTAs for the persistent forward convolutions (0: one per SM)."""
+        self._check(self.lib.hpf_prop_set_ctas(self.h, int(ctas)))
 
     def set_weights(self, params):
         pp, _a = _ptr(params, np.float32, (self.n_params,), "params")

@@ -99,6 +99,53 @@ def test_forward_matches_oracle(hpf_gpu, mesh):
     assert np.max(np.abs(y - yo)) < 0.1 * np.max(np.abs(yo))
 
 
+@pytest.mark.parametrize("ctas", [1, 3, 7])
+def test_forward_does_not_depend_on_the_cta_split(hpf_gpu, ctas):
+    # few CTAs: long sweeps through many columns, the accumulator ring wrapping
+    # many times, runs of planes starting and ending inside columns
+    mesh = (26, 34, 18)
+    params = rand_params(6)
+    x = rand_phi(grid(mesh), 7).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        y0 = net.forward(x)
+        net.set_ctas(ctas)
+        y1 = net.forward(x)
+        net.set_ctas(0)
+        y2 = net.forward(x)
+    assert np.array_equal(y0, y1)
+    assert np.array_equal(y0, y2)
+    ye, _, _, _ = E.forward(params, x)
+    within_emulated(y1, ye, "output")
+
+
+def window(a, c, r=3):
+    """The periodic (2r + 1)^3 window of a planar mesh a [C][Mz][My][Mx]
+    centred on c = (z, y, x): the receptive field of the three layers there."""
+    idx = [np.arange(ci - r, ci + r + 1) % a.shape[1 + k] for k, ci in enumerate(c)]
+    return a[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+
+
+def test_forward_full_mesh_sampled(hpf_gpu):
+    # the 70^3 mesh of the 1M-bead melt, launched as every forward is (one CTA
+    # per SM): outputs on the faces, at column and row boundaries of the
+    # sweep (x = 13 / 14, y = 7 / 8) and at random voxels against the emulated
+    # oracle evaluated on each voxel's 7^3 receptive field
+    mesh = (70, 70, 70)
+    params = rand_params(3)
+    x = rand_phi(grid(mesh), 4).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        y = net.forward(x)
+    rng = np.random.default_rng(5)
+    special = [0, 1, 7, 8, 13, 14, 27, 28, 55, 56, 63, 64, 68, 69]
+    pts = [tuple(rng.choice(special, 3)) for _ in range(120)]
+    pts += [tuple(rng.integers(0, 70, 3)) for _ in range(80)]
+    got = np.array([y[:, z, yy, xx] for z, yy, xx in pts])
+    want = np.array([E.forward(params, window(x, p))[0][:, 3, 3, 3] for p in pts])
+    within_emulated(got, want, "sampled output")
+
+
 def test_zero_weights_predict_no_change(hpf_gpu):
     mesh = (13, 10, 5)
     with hpf_gpu.Propagator(mesh) as net:
