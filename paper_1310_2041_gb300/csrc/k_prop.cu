@@ -565,9 +565,9 @@ __global__ void k_pack_tc_image(const __nv_bfloat16* __restrict__ W, int k,
 // epilogue reads a finished plane, resets its slot and hands it back before
 // its own arithmetic and stores.
 //
-// Warp 0: TMA producer (a ring of kSwStages plane boxes); warp 1: owner of
-// the tensor memory and MMA issuer; warps 2..5: epilogue, one tensor-memory
-// lane quarter each.  Every wait is bounded; one that gives up raises
+// Warp 0: TMA producer (a ring of kSwStages two-plane stages); warp 1: owner
+// of the tensor memory and MMA issuer; warps 2..9: epilogue, two per
+// tensor-memory lane quarter, each with one channel half (8 channels).  Every wait is bounded; one that gives up raises
 // kFlagTimeout and a shared abort word that ends every role's loop, after
 // which the CTA waits (bounded) for its copies and MMAs in flight and
 // releases its tensor memory.
@@ -578,7 +578,7 @@ constexpr uint32_t kSwHalfBytes = 2u * kSwPlaneBytes;    // one channel half of 
 constexpr uint32_t kSwStageBytes = 2u * kSwHalfBytes;    // two input planes
 constexpr int kSwStages = 9;
 constexpr int kSwRingMax = 10;
-constexpr int kSwEpiWarps = 4;
+constexpr int kSwEpiWarps = 8;                           // two per tensor-memory lane quarter
 constexpr int kSwThreads = 32 * (2 + kSwEpiWarps);
 constexpr int kSwPerSM = 2;                              // CTAs (sweeps) per SM
 constexpr size_t kSwSmemFloor = 80 * 1024;               // at most two CTAs per SM
@@ -740,31 +740,55 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
         : "memory");
 }
 
-// Initial value of a slot for this warp's lanes: the bias in the dx = 0 block
-// (channels 0..15 of the first layer, columns 16..31 of the second, columns
-// 2 and 3 of the last), zero elsewhere.
-template <int kL>
-__device__ __forceinline__ void sw_reset_slot(uint32_t taddr, const float (&binit)[16]) {
-    float zero[16];
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
 #pragma unroll
-    for (int c = 0; c < 16; ++c) zero[c] = 0.f;
+    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+        : "memory");
+}
+
+// Initial value of a slot, the columns of this warp's channel half g: the
+// bias in the dx = 0 block (channels 8g .. 8g + 7 of the first layer, columns
+// 16 + 8g .. of the second), zero elsewhere; the last layer's 16 columns
+// (bias in columns 2 and 3) belong to the g = 0 warps.
+template <int kL>
+__device__ __forceinline__ void sw_reset_slot(uint32_t taddr, int g, const float (&binit)[16]) {
+    float zero[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) zero[c] = 0.f;
     if (kL == 1) {
-        tmem_st16(taddr, zero);
-        tmem_st16(taddr + 16, binit);
-        tmem_st16(taddr + 32, zero);
-    } else {
+        tmem_st8(taddr + 8 * g, zero);
+        tmem_st8(taddr + 16 + 8 * g, binit);
+        tmem_st8(taddr + 32 + 8 * g, zero);
+    } else if (kL == 0) {
+        tmem_st8(taddr + 8 * g, binit);
+    } else if (g == 0) {
         tmem_st16(taddr, binit);
     }
 }
 
-// A voxel's two channel halves to the padded layout, with its periodic
-// copies in the halo when it lies on a face (up to eight at a corner).
-__device__ __forceinline__ void sw_store_act(__nv_bfloat16* __restrict__ act, const SweepArgs& a,
-                                             int X, int Y, int Z, uint4 lo, uint4 hi) {
+// One channel half (8 BF16 channels) of a voxel to the padded layout, with
+// its periodic copies in the halo when it lies on a face (up to eight at a
+// corner).
+__device__ __forceinline__ void sw_store_half(__nv_bfloat16* __restrict__ act, const SweepArgs& a,
+                                              int X, int Y, int Z, int h, uint4 v) {
     const int xs[2] = {X + 1, X == 0 ? a.mx + 1 : (X == a.mx - 1 ? 0 : -1)};
     const int ys[2] = {Y + 1, Y == 0 ? a.my + 1 : (Y == a.my - 1 ? 0 : -1)};
     const int zs[2] = {Z + 1, Z == 0 ? a.mz + 1 : (Z == a.mz - 1 ? 0 : -1)};
-    const size_t hs = (size_t)(a.mz + 2) * a.py * a.px;  // voxels per half
+    uint4* base = reinterpret_cast<uint4*>(act) + (size_t)h * (a.mz + 2) * a.py * a.px;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (zs[k] < 0) continue;
@@ -774,10 +798,7 @@ __device__ __forceinline__ void sw_store_act(__nv_bfloat16* __restrict__ act, co
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 if (xs[i] < 0) continue;
-                uint4* o = reinterpret_cast<uint4*>(act) +
-                           ((size_t)zs[k] * a.py + ys[j]) * a.px + xs[i];
-                o[0] = lo;
-                o[hs] = hi;
+                base[((size_t)zs[k] * a.py + ys[j]) * a.px + xs[i]] = v;
             }
         }
     }
@@ -850,6 +871,9 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
     const uint32_t accf_b = bar0 + 16 * kSwStages;
     const uint32_t w_b = accf_b + 8 * kSwRingMax, done_b = w_b + 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the next layer may be scheduled now: its CTAs take an SM as ours leave it
+    // and run their prologue while this grid finishes
+    griddep_launch_dependents();
     if (tid == 0) {
         for (int k = 0; k < kSwBars; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k) : "memory");
@@ -869,21 +893,24 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    const int eg = (warp - 2) >> 2;  // an epilogue warp's channel half
     float binit[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) binit[c] = 0.f;
-    if (kL == 2) {
-        binit[2] = a.bias[0];
-        binit[3] = a.bias[1];
-    } else {
+    if (warp >= 2) {
+        if (kL == 2) {
+            binit[2] = a.bias[0];
+            binit[3] = a.bias[1];
+        } else {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) binit[c] = a.bias[c];
+            for (int c = 0; c < 8; ++c) binit[c] = a.bias[8 * eg + c];
+        }
     }
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     if (warp >= 2) {
 #pragma unroll 1
         for (int s = 0; s < kSwRing; ++s)
-            sw_reset_slot<kL>(tmem + (uint32_t)((kSwRing - 1 - s) * C) + lane_off, binit);
+            sw_reset_slot<kL>(tmem + (uint32_t)((kSwRing - 1 - s) * C) + lane_off, eg, binit);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -910,6 +937,7 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
             "[%3];" ::"r"(w_s),
             "l"(src), "r"(kWBytes), "r"(w_b)
             : "memory");
+        griddep_wait();  // the activations are the previous layer's output
         // Stages run up to kSwStages ahead (a stage is reused once the MMAs that
         // read it are done); between issues the producer watches the copies
         // land, in order, and publishes their count, so that the MMA thread
@@ -970,6 +998,7 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
         // ---------------------------------------------------------------- MMA issuer
         // A single thread: descriptors are formed once and offset per MMA (the
         // start-address field, in 16-byte units, is the low bits).
+        griddep_wait();
         bool ok = sw_wait(w_b, 0, abort_w, a.flag);
         const uint64_t adesc0 = umma_smem_desc(stage_s, kSwHalfBytes, 128u);
         const uint64_t bdesc0 = umma_smem_desc(w_s, 16u * 3 * RW, 128u);
@@ -1035,6 +1064,7 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------------- epilogue
+        griddep_wait();  // before the first store
         const int r = 32 * (warp & 3) + lane, bx = r & 15, by = r >> 4;
         int k = 0;
         bool ok = true;
@@ -1054,17 +1084,23 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t taddr = tmem + (uint32_t)((kSwRing - 1 - slot) * C) + lane_off;
-                float v[C];
+                // this warp's columns: per dx block (second layer) its 8 channels
+                float v[24];
+                if (kL == 1) {
 #pragma unroll
-                for (int c = 0; c < C; c += 16) tmem_ld16(taddr + c, v + c);
+                    for (int b = 0; b < 3; ++b) tmem_ld8(taddr + 16 * b + 8 * eg, v + 8 * b);
+                } else if (kL == 0 || eg == 0) {
+                    tmem_ld8(taddr + (kL == 0 ? 8 * eg : 0), v);
+                }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                sw_reset_slot<kL>(taddr, binit);
+                sw_reset_slot<kL>(taddr, eg, binit);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) count_release(rel_s + 4u * (warp - 2));
                 const size_t gv = ((size_t)zo * a.my + Y) * a.mx + X;
                 if (kL == 2) {
+                    if (eg != 0) continue;
                     float o[2];
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
@@ -1080,33 +1116,30 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                         }
                     }
                 } else {
-                    float o[16];
+                    float o[8];
                     if (kL == 1) {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            o[c] = __shfl_up_sync(0xffffffffu, v[c], 1) + v[16 + c] +
-                                   __shfl_down_sync(0xffffffffu, v[32 + c], 1);
+                        for (int c = 0; c < 8; ++c)
+                            o[c] = __shfl_up_sync(0xffffffffu, v[c], 1) + v[8 + c] +
+                                   __shfl_down_sync(0xffffffffu, v[16 + c], 1);
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) o[c] = v[c];
+                        for (int c = 0; c < 8; ++c) o[c] = v[c];
                     }
                     if (valid) {
                         if (a.z_out) {
-                            float4* zo4 = reinterpret_cast<float4*>(a.z_out + gv * kPC);
-#pragma unroll
-                            for (int c4 = 0; c4 < 4; ++c4)
-                                zo4[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2],
-                                                      o[4 * c4 + 3]);
+                            float4* zo4 = reinterpret_cast<float4*>(a.z_out + gv * kPC + 8 * eg);
+                            zo4[0] = make_float4(o[0], o[1], o[2], o[3]);
+                            zo4[1] = make_float4(o[4], o[5], o[6], o[7]);
                         }
-                        __nv_bfloat162 h[8];
+                        __nv_bfloat162 h[4];
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
+                        for (int c = 0; c < 4; ++c) {
                             const float u = o[2 * c], w = o[2 * c + 1];
                             h[c] = __floats2bfloat162_rn(__fdividef(u, 1.0f + __expf(-u)),
                                                          __fdividef(w, 1.0f + __expf(-w)));
                         }
-                        sw_store_act(a.act_out, a, X, Y, zo, reinterpret_cast<uint4*>(h)[0],
-                                     reinterpret_cast<uint4*>(h)[1]);
+                        sw_store_half(a.act_out, a, X, Y, zo, eg, *reinterpret_cast<uint4*>(h));
                     }
                 }
             }
@@ -1163,7 +1196,9 @@ template <int kL>
 void launch_conv_sweep(const CUtensorMap& tmap, const SweepArgs& a, int ctas, cudaStream_t s) {
     conv_sweep_setup();
     const int grid = a.total < ctas ? a.total : ctas;
-    if (grid > 0) k_conv_sweep<kL><<<grid, kSwThreads, sw_smem_bytes(kL), s>>>(tmap, a);
+    // programmatic launch: the prologue overlaps the previous layer's tail;
+    // every role waits for the previous grid before touching its output
+    if (grid > 0) launch_pdl(k_conv_sweep<kL>, grid, kSwThreads, sw_smem_bytes(kL), s, tmap, a);
 }
 
 // Weight image of layer kL in the B layout of k_conv_sweep, kTcWCopies times:
