@@ -671,10 +671,12 @@ __device__ __forceinline__ void count_publish(uint32_t addr, uint32_t v) {
     asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target,
+__device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target, uint32_t& known,
                                               volatile int* abort_w, int* flag) {
+    if (known >= target) return true;
     for (unsigned it = 0; it < kTcWaitLimit; ++it) {
-        if (count_acquire(addr) >= target) return true;
+        known = count_acquire(addr);
+        if (known >= target) return true;
         if (*abort_w) return false;
     }
     *abort_w = 1;
@@ -682,8 +684,11 @@ __device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target,
     return false;
 }
 
-__device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target,
+// known: the smallest count seen so far (counts only grow), so that a target
+// it already covers needs no loads.
+__device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target, uint32_t& known,
                                                  volatile int* abort_w, int* flag) {
+    if (known >= target) return true;
     for (unsigned it = 0; it < kTcWaitLimit; ++it) {
         uint32_t m = count_acquire(addr);
 #pragma unroll
@@ -691,6 +696,7 @@ __device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target,
             const uint32_t c = count_acquire(addr + 4u * w);
             m = c < m ? c : m;
         }
+        known = m;
         if (m >= target) return true;
         if (*abort_w) return false;
     }
@@ -1007,8 +1013,9 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
         in.begin(a, q0, q1);
         int kb = 0;       // ring index of the run's first plane
         int s_first = 0;  // its slot
+        uint32_t known_loaded = 0, known_released = 0;
         for (int si = 0; si < n_stages && ok; ++si) {
-            if (!sw_wait_count(loaded_s, (uint32_t)(si + 1), abort_w, a.flag)) {
+            if (!sw_wait_count(loaded_s, (uint32_t)(si + 1), known_loaded, abort_w, a.flag)) {
                 ok = false;
                 break;
             }
@@ -1024,7 +1031,8 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                 const int khi = kb + hi - zs;
                 if (zi + 1 < ze && khi >= kSwRing) {
                     // plane khi is first fed now: its slot was released with plane khi - R
-                    if (!sw_wait_released(rel_s, (uint32_t)(khi - kSwRing + 1), abort_w, a.flag)) {
+                    if (!sw_wait_released(rel_s, (uint32_t)(khi - kSwRing + 1), known_released,
+                                          abort_w, a.flag)) {
                         ok = false;
                         break;
                     }
@@ -1328,16 +1336,17 @@ __device__ __forceinline__ void input_features(const float* __restrict__ x, int 
     f[3] = b1;
 }
 
-// One thread per voxel of the padded array [Mz + 2][My + 2][Mx + 2] (halo
+// One thread per voxel of the padded array [Mz + 2][My + 2][Mx + 2] (grid y:
+// the padded plane; halo
 // included, each halo voxel a copy of the opposite face): out_x in the padded
 // layout of the forward convolutions [2][Mz + 2][py][px][8]; out (optional, for the
 // weight gradient): the plain four channels [V][16] at the interior voxels.
 __global__ void k_pack_input(const float* __restrict__ x, PropGeom g, int px, int py, float scale,
                              __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_x) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // voxel of the padded plane hz
     const int wx = g.mx + 2, wy = g.my + 2, wz = g.mz + 2;
-    if (i >= (long long)wx * wy * wz) return;
-    const int hx = (int)(i % wx), hy = (int)((i / wx) % wy), hz = (int)(i / ((long long)wx * wy));
+    if (i >= wx * wy) return;
+    const int hy = i / wx, hx = i - hy * wx, hz = blockIdx.y;
     const int xi = hx == 0 ? g.mx - 1 : (hx == g.mx + 1 ? 0 : hx - 1);
     const int yi = hy == 0 ? g.my - 1 : (hy == g.my + 1 ? 0 : hy - 1);
     const int z = hz == 0 ? g.mz - 1 : (hz == g.mz + 1 ? 0 : hz - 1);
@@ -1745,8 +1754,8 @@ SweepArgs sweep_args(const hpf_prop* p, int layer, int* flag) {
 // output divided by scale).
 void prop_forward(hpf_prop* p, const float* x, bool keep_z, cudaStream_t s, int* flag,
                   float* y_planar = nullptr) {
-    const long long hv = (long long)(p->g.mx + 2) * (p->g.my + 2) * (p->g.mz + 2);
-    k_pack_input<<<(unsigned)((hv + 255) / 256), 256, 0, s>>>(
+    const int hp = (p->g.mx + 2) * (p->g.my + 2);  // padded voxels per plane
+    k_pack_input<<<dim3((unsigned)((hp + 255) / 256), (unsigned)(p->g.mz + 2)), 256, 0, s>>>(
         x, p->g, p->px, p->py, p->scale, keep_z ? p->act[0] : nullptr, p->act_x);
     SweepArgs a = sweep_args(p, 0, flag);
     a.z_out = keep_z ? p->z[0] : nullptr;
