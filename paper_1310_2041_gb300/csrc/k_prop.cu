@@ -675,6 +675,7 @@ __device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target, ui
                                               volatile int* abort_w, int* flag) {
     if (known >= target) return true;
     for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        if (it) __nanosleep(32);
         known = count_acquire(addr);
         if (known >= target) return true;
         if (*abort_w) return false;
@@ -690,6 +691,7 @@ __device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target,
                                                  volatile int* abort_w, int* flag) {
     if (known >= target) return true;
     for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+        if (it) __nanosleep(32);  // a poll leaves the issue slots to the working warps
         uint32_t m = count_acquire(addr);
 #pragma unroll
         for (int w = 1; w < kSwEpiWarps; ++w) {
@@ -988,6 +990,8 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                 *abort_w = 1;
                 atomicOr(a.flag, kFlagTimeout);
                 break;
+            } else {
+                __nanosleep(64);  // nothing to issue or publish yet
             }
         }
         // every copy issued lands before the CTA ends (the last phase of each
