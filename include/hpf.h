@@ -478,9 +478,13 @@ hpf_status hpf_prop_set_weights(hpf_prop* prop, const float* params);
 /* Copy the FP32 parameters out (synchronises for a host destination). */
 hpf_status hpf_prop_get_weights(hpf_prop* prop, float* params);
 
-/* dphi [2][Mz][My][Mx] = network(x [4][Mz][My][Mx]).  Synchronises for a
- * host destination (and then reports HPF_ERR_TIMEOUT as above); with a
- * device destination it returns without waiting. */
+/* dphi [2][Mz][My][Mx] = network(x [4][Mz][My][Mx]).  Arrays on the current
+ * device are read and written in place by the kernels on the handle's
+ * stream (x is consumed by the first kernel, so it may alias dphi; neither
+ * may change until the stream has passed the call); host arrays go through
+ * the handle's staging buffers.  Synchronises for a host destination (and
+ * then reports HPF_ERR_TIMEOUT as above); with a device destination it
+ * returns without waiting.  Errors: HPF_ERR_INVALID (NULL), HPF_ERR_CUDA. */
 hpf_status hpf_prop_forward(hpf_prop* prop, const float* x, float* dphi);
 
 /* Autoregressive use of a network trained at lag 1 (the per-step variant of
