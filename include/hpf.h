@@ -469,8 +469,9 @@ hpf_status hpf_prop_set_scale(hpf_prop* prop, float scale);
 hpf_status hpf_prop_get_scale(const hpf_prop* prop, float* scale);
 
 /* At most ctas CTAs for the persistent forward convolutions (the output
- * planes are split evenly over them); 0 restores one CTA per SM.  Results do
- * not depend on it.  Errors: HPF_ERR_INVALID (ctas < 0). */
+ * planes are split evenly over them); 0 restores the default of two CTAs per
+ * SM.  Results do not depend on it (bit for bit).  Errors: HPF_ERR_INVALID
+ * (ctas < 0). */
 hpf_status hpf_prop_set_ctas(hpf_prop* prop, int32_t ctas);
 
 /* Load [param_count] FP32 parameters (and reset Adam); synchronises. */

@@ -647,7 +647,8 @@ class Propagator:
         self._check(self.lib.hpf_prop_set_scale(self.h, float(value)))
 
     def set_ctas(self, ctas: int):
-        """At most ctas CTAs for the persistent forward convolutions (0: one per SM)."""
+        """At most ctas CTAs for the persistent forward convolutions (0: the
+        default, two per SM); results do not depend on it."""
         self._check(self.lib.hpf_prop_set_ctas(self.h, int(ctas)))
 
     def set_weights(self, params):

@@ -119,6 +119,24 @@ def test_forward_does_not_depend_on_the_cta_split(hpf_gpu, ctas):
     within_emulated(y1, ye, "output")
 
 
+@pytest.mark.parametrize("mesh", [(70, 70, 2), (13, 10, 5), (3, 2, 2)],
+                         ids=lambda m: "x".join(map(str, m)))
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_forward_split_on_thin_and_tiny_meshes(hpf_gpu, mesh, ctas):
+    # Mz = 2: every run of input planes wraps in z and ends with a padding
+    # plane past the padded array; a mesh smaller than one box in x and y
+    params = rand_params(8)
+    x = rand_phi(grid(mesh), 9).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        y0 = net.forward(x)
+        net.set_ctas(ctas)
+        y1 = net.forward(x)
+    assert np.array_equal(y0, y1)
+    ye, _, _, _ = E.forward(params, x)
+    within_emulated(y1, ye, "output")
+
+
 def window(a, c, r=3):
     """The periodic (2r + 1)^3 window of a planar mesh a [C][Mz][My][Mx]
     centred on c = (z, y, x): the receptive field of the three layers there."""
