@@ -1347,6 +1347,9 @@ __device__ __forceinline__ void input_features(const float* __restrict__ x, int 
 // weight gradient): the plain four channels [V][16] at the interior voxels.
 __global__ void k_pack_input(const float* __restrict__ x, PropGeom g, int px, int py, float scale,
                              __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_x) {
+    // the first convolution (a programmatic launch) may start its prologue now;
+    // it waits for this grid before reading what it writes
+    griddep_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;  // voxel of the padded plane hz
     const int wx = g.mx + 2, wy = g.my + 2, wz = g.mz + 2;
     if (i >= wx * wy) return;
