@@ -468,6 +468,16 @@ int32_t hpf_prop_param_count(void);
 hpf_status hpf_prop_set_scale(hpf_prop* prop, float scale);
 hpf_status hpf_prop_get_scale(const hpf_prop* prop, float* scale);
 
+/* Self-test of the forward convolutions' bounded waits: the first layer runs
+ * on the handle's current input with its finished output planes never
+ * signalled, so every CTA's waits run out (0.2 s), raise the timeout flag,
+ * end every role of the CTA and release its tensor memory.  The flag is
+ * cleared again, so the handle stays usable; *seconds (may be NULL) is the
+ * host-measured time.  Returns HPF_ERR_TIMEOUT when the waits gave up as
+ * designed, HPF_OK if they did not act.  Synchronises.
+ * Errors: HPF_ERR_INVALID, HPF_ERR_CUDA. */
+hpf_status hpf_prop_selftest_timeout(hpf_prop* prop, double* seconds);
+
 /* At most ctas CTAs for the persistent forward convolutions (the output
  * planes are split evenly over them); 0 restores the default of two CTAs per
  * SM.  Results do not depend on it (bit for bit).  Errors: HPF_ERR_INVALID

@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <chrono>
 #include <string>
 
 #include "hpf_internal.cuh"
@@ -614,6 +615,8 @@ struct SweepArgs {
     int* flag;
     int mx, my, mz, px, py;    // mesh and padded pitches
     int ncx, total;            // columns along x; output planes of all columns
+    int withhold;              // self-test: no finished plane is signalled, so the
+                               // epilogue's waits give up (hpf_prop_selftest_timeout)
 };
 
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
@@ -628,10 +631,26 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return done != 0;
 }
 
+// A wait gives up after kTcWaitLimit polls or kSwWaitNs of wall time,
+// whichever comes first (work that arrives at all arrives within
+// microseconds); the clock is read every 64 polls.
+constexpr unsigned long long kSwWaitNs = 200000000ull;
+
+__device__ __forceinline__ unsigned long long sw_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool sw_late(unsigned it, unsigned long long t0) {
+    return (it & 63u) == 63u && sw_now() - t0 > kSwWaitNs;
+}
+
 // Bounded wait that also gives up when another role has aborted.
 __device__ __forceinline__ bool sw_wait(uint32_t bar, uint32_t parity, volatile int* abort_w,
                                         int* flag) {
-    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+    const unsigned long long t0 = sw_now();
+    for (unsigned it = 0; it < kTcWaitLimit && !sw_late(it, t0); ++it) {
         if (mbar_test(bar, parity)) return true;
         if (*abort_w) return false;
     }
@@ -674,7 +693,8 @@ __device__ __forceinline__ void count_publish(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target, uint32_t& known,
                                               volatile int* abort_w, int* flag) {
     if (known >= target) return true;
-    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+    const unsigned long long t0 = sw_now();
+    for (unsigned it = 0; it < kTcWaitLimit && !sw_late(it, t0); ++it) {
         if (it) __nanosleep(32);
         known = count_acquire(addr);
         if (known >= target) return true;
@@ -690,7 +710,8 @@ __device__ __forceinline__ bool sw_wait_count(uint32_t addr, uint32_t target, ui
 __device__ __forceinline__ bool sw_wait_released(uint32_t addr, uint32_t target, uint32_t& known,
                                                  volatile int* abort_w, int* flag) {
     if (known >= target) return true;
-    for (unsigned it = 0; it < kTcWaitLimit; ++it) {
+    const unsigned long long t0 = sw_now();
+    for (unsigned it = 0; it < kTcWaitLimit && !sw_late(it, t0); ++it) {
         if (it) __nanosleep(32);  // a poll leaves the issue slots to the working warps
         uint32_t m = count_acquire(addr);
 #pragma unroll
@@ -954,6 +975,7 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
         in.begin(a, q0, q1);
         int si = 0, pub = 0;
         unsigned idle = 0;
+        unsigned long long idle_t0 = 0;
         while (si < n_stages || pub < si) {
             bool progress = false;
             const int st = si % kSwStages;
@@ -986,23 +1008,28 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                 idle = 0;
             } else if (*abort_w) {
                 break;
-            } else if (++idle >= kTcWaitLimit) {
-                *abort_w = 1;
-                atomicOr(a.flag, kFlagTimeout);
-                break;
             } else {
+                if (idle == 0) idle_t0 = sw_now();
+                if (++idle >= kTcWaitLimit || sw_late(idle, idle_t0)) {
+                    *abort_w = 1;
+                    atomicOr(a.flag, kFlagTimeout);
+                    break;
+                }
                 __nanosleep(64);  // nothing to issue or publish yet
             }
         }
         // every copy issued lands before the CTA ends (the last phase of each
         // stage is the one to wait for)
         const int used = si < kSwStages ? si : kSwStages;
+        const unsigned long long t0 = sw_now();
         for (int st = 0; st < used; ++st) {
             const int j = si - 1 - ((si - 1 - st) % kSwStages);
-            for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(full_b + 8 * st, (j / kSwStages) & 1); ++k) {
+            for (unsigned k = 0; k < kTcWaitLimit && !sw_late(k, t0) &&
+                                 !mbar_test(full_b + 8 * st, (j / kSwStages) & 1);
+                 ++k) {
             }
         }
-        for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(w_b, 0); ++k) {
+        for (unsigned k = 0; k < kTcWaitLimit && !sw_late(k, t0) && !mbar_test(w_b, 0); ++k) {
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
@@ -1060,7 +1087,7 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
                     dzi += n;
                     slot = kSwRing - 1;
                 }
-                if (zi - 1 >= zs) {  // plane zi - 1 has all its inputs
+                if (zi - 1 >= zs && !a.withhold) {  // plane zi - 1 has all its inputs
                     int s1 = s_first + (zi - 1 - zs);
                     while (s1 >= kSwRing) s1 -= kSwRing;
                     umma_commit(accf_b + 8 * s1);
@@ -1072,7 +1099,8 @@ __global__ void __launch_bounds__(kSwThreads, kSwPerSM)
             in.next(a);
         }
         umma_commit(done_b);
-        for (unsigned k = 0; k < kTcWaitLimit && !mbar_test(done_b, 0); ++k) {
+        const unsigned long long t0 = sw_now();
+        for (unsigned k = 0; k < kTcWaitLimit && !sw_late(k, t0) && !mbar_test(done_b, 0); ++k) {
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------------------- epilogue
@@ -2035,6 +2063,28 @@ hpf_status hpf_prop_set_weights(hpf_prop* p, const float* params) {
 hpf_status hpf_prop_get_weights(hpf_prop* p, float* params) {
     if (!p || !params) return HPF_ERR_INVALID;
     return prop_copy_out(p, params, p->params, sizeof(float) * p->np);
+}
+
+hpf_status hpf_prop_selftest_timeout(hpf_prop* p, double* seconds) {
+    if (!p) return HPF_ERR_INVALID;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return HPF_ERR_CUDA;
+    }
+    // the first layer on the handle's current input, its finished planes never
+    // signalled: every CTA's epilogue waits run out, the CTAs abort and release
+    // their tensor memory
+    SweepArgs a = sweep_args(p, 0, p->flag);
+    a.act_out = p->act[1];
+    a.withhold = 1;
+    const auto t0 = std::chrono::steady_clock::now();
+    launch_conv_sweep<0>(p->tmap[0], a, p->ctas, p->stream);
+    hpf_status st = prop_launched(p);
+    if (st == HPF_OK) st = prop_flag_status(p);  // synchronises; clears the flag it reports
+    if (seconds)
+        *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
 }
 
 hpf_status hpf_prop_set_ctas(hpf_prop* p, int32_t ctas) {

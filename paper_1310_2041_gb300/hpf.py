@@ -148,6 +148,7 @@ def load():
         L.hpf_prop_set_scale.argtypes = [vp, ctypes.c_float]
         L.hpf_prop_get_scale.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.hpf_prop_set_ctas.argtypes = [vp, i32]
+        L.hpf_prop_selftest_timeout.argtypes = [vp, dp]
         L.hpf_prop_forward.argtypes = [vp, vp, vp]
         L.hpf_prop_rollout.argtypes = [vp, vp, i32, vp]
         L.hpf_prop_backward.argtypes = [vp, vp, vp, vp, dp]
@@ -162,6 +163,7 @@ def load():
                                        ctypes.POINTER(LearnedStats)]
         for name in ("hpf_prop_init", "hpf_prop_destroy", "hpf_prop_set_weights",
                      "hpf_prop_set_scale", "hpf_prop_get_scale", "hpf_prop_set_ctas",
+                     "hpf_prop_selftest_timeout",
                      "hpf_prop_get_weights", "hpf_prop_forward", "hpf_prop_rollout",
                      "hpf_prop_backward",
                      "hpf_prop_adam_step", "hpf_prop_train_step", "hpf_density_phi",
@@ -650,6 +652,13 @@ class Propagator:
         """At most ctas CTAs for the persistent forward convolutions (0: the
         default, two per SM); results do not depend on it."""
         self._check(self.lib.hpf_prop_set_ctas(self.h, int(ctas)))
+
+    def selftest_timeout(self):
+        """Run the forward convolutions' wait self-test; returns (status code,
+        seconds): HPF_ERR_TIMEOUT (6) when the bounded waits gave up as designed."""
+        secs = ctypes.c_double()
+        st = self.lib.hpf_prop_selftest_timeout(self.h, ctypes.byref(secs))
+        return int(st), float(secs.value)
 
     def set_weights(self, params):
         pp, _a = _ptr(params, np.float32, (self.n_params,), "params")

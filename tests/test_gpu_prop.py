@@ -137,6 +137,29 @@ def test_forward_split_on_thin_and_tiny_meshes(hpf_gpu, mesh, ctas):
     within_emulated(y1, ye, "output")
 
 
+def test_sweep_waits_give_up_and_the_handle_stays_usable(hpf_gpu):
+    # the first layer with its finished planes never signalled: every CTA's
+    # bounded waits must run out (no hang), the timeout be reported once, the
+    # tensor memory be released, and the next forward be unaffected
+    mesh = (26, 34, 18)
+    params = rand_params(10)
+    x = rand_phi(grid(mesh), 11).astype(np.float32)
+    with hpf_gpu.Propagator(mesh) as net:
+        net.set_weights(hpf_gpu.pack_params(params))
+        y0 = net.forward(x)
+        st, secs = net.selftest_timeout()
+        assert st == 6, st  # HPF_ERR_TIMEOUT
+        assert secs < 5.0
+        y1 = net.forward(x)
+        net.set_ctas(3)  # long sweeps: the abort path with slots waiting for releases
+        st, _ = net.selftest_timeout()
+        assert st == 6, st
+        net.set_ctas(0)
+        y2 = net.forward(x)
+    assert np.array_equal(y0, y1)
+    assert np.array_equal(y0, y2)
+
+
 def window(a, c, r=3):
     """The periodic (2r + 1)^3 window of a planar mesh a [C][Mz][My][Mx]
     centred on c = (z, y, x): the receptive field of the three layers there."""
