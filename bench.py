@@ -161,6 +161,26 @@ def traffic_record(workload: str):
     return None
 
 
+PROP_SRC = [os.path.join(ROOT, "paper_1310_2041_gb300", "csrc", "k_prop.cu")]
+
+
+def conv_traffic_record(workload: str):
+    """DRAM bytes per inference of the three forward convolutions on `workload`
+    from the committed ncu summary, valid only while k_prop.cu is unchanged
+    since the capture."""
+    try:
+        recs = json.load(open(TRAFFIC_FILE))["k_conv_sweep"]
+    except (OSError, KeyError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in PROP_SRC:
+        h.update(open(f, "rb").read())
+    for rec in recs:
+        if rec.get("workload") == workload and rec.get("source_sha256") == h.hexdigest():
+            return rec
+    return None
+
+
 def thermostat_params(args):
     if args.thermostat == "nh":
         return {"thermostat": 1, "nh_tau": args.nh_tau}
@@ -931,6 +951,7 @@ def run_propagator(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         clk = clocks.stop()
     infer_ms = statistics.median(ms)
+    rec = conv_traffic_record("propagator_70")
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
         peak_src = "measured"
@@ -946,7 +967,8 @@ def run_propagator(args):
             "config": {"workload": "propagator_70", "mesh": M,
                        "l2": "flushed (256 MB write) before each timed inference"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (rec or {}).get("dram_bytes_per_inference"),
                          "peak_source": peak_src, "kernel": "k_conv_sweep (three layers)",
                          "algo_flops_per_inference": flops},
             "roofline_hbm": {"bound": "hbm", "achieved": infer_bytes / (infer_ms * 1e-3) / 1e9,
