@@ -893,7 +893,9 @@ def run_learned(args):
                        "infer_ms": infer_ms, "net_by_lag": by_lag,
                        "smoothed": smoothed},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (conv_traffic_record("propagator_70") or {}).get(
+                             "dram_bytes_per_inference"),
                          "peak_source": peak_src,
                          "kernel": "k_conv_sweep (three layers, whole forward)",
                          "algo_flops_per_inference": flops},
