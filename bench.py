@@ -954,6 +954,18 @@ def run_propagator(args):
         clk = clocks.stop()
     infer_ms = statistics.median(ms)
     rec = conv_traffic_record("propagator_70")
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's FP64 forward (numpy) on the same input, once: about 2 s
+        from oracle import propagator as P
+        xs = x.cpu().numpy().astype(np.float64)
+        t = time.perf_counter()
+        P.forward(P.init_params(1), xs)
+        fwd = time.perf_counter() - t
+        cpu = {"value": 1.0 / fwd, "unit": "inferences/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"one FP64 forward of the oracle (numpy, its BLAS threads) on the "
+                         f"full {M}^3 mesh ({fwd:.2f} s)"}
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
         peak_src = "measured"
@@ -977,7 +989,7 @@ def run_propagator(args):
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": infer_bytes / (infer_ms * 1e-3) / 1e9 / hbm_peak,
                              "peak_source": hbm_src, "algo_bytes_per_inference": infer_bytes},
-            "cpu_baseline": None, "e2e": None, "clocks": clk}
+            "cpu_baseline": cpu, "e2e": None, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
