@@ -301,6 +301,8 @@ void derive_constants(hpf_ctx* c) {
     e.r0 = p.bond_r0;
     e.r0_hi = (float)p.bond_r0;
     e.r0_lo = (float)(p.bond_r0 - (double)e.r0_hi);
+    e.bond_k_hi = (float)p.bond_k;
+    e.bond_k_lo = (float)(p.bond_k - (double)e.bond_k_hi);
     e.kT = p.kT;
     e.angle_k = p.angle_k;
     e.cos0 = p.angle_cos0;

@@ -99,6 +99,7 @@ struct EnergyConsts {
     double bond_k;
     double r0;
     float r0_hi, r0_lo;  // r0 as a float-float pair
+    float bond_k_hi, bond_k_lo;  // bond_k as a float-float pair
     double kT;
     double inv_kappa;
     double phi_c;       // phi per fixed-point unit: 2^-39 / (rho0 h^3)

@@ -32,14 +32,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 }
 
 // The bond energy k (|d| - r0)^2 of d = x_i - x_j in float-float arithmetic
-// (pairs of FP32 numbers): each component of d exactly by two-sum, |d|^2 with
-// the exact error of each square (FMA) to about 2^-46, |d| from the
-// correctly rounded square root plus its residual, |d| - r0 against
-// r0 = r0_hi + r0_lo, and only the square of that in FP64.  Accurate to about
-// 1e-14 of |d|, like an FP64 evaluation, at a small part of its cost on a
-// GPU whose FP64 rate is low.
-__device__ __forceinline__ double bond_energy_ff(float xi, float yi, float zi, float xj, float yj,
-                                                 float zj, const EnergyConsts& e) {
+// (pairs of FP32 numbers), added to the float-float sum (uh, ul): each
+// component of d exactly by two-sum, |d|^2 with the exact error of each
+// square (FMA) to about 2^-46, |d| from the correctly rounded square root plus
+// its residual, |d| - r0 = a + b against r0 = r0_hi + r0_lo, renormalised
+// by two-sum; then (a + b)^2 = a^2 + 2ab + b^2 with |b| <= ulp(a)/2 -- a^2
+// exactly as p + pe,
+// 2ab rounded (2^-24 of a term 2^-23 below a^2), b^2 (2^-48 of a^2)
+// dropped -- times k = k_hi + k_lo, and a two-sum accumulation.  About
+// 2^-45 relative per term, like an FP64 evaluation, with no FP64 instruction
+// (this GPU's FP64 rate is 1/64 of its FP32 rate).
+__device__ __forceinline__ void bond_energy_ff(float xi, float yi, float zi, float xj, float yj,
+                                               float zj, const EnergyConsts& e, float& uh,
+                                               float& ul) {
     float hx, lx, hy, ly, hz, lz;
     two_sum(xi, -xj, hx, lx);
     two_sum(yi, -yj, hy, ly);
@@ -47,25 +52,41 @@ __device__ __forceinline__ double bond_energy_ff(float xi, float yi, float zi, f
     float H = 0.f, L = 0.f;
     const float hs[3] = {hx, hy, hz}, ls[3] = {lx, ly, lz};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float p = __fmul_rn(hs[a], hs[a]);
-        const float pe = fmaf(hs[a], hs[a], -p);                        // exact error of h^2
-        const float rest = fmaf(2.0f * hs[a], ls[a], fmaf(ls[a], ls[a], pe));  // 2hl + l^2 + pe
+    for (int c = 0; c < 3; ++c) {
+        const float p = __fmul_rn(hs[c], hs[c]);
+        const float pe = fmaf(hs[c], hs[c], -p);                        // exact error of h^2
+        const float rest = fmaf(2.0f * hs[c], ls[c], fmaf(ls[c], ls[c], pe));  // 2hl + l^2 + pe
         float t;
         two_sum(H, p, H, t);
         L = __fadd_rn(L, __fadd_rn(t, rest));
     }
     const float H2 = __fadd_rn(H, L);
     const float L2 = __fsub_rn(L, __fsub_rn(H2, H));
-    if (!(H2 > 0.f)) return e.bond_k * e.r0 * e.r0;
-    const float r = sqrtf(H2);
-    const float res = __fadd_rn(fmaf(-r, r, H2), L2);  // H2 - r^2 is exact
-    const float r_lo = 0.5f * res * rsqrtf(H2);
     float a, b;
-    two_sum(r, -e.r0_hi, a, b);
-    b = __fadd_rn(b, __fsub_rn(r_lo, e.r0_lo));
-    const double dr = (double)a + (double)b;
-    return e.bond_k * dr * dr;
+    if (H2 > 0.f) {
+        const float r = sqrtf(H2);
+        const float res = __fadd_rn(fmaf(-r, r, H2), L2);  // H2 - r^2 is exact
+        const float r_lo = 0.5f * res * rsqrtf(H2);
+        two_sum(r, -e.r0_hi, a, b);
+        b = __fadd_rn(b, __fsub_rn(r_lo, e.r0_lo));
+    } else {  // coincident beads: |d| - r0 = -r0
+        a = -e.r0_hi;
+        b = -e.r0_lo;
+    }
+    // renormalised, so that |b| <= ulp(a)/2 also when |d| is close to r0 (then
+    // the two parts of the difference are of similar size)
+    two_sum(a, b, a, b);
+    const float p = __fmul_rn(a, a);
+    const float pe = fmaf(a, a, -p);
+    const float q = fmaf(2.0f * a, b, pe);
+    const float u = __fmul_rn(e.bond_k_hi, p);
+    const float ue = fmaf(e.bond_k_hi, p, -u);
+    const float w = fmaf(e.bond_k_hi, q, fmaf(e.bond_k_lo, p, ue));
+    float s, t;
+    two_sum(uh, u, s, t);
+    t = __fadd_rn(t, __fadd_rn(ul, w));
+    uh = __fadd_rn(s, t);
+    ul = __fsub_rn(t, __fsub_rn(uh, s));
 }
 
 // Exact unsigned 128-bit sums (the field energy's node sums).
@@ -158,7 +179,8 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
                                                             EnergyConsts e,
                                                             double* __restrict__ partials) {
     __shared__ double sh[kRedBlock / 32];
-    double ub = 0.0;
+    double ub = 0.0;          // angle and dihedral energies (FP64)
+    float uh = 0.f, ul = 0.f;  // bond energy, float-float
     float kf = 0.f, pfx = 0.f, pfy = 0.f, pfz = 0.f;  // this thread's few beads
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float x = st.x[i], y = st.y[i], z = st.z[i];
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         if (m & kBondNext) {
             const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
             bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
-            ub += bond_energy_ff(x, y, z, xj, yj, zj, e);
+            bond_energy_ff(x, y, z, xj, yj, zj, e, uh, ul);
         }
         if (c.two_ka != 0.f) {
             angle_forces_of(st, meta, i, m, c, fx, fy, fz);
@@ -229,6 +251,7 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
         pfy += uy;
         pfz += uz;
     }
+    ub += (double)uh + (double)ul;
     const double vals[kBeadVals] = {0.5 * e.mass * (double)kf, ub, e.mass * (double)pfx,
                                     e.mass * (double)pfy, e.mass * (double)pfz};
 #pragma unroll
