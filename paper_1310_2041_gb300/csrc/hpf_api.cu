@@ -38,6 +38,12 @@ struct hpf_ctx {
     long long mesh_step = -1;         // step whose positions it holds (-1: none / injected)
     bool next_zero = false;           // the other mesh is known to be all zero
     long long part_step = -1;         // step whose partial mesh hpf_step_partial handed out
+    // deposit at the end of hpf_step calls: switched on when the observables
+    // of a step's final state had to scatter it, off again when such a
+    // deposit was not used before the next call
+    bool want_end_mesh = false;
+    bool end_mesh_unused = false;     // the last call's end deposit is still unread
+    long long end_of_call_step = -1;  // the step the last hpf_step call ended on
     float4* G = nullptr;              // field mesh (ghosted)
     float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
     FieldCoef* d_coef = nullptr;      // the stencil coefficients in device memory
@@ -406,7 +412,10 @@ int autotune_tile(cudaStream_t s, int S, Fill fill) {
 // The context's mesh holds the density of the current positions afterwards:
 // scatter into the other buffer (cleared first unless known zero) and flip.
 hpf_status scatter_current(hpf_ctx* c) {
-    if (c->mesh_step == c->step) return HPF_OK;
+    if (c->mesh_step == c->step) {
+        c->end_mesh_unused = false;
+        return HPF_OK;
+    }
     unsigned long long* dst = mesh_buf(c, c->dmesh ^ 1);
     {
         StageScope sc(c, HPF_STAGE_SCATTER, c->n > 0 ? 1 : 0);
@@ -671,10 +680,13 @@ hpf_status energy_launch(hpf_ctx* c) {
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
     hpf_status s = ensure_field(c);
     if (s != HPF_OK) return s;
-    // the mesh of the current positions for the field energy
+    // the mesh of the current positions for the field energy; when the last
+    // hpf_step call ended here without depositing it, later calls deposit
+    // their final positions in their last launch
+    if (c->mesh_step != c->step && c->end_of_call_step == c->step) c->want_end_mesh = true;
     if ((s = scatter_current(c)) != HPF_OK) return s;
     {
-        StageScope sc(c, HPF_STAGE_ENERGY, c->n > 0 ? 3 : 2);
+        StageScope sc(c, HPF_STAGE_ENERGY, energy_launches(c->n, c->S));
         launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
                       reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->ec,
                       c->partials, c->d_out6, c->stream);
@@ -947,6 +959,28 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     return HPF_OK;
 }
 
+// New state (tag order, device staging) into storage order, its density
+// deposited into the other mesh in the same pass: that mesh becomes the
+// context's, holding the density of the positions at `step`.
+static hpf_status repermute_deposit(hpf_ctx* c, const float* pos_tag, const float* vel_tag,
+                                    long long step) {
+    unsigned long long* dst = mesh_buf(c, c->dmesh ^ 1);
+    if (!c->next_zero)
+        CUDA_TRY(c, cudaMemsetAsync(dst, 0, sizeof(unsigned long long) * mesh_words(c), c->stream));
+    {
+        StageScope sc(c, HPF_STAGE_OTHER, 1);
+        launch_repermute(pos_tag, vel_tag, c->meta, c->n, cur_state(c), c->geom, dst, c->dflag,
+                         c->stream);
+    }
+    LAUNCH_CHECK(c);
+    c->dmesh ^= 1;
+    c->next_zero = false;
+    c->step = step;
+    c->mesh_step = step;
+    c->end_mesh_unused = false;
+    return HPF_OK;
+}
+
 hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int64_t step) {
     if (!c) return HPF_ERR_INVALID;
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
@@ -964,14 +998,9 @@ hpf_status hpf_update_state(hpf_ctx* c, const float* pos, const float* vel, int6
     float* svel = spos + 3 * (size_t)n;
     CUDA_TRY(c, cudaMemcpyAsync(spos, pos, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(svel, vel, sizeof(float) * 3 * n, cudaMemcpyDefault, c->stream));
-    {
-        StageScope sc(c, HPF_STAGE_OTHER, 1);
-        launch_repermute(spos, svel, c->meta, n, cur_state(c), c->dflag, c->stream);
-    }
-    LAUNCH_CHECK(c);
-    c->step = step;
+    hpf_status s = repermute_deposit(c, spos, svel, step);
+    if (s != HPF_OK) return s;
     c->field_valid = false;
-    c->mesh_step = -1;
     c->part_step = -1;
     return HPF_OK;
 }
@@ -1039,19 +1068,16 @@ hpf_status hpf_apply_state(hpf_ctx* c, int64_t step) {
     if (n > 0) {
         const int k = c->up_slot;
         CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->up_done[k], 0));
-        {
-            StageScope sc(c, HPF_STAGE_OTHER, 1);
-            launch_repermute(c->up_stage[k], c->up_stage[k] + 3 * (size_t)n, c->meta, n,
-                             cur_state(c), c->dflag, c->stream);
-        }
-        LAUNCH_CHECK(c);
+        hpf_status s = repermute_deposit(c, c->up_stage[k], c->up_stage[k] + 3 * (size_t)n, step);
+        if (s != HPF_OK) return s;
         CUDA_TRY(c, cudaEventRecord(c->up_free[k], c->stream));
         c->up_slot ^= 1;
+    } else {
+        c->mesh_step = -1;
     }
     c->up_pending = false;
     c->step = step;
     c->field_valid = false;
-    c->mesh_step = -1;
     c->part_step = -1;
     return HPF_OK;
 }
@@ -1132,12 +1158,38 @@ hpf_status hpf_forces(hpf_ctx* c, float* F_out, int32_t which) {
     return copy_out(c, F_out, c->out_f, sizeof(float) * 3 * c->n);
 }
 
+// Whether the launch of `chunk` steps from the current step deposits its final
+// positions into the other mesh: always when it ends on a refresh step and
+// that mesh is already clear (the field kernel clears it); also, as the last
+// launch of an hpf_step call, when calls have been followed by the
+// observables of their final state (the other mesh is cleared first if
+// need be: a memset costs far less than the scatter it saves).
+static hpf_status plan_deposit(hpf_ctx* c, long long chunk, bool last, bool& fuse) {
+    const bool refresh_end = (c->step + chunk) % c->p.field_every == 0;
+    fuse = refresh_end && c->next_zero;
+    if (!fuse && last && c->want_end_mesh && c->n > 0) {
+        if (!c->next_zero) {
+            CUDA_TRY(c, cudaMemsetAsync(mesh_buf(c, c->dmesh ^ 1), 0,
+                                        sizeof(unsigned long long) * mesh_words(c), c->stream));
+            c->next_zero = true;
+        }
+        fuse = true;
+    }
+    if (fuse && last && !refresh_end) c->end_mesh_unused = true;
+    return HPF_OK;
+}
+
 hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
     if (!c) return HPF_ERR_INVALID;
     if (n_steps < 0) return fail(c, HPF_ERR_INVALID, "n_steps must be >= 0");
     if (!c->has_state) return fail(c, HPF_ERR_STATE, "no state loaded");
     const long long fe = c->p.field_every;
     long long left = n_steps;
+    if (n_steps > 0) {
+        // an end deposit nobody read: stop making them
+        if (c->end_mesh_unused) c->want_end_mesh = false;
+        c->end_mesh_unused = false;
+    }
     if (c->nh) {
         while (left > 0) {
             hpf_status s = ensure_field(c);
@@ -1147,10 +1199,12 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
             if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
                 if ((s = sort_beads(c)) != HPF_OK) return s;
             }
-            const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
+            bool fuse;
+            if ((s = plan_deposit(c, chunk, chunk == left, fuse)) != HPF_OK) return s;
             if ((s = advance_nh(c, (int)chunk, fuse)) != HPF_OK) return s;
             left -= chunk;
         }
+        c->end_of_call_step = c->step;
         return HPF_OK;
     }
     while (left > 0) {
@@ -1164,11 +1218,12 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
             if ((s = sort_beads(c)) != HPF_OK) return s;
         }
-        // the launch that ends on a refresh step also scatters its final positions
-        const bool fuse = ((c->step + chunk) % fe == 0) && c->next_zero;
+        bool fuse;
+        if ((s = plan_deposit(c, chunk, chunk == left, fuse)) != HPF_OK) return s;
         if ((s = advance(c, (int)chunk, fuse)) != HPF_OK) return s;
         left -= chunk;
     }
+    c->end_of_call_step = c->step;
     return HPF_OK;
 }
 

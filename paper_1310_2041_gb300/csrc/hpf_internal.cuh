@@ -834,7 +834,8 @@ void launch_set_counter(long long* step, long long v, cudaStream_t s);
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,
                       int* flag, cudaStream_t s);
 void launch_repermute(const float* pos_tag, const float* vel_tag, const uint32_t* meta, int n,
-                      StateBuf st, int* flag, cudaStream_t s);
+                      StateBuf st, const MeshGeom& g, unsigned long long* D, int* flag,
+                      cudaStream_t s);
 
 long long sort_key_space(const MeshGeom& g);
 long long scan_scratch_words(long long L);
@@ -871,6 +872,7 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
                           int tile);
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);
 int energy_partials_needed(int n, int nodes, int S);
+int energy_launches(int n, int S);  // kernels launch_energy issues
 
 // learned density propagator (the network lives in k_prop.cu)
 bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);

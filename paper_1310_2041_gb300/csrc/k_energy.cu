@@ -6,22 +6,15 @@ namespace hpf {
 
 // ------------------------------------------------------------------ A7 FP64 observables
 
-constexpr int kRedBlock = 256;
-constexpr int kBeadVals = 5;  // kinetic, bond, px, py, pz
-constexpr int kBeadsPerThread = 8;  // grid-stride share of a thread (on average)
-constexpr int kNodesPerThread = 8;
-
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-    return r;  // valid in thread 0
-}
+constexpr int kRedBlock = 256;    // the bead and node kernels
+constexpr int kFinalBlock = 1024;  // the one block that combines their partials
+constexpr int kBeadVals = 5;       // kinetic, bond, px, py, pz
+// Grid-stride shares (on average) of a bead or node thread: small, so that a
+// million beads make about 2000 blocks, which the SMs take in several waves
+// with little left over for the last one (at 8 beads a thread the 489 blocks
+// of a million beads came to just over one wave of three blocks per SM).
+constexpr int kBeadsPerThread = 2;
+constexpr int kNodesPerThread = 2;
 
 // Knuth's two-sum: s + t == a + b exactly (round-to-nearest, no contraction).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
@@ -29,6 +22,41 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
     const float bv = __fsub_rn(s, a);
     const float av = __fsub_rn(s, bv);
     t = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Float-float sums (h, l): the partial sums of every observable are carried as
+// pairs of FP32 numbers, added with two-sum and renormalised, so that the
+// block and warp reductions run on the FP32 pipe (this GPU's FP64 rate is
+// 1/64 of its FP32 rate) with about 2^-45 relative error per addition, and in
+// a fixed tree, so that every bit is the same from run to run.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_norm(float s, float t) {
+    const float h = __fadd_rn(s, t);
+    return FF{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FF ff_plus(FF a, float x) {
+    float s, t;
+    two_sum(a.h, x, s, t);
+    return ff_norm(s, __fadd_rn(t, a.l));
+}
+__device__ __forceinline__ FF ff_plus(FF a, FF b) {
+    float s, t;
+    two_sum(a.h, b.h, s, t);
+    return ff_norm(s, __fadd_rn(t, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ff_from_double(double v) {
+    const float h = (float)v;
+    return FF{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.h + (double)v.l; }
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_plus(v, FF{__shfl_down_sync(0xffffffffu, v.h, o),
+                          __shfl_down_sync(0xffffffffu, v.l, o)});
+    return v;  // lane 0
 }
 
 // The bond energy k (|d| - r0)^2 of d = x_i - x_j in float-float arithmetic
@@ -104,18 +132,12 @@ __device__ __forceinline__ U128 u128_mul(unsigned long long a, unsigned long lon
 __device__ __forceinline__ double u128_to_double(const U128& v) {
     return (double)v.hi * 18446744073709551616.0 + (double)v.lo;
 }
-__device__ __forceinline__ U128 block_sum_u128(U128 v, U128* sh) {
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         u128_add(v, U128{__shfl_down_sync(0xffffffffu, v.lo, o),
                          __shfl_down_sync(0xffffffffu, v.hi, o)});
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    U128 r{0ull, 0ull};
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u128_add(r, sh[k]);
-    return r;  // valid in thread 0
+    return v;  // lane 0
 }
 
 // |d| in FP64 from an FP32 reciprocal-square-root seed and one Newton step
@@ -167,22 +189,24 @@ __device__ __forceinline__ double dihedral_energy_fp64(const StateBuf& st, int i
 // v_n = v + dt/(2m) F_n, then kinetic energy, momentum and the bond energy of
 // the bond to the next bead (each bond once).  The bond energy is formed in
 // float-float (bond_energy_ff), the angle and dihedral energies in FP64, all
-// from the FP32 positions with exact differences; v_n and its
-// squares are FP32 (the FP32 force already limits them to ~1e-7) and are
-// summed in FP32 over each thread's few beads (at most 8 on average), FP64
-// from the block sums on: this GPU's FP64 rate is low.
-__global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
-                                                            const uint32_t* __restrict__ meta,
-                                                            int n, MeshGeom g,
-                                                            const float4* __restrict__ G,
-                                                            StepConsts c, long long step,
-                                                            EnergyConsts e,
-                                                            double* __restrict__ partials) {
-    __shared__ double sh[kRedBlock / 32];
-    double ub = 0.0;          // angle and dihedral energies (FP64)
+// from the FP32 positions with exact differences; v_n and |v_n|^2 are FP32
+// (the FP32 force already limits them to ~1e-7) and are summed in float-float
+// over the thread's beads, its warp and its block, into one float-float
+// partial per observable and block (kinetic energy without the factor m/2 and
+// momentum without m, both applied in FP64 in k_energy_final).
+// Block blk of nb bead blocks (grid-stride over the beads within them).
+__device__ __forceinline__ void energy_beads_block(const StateBuf& st,
+                                                   const uint32_t* __restrict__ meta, int n,
+                                                   const MeshGeom& g,
+                                                   const float4* __restrict__ G,
+                                                   const StepConsts& c, long long step,
+                                                   const EnergyConsts& e,
+                                                   float2* __restrict__ partials, int blk, int nb,
+                                                   FF (*sh)[kRedBlock / 32]) {
+    double ub = 0.0;           // angle and dihedral energies (FP64)
     float uh = 0.f, ul = 0.f;  // bond energy, float-float
-    float kf = 0.f, pfx = 0.f, pfy = 0.f, pfz = 0.f;  // this thread's few beads
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    FF kf{0.f, 0.f}, pfx{0.f, 0.f}, pfy{0.f, 0.f}, pfz{0.f, 0.f};
+    for (int i = blk * kRedBlock + threadIdx.x; i < n; i += nb * kRedBlock) {
         const float x = st.x[i], y = st.y[i], z = st.z[i];
         const float vx = st.vx[i], vy = st.vy[i], vz = st.vz[i];
         const uint32_t m = meta[i];
@@ -246,18 +270,25 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
             uy = c.sig_v * ny;
             uz = c.sig_v * nz;
         }
-        kf = fmaf(ux, ux, fmaf(uy, uy, fmaf(uz, uz, kf)));
-        pfx += ux;
-        pfy += uy;
-        pfz += uz;
+        kf = ff_plus(kf, fmaf(ux, ux, fmaf(uy, uy, __fmul_rn(uz, uz))));
+        pfx = ff_plus(pfx, ux);
+        pfy = ff_plus(pfy, uy);
+        pfz = ff_plus(pfz, uz);
     }
-    ub += (double)uh + (double)ul;
-    const double vals[kBeadVals] = {0.5 * e.mass * (double)kf, ub, e.mass * (double)pfx,
-                                    e.mass * (double)pfy, e.mass * (double)pfz};
+    FF v[kBeadVals] = {kf, ff_norm(uh, ul), pfx, pfy, pfz};
+    if (c.two_ka != 0.f || c.kd != 0.f) v[1] = ff_plus(v[1], ff_from_double(ub));
+    const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kBeadVals; ++k) {
-        const double s = block_sum(vals[k], sh);
-        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kBeadVals + k] = s;
+        v[k] = warp_sum_ff(v[k]);
+        if ((threadIdx.x & 31) == 0) sh[k][w] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kBeadVals) {
+        FF r = sh[threadIdx.x][0];
+#pragma unroll
+        for (int j = 1; j < kRedBlock / 32; ++j) r = ff_plus(r, sh[threadIdx.x][j]);
+        partials[(size_t)blk * kBeadVals + threadIdx.x] = make_float2(r.h, r.l);
     }
 }
 
@@ -274,16 +305,15 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_beads(StateBuf st,
 // final combination.  Per block: the kS (kS + 1) / 2 pair sums (K <= K'),
 // sum T^2 and sum T, each as (lo, hi).
 template <int kS>
-__global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __restrict__ D,
-                                                            int nodes,
-                                                            unsigned long long* __restrict__ part) {
+__device__ __forceinline__ void energy_nodes_block(const long long* __restrict__ D, int nodes,
+                                                   unsigned long long* __restrict__ part, int blk,
+                                                   int nn, U128 (*sh)[kRedBlock / 32]) {
     constexpr int kP = kS * (kS + 1) / 2;
-    __shared__ U128 sh[kRedBlock / 32];
-    U128 acc[kP + 2];
+    constexpr int kQ = kP + 2;
+    U128 acc[kQ];
 #pragma unroll
-    for (int q = 0; q < kP + 2; ++q) acc[q] = U128{0ull, 0ull};
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
-         node += gridDim.x * blockDim.x) {
+    for (int q = 0; q < kQ; ++q) acc[q] = U128{0ull, 0ull};
+    for (int node = blk * kRedBlock + threadIdx.x; node < nodes; node += nn * kRedBlock) {
         unsigned long long d[kS];
         unsigned long long T = 0ull;
 #pragma unroll
@@ -299,67 +329,153 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __r
         u128_add(acc[kP], u128_mul(T, T));
         u128_add(acc[kP + 1], U128{T, 0ull});
     }
+    const int w = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < kP + 2; ++q) {
-        const U128 v = block_sum_u128(acc[q], sh);
-        if (threadIdx.x == 0) {
-            part[((size_t)blockIdx.x * (kP + 2) + q) * 2] = v.lo;
-            part[((size_t)blockIdx.x * (kP + 2) + q) * 2 + 1] = v.hi;
-        }
+    for (int q = 0; q < kQ; ++q) {
+        acc[q] = warp_sum_u128(acc[q]);
+        if ((threadIdx.x & 31) == 0) sh[q][w] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kQ) {
+        U128 r = sh[threadIdx.x][0];
+#pragma unroll
+        for (int j = 1; j < kRedBlock / 32; ++j) u128_add(r, sh[threadIdx.x][j]);
+        part[((size_t)blk * kQ + threadIdx.x) * 2] = r.lo;
+        part[((size_t)blk * kQ + threadIdx.x) * 2 + 1] = r.hi;
     }
 }
 
-__global__ void __launch_bounds__(kRedBlock) k_energy_final(const double* __restrict__ bead_part,
-                                                            int nb,
-                                                            const unsigned long long* __restrict__ node_part,
-                                                            int nn, int nodes, EnergyConsts e,
-                                                            double* __restrict__ out6) {
-    __shared__ double sh[kRedBlock / 32];
-    __shared__ U128 shu[kRedBlock / 32];
-    __shared__ double s_field;
-    double acc[kBeadVals];
-    for (int k = 0; k < kBeadVals; ++k) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) v += bead_part[(size_t)b * kBeadVals + k];
-        acc[k] = block_sum(v, sh);
-    }
-    // the field energy's exact sums, then their combination
-    const int nq = e.S * (e.S + 1) / 2 + 2;
-    double q_chi = 0.0, t2 = 0.0, t1 = 0.0;
-    int k = 0, kp = 0;
-    for (int q = 0; q < nq; ++q) {
-        U128 v{0ull, 0ull};
-        for (int b = threadIdx.x; b < nn; b += blockDim.x)
-            u128_add(v, U128{node_part[((size_t)b * nq + q) * 2],
-                             node_part[((size_t)b * nq + q) * 2 + 1]});
-        const U128 tot = block_sum_u128(v, shu);
-        if (threadIdx.x == 0) {
-            const double val = u128_to_double(tot);
-            if (q < nq - 2) {
-                q_chi += (k == kp ? 1.0 : 2.0) * e.chi[k][kp] * val;
-                if (++kp == e.S) kp = ++k;
-            } else if (q == nq - 2) {
-                t2 = val;
-            } else {
-                t1 = val;
-            }
+// The node sums alone (many species: their accumulators would not fit the
+// register budget of the combined kernel below).
+template <int kS>
+__global__ void __launch_bounds__(kRedBlock) k_energy_nodes(const long long* __restrict__ D,
+                                                            int nodes,
+                                                            unsigned long long* __restrict__ part) {
+    __shared__ U128 sh[kS * (kS + 1) / 2 + 2][kRedBlock / 32];
+    energy_nodes_block<kS>(D, nodes, part, blockIdx.x, gridDim.x, sh);
+    griddep_launch_dependents();
+}
+
+// One launch for the bead and node sums: blocks 0 .. nn - 1 take the nodes
+// (kN species; 0: none), the rest the beads, so the two run side by side.
+template <int kN>
+__global__ void __launch_bounds__(kRedBlock, 4) k_energy_main(StateBuf st,
+                                                              const uint32_t* __restrict__ meta,
+                                                              int n, MeshGeom g,
+                                                              const float4* __restrict__ G,
+                                                              StepConsts c, long long step,
+                                                              EnergyConsts e,
+                                                              float2* __restrict__ bead_part,
+                                                              int nb, const long long* __restrict__ D,
+                                                              unsigned long long* __restrict__ node_part,
+                                                              int nn) {
+    constexpr int kQ = kN * (kN + 1) / 2 + 2;
+    constexpr int kBytes = (int)sizeof(U128) * kQ > (int)sizeof(FF) * kBeadVals
+                               ? (int)sizeof(U128) * kQ
+                               : (int)sizeof(FF) * kBeadVals;
+    __shared__ __align__(16) unsigned char sm[kBytes * (kRedBlock / 32)];
+    int blk = (int)blockIdx.x;
+    if constexpr (kN > 0) {
+        if (blk < nn) {
+            energy_nodes_block<kN>(D, g.nodes, node_part, blk, nn,
+                                   reinterpret_cast<U128(*)[kRedBlock / 32]>(sm));
+            griddep_launch_dependents();
+            return;
         }
+        blk -= nn;
     }
-    if (threadIdx.x == 0) {
+    energy_beads_block(st, meta, n, g, G, c, step, e, bead_part, blk, nb,
+                       reinterpret_cast<FF(*)[kRedBlock / 32]>(sm));
+    // the combining kernel may be scheduled once every block is here
+    griddep_launch_dependents();
+}
+
+// One block: the bead partials (float-float) and the node partials (exact
+// 128-bit) summed over the blocks in a fixed order -- each thread a strided
+// share of the blocks, its loads all in flight together, then its warp, then
+// one lane per value over the warps -- and combined in FP64.
+template <int kS>
+__global__ void __launch_bounds__(kFinalBlock) k_energy_final(const float2* __restrict__ bead_part,
+                                                              int nb,
+                                                              const unsigned long long* __restrict__ node_part,
+                                                              int nn, int nodes, EnergyConsts e,
+                                                              double* __restrict__ out6) {
+    constexpr int kP = kS * (kS + 1) / 2;
+    constexpr int kQ = kP + 2;
+    constexpr int kW = kFinalBlock / 32;
+    __shared__ FF shf[kBeadVals][kW];
+    __shared__ U128 shu[kQ][kW];
+    __shared__ double res[kBeadVals + kQ];
+    griddep_wait();  // launched programmatically after the partial sums
+    FF acc[kBeadVals];
+#pragma unroll
+    for (int k = 0; k < kBeadVals; ++k) acc[k] = FF{0.f, 0.f};
+    for (int b = threadIdx.x; b < nb; b += kFinalBlock) {
+        float2 p[kBeadVals];
+#pragma unroll
+        for (int k = 0; k < kBeadVals; ++k) p[k] = bead_part[(size_t)b * kBeadVals + k];
+#pragma unroll
+        for (int k = 0; k < kBeadVals; ++k) acc[k] = ff_plus(acc[k], FF{p[k].x, p[k].y});
+    }
+    U128 qa[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) qa[q] = U128{0ull, 0ull};
+    for (int b = threadIdx.x; b < nn; b += kFinalBlock) {
+        U128 p[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            p[q] = U128{node_part[((size_t)b * kQ + q) * 2], node_part[((size_t)b * kQ + q) * 2 + 1]};
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) u128_add(qa[q], p[q]);
+    }
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kBeadVals; ++k) {
+        acc[k] = warp_sum_ff(acc[k]);
+        if ((threadIdx.x & 31) == 0) shf[k][w] = acc[k];
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        qa[q] = warp_sum_u128(qa[q]);
+        if ((threadIdx.x & 31) == 0) shu[q][w] = qa[q];
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < kBeadVals) {
+        FF r = shf[t][0];
+        for (int j = 1; j < kW; ++j) r = ff_plus(r, shf[t][j]);
+        res[t] = ff_to_double(r);
+    } else if (t >= 32 && t < 32 + kQ) {  // another warp, so that both run at once
+        U128 r = shu[t - 32][0];
+        for (int j = 1; j < kW; ++j) u128_add(r, shu[t - 32][j]);
+        res[kBeadVals + t - 32] = u128_to_double(r);
+    }
+    __syncthreads();
+    if (t == 0) {
+        double q_chi = 0.0;
+        int q = 0;
+        for (int k = 0; k < kS; ++k)
+            for (int kp = k; kp < kS; ++kp, ++q)
+                q_chi += (k == kp ? 1.0 : 2.0) * e.chi[k][kp] * res[kBeadVals + q];
+        const double t2 = res[kBeadVals + kP], t1 = res[kBeadVals + kP + 1];
         const double pc = e.phi_c;
-        s_field = e.w_scale * (0.5 * e.kT * pc * pc * q_chi +
-                               0.5 * e.inv_kappa * (pc * pc * t2 - 2.0 * pc * t1 + (double)nodes));
-        const double ke = acc[0], ub = acc[1], w = s_field;
+        const double w_f = e.w_scale * (0.5 * e.kT * pc * pc * q_chi +
+                                        0.5 * e.inv_kappa * (pc * pc * t2 - 2.0 * pc * t1 +
+                                                             (double)nodes));
+        const double ke = 0.5 * e.mass * res[0], ub = res[1];
+        const double px = e.mass * res[2], py = e.mass * res[3], pz = e.mass * res[4];
         out6[0] = ke;
         out6[1] = ub;
-        out6[2] = w;
-        out6[3] = ke + ub + w;
-        out6[4] = sqrt(acc[2] * acc[2] + acc[3] * acc[3] + acc[4] * acc[4]);
+        out6[2] = w_f;
+        out6[3] = ke + ub + w_f;
+        out6[4] = sqrt(px * px + py * py + pz * pz);
         out6[5] = e.n > 0 ? 2.0 * ke / (3.0 * (double)e.n) : 0.0;
     }
 }
 
 static int energy_blocks(int count, int per_thread);
+
+int energy_launches(int n, int S) { return S <= 3 ? 2 : (n > 0 ? 3 : 2); }
 
 int energy_partials_needed(int n, int nodes, int S) {
     // bead partials (doubles), then per node block (S (S + 1) / 2 + 2) sums of two words
@@ -380,18 +496,43 @@ void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
                    double* partials, double* out6, cudaStream_t s) {
     const int nb = energy_blocks(n, kBeadsPerThread);
     const int nn = energy_blocks(g.nodes, kNodesPerThread);
-    double* bead_part = partials;
+    // bead partials: kBeadVals float-float pairs (one double's room each) per block
+    float2* bead_part = reinterpret_cast<float2*>(partials);
     unsigned long long* node_part =
         reinterpret_cast<unsigned long long*>(partials + (size_t)nb * kBeadVals);
-    if (nb > 0) k_energy_beads<<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part);
-    switch (e.S) {
-#define HPF_NODES(k) \
+    // up to three species: node and bead sums in one launch; more species:
+    // the node sums in a launch of their own, after the beads
+    if (e.S <= 3) {
+        switch (e.S) {
+#define HPF_MAIN(k)                                                                              \
+    case k:                                                                                      \
+        k_energy_main<k><<<nn + nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part, \
+                                                       nb, D, node_part, nn);                    \
+        break;
+            HPF_MAIN(1) HPF_MAIN(2) HPF_MAIN(3)
+#undef HPF_MAIN
+        }
+    } else {
+        if (nb > 0)
+            k_energy_main<0><<<nb, kRedBlock, 0, s>>>(st, meta, n, g, G, c, step, e, bead_part, nb,
+                                                      D, node_part, 0);
+        switch (e.S) {
+#define HPF_NODES(k)                                                                     \
     case k: k_energy_nodes<k><<<nn, kRedBlock, 0, s>>>(D, g.nodes, node_part); break;
-        HPF_NODES(1) HPF_NODES(2) HPF_NODES(3) HPF_NODES(4)
-        HPF_NODES(5) HPF_NODES(6) HPF_NODES(7) HPF_NODES(8)
+            HPF_NODES(4) HPF_NODES(5) HPF_NODES(6) HPF_NODES(7) HPF_NODES(8)
 #undef HPF_NODES
+        }
     }
-    k_energy_final<<<1, kRedBlock, 0, s>>>(bead_part, nb, node_part, nn, g.nodes, e, out6);
+    switch (e.S) {
+#define HPF_FINAL(k)                                                                        \
+    case k:                                                                                 \
+        launch_pdl(k_energy_final<k>, dim3(1), dim3(kFinalBlock), 0, s, (const float2*)bead_part, \
+                   nb, (const unsigned long long*)node_part, nn, g.nodes, e, out6);         \
+        break;
+        HPF_FINAL(1) HPF_FINAL(2) HPF_FINAL(3) HPF_FINAL(4)
+        HPF_FINAL(5) HPF_FINAL(6) HPF_FINAL(7) HPF_FINAL(8)
+#undef HPF_FINAL
+    }
 }
 
 }  // namespace hpf

@@ -70,12 +70,16 @@ __global__ void k_unpermute(StateBuf st, const uint32_t* __restrict__ meta, int 
 
 // New positions and velocities given in tag order, written in storage order
 // (the inverse of k_unpermute); a non-finite value raises the device flag.
+// With D, each bead's eight CIC weights of the new positions are also added
+// to D[T] (the next field refresh and the observables need that density,
+// which then costs no second pass over the beads).
 __global__ void k_repermute(const float* __restrict__ pos_tag, const float* __restrict__ vel_tag,
-                            const uint32_t* __restrict__ meta, int n, StateBuf st,
-                            int* __restrict__ flag) {
+                            const uint32_t* __restrict__ meta, int n, StateBuf st, MeshGeom g,
+                            unsigned long long* __restrict__ D, int* __restrict__ flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t tag = meta[i] & kTagMask;
+    const uint32_t m = meta[i];
+    const uint32_t tag = m & kTagMask;
     const float x = pos_tag[3 * tag], y = pos_tag[3 * tag + 1], z = pos_tag[3 * tag + 2];
     const float vx = vel_tag[3 * tag], vy = vel_tag[3 * tag + 1], vz = vel_tag[3 * tag + 2];
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
@@ -87,6 +91,12 @@ __global__ void k_repermute(const float* __restrict__ pos_tag, const float* __re
     st.vx[i] = vx;
     st.vy[i] = vy;
     st.vz[i] = vz;
+    if (D) {
+        const AxisCoord ax = axis_coord(x, g.inv_h[0], g.mx, g.inv_m[0]);
+        const AxisCoord ay = axis_coord(y, g.inv_h[1], g.my, g.inv_m[1]);
+        const AxisCoord az = axis_coord(z, g.inv_h[2], g.mz, g.inv_m[2]);
+        scatter_bead(D + (size_t)((m >> kTypeShift) & kTypeMask) * g.nodes, g, ax, ay, az);
+    }
 }
 
 __global__ void k_order(const uint32_t* __restrict__ meta, int n, int32_t* __restrict__ order) {
@@ -124,9 +134,10 @@ void launch_mark_bonds(const int32_t* bonds, long long nb, int n, uint32_t* meta
 }
 
 void launch_repermute(const float* pos_tag, const float* vel_tag, const uint32_t* meta, int n,
-                      StateBuf st, int* flag, cudaStream_t s) {
+                      StateBuf st, const MeshGeom& g, unsigned long long* D, int* flag,
+                      cudaStream_t s) {
     if (n <= 0) return;
-    k_repermute<<<(n + 255) / 256, 256, 0, s>>>(pos_tag, vel_tag, meta, n, st, flag);
+    k_repermute<<<(n + 255) / 256, 256, 0, s>>>(pos_tag, vel_tag, meta, n, st, g, D, flag);
 }
 
 void launch_unpermute(StateBuf st, const uint32_t* meta, int n, float* pos_tag, float* vel_tag,

@@ -207,6 +207,50 @@ def test_mesh_deposited_by_the_step_kernel_is_exact(hpf_gpu, orc, fe, steps):
     assert E[2] == pytest.approx(orc.field_energy(op, Do), rel=1e-12)
 
 
+def test_observed_steps_deposit_their_final_positions(hpf_gpu, orc):
+    """Once hpf_step calls are followed by the observables of their final
+    state, each call's last launch deposits its final positions, and a state
+    upload deposits the new positions in its permutation pass.  The mesh the
+    observables then use must be the exact scatter of the positions, at
+    refresh and other steps, with no standalone scatter after the first
+    observed call; when calls stop being observed the deposits stop, and the
+    observables stay exact."""
+    w = W.diblock(200, 6, 4, 9.0, 9, 1.0, field_every=4)
+    s, d, pp = make(hpf_gpu, w)
+    op = oparams(orc, pp)
+
+    def check():
+        E = s.energy()
+        pos, _, _ = s.get_state()
+        D = s.scatter_density()
+        Do = orc.scatter(op, pos, d["type"])
+        np.testing.assert_array_equal(D, Do)
+        assert E[2] == pytest.approx(orc.field_energy(op, Do), rel=1e-12)
+        return pos
+
+    s.profile(True)
+    s.profile_read()
+    for _ in range(9):      # across two refreshes (steps 4 and 8)
+        s.step(1)
+        check()
+    # the field refresh at step 0 and the first observed call's own scatter
+    assert s.profile_read()["scatter"][1] == 2
+    s.step(1)
+    s.step(1)               # the first call's end deposit went unread
+    s.step(2)
+    pos = check()
+    rng = np.random.default_rng(11)
+    pos2 = (pos + rng.normal(0.0, 0.05, pos.shape)).astype(np.float32)
+    vel2 = rng.normal(0.0, 1.0, pos.shape).astype(np.float32)
+    s.profile_read()
+    s.update_state(pos2, vel2, 6)
+    np.testing.assert_array_equal(check(), pos2)
+    s.step(3)
+    check()
+    assert s.profile_read()["scatter"][1] == 0
+    s.close()
+
+
 def test_long_chains_take_the_halo_kernel(hpf_gpu, orc):
     """Chains longer than 64 beads cannot be packed into warp segments; the
     CTA kernel with recomputed halos advances them."""
