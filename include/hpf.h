@@ -155,8 +155,8 @@ hpf_status hpf_update_state(hpf_ctx* ctx, const float* pos, const float* vel, in
  * from the host, pinned memory) into one of two context-owned staging slots
  * on the context's own copy stream and returns at once.  The caller keeps
  * both arrays valid and unchanged until the copy has run, which is certain
- * once a later synchronising call on this context (hpf_energy_finish,
- * hpf_energy, hpf_get_state) has returned after hpf_apply_state.
+ * once hpf_energy or hpf_get_state, called after hpf_apply_state, has
+ * returned, or hpf_energy_finish of an hpf_energy_start called after it.
  * The copy is ordered after no other work (it runs on a non-blocking stream
  * so that it can overlap the context's): device-resident inputs must be
  * complete when hpf_upload_state is called (their producer's stream
@@ -307,11 +307,14 @@ hpf_status hpf_step_partial(hpf_ctx* ctx, int32_t n_steps, int32_t* steps_done, 
  * Errors: HPF_ERR_INVALID (out NULL), HPF_ERR_STATE, HPF_ERR_NONFINITE, HPF_ERR_CUDA. */
 hpf_status hpf_energy(hpf_ctx* ctx, double out[6]);
 /* hpf_energy in two halves: hpf_energy_start enqueues the kernels and the
- * copy of the six values to a pinned mirror on the context's stream and
- * returns; hpf_energy_finish synchronises the stream and returns the values
- * of the step at which hpf_energy_start was called (work enqueued between the
- * two, e.g. hpf_apply_state and hpf_step of the next step, runs before it
- * returns).  While a start is pending, hpf_energy, hpf_nh_conserved,
+ * copy of the six values (and of the kernels' error word) to pinned mirrors
+ * on the context's stream and returns; hpf_energy_finish waits for those
+ * copies only and returns the values of the step at which hpf_energy_start
+ * was called, with the errors raised up to that point.  Work enqueued
+ * between the two (hpf_upload_state, hpf_apply_state and hpf_step of the
+ * next step) may still be running when it returns, so the next step's work
+ * overlaps the host's reading of this one's; its errors surface at the next
+ * synchronising call.  While a start is pending, hpf_energy, hpf_nh_conserved,
  * hpf_get_thermostat, hpf_set_thermostat, hpf_batch_energy and a second
  * hpf_energy_start return HPF_ERR_STATE.
  * Errors: as hpf_energy; HPF_ERR_STATE (hpf_energy_finish without a start). */

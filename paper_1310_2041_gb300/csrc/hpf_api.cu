@@ -92,6 +92,7 @@ struct hpf_ctx {
     bool up_ready = false;    // stream, events and both slots exist
     bool up_pending = false;
     bool energy_pending = false;  // hpf_energy_start issued, hpf_energy_finish not yet
+    cudaEvent_t energy_ev = nullptr;  // after hpf_energy_start's copies to the host
 };
 
 // Buffers of the learned-propagator driver and the density judge.
@@ -382,30 +383,48 @@ void fill_field_rep(hpf_ctx* c, int tile, int dm, TiledFieldRep& fr, int& blocks
 template <class Params, class Fill>
 int autotune_tile(cudaStream_t s, int S, Fill fill) {
     if (S > 4) return -1;
-    cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    // Each candidate timed launch by launch (an event between launches, so
+    // what counts is a launch's own duration, as in a step loop where the
+    // next kernel waits on the field), the median of kReps launches per
+    // round, the best of kRounds interleaved rounds (a single timing of a few
+    // launches picked a 1.5x slower tile often enough to matter).
+    constexpr int kRounds = 3, kReps = 5;
+    cudaEvent_t ev[kReps + 1];
+    int made = 0;
+    for (; made <= kReps; ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+    if (made <= kReps) {
+        for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
         cudaGetLastError();
         return 0;
     }
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int t = 0; t < field_tile_candidates(); ++t) {
-        Params p;
-        fill(t, p);
-        launch_field_tiled(p, S, t, s);  // warm
-        cudaEventRecord(a, s);
-        for (int rep = 0; rep < 3; ++rep) launch_field_tiled(p, S, t, s);
-        cudaEventRecord(b, s);
-        float ms = 0.f;
-        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess &&
-            ms < best_ms) {
-            best_ms = ms;
-            best = t;
+    const int cands = field_tile_candidates();
+    std::vector<float> score(cands, 1e30f);
+    for (int round = 0; round < kRounds; ++round) {
+        for (int t = 0; t < cands; ++t) {
+            Params p;
+            fill(t, p);
+            launch_field_tiled(p, S, t, s);  // warm
+            cudaEventRecord(ev[0], s);
+            for (int rep = 0; rep < kReps; ++rep) {
+                launch_field_tiled(p, S, t, s);
+                cudaEventRecord(ev[rep + 1], s);
+            }
+            if (cudaEventSynchronize(ev[kReps]) != cudaSuccess) continue;
+            float d[kReps];
+            bool ok = true;
+            for (int rep = 0; rep < kReps; ++rep)
+                ok = ok && cudaEventElapsedTime(&d[rep], ev[rep], ev[rep + 1]) == cudaSuccess;
+            if (!ok) continue;
+            std::sort(d, d + kReps);
+            score[t] = std::min(score[t], d[kReps / 2]);
         }
     }
+    int best = 0;
+    for (int t = 1; t < cands; ++t)
+        if (score[t] < score[best]) best = t;
     cudaGetLastError();
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    for (int k = 0; k <= kReps; ++k) cudaEventDestroy(ev[k]);
     return best;
 }
 
@@ -661,16 +680,21 @@ double nh_pending_half(const hpf_ctx* c, double& xi, double& eta, double& K) {
     return s;
 }
 
+// The kernels' error word as copied to the host.
+hpf_status flag_status(hpf_ctx* c, int word) {
+    if (word & kFlagNonFinite)
+        return fail(c, HPF_ERR_NONFINITE, "a position or velocity became non-finite");
+    if (word & kFlagRange)
+        return fail(c, HPF_ERR_OVERFLOW, "a bead left the +-2^18-cell coordinate range");
+    if (word & kFlagTimeout) return fail(c, HPF_ERR_TIMEOUT, "a device wait timed out");
+    return HPF_OK;
+}
+
 hpf_status check_flags(hpf_ctx* c) {
     CUDA_TRY(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
                                 c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (c->hflag[0] & kFlagNonFinite)
-        return fail(c, HPF_ERR_NONFINITE, "a position or velocity became non-finite");
-    if (c->hflag[0] & kFlagRange)
-        return fail(c, HPF_ERR_OVERFLOW, "a bead left the +-2^18-cell coordinate range");
-    if (c->hflag[0] & kFlagTimeout) return fail(c, HPF_ERR_TIMEOUT, "a device wait timed out");
-    return HPF_OK;
+    return flag_status(c, c->hflag[0]);
 }
 
 // The observables of the current step: kernels and the copies of the six
@@ -697,6 +721,10 @@ hpf_status energy_launch(hpf_ctx* c) {
     if (c->nh)
         CUDA_TRY(c, cudaMemcpyAsync(c->h_nh, c->nh, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                                     c->stream));
+    // the error word as it stands after these kernels, for hpf_energy_finish
+    CUDA_TRY(c, cudaMemcpyAsync(c->hflag + 7, c->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->energy_ev, c->stream));
     return HPF_OK;
 }
 
@@ -773,6 +801,7 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
                                                                    c->p.n_species));
     e = e ? e : cudaMalloc(&c->d_out6, sizeof(double) * 8);
     e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
+    e = e ? e : cudaEventCreateWithFlags(&c->energy_ev, cudaEventDisableTiming);
     if (params->thermostat == 1) {
         e = e ? e : cudaMalloc(&c->nh, sizeof(NhDev));
         e = e ? e : cudaMalloc(&c->nh_part, sizeof(double) * (nh_blocks((int)n) + 1));
@@ -846,6 +875,7 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->d_out6);
     cudaFreeHost(c->h_out6);
+    if (c->energy_ev) cudaEventDestroy(c->energy_ev);
     cudaFree(c->nh);
     cudaFree(c->nh_part);
     cudaFree(c->nh_F);
@@ -1302,7 +1332,10 @@ hpf_status hpf_energy_finish(hpf_ctx* c, double out[6]) {
     if (!c || !out) return fail(c, HPF_ERR_INVALID, "out is required");
     if (!c->energy_pending) return fail(c, HPF_ERR_STATE, "no hpf_energy_start pending");
     c->energy_pending = false;
-    const hpf_status s = check_flags(c);
+    // waits for the observables' own copies only: work enqueued after
+    // hpf_energy_start (the next step's upload, permutation, step) keeps running
+    CUDA_TRY(c, cudaEventSynchronize(c->energy_ev));
+    const hpf_status s = flag_status(c, c->hflag[7]);
     if (s != HPF_OK) return s;
     energy_finish(c, out);
     return HPF_OK;

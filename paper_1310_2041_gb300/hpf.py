@@ -337,8 +337,9 @@ class System:
         """Start copying new positions and velocities (tag order); returns at
         once.  The copy is not ordered after other GPU work: device arrays
         must be complete when this is called.  The arrays are kept referenced
-        here until a synchronising call after apply_state (energy_finish,
-        energy, get_state)."""
+        here until a synchronising call has covered the apply_state that
+        consumes them (energy or get_state after it, or energy_finish of an
+        energy_start issued after it)."""
         pp, a = _ptr(pos, np.float32, (self.n, 3), "pos")
         vp, b = _ptr(vel, np.float32, (self.n, 3), "vel")
         self._check(self.lib.hpf_upload_state(self.h, pp, vp))
@@ -355,19 +356,25 @@ class System:
             self._up = []
         return self._up
 
-    def _synced(self):
-        # uploads applied before a synchronising call have been copied
-        self._up = [u for u in self._uploads() if not u[1]]
+    def _synced(self, applied=None):
+        # uploads applied before a synchronising point have been copied
+        # (applied: the uploads that had been applied at that point)
+        done = applied if applied is not None else [u for u in self._uploads() if u[1]]
+        self._up = [u for u in self._uploads() if not any(u is d for d in done)]
 
     def energy_start(self):
         """Enqueue the observables of the current step (see energy_finish)."""
         self._check(self.lib.hpf_energy_start(self.h))
+        self._energy_applied = [u for u in self._uploads() if u[1]]
 
     def energy_finish(self):
-        """The six observables of the step energy_start was called at."""
+        """The six observables of the step energy_start was called at; waits
+        only for the work enqueued up to energy_start (later work, such as the
+        next step's apply_state and step, may still be running)."""
         out = (ctypes.c_double * 6)()
         self._check(self.lib.hpf_energy_finish(self.h, out))
-        self._synced()
+        self._synced(getattr(self, "_energy_applied", []))
+        self._energy_applied = []
         return np.array(list(out))
 
     def get_state(self, pos=None, vel=None):
