@@ -44,6 +44,11 @@ struct hpf_ctx {
     bool want_end_mesh = false;
     bool end_mesh_unused = false;     // the last call's end deposit is still unread
     long long end_of_call_step = -1;  // the step the last hpf_step call ended on
+    // observables' bead partials formed by the step launch that ended at
+    // obs_step (k_step_warp_obs), obs_nb CTAs' worth
+    float2* obs_part = nullptr;
+    long long obs_step = -1;
+    int obs_nb = 0;
     float4* G = nullptr;              // field mesh (ghosted)
     float4* field_stage = nullptr;    // dense copy of the field for hpf_field's output
     FieldCoef* d_coef = nullptr;      // the stencil coefficients in device memory
@@ -566,7 +571,8 @@ hpf_status sort_beads(hpf_ctx* c) {
 // field (1 - j/K) G + (j/K) lerp_G2 at window step j, lerp_j0 at the first
 // sub-step, lerp_inv_k = 1/K.
 hpf_status advance(hpf_ctx* c, int chunk, bool fuse, const float4* lerp_G2 = nullptr,
-                   int lerp_j0 = 0, float lerp_inv_k = 0.f) {
+                   int lerp_j0 = 0, float lerp_inv_k = 0.f, bool obs = false) {
+    c->obs_step = -1;
     {
         StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? 1 : 0);
         if (c->warp_mode) {
@@ -596,6 +602,10 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse, const float4* lerp_G2 = nul
             if (lerp_G2)
                 launch_step_warp_lerp(p, lerp_G2, lerp_j0, lerp_inv_k, c->C,
                                       step_thermostat(c->sc), c->stream);
+            else if (obs)
+                c->obs_nb = launch_step_warp_obs(p, c->C, step_thermostat(c->sc), c->obs_part,
+                                                 (float)c->ec.half_dt_m, bond_ff(c->ec),
+                                                 c->stream);
             else
                 launch_step_warp_single(p, c->C, step_thermostat(c->sc), c->stream);
         } else
@@ -611,6 +621,7 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse, const float4* lerp_G2 = nul
         c->mesh_step = c->step;
         c->next_zero = false;
     }
+    if (obs && c->obs_nb > 0) c->obs_step = c->step;
     return HPF_OK;
 }
 
@@ -618,6 +629,7 @@ hpf_status advance(hpf_ctx* c, int chunk, bool fuse, const float4* lerp_G2 = nul
 // one, see k_nh.cu); with fuse the last launch deposits its positions into
 // the other mesh (which must be zero).
 hpf_status advance_nh(hpf_ctx* c, int chunk, bool fuse) {
+    c->obs_step = -1;
     {
         StageScope sc(c, HPF_STAGE_STEP, c->n > 0 ? chunk + 1 : 0);
         if (c->n > 0) {
@@ -710,10 +722,17 @@ hpf_status energy_launch(hpf_ctx* c) {
     if (c->mesh_step != c->step && c->end_of_call_step == c->step) c->want_end_mesh = true;
     if ((s = scatter_current(c)) != HPF_OK) return s;
     {
-        StageScope sc(c, HPF_STAGE_ENERGY, energy_launches(c->n, c->S));
-        launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step,
-                      reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh)), c->ec,
-                      c->partials, c->d_out6, c->stream);
+        const long long* Dm = reinterpret_cast<const long long*>(mesh_buf(c, c->dmesh));
+        if (c->obs_step == c->step) {
+            // the bead terms came with the step launch: node sums and combination
+            StageScope sc(c, HPF_STAGE_ENERGY, 2);
+            launch_energy_nodes_only(c->n, c->geom, Dm, c->ec, c->obs_part, c->obs_nb,
+                                     c->partials, c->d_out6, c->stream);
+        } else {
+            StageScope sc(c, HPF_STAGE_ENERGY, energy_launches(c->n, c->S));
+            launch_energy(cur_state(c), c->meta, c->n, c->geom, c->G, c->sc, c->step, Dm, c->ec,
+                          c->partials, c->d_out6, c->stream);
+        }
     }
     LAUNCH_CHECK(c);
     CUDA_TRY(c, cudaMemcpyAsync(c->h_out6, c->d_out6, sizeof(double) * 6, cudaMemcpyDeviceToHost,
@@ -802,6 +821,7 @@ hpf_status hpf_init(const hpf_params* params, void* stream, hpf_ctx** out) {
     e = e ? e : cudaMalloc(&c->d_out6, sizeof(double) * 8);
     e = e ? e : cudaMallocHost(&c->h_out6, sizeof(double) * 8);
     e = e ? e : cudaEventCreateWithFlags(&c->energy_ev, cudaEventDisableTiming);
+    e = e ? e : cudaMalloc(&c->obs_part, sizeof(float2) * kBeadVals * step_warp_grid_cap());
     if (params->thermostat == 1) {
         e = e ? e : cudaMalloc(&c->nh, sizeof(NhDev));
         e = e ? e : cudaMalloc(&c->nh_part, sizeof(double) * (nh_blocks((int)n) + 1));
@@ -876,6 +896,7 @@ hpf_status hpf_destroy(hpf_ctx* c) {
     cudaFree(c->d_out6);
     cudaFreeHost(c->h_out6);
     if (c->energy_ev) cudaEventDestroy(c->energy_ev);
+    cudaFree(c->obs_part);
     cudaFree(c->nh);
     cudaFree(c->nh_part);
     cudaFree(c->nh_F);
@@ -981,6 +1002,7 @@ hpf_status hpf_set_state(hpf_ctx* c, const float* pos, const float* vel, const i
     if (s2 != HPF_OK) return s2;
     c->step = step;
     c->field_step = -1;
+    c->obs_step = -1;
     if (c->nh) {
         // a loaded state starts with the thermostat at rest (hpf_set_thermostat restores one)
         CUDA_TRY(c, cudaMemsetAsync(c->nh, 0, sizeof(NhDev), c->stream));
@@ -1008,6 +1030,7 @@ static hpf_status repermute_deposit(hpf_ctx* c, const float* pos_tag, const floa
     c->step = step;
     c->mesh_step = step;
     c->end_mesh_unused = false;
+    c->obs_step = -1;
     return HPF_OK;
 }
 
@@ -1194,9 +1217,14 @@ hpf_status hpf_forces(hpf_ctx* c, float* F_out, int32_t which) {
 // launch of an hpf_step call, when calls have been followed by the
 // observables of their final state (the other mesh is cleared first if
 // need be: a memset costs far less than the scatter it saves).
-static hpf_status plan_deposit(hpf_ctx* c, long long chunk, bool last, bool& fuse) {
+// Such a launch, when it does not end on a refresh step (where F_n needs the
+// new field), also forms the observables' bead terms of its final state
+// (obs) if the step kernel supports them here: warp form, Langevin or no
+// thermostat, bonds only, interpolated-gradient force.
+static hpf_status plan_deposit(hpf_ctx* c, long long chunk, bool last, bool& fuse, bool& obs) {
     const bool refresh_end = (c->step + chunk) % c->p.field_every == 0;
     fuse = refresh_end && c->next_zero;
+    obs = false;
     if (!fuse && last && c->want_end_mesh && c->n > 0) {
         if (!c->next_zero) {
             CUDA_TRY(c, cudaMemsetAsync(mesh_buf(c, c->dmesh ^ 1), 0,
@@ -1205,7 +1233,11 @@ static hpf_status plan_deposit(hpf_ctx* c, long long chunk, bool last, bool& fus
         }
         fuse = true;
     }
-    if (fuse && last && !refresh_end) c->end_mesh_unused = true;
+    if (fuse && last && !refresh_end) {
+        c->end_mesh_unused = true;
+        obs = c->warp_mode && !c->nh && step_thermostat(c->sc) <= 1 && c->sc.force_mode == 0 &&
+              bonded_level(c->sc) == 0;
+    }
     return HPF_OK;
 }
 
@@ -1229,8 +1261,8 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
             if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
                 if ((s = sort_beads(c)) != HPF_OK) return s;
             }
-            bool fuse;
-            if ((s = plan_deposit(c, chunk, chunk == left, fuse)) != HPF_OK) return s;
+            bool fuse, obs;
+            if ((s = plan_deposit(c, chunk, chunk == left, fuse, obs)) != HPF_OK) return s;
             if ((s = advance_nh(c, (int)chunk, fuse)) != HPF_OK) return s;
             left -= chunk;
         }
@@ -1248,9 +1280,9 @@ hpf_status hpf_step(hpf_ctx* c, int32_t n_steps) {
         if (c->p.sort_every > 0 && c->step - c->last_sort_step >= c->p.sort_every) {
             if ((s = sort_beads(c)) != HPF_OK) return s;
         }
-        bool fuse;
-        if ((s = plan_deposit(c, chunk, chunk == left, fuse)) != HPF_OK) return s;
-        if ((s = advance(c, (int)chunk, fuse)) != HPF_OK) return s;
+        bool fuse, obs;
+        if ((s = plan_deposit(c, chunk, chunk == left, fuse, obs)) != HPF_OK) return s;
+        if ((s = advance(c, (int)chunk, fuse, nullptr, 0, 0.f, obs)) != HPF_OK) return s;
         left -= chunk;
     }
     c->end_of_call_step = c->step;
@@ -1621,6 +1653,7 @@ int batch_thermostat(hpf_batch* b) {
 
 void batch_advance(hpf_batch* b, long long chunk, bool fuse) {
     for (auto* c : b->rep) {
+        c->obs_step = -1;
         c->cur ^= 1;
         c->step += chunk;
         if (fuse) {
@@ -1816,6 +1849,7 @@ hpf_status hpf_batch_step(hpf_batch* b, int32_t n_steps) {
                     c0->launches[HPF_STAGE_OTHER] += 2;
                 }
                 for (auto* c : b->rep) {
+                    c->obs_step = -1;
                     c->step += 2 * fe * pairs;
                     c->mesh_step = c->step;
                     c->next_zero = false;

@@ -525,6 +525,123 @@ __device__ __forceinline__ void gather_field_mode(const float4* __restrict__ Gt,
     else gather_field(Gt, g, ax, ay, az, fx, fy, fz);
 }
 
+// ------------------------------------------------------------------ float-float sums
+
+// Per-block partial sums of the observables' bead terms, in this order:
+// |v_n|^2 (kinetic energy without m/2), bond energy, momentum x, y, z
+// (without m); each a float-float pair (h, l).
+constexpr int kBeadVals = 5;
+
+
+// Knuth's two-sum: s + t == a + b exactly (round-to-nearest, no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    t = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Float-float sums (h, l): the partial sums of every observable are carried as
+// pairs of FP32 numbers, added with two-sum and renormalised, so that the
+// block and warp reductions run on the FP32 pipe (this GPU's FP64 rate is
+// 1/64 of its FP32 rate) with about 2^-45 relative error per addition, and in
+// a fixed tree, so that every bit is the same from run to run.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_norm(float s, float t) {
+    const float h = __fadd_rn(s, t);
+    return FF{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FF ff_plus(FF a, float x) {
+    float s, t;
+    two_sum(a.h, x, s, t);
+    return ff_norm(s, __fadd_rn(t, a.l));
+}
+__device__ __forceinline__ FF ff_plus(FF a, FF b) {
+    float s, t;
+    two_sum(a.h, b.h, s, t);
+    return ff_norm(s, __fadd_rn(t, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ff_from_double(double v) {
+    const float h = (float)v;
+    return FF{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.h + (double)v.l; }
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_plus(v, FF{__shfl_down_sync(0xffffffffu, v.h, o),
+                          __shfl_down_sync(0xffffffffu, v.l, o)});
+    return v;  // lane 0
+}
+
+// The bond energy k (|d| - r0)^2 of d = x_i - x_j in float-float arithmetic
+// (pairs of FP32 numbers), added to the float-float sum (uh, ul): each
+// component of d exactly by two-sum, |d|^2 with the exact error of each
+// square (FMA) to about 2^-46, |d| from the correctly rounded square root plus
+// its residual, |d| - r0 = a + b against r0 = r0_hi + r0_lo, renormalised
+// by two-sum; then (a + b)^2 = a^2 + 2ab + b^2 with |b| <= ulp(a)/2 -- a^2
+// exactly as p + pe,
+// 2ab rounded (2^-24 of a term 2^-23 below a^2), b^2 (2^-48 of a^2)
+// dropped -- times k = k_hi + k_lo, and a two-sum accumulation.  About
+// 2^-45 relative per term, like an FP64 evaluation, with no FP64 instruction
+// (this GPU's FP64 rate is 1/64 of its FP32 rate).
+struct BondFF {
+    float r0_hi, r0_lo;  // r0 as a float-float pair
+    float k_hi, k_lo;    // the bond constant k as a float-float pair
+};
+__device__ __forceinline__ void bond_energy_ff(float xi, float yi, float zi, float xj, float yj,
+                                               float zj, const BondFF& e, float& uh,
+                                               float& ul) {
+    float hx, lx, hy, ly, hz, lz;
+    two_sum(xi, -xj, hx, lx);
+    two_sum(yi, -yj, hy, ly);
+    two_sum(zi, -zj, hz, lz);
+    float H = 0.f, L = 0.f;
+    const float hs[3] = {hx, hy, hz}, ls[3] = {lx, ly, lz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float p = __fmul_rn(hs[c], hs[c]);
+        const float pe = fmaf(hs[c], hs[c], -p);                        // exact error of h^2
+        const float rest = fmaf(2.0f * hs[c], ls[c], fmaf(ls[c], ls[c], pe));  // 2hl + l^2 + pe
+        float t;
+        two_sum(H, p, H, t);
+        L = __fadd_rn(L, __fadd_rn(t, rest));
+    }
+    const float H2 = __fadd_rn(H, L);
+    const float L2 = __fsub_rn(L, __fsub_rn(H2, H));
+    float a, b;
+    if (H2 > 0.f) {
+        const float r = sqrtf(H2);
+        const float res = __fadd_rn(fmaf(-r, r, H2), L2);  // H2 - r^2 is exact
+        const float r_lo = 0.5f * res * rsqrtf(H2);
+        two_sum(r, -e.r0_hi, a, b);
+        b = __fadd_rn(b, __fsub_rn(r_lo, e.r0_lo));
+    } else {  // coincident beads: |d| - r0 = -r0
+        a = -e.r0_hi;
+        b = -e.r0_lo;
+    }
+    // renormalised, so that |b| <= ulp(a)/2 also when |d| is close to r0 (then
+    // the two parts of the difference are of similar size)
+    two_sum(a, b, a, b);
+    const float p = __fmul_rn(a, a);
+    const float pe = fmaf(a, a, -p);
+    const float q = fmaf(2.0f * a, b, pe);
+    const float u = __fmul_rn(e.k_hi, p);
+    const float ue = fmaf(e.k_hi, p, -u);
+    const float w = fmaf(e.k_hi, q, fmaf(e.k_lo, p, ue));
+    float s, t;
+    two_sum(uh, u, s, t);
+    t = __fadd_rn(t, __fadd_rn(ul, w));
+    uh = __fadd_rn(s, t);
+    ul = __fsub_rn(t, __fsub_rn(uh, s));
+}
+
+__host__ __device__ __forceinline__ BondFF bond_ff(const EnergyConsts& e) {
+    return BondFF{e.r0_hi, e.r0_lo, e.bond_k_hi, e.bond_k_lo};
+}
+
 // Harmonic bond U = k (r - r0)^2 seen from bead i: F_i += -2k (1 - r0 / r) d, d = x_i - x_j,
 // with 1 / r from the hardware reciprocal square root (2 ulp: about 1e-6 of a
 // typical bond force).
@@ -851,6 +968,12 @@ int launch_sort(const SortBufs& b, StateBuf in, StateBuf out, const uint32_t* me
 int step_halo_max();
 void launch_step_warp_batch(const BatchStepParams& p, int max_seg_total, int therm,
                             cudaStream_t s);
+// A single context's launch that also writes the observables' bead partials
+// of its final state (kBeadVals float-float pairs per CTA); returns the CTA
+// count.  Bonds only, force_mode 0, therm 0 or 1.
+int launch_step_warp_obs(const SingleStepParams& p, int max_seg, int therm, float2* part,
+                         float half_dt_m, const BondFF& bond, cudaStream_t s);
+int step_warp_grid_cap();  // CTAs of the persistent step grid on this device
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm, cudaStream_t s);
 // A learned window: the field (1 - j/K) G + j/K G2 at window step j (j0 at the
 // launch's first sub-step, inv_k = 1/K); a single context, force_mode 0.
@@ -873,6 +996,9 @@ bool make_mesh_tensor_map(CUtensorMap* map, const long long* D, const MeshGeom& 
 void tile_grid(const MeshGeom& g, int tile, int* tiles_x, int* tiles_y, int* blocks);
 int energy_partials_needed(int n, int nodes, int S);
 int energy_launches(int n, int S);  // kernels launch_energy issues
+void launch_energy_nodes_only(int n, MeshGeom g, const long long* D, const EnergyConsts& e,
+                              const float2* bead_part, int nb_bead, double* partials,
+                              double* out6, cudaStream_t s);
 
 // learned density propagator (the network lives in k_prop.cu)
 bool prop_mesh_is(const hpf_prop* p, const MeshGeom& g);

@@ -8,114 +8,12 @@ namespace hpf {
 
 constexpr int kRedBlock = 256;    // the bead and node kernels
 constexpr int kFinalBlock = 1024;  // the one block that combines their partials
-constexpr int kBeadVals = 5;       // kinetic, bond, px, py, pz
 // Grid-stride shares (on average) of a bead or node thread: small, so that a
 // million beads make about 2000 blocks, which the SMs take in several waves
 // with little left over for the last one (at 8 beads a thread the 489 blocks
 // of a million beads came to just over one wave of three blocks per SM).
 constexpr int kBeadsPerThread = 2;
 constexpr int kNodesPerThread = 2;
-
-// Knuth's two-sum: s + t == a + b exactly (round-to-nearest, no contraction).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
-    s = __fadd_rn(a, b);
-    const float bv = __fsub_rn(s, a);
-    const float av = __fsub_rn(s, bv);
-    t = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
-}
-
-// Float-float sums (h, l): the partial sums of every observable are carried as
-// pairs of FP32 numbers, added with two-sum and renormalised, so that the
-// block and warp reductions run on the FP32 pipe (this GPU's FP64 rate is
-// 1/64 of its FP32 rate) with about 2^-45 relative error per addition, and in
-// a fixed tree, so that every bit is the same from run to run.
-struct FF {
-    float h, l;
-};
-__device__ __forceinline__ FF ff_norm(float s, float t) {
-    const float h = __fadd_rn(s, t);
-    return FF{h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ FF ff_plus(FF a, float x) {
-    float s, t;
-    two_sum(a.h, x, s, t);
-    return ff_norm(s, __fadd_rn(t, a.l));
-}
-__device__ __forceinline__ FF ff_plus(FF a, FF b) {
-    float s, t;
-    two_sum(a.h, b.h, s, t);
-    return ff_norm(s, __fadd_rn(t, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ FF ff_from_double(double v) {
-    const float h = (float)v;
-    return FF{h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.h + (double)v.l; }
-__device__ __forceinline__ FF warp_sum_ff(FF v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = ff_plus(v, FF{__shfl_down_sync(0xffffffffu, v.h, o),
-                          __shfl_down_sync(0xffffffffu, v.l, o)});
-    return v;  // lane 0
-}
-
-// The bond energy k (|d| - r0)^2 of d = x_i - x_j in float-float arithmetic
-// (pairs of FP32 numbers), added to the float-float sum (uh, ul): each
-// component of d exactly by two-sum, |d|^2 with the exact error of each
-// square (FMA) to about 2^-46, |d| from the correctly rounded square root plus
-// its residual, |d| - r0 = a + b against r0 = r0_hi + r0_lo, renormalised
-// by two-sum; then (a + b)^2 = a^2 + 2ab + b^2 with |b| <= ulp(a)/2 -- a^2
-// exactly as p + pe,
-// 2ab rounded (2^-24 of a term 2^-23 below a^2), b^2 (2^-48 of a^2)
-// dropped -- times k = k_hi + k_lo, and a two-sum accumulation.  About
-// 2^-45 relative per term, like an FP64 evaluation, with no FP64 instruction
-// (this GPU's FP64 rate is 1/64 of its FP32 rate).
-__device__ __forceinline__ void bond_energy_ff(float xi, float yi, float zi, float xj, float yj,
-                                               float zj, const EnergyConsts& e, float& uh,
-                                               float& ul) {
-    float hx, lx, hy, ly, hz, lz;
-    two_sum(xi, -xj, hx, lx);
-    two_sum(yi, -yj, hy, ly);
-    two_sum(zi, -zj, hz, lz);
-    float H = 0.f, L = 0.f;
-    const float hs[3] = {hx, hy, hz}, ls[3] = {lx, ly, lz};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float p = __fmul_rn(hs[c], hs[c]);
-        const float pe = fmaf(hs[c], hs[c], -p);                        // exact error of h^2
-        const float rest = fmaf(2.0f * hs[c], ls[c], fmaf(ls[c], ls[c], pe));  // 2hl + l^2 + pe
-        float t;
-        two_sum(H, p, H, t);
-        L = __fadd_rn(L, __fadd_rn(t, rest));
-    }
-    const float H2 = __fadd_rn(H, L);
-    const float L2 = __fsub_rn(L, __fsub_rn(H2, H));
-    float a, b;
-    if (H2 > 0.f) {
-        const float r = sqrtf(H2);
-        const float res = __fadd_rn(fmaf(-r, r, H2), L2);  // H2 - r^2 is exact
-        const float r_lo = 0.5f * res * rsqrtf(H2);
-        two_sum(r, -e.r0_hi, a, b);
-        b = __fadd_rn(b, __fsub_rn(r_lo, e.r0_lo));
-    } else {  // coincident beads: |d| - r0 = -r0
-        a = -e.r0_hi;
-        b = -e.r0_lo;
-    }
-    // renormalised, so that |b| <= ulp(a)/2 also when |d| is close to r0 (then
-    // the two parts of the difference are of similar size)
-    two_sum(a, b, a, b);
-    const float p = __fmul_rn(a, a);
-    const float pe = fmaf(a, a, -p);
-    const float q = fmaf(2.0f * a, b, pe);
-    const float u = __fmul_rn(e.bond_k_hi, p);
-    const float ue = fmaf(e.bond_k_hi, p, -u);
-    const float w = fmaf(e.bond_k_hi, q, fmaf(e.bond_k_lo, p, ue));
-    float s, t;
-    two_sum(uh, u, s, t);
-    t = __fadd_rn(t, __fadd_rn(ul, w));
-    uh = __fadd_rn(s, t);
-    ul = __fsub_rn(t, __fsub_rn(uh, s));
-}
 
 // Exact unsigned 128-bit sums (the field energy's node sums).
 struct U128 {
@@ -216,7 +114,7 @@ __device__ __forceinline__ void energy_beads_block(const StateBuf& st,
         if (m & kBondNext) {
             const float xj = st.x[i + 1], yj = st.y[i + 1], zj = st.z[i + 1];
             bond_force(x - xj, y - yj, z - zj, c.two_k, c.r0, fx, fy, fz);
-            bond_energy_ff(x, y, z, xj, yj, zj, e, uh, ul);
+            bond_energy_ff(x, y, z, xj, yj, zj, bond_ff(e), uh, ul);
         }
         if (c.two_ka != 0.f) {
             angle_forces_of(st, meta, i, m, c, fx, fy, fz);
@@ -532,6 +430,33 @@ void launch_energy(StateBuf st, const uint32_t* meta, int n, MeshGeom g, const f
         HPF_FINAL(1) HPF_FINAL(2) HPF_FINAL(3) HPF_FINAL(4)
         HPF_FINAL(5) HPF_FINAL(6) HPF_FINAL(7) HPF_FINAL(8)
 #undef HPF_FINAL
+    }
+}
+
+// The node sums and the combination, with bead partials formed elsewhere
+// (nb_bead CTAs' worth, by the step launch that ended at this state).
+void launch_energy_nodes_only(int n, MeshGeom g, const long long* D, const EnergyConsts& e,
+                              const float2* bead_part, int nb_bead, double* partials,
+                              double* out6, cudaStream_t s) {
+    const int nb = energy_blocks(n, kBeadsPerThread);
+    const int nn = energy_blocks(g.nodes, kNodesPerThread);
+    unsigned long long* node_part =
+        reinterpret_cast<unsigned long long*>(partials + (size_t)nb * kBeadVals);
+    switch (e.S) {
+#define HPF_ONLY(k)                                                                         \
+    case k:                                                                                 \
+        if (k <= 3)                                                                         \
+            k_energy_main<(k <= 3 ? k : 0)><<<nn, kRedBlock, 0, s>>>(                       \
+                StateBuf{}, nullptr, 0, g, nullptr, StepConsts{}, 0, e, nullptr, 0, D,      \
+                node_part, nn);                                                             \
+        else                                                                                \
+            k_energy_nodes<k><<<nn, kRedBlock, 0, s>>>(D, g.nodes, node_part);              \
+        launch_pdl(k_energy_final<k>, dim3(1), dim3(kFinalBlock), 0, s, bead_part, nb_bead, \
+                   (const unsigned long long*)node_part, nn, g.nodes, e, out6);             \
+        break;
+        HPF_ONLY(1) HPF_ONLY(2) HPF_ONLY(3) HPF_ONLY(4)
+        HPF_ONLY(5) HPF_ONLY(6) HPF_ONLY(7) HPF_ONLY(8)
+#undef HPF_ONLY
     }
 }
 

@@ -481,17 +481,18 @@ __device__ __forceinline__ void cell_check(Bead& b, const float4* __restrict__ G
     f2 = __fsub_rn(s2, flz);
 }
 
-// Kick of one bead: field (cached cell polynomial at offsets f), friction,
+// Force on one bead: field (cached cell polynomial at offsets f), friction,
 // noise (nx, ny, nz) and the bond force (bx, by, bz) already summed over its
-// chain neighbours.  Andersen (kTherm 2): a colliding bead's on-step velocity
-// is sqrt(kT/m) (nx, ny, nz) before the second half kick.
+// chain neighbours.
 template <int kTherm, int kForce, int kLerp = 0>
-__device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
-                                          float ny, float nz, float bx, float by, float bz,
-                                          const StepConsts& c, const MeshGeom& g,
-                                          const float4* __restrict__ cache, int slot,
-                                          bool coll, float a = 0.f) {
-    float fx = -c.fric * b.vx, fy = -c.fric * b.vy, fz = -c.fric * b.vz;
+__device__ __forceinline__ void bead_force(const Bead& b, float f0, float f1, float f2, float nx,
+                                           float ny, float nz, float bx, float by, float bz,
+                                           const StepConsts& c, const MeshGeom& g,
+                                           const float4* __restrict__ cache, int slot, float a,
+                                           float& fx, float& fy, float& fz) {
+    fx = -c.fric * b.vx;
+    fy = -c.fric * b.vy;
+    fz = -c.fric * b.vz;
     if (kLerp) {
         // the field (1 - a) G0 + a G2: P0 + a (P2 - P0) of the two cached polynomials
         constexpr int st = 2 * kWarpBlock;
@@ -516,6 +517,19 @@ __device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2,
     fx += bx;
     fy += by;
     fz += bz;
+}
+
+// Kick of one bead by that force.  Andersen (kTherm 2): a colliding bead's
+// on-step velocity is sqrt(kT/m) (nx, ny, nz) before the second half kick.
+template <int kTherm, int kForce, int kLerp = 0>
+__device__ __forceinline__ void kick_bead(Bead& b, float f0, float f1, float f2, float nx,
+                                          float ny, float nz, float bx, float by, float bz,
+                                          const StepConsts& c, const MeshGeom& g,
+                                          const float4* __restrict__ cache, int slot,
+                                          bool coll, float a = 0.f) {
+    float fx, fy, fz;
+    bead_force<kTherm, kForce, kLerp>(b, f0, f1, f2, nx, ny, nz, bx, by, bz, c, g, cache, slot, a,
+                                      fx, fy, fz);
     if (kTherm == 2 && coll) {
         const float h = 0.5f * c.dt_m;
         b.vx = fmaf(h, fx, c.sig_v * nx);
@@ -551,8 +565,70 @@ __device__ __forceinline__ void finish_bead(const Bead& b, long long i, StateBuf
     }
 }
 
+// The observables' bead terms of a segment's final state (what the next
+// sub-step's force evaluation would form, never applied): F_n at the final
+// positions with step `step`'s noise, the on-step velocity
+// v_n = v + dt/(2m) F_n, |v_n|^2 and v_n added to the thread's float-float
+// sums, and the energy of each bond once (the bond to the next bead: b0's to
+// b1, b1's to the next lane's b0).  Bonds only, interpolated-gradient force,
+// no Andersen redraw.
+struct ObsArgs {
+    float2* part;     // [gridDim.x][kBeadVals] float-float block partials
+    float half_dt_m;  // dt / (2m)
+    BondFF bond;
+};
+
+template <int kTherm>
+__device__ __forceinline__ void observe_segment(Bead& b0, Bead& b1, bool a0, bool a1, bool p0,
+                                                bool n0, bool n1, long long step,
+                                                const MeshGeom& g, const float4* __restrict__ G,
+                                                const StepConsts& c, float4* wcache, int tid,
+                                                const ObsArgs& o, FF* acc) {
+    const int lane = tid & 31;
+    float w0x, w0y, w0z, w1x, w1y, w1z;
+    warp_bonded_forces<0>(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, p0, n0, n1, c, lane, w0x, w0y, w0z,
+                          w1x, w1y, w1z);
+    float f00, f01, f02, f10, f11, f12;
+    cell_check<0>(b0, G, g, wcache, tid, f00, f01, f02);
+    cell_check<0>(b1, G, g, wcache, kWarpBlock + tid, f10, f11, f12);
+    float g0x = 0.f, g0y = 0.f, g0z = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
+    if (kTherm == 1) {
+        gauss3(c, b0.m & kTagMask, step, g0x, g0y, g0z);
+        gauss3(c, b1.m & kTagMask, step, g1x, g1y, g1z);
+    }
+    float F0x, F0y, F0z, F1x, F1y, F1z;
+    bead_force<kTherm, 0>(b0, f00, f01, f02, g0x, g0y, g0z, w0x, w0y, w0z, c, g, wcache, tid, 0.f,
+                          F0x, F0y, F0z);
+    bead_force<kTherm, 0>(b1, f10, f11, f12, g1x, g1y, g1z, w1x, w1y, w1z, c, g, wcache,
+                          kWarpBlock + tid, 0.f, F1x, F1y, F1z);
+    // the next lane's first bead (every lane takes part in the shuffles)
+    const float qx = __shfl_down_sync(0xffffffffu, b0.x, 1);
+    const float qy = __shfl_down_sync(0xffffffffu, b0.y, 1);
+    const float qz = __shfl_down_sync(0xffffffffu, b0.z, 1);
+    float uh = acc[1].h, ul = acc[1].l;
+    if (n0) bond_energy_ff(b0.x, b0.y, b0.z, b1.x, b1.y, b1.z, o.bond, uh, ul);
+    if (n1) bond_energy_ff(b1.x, b1.y, b1.z, qx, qy, qz, o.bond, uh, ul);
+    acc[1] = FF{uh, ul};
+    const float hf = o.half_dt_m;
+    if (a0) {
+        const float ux = fmaf(hf, F0x, b0.vx), uy = fmaf(hf, F0y, b0.vy), uz = fmaf(hf, F0z, b0.vz);
+        acc[0] = ff_plus(acc[0], fmaf(ux, ux, fmaf(uy, uy, __fmul_rn(uz, uz))));
+        acc[2] = ff_plus(acc[2], ux);
+        acc[3] = ff_plus(acc[3], uy);
+        acc[4] = ff_plus(acc[4], uz);
+    }
+    if (a1) {
+        const float ux = fmaf(hf, F1x, b1.vx), uy = fmaf(hf, F1y, b1.vy), uz = fmaf(hf, F1z, b1.vz);
+        acc[0] = ff_plus(acc[0], fmaf(ux, ux, fmaf(uy, uy, __fmul_rn(uz, uz))));
+        acc[2] = ff_plus(acc[2], ux);
+        acc[3] = ff_plus(acc[3], uy);
+        acc[4] = ff_plus(acc[4], uz);
+    }
+}
+
 // One warp advances one segment (whole chains, base .. base + cnt) by n_sub steps.
-template <int kTherm, int kForce, int kBonded, int kLerp = 0>
+// kObs: also the observables' terms of the final state (observe_segment).
+template <int kTherm, int kForce, int kBonded, int kLerp = 0, int kObs = 0>
 __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateBuf& out,
                                                 const uint32_t* __restrict__ meta, int base,
                                                 int cnt, int n_sub, long long step0,
@@ -561,7 +637,9 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
                                                 unsigned long long* __restrict__ D_next,
                                                 int* __restrict__ flag, float4* wcache, int tid,
                                                 const float4* __restrict__ G2 = nullptr,
-                                                int lerp_j0 = 0, float lerp_inv_k = 0.f) {
+                                                int lerp_j0 = 0, float lerp_inv_k = 0.f,
+                                                const ObsArgs* obs = nullptr,
+                                                FF* obs_acc = nullptr) {
     const int lane = tid & 31;
     const float nan = __int_as_float(0x7fc00000);
     const int j0 = 2 * lane, j1 = j0 + 1;
@@ -616,6 +694,9 @@ __device__ __forceinline__ void advance_segment(const StateBuf& in, const StateB
         b1.y = fmaf(c.dt, b1.vy, b1.y);
         b1.z = fmaf(c.dt, b1.vz, b1.z);
     }
+    if constexpr (kObs != 0)
+        observe_segment<kTherm>(b0, b1, a0, a1, p0, n0, n1, step0 + n_sub, g, G, c, wcache, tid,
+                                *obs, obs_acc);
     if (a0) finish_bead(b0, (long long)base + j0, out, g, D_next, flag);
     if (a1) finish_bead(b1, (long long)base + j1, out, g, D_next, flag);
 }
@@ -660,6 +741,45 @@ __global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_batch(
                                                  rp.seg_start[s],
                                 rp.seg_count[s], p.n_sub, step0, rp.g, rp.G, rp.c,
                                 p.fuse ? rp.D[p.dnext] : nullptr, p.flag, wcache, tid);
+    }
+}
+
+// A single context's launch that also forms the observables' bead terms of
+// its final state (bonds only, interpolated-gradient force, Langevin or no
+// thermostat): each thread's float-float sums over its segments, then the
+// block's, one partial per CTA for k_energy_final.
+template <int kTherm>
+__global__ void __launch_bounds__(kWarpBlock, 2) k_step_warp_obs(
+    const __grid_constant__ SingleStepParams p, const ObsArgs o) {
+    griddep_wait();
+    griddep_launch_dependents();
+    extern __shared__ float4 wcache[];
+    __shared__ FF sh[kBeadVals][kWarpBlock / 32];
+    const int tid = threadIdx.x;
+    const BatchStepRep& rp = p.rep[0];
+    const int total = *rp.n_seg;
+    const int warps_total = gridDim.x * (kWarpBlock / 32);
+    const long long step0 = p.step0;
+    FF acc[kBeadVals];
+#pragma unroll
+    for (int k = 0; k < kBeadVals; ++k) acc[k] = FF{0.f, 0.f};
+    for (int w = blockIdx.x * (kWarpBlock / 32) + (tid >> 5); w < total; w += warps_total)
+        advance_segment<kTherm, 0, 0, 0, 1>(rp.st[p.cur], rp.st[p.cur ^ 1], rp.meta,
+                                            rp.seg_start[w], rp.seg_count[w], p.n_sub, step0,
+                                            rp.g, rp.G, rp.c, p.fuse ? rp.D[p.dnext] : nullptr,
+                                            p.flag, wcache, tid, nullptr, 0, 0.f, &o, acc);
+    const int wi = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kBeadVals; ++k) {
+        acc[k] = warp_sum_ff(acc[k]);
+        if ((tid & 31) == 0) sh[k][wi] = acc[k];
+    }
+    __syncthreads();
+    if (tid < kBeadVals) {
+        FF r = sh[tid][0];
+#pragma unroll
+        for (int j = 1; j < kWarpBlock / 32; ++j) r = ff_plus(r, sh[tid][j]);
+        o.part[(size_t)blockIdx.x * kBeadVals + tid] = make_float2(r.h, r.l);
     }
 }
 
@@ -736,6 +856,10 @@ static int warp_grid_cap() {
     once_per_device(once, [dev] {
         warp_attrs<HPF_MAX_REPLICAS>();
         warp_attrs<1>();
+        cudaFuncSetAttribute(k_step_warp_obs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
+        cudaFuncSetAttribute(k_step_warp_obs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWarpSmem);
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -810,6 +934,20 @@ void launch_step_warp_lerp(const SingleStepParams& p, const float4* G2, int j0, 
         else if (bonded == 1) launch_lerp_k<0, 1>(p, G2, j0, inv_k, blocks, s);
         else launch_lerp_k<0, 0>(p, G2, j0, inv_k, blocks, s);
     }
+}
+
+int step_warp_grid_cap() { return warp_grid_cap(); }
+
+int launch_step_warp_obs(const SingleStepParams& p, int max_seg, int therm, float2* part,
+                         float half_dt_m, const BondFF& bond, cudaStream_t s) {
+    if (max_seg <= 0 || p.n_sub <= 0) return 0;
+    const int cap = warp_grid_cap();
+    const int need = (max_seg + kWarpBlock / 32 - 1) / (kWarpBlock / 32);
+    const int blocks = need < cap ? need : cap;
+    const ObsArgs o{part, half_dt_m, bond};
+    if (therm == 1) launch_pdl(k_step_warp_obs<1>, blocks, kWarpBlock, kWarpSmem, s, p, o);
+    else launch_pdl(k_step_warp_obs<0>, blocks, kWarpBlock, kWarpSmem, s, p, o);
+    return blocks;
 }
 
 void launch_step_warp_single(const SingleStepParams& p, int max_seg, int therm,

@@ -251,6 +251,59 @@ def test_observed_steps_deposit_their_final_positions(hpf_gpu, orc):
     s.close()
 
 
+def test_observed_steps_form_the_observables_in_the_step_launch(hpf_gpu, orc):
+    """An observed hpf_step call whose launch does not end on a refresh step
+    forms the observables' bead terms (F_n on the field in force, the on-step
+    velocity, |v_n|^2, momentum, bond energies) in that launch; hpf_energy
+    then runs only the node sums and the combination (two launches where the
+    full pass takes three with four species).  At every step the observables
+    must match the oracle (given the field of the last refresh) at the usual
+    bars, and the full pass of a batch member on the same trajectory (a
+    batch's steps never form them) to its summation order."""
+    chi = [[0.0, 0.8, 0.3, 0.5], [0.8, 0.0, 0.6, 0.2], [0.3, 0.6, 0.0, 0.9],
+           [0.5, 0.2, 0.9, 0.0]]
+    w = W.Workload("abcd", [(136, [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4)], 9.0, 9, 4, chi, 0.1,
+                   field_every=4, steps=10)
+    s, d, pp = make(hpf_gpu, w, data=thermal(W.generate(w)))
+    bt = hpf_gpu.Batch([hpf_gpu.make_params(**pp)])
+    rep = bt.replica(0)
+    rep.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
+    op = oparams(orc, pp)
+    s.profile(True)
+    s.profile_read()
+    ref = d["pos"]  # positions the field in force was formed from
+    for k in range(7):
+        s.step(1)
+        bt.step(1)
+        E = s.energy()
+        launches = s.profile_read()["energy"][1]
+        pos, vel, st = s.get_state()
+        if st % w.field_every == 0:
+            ref = pos
+        Vr, Gr = orc.field(op, orc.scatter(op, ref, d["type"]))
+        Eo = orc.energy(op, pos, vel, d["type"], d["bonds"], Vr, Gr, st)
+        assert E[1] == pytest.approx(Eo[1], rel=1e-12, abs=1e-12)
+        assert E[2] == pytest.approx(Eo[2], rel=1e-12)
+        assert E[0] == pytest.approx(Eo[0], rel=1e-7)
+        assert E[3] == pytest.approx(Eo[3], rel=1e-7)
+        assert E[4] == pytest.approx(Eo[4], rel=1e-4, abs=1e-6 * w.n_beads)
+        assert E[5] == pytest.approx(Eo[5], rel=1e-7)
+        # the first observed call and refresh steps take the full pass
+        fused = k > 0 and st % w.field_every != 0
+        assert launches == (2 if fused else 3)
+        pb, vb, sb = rep.get_state()
+        assert sb == st
+        np.testing.assert_array_equal(pb, pos)
+        np.testing.assert_array_equal(vb, vel)
+        Eb = rep.energy()
+        assert Eb[1] == pytest.approx(E[1], rel=1e-12)
+        assert Eb[2] == E[2]
+        assert Eb[0] == pytest.approx(E[0], rel=1e-9)
+        assert Eb[4] == pytest.approx(E[4], rel=1e-6, abs=1e-9 * w.n_beads)
+    s.close()
+    bt.close()
+
+
 def test_long_chains_take_the_halo_kernel(hpf_gpu, orc):
     """Chains longer than 64 beads cannot be packed into warp segments; the
     CTA kernel with recomputed halos advances them."""

@@ -6,11 +6,11 @@ makes the step wait for it.  hpf_energy_start / hpf_energy_finish split
 hpf_energy, and hpf_energy_finish waits only for the work enqueued up to
 its start.  A pipelined loop (the upload of step k + 1 issued before the
 observables of step k are read), and a deeper one (step k + 1's permutation
-and step also enqueued before they are read), must give, bit for bit, the
-observables and final state of the serial loop (hpf_update_state, hpf_step,
-hpf_energy), with
-a different input array every step, so that a wrong slot or an unfinished
-copy would show.  Misuse is an error, not a race.
+and step and step k + 2's upload also enqueued before they are read), must
+give, bit for bit, the observables and final state of the serial loop
+(hpf_update_state, hpf_step, hpf_energy), with a different input array
+every step, so that a wrong slot or an unfinished copy would show.  Misuse
+is an error, not a race.
 """
 import numpy as np
 import pytest
@@ -65,8 +65,9 @@ def test_pipelined_loop_equals_the_serial_loop(hpf_gpu, device_inputs):
     np.testing.assert_array_equal(np.array(Ea), np.array(Eb))
     np.testing.assert_array_equal(pa, pb)
     np.testing.assert_array_equal(va, vb)
-    # deeper: step k + 1's permutation and step enqueued before step k's
-    # observables are read (hpf_energy_finish waits for its own copies only)
+    # deeper: step k + 1's permutation and step, and step k + 2's upload,
+    # enqueued before step k's observables are read (hpf_energy_finish waits
+    # for its own copies only)
     c = hpf_gpu.System(hpf_gpu.make_params(**pp))
     c.set_state(d["pos"], d["vel"], d["type"], d["bonds"])
     Ec = []
@@ -79,11 +80,11 @@ def test_pipelined_loop_equals_the_serial_loop(hpf_gpu, device_inputs):
         if k + 1 < len(host):
             c.apply_state(3 * (k + 1))
             c.step(2)
+            if k + 2 < len(host):
+                c.upload_state(*host[k + 2])
         Ec.append(c.energy_finish())
         if k + 1 < len(host):
             c.energy_start()
-            if k + 2 < len(host):
-                c.upload_state(*host[k + 2])
     pc, vc, sc = c.get_state()
     assert sa == sc
     np.testing.assert_array_equal(np.array(Ea), np.array(Ec))
