@@ -643,7 +643,7 @@ hpf_status advance_nh(hpf_ctx* c, int chunk, bool fuse) {
             p.c = c->sc;
             p.t = c->nhc;
             p.nh = c->nh;
-            p.part = c->nh_part;
+            p.part = reinterpret_cast<float2*>(c->nh_part);  // one double's room per block
             p.flag = c->dflag;
             // one launch; the state and (after a force evaluation) the force buffers swap
             auto launch = [&](bool kick_drift, bool force_kick, unsigned long long* D_next) {

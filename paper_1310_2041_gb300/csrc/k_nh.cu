@@ -7,8 +7,8 @@
 // step is split where K is needed:
 //   force_kick : F_n at the current positions (stored for the next launch);
 //                v^E = v + dt/(2m) F_n; the kinetic energy of v^E is summed
-//                (FP32 over each thread's few beads, FP64 from the warp sums
-//                on, block partials added in a fixed order) and the last
+//                (float-float pairs of FP32 numbers through the thread, warp
+//                and block, block partials added in a fixed order) and the last
 //                block to finish applies the two thermostat half steps T(dt/2)
 //                (the end of step n - 1, the start of step n), writing the
 //                velocity scales s1, s2 and xi, eta;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
     // scales are read only after it has completed
     griddep_wait();
     griddep_launch_dependents();
-    __shared__ double s_ke[kNhBlock / 32];
+    __shared__ FF s_ke[kNhBlock / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31;
     Drift d;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
     d.s2 = d.on ? p.nh->s2 : 1.0f;
     d.hdt_m = 0.5f * p.c.dt_m;
     d.dt = p.c.dt;
-    float ke = 0.0f;  // this thread's beads, FP32 (a few beads); FP64 from the warp sum up
+    FF ke{0.f, 0.f};  // this thread's beads, float-float (FP32 pipe) up to the last block
 #pragma unroll 2
     for (int i = blockIdx.x * kNhBlock + tid; i < p.n; i += gridDim.x * kNhBlock) {
         const uint32_t m = p.meta[i];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
             vx = fmaf(d.hdt_m, fx, vx);
             vy = fmaf(d.hdt_m, fy, vy);
             vz = fmaf(d.hdt_m, fz, vz);
-            ke += fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+            ke = ff_plus(ke, fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
         }
         p.out.x[i] = x;
         p.out.y[i] = y;
@@ -196,15 +196,16 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
         }
     }
     if (!p.force_kick) return;
-    // the kinetic-energy sum: warp, block, then the blocks' partials in order
-    double kd = (double)ke;
-    for (int o = 16; o > 0; o >>= 1) kd += __shfl_down_sync(0xffffffffu, kd, o);
-    if (lane == 0) s_ke[tid >> 5] = kd;
+    // the kinetic-energy sum in float-float on the FP32 pipe (this GPU's FP64
+    // rate is 1/64 of its FP32 rate): warp, block, then the blocks' partials
+    // in a fixed order
+    ke = warp_sum_ff(ke);
+    if (lane == 0) s_ke[tid >> 5] = ke;
     __syncthreads();
     if (tid == 0) {
-        double b = 0.0;
-        for (int k = 0; k < kNhBlock / 32; ++k) b += s_ke[k];
-        p.part[blockIdx.x] = b;
+        FF b = s_ke[0];
+        for (int k = 1; k < kNhBlock / 32; ++k) b = ff_plus(b, s_ke[k]);
+        p.part[blockIdx.x] = make_float2(b.h, b.l);
         __threadfence();
         s_last = atomicAdd(&p.nh->ticket, 1u) == gridDim.x - 1;
     }
@@ -213,15 +214,19 @@ __global__ void __launch_bounds__(kNhBlock) k_nh_step(const __grid_constant__ Nh
     // the last block sums the partials in a fixed order (strided per thread,
     // then the same shuffle tree and warp order as above)
     __threadfence();
-    double v = 0.0;
-    for (int k = tid; k < (int)gridDim.x; k += kNhBlock) v += __ldcg(&p.part[k]);
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    FF v{0.f, 0.f};
+    for (int k = tid; k < (int)gridDim.x; k += kNhBlock) {
+        const float2 q = __ldcg(&p.part[k]);
+        v = ff_plus(v, FF{q.x, q.y});
+    }
+    v = warp_sum_ff(v);
     __syncthreads();
     if (lane == 0) s_ke[tid >> 5] = v;
     __syncthreads();
     if (tid != 0) return;
-    double sum = 0.0;
-    for (int k = 0; k < kNhBlock / 32; ++k) sum += s_ke[k];
+    FF tot = s_ke[0];
+    for (int k = 1; k < kNhBlock / 32; ++k) tot = ff_plus(tot, s_ke[k]);
+    const double sum = ff_to_double(tot);
     double K = 0.5 * p.t.mass * sum;
     double xi = p.nh->xi, eta = p.nh->eta;
     p.nh->ke = K;

@@ -30,7 +30,7 @@ struct NhParams {
     StepConsts c;
     NhConsts t;
     NhDev* nh;
-    double* part;     // [blocks] kinetic-energy partials
+    float2* part;     // [blocks] kinetic-energy partials (float-float)
     unsigned long long* D_next;  // deposit the final positions (kick_drift-only launches)
     int* flag;
     int kick_drift;  // v = s2 (s1 v) + dt/(2m) F; x += dt v
