@@ -149,6 +149,50 @@ def test_forces_match_oracle(hpf_gpu, orc, w, which):
     assert ok, worst
 
 
+def species_workload(S):
+    """Chains of 10 beads cycling through S species; a seeded symmetric chi."""
+    rng = np.random.default_rng(100 + S)
+    chi = rng.uniform(0.2, 1.5, (S, S))
+    chi = np.triu(chi, 1)
+    chi = (chi + chi.T).tolist()
+    return W.Workload(f"species{S}", [(90, [k % S for k in range(10)])], 7.9, 8, S, chi, 0.1,
+                      field_every=3, steps=10)
+
+
+@pytest.mark.parametrize("S", [1, 5, 8])
+def test_species_counts_outside_the_tiled_range(hpf_gpu, orc, S):
+    """One species and more than four take other paths (the untiled stencil,
+    the node sums in a launch of their own, per-S instantiations): the mesh
+    is exact, the field, forces and observables match the oracle at the
+    usual bars, and so does a 10-step trajectory."""
+    w = species_workload(S)
+    s, d, pp = make(hpf_gpu, w, data=thermal(W.generate(w)))
+    op = oparams(orc, pp)
+    Do = orc.scatter(op, d["pos"], d["type"])
+    np.testing.assert_array_equal(s.scatter_density(), Do)
+    Vo, Go = orc.field(op, Do)
+    Fm = s.field(D_in=Do)
+    scale = np.max(np.abs(Go)) + 1e-30
+    np.testing.assert_allclose(Fm[..., :3], Go, rtol=1e-5, atol=1e-6 * scale)
+    np.testing.assert_allclose(Fm[..., 3], Vo, rtol=1e-5, atol=1e-6 * (np.max(np.abs(Vo)) + 1))
+    Fo = orc.field_force(op, d["pos"], d["type"], Go) + orc.bond_force(op, d["pos"], d["bonds"])
+    ok, worst = force_ok(s.forces(3), Fo)
+    assert ok, worst
+    s.close()
+    s, d, pp = make(hpf_gpu, w, data=d)
+    E = s.energy()
+    Eo = orc.energy(op, d["pos"], d["vel"], d["type"], d["bonds"], Vo, Go, 0)
+    assert E[1] == pytest.approx(Eo[1], rel=1e-12, abs=1e-12)
+    assert E[2] == pytest.approx(Eo[2], rel=1e-12)
+    assert E[0] == pytest.approx(Eo[0], rel=1e-7)
+    s.step(10)
+    pos, vel, _ = s.get_state()
+    po, vo, _ = orc.run(op, d["pos"], d["vel"], d["type"], d["bonds"], 0, 10)
+    assert np.max(np.abs(pos - po)) <= 1e-4
+    assert np.max(np.abs(vel - vo)) <= 1e-4
+    s.close()
+
+
 def test_uniform_lattice_gives_exactly_zero_field_force(hpf_gpu):
     M = 6
     g = np.stack(np.meshgrid(np.arange(M), np.arange(M), np.arange(M), indexing="ij"), -1)
