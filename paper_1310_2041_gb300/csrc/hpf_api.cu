@@ -493,6 +493,7 @@ hpf_status run_field(hpf_ctx* c) {
     c->next_zero = true;
     c->field_valid = true;
     c->field_step = c->step;
+    c->obs_step = -1;  // observables' terms formed on the previous field are stale
     return HPF_OK;
 }
 
@@ -502,6 +503,7 @@ hpf_status run_field(hpf_ctx* c) {
 hpf_status field_from(hpf_ctx* c, const unsigned long long* D, const CUtensorMap& tm, bool tm_ok,
                       unsigned long long* D_clear, float4* G_out = nullptr) {
     float4* G = G_out ? G_out : c->G;
+    if (!G_out) c->obs_step = -1;  // the context's field changes
     {
         StageScope sc(c, HPF_STAGE_FIELD, 1);
         if (c->S <= 4 && c->field_tile >= 0) {
@@ -1294,6 +1296,7 @@ hpf_status hpf_set_tag_base(hpf_ctx* c, int64_t tag_base) {
     if (tag_base < 0 || tag_base + (int64_t)c->n > (int64_t)HPF_MAX_BEADS + 1)
         return fail(c, HPF_ERR_INVALID, "tag_base + n_beads must stay within 2^24");
     c->sc.tag_base = (uint32_t)tag_base;
+    c->obs_step = -1;  // the noise of F_n depends on it
     return HPF_OK;
 }
 
@@ -1604,6 +1607,7 @@ hpf_status batch_refresh(hpf_batch* b) {
         c->next_zero = true;
         c->field_valid = true;
         c->field_step = c->step;
+        c->obs_step = -1;
     }
     return HPF_OK;
 }

@@ -344,6 +344,20 @@ def test_observed_steps_form_the_observables_in_the_step_launch(hpf_gpu, orc):
         assert Eb[2] == E[2]
         assert Eb[0] == pytest.approx(E[0], rel=1e-9)
         assert Eb[4] == pytest.approx(E[4], rel=1e-6, abs=1e-9 * w.n_beads)
+    # a step whose terms were formed in the launch, then another field put in
+    # force (an injected mesh): the observables take the full pass on it
+    s.step(2)
+    pos, vel, st = s.get_state()
+    assert st % w.field_every != 0
+    Dj = orc.scatter(op, d["pos"], d["type"])
+    s.field(D_in=Dj)
+    s.profile_read()
+    E = s.energy()
+    assert s.profile_read()["energy"][1] == 3
+    Vj, Gj = orc.field(op, Dj)
+    Eo = orc.energy(op, pos, vel, d["type"], d["bonds"], Vj, Gj, st)
+    assert E[0] == pytest.approx(Eo[0], rel=1e-7)
+    assert E[2] == pytest.approx(Eo[2], rel=1e-12)
     s.close()
     bt.close()
 
