@@ -570,14 +570,21 @@ def run_ours(args):
                         sysm.upload_state(host["pos"], host["vel"])
 
         pipelined(3)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pipelined(args.e2e_steps)
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+        # three timed loops, the median reported (the host-to-device link and
+        # the host's wake-ups make single loops vary by a few per cent)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pipelined(args.e2e_steps)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        te = statistics.median(times)
         e2e = {"value": n_total * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 6 * 8,
                "steps": args.e2e_steps,
+               "loops": [n_total * args.e2e_steps / t for t in times],
+               "of": f"median of {len(times)} timed loops of {args.e2e_steps} steps",
                "path": "per step: hpf_upload_state(positions and velocities from pinned "
                        "host, double-buffered, issued while the previous step runs) + "
                        "hpf_apply_state + hpf_step(1) + hpf_energy_start/finish (to host; "
