@@ -83,7 +83,8 @@ __device__ __forceinline__ double dihedral_energy_fp64(const StateBuf& st, int i
     return e.dih_k * (1.0 + cn * e.dih_cd + sn * e.dih_sd);
 }
 
-// Per bead: F_n exactly as the step kernel forms it, the on-step velocity
+// Per bead: F_n with the terms the step kernel's kick uses (bonds, the field
+// by a direct trilinear gather, friction, step n's noise), the on-step velocity
 // v_n = v + dt/(2m) F_n, then kinetic energy, momentum and the bond energy of
 // the bond to the next bead (each bond once).  The bond energy is formed in
 // float-float (bond_energy_ff), the angle and dihedral energies in FP64, all
@@ -190,9 +191,8 @@ __device__ __forceinline__ void energy_beads_block(const StateBuf& st,
     }
 }
 
-// Per node: the field-energy density of the mesh D (FP64 from exact integers).
-// Instantiated per species count: this GPU's FP64 rate is low, and loops to
-// the species bound would issue predicated FP64 work for absent species.
+// Per node: the exact integer sums behind the field energy, instantiated per
+// species count (the kS (kS + 1) / 2 + 2 sums are register arrays).
 // The field energy from exact integer sums.  With phi_K = phi_c D_K (D the
 // int64 fixed-point density, non-negative) and T = sum_K D_K per node,
 //   W / (rho0 h^3) = 1/2 kT phi_c^2 sum_KK' chi_KK' S_KK'
