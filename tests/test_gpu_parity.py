@@ -295,6 +295,30 @@ def test_observed_steps_deposit_their_final_positions(hpf_gpu, orc):
     s.close()
 
 
+@pytest.mark.parametrize("therm", [dict(thermostat=1, nh_tau=0.3),
+                                   dict(thermostat=2, andersen_nu=1.0)], ids=["nh", "andersen"])
+def test_observed_steps_deposit_under_the_other_thermostats(hpf_gpu, orc, therm):
+    """Nose-Hoover (its own launch sequence) and Andersen (no fused
+    observables) also deposit the final positions of observed calls: the mesh
+    the observables use is the exact scatter of the positions at every step,
+    and no standalone scatter runs after the first observed call."""
+    w = W.diblock(200, 6, 4, 9.0, 9, 1.0, field_every=4)
+    s, d, pp = make(hpf_gpu, w, **therm)
+    op = oparams(orc, pp)
+    s.profile(True)
+    s.profile_read()
+    for _ in range(7):
+        s.step(1)
+        E = s.energy()
+        pos, _, _ = s.get_state()
+        D = s.scatter_density()
+        Do = orc.scatter(op, pos, d["type"])
+        np.testing.assert_array_equal(D, Do)
+        assert E[2] == pytest.approx(orc.field_energy(op, Do), rel=1e-12)
+    assert s.profile_read()["scatter"][1] == 2
+    s.close()
+
+
 def test_observed_steps_form_the_observables_in_the_step_launch(hpf_gpu, orc):
     """An observed hpf_step call whose launch does not end on a refresh step
     forms the observables' bead terms (F_n on the field in force, the on-step
