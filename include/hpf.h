@@ -331,8 +331,9 @@ hpf_status hpf_energy_finish(hpf_ctx* ctx, double out[6]);
  * n) on the kinetic energy K of v^E, each
  *   xi += (h/2) G(K); v *= exp(-xi h); K *= exp(-2 xi h); eta += xi h; xi += (h/2) G(K),
  *   G(K) = (2K / (g kT) - 1) / tau^2, h = dt/2;
- * then v <- v + dt/(2m) F_n; x <- x + dt v.  K is summed in FP64 over the
- * beads in a fixed order.  hpf_energy reports the step's on-step quantities
+ * then v <- v + dt/(2m) F_n; x <- x + dt v.  K is summed over the beads in
+ * a fixed order in float-float arithmetic (pairs of FP32 numbers, about
+ * 2^-45 relative per addition) and used in FP64.  hpf_energy reports the step's on-step quantities
  * after the pending half step (kinetic energy, |P| and T of s v^E).  Chains
  * of any length; not available in batches or learned windows.
  *
