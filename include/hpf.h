@@ -292,8 +292,16 @@ hpf_status hpf_set_tag_base(hpf_ctx* ctx, int64_t tag_base);
  * its thermostat couples every bead at every step), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step_partial(hpf_ctx* ctx, int32_t n_steps, int32_t* steps_done, int64_t** mesh);
 
-/* Observables at the current step, reduced in a fixed order (synchronises;
- * the values do not depend on the GPU):
+/* Observables at the current step, reduced in a fixed order (synchronises).
+ * The bead terms are summed in float-float arithmetic over a grid set by n
+ * alone (the bits do not depend on the GPU), except when the last hpf_step
+ * call's final launch formed them itself: once calls are followed by the
+ * observables of their end state, such a launch that does not end on a
+ * refresh step (Langevin or no thermostat, bonds only, force_mode 0) forms
+ * them from its final positions, and their order then follows the
+ * persistent step grid (the SM count); either way the same quantities to
+ * rounding.  Likewise such calls deposit their final positions, so the field
+ * term needs no separate scatter.  Values:
  * out[0] kinetic energy of v_n = v_{n-1/2} + dt/(2m) F_n (F_n as in hpf_step;
  *   with Andersen, a bead colliding at step n counts its redrawn velocity),
  * out[1] bonded energy: bonds sum k (r - r0)^2 (float-float, ~1e-14 relative
