@@ -253,7 +253,12 @@ hpf_status hpf_forces(hpf_ctx* ctx, float* F_out, int32_t which);
  * friction or noise force; a bead collides at step n when the uniform of word
  * 0 of Philox4x32-10(counter = (tag, n lo, n hi, 1)) is below fl32(nu dt),
  * and then takes v <- sqrt(kT/m) xi + dt/(2m) F (xi as above): its on-step
- * velocity redrawn from the Maxwell distribution.
+ * velocity redrawn from the Maxwell distribution.  A launch that ends on a
+ * refresh step deposits its final positions for that refresh.  Once
+ * hpf_energy has been called on the state an hpf_step call ended at, later
+ * calls' last launches also deposit their final positions (and, see
+ * hpf_energy, form the observables' bead terms), until a call's deposit goes
+ * unread before the next call; results do not depend on it.
  * Errors: HPF_ERR_INVALID (n_steps < 0), HPF_ERR_STATE, HPF_ERR_CUDA. */
 hpf_status hpf_step(hpf_ctx* ctx, int32_t n_steps);
 
