@@ -138,8 +138,9 @@ hpf_status hpf_set_state(hpf_ctx* ctx, const float* pos, const float* vel, const
 /* Replace positions and velocities ([n][3] float32 in tag order, host or
  * device) and set the step, keeping the species, the bonds and the bead order
  * of the last sort: the light way to continue from modified coordinates
- * (hpf_set_state reloads the topology and re-sorts).  The density and the
- * field of the old positions are dropped.  Asynchronous: a non-finite value
+ * (hpf_set_state reloads the topology and re-sorts).  The field of the old
+ * positions is dropped; the density of the new ones is deposited in the same
+ * pass that puts them into the library's bead order.  Asynchronous: a non-finite value
  * is reported by the next synchronising call (HPF_ERR_NONFINITE), and the
  * caller's buffers must stay unchanged until the stream reaches the call.
  * Errors: HPF_ERR_INVALID, HPF_ERR_STATE (no hpf_set_state yet), HPF_ERR_CUDA. */
