@@ -42,6 +42,18 @@ STEP_SRC = [os.path.join(ROOT, "paper_1310_2041_gb300", "csrc", f)
             for f in ("k_step.cu", "hpf_internal.cuh")]
 
 
+# When a list, the runners append their line here instead of printing it
+# (the default run gathers the other configurations' lines into its own).
+_CAPTURE = None
+
+
+def emit(line):
+    if _CAPTURE is not None:
+        _CAPTURE.append(line)
+    else:
+        print(json.dumps(line), flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -55,6 +67,9 @@ def parse():
                          "all-reduce at every refresh, strong scaling) or run N replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the short runs of the 8.1M ternary blend and "
+                         "the 64-replica batch whose lines ride along under \"configs\"")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--thermostat", default="langevin", choices=["langevin", "nh", "andersen"],
                     help="plain workloads: Langevin (the default), Nose-Hoover or Andersen NVT")
@@ -617,7 +632,7 @@ def run_ours(args):
                            "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        emit(line)
     sysm.close()
     if dist:
         dist.destroy_process_group()
@@ -726,7 +741,7 @@ def run_batch(args):
                        "speedup_vs_plain": value / plain_value},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": int(sum(v[1] for v in prof.values())), "clocks": clk}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -1020,6 +1035,45 @@ def run_propagator(args):
     return 0
 
 
+def run_default_with_configs(args):
+    """The headline run, then short runs of the 8.1M ternary blend (config 3,
+    the workload whose state exceeds L2) and of the 64-replica batch (config
+    4), each with its roofline and CPU baseline, attached to the headline's
+    line under "configs"; the headline's keys are those of the run alone."""
+    import copy
+    global _CAPTURE
+    _CAPTURE = []
+    try:
+        run_ours(args)
+        lines = _CAPTURE
+    finally:
+        _CAPTURE = None
+    if not lines:
+        return 0
+    head = lines[0]
+    extras = {}
+    for name, fn, over in (("ternary_8m", run_ours,
+                            dict(workload="ternary_8m", steps=20, warmup=5, no_e2e=True)),
+                           ("replicas64", run_batch,
+                            dict(workload="replicas64", steps=40, warmup=10))):
+        a2 = copy.copy(args)
+        for k, v in over.items():
+            setattr(a2, k, v)
+        _CAPTURE = []
+        try:
+            fn(a2)
+            sub = _CAPTURE[0] if _CAPTURE else None
+            extras[name] = ({k: v for k, v in sub.items() if k not in ("metric", "e2e")}
+                            if sub else {"error": "no line"})
+        except Exception as exc:  # the headline line is printed regardless
+            extras[name] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        finally:
+            _CAPTURE = None
+    head["configs"] = extras
+    emit(head)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1030,6 +1084,11 @@ def main():
         return run_learned(args)
     if args.workload == "propagator":
         return run_propagator(args)
+    default = (args.workload == "a10b10_1m" and args.gpus == 1 and args.thermostat == "langevin"
+               and not args.angle_k and not args.dihedral_k
+               and int(os.environ.get("WORLD_SIZE", "1")) == 1)
+    if default and not args.no_configs:
+        return run_default_with_configs(args)
     return run_ours(args)
 
 
